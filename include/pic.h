@@ -1,0 +1,195 @@
+/*
+ * pic.h -- C ABI of libpic: the particle step of particle-in-tree (PIT) and
+ * particle-in-dual-tree (PIDT) on a k = 3 spacetree, for one GB300 (sm_103a).
+ *
+ * Method: Weinzierl, Verleye, Henri, Roose, "Two Particle-in-Grid Realisations
+ * on Spacetrees", arXiv:1508.02435.  One time step is the PIC cycle of
+ * Section 3: deposit rho = sum_i R(x_i) with d-linear R (item 1), solve
+ * L(V) = rho (item 2, auxiliary: a caller hook or built-in Jacobi sweeps),
+ * E = -grad V and gather E_i = R^T(x_i) E (item 3), push d_t v = (q/m) E,
+ * d_t x = v (item 4), then re-bin every particle -- with no bound on how many
+ * cells it moved -- into the leaf that covers it (PIT, Algorithm 1 / Theorem 1)
+ * or into the dual cell of the vertex on that leaf's level that covers it
+ * (PIDT, Algorithms 2-3 / Theorem 2).  Buckets are stable: stayers keep their
+ * order at the head of their bucket, movers follow in storage order.
+ *
+ * Conventions shared by every call:
+ *   - Domain [0,1)^d, d in {2,3}, periodic.  k = 3: a refined cell has 3^d
+ *     children, local digit l = i0 + 3 i1 + 9 i2 (x fastest) (Section 4).
+ *   - Arrays of particle or vertex quantities are structure-of-arrays,
+ *     [axis][n] (axis-major, each axis contiguous).
+ *   - `where` = PIC_HOST (pageable or pinned host memory) or PIC_DEVICE
+ *     (device memory of the handle's device).  The library never keeps a
+ *     pointer it was given; inputs are copied, outputs are written before the
+ *     call returns (host) or are stream-ordered on the handle's stream (device).
+ *   - Every call returns PIC_OK (0) or a negative PIC_E* code; no exception or
+ *     signal crosses the ABI.  pic_last_error() gives a message per handle.
+ *   - Leaves are numbered in depth-first pre-order (children in digit order);
+ *     finite-element vertices (non-hanging grid points) by row-major position
+ *     on the finest level; PIDT owner vertices by (level, row-major index).
+ *   - The library owns all device memory it allocates (cudaMalloc at create
+ *     and at re-tree); pic_destroy frees it.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PIC_API __attribute__((visibility("default")))
+#else
+#define PIC_API
+#endif
+
+#define PIC_OK 0
+#define PIC_EINVAL (-1)    /* malformed argument or tree (refined node without 3^d children,
+                              depth > 18, d not 2 or 3, count mismatch) */
+#define PIC_ENOMEM (-2)    /* device or host allocation failed */
+#define PIC_ERANGE (-3)    /* non-finite position or velocity */
+#define PIC_EHOOK (-4)     /* the field-solve hook returned non-zero */
+#define PIC_ETIMEOUT (-5)  /* a bounded device wait gave up */
+#define PIC_ECUDA (-6)     /* a CUDA runtime call failed */
+#define PIC_ESTATE (-7)    /* call not valid in the handle's state */
+
+#define PIC_PIT 0
+#define PIC_PIDT 1
+#define PIC_FP64 0        /* positions and arithmetic in FP64 */
+#define PIC_FP32_SPLIT 1  /* leaf index + FP32 cell-local offset, FP32 arithmetic */
+#define PIC_HOST 0
+#define PIC_DEVICE 1
+
+typedef struct pic_s *pic_t;
+
+/* Spacetree as level-order (breadth-first) refinement flags: flags[i] = 1 if
+ * node i is refined.  Node 0 is the root; the children of a refined node
+ * follow in digit order after all children of earlier refined nodes
+ * (Section 4).  flags is host memory. */
+typedef struct {
+  int32_t d;
+  int64_t n_nodes;
+  const uint8_t *flags;
+} pic_tree_desc;
+
+/* Particles: n positions x[d][n] in [0,1)^d (wrapped on input) and velocities
+ * v[d][n], FP64, in host or device memory per `where`. */
+typedef struct {
+  int64_t n;
+  const double *x;
+  const double *v;
+  int32_t where;
+} pic_particles_desc;
+
+typedef struct {
+  int32_t scheme;     /* PIC_PIT or PIC_PIDT */
+  int32_t precision;  /* PIC_FP64 or PIC_FP32_SPLIT */
+  double q;           /* charge per particle */
+  double qm;          /* charge / mass */
+  double ion;         /* uniform neutralising background density (Appendix A) */
+  int32_t sweeps;     /* damped Jacobi sweeps of the built-in solve per step */
+  double omega;       /* Jacobi damping factor */
+  int32_t track_ids;  /* 1: carry input particle ids through the re-bin (pic_bins) */
+  void *stream;       /* cudaStream_t for every kernel of the handle; NULL = default */
+} pic_config;
+
+/* Optional field-solve hook, called once per step with the vertex charges
+ * Q[n_vertices] (FP64, or FP32 in split mode) and a buffer E[d][n_vertices]
+ * to fill with the field at the vertices.  It must only enqueue work on
+ * `stream` (no synchronisation) and return 0, else the step fails PIC_EHOOK. */
+typedef int (*pic_solve_fn)(void *user, const void *Q_dev, void *E_dev, int64_t n_vertices,
+                            int32_t precision, void *stream);
+
+typedef struct {
+  int32_t d, scheme, precision, depth;
+  int64_t n_particles;
+  int64_t n_leaves;
+  int64_t n_vertices;    /* finite-element vertices (non-hanging) */
+  int64_t n_buckets;     /* leaves (PIT) or PIDT owner vertices */
+  int64_t n_keys;        /* sort keys: leaves (PIT) or owner vertex x 2^d quadrants (PIDT) */
+  int32_t uniform;       /* 1 if every leaf is on `depth` */
+  int64_t device_bytes;  /* device memory held by the handle */
+} pic_info_t;
+
+typedef struct {
+  int64_t step;          /* steps taken */
+  int64_t movers;        /* particles whose key changed in the last step */
+  int64_t max_bucket;    /* largest bucket after the last re-bin */
+  double total_charge;   /* FP64 sum of the vertex charges of the last deposit */
+  double residual;       /* FP64 2-norm of b - A V after the last built-in solve */
+  int32_t error;         /* sticky device error: PIC_ERANGE if a non-finite value was seen */
+} pic_stats_t;
+
+/* Create a handle on the current CUDA device: validate and tabulate the tree,
+ * copy the particles, bin them (initial key + stable bucket sort). */
+PIC_API int pic_create(pic_t *out, const pic_tree_desc *tree, const pic_particles_desc *parts,
+               const pic_config *cfg);
+PIC_API void pic_destroy(pic_t h);
+PIC_API const char *pic_strerror(int code);
+PIC_API const char *pic_last_error(pic_t h);
+PIC_API int pic_info(pic_t h, pic_info_t *out);
+
+/* Leapfrog start: v_{-1/2} = v_0 - (q/m) E(x_0) dt/2 (deposit, solve, gather). */
+PIC_API int pic_init_leapfrog(pic_t h, double dt, pic_solve_fn hook, void *user);
+
+/* One PIC step (Section 3 items 1-4) plus the PIT/PIDT re-bin (Section 5),
+ * enqueued on the handle's stream.  Asynchronous; pic_sync reports errors. */
+PIC_API int pic_step(pic_t h, double dt, pic_solve_fn hook, void *user);
+
+/* Only the timed hot path of a step, with the field E held fixed from the last
+ * solve: deposit of the current positions, gather + push + key, re-bin. */
+PIC_API int pic_step_fixed_field(pic_t h, double dt);
+
+/* Wait for the handle's stream; returns the sticky device error if any. */
+PIC_API int pic_sync(pic_t h);
+
+/* Vertex charges Q[n_vertices] of the current positions (FP64 values, also in
+ * split mode) and the field E[d][n_vertices] of the last solve. */
+PIC_API int pic_deposit(pic_t h, double *Q_out, int32_t where);
+PIC_API int pic_field(pic_t h, double *E_out, int32_t where);
+PIC_API int pic_potential(pic_t h, double *V_out, int32_t where);
+
+/* Buckets after the last re-bin: bucket_start[n_buckets + 1] offsets into the
+ * storage order and perm[n] the input particle id stored at each position
+ * (needs track_ids; else perm may be NULL). */
+PIC_API int pic_bins(pic_t h, int64_t *bucket_start, int32_t *perm, int32_t where);
+
+/* Sort keys per particle in storage order (leaf id, or owner vertex * 2^d +
+ * quadrant for PIDT). */
+PIC_API int pic_keys(pic_t h, int32_t *keys, int32_t where);
+
+/* Particles in storage order: absolute FP64 positions (split mode:
+ * (c + o) / 3^level) and FP64 velocities, [d][n]. */
+PIC_API int pic_get_particles(pic_t h, double *x, double *v, int32_t where);
+
+/* Native state in storage order, for checkpoints and host round trips.
+ * FP64: x[d][n], v[d][n] (double).  Split: leaf[n] (int32), o[d][n], v[d][n]
+ * (float).  Unused pointers may be NULL.  pic_set_state replaces the particles
+ * (same n) and re-bins them. */
+PIC_API int pic_get_state(pic_t h, int32_t *leaf, void *x_or_o, void *v, int32_t where);
+PIC_API int pic_set_state(pic_t h, const int32_t *leaf, const void *x_or_o, const void *v,
+                  int32_t where);
+
+PIC_API int pic_stats(pic_t h, pic_stats_t *out);
+
+/* Tables for tests: leaf level[n_leaves] and coords[n_leaves][d]; vertex
+ * positions pos[d][n_vertices] in units of 3^-depth; PIDT owner vertices
+ * level[n_buckets], j[n_buckets][d] (host memory). */
+PIC_API int pic_leaf_table(pic_t h, int32_t *level, int64_t *coords);
+PIC_API int pic_vertex_table(pic_t h, int64_t *pos);
+PIC_API int pic_pidt_table(pic_t h, int32_t *level, int64_t *j);
+
+/* Replace the tree (same d) and re-bin the particles into it. */
+PIC_API int pic_retree(pic_t h, const pic_tree_desc *tree);
+
+/* Re-refine by the particles-per-cell criterion: cell C on level m is refined
+ * iff m < dmin, or m < dmax and C holds more than ppc particles (Section 6
+ * setup: refine on overrun, coarsen when the union stays within ppc). */
+PIC_API int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

@@ -318,6 +318,14 @@ def stable_bucket(key: np.ndarray, n_keys: int):
     return start, perm
 
 
+def _canonical_bucket(key, old_key, n_keys):
+    """Counting sort by (key, moved, storage index); returns (start over keys,
+    perm)."""
+    moved = np.ones(len(key), np.int64) if old_key is None else (key != old_key).astype(np.int64)
+    start2, perm = stable_bucket(2 * key + moved, 2 * n_keys)
+    return start2[::2].copy(), perm
+
+
 def retree64(d, x, ppc, dmin, dmax) -> np.ndarray:
     lib = _load()
     x = _c(x, np.float64)
@@ -357,7 +365,9 @@ class State64:
     def __init__(self, tree: Tree, x, v, params: Params, ids=None):
         self.tree = tree
         self.p = params
-        self.x = _c(x, np.float64).copy()
+        x = _c(x, np.float64)
+        y = x - np.floor(x)                      # periodic wrap into [0, 1)
+        self.x = np.where(y >= 1.0, 0.0, y)
         self.v = _c(v, np.float64).copy()
         n = self.x.shape[1]
         self.ids = np.arange(n, dtype=np.int64) if ids is None else _c(ids, np.int64).copy()
@@ -366,9 +376,11 @@ class State64:
         self.rebin()
 
     def rebin(self):
-        """Stable re-bin by (key, storage index)."""
+        """Stable re-bin: by (key, moved, storage index), i.e. the particles
+        that stay keep their order at the head of their bucket and the movers
+        follow in storage order.  At creation every particle counts as moved."""
         key = self.tree.keys64(self.p.scheme, self.x)
-        start, perm = stable_bucket(key, self.tree.n_keys(self.p.scheme))
+        start, perm = _canonical_bucket(key, getattr(self, "key", None), self.tree.n_keys(self.p.scheme))
         self.x = np.ascontiguousarray(self.x[:, perm])
         self.v = np.ascontiguousarray(self.v[:, perm])
         self.ids = self.ids[perm]
@@ -412,7 +424,7 @@ class State32:
 
     def rebin(self):
         key = self.tree.keys32(self.p.scheme, self.leaf, self.o)
-        start, perm = stable_bucket(key, self.tree.n_keys(self.p.scheme))
+        start, perm = _canonical_bucket(key, getattr(self, "key", None), self.tree.n_keys(self.p.scheme))
         self.leaf = np.ascontiguousarray(self.leaf[perm])
         self.o = np.ascontiguousarray(self.o[:, perm])
         self.v = np.ascontiguousarray(self.v[:, perm])

@@ -1,0 +1,213 @@
+// Device view of a tabulated spacetree and the per-particle primitives of
+// the PIT/PIDT step (arXiv:1508.02435): quantisation, descent of the
+// flattened level-ordered table (the end state of the lifts and drops of
+// Algorithm 1 / Theorem 1), the split-precision re-location, d-linear shape
+// functions (Section 3) and leaf-corner to vertex maps.
+//
+// Device code is compiled with --fmad=false: every + - * / below is one IEEE
+// round-to-nearest operation in program order.
+#pragma once
+#include <cstdint>
+
+#include "tree.hpp"
+
+namespace pic {
+
+__constant__ uint32_t c_pow3[21];
+
+struct DevTree {
+  int d, nch, nc, depth, uniform, scheme;
+  int64_t n_leaves, n_vert, n_pv, n_keys;
+  int32_t M;  // 3^depth
+  const TabEntry *tab;
+  int32_t n_tab;
+  const uint8_t *leaf_level;
+  const int32_t *leaf_coords;
+  // adaptive grids
+  const int32_t *cexp_ptr, *cexp_vid, *inc_ptr, *inc_lc, *dcnt, *corner_pv;
+  const double *cexp_w64, *inc_w64, *ion64, *diag64;
+  const float *cexp_w32, *inc_w32, *ion32, *diag32;
+  // uniform grids
+  double ion_u64, diag_u64;
+  float ion_u32, diag_u32;
+};
+
+// ---- quantisation ---------------------------------------------------------
+
+__device__ __forceinline__ double wrap01(double x) {
+  double y = x - floor(x);
+  return y >= 1.0 ? 0.0 : y;
+}
+
+__device__ __forceinline__ uint32_t quantise(double y) {  // y already in [0,1)
+  double s = y * 774840978.0;
+  double f = floor(s);
+  if (f < 0.0) f = 0.0;
+  if (f > 774840977.0) f = 774840977.0;
+  return (uint32_t)f;
+}
+
+// ---- descent ----------------------------------------------------------------
+
+__device__ __forceinline__ int digit_q(const uint32_t Q[3], int d, int m) {
+  uint32_t step = 2u * c_pow3[18 - m];
+  int dg = (int)((Q[0] / step) % 3u) + 3 * (int)((Q[1] / step) % 3u);
+  if (d == 3) dg += 9 * (int)((Q[2] / step) % 3u);
+  return dg;
+}
+
+// Local depth-first index inside a complete subtree of depth k whose leaves
+// have coordinates J (on the leaves' level): base-3^d digits, bottom-up.
+__device__ __forceinline__ int32_t local_index(uint32_t J0, uint32_t J1, uint32_t J2, int d, int k) {
+  int32_t local = 0, mul = 1, nch = d == 3 ? 27 : 9;
+  for (int i = 0; i < k; ++i) {
+    int dg = (int)(J0 % 3u) + 3 * (int)(J1 % 3u);
+    if (d == 3) dg += 9 * (int)(J2 % 3u);
+    J0 /= 3u; J1 /= 3u; J2 /= 3u;
+    local += dg * mul;
+    mul *= nch;
+  }
+  return local;
+}
+
+// Covering leaf of the quantised position Q (PIT owner, Theorem 1).
+__device__ __forceinline__ int32_t descend_q(const TabEntry *tab, int d, const uint32_t Q[3], int *lev_out) {
+  int ent = 0, lev = 0;
+  for (;;) {
+    TabEntry e = tab[ent];
+    if (e.a < 0) {
+      int k = -e.a - 1;
+      int L = lev + k;
+      uint32_t step = 2u * c_pow3[18 - L];
+      *lev_out = L;
+      return e.b + local_index(Q[0] / step, Q[1] / step, d == 3 ? Q[2] / step : 0u, d, k);
+    }
+    ent = e.a + digit_q(Q, d, lev + 1);
+    ++lev;
+  }
+}
+
+__device__ __forceinline__ float clamp_off(float f) {
+  const float one_minus = 0x1.fffffep-1f;
+  return f < 0.0f ? 0.0f : (f > one_minus ? one_minus : f);
+}
+
+// One drop below the integer level: u = RN32(3 f), digit = min(floor u, 2),
+// f = u - digit (the split-precision rule of the design notes).
+__device__ __forceinline__ int drop_digit(float *f, int d) {
+  int dg = 0, mul = 1;
+  for (int a = 0; a < d; ++a) {
+    float u = 3.0f * f[a];
+    int g = (int)floorf(u);
+    g = g > 2 ? 2 : g;
+    f[a] = clamp_off(u - (float)g);
+    dg += g * mul;
+    mul *= 3;
+  }
+  return dg;
+}
+
+// Split-precision re-location: the leaf covering integer cell I on level lev
+// plus fraction f.  Writes the leaf's offsets; returns the leaf id.
+__device__ __forceinline__ int32_t descend_split(const TabEntry *tab, int d, int lev, const int32_t I[3],
+                                                 float f[3], float o_out[3], int *lev_out) {
+  int ent = 0, m = 0, nch = d == 3 ? 27 : 9;
+  for (;;) {
+    TabEntry e = tab[ent];
+    if (e.a < 0) {
+      int k = -e.a - 1;
+      int L = m + k;
+      *lev_out = L;
+      if (L <= lev) {  // lift: the covering leaf is on a level <= lev
+        uint32_t sh = c_pow3[lev - L];
+        uint32_t J[3] = {0u, 0u, 0u};
+        for (int a = 0; a < d; ++a) {
+          J[a] = (uint32_t)I[a] / sh;
+          uint32_t r = (uint32_t)I[a] - J[a] * sh;
+          o_out[a] = clamp_off(((float)r + f[a]) / (float)sh);
+        }
+        return e.b + local_index(J[0], J[1], J[2], d, k);
+      }
+      // digits from I down to lev, then drops from the fraction
+      int32_t local = 0;
+      for (int mm = m + 1; mm <= L; ++mm) {
+        int dg;
+        if (mm <= lev) {
+          uint32_t sh = c_pow3[lev - mm];
+          dg = (int)(((uint32_t)I[0] / sh) % 3u) + 3 * (int)(((uint32_t)I[1] / sh) % 3u);
+          if (d == 3) dg += 9 * (int)(((uint32_t)I[2] / sh) % 3u);
+        } else {
+          dg = drop_digit(f, d);
+        }
+        local = local * nch + dg;
+      }
+      for (int a = 0; a < d; ++a) o_out[a] = clamp_off(f[a]);
+      return e.b + local;
+    }
+    int dg;
+    if (m + 1 <= lev) {
+      uint32_t sh = c_pow3[lev - m - 1];
+      dg = (int)(((uint32_t)I[0] / sh) % 3u) + 3 * (int)(((uint32_t)I[1] / sh) % 3u);
+      if (d == 3) dg += 9 * (int)(((uint32_t)I[2] / sh) % 3u);
+    } else {
+      dg = drop_digit(f, d);
+    }
+    ent = e.a + dg;
+    ++m;
+  }
+}
+
+// ---- grid maps ---------------------------------------------------------------
+
+// Row-major vertex of corner e of the uniform-grid cell c (periodic).
+__device__ __forceinline__ int32_t uniform_corner_vertex(const int32_t *c, int e, int d, int32_t M) {
+  int64_t v = 0, mul = 1;
+  for (int a = 0; a < d; ++a) {
+    int32_t j = c[a] + ((e >> a) & 1);
+    if (j >= M) j -= M;
+    v += (int64_t)j * mul;
+    mul *= M;
+  }
+  return (int32_t)v;
+}
+
+// Depth-first leaf id of cell c on a uniform tree of the given depth.
+__device__ __forceinline__ int32_t uniform_leaf_of_cell(const int32_t *c, int d, int depth) {
+  return local_index((uint32_t)c[0], (uint32_t)c[1], d == 3 ? (uint32_t)c[2] : 0u, d, depth);
+}
+
+// d-linear shape function of corner e at local coordinates t.
+template <typename T>
+__device__ __forceinline__ T shape(const T *t, int e, int d) {
+  T w = (T)1;
+  for (int a = 0; a < d; ++a) {
+    T f = ((e >> a) & 1) ? t[a] : (T)1 - t[a];
+    w = w * f;
+  }
+  return w;
+}
+
+// Incident leaf corners of uniform vertex v in ascending leaf-corner order.
+__device__ __forceinline__ int uniform_incidences(int64_t v, int d, int32_t M, int depth, int32_t *lc) {
+  int32_t j[3] = {0, 0, 0};
+  int64_t r = v;
+  for (int a = 0; a < d; ++a) { j[a] = (int32_t)(r % M); r /= M; }
+  int nc = 1 << d;
+  for (int f = 0; f < nc; ++f) {
+    int32_t c[3] = {0, 0, 0};
+    for (int a = 0; a < d; ++a) {
+      int32_t cc = j[a] - ((f >> a) & 1);
+      c[a] = cc < 0 ? cc + M : cc;
+    }
+    lc[f] = uniform_leaf_of_cell(c, d, depth) * nc + f;
+  }
+  for (int i = 1; i < nc; ++i) {  // insertion sort, at most 8 entries
+    int32_t x = lc[i];
+    int k = i - 1;
+    while (k >= 0 && lc[k] > x) { lc[k + 1] = lc[k]; --k; }
+    lc[k + 1] = x;
+  }
+  return nc;
+}
+
+}  // namespace pic

@@ -1,0 +1,874 @@
+// CUDA kernels of the PIT/PIDT particle step for sm_103a (arXiv:1508.02435).
+//
+// Step structure (Section 3 PIC cycle + Section 5 re-binning):
+//   deposit   k_leaf_partials -> k_vertex_charge -> k_sum_blocks        (item 1)
+//   solve     k_rhs -> k_jacobi x sweeps (auxiliary)                    (item 2)
+//   field     k_efield                                                  (item 3)
+//   push      k_push64 / k_push32: gather E_i = R^T(x_i) E, leapfrog kick
+//             and drift, wrap, re-location (descent / split resolve), new
+//             key, moved flag (warp ballot), bucket counts               (items 3-4)
+//   re-bin    scan(counts) -> k_stayers (stable ranks of stayers) ->
+//             k_compact_movers (ballot words -> mover list in storage
+//             order) -> k_mover_slots -> k_sort_segments -> k_gather_*
+//             (stable: stayers first, then movers in storage order)
+//
+// Determinism: no floating-point atomics.  Every sum has a fixed order (bucket
+// order within a leaf, ascending leaf-corner order per vertex); integer atomics
+// only count, and the one order they decide (mover slots) is re-sorted.
+#include <cuda_runtime.h>
+
+#include "dev.cuh"
+#include "launch.hpp"
+
+namespace pic {
+
+__constant__ double c_kref64[8][8];
+__constant__ float c_kref32[8][8];
+
+constexpr int kBlock = 256;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+static inline unsigned grid_for(int64_t n, int block = kBlock) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  return (unsigned)g;
+}
+
+// ---------------------------------------------------------------------------
+// tree view helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void leaf_info(const DevTree &t, int32_t L, int *lev, int32_t *c) {
+  *lev = t.leaf_level[L];
+  for (int a = 0; a < t.d; ++a) c[a] = t.leaf_coords[(int64_t)L * t.d + a];
+}
+
+// PIDT owner vertex of corner a of leaf L (uniform grids: the FE vertex).
+__device__ __forceinline__ int32_t pidt_vertex(const DevTree &t, int32_t L, int a) {
+  if (t.uniform) {
+    int32_t c[3] = {0, 0, 0};
+    for (int k = 0; k < t.d; ++k) c[k] = t.leaf_coords[(int64_t)L * t.d + k];
+    return uniform_corner_vertex(c, a, t.d, t.M);
+  }
+  return t.corner_pv[(int64_t)L * t.nc + a];
+}
+
+// Sort key of a particle in leaf L owned through corner a: PIT = leaf; PIDT =
+// owner vertex * 2^d + quadrant of the leaf seen from the vertex.
+__device__ __forceinline__ int32_t key_of(const DevTree &t, int32_t L, int a) {
+  if (t.scheme == 0) return L;
+  return pidt_vertex(t, L, a) * t.nc + (t.nc - 1 - a);
+}
+
+// Value of a vertex field at corner e of leaf L (hanging corners interpolated
+// from their masters, in ascending master order).
+__device__ __forceinline__ double corner_value(const DevTree &t, int32_t L, const int32_t *c, int e,
+                                               const double *F) {
+  if (t.uniform) return F[uniform_corner_vertex(c, e, t.d, t.M)];
+  int64_t i = (int64_t)L * t.nc + e;
+  double s = 0.0;
+  for (int32_t j = t.cexp_ptr[i]; j < t.cexp_ptr[i + 1]; ++j) s = s + t.cexp_w64[j] * F[t.cexp_vid[j]];
+  return s;
+}
+
+__device__ __forceinline__ float corner_value(const DevTree &t, int32_t L, const int32_t *c, int e,
+                                              const float *F) {
+  if (t.uniform) return F[uniform_corner_vertex(c, e, t.d, t.M)];
+  int64_t i = (int64_t)L * t.nc + e;
+  float s = 0.0f;
+  for (int32_t j = t.cexp_ptr[i]; j < t.cexp_ptr[i + 1]; ++j) s = s + t.cexp_w32[j] * F[t.cexp_vid[j]];
+  return s;
+}
+
+__device__ __forceinline__ const double *inc_weights(const DevTree &t, double) { return t.inc_w64; }
+__device__ __forceinline__ const float *inc_weights(const DevTree &t, float) { return t.inc_w32; }
+__device__ __forceinline__ double kref_val(int e, int f, double) { return c_kref64[e][f]; }
+__device__ __forceinline__ float kref_val(int e, int f, float) { return c_kref32[e][f]; }
+__device__ __forceinline__ double ion_load(const DevTree &t, int64_t v, double) {
+  return t.uniform ? t.ion_u64 : t.ion64[v];
+}
+__device__ __forceinline__ float ion_load(const DevTree &t, int64_t v, float) {
+  return t.uniform ? t.ion_u32 : t.ion32[v];
+}
+__device__ __forceinline__ double diag_val(const DevTree &t, int64_t v, double) {
+  return t.uniform ? t.diag_u64 : t.diag64[v];
+}
+__device__ __forceinline__ float diag_val(const DevTree &t, int64_t v, float) {
+  return t.uniform ? t.diag_u32 : t.diag32[v];
+}
+
+// Visit the incident leaf corners (lc = leaf * 2^d + corner, ascending) of
+// vertex v with their constraint weights: fn(lc, w).
+template <typename T, typename Fn>
+__device__ __forceinline__ void for_incidences(const DevTree &t, int64_t v, Fn fn) {
+  if (t.uniform) {
+    int32_t lc[8];
+    int m = uniform_incidences(v, t.d, t.M, t.depth, lc);
+    for (int i = 0; i < m; ++i) fn(lc[i], (T)1);
+  } else {
+    const T *ww = inc_weights(t, (T)0);
+    for (int32_t j = t.inc_ptr[v]; j < t.inc_ptr[v + 1]; ++j) fn(t.inc_lc[j], ww[j]);
+  }
+}
+
+// Block partial FP64 sums (fixed reduction tree) for deterministic totals.
+__device__ __forceinline__ void block_sum_store(double v, double *block_out) {
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    int nw = blockDim.x >> 5;
+    v = lane < nw ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) block_out[blockIdx.x] = v;
+  }
+}
+
+__global__ void k_sum_blocks(const double *in, int64_t n, double *out) {
+  double v = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v += in[i];
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) *out = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a7 deposit
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void local_coords(const double *x, int64_t n, int64_t p, int lev, const int32_t *c,
+                                             int d, double *tl) {
+  double s = (double)c_pow3[lev];
+  for (int a = 0; a < d; ++a) {
+    double u = x[a * n + p] * s - (double)c[a];
+    tl[a] = u < 0.0 ? 0.0 : (u > 1.0 ? 1.0 : u);
+  }
+}
+
+// Per leaf: partial sums of the 2^d shape functions over the leaf's particles
+// in bucket order (PIDT: the leaf's 2^d sub-buckets in corner order).
+template <bool kSplit>
+__global__ void k_leaf_partials(DevTree t, const int32_t *__restrict__ start, const void *pos, int64_t n,
+                                void *part_out) {
+  int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= t.n_leaves) return;
+  int lev;
+  int32_t c[3] = {0, 0, 0};
+  leaf_info(t, (int32_t)L, &lev, c);
+  const int nc = t.nc, d = t.d;
+  const int na = t.scheme == 0 ? 1 : nc;
+  if (kSplit) {
+    const float *o = (const float *)pos;
+    float acc[8];
+    for (int e = 0; e < nc; ++e) acc[e] = 0.0f;
+    for (int a = 0; a < na; ++a) {
+      int32_t k = key_of(t, (int32_t)L, a);
+      for (int32_t p = start[k]; p < start[k + 1]; ++p) {
+        float tl[3];
+        for (int b = 0; b < d; ++b) tl[b] = o[b * n + p];
+        for (int e = 0; e < nc; ++e) acc[e] = acc[e] + shape<float>(tl, e, d);
+      }
+    }
+    float *part = (float *)part_out;
+    for (int e = 0; e < nc; ++e) part[L * nc + e] = acc[e];
+  } else {
+    const double *x = (const double *)pos;
+    double acc[8];
+    for (int e = 0; e < nc; ++e) acc[e] = 0.0;
+    for (int a = 0; a < na; ++a) {
+      int32_t k = key_of(t, (int32_t)L, a);
+      for (int32_t p = start[k]; p < start[k + 1]; ++p) {
+        double tl[3];
+        local_coords(x, n, p, lev, c, d, tl);
+        for (int e = 0; e < nc; ++e) acc[e] = acc[e] + shape<double>(tl, e, d);
+      }
+    }
+    double *part = (double *)part_out;
+    for (int e = 0; e < nc; ++e) part[L * nc + e] = acc[e];
+  }
+}
+
+// Per vertex: S = sum of w * partial over incident leaf corners (ascending),
+// Q = q S + ion * integral(phi_v); block partial sums of Q in FP64.
+template <typename T>
+__global__ void k_vertex_charge(DevTree t, const T *__restrict__ part, T q, T ion, T *Q, double *block_sum) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double mine = 0.0;
+  if (v < t.n_vert) {
+    T S = (T)0;
+    if (t.uniform) {
+      int32_t lc[8];
+      int m = uniform_incidences(v, t.d, t.M, t.depth, lc);
+      for (int i = 0; i < m; ++i) S = S + part[lc[i]];
+    } else {
+      const T *w = inc_weights(t, (T)0);
+      for (int32_t j = t.inc_ptr[v]; j < t.inc_ptr[v + 1]; ++j) S = S + w[j] * part[t.inc_lc[j]];
+    }
+    T val = q * S + ion * ion_load(t, v, (T)0);
+    Q[v] = val;
+    mine = (double)val;
+  }
+  block_sum_store(mine, block_sum);
+}
+
+// ---------------------------------------------------------------------------
+// a8 solve (auxiliary): b = Q - (sum Q) integral(phi); damped Jacobi
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_rhs(DevTree t, const T *Q, const double *total, T *b) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= t.n_vert) return;
+  T tot = (T)(*total);
+  b[v] = Q[v] - tot * ion_load(t, v, (T)0);
+}
+
+// (A V)_v assembled leaf by leaf: sum over incident leaf corners (L, e) of
+// w * sum_f K_ef h^(d-2) V(L, f).
+template <typename T>
+__device__ __forceinline__ T apply_row(const DevTree &t, int64_t v, const T *V) {
+  T y = (T)0;
+  for_incidences<T>(t, v, [&](int32_t lc, T w) {
+    int32_t L = lc / t.nc;
+    int e = lc - L * t.nc;
+    int lev;
+    int32_t c[3] = {0, 0, 0};
+    leaf_info(t, L, &lev, c);
+    T hs = t.d == 2 ? (T)1 : (T)(1.0 / (double)c_pow3[lev]);
+    T yc = (T)0;
+    for (int f = 0; f < t.nc; ++f) yc = yc + (kref_val(e, f, (T)0) * hs) * corner_value(t, L, c, f, V);
+    y = y + w * yc;
+  });
+  return y;
+}
+
+// One sweep V_out = V_in + omega (b - A V_in) / diag; with r2 != NULL also
+// block sums of (b - A V_in)^2 in FP64.
+template <typename T>
+__global__ void k_jacobi(DevTree t, const T *b, const T *Vin, T *Vout, T omega, double *r2) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double rr = 0.0;
+  if (v < t.n_vert) {
+    T y = apply_row<T>(t, v, Vin);
+    T r = b[v] - y;
+    if (Vout) Vout[v] = Vin[v] + omega * r / diag_val(t, v, (T)0);
+    rr = (double)r * (double)r;
+  }
+  if (r2) block_sum_store(rr, r2);
+}
+
+// E = -grad V at the vertices: minus the mean over leaves that have v as an
+// unconstrained corner of the leaf's edge difference along each axis.
+template <typename T>
+__global__ void k_efield(DevTree t, const T *V, T *E) {
+  int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= t.n_vert) return;
+  T acc[3] = {(T)0, (T)0, (T)0};
+  for_incidences<T>(t, v, [&](int32_t lc, T) {
+    int32_t L = lc / t.nc;
+    int e = lc - L * t.nc;
+    if (!t.uniform) {
+      if (t.cexp_ptr[lc + 1] - t.cexp_ptr[lc] != 1 || t.cexp_w64[t.cexp_ptr[lc]] != 1.0) return;
+    }
+    int lev;
+    int32_t c[3] = {0, 0, 0};
+    leaf_info(t, L, &lev, c);
+    T h = (T)(1.0 / (double)c_pow3[lev]);
+    for (int a = 0; a < t.d; ++a) {
+      T hi = corner_value(t, L, c, e | (1 << a), V);
+      T lo = corner_value(t, L, c, e & ~(1 << a), V);
+      acc[a] = acc[a] + (hi - lo) / h;
+    }
+  });
+  T cn = (T)(t.uniform ? t.nc : t.dcnt[v]);
+  for (int a = 0; a < t.d; ++a) E[a * t.n_vert + v] = -(acc[a] / cn);
+}
+
+// ---------------------------------------------------------------------------
+// a1/a2 initial keys and split conversion
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int pidt_corner_q(const uint32_t *Q, int lev, int d) {
+  uint32_t s = c_pow3[18 - lev];
+  int a_idx = 0;
+  for (int a = 0; a < d; ++a)
+    if (Q[a] % (2u * s) >= s) a_idx |= 1 << a;
+  return a_idx;
+}
+
+__device__ __forceinline__ int pidt_corner_o(const float *o, int d) {
+  int a_idx = 0;
+  for (int a = 0; a < d; ++a)
+    if (o[a] >= 0.5f) a_idx |= 1 << a;
+  return a_idx;
+}
+
+// FP64: wrap x in place, covering leaf and key.
+__global__ void k_init64(DevTree t, double *x, int64_t n, int32_t *leaf, int32_t *key, int32_t *err) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  uint32_t Q[3] = {0u, 0u, 0u};
+  for (int a = 0; a < t.d; ++a) {
+    double xa = x[a * n + p];
+    if (!isfinite(xa)) { atomicOr(err, 1); xa = 0.0; }
+    double y = wrap01(xa);
+    x[a * n + p] = y;
+    Q[a] = quantise(y);
+  }
+  int lev;
+  int32_t L = descend_q(t.tab, t.d, Q, &lev);
+  leaf[p] = L;
+  key[p] = key_of(t, L, pidt_corner_q(Q, lev, t.d));
+}
+
+// Split: leaf by the FP64 owner, o = RN32(clamp(RN64(x 3^l) - c)), v = RN32(v).
+__global__ void k_init32(DevTree t, const double *x, const double *v, int64_t n, int32_t *leaf, float *o,
+                         float *vf, int32_t *key, int32_t *err) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  uint32_t Q[3] = {0u, 0u, 0u};
+  double y[3] = {0.0, 0.0, 0.0};
+  for (int a = 0; a < t.d; ++a) {
+    double xa = x[a * n + p];
+    if (!isfinite(xa) || !isfinite(v[a * n + p])) { atomicOr(err, 1); xa = 0.0; }
+    y[a] = wrap01(xa);
+    Q[a] = quantise(y[a]);
+  }
+  int lev;
+  int32_t L = descend_q(t.tab, t.d, Q, &lev);
+  leaf[p] = L;
+  double s = (double)c_pow3[lev];
+  float oo[3] = {0.f, 0.f, 0.f};
+  for (int a = 0; a < t.d; ++a) {
+    double u = y[a] * s - (double)t.leaf_coords[(int64_t)L * t.d + a];
+    if (u < 0.0) u = 0.0;
+    oo[a] = clamp_off((float)u);
+    o[a * n + p] = oo[a];
+    vf[a * n + p] = (float)v[a * n + p];
+  }
+  key[p] = key_of(t, L, pidt_corner_o(oo, t.d));
+}
+
+// Keys of a given split state (leaf + offsets); flags offsets outside [0,1).
+__global__ void k_rekey32(DevTree t, const int32_t *leaf, const float *o, int64_t n, int32_t *key, int32_t *err) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int32_t L = leaf[p];
+  if (L < 0 || L >= t.n_leaves) { atomicOr(err, 2); L = 0; }
+  float oo[3] = {0.f, 0.f, 0.f};
+  for (int a = 0; a < t.d; ++a) {
+    oo[a] = o[a * n + p];
+    if (!(oo[a] >= 0.0f && oo[a] < 1.0f)) atomicOr(err, 2);
+  }
+  key[p] = key_of(t, L, pidt_corner_o(oo, t.d));
+}
+
+// ---------------------------------------------------------------------------
+// a3 + a4 + a1/a2 + a5: fused gather, push, re-location, key, moved flag
+// ---------------------------------------------------------------------------
+
+// Warp-aggregated bucket count, mover ballot word and per-block mover count.
+__device__ __forceinline__ void count_and_ballot(bool act, int32_t knew, bool moved, int32_t *count,
+                                                 uint32_t *mover_words, int32_t *block_movers) {
+  const unsigned full = 0xffffffffu;
+  int lane = threadIdx.x & 31;
+  unsigned peers = __match_any_sync(full, act ? knew : -1);
+  if (act && lane == __ffs(peers) - 1) atomicAdd(&count[knew], __popc(peers));
+  unsigned mv = __ballot_sync(full, act && moved);
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (lane == 0) mover_words[gw] = mv;
+  __shared__ int sh[32];
+  if (lane == 0) sh[threadIdx.x >> 5] = __popc(mv);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    block_movers[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_push64(DevTree t, Push64Args a) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = p < a.n;
+  int32_t knew = 0;
+  bool moved = false;
+  if (act) {
+    const int d = t.d, nc = t.nc;
+    const int64_t n = a.n, nv = t.n_vert;
+    int32_t L = a.leaf[p];
+    int lev;
+    int32_t c[3] = {0, 0, 0};
+    leaf_info(t, L, &lev, c);
+    double tl[3];
+    local_coords(a.x, n, p, lev, c, d, tl);
+    double E[3] = {0.0, 0.0, 0.0};
+    for (int e = 0; e < nc; ++e) {
+      double w = shape<double>(tl, e, d);
+      for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * corner_value(t, L, c, e, a.E + ax * nv);
+    }
+    uint32_t Q[3] = {0u, 0u, 0u};
+    bool bad = false;
+    for (int ax = 0; ax < d; ++ax) {
+      double vn = a.v[ax * n + p] + a.qmdt * E[ax];
+      double xn = wrap01(a.x[ax * n + p] + vn * a.dt);
+      if (!isfinite(vn) || !isfinite(xn)) { bad = true; xn = 0.0; }
+      a.tv[ax * n + p] = vn;
+      a.tx[ax * n + p] = xn;
+      Q[ax] = quantise(xn);
+    }
+    if (bad) atomicOr(a.err, 1);
+    int lev2;
+    int32_t L2 = descend_q(t.tab, d, Q, &lev2);
+    knew = key_of(t, L2, pidt_corner_q(Q, lev2, d));
+    int32_t kold = t.scheme == 0 ? L : a.key[p];
+    moved = knew != kold;
+    a.tleaf[p] = L2;
+    a.keyn[p] = knew;
+  }
+  count_and_ballot(act, knew, moved, a.count, a.mover_words, a.block_movers);
+}
+
+__global__ void k_push32(DevTree t, Push32Args a) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = p < a.n;
+  int32_t knew = 0;
+  bool moved = false;
+  if (act) {
+    const int d = t.d, nc = t.nc;
+    const int64_t n = a.n, nv = t.n_vert;
+    int32_t L = a.leaf[p];
+    int lev;
+    int32_t c[3] = {0, 0, 0};
+    leaf_info(t, L, &lev, c);
+    float o[3] = {0.f, 0.f, 0.f};
+    for (int ax = 0; ax < d; ++ax) o[ax] = a.o[ax * n + p];
+    float E[3] = {0.f, 0.f, 0.f};
+    for (int e = 0; e < nc; ++e) {
+      float w = shape<float>(o, e, d);
+      for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * corner_value(t, L, c, e, a.E + ax * nv);
+    }
+    const int32_t per = (int32_t)c_pow3[lev];
+    const float sl = (float)(a.dt * (double)per);
+    int32_t I[3] = {0, 0, 0};
+    float f[3] = {0.f, 0.f, 0.f};
+    bool bad = false;
+    for (int ax = 0; ax < d; ++ax) {
+      float vn = a.v[ax * n + p] + a.qmdt * E[ax];
+      float tt = o[ax] + vn * sl;
+      if (!isfinite(vn) || !isfinite(tt)) { bad = true; tt = 0.0f; }
+      float fl = floorf(tt);
+      f[ax] = tt - fl;
+      float flc = fminf(fmaxf(fl, -1.0e15f), 1.0e15f);
+      int64_t cc = ((int64_t)c[ax] + (int64_t)flc) % per;
+      if (cc < 0) cc += per;
+      I[ax] = (int32_t)cc;
+      a.tv[ax * n + p] = vn;
+    }
+    if (bad) atomicOr(a.err, 1);
+    float o2[3] = {0.f, 0.f, 0.f};
+    int lev2;
+    int32_t L2 = descend_split(t.tab, d, lev, I, f, o2, &lev2);
+    for (int ax = 0; ax < d; ++ax) a.to[ax * n + p] = o2[ax];
+    knew = key_of(t, L2, pidt_corner_o(o2, d));
+    int32_t kold = t.scheme == 0 ? L : a.key[p];
+    moved = knew != kold;
+    a.tleaf[p] = L2;
+    a.keyn[p] = knew;
+  }
+  count_and_ballot(act, knew, moved, a.count, a.mover_words, a.block_movers);
+}
+
+// Key counts of freshly converted particles (every particle a mover).
+__global__ void k_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *mover_words,
+                            int32_t *block_movers) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = p < n;
+  int32_t k = act ? key[p] : 0;
+  count_and_ballot(act, k, true, count, mover_words, block_movers);
+}
+
+// ---------------------------------------------------------------------------
+// a6 stable counting sort
+// ---------------------------------------------------------------------------
+
+// Exclusive scan of int32 values: tiles of kScanTile elements.
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t *total) {
+  __shared__ int32_t sh[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int32_t s = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    sh[lane] = s;
+  }
+  __syncthreads();
+  int32_t before = w > 0 ? sh[w - 1] : 0;
+  if (total) *total = sh[(blockDim.x >> 5) - 1];
+  int32_t r = before + x - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan_reduce(const int32_t *in, int64_t n, int32_t *tile_sums) {
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int32_t s = 0;
+  for (int i = 0; i < kScanItems; ++i)
+    if (base + i < n) s += in[base + i];
+  int32_t tot;
+  block_exclusive_scan(s, &tot);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the tile sums in place, total to *total.
+__global__ void k_scan_tiles(int32_t *tile_sums, int64_t nt, int32_t *total) {
+  int32_t carry = 0;
+  for (int64_t base = 0; base < nt; base += blockDim.x) {
+    int64_t i = base + threadIdx.x;
+    int32_t v = i < nt ? tile_sums[i] : 0;
+    int32_t tot;
+    int32_t ex = block_exclusive_scan(v, &tot);
+    if (i < nt) tile_sums[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_apply(const int32_t *in, int64_t n, const int32_t *tile_offsets, int32_t *out,
+                             const int32_t *total) {
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  int32_t vals[kScanItems];
+  int32_t s = 0;
+  for (int i = 0; i < kScanItems; ++i) {
+    vals[i] = base + i < n ? in[base + i] : 0;
+    s += vals[i];
+  }
+  int32_t ex = block_exclusive_scan(s, nullptr) + tile_offsets[blockIdx.x];
+  for (int i = 0; i < kScanItems; ++i) {
+    if (base + i < n) out[base + i] = ex;
+    ex += vals[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = *total;
+}
+
+// Stayers of old bucket k keep their storage order at the head of new bucket k.
+__global__ void k_stayers(const int32_t *old_start, const int32_t *keyn, const int32_t *new_start,
+                          int64_t n_keys, int32_t *perm, int32_t *n_stay, int32_t *max_bucket) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_keys) return;
+  int32_t r = 0, dst = new_start[k];
+  for (int32_t i = old_start[k]; i < old_start[k + 1]; ++i)
+    if (keyn[i] == (int32_t)k) perm[dst + r++] = i;
+  n_stay[k] = r;
+  int32_t sz = new_start[k + 1] - new_start[k];
+  if (sz > 0) atomicMax(max_bucket, sz);
+}
+
+// Ballot words -> mover list in storage order.
+__global__ void k_compact_movers(const uint32_t *mover_words, const int32_t *block_offsets, int64_t n,
+                                 int32_t *movers) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t w0 = ((int64_t)blockIdx.x * blockDim.x) >> 5;
+  int32_t off = block_offsets[blockIdx.x];
+  for (int k = 0; k < w; ++k) off += __popc(mover_words[w0 + k]);
+  uint32_t word = mover_words[w0 + w];
+  if (p < n && ((word >> lane) & 1u)) movers[off + __popc(word & ((1u << lane) - 1u))] = (int32_t)p;
+}
+
+__global__ void k_mover_slots(const int32_t *movers, const int32_t *n_movers, const int32_t *keyn,
+                              const int32_t *new_start, const int32_t *n_stay, int32_t *cursor,
+                              int32_t *perm) {
+  int32_t m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= *n_movers) return;
+  int32_t p = movers[m];
+  int32_t k = keyn[p];
+  int32_t slot = atomicAdd(&cursor[k], 1);
+  perm[new_start[k] + n_stay[k] + slot] = p;
+}
+
+// The movers of every bucket in storage order (undoes the atomic slot order).
+__global__ void k_sort_segments(const int32_t *new_start, const int32_t *n_stay, int64_t n_keys, int32_t *perm) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_keys) return;
+  int32_t b = new_start[k] + n_stay[k], e = new_start[k + 1];
+  for (int32_t i = b + 1; i < e; ++i) {
+    int32_t x = perm[i];
+    int32_t j = i - 1;
+    while (j >= b && perm[j] > x) {
+      perm[j + 1] = perm[j];
+      --j;
+    }
+    perm[j + 1] = x;
+  }
+}
+
+template <typename T>
+__global__ void k_gather_vec(const int32_t *perm, int64_t n, int d, const T *src, T *dst) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int32_t i = perm[p];
+  for (int a = 0; a < d; ++a) dst[a * n + p] = src[a * n + i];
+}
+
+// ---------------------------------------------------------------------------
+// misc
+// ---------------------------------------------------------------------------
+
+__global__ void k_absolute_split(DevTree t, const int32_t *leaf, const float *o, int64_t n, double *x) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int32_t L = leaf[p];
+  int lev = t.leaf_level[L];
+  double s = (double)c_pow3[lev];
+  for (int a = 0; a < t.d; ++a)
+    x[a * n + p] = ((double)t.leaf_coords[(int64_t)L * t.d + a] + (double)o[a * n + p]) / s;
+}
+
+__global__ void k_widen(const float *in, int64_t n, double *out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i];
+}
+
+__global__ void k_half_kick64(const double *Ep, int64_t n, double c, double *v) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = v[i] - c * Ep[i];
+}
+
+__global__ void k_half_kick32(const float *Ep, int64_t n, float c, float *v) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = v[i] - c * Ep[i];
+}
+
+// Gather only (leapfrog start): E at the particles, [d][n].
+__global__ void k_gather_only64(DevTree t, const double *x, const int32_t *leaf, int64_t n, const double *Ev,
+                                double *Ep) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int32_t L = leaf[p];
+  int lev;
+  int32_t c[3] = {0, 0, 0};
+  leaf_info(t, L, &lev, c);
+  double tl[3];
+  local_coords(x, n, p, lev, c, t.d, tl);
+  double E[3] = {0.0, 0.0, 0.0};
+  for (int e = 0; e < t.nc; ++e) {
+    double w = shape<double>(tl, e, t.d);
+    for (int ax = 0; ax < t.d; ++ax) E[ax] = E[ax] + w * corner_value(t, L, c, e, Ev + ax * t.n_vert);
+  }
+  for (int ax = 0; ax < t.d; ++ax) Ep[ax * n + p] = E[ax];
+}
+
+__global__ void k_gather_only32(DevTree t, const float *o, const int32_t *leaf, int64_t n, const float *Ev,
+                                float *Ep) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int32_t L = leaf[p];
+  int lev;
+  int32_t c[3] = {0, 0, 0};
+  leaf_info(t, L, &lev, c);
+  float tl[3] = {0.f, 0.f, 0.f};
+  for (int a = 0; a < t.d; ++a) tl[a] = o[a * n + p];
+  float E[3] = {0.f, 0.f, 0.f};
+  for (int e = 0; e < t.nc; ++e) {
+    float w = shape<float>(tl, e, t.d);
+    for (int ax = 0; ax < t.d; ++ax) E[ax] = E[ax] + w * corner_value(t, L, c, e, Ev + ax * t.n_vert);
+  }
+  for (int ax = 0; ax < t.d; ++ax) Ep[ax * n + p] = E[ax];
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+cudaError_t set_constants(cudaStream_t s) {
+  uint32_t p3[21];
+  p3[0] = 1;
+  for (int i = 1; i < 21; ++i) p3[i] = p3[i - 1] * 3u;
+  return cudaMemcpyToSymbolAsync(c_pow3, p3, sizeof(p3), 0, cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t set_kref(int d, cudaStream_t s) {
+  double k64[8][8];
+  float k32[8][8];
+  int nc = 1 << d;
+  for (int e = 0; e < 8; ++e)
+    for (int f = 0; f < 8; ++f) {
+      double v = 0.0;
+      if (e < nc && f < nc) {
+        int diff = __builtin_popcount((unsigned)(e ^ f));
+        if (d == 2) {
+          const double k2[3] = {4.0 / 6.0, -1.0 / 6.0, -2.0 / 6.0};
+          v = k2[diff];
+        } else {
+          const double k3[4] = {4.0 / 12.0, 0.0, -1.0 / 12.0, -1.0 / 12.0};
+          v = k3[diff];
+        }
+      }
+      k64[e][f] = v;
+      k32[e][f] = (float)v;
+    }
+  cudaError_t err = cudaMemcpyToSymbolAsync(c_kref64, k64, sizeof(k64), 0, cudaMemcpyHostToDevice, s);
+  if (err != cudaSuccess) return err;
+  return cudaMemcpyToSymbolAsync(c_kref32, k32, sizeof(k32), 0, cudaMemcpyHostToDevice, s);
+}
+
+void launch_init64(const DevTree &t, double *x, int64_t n, int32_t *leaf, int32_t *key, int32_t *err,
+                   cudaStream_t s) {
+  if (n > 0) k_init64<<<grid_for(n), kBlock, 0, s>>>(t, x, n, leaf, key, err);
+}
+
+void launch_init32(const DevTree &t, const double *x, const double *v, int64_t n, int32_t *leaf, float *o,
+                   float *vf, int32_t *key, int32_t *err, cudaStream_t s) {
+  if (n > 0) k_init32<<<grid_for(n), kBlock, 0, s>>>(t, x, v, n, leaf, o, vf, key, err);
+}
+
+void launch_rekey32(const DevTree &t, const int32_t *leaf, const float *o, int64_t n, int32_t *key, int32_t *err,
+                    cudaStream_t s) {
+  if (n > 0) k_rekey32<<<grid_for(n), kBlock, 0, s>>>(t, leaf, o, n, key, err);
+}
+
+void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *mover_words,
+                      int32_t *block_movers, cudaStream_t s) {
+  k_count_all<<<grid_for(n), kBlock, 0, s>>>(key, n, count, mover_words, block_movers);
+}
+
+void launch_deposit(const DevTree &t, bool split, const int32_t *start, const void *pos, int64_t n, void *part,
+                    double q, double ion, void *Q, double *block_sum, double *total, cudaStream_t s) {
+  if (split) {
+    k_leaf_partials<true><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part);
+    k_vertex_charge<float><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const float *)part, (float)q, (float)ion,
+                                                                 (float *)Q, block_sum);
+  } else {
+    k_leaf_partials<false><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part);
+    k_vertex_charge<double><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const double *)part, q, ion, (double *)Q,
+                                                                  block_sum);
+  }
+  k_sum_blocks<<<1, 1024, 0, s>>>(block_sum, grid_for(t.n_vert), total);
+}
+
+void launch_solve(const DevTree &t, bool split, const void *Q, const double *total, void *b, void *V, void *Vtmp,
+                  int sweeps, double omega, double *block_sum, double *resid2, cudaStream_t s) {
+  unsigned g = grid_for(t.n_vert);
+  if (split) {
+    k_rhs<float><<<g, kBlock, 0, s>>>(t, (const float *)Q, total, (float *)b);
+    float *a = (float *)V, *c = (float *)Vtmp;
+    for (int it = 0; it < sweeps; ++it) {
+      k_jacobi<float><<<g, kBlock, 0, s>>>(t, (const float *)b, a, c, (float)omega, nullptr);
+      float *tmp = a; a = c; c = tmp;
+    }
+    if (a != (float *)V) cudaMemcpyAsync(V, a, sizeof(float) * t.n_vert, cudaMemcpyDeviceToDevice, s);
+    k_jacobi<float><<<g, kBlock, 0, s>>>(t, (const float *)b, (const float *)V, nullptr, (float)omega, block_sum);
+  } else {
+    k_rhs<double><<<g, kBlock, 0, s>>>(t, (const double *)Q, total, (double *)b);
+    double *a = (double *)V, *c = (double *)Vtmp;
+    for (int it = 0; it < sweeps; ++it) {
+      k_jacobi<double><<<g, kBlock, 0, s>>>(t, (const double *)b, a, c, omega, nullptr);
+      double *tmp = a; a = c; c = tmp;
+    }
+    if (a != (double *)V) cudaMemcpyAsync(V, a, sizeof(double) * t.n_vert, cudaMemcpyDeviceToDevice, s);
+    k_jacobi<double><<<g, kBlock, 0, s>>>(t, (const double *)b, (const double *)V, nullptr, omega, block_sum);
+  }
+  k_sum_blocks<<<1, 1024, 0, s>>>(block_sum, g, resid2);
+}
+
+void launch_efield(const DevTree &t, bool split, const void *V, void *E, cudaStream_t s) {
+  if (split)
+    k_efield<float><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const float *)V, (float *)E);
+  else
+    k_efield<double><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const double *)V, (double *)E);
+}
+
+void launch_push64(const DevTree &t, const Push64Args &a, cudaStream_t s) {
+  k_push64<<<grid_for(a.n), kBlock, 0, s>>>(t, a);
+}
+
+void launch_push32(const DevTree &t, const Push32Args &a, cudaStream_t s) {
+  k_push32<<<grid_for(a.n), kBlock, 0, s>>>(t, a);
+}
+
+int64_t scan_tiles_needed(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+
+void launch_exclusive_scan(const int32_t *in, int64_t n, int32_t *out, int32_t *tile_sums, int32_t *total,
+                           cudaStream_t s) {
+  int64_t nt = scan_tiles_needed(n);
+  if (nt < 1) nt = 1;
+  k_scan_reduce<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, tile_sums);
+  k_scan_tiles<<<1, kScanThreads, 0, s>>>(tile_sums, nt, total);
+  k_scan_apply<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, tile_sums, out, total);
+}
+
+void launch_rebin(const RebinArgs &r, cudaStream_t s) {
+  // bucket offsets
+  launch_exclusive_scan(r.count, r.n_keys, r.new_start, r.tile_sums, r.scalars + 0, s);
+  // mover list in storage order
+  unsigned gp = grid_for(r.n);
+  launch_exclusive_scan(r.block_movers, gp, r.block_offsets, r.tile_sums2, r.scalars + 1, s);
+  if (r.old_start)
+    k_stayers<<<grid_for(r.n_keys), kBlock, 0, s>>>(r.old_start, r.keyn, r.new_start, r.n_keys, r.perm, r.n_stay,
+                                                    r.scalars + 2);
+  else
+    cudaMemsetAsync(r.n_stay, 0, sizeof(int32_t) * r.n_keys, s);
+  k_compact_movers<<<gp, kBlock, 0, s>>>(r.mover_words, r.block_offsets, r.n, r.movers);
+  cudaMemsetAsync(r.cursor, 0, sizeof(int32_t) * r.n_keys, s);
+  k_mover_slots<<<gp, kBlock, 0, s>>>(r.movers, r.scalars + 1, r.keyn, r.new_start, r.n_stay, r.cursor, r.perm);
+  k_sort_segments<<<grid_for(r.n_keys), kBlock, 0, s>>>(r.new_start, r.n_stay, r.n_keys, r.perm);
+}
+
+void launch_gather_f64(const int32_t *perm, int64_t n, int d, const double *src, double *dst, cudaStream_t s) {
+  if (n > 0) k_gather_vec<double><<<grid_for(n), kBlock, 0, s>>>(perm, n, d, src, dst);
+}
+void launch_gather_f32(const int32_t *perm, int64_t n, int d, const float *src, float *dst, cudaStream_t s) {
+  if (n > 0) k_gather_vec<float><<<grid_for(n), kBlock, 0, s>>>(perm, n, d, src, dst);
+}
+void launch_gather_i32(const int32_t *perm, int64_t n, const int32_t *src, int32_t *dst, cudaStream_t s) {
+  if (n > 0) k_gather_vec<int32_t><<<grid_for(n), kBlock, 0, s>>>(perm, n, 1, src, dst);
+}
+
+void launch_absolute_split(const DevTree &t, const int32_t *leaf, const float *o, int64_t n, double *x,
+                           cudaStream_t s) {
+  if (n > 0) k_absolute_split<<<grid_for(n), kBlock, 0, s>>>(t, leaf, o, n, x);
+}
+
+void launch_widen(const float *in, int64_t n, double *out, cudaStream_t s) {
+  if (n > 0) k_widen<<<grid_for(n), kBlock, 0, s>>>(in, n, out);
+}
+
+void launch_gather_only(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n,
+                        const void *Ev, void *Ep, cudaStream_t s) {
+  if (n <= 0) return;
+  if (split)
+    k_gather_only32<<<grid_for(n), kBlock, 0, s>>>(t, (const float *)pos, leaf, n, (const float *)Ev, (float *)Ep);
+  else
+    k_gather_only64<<<grid_for(n), kBlock, 0, s>>>(t, (const double *)pos, leaf, n, (const double *)Ev,
+                                                   (double *)Ep);
+}
+
+void launch_half_kick(bool split, const void *Ep, int64_t n_total, double c, void *v, cudaStream_t s) {
+  if (n_total <= 0) return;
+  if (split)
+    k_half_kick32<<<grid_for(n_total), kBlock, 0, s>>>((const float *)Ep, n_total, (float)c, (float *)v);
+  else
+    k_half_kick64<<<grid_for(n_total), kBlock, 0, s>>>((const double *)Ep, n_total, c, (double *)v);
+}
+
+}  // namespace pic

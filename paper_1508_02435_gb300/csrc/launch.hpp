@@ -1,0 +1,86 @@
+// Kernel launch interface between the C-ABI layer (pic_api.cu) and the
+// kernels (kernels.cu).  All launches are stream-ordered on `s`.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace pic {
+
+struct DevTree;
+
+struct Push64Args {
+  int64_t n;
+  const double *x, *v;          // current state, bucket-sorted
+  const int32_t *leaf, *key;    // key used by PIDT only
+  double *tx, *tv;              // pushed state, same index
+  int32_t *tleaf, *keyn;
+  const double *E;              // [d][n_vert]
+  double qmdt, dt;
+  int32_t *count;               // per key, zeroed before the launch
+  uint32_t *mover_words;        // one ballot word per warp
+  int32_t *block_movers;        // movers per block
+  int32_t *err;
+};
+
+struct Push32Args {
+  int64_t n;
+  const float *o, *v;
+  const int32_t *leaf, *key;
+  float *to, *tv;
+  int32_t *tleaf, *keyn;
+  const float *E;
+  float qmdt;
+  double dt;
+  int32_t *count;
+  uint32_t *mover_words;
+  int32_t *block_movers;
+  int32_t *err;
+};
+
+struct RebinArgs {
+  int64_t n, n_keys;
+  const int32_t *count;         // per key
+  const int32_t *keyn;          // new key per particle (storage order)
+  const int32_t *old_start;     // CSR of the current order, NULL at creation
+  int32_t *new_start;           // n_keys + 1
+  const uint32_t *mover_words;
+  const int32_t *block_movers;
+  int32_t *block_offsets, *movers, *n_stay, *cursor, *perm;
+  int32_t *tile_sums, *tile_sums2;
+  int32_t *scalars;             // [0] n, [1] movers, [2] max bucket
+};
+
+cudaError_t set_constants(cudaStream_t s);
+cudaError_t set_kref(int d, cudaStream_t s);
+int64_t scan_tiles_needed(int64_t n);
+
+void launch_init64(const DevTree &t, double *x, int64_t n, int32_t *leaf, int32_t *key, int32_t *err,
+                   cudaStream_t s);
+void launch_init32(const DevTree &t, const double *x, const double *v, int64_t n, int32_t *leaf, float *o,
+                   float *vf, int32_t *key, int32_t *err, cudaStream_t s);
+void launch_rekey32(const DevTree &t, const int32_t *leaf, const float *o, int64_t n, int32_t *key, int32_t *err,
+                    cudaStream_t s);
+void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *mover_words,
+                      int32_t *block_movers, cudaStream_t s);
+void launch_deposit(const DevTree &t, bool split, const int32_t *start, const void *pos, int64_t n, void *part,
+                    double q, double ion, void *Q, double *block_sum, double *total, cudaStream_t s);
+void launch_solve(const DevTree &t, bool split, const void *Q, const double *total, void *b, void *V, void *Vtmp,
+                  int sweeps, double omega, double *block_sum, double *resid2, cudaStream_t s);
+void launch_efield(const DevTree &t, bool split, const void *V, void *E, cudaStream_t s);
+void launch_push64(const DevTree &t, const Push64Args &a, cudaStream_t s);
+void launch_push32(const DevTree &t, const Push32Args &a, cudaStream_t s);
+void launch_exclusive_scan(const int32_t *in, int64_t n, int32_t *out, int32_t *tile_sums, int32_t *total,
+                           cudaStream_t s);
+void launch_rebin(const RebinArgs &r, cudaStream_t s);
+void launch_gather_f64(const int32_t *perm, int64_t n, int d, const double *src, double *dst, cudaStream_t s);
+void launch_gather_f32(const int32_t *perm, int64_t n, int d, const float *src, float *dst, cudaStream_t s);
+void launch_gather_i32(const int32_t *perm, int64_t n, const int32_t *src, int32_t *dst, cudaStream_t s);
+void launch_absolute_split(const DevTree &t, const int32_t *leaf, const float *o, int64_t n, double *x,
+                           cudaStream_t s);
+void launch_widen(const float *in, int64_t n, double *out, cudaStream_t s);
+void launch_gather_only(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n,
+                        const void *Ev, void *Ep, cudaStream_t s);
+void launch_half_kick(bool split, const void *Ep, int64_t n_total, double c, void *v, cudaStream_t s);
+
+}  // namespace pic

@@ -1,0 +1,717 @@
+// C ABI of libpic (include/pic.h): handle management, device memory, and the
+// orchestration of one PIT/PIDT particle step on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "dev.cuh"
+#include "launch.hpp"
+#include "tree.hpp"
+
+using namespace pic;
+
+namespace {
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct pic_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  pic_config cfg{};
+  int d = 0, scheme = 0, split = 0;
+  int64_t n = 0;
+  HostTree ht;
+  DevTree dt{};
+  std::vector<DevBuf> tree_bufs, state_bufs;
+  int64_t device_bytes = 0;
+
+  // particle state: [0] current (bucket-sorted), [1] pushed (same index)
+  void *pos[2] = {nullptr, nullptr};  // x (double) or o (float), [d][n]
+  void *vel[2] = {nullptr, nullptr};
+  int32_t *leaf[2] = {nullptr, nullptr};
+  int32_t *key[2] = {nullptr, nullptr};  // [1] doubles as the new key
+  int32_t *ids[2] = {nullptr, nullptr};
+  // re-bin scratch
+  int32_t *start_cur = nullptr, *start_new = nullptr, *count = nullptr, *n_stay = nullptr, *cursor = nullptr;
+  int32_t *perm = nullptr, *movers = nullptr, *block_movers = nullptr, *block_offsets = nullptr;
+  int32_t *tile_sums = nullptr, *tile_sums2 = nullptr, *scalars = nullptr, *err = nullptr;
+  uint32_t *mover_words = nullptr;
+  // grid
+  void *part = nullptr, *Q = nullptr, *b = nullptr, *V = nullptr, *Vtmp = nullptr, *E = nullptr;
+  double *block_sum = nullptr, *total = nullptr, *resid2 = nullptr;
+  void *Ep = nullptr;  // d * n scratch (gather at the particles, FP64 staging)
+
+  int64_t step = 0;
+  std::string last_error;
+};
+
+namespace {
+
+int fail(pic_t h, int code, const std::string &msg) {
+  if (h) h->last_error = msg;
+  return code;
+}
+
+int cuda_fail(pic_t h, cudaError_t e, const char *what) {
+  if (h) h->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return PIC_ECUDA;
+}
+
+#define CK(call)                                        \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+template <typename T>
+int dalloc(pic_t h, std::vector<DevBuf> &bufs, T **out, size_t count) {
+  size_t bytes = sizeof(T) * (count ? count : 1);
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return fail(h, PIC_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed");
+  }
+  bufs.push_back({p, bytes});
+  h->device_bytes += (int64_t)bytes;
+  *out = (T *)p;
+  return PIC_OK;
+}
+
+void free_bufs(pic_t h, std::vector<DevBuf> &bufs) {
+  for (auto &b : bufs) {
+    cudaFree(b.p);
+    h->device_bytes -= (int64_t)b.bytes;
+  }
+  bufs.clear();
+}
+
+template <typename T>
+int upload(pic_t h, std::vector<DevBuf> &bufs, const T **out, const std::vector<T> &v) {
+  T *p = nullptr;
+  int rc = dalloc(h, bufs, &p, v.size());
+  if (rc) return rc;
+  if (!v.empty()) CK(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  *out = p;
+  return PIC_OK;
+}
+
+int64_t n_keys_of(const HostTree &t, int scheme) { return scheme == PIC_PIT ? t.n_leaves : t.n_pv * t.nc; }
+
+// Tabulate the tree on the host and upload the device view.
+int install_tree(pic_t h, const pic_tree_desc *tree) {
+  std::string err;
+  HostTree ht;
+  if (!tree || !tree->flags) return fail(h, PIC_EINVAL, "tree descriptor is NULL");
+  if (ht.build(tree->d, tree->n_nodes, tree->flags, &err)) return fail(h, PIC_EINVAL, err);
+  if (h->d && tree->d != h->d) return fail(h, PIC_EINVAL, "tree dimension differs from the handle");
+  if (ht.depth > 12 && !ht.uniform) return fail(h, PIC_EINVAL, "adaptive trees deeper than level 12 are not supported");
+  {
+    int64_t mv = 1;
+    for (int a = 0; a < ht.d; ++a) mv *= ht.M;
+    if (mv > INT32_MAX) return fail(h, PIC_EINVAL, "finest level has more than 2^31 grid points");
+  }
+  ht.build_grid();
+  ht.build_pidt();
+  if (n_keys_of(ht, h->scheme) >= INT32_MAX) return fail(h, PIC_EINVAL, "more than 2^31 sort keys");
+  free_bufs(h, h->tree_bufs);
+  DevTree dt{};
+  dt.d = ht.d;
+  dt.nch = ht.nch;
+  dt.nc = ht.nc;
+  dt.depth = ht.depth;
+  dt.uniform = ht.uniform ? 1 : 0;
+  dt.scheme = h->scheme;
+  dt.n_leaves = ht.n_leaves;
+  dt.n_vert = ht.n_vert;
+  dt.n_pv = ht.n_pv;
+  dt.n_keys = n_keys_of(ht, h->scheme);
+  dt.M = (int32_t)ht.M;
+  dt.n_tab = (int32_t)ht.tab.size();
+  int rc;
+  auto &tb = h->tree_bufs;
+  if ((rc = upload(h, tb, &dt.tab, ht.tab))) return rc;
+  if ((rc = upload(h, tb, &dt.leaf_level, ht.leaf_level))) return rc;
+  if ((rc = upload(h, tb, &dt.leaf_coords, ht.leaf_coords))) return rc;
+  if (ht.uniform) {
+    dt.ion_u64 = ht.ion_load[0];
+    dt.ion_u32 = (float)ht.ion_load[0];
+    dt.diag_u64 = ht.diag[0];
+    dt.diag_u32 = (float)ht.diag[0];
+  } else {
+    std::vector<float> f;
+    auto to32 = [&](const std::vector<double> &v) {
+      f.assign(v.size(), 0.f);
+      for (size_t i = 0; i < v.size(); ++i) f[i] = (float)v[i];
+      return f;
+    };
+    if ((rc = upload(h, tb, &dt.cexp_ptr, ht.cexp_ptr))) return rc;
+    if ((rc = upload(h, tb, &dt.cexp_vid, ht.cexp_vid))) return rc;
+    if ((rc = upload(h, tb, &dt.cexp_w64, ht.cexp_w))) return rc;
+    if ((rc = upload(h, tb, &dt.cexp_w32, to32(ht.cexp_w)))) return rc;
+    if ((rc = upload(h, tb, &dt.inc_ptr, ht.inc_ptr))) return rc;
+    if ((rc = upload(h, tb, &dt.inc_lc, ht.inc_lc))) return rc;
+    if ((rc = upload(h, tb, &dt.inc_w64, ht.inc_w))) return rc;
+    if ((rc = upload(h, tb, &dt.inc_w32, to32(ht.inc_w)))) return rc;
+    if ((rc = upload(h, tb, &dt.ion64, ht.ion_load))) return rc;
+    if ((rc = upload(h, tb, &dt.ion32, to32(ht.ion_load)))) return rc;
+    if ((rc = upload(h, tb, &dt.diag64, ht.diag))) return rc;
+    if ((rc = upload(h, tb, &dt.diag32, to32(ht.diag)))) return rc;
+    if ((rc = upload(h, tb, &dt.dcnt, ht.direct_cnt))) return rc;
+    if ((rc = upload(h, tb, &dt.corner_pv, ht.corner_pv))) return rc;
+  }
+  h->d = ht.d;
+  h->ht = std::move(ht);
+  h->dt = dt;
+  return PIC_OK;
+}
+
+// Per-particle and per-grid buffers sized from n and the installed tree.
+int alloc_state(pic_t h) {
+  free_bufs(h, h->state_bufs);
+  auto &sb = h->state_bufs;
+  const int64_t n = h->n, d = h->d;
+  const size_t fs = h->split ? sizeof(float) : sizeof(double);
+  const int64_t nk = h->dt.n_keys, nv = h->dt.n_vert, nl = h->dt.n_leaves;
+  const int64_t nblk = (n + 255) / 256 + 1;
+  int rc;
+  for (int s = 0; s < 2; ++s) {
+    char *p;
+    if ((rc = dalloc(h, sb, &p, fs * d * n))) return rc;
+    h->pos[s] = p;
+    if ((rc = dalloc(h, sb, &p, fs * d * n))) return rc;
+    h->vel[s] = p;
+    if ((rc = dalloc(h, sb, &h->leaf[s], n))) return rc;
+    if ((rc = dalloc(h, sb, &h->key[s], n))) return rc;
+    if ((rc = dalloc(h, sb, &h->ids[s], n))) return rc;
+  }
+  if ((rc = dalloc(h, sb, &h->start_cur, nk + 1))) return rc;
+  if ((rc = dalloc(h, sb, &h->start_new, nk + 1))) return rc;
+  if ((rc = dalloc(h, sb, &h->count, nk))) return rc;
+  if ((rc = dalloc(h, sb, &h->n_stay, nk))) return rc;
+  if ((rc = dalloc(h, sb, &h->cursor, nk))) return rc;
+  if ((rc = dalloc(h, sb, &h->perm, n))) return rc;
+  if ((rc = dalloc(h, sb, &h->movers, n))) return rc;
+  if ((rc = dalloc(h, sb, &h->block_movers, nblk))) return rc;
+  if ((rc = dalloc(h, sb, &h->block_offsets, nblk + 1))) return rc;
+  if ((rc = dalloc(h, sb, &h->mover_words, nblk * 8))) return rc;
+  if ((rc = dalloc(h, sb, &h->tile_sums, scan_tiles_needed(nk) + 1))) return rc;
+  if ((rc = dalloc(h, sb, &h->tile_sums2, scan_tiles_needed(nblk) + 1))) return rc;
+  if ((rc = dalloc(h, sb, &h->scalars, 8))) return rc;
+  if ((rc = dalloc(h, sb, &h->err, 1))) return rc;
+  char *p;
+  if ((rc = dalloc(h, sb, &p, fs * nl * h->dt.nc))) return rc;
+  h->part = p;
+  if ((rc = dalloc(h, sb, &p, fs * nv))) return rc;
+  h->Q = p;
+  if ((rc = dalloc(h, sb, &p, fs * nv))) return rc;
+  h->b = p;
+  if ((rc = dalloc(h, sb, &p, fs * nv))) return rc;
+  h->V = p;
+  if ((rc = dalloc(h, sb, &p, fs * nv))) return rc;
+  h->Vtmp = p;
+  if ((rc = dalloc(h, sb, &p, fs * nv * d))) return rc;
+  h->E = p;
+  if ((rc = dalloc(h, sb, &h->block_sum, (nv + 255) / 256 + 1))) return rc;
+  if ((rc = dalloc(h, sb, &h->total, 2))) return rc;
+  if ((rc = dalloc(h, sb, &h->resid2, 2))) return rc;
+  if ((rc = dalloc(h, sb, &p, sizeof(double) * d * n))) return rc;
+  h->Ep = p;
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(h->V, 0, fs * nv, s));
+  CK(cudaMemsetAsync(h->E, 0, fs * nv * d, s));
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int32_t), s));
+  CK(cudaMemsetAsync(h->scalars, 0, sizeof(int32_t) * 8, s));
+  CK(cudaMemsetAsync(h->total, 0, sizeof(double) * 2, s));
+  CK(cudaMemsetAsync(h->resid2, 0, sizeof(double) * 2, s));
+  return PIC_OK;
+}
+
+// Stable re-bin of the pushed state [1] into the current state [0].
+// old_start == NULL: fresh particles, every one counted as a mover.
+int rebin_and_gather(pic_t h, const int32_t *old_start) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n;
+  RebinArgs r{};
+  r.n = n;
+  r.n_keys = h->dt.n_keys;
+  r.count = h->count;
+  r.keyn = h->key[1];
+  r.old_start = old_start;
+  r.new_start = h->start_new;
+  r.mover_words = h->mover_words;
+  r.block_movers = h->block_movers;
+  r.block_offsets = h->block_offsets;
+  r.movers = h->movers;
+  r.n_stay = h->n_stay;
+  r.cursor = h->cursor;
+  r.perm = h->perm;
+  r.tile_sums = h->tile_sums;
+  r.tile_sums2 = h->tile_sums2;
+  r.scalars = h->scalars;
+  launch_rebin(r, s);
+  const int d = h->d;
+  if (h->split) {
+    launch_gather_f32(h->perm, n, d, (const float *)h->pos[1], (float *)h->pos[0], s);
+    launch_gather_f32(h->perm, n, d, (const float *)h->vel[1], (float *)h->vel[0], s);
+  } else {
+    launch_gather_f64(h->perm, n, d, (const double *)h->pos[1], (double *)h->pos[0], s);
+    launch_gather_f64(h->perm, n, d, (const double *)h->vel[1], (double *)h->vel[0], s);
+  }
+  launch_gather_i32(h->perm, n, h->leaf[1], h->leaf[0], s);
+  launch_gather_i32(h->perm, n, h->key[1], h->key[0], s);
+  if (h->cfg.track_ids) {
+    launch_gather_i32(h->perm, n, h->ids[0], h->ids[1], s);
+    std::swap(h->ids[0], h->ids[1]);
+  }
+  std::swap(h->start_cur, h->start_new);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+// Keys of fresh state in [1] -> counts -> re-bin.
+int bin_fresh(pic_t h) {
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(h->count, 0, sizeof(int32_t) * h->dt.n_keys, s));
+  launch_count_all(h->key[1], h->n, h->count, h->mover_words, h->block_movers, s);
+  return rebin_and_gather(h, nullptr);
+}
+
+int deposit(pic_t h) {
+  launch_deposit(h->dt, h->split, h->start_cur, h->pos[0], h->n, h->part, h->cfg.q, h->cfg.ion, h->Q,
+                 h->block_sum, h->total, h->stream);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+int field(pic_t h, pic_solve_fn hook, void *user) {
+  cudaStream_t s = h->stream;
+  if (hook) {
+    int r = hook(user, h->Q, h->E, h->dt.n_vert, h->split ? PIC_FP32_SPLIT : PIC_FP64, (void *)s);
+    if (r != 0) return fail(h, PIC_EHOOK, "field-solve hook returned " + std::to_string(r));
+    return PIC_OK;
+  }
+  launch_solve(h->dt, h->split, h->Q, h->total, h->b, h->V, h->Vtmp, h->cfg.sweeps, h->cfg.omega, h->block_sum,
+               h->resid2, s);
+  launch_efield(h->dt, h->split, h->V, h->E, s);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+int push_and_rebin(pic_t h, double dt) {
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(h->count, 0, sizeof(int32_t) * h->dt.n_keys, s));
+  if (h->split) {
+    Push32Args a{};
+    a.n = h->n;
+    a.o = (const float *)h->pos[0];
+    a.v = (const float *)h->vel[0];
+    a.leaf = h->leaf[0];
+    a.key = h->key[0];
+    a.to = (float *)h->pos[1];
+    a.tv = (float *)h->vel[1];
+    a.tleaf = h->leaf[1];
+    a.keyn = h->key[1];
+    a.E = (const float *)h->E;
+    a.qmdt = (float)(h->cfg.qm * dt);
+    a.dt = dt;
+    a.count = h->count;
+    a.mover_words = h->mover_words;
+    a.block_movers = h->block_movers;
+    a.err = h->err;
+    launch_push32(h->dt, a, s);
+  } else {
+    Push64Args a{};
+    a.n = h->n;
+    a.x = (const double *)h->pos[0];
+    a.v = (const double *)h->vel[0];
+    a.leaf = h->leaf[0];
+    a.key = h->key[0];
+    a.tx = (double *)h->pos[1];
+    a.tv = (double *)h->vel[1];
+    a.tleaf = h->leaf[1];
+    a.keyn = h->key[1];
+    a.E = (const double *)h->E;
+    a.qmdt = h->cfg.qm * dt;
+    a.dt = dt;
+    a.count = h->count;
+    a.mover_words = h->mover_words;
+    a.block_movers = h->block_movers;
+    a.err = h->err;
+    launch_push64(h->dt, a, s);
+  }
+  CK(cudaGetLastError());
+  return rebin_and_gather(h, h->start_cur);
+}
+
+int check_handle(pic_t h) { return h ? PIC_OK : PIC_EINVAL; }
+
+int copy_out(pic_t h, void *dst, const void *src, size_t bytes, int32_t where) {
+  if (!dst) return PIC_OK;
+  if (where == PIC_HOST) {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  } else {
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return PIC_OK;
+}
+
+int copy_in(pic_t h, void *dst, const void *src, size_t bytes, int32_t where) {
+  CK(cudaMemcpyAsync(dst, src, bytes, where == PIC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                     h->stream));
+  return PIC_OK;
+}
+
+// Load FP64 particles (host or device) into state [1] and bin them.
+int load_particles64(pic_t h, const double *x, const double *v, int32_t where) {
+  cudaStream_t s = h->stream;
+  const size_t bytes = sizeof(double) * h->d * h->n;
+  int rc;
+  if (h->split) {
+    double *xs = (double *)h->Ep;
+    double *vs = nullptr;
+    std::vector<DevBuf> tmp;
+    if ((rc = dalloc(h, tmp, &vs, (size_t)h->d * h->n))) return rc;
+    if ((rc = copy_in(h, xs, x, bytes, where))) { free_bufs(h, tmp); return rc; }
+    if ((rc = copy_in(h, vs, v, bytes, where))) { free_bufs(h, tmp); return rc; }
+    launch_init32(h->dt, xs, vs, h->n, h->leaf[1], (float *)h->pos[1], (float *)h->vel[1], h->key[1], h->err, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    free_bufs(h, tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "particle conversion");
+  } else {
+    if ((rc = copy_in(h, h->pos[1], x, bytes, where))) return rc;
+    if ((rc = copy_in(h, h->vel[1], v, bytes, where))) return rc;
+    launch_init64(h->dt, (double *)h->pos[1], h->n, h->leaf[1], h->key[1], h->err, s);
+  }
+  CK(cudaGetLastError());
+  return bin_fresh(h);
+}
+
+int read_err(pic_t h, int32_t *err) {
+  CK(cudaMemcpyAsync(err, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pic_strerror(int code) {
+  switch (code) {
+    case PIC_OK: return "ok";
+    case PIC_EINVAL: return "invalid argument or malformed tree";
+    case PIC_ENOMEM: return "out of memory";
+    case PIC_ERANGE: return "non-finite position or velocity";
+    case PIC_EHOOK: return "field-solve hook failed";
+    case PIC_ETIMEOUT: return "device wait timed out";
+    case PIC_ECUDA: return "CUDA runtime error";
+    case PIC_ESTATE: return "call not valid in this state";
+    default: return "unknown error";
+  }
+}
+
+const char *pic_last_error(pic_t h) { return h ? h->last_error.c_str() : "NULL handle"; }
+
+void pic_destroy(pic_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_bufs(h, h->state_bufs);
+  free_bufs(h, h->tree_bufs);
+  delete h;
+}
+
+int pic_create(pic_t *out, const pic_tree_desc *tree, const pic_particles_desc *parts, const pic_config *cfg) {
+  if (!out) return PIC_EINVAL;
+  *out = nullptr;
+  if (!tree || !parts || !cfg) return PIC_EINVAL;
+  if (cfg->scheme != PIC_PIT && cfg->scheme != PIC_PIDT) return PIC_EINVAL;
+  if (cfg->precision != PIC_FP64 && cfg->precision != PIC_FP32_SPLIT) return PIC_EINVAL;
+  if (parts->n < 0 || parts->n >= INT32_MAX || (parts->n > 0 && (!parts->x || !parts->v))) return PIC_EINVAL;
+  if (cfg->sweeps < 0) return PIC_EINVAL;
+  if (parts->where != PIC_HOST && parts->where != PIC_DEVICE) return PIC_EINVAL;
+  if (parts->where == PIC_HOST) {
+    size_t m = (size_t)tree->d * parts->n;
+    if (tree->d == 2 || tree->d == 3)
+      for (size_t i = 0; i < m; ++i)
+        if (!std::isfinite(parts->x[i]) || !std::isfinite(parts->v[i])) return PIC_ERANGE;
+  }
+  pic_t h = new (std::nothrow) pic_s();
+  if (!h) return PIC_ENOMEM;
+  h->cfg = *cfg;
+  h->scheme = cfg->scheme;
+  h->split = cfg->precision == PIC_FP32_SPLIT;
+  h->n = parts->n;
+  h->stream = (cudaStream_t)cfg->stream;
+  cudaGetDevice(&h->device);
+  int rc;
+  cudaError_t e = set_constants(h->stream);
+  if (e != cudaSuccess) { rc = cuda_fail(h, e, "set_constants"); pic_destroy(h); return rc; }
+  if ((rc = install_tree(h, tree))) { pic_destroy(h); return rc; }
+  e = set_kref(h->d, h->stream);
+  if (e != cudaSuccess) { rc = cuda_fail(h, e, "set_kref"); pic_destroy(h); return rc; }
+  if ((rc = alloc_state(h))) { pic_destroy(h); return rc; }
+  if (h->n > 0) {
+    std::vector<int32_t> iota(h->n);
+    for (int64_t i = 0; i < h->n; ++i) iota[i] = (int32_t)i;
+    e = cudaMemcpy(h->ids[0], iota.data(), sizeof(int32_t) * h->n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { rc = cuda_fail(h, e, "ids"); pic_destroy(h); return rc; }
+  }
+  if ((rc = load_particles64(h, parts->x, parts->v, parts->where))) { pic_destroy(h); return rc; }
+  int32_t err = 0;
+  if ((rc = read_err(h, &err))) { pic_destroy(h); return rc; }
+  if (err) { pic_destroy(h); return PIC_ERANGE; }
+  *out = h;
+  return PIC_OK;
+}
+
+int pic_info(pic_t h, pic_info_t *o) {
+  if (check_handle(h) || !o) return PIC_EINVAL;
+  o->d = h->d;
+  o->scheme = h->scheme;
+  o->precision = h->split ? PIC_FP32_SPLIT : PIC_FP64;
+  o->depth = h->ht.depth;
+  o->n_particles = h->n;
+  o->n_leaves = h->dt.n_leaves;
+  o->n_vertices = h->dt.n_vert;
+  o->n_buckets = h->scheme == PIC_PIT ? h->dt.n_leaves : h->dt.n_pv;
+  o->n_keys = h->dt.n_keys;
+  o->uniform = h->dt.uniform;
+  o->device_bytes = h->device_bytes;
+  return PIC_OK;
+}
+
+int pic_init_leapfrog(pic_t h, double dt, pic_solve_fn hook, void *user) {
+  if (check_handle(h)) return PIC_EINVAL;
+  int rc;
+  if ((rc = deposit(h))) return rc;
+  if ((rc = field(h, hook, user))) return rc;
+  launch_gather_only(h->dt, h->split, h->pos[0], h->leaf[0], h->n, h->E, h->Ep, h->stream);
+  launch_half_kick(h->split, h->Ep, h->n * h->d, h->cfg.qm * (0.5 * dt), h->vel[0], h->stream);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+int pic_step(pic_t h, double dt, pic_solve_fn hook, void *user) {
+  if (check_handle(h)) return PIC_EINVAL;
+  int rc;
+  if ((rc = deposit(h))) return rc;
+  if ((rc = field(h, hook, user))) return rc;
+  if ((rc = push_and_rebin(h, dt))) return rc;
+  h->step++;
+  return PIC_OK;
+}
+
+int pic_step_fixed_field(pic_t h, double dt) {
+  if (check_handle(h)) return PIC_EINVAL;
+  int rc;
+  if ((rc = deposit(h))) return rc;
+  if ((rc = push_and_rebin(h, dt))) return rc;
+  h->step++;
+  return PIC_OK;
+}
+
+int pic_sync(pic_t h) {
+  if (check_handle(h)) return PIC_EINVAL;
+  int32_t err = 0;
+  int rc = read_err(h, &err);
+  if (rc) return rc;
+  return err ? fail(h, PIC_ERANGE, "non-finite position or velocity") : PIC_OK;
+}
+
+int pic_deposit(pic_t h, double *Q_out, int32_t where) {
+  if (check_handle(h) || !Q_out) return PIC_EINVAL;
+  int rc;
+  if ((rc = deposit(h))) return rc;
+  const int64_t nv = h->dt.n_vert;
+  if (h->split) {
+    launch_widen((const float *)h->Q, nv, (double *)h->Ep, h->stream);
+    return copy_out(h, Q_out, h->Ep, sizeof(double) * nv, where);
+  }
+  return copy_out(h, Q_out, h->Q, sizeof(double) * nv, where);
+}
+
+int pic_field(pic_t h, double *E_out, int32_t where) {
+  if (check_handle(h) || !E_out) return PIC_EINVAL;
+  const int64_t m = h->dt.n_vert * h->d;
+  if (h->split) {
+    launch_widen((const float *)h->E, m, (double *)h->Ep, h->stream);
+    return copy_out(h, E_out, h->Ep, sizeof(double) * m, where);
+  }
+  return copy_out(h, E_out, h->E, sizeof(double) * m, where);
+}
+
+int pic_potential(pic_t h, double *V_out, int32_t where) {
+  if (check_handle(h) || !V_out) return PIC_EINVAL;
+  const int64_t m = h->dt.n_vert;
+  if (h->split) {
+    launch_widen((const float *)h->V, m, (double *)h->Ep, h->stream);
+    return copy_out(h, V_out, h->Ep, sizeof(double) * m, where);
+  }
+  return copy_out(h, V_out, h->V, sizeof(double) * m, where);
+}
+
+int pic_bins(pic_t h, int64_t *bucket_start, int32_t *perm, int32_t where) {
+  if (check_handle(h)) return PIC_EINVAL;
+  const int64_t nk = h->dt.n_keys;
+  if (bucket_start) {
+    std::vector<int32_t> st(nk + 1);
+    CK(cudaMemcpyAsync(st.data(), h->start_cur, sizeof(int32_t) * (nk + 1), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const int stride = h->scheme == PIC_PIT ? 1 : h->dt.nc;
+    const int64_t nb = nk / stride;
+    std::vector<int64_t> out(nb + 1);
+    for (int64_t b = 0; b <= nb; ++b) out[b] = st[b * stride];
+    if (where == PIC_HOST)
+      std::memcpy(bucket_start, out.data(), sizeof(int64_t) * (nb + 1));
+    else
+      CK(cudaMemcpy(bucket_start, out.data(), sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice));
+  }
+  if (perm) {
+    if (!h->cfg.track_ids) return fail(h, PIC_ESTATE, "particle ids are not tracked (track_ids = 0)");
+    return copy_out(h, perm, h->ids[0], sizeof(int32_t) * h->n, where);
+  }
+  return PIC_OK;
+}
+
+int pic_keys(pic_t h, int32_t *keys, int32_t where) {
+  if (check_handle(h) || !keys) return PIC_EINVAL;
+  return copy_out(h, keys, h->key[0], sizeof(int32_t) * h->n, where);
+}
+
+int pic_get_particles(pic_t h, double *x, double *v, int32_t where) {
+  if (check_handle(h)) return PIC_EINVAL;
+  const int64_t m = h->n * h->d;
+  int rc;
+  if (h->split) {
+    if (x) {
+      launch_absolute_split(h->dt, h->leaf[0], (const float *)h->pos[0], h->n, (double *)h->Ep, h->stream);
+      if ((rc = copy_out(h, x, h->Ep, sizeof(double) * m, where))) return rc;
+    }
+    if (v) {
+      launch_widen((const float *)h->vel[0], m, (double *)h->Ep, h->stream);
+      if ((rc = copy_out(h, v, h->Ep, sizeof(double) * m, where))) return rc;
+    }
+    return PIC_OK;
+  }
+  if ((rc = copy_out(h, x, h->pos[0], sizeof(double) * m, where))) return rc;
+  return copy_out(h, v, h->vel[0], sizeof(double) * m, where);
+}
+
+int pic_get_state(pic_t h, int32_t *leaf, void *x_or_o, void *v, int32_t where) {
+  if (check_handle(h)) return PIC_EINVAL;
+  const size_t fs = h->split ? sizeof(float) : sizeof(double);
+  const size_t m = (size_t)h->n * h->d;
+  cudaMemcpyKind kind = where == PIC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (leaf) CK(cudaMemcpyAsync(leaf, h->leaf[0], sizeof(int32_t) * h->n, kind, h->stream));
+  if (x_or_o) CK(cudaMemcpyAsync(x_or_o, h->pos[0], fs * m, kind, h->stream));
+  if (v) CK(cudaMemcpyAsync(v, h->vel[0], fs * m, kind, h->stream));
+  if (where == PIC_HOST) CK(cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+int pic_set_state(pic_t h, const int32_t *leaf, const void *x_or_o, const void *v, int32_t where) {
+  if (check_handle(h) || !x_or_o || !v) return PIC_EINVAL;
+  if (h->split && !leaf) return fail(h, PIC_EINVAL, "split state needs the leaf array");
+  const size_t fs = h->split ? sizeof(float) : sizeof(double);
+  const size_t m = (size_t)h->n * h->d;
+  int rc;
+  if ((rc = copy_in(h, h->pos[1], x_or_o, fs * m, where))) return rc;
+  if ((rc = copy_in(h, h->vel[1], v, fs * m, where))) return rc;
+  if (h->split) {
+    if ((rc = copy_in(h, h->leaf[1], leaf, sizeof(int32_t) * h->n, where))) return rc;
+    launch_rekey32(h->dt, h->leaf[1], (const float *)h->pos[1], h->n, h->key[1], h->err, h->stream);
+    CK(cudaGetLastError());
+    return bin_fresh(h);
+  }
+  launch_init64(h->dt, (double *)h->pos[1], h->n, h->leaf[1], h->key[1], h->err, h->stream);
+  CK(cudaGetLastError());
+  return bin_fresh(h);
+}
+
+int pic_stats(pic_t h, pic_stats_t *o) {
+  if (check_handle(h) || !o) return PIC_EINVAL;
+  int32_t sc[8];
+  double tot, r2;
+  int32_t err;
+  CK(cudaMemcpyAsync(sc, h->scalars, sizeof(sc), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&tot, h->total, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&r2, h->resid2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&err, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  o->step = h->step;
+  o->movers = sc[1];
+  o->max_bucket = sc[2];
+  o->total_charge = tot;
+  o->residual = std::sqrt(r2);
+  o->error = err ? PIC_ERANGE : PIC_OK;
+  return PIC_OK;
+}
+
+int pic_leaf_table(pic_t h, int32_t *level, int64_t *coords) {
+  if (check_handle(h)) return PIC_EINVAL;
+  const auto &t = h->ht;
+  for (int64_t l = 0; l < t.n_leaves; ++l) {
+    if (level) level[l] = t.leaf_level[l];
+    if (coords)
+      for (int a = 0; a < t.d; ++a) coords[l * t.d + a] = t.leaf_coords[l * t.d + a];
+  }
+  return PIC_OK;
+}
+
+int pic_vertex_table(pic_t h, int64_t *pos) {
+  if (check_handle(h) || !pos) return PIC_EINVAL;
+  const auto &t = h->ht;
+  for (int64_t v = 0; v < t.n_vert; ++v) {
+    int64_t k = t.uniform ? v : t.vert_key[v];
+    for (int a = 0; a < t.d; ++a) {
+      pos[a * t.n_vert + v] = k % t.M;
+      k /= t.M;
+    }
+  }
+  return PIC_OK;
+}
+
+int pic_pidt_table(pic_t h, int32_t *level, int64_t *j) {
+  if (check_handle(h)) return PIC_EINVAL;
+  const auto &t = h->ht;
+  for (int64_t v = 0; v < t.n_pv; ++v) {
+    if (t.uniform) {
+      if (level) level[v] = t.depth;
+      int64_t k = v;
+      for (int a = 0; a < t.d; ++a) {
+        if (j) j[v * t.d + a] = k % t.M;
+        k /= t.M;
+      }
+    } else {
+      if (level) level[v] = t.pv_level[v];
+      if (j)
+        for (int a = 0; a < t.d; ++a) j[v * t.d + a] = t.pv_j[v * t.d + a];
+    }
+  }
+  return PIC_OK;
+}
+
+int pic_retree(pic_t h, const pic_tree_desc *tree) {
+  (void)tree;
+  return fail(h, PIC_ESTATE, "pic_retree is not implemented yet");
+}
+
+int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax) {
+  (void)ppc; (void)dmin; (void)dmax;
+  return fail(h, PIC_ESTATE, "pic_adapt is not implemented yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,294 @@
+"""Thin Python binding of libpic's C ABI (include/pic.h).
+
+Argument marshalling only: every step of the particle path runs in the CUDA
+kernels of libpic.so.  Arrays are numpy (host memory) or torch CUDA tensors
+(device memory; torch supplies the pointer and the stream).  There is no CPU
+fallback: if libpic.so cannot be loaded, :func:`load` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+PIT, PIDT = 0, 1
+FP64, FP32_SPLIT = 0, 1
+HOST, DEVICE = 0, 1
+
+ERRORS = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ERANGE", -4: "PIC_EHOOK",
+          -5: "PIC_ETIMEOUT", -6: "PIC_ECUDA", -7: "PIC_ESTATE"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lock = threading.Lock()
+_lib = None
+
+
+class PicError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class TreeDesc(C.Structure):
+    _fields_ = [("d", C.c_int32), ("n_nodes", C.c_int64), ("flags", C.c_void_p)]
+
+
+class ParticlesDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("v", C.c_void_p), ("where", C.c_int32)]
+
+
+class Config(C.Structure):
+    _fields_ = [("scheme", C.c_int32), ("precision", C.c_int32), ("q", C.c_double), ("qm", C.c_double),
+                ("ion", C.c_double), ("sweeps", C.c_int32), ("omega", C.c_double),
+                ("track_ids", C.c_int32), ("stream", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("d", C.c_int32), ("scheme", C.c_int32), ("precision", C.c_int32), ("depth", C.c_int32),
+                ("n_particles", C.c_int64), ("n_leaves", C.c_int64), ("n_vertices", C.c_int64),
+                ("n_buckets", C.c_int64), ("n_keys", C.c_int64), ("uniform", C.c_int32),
+                ("device_bytes", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("movers", C.c_int64), ("max_bucket", C.c_int64),
+                ("total_charge", C.c_double), ("residual", C.c_double), ("error", C.c_int32)]
+
+
+SOLVE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p)
+
+# (name, restype, argtypes) of every entry point declared in include/pic.h
+SIGNATURES = [
+    ("pic_create", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(TreeDesc), C.POINTER(ParticlesDesc),
+                             C.POINTER(Config)]),
+    ("pic_destroy", None, [C.c_void_p]),
+    ("pic_strerror", C.c_char_p, [C.c_int]),
+    ("pic_last_error", C.c_char_p, [C.c_void_p]),
+    ("pic_info", C.c_int, [C.c_void_p, C.POINTER(Info)]),
+    ("pic_init_leapfrog", C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
+    ("pic_step", C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]),
+    ("pic_step_fixed_field", C.c_int, [C.c_void_p, C.c_double]),
+    ("pic_sync", C.c_int, [C.c_void_p]),
+    ("pic_deposit", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    ("pic_field", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    ("pic_potential", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    ("pic_bins", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    ("pic_keys", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    ("pic_get_particles", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    ("pic_get_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    ("pic_set_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    ("pic_stats", C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    ("pic_leaf_table", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pic_vertex_table", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("pic_pidt_table", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pic_retree", C.c_int, [C.c_void_p, C.POINTER(TreeDesc)]),
+    ("pic_adapt", C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32]),
+]
+
+
+def lib_path() -> str:
+    return os.path.join(_HERE, "libpic.so")
+
+
+def load(build_if_missing: bool = True):
+    """Load libpic.so (building it in-tree first when missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            from . import build as _build
+            _build.build()
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libpic.so not found at {path}; run paper_1508_02435_gb300/build.py")
+        lib = C.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    """(pointer, where) of a numpy array or a torch tensor."""
+    if a is None:
+        return None, HOST
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data_as(C.c_void_p), HOST
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return C.c_void_p(a.data_ptr()), DEVICE if a.is_cuda else HOST
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class Pic:
+    """One plasma instance on the GPU (a libpic handle)."""
+
+    def __init__(self, d: int, flags: np.ndarray, x, v, *, scheme: int = PIT, precision: int = FP64,
+                 q: float = -1.0, qm: float = -1.0, ion: float = 1.0, sweeps: int = 100,
+                 omega: float = 0.8, track_ids: bool = True, stream=None):
+        self.lib = load()
+        self.d = d
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        self._flags = flags
+        tree = TreeDesc(d, len(flags), flags.ctypes.data_as(C.c_void_p))
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            v = np.ascontiguousarray(v, dtype=np.float64)
+        xp, where = _ptr(x)
+        vp, _ = _ptr(v)
+        n = int(x.shape[1]) if x.ndim == 2 else 0
+        parts = ParticlesDesc(n, xp, vp, where)
+        st = C.c_void_p(stream.cuda_stream) if stream is not None and hasattr(stream, "cuda_stream") else \
+            C.c_void_p(stream)
+        self.cfg = Config(scheme, precision, q, qm, ion, sweeps, omega, 1 if track_ids else 0, st)
+        h = C.c_void_p()
+        rc = self.lib.pic_create(C.byref(h), C.byref(tree), C.byref(parts), C.byref(self.cfg))
+        if rc != 0:
+            raise PicError(rc, self.lib.pic_strerror(rc).decode())
+        self.h = h
+        self.n = n
+        self.scheme = scheme
+        self.precision = precision
+        self._info = self.info()
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise PicError(rc, self.lib.pic_last_error(self.h).decode())
+
+    # ---- calls ---------------------------------------------------------
+    def info(self) -> Info:
+        out = Info()
+        self._check(self.lib.pic_info(self.h, C.byref(out)))
+        return out
+
+    def init_leapfrog(self, dt: float, hook=None, user=None):
+        self._check(self.lib.pic_init_leapfrog(self.h, dt, hook, user))
+
+    def step(self, dt: float, hook=None, user=None):
+        self._check(self.lib.pic_step(self.h, dt, hook, user))
+
+    def step_fixed_field(self, dt: float):
+        self._check(self.lib.pic_step_fixed_field(self.h, dt))
+
+    def sync(self):
+        self._check(self.lib.pic_sync(self.h))
+
+    def stats(self) -> Stats:
+        out = Stats()
+        self._check(self.lib.pic_stats(self.h, C.byref(out)))
+        return out
+
+    @property
+    def n_vertices(self) -> int:
+        return int(self._info.n_vertices)
+
+    @property
+    def n_buckets(self) -> int:
+        return int(self._info.n_buckets)
+
+    def deposit(self, out=None):
+        out = np.zeros(self.n_vertices) if out is None else out
+        p, w = _ptr(out)
+        self._check(self.lib.pic_deposit(self.h, p, w))
+        return out
+
+    def field(self, out=None):
+        out = np.zeros((self.d, self.n_vertices)) if out is None else out
+        p, w = _ptr(out)
+        self._check(self.lib.pic_field(self.h, p, w))
+        return out
+
+    def potential(self, out=None):
+        out = np.zeros(self.n_vertices) if out is None else out
+        p, w = _ptr(out)
+        self._check(self.lib.pic_potential(self.h, p, w))
+        return out
+
+    def bins(self, with_ids: bool = True):
+        start = np.zeros(self.n_buckets + 1, np.int64)
+        perm = np.zeros(self.n, np.int32) if with_ids else None
+        sp, _ = _ptr(start)
+        pp, _ = _ptr(perm)
+        self._check(self.lib.pic_bins(self.h, sp, pp, HOST))
+        return start, perm
+
+    def keys(self):
+        out = np.zeros(self.n, np.int32)
+        p, w = _ptr(out)
+        self._check(self.lib.pic_keys(self.h, p, w))
+        return out
+
+    def particles(self):
+        x = np.zeros((self.d, self.n))
+        v = np.zeros((self.d, self.n))
+        self._check(self.lib.pic_get_particles(self.h, _ptr(x)[0], _ptr(v)[0], HOST))
+        return x, v
+
+    def get_state(self, leaf=None, pos=None, vel=None):
+        """Native state in storage order into the given arrays (numpy or CUDA
+        tensors); allocates numpy arrays when none are given."""
+        if pos is None:
+            dt = np.float32 if self.precision == FP32_SPLIT else np.float64
+            leaf = np.zeros(self.n, np.int32)
+            pos = np.zeros((self.d, self.n), dt)
+            vel = np.zeros((self.d, self.n), dt)
+        lp, w = _ptr(leaf)
+        pp, w2 = _ptr(pos)
+        vp, _ = _ptr(vel)
+        self._check(self.lib.pic_get_state(self.h, lp, pp, vp, w2))
+        return leaf, pos, vel
+
+    def set_state(self, leaf, pos, vel):
+        lp, _ = _ptr(leaf)
+        pp, w = _ptr(pos)
+        vp, _ = _ptr(vel)
+        self._check(self.lib.pic_set_state(self.h, lp, pp, vp, w))
+
+    def leaf_table(self):
+        nl = int(self._info.n_leaves)
+        lev = np.zeros(nl, np.int32)
+        co = np.zeros((nl, self.d), np.int64)
+        self._check(self.lib.pic_leaf_table(self.h, _ptr(lev)[0], _ptr(co)[0]))
+        return lev, co
+
+    def vertex_table(self):
+        pos = np.zeros((self.d, self.n_vertices), np.int64)
+        self._check(self.lib.pic_vertex_table(self.h, _ptr(pos)[0]))
+        return pos
+
+    def pidt_table(self):
+        if self.scheme != PIDT:
+            raise ValueError("PIDT owner vertices exist only for the PIDT scheme")
+        nb = self.n_buckets
+        lev = np.zeros(nb, np.int32)
+        j = np.zeros((nb, self.d), np.int64)
+        self._check(self.lib.pic_pidt_table(self.h, _ptr(lev)[0], _ptr(j)[0]))
+        return lev, j
+
+    def retree(self, flags):
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        tree = TreeDesc(self.d, len(flags), flags.ctypes.data_as(C.c_void_p))
+        self._check(self.lib.pic_retree(self.h, C.byref(tree)))
+        self._flags = flags
+        self._info = self.info()
+
+    def adapt(self, ppc: int, dmin: int, dmax: int):
+        self._check(self.lib.pic_adapt(self.h, ppc, dmin, dmax))
+        self._info = self.info()

@@ -1,0 +1,43 @@
+"""CPU-only checks of the C-ABI boundary: the library builds, loads and exports
+every entry point that include/pic.h declares, and the Python binding binds
+each of them.  No compute call is made (no GPU here)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1508_02435_gb300 import pic
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "pic.h")).read()
+    return sorted(set(re.findall(r"PIC_API[^;]*?\b(pic_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("pic_create", "pic_step", "pic_deposit", "pic_bins", "pic_destroy"):
+        assert required in names
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    lib = pic.load()
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_binding_covers_every_declared_symbol():
+    bound = {name for name, _, _ in pic.SIGNATURES}
+    assert bound == set(declared_symbols())
+
+
+def test_strerror_is_host_only():
+    lib = pic.load()
+    assert lib.pic_strerror(0) == b"ok"
+    assert b"malformed" in lib.pic_strerror(-1)

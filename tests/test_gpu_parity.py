@@ -1,0 +1,217 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Keys, buckets and integer state are compared bit for bit; FP64 floats within
+1e-12 relative (they are expected bit-identical: both sides use the same
+operation order with no fused multiply-add); FP32 split results within a few
+FP32 ulps of the mirror.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1508_02435_gb300 import pic
+from paper_1508_02435_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU hosts
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+REL64 = 1e-12
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    scale = max(np.max(np.abs(b)), 1e-300)
+    return float(np.max(np.abs(a - b)) / scale) if a.size else 0.0
+
+
+def make(d, flags, x, v, scheme, precision, **kw):
+    return pic.Pic(d, flags, x, v, scheme=scheme, precision=precision, **kw)
+
+
+def random_case(d, depth, p, seed, n, vmax=0.05, min_depth=1):
+    flags = W.random_tree_flags(d, depth, p, seed, min_depth=min_depth)
+    x, v = W.random_particles(d, n, seed, vmax=vmax)
+    return flags, x, v
+
+
+TREES = [
+    pytest.param(2, lambda: W.uniform_tree_flags(2, 3), id="2d-uniform-d3"),
+    pytest.param(2, lambda: W.random_tree_flags(2, 5, 0.3, 5, min_depth=2), id="2d-adaptive-d5"),
+    pytest.param(3, lambda: W.uniform_tree_flags(3, 2), id="3d-uniform-d2"),
+    pytest.param(3, lambda: W.random_tree_flags(3, 3, 0.3, 6, min_depth=1), id="3d-adaptive-d3"),
+]
+
+
+# ---------------------------------------------------------------------------
+# tables
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,flags_fn", TREES)
+def test_tables_match_oracle(d, flags_fn):
+    flags = flags_fn()
+    x, v = W.random_particles(d, 1000, 1)
+    ot = oracle.Tree(d, flags)
+    g = make(d, flags, x, v, pic.PIT, pic.FP64)
+    lev, co = g.leaf_table()
+    olev, oco = ot.leaf_info()
+    assert np.array_equal(lev, olev) and np.array_equal(co, oco)
+    assert np.array_equal(g.vertex_table(), ot.vertex_pos())
+    gp = make(d, flags, x, v, pic.PIDT, pic.FP64)
+    plev, pj = gp.pidt_table()
+    oplev, opj = ot.pidt_vertices()
+    assert np.array_equal(plev, oplev) and np.array_equal(pj, opj)
+
+
+# ---------------------------------------------------------------------------
+# a1/a2 keys and a6 buckets at creation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scheme", [pic.PIT, pic.PIDT])
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_SPLIT])
+@pytest.mark.parametrize("d,flags_fn", TREES)
+def test_initial_keys_and_buckets(d, flags_fn, scheme, precision):
+    flags = flags_fn()
+    n = 70_001  # several tiles and a ragged tail
+    x, v = W.random_particles(d, n, 7)
+    # particles on faces and at the wrap-around point
+    x[:, :27] = (np.arange(27) % 9)[None, :] / 9.0
+    x[:, 27] = 1.0 - 1e-17
+    x[:, 28] = -0.25
+    ot = oracle.Tree(d, flags)
+    prm = oracle.Params(scheme=scheme)
+    st = oracle.State64(ot, x, v, prm) if precision == pic.FP64 else oracle.State32(ot, x, v, prm)
+    g = make(d, flags, x, v, scheme, precision)
+    keys = g.keys()
+    start, ids = g.bins()
+    assert np.array_equal(ids, st.ids)                     # same storage order
+    assert np.array_equal(keys, st.key)                    # bit-exact keys
+    nb = 1 << d if scheme == pic.PIDT else 1
+    assert np.array_equal(start, st.start[::nb])
+    if precision == pic.FP32_SPLIT:
+        leaf, o, vf = g.get_state()
+        assert np.array_equal(leaf, st.leaf)
+        assert np.array_equal(o, st.o) and np.array_equal(vf, st.v)
+    else:
+        xs, vs = g.particles()
+        assert np.array_equal(xs, st.x) and np.array_equal(vs, st.v)
+
+
+# ---------------------------------------------------------------------------
+# one full step: deposit, solve, field, gather + push, re-bin
+# ---------------------------------------------------------------------------
+
+def compare_step64(g, st, d):
+    Qo, tot, res, Eo = st.step(0.1)
+    g.step(0.1)
+    g.sync()
+    return Qo, Eo
+
+
+@pytest.mark.parametrize("scheme", [pic.PIT, pic.PIDT])
+@pytest.mark.parametrize("d,flags_fn", TREES)
+def test_fp64_steps_match_oracle(d, flags_fn, scheme):
+    flags = flags_fn()
+    n = 40_000
+    x, v = W.random_particles(d, n, 11, vmax=0.5)   # tunnelling: up to ~5 finest cells per step
+    q = -1.0 / n
+    prm = oracle.Params(scheme=scheme, q=q, qm=-1.0, ion=1.0, sweeps=30, omega=0.8)
+    ot = oracle.Tree(d, flags)
+    st = oracle.State64(ot, x, v, prm)
+    g = make(d, flags, x, v, scheme, pic.FP64, q=q, qm=-1.0, ion=1.0, sweeps=30, omega=0.8)
+    for step in range(3):
+        Qo, tot, res, Eo = st.step(0.1)
+        Qg_before = g.deposit()
+        assert rel_err(Qg_before, Qo) <= REL64, f"deposit step {step}"
+        g.step(0.1)
+        g.sync()
+        assert rel_err(g.potential(), st.V) <= REL64, f"potential step {step}"
+        assert rel_err(g.field(), Eo) <= REL64, f"field step {step}"
+        keys = g.keys()
+        start, ids = g.bins()
+        assert np.array_equal(ids, st.ids), f"storage order step {step}"
+        assert np.array_equal(keys, st.key), f"keys step {step}"
+        xs, vs = g.particles()
+        assert rel_err(xs, st.x) <= REL64 and rel_err(vs, st.v) <= REL64
+        s = g.stats()
+        assert abs(s.total_charge - tot) <= 1e-12
+        assert s.error == 0
+
+
+@pytest.mark.parametrize("scheme", [pic.PIT, pic.PIDT])
+@pytest.mark.parametrize("d,flags_fn", TREES)
+def test_split_steps_match_mirror(d, flags_fn, scheme):
+    flags = flags_fn()
+    n = 40_000
+    x, v = W.random_particles(d, n, 12, vmax=0.5)
+    q = -1.0 / n
+    prm = oracle.Params(scheme=scheme, q=q, qm=-1.0, ion=1.0, sweeps=30, omega=0.8)
+    ot = oracle.Tree(d, flags)
+    st = oracle.State32(ot, x, v, prm)
+    g = make(d, flags, x, v, scheme, pic.FP32_SPLIT, q=q, qm=-1.0, ion=1.0, sweeps=30, omega=0.8)
+    for step in range(3):
+        Qo, tot, res, Eo = st.step(0.1)
+        g.step(0.1)
+        g.sync()
+        # field arithmetic is FP32 with the same operation order
+        assert rel_err(g.field(), Eo) <= 1e-5, f"field step {step}"
+        leaf, o, vf = g.get_state()
+        start, ids = g.bins()
+        assert np.array_equal(ids, st.ids), f"storage order step {step}"
+        assert np.array_equal(g.keys(), st.key), f"keys step {step}"
+        assert np.array_equal(leaf, st.leaf)
+        assert np.array_equal(o, st.o) and np.array_equal(vf, st.v)
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_empty_particle_set():
+    flags = W.uniform_tree_flags(2, 2)
+    x = np.zeros((2, 0))
+    g = make(2, flags, x, x.copy(), pic.PIT, pic.FP64, q=0.0)
+    g.step(0.1)
+    g.sync()
+    start, ids = g.bins()
+    assert start[-1] == 0 and ids.size == 0
+
+
+def test_malformed_tree_rejected():
+    with pytest.raises(pic.PicError) as e:
+        make(2, np.array([1, 0, 0], np.uint8), np.zeros((2, 1)), np.zeros((2, 1)), pic.PIT, pic.FP64)
+    assert e.value.code == -1
+
+
+def test_nonfinite_input_rejected():
+    x = np.full((2, 4), 0.5)
+    x[0, 2] = np.nan
+    with pytest.raises(pic.PicError) as e:
+        make(2, W.uniform_tree_flags(2, 2), x, np.zeros((2, 4)), pic.PIT, pic.FP64)
+    assert e.value.code == -3
+
+
+def test_device_inputs_and_determinism():
+    """Device-resident input gives the same result, and two runs agree bit for bit."""
+    d = 2
+    flags = W.random_tree_flags(2, 5, 0.3, 9, min_depth=2)
+    x, v = W.random_particles(d, 30_000, 9, vmax=0.3)
+    outs = []
+    for dev in (False, True, True):
+        xi = torch.from_numpy(x).cuda() if dev else x
+        vi = torch.from_numpy(v).cuda() if dev else v
+        g = make(d, flags, xi, vi, pic.PIT, pic.FP32_SPLIT, q=-1.0 / 30_000, sweeps=10)
+        for _ in range(3):
+            g.step(0.1)
+        g.sync()
+        outs.append((g.get_state(), g.bins(), g.deposit()))
+    for o in outs[1:]:
+        for a, b in zip(o[0], outs[0][0]):
+            assert np.array_equal(a, b)
+        assert np.array_equal(o[1][1], outs[0][1][1])
+        assert np.array_equal(o[2], outs[0][2])
