@@ -1,0 +1,322 @@
+"""Benchmark of the PIT/PIDT particle step on one GB300 (or N replicas).
+
+Metric: particle updates per second of the hot path -- deposit of the current
+positions, fused gather + leapfrog push + re-location + key, stable re-bin --
+with the field held fixed (the Poisson solve is auxiliary and timed apart).
+
+Default workload: the 3D uniform Langmuir plasma, tripartition depth 5 (243^3
+leaves), 8 particles per cell (114,791,256 particles), FP32 split precision
+(int32 leaf + 3 x FP32 offset + 3 x FP32 velocity), PIT buckets.
+
+One JSON line on rank 0.  `--impl reference` times the CPU oracle instead, on a
+bounded sample of the same workload.  Under torchrun every rank runs its own
+replica (the path has no exchange step on one instance per GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1508_02435_gb300 import workloads as W  # noqa: E402
+
+METRIC = "particle-updates/sec (push+rebin+deposit+gather)"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+# Algorithmic bytes per particle-step of the whole hot path (deposit read,
+# state read, state write, amortised grid terms), 3D split / FP64, 2D split /
+# FP64 at 16 particles per cell.
+STEP_BYTES = {(3, 1): 70.0, (3, 0): 132.0, (2, 1): 48.5, (2, 0): 89.0}
+
+
+def kernel_bytes(d: int, split: bool, ppc: float) -> dict:
+    """Algorithmic bytes per particle of each phase as the kernels implement it:
+    what each phase must read and write, grid arrays amortised over ppc."""
+    f = 4 if split else 8
+    state = (d * 2 * f + 4)                       # position/offset + velocity + leaf
+    grid_e = d * f / ppc                          # vertex field, read once
+    nc = 1 << d
+    return {
+        "deposit": d * f + (nc * f) / ppc * 2 + f / ppc,   # offsets + leaf partials w/r + Q
+        "push": state + grid_e + state + 4,                # state in, field, state out, key
+        "rebin": 4 + 4 + 4 + 4 + 4,                        # keys, perm, mover list
+        "permute": 4 + state + state + 4,                  # perm, gather in, scatter out, key
+    }
+
+
+def load_peaks():
+    try:
+        return json.load(open(PEAKS)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                mx = float(parts[2].split()[0])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload(name: str):
+    if name == "langmuir3d":
+        w = W.langmuir(3, 5, 8, vth=0.05, dt=0.1, steps=200)
+        return w, {"workload": "3D uniform Langmuir, depth 5 (243^3 leaves), 8 ppc, "
+                               f"{w.n} particles, vth=0.05, omega_p dt=0.1",
+                   "precision": "fp32_split", "scheme": "PIT", "d": 3, "ppc": 8}
+    if name == "langmuir3d-small":
+        w = W.langmuir(3, 4, 8, vth=0.05, dt=0.1, steps=200)
+        return w, {"workload": "3D uniform Langmuir, depth 4 (81^3 leaves), 8 ppc, "
+                               f"{w.n} particles (profiling case)",
+                   "precision": "fp32_split", "scheme": "PIT", "d": 3, "ppc": 8}
+    if name == "langmuir2d":
+        w = W.langmuir(2, 3, 16)
+        return w, {"workload": f"2D uniform Langmuir, depth 3 (27^2 leaves), 16 ppc, {w.n} particles",
+                   "precision": "fp64", "scheme": "PIT", "d": 2, "ppc": 16}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def oracle_rate(d: int, split: bool, scheme: int, budget_s: float):
+    """The CPU oracle, as it stands, timed on a bounded sample of the workload:
+    the same 3D Langmuir plasma on a depth-3 tree (27^3 leaves, 8 ppc, 157,464
+    particles), deposit + gather/push + re-bin with the field held fixed."""
+    import oracle
+
+    w = W.langmuir(d, 3, 8 if d == 3 else 16, vth=0.05)
+    tree = oracle.Tree(d, w.flags)
+    prm = oracle.Params(scheme=scheme, q=w.q, qm=w.qm, ion=w.ion, sweeps=10, omega=0.8)
+    st = oracle.State32(tree, w.x, w.v, prm) if split else oracle.State64(tree, w.x, w.v, prm)
+    Q, tot, res, E = st.field()
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        if split:
+            tree.deposit32(scheme, st.leaf, st.o, np.float32(w.q), np.float32(w.ion))
+            tree.push32(st.leaf, st.o, st.v, E, w.qm, w.dt)
+        else:
+            tree.deposit64(scheme, st.x, w.q, w.ion)
+            tree.push64(st.x, st.v, E, w.qm, w.dt)
+        st.rebin()
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return w.n * steps / el, {"kind": "oracle", "cores": 1,
+                              "sample": f"{steps} steps of the depth-3 3D Langmuir sample ({w.n} particles), "
+                                        "single-threaded C oracle, field fixed"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w_name = args.workload
+    d = 3 if w_name.startswith("langmuir3d") else 2
+    split = d == 3
+    rates = []
+    for _ in range(args.warmup):
+        oracle_rate(d, split, 0, 1.0)
+    for _ in range(args.steps):
+        r, info = oracle_rate(d, split, 0, max(2.0, 20.0 / max(args.steps, 1)))
+        rates.append(r)
+    value = statistics.median(rates)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-updates/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "dtype": "f32" if split else "f64", "data": "synthetic",
+           "config": {"workload": "3D uniform Langmuir (bounded oracle sample: depth 3, 8 ppc)" if d == 3
+                      else "2D uniform Langmuir depth 3", "scheme": "PIT",
+                      "precision": "fp32_split" if split else "fp64"},
+           "cpu_baseline": {"value": value, "unit": "particle-updates/s", **info},
+           "e2e": {"value": value, "unit": "particle-updates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="langmuir3d", choices=["langmuir3d", "langmuir3d-small", "langmuir2d"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_1508_02435_gb300 import pic
+
+    w, cfg = build_workload(args.workload)
+    d = cfg["d"]
+    split = cfg["precision"] == "fp32_split"
+    stream = torch.cuda.Stream()
+    g = pic.Pic(d, w.flags, w.x, w.v, scheme=pic.PIT, precision=pic.FP32_SPLIT if split else pic.FP64,
+                q=w.q, qm=w.qm, ion=w.ion, sweeps=10, omega=0.8, track_ids=False, stream=stream)
+    n = g.n
+    del w.x, w.v
+    g.init_leapfrog(w.dt)
+    for _ in range(max(args.warmup, 3)):
+        g.step_fixed_field(w.dt)
+    g.sync()
+
+    # ---- timed region: device-resident state --------------------------
+    g.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            g.step_fixed_field(w.dt)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    phases = g.phase_times()
+    g.profile(False)
+    st = g.stats()
+    if st.error:
+        raise SystemExit("device reported non-finite particle state")
+    t_max = ms
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    ms_step = t_max / args.steps
+    value = world * n * args.steps / (t_max / 1e3)
+
+    # ---- end to end through the C ABI with host buffers ------------------
+    fs = 4 if split else 8
+    leaf_h = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    pos_h = torch.empty((d, n), dtype=torch.float32 if split else torch.float64, pin_memory=True)
+    vel_h = torch.empty_like(pos_h, pin_memory=True)
+    g.get_state(leaf_h, pos_h, vel_h)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        g.set_state(leaf_h, pos_h, vel_h)
+        g.step_fixed_field(w.dt)
+        g.get_state(leaf_h, pos_h, vel_h)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    state_bytes = n * (4 + 2 * d * fs)
+    e2e_value = world * n * args.e2e_steps / e2e_s
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peaks, peak_kind = load_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    kb = kernel_bytes(d, split, cfg["ppc"])
+    dom = max(("deposit", "push", "rebin", "permute"), key=lambda k: phases[k][0])
+    dom_ms = phases[dom][0] / args.steps
+    achieved = kb[dom] * n / (dom_ms / 1e3) / 1e9
+    step_bytes = STEP_BYTES[(d, 1 if split else 0)]
+    traffic = None
+    launches = sum(k for _, k in phases.values())
+    out = {
+        "metric": METRIC, "value": value, "unit": "particle-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if split else "f64", "data": "synthetic",
+        "config": {**cfg, "n_particles": n, "field": "held fixed (solve timed apart)",
+                   "l2": "inputs larger than L2 (state > 3 GB)",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_particle": kb[dom]},
+        "step_roofline": {"bytes_per_particle": step_bytes,
+                          "achieved_gbs": step_bytes * n / (ms_step / 1e3) / 1e9,
+                          "frac": step_bytes * n / (ms_step / 1e3) / 1e9 / hbm},
+        "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_value, "unit": "particle-updates/s", "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes, "steps": args.e2e_steps},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        rate, info = oracle_rate(d, split, 0, args.oracle_seconds)
+        out["cpu_baseline"] = {"value": rate, "unit": "particle-updates/s", **info}
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

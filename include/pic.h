@@ -174,6 +174,24 @@ PIC_API int pic_set_state(pic_t h, const int32_t *leaf, const void *x_or_o, cons
 
 PIC_API int pic_stats(pic_t h, pic_stats_t *out);
 
+/* Phases of a step for pic_phase_times. */
+#define PIC_PHASE_DEPOSIT 0  /* leaf partial sums + vertex charges + FP64 total */
+#define PIC_PHASE_SOLVE 1    /* built-in Jacobi sweeps + vertex field (or the hook) */
+#define PIC_PHASE_PUSH 2     /* fused gather + push + re-location + key + counts */
+#define PIC_PHASE_REBIN 3    /* offsets scan, stayer ranks, mover compaction + slots */
+#define PIC_PHASE_PERMUTE 4  /* permutation of the particle arrays into bucket order */
+#define PIC_NPHASES 5
+
+/* Per-phase device timing with CUDA events recorded on the handle's stream
+ * around every phase of every later call.  enable = 0 stops recording;
+ * enable = 1 (re)starts it from zero. */
+PIC_API int pic_profile(pic_t h, int32_t enable);
+
+/* Synchronises the stream and returns, per phase, the summed device time in
+ * milliseconds and the number of this library's kernels launched, since the
+ * last pic_profile(h, 1).  Both arrays have PIC_NPHASES entries. */
+PIC_API int pic_phase_times(pic_t h, double *ms, int64_t *kernels);
+
 /* Tables for tests: leaf level[n_leaves] and coords[n_leaves][d]; vertex
  * positions pos[d][n_vertices] in units of 3^-depth; PIDT owner vertices
  * level[n_buckets], j[n_buckets][d] (host memory). */

@@ -17,6 +17,8 @@
 // only count, and the one order they decide (mover slots) is re-sorted.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "dev.cuh"
 #include "launch.hpp"
 
@@ -29,6 +31,10 @@ constexpr int kBlock = 256;
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
+
+static std::atomic<int64_t> g_launches{0};
+int64_t launches() { return g_launches.load(); }
+#define COUNT(k) g_launches.fetch_add(k)
 
 static inline unsigned grid_for(int64_t n, int block = kBlock) {
   int64_t g = (n + block - 1) / block;
@@ -734,76 +740,76 @@ cudaError_t set_kref(int d, cudaStream_t s) {
 
 void launch_init64(const DevTree &t, double *x, int64_t n, int32_t *leaf, int32_t *key, int32_t *err,
                    cudaStream_t s) {
-  if (n > 0) k_init64<<<grid_for(n), kBlock, 0, s>>>(t, x, n, leaf, key, err);
+  if (n > 0) { COUNT(1); k_init64<<<grid_for(n), kBlock, 0, s>>>(t, x, n, leaf, key, err); }
 }
 
 void launch_init32(const DevTree &t, const double *x, const double *v, int64_t n, int32_t *leaf, float *o,
                    float *vf, int32_t *key, int32_t *err, cudaStream_t s) {
-  if (n > 0) k_init32<<<grid_for(n), kBlock, 0, s>>>(t, x, v, n, leaf, o, vf, key, err);
+  if (n > 0) { COUNT(1); k_init32<<<grid_for(n), kBlock, 0, s>>>(t, x, v, n, leaf, o, vf, key, err); }
 }
 
 void launch_rekey32(const DevTree &t, const int32_t *leaf, const float *o, int64_t n, int32_t *key, int32_t *err,
                     cudaStream_t s) {
-  if (n > 0) k_rekey32<<<grid_for(n), kBlock, 0, s>>>(t, leaf, o, n, key, err);
+  if (n > 0) { COUNT(1); k_rekey32<<<grid_for(n), kBlock, 0, s>>>(t, leaf, o, n, key, err); }
 }
 
 void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *mover_words,
                       int32_t *block_movers, cudaStream_t s) {
-  k_count_all<<<grid_for(n), kBlock, 0, s>>>(key, n, count, mover_words, block_movers);
+  { COUNT(1); k_count_all<<<grid_for(n), kBlock, 0, s>>>(key, n, count, mover_words, block_movers); }
 }
 
 void launch_deposit(const DevTree &t, bool split, const int32_t *start, const void *pos, int64_t n, void *part,
                     double q, double ion, void *Q, double *block_sum, double *total, cudaStream_t s) {
   if (split) {
-    k_leaf_partials<true><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part);
-    k_vertex_charge<float><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const float *)part, (float)q, (float)ion,
-                                                                 (float *)Q, block_sum);
+    { COUNT(1); k_leaf_partials<true><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part); }
+    { COUNT(1); k_vertex_charge<float><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const float *)part, (float)q, (float)ion,
+                                                                 (float *)Q, block_sum); }
   } else {
-    k_leaf_partials<false><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part);
-    k_vertex_charge<double><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const double *)part, q, ion, (double *)Q,
-                                                                  block_sum);
+    { COUNT(1); k_leaf_partials<false><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part); }
+    { COUNT(1); k_vertex_charge<double><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const double *)part, q, ion, (double *)Q,
+                                                                  block_sum); }
   }
-  k_sum_blocks<<<1, 1024, 0, s>>>(block_sum, grid_for(t.n_vert), total);
+  { COUNT(1); k_sum_blocks<<<1, 1024, 0, s>>>(block_sum, grid_for(t.n_vert), total); }
 }
 
 void launch_solve(const DevTree &t, bool split, const void *Q, const double *total, void *b, void *V, void *Vtmp,
                   int sweeps, double omega, double *block_sum, double *resid2, cudaStream_t s) {
   unsigned g = grid_for(t.n_vert);
   if (split) {
-    k_rhs<float><<<g, kBlock, 0, s>>>(t, (const float *)Q, total, (float *)b);
+    { COUNT(1); k_rhs<float><<<g, kBlock, 0, s>>>(t, (const float *)Q, total, (float *)b); }
     float *a = (float *)V, *c = (float *)Vtmp;
     for (int it = 0; it < sweeps; ++it) {
-      k_jacobi<float><<<g, kBlock, 0, s>>>(t, (const float *)b, a, c, (float)omega, nullptr);
+      { COUNT(1); k_jacobi<float><<<g, kBlock, 0, s>>>(t, (const float *)b, a, c, (float)omega, nullptr); }
       float *tmp = a; a = c; c = tmp;
     }
     if (a != (float *)V) cudaMemcpyAsync(V, a, sizeof(float) * t.n_vert, cudaMemcpyDeviceToDevice, s);
-    k_jacobi<float><<<g, kBlock, 0, s>>>(t, (const float *)b, (const float *)V, nullptr, (float)omega, block_sum);
+    { COUNT(1); k_jacobi<float><<<g, kBlock, 0, s>>>(t, (const float *)b, (const float *)V, nullptr, (float)omega, block_sum); }
   } else {
-    k_rhs<double><<<g, kBlock, 0, s>>>(t, (const double *)Q, total, (double *)b);
+    { COUNT(1); k_rhs<double><<<g, kBlock, 0, s>>>(t, (const double *)Q, total, (double *)b); }
     double *a = (double *)V, *c = (double *)Vtmp;
     for (int it = 0; it < sweeps; ++it) {
-      k_jacobi<double><<<g, kBlock, 0, s>>>(t, (const double *)b, a, c, omega, nullptr);
+      { COUNT(1); k_jacobi<double><<<g, kBlock, 0, s>>>(t, (const double *)b, a, c, omega, nullptr); }
       double *tmp = a; a = c; c = tmp;
     }
     if (a != (double *)V) cudaMemcpyAsync(V, a, sizeof(double) * t.n_vert, cudaMemcpyDeviceToDevice, s);
-    k_jacobi<double><<<g, kBlock, 0, s>>>(t, (const double *)b, (const double *)V, nullptr, omega, block_sum);
+    { COUNT(1); k_jacobi<double><<<g, kBlock, 0, s>>>(t, (const double *)b, (const double *)V, nullptr, omega, block_sum); }
   }
-  k_sum_blocks<<<1, 1024, 0, s>>>(block_sum, g, resid2);
+  { COUNT(1); k_sum_blocks<<<1, 1024, 0, s>>>(block_sum, g, resid2); }
 }
 
 void launch_efield(const DevTree &t, bool split, const void *V, void *E, cudaStream_t s) {
   if (split)
-    k_efield<float><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const float *)V, (float *)E);
+    { COUNT(1); k_efield<float><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const float *)V, (float *)E); }
   else
-    k_efield<double><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const double *)V, (double *)E);
+    { COUNT(1); k_efield<double><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const double *)V, (double *)E); }
 }
 
 void launch_push64(const DevTree &t, const Push64Args &a, cudaStream_t s) {
-  k_push64<<<grid_for(a.n), kBlock, 0, s>>>(t, a);
+  { COUNT(1); k_push64<<<grid_for(a.n), kBlock, 0, s>>>(t, a); }
 }
 
 void launch_push32(const DevTree &t, const Push32Args &a, cudaStream_t s) {
-  k_push32<<<grid_for(a.n), kBlock, 0, s>>>(t, a);
+  { COUNT(1); k_push32<<<grid_for(a.n), kBlock, 0, s>>>(t, a); }
 }
 
 int64_t scan_tiles_needed(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
@@ -812,9 +818,9 @@ void launch_exclusive_scan(const int32_t *in, int64_t n, int32_t *out, int32_t *
                            cudaStream_t s) {
   int64_t nt = scan_tiles_needed(n);
   if (nt < 1) nt = 1;
-  k_scan_reduce<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, tile_sums);
-  k_scan_tiles<<<1, kScanThreads, 0, s>>>(tile_sums, nt, total);
-  k_scan_apply<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, tile_sums, out, total);
+  { COUNT(1); k_scan_reduce<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, tile_sums); }
+  { COUNT(1); k_scan_tiles<<<1, kScanThreads, 0, s>>>(tile_sums, nt, total); }
+  { COUNT(1); k_scan_apply<<<(unsigned)nt, kScanThreads, 0, s>>>(in, n, tile_sums, out, total); }
 }
 
 void launch_rebin(const RebinArgs &r, cudaStream_t s) {
@@ -824,51 +830,51 @@ void launch_rebin(const RebinArgs &r, cudaStream_t s) {
   unsigned gp = grid_for(r.n);
   launch_exclusive_scan(r.block_movers, gp, r.block_offsets, r.tile_sums2, r.scalars + 1, s);
   if (r.old_start)
-    k_stayers<<<grid_for(r.n_keys), kBlock, 0, s>>>(r.old_start, r.keyn, r.new_start, r.n_keys, r.perm, r.n_stay,
-                                                    r.scalars + 2);
+    { COUNT(1); k_stayers<<<grid_for(r.n_keys), kBlock, 0, s>>>(r.old_start, r.keyn, r.new_start, r.n_keys, r.perm, r.n_stay,
+                                                    r.scalars + 2); }
   else
     cudaMemsetAsync(r.n_stay, 0, sizeof(int32_t) * r.n_keys, s);
-  k_compact_movers<<<gp, kBlock, 0, s>>>(r.mover_words, r.block_offsets, r.n, r.movers);
+  { COUNT(1); k_compact_movers<<<gp, kBlock, 0, s>>>(r.mover_words, r.block_offsets, r.n, r.movers); }
   cudaMemsetAsync(r.cursor, 0, sizeof(int32_t) * r.n_keys, s);
-  k_mover_slots<<<gp, kBlock, 0, s>>>(r.movers, r.scalars + 1, r.keyn, r.new_start, r.n_stay, r.cursor, r.perm);
-  k_sort_segments<<<grid_for(r.n_keys), kBlock, 0, s>>>(r.new_start, r.n_stay, r.n_keys, r.perm);
+  { COUNT(1); k_mover_slots<<<gp, kBlock, 0, s>>>(r.movers, r.scalars + 1, r.keyn, r.new_start, r.n_stay, r.cursor, r.perm); }
+  { COUNT(1); k_sort_segments<<<grid_for(r.n_keys), kBlock, 0, s>>>(r.new_start, r.n_stay, r.n_keys, r.perm); }
 }
 
 void launch_gather_f64(const int32_t *perm, int64_t n, int d, const double *src, double *dst, cudaStream_t s) {
-  if (n > 0) k_gather_vec<double><<<grid_for(n), kBlock, 0, s>>>(perm, n, d, src, dst);
+  if (n > 0) { COUNT(1); k_gather_vec<double><<<grid_for(n), kBlock, 0, s>>>(perm, n, d, src, dst); }
 }
 void launch_gather_f32(const int32_t *perm, int64_t n, int d, const float *src, float *dst, cudaStream_t s) {
-  if (n > 0) k_gather_vec<float><<<grid_for(n), kBlock, 0, s>>>(perm, n, d, src, dst);
+  if (n > 0) { COUNT(1); k_gather_vec<float><<<grid_for(n), kBlock, 0, s>>>(perm, n, d, src, dst); }
 }
 void launch_gather_i32(const int32_t *perm, int64_t n, const int32_t *src, int32_t *dst, cudaStream_t s) {
-  if (n > 0) k_gather_vec<int32_t><<<grid_for(n), kBlock, 0, s>>>(perm, n, 1, src, dst);
+  if (n > 0) { COUNT(1); k_gather_vec<int32_t><<<grid_for(n), kBlock, 0, s>>>(perm, n, 1, src, dst); }
 }
 
 void launch_absolute_split(const DevTree &t, const int32_t *leaf, const float *o, int64_t n, double *x,
                            cudaStream_t s) {
-  if (n > 0) k_absolute_split<<<grid_for(n), kBlock, 0, s>>>(t, leaf, o, n, x);
+  if (n > 0) { COUNT(1); k_absolute_split<<<grid_for(n), kBlock, 0, s>>>(t, leaf, o, n, x); }
 }
 
 void launch_widen(const float *in, int64_t n, double *out, cudaStream_t s) {
-  if (n > 0) k_widen<<<grid_for(n), kBlock, 0, s>>>(in, n, out);
+  if (n > 0) { COUNT(1); k_widen<<<grid_for(n), kBlock, 0, s>>>(in, n, out); }
 }
 
 void launch_gather_only(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n,
                         const void *Ev, void *Ep, cudaStream_t s) {
   if (n <= 0) return;
   if (split)
-    k_gather_only32<<<grid_for(n), kBlock, 0, s>>>(t, (const float *)pos, leaf, n, (const float *)Ev, (float *)Ep);
+    { COUNT(1); k_gather_only32<<<grid_for(n), kBlock, 0, s>>>(t, (const float *)pos, leaf, n, (const float *)Ev, (float *)Ep); }
   else
-    k_gather_only64<<<grid_for(n), kBlock, 0, s>>>(t, (const double *)pos, leaf, n, (const double *)Ev,
-                                                   (double *)Ep);
+    { COUNT(1); k_gather_only64<<<grid_for(n), kBlock, 0, s>>>(t, (const double *)pos, leaf, n, (const double *)Ev,
+                                                   (double *)Ep); }
 }
 
 void launch_half_kick(bool split, const void *Ep, int64_t n_total, double c, void *v, cudaStream_t s) {
   if (n_total <= 0) return;
   if (split)
-    k_half_kick32<<<grid_for(n_total), kBlock, 0, s>>>((const float *)Ep, n_total, (float)c, (float *)v);
+    { COUNT(1); k_half_kick32<<<grid_for(n_total), kBlock, 0, s>>>((const float *)Ep, n_total, (float)c, (float *)v); }
   else
-    k_half_kick64<<<grid_for(n_total), kBlock, 0, s>>>((const double *)Ep, n_total, c, (double *)v);
+    { COUNT(1); k_half_kick64<<<grid_for(n_total), kBlock, 0, s>>>((const double *)Ep, n_total, c, (double *)v); }
 }
 
 }  // namespace pic

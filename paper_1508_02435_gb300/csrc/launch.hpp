@@ -51,6 +51,9 @@ struct RebinArgs {
   int32_t *scalars;             // [0] n, [1] movers, [2] max bucket
 };
 
+// Kernels launched by this library so far (all handles of the process).
+int64_t launches();
+
 cudaError_t set_constants(cudaStream_t s);
 cudaError_t set_kref(int d, cudaStream_t s);
 int64_t scan_tiles_needed(int64_t n);

@@ -54,6 +54,18 @@ struct pic_s {
 
   int64_t step = 0;
   std::string last_error;
+
+  // per-phase event timing (pic_profile / pic_phase_times)
+  struct Pending {
+    int phase;
+    cudaEvent_t a, b;
+    int64_t kernels;
+  };
+  bool prof = false;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double phase_ms[PIC_NPHASES] = {0, 0, 0, 0, 0};
+  int64_t phase_kernels[PIC_NPHASES] = {0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -238,6 +250,53 @@ int alloc_state(pic_t h) {
   return PIC_OK;
 }
 
+cudaEvent_t take_event(pic_t h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Sums the recorded phase intervals into the per-phase totals.
+int drain_profile(pic_t h) {
+  CK(cudaStreamSynchronize(h->stream));
+  for (auto &p : h->pending) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, p.a, p.b));
+    h->phase_ms[p.phase] += ms;
+    h->phase_kernels[p.phase] += p.kernels;
+    h->event_pool.push_back(p.a);
+    h->event_pool.push_back(p.b);
+  }
+  h->pending.clear();
+  return PIC_OK;
+}
+
+// Records CUDA events around one phase on the handle's stream when profiling.
+struct PhaseScope {
+  pic_t h;
+  int phase;
+  cudaEvent_t a = nullptr;
+  int64_t k0 = 0;
+  PhaseScope(pic_t h_, int phase_) : h(h_), phase(phase_) {
+    if (!h->prof) return;
+    a = take_event(h);
+    cudaEventRecord(a, h->stream);
+    k0 = launches();
+  }
+  ~PhaseScope() {
+    if (!h->prof || !a) return;
+    cudaEvent_t b = take_event(h);
+    cudaEventRecord(b, h->stream);
+    h->pending.push_back({phase, a, b, launches() - k0});
+    if (h->pending.size() > 4096) drain_profile(h);
+  }
+};
+
 // Stable re-bin of the pushed state [1] into the current state [0].
 // old_start == NULL: fresh particles, every one counted as a mover.
 int rebin_and_gather(pic_t h, const int32_t *old_start) {
@@ -260,7 +319,11 @@ int rebin_and_gather(pic_t h, const int32_t *old_start) {
   r.tile_sums = h->tile_sums;
   r.tile_sums2 = h->tile_sums2;
   r.scalars = h->scalars;
-  launch_rebin(r, s);
+  {
+    PhaseScope ps(h, PIC_PHASE_REBIN);
+    launch_rebin(r, s);
+  }
+  PhaseScope ps(h, PIC_PHASE_PERMUTE);
   const int d = h->d;
   if (h->split) {
     launch_gather_f32(h->perm, n, d, (const float *)h->pos[1], (float *)h->pos[0], s);
@@ -289,6 +352,7 @@ int bin_fresh(pic_t h) {
 }
 
 int deposit(pic_t h) {
+  PhaseScope ps(h, PIC_PHASE_DEPOSIT);
   launch_deposit(h->dt, h->split, h->start_cur, h->pos[0], h->n, h->part, h->cfg.q, h->cfg.ion, h->Q,
                  h->block_sum, h->total, h->stream);
   CK(cudaGetLastError());
@@ -296,6 +360,7 @@ int deposit(pic_t h) {
 }
 
 int field(pic_t h, pic_solve_fn hook, void *user) {
+  PhaseScope ps(h, PIC_PHASE_SOLVE);
   cudaStream_t s = h->stream;
   if (hook) {
     int r = hook(user, h->Q, h->E, h->dt.n_vert, h->split ? PIC_FP32_SPLIT : PIC_FP64, (void *)s);
@@ -312,6 +377,7 @@ int field(pic_t h, pic_solve_fn hook, void *user) {
 int push_and_rebin(pic_t h, double dt) {
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(h->count, 0, sizeof(int32_t) * h->dt.n_keys, s));
+  PhaseScope *ps = new PhaseScope(h, PIC_PHASE_PUSH);
   if (h->split) {
     Push32Args a{};
     a.n = h->n;
@@ -351,11 +417,14 @@ int push_and_rebin(pic_t h, double dt) {
     a.err = h->err;
     launch_push64(h->dt, a, s);
   }
+  delete ps;
   CK(cudaGetLastError());
   return rebin_and_gather(h, h->start_cur);
 }
 
 int check_handle(pic_t h) { return h ? PIC_OK : PIC_EINVAL; }
+
+
 
 int copy_out(pic_t h, void *dst, const void *src, size_t bytes, int32_t where) {
   if (!dst) return PIC_OK;
@@ -428,6 +497,11 @@ const char *pic_last_error(pic_t h) { return h ? h->last_error.c_str() : "NULL h
 void pic_destroy(pic_t h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  for (auto &p : h->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : h->event_pool) cudaEventDestroy(e);
   free_bufs(h, h->state_bufs);
   free_bufs(h, h->tree_bufs);
   delete h;
@@ -657,6 +731,29 @@ int pic_stats(pic_t h, pic_stats_t *o) {
   o->total_charge = tot;
   o->residual = std::sqrt(r2);
   o->error = err ? PIC_ERANGE : PIC_OK;
+  return PIC_OK;
+}
+
+int pic_profile(pic_t h, int32_t enable) {
+  if (check_handle(h)) return PIC_EINVAL;
+  int rc = drain_profile(h);
+  if (rc) return rc;
+  for (int i = 0; i < PIC_NPHASES; ++i) {
+    h->phase_ms[i] = 0.0;
+    h->phase_kernels[i] = 0;
+  }
+  h->prof = enable != 0;
+  return PIC_OK;
+}
+
+int pic_phase_times(pic_t h, double *ms, int64_t *kernels) {
+  if (check_handle(h)) return PIC_EINVAL;
+  int rc = drain_profile(h);
+  if (rc) return rc;
+  for (int i = 0; i < PIC_NPHASES; ++i) {
+    if (ms) ms[i] = h->phase_ms[i];
+    if (kernels) kernels[i] = h->phase_kernels[i];
+  }
   return PIC_OK;
 }
 

@@ -80,6 +80,8 @@ SIGNATURES = [
     ("pic_get_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     ("pic_set_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     ("pic_stats", C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    ("pic_profile", C.c_int, [C.c_void_p, C.c_int32]),
+    ("pic_phase_times", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_leaf_table", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_vertex_table", C.c_int, [C.c_void_p, C.c_void_p]),
     ("pic_pidt_table", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -260,6 +262,18 @@ class Pic:
         pp, w = _ptr(pos)
         vp, _ = _ptr(vel)
         self._check(self.lib.pic_set_state(self.h, lp, pp, vp, w))
+
+    PHASES = ("deposit", "solve", "push", "rebin", "permute")
+
+    def profile(self, enable: bool = True):
+        self._check(self.lib.pic_profile(self.h, 1 if enable else 0))
+
+    def phase_times(self):
+        """{phase: (device ms, kernels launched)} since profile(True)."""
+        ms = np.zeros(5)
+        k = np.zeros(5, np.int64)
+        self._check(self.lib.pic_phase_times(self.h, _ptr(ms)[0], _ptr(k)[0]))
+        return {name: (float(ms[i]), int(k[i])) for i, name in enumerate(self.PHASES)}
 
     def leaf_table(self):
         nl = int(self._info.n_leaves)

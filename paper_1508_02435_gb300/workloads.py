@@ -147,8 +147,17 @@ def langmuir(d: int, depth: int, ppc: int, vth: float = 0.05, amp: float = 0.01,
     per_axis = round(ppc ** (1.0 / d))
     if per_axis ** d != ppc:
         raise ValueError("ppc must be a perfect d-th power for the quiet start")
-    x = _stratified(3 ** depth, per_axis, d)
-    x[0] = _perturbed_coordinate(x[0], amp, k)
+    m = 3 ** depth * per_axis
+    g = (np.arange(m, dtype=np.float64) + 0.5) / m
+    gx = _perturbed_coordinate(g, amp, k)
+    # particle index p = ix + m*iy (+ m^2*iz): x fastest
+    x = np.empty((d, m ** d))
+    x[0] = np.tile(gx, m ** (d - 1))
+    if d == 2:
+        x[1] = np.repeat(g, m)
+    else:
+        x[1] = np.tile(np.repeat(g, m), m)
+        x[2] = np.repeat(g, m * m)
     n = x.shape[1]
     rng = np.random.default_rng(seed)
     v = rng.standard_normal((d, n)) * vth
