@@ -21,6 +21,9 @@ struct DevTree {
   int32_t M;  // 3^depth
   const TabEntry *tab;
   int32_t n_tab;
+  // uniform trees: spread[a * M + c] = base-3 digits of c interleaved on axis a,
+  // so the depth-first leaf id of cell c is the sum over the axes
+  const int32_t *spread;
   const uint8_t *leaf_level;
   const int32_t *leaf_coords;
   // adaptive grids
@@ -159,6 +162,17 @@ __device__ __forceinline__ int32_t descend_split(const TabEntry *tab, int d, int
 
 // ---- grid maps ---------------------------------------------------------------
 
+// Row-major vertex ids of the 2^d corners of uniform-grid cell c (periodic).
+__device__ __forceinline__ void uniform_corner_vertices(const int32_t *c, int d, int32_t M, int32_t *vid) {
+  int32_t x0 = c[0], x1 = c[0] + 1 == M ? 0 : c[0] + 1;
+  int32_t y0 = c[1] * M, y1 = (c[1] + 1 == M ? 0 : c[1] + 1) * M;
+  vid[0] = x0 + y0; vid[1] = x1 + y0; vid[2] = x0 + y1; vid[3] = x1 + y1;
+  if (d == 3) {
+    int32_t z0 = c[2] * M * M, z1 = (c[2] + 1 == M ? 0 : c[2] + 1) * M * M;
+    for (int e = 0; e < 4; ++e) { vid[e + 4] = vid[e] + z1; vid[e] += z0; }
+  }
+}
+
 // Row-major vertex of corner e of the uniform-grid cell c (periodic).
 __device__ __forceinline__ int32_t uniform_corner_vertex(const int32_t *c, int e, int d, int32_t M) {
   int64_t v = 0, mul = 1;
@@ -171,9 +185,11 @@ __device__ __forceinline__ int32_t uniform_corner_vertex(const int32_t *c, int e
   return (int32_t)v;
 }
 
-// Depth-first leaf id of cell c on a uniform tree of the given depth.
-__device__ __forceinline__ int32_t uniform_leaf_of_cell(const int32_t *c, int d, int depth) {
-  return local_index((uint32_t)c[0], (uint32_t)c[1], d == 3 ? (uint32_t)c[2] : 0u, d, depth);
+// Depth-first leaf id of cell c on a uniform tree (digit-interleave tables).
+__device__ __forceinline__ int32_t uniform_leaf_of_cell(const int32_t *spread, int32_t M, const int32_t *c, int d) {
+  int32_t l = __ldg(spread + c[0]) + __ldg(spread + M + c[1]);
+  if (d == 3) l += __ldg(spread + 2 * M + c[2]);
+  return l;
 }
 
 // d-linear shape function of corner e at local coordinates t.
@@ -188,7 +204,7 @@ __device__ __forceinline__ T shape(const T *t, int e, int d) {
 }
 
 // Incident leaf corners of uniform vertex v in ascending leaf-corner order.
-__device__ __forceinline__ int uniform_incidences(int64_t v, int d, int32_t M, int depth, int32_t *lc) {
+__device__ __forceinline__ int uniform_incidences(int64_t v, int d, int32_t M, const int32_t *spread, int32_t *lc) {
   int32_t j[3] = {0, 0, 0};
   int64_t r = v;
   for (int a = 0; a < d; ++a) { j[a] = (int32_t)(r % M); r /= M; }
@@ -199,7 +215,7 @@ __device__ __forceinline__ int uniform_incidences(int64_t v, int d, int32_t M, i
       int32_t cc = j[a] - ((f >> a) & 1);
       c[a] = cc < 0 ? cc + M : cc;
     }
-    lc[f] = uniform_leaf_of_cell(c, d, depth) * nc + f;
+    lc[f] = uniform_leaf_of_cell(spread, M, c, d) * nc + f;
   }
   for (int i = 1; i < nc; ++i) {  // insertion sort, at most 8 entries
     int32_t x = lc[i];

@@ -56,7 +56,9 @@ __device__ __forceinline__ int32_t pidt_vertex(const DevTree &t, int32_t L, int 
   if (t.uniform) {
     int32_t c[3] = {0, 0, 0};
     for (int k = 0; k < t.d; ++k) c[k] = t.leaf_coords[(int64_t)L * t.d + k];
-    return uniform_corner_vertex(c, a, t.d, t.M);
+    int32_t vid[8];
+    uniform_corner_vertices(c, t.d, t.M, vid);
+    return vid[a];
   }
   return t.corner_pv[(int64_t)L * t.nc + a];
 }
@@ -111,7 +113,7 @@ template <typename T, typename Fn>
 __device__ __forceinline__ void for_incidences(const DevTree &t, int64_t v, Fn fn) {
   if (t.uniform) {
     int32_t lc[8];
-    int m = uniform_incidences(v, t.d, t.M, t.depth, lc);
+    int m = uniform_incidences(v, t.d, t.M, t.spread, lc);
     for (int i = 0; i < m; ++i) fn(lc[i], (T)1);
   } else {
     const T *ww = inc_weights(t, (T)0);
@@ -215,7 +217,7 @@ __global__ void k_vertex_charge(DevTree t, const T *__restrict__ part, T q, T io
     T S = (T)0;
     if (t.uniform) {
       int32_t lc[8];
-      int m = uniform_incidences(v, t.d, t.M, t.depth, lc);
+      int m = uniform_incidences(v, t.d, t.M, t.spread, lc);
       for (int i = 0; i < m; ++i) S = S + part[lc[i]];
     } else {
       const T *w = inc_weights(t, (T)0);
@@ -419,9 +421,18 @@ __global__ void k_push64(DevTree t, Push64Args a) {
     double tl[3];
     local_coords(a.x, n, p, lev, c, d, tl);
     double E[3] = {0.0, 0.0, 0.0};
-    for (int e = 0; e < nc; ++e) {
-      double w = shape<double>(tl, e, d);
-      for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * corner_value(t, L, c, e, a.E + ax * nv);
+    if (t.uniform) {
+      int32_t vid[8];
+      uniform_corner_vertices(c, d, t.M, vid);
+      for (int e = 0; e < nc; ++e) {
+        double w = shape<double>(tl, e, d);
+        for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * a.E[ax * nv + vid[e]];
+      }
+    } else {
+      for (int e = 0; e < nc; ++e) {
+        double w = shape<double>(tl, e, d);
+        for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * corner_value(t, L, c, e, a.E + ax * nv);
+      }
     }
     uint32_t Q[3] = {0u, 0u, 0u};
     bool bad = false;
@@ -435,12 +446,20 @@ __global__ void k_push64(DevTree t, Push64Args a) {
     }
     if (bad) atomicOr(a.err, 1);
     int lev2;
-    int32_t L2 = descend_q(t.tab, d, Q, &lev2);
+    int32_t L2;
+    if (t.uniform) {
+      uint32_t step = 2u * c_pow3[18 - t.depth];
+      int32_t cc[3] = {(int32_t)(Q[0] / step), (int32_t)(Q[1] / step), d == 3 ? (int32_t)(Q[2] / step) : 0};
+      L2 = uniform_leaf_of_cell(t.spread, t.M, cc, d);
+      lev2 = t.depth;
+    } else {
+      L2 = descend_q(t.tab, d, Q, &lev2);
+    }
     knew = key_of(t, L2, pidt_corner_q(Q, lev2, d));
     int32_t kold = t.scheme == 0 ? L : a.key[p];
     moved = knew != kold;
     a.tleaf[p] = L2;
-    a.keyn[p] = knew;
+    if (t.scheme != 0) a.keyn[p] = knew;  // PIT: the key array is the leaf array
   }
   count_and_ballot(act, knew, moved, a.count, a.mover_words, a.block_movers);
 }
@@ -460,12 +479,21 @@ __global__ void k_push32(DevTree t, Push32Args a) {
     float o[3] = {0.f, 0.f, 0.f};
     for (int ax = 0; ax < d; ++ax) o[ax] = a.o[ax * n + p];
     float E[3] = {0.f, 0.f, 0.f};
-    for (int e = 0; e < nc; ++e) {
-      float w = shape<float>(o, e, d);
-      for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * corner_value(t, L, c, e, a.E + ax * nv);
+    if (t.uniform) {
+      int32_t vid[8];
+      uniform_corner_vertices(c, d, t.M, vid);
+      for (int e = 0; e < nc; ++e) {
+        float w = shape<float>(o, e, d);
+        for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * a.E[ax * nv + vid[e]];
+      }
+    } else {
+      for (int e = 0; e < nc; ++e) {
+        float w = shape<float>(o, e, d);
+        for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * corner_value(t, L, c, e, a.E + ax * nv);
+      }
     }
     const int32_t per = (int32_t)c_pow3[lev];
-    const float sl = (float)(a.dt * (double)per);
+    const float sl = a.sl[lev];
     int32_t I[3] = {0, 0, 0};
     float f[3] = {0.f, 0.f, 0.f};
     bool bad = false;
@@ -475,22 +503,36 @@ __global__ void k_push32(DevTree t, Push32Args a) {
       if (!isfinite(vn) || !isfinite(tt)) { bad = true; tt = 0.0f; }
       float fl = floorf(tt);
       f[ax] = tt - fl;
-      float flc = fminf(fmaxf(fl, -1.0e15f), 1.0e15f);
-      int64_t cc = ((int64_t)c[ax] + (int64_t)flc) % per;
-      if (cc < 0) cc += per;
-      I[ax] = (int32_t)cc;
+      int32_t cc;
+      if (fabsf(fl) < 1.0e9f) {
+        cc = c[ax] + (int32_t)fl;               // periodic wrap, 32-bit
+        if (cc < 0 || cc >= per) {
+          cc %= per;
+          if (cc < 0) cc += per;
+        }
+      } else {
+        int64_t c64 = ((int64_t)c[ax] + (int64_t)fminf(fmaxf(fl, -1.0e15f), 1.0e15f)) % per;
+        cc = (int32_t)(c64 < 0 ? c64 + per : c64);
+      }
+      I[ax] = cc;
       a.tv[ax * n + p] = vn;
     }
     if (bad) atomicOr(a.err, 1);
     float o2[3] = {0.f, 0.f, 0.f};
     int lev2;
-    int32_t L2 = descend_split(t.tab, d, lev, I, f, o2, &lev2);
+    int32_t L2;
+    if (t.uniform) {  // the covering leaf is the cell I itself; o = f
+      L2 = uniform_leaf_of_cell(t.spread, t.M, I, d);
+      for (int ax = 0; ax < d; ++ax) o2[ax] = clamp_off(f[ax]);
+    } else {
+      L2 = descend_split(t.tab, d, lev, I, f, o2, &lev2);
+    }
     for (int ax = 0; ax < d; ++ax) a.to[ax * n + p] = o2[ax];
     knew = key_of(t, L2, pidt_corner_o(o2, d));
     int32_t kold = t.scheme == 0 ? L : a.key[p];
     moved = knew != kold;
     a.tleaf[p] = L2;
-    a.keyn[p] = knew;
+    if (t.scheme != 0) a.keyn[p] = knew;  // PIT: the key array is the leaf array
   }
   count_and_ballot(act, knew, moved, a.count, a.mover_words, a.block_movers);
 }

@@ -32,6 +32,7 @@ struct Push32Args {
   const float *E;
   float qmdt;
   double dt;
+  float sl[19];                 // RN32(dt * 3^level) per level
   int32_t *count;
   uint32_t *mover_words;
   int32_t *block_movers;

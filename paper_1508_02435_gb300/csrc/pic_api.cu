@@ -157,6 +157,18 @@ int install_tree(pic_t h, const pic_tree_desc *tree) {
   if ((rc = upload(h, tb, &dt.leaf_level, ht.leaf_level))) return rc;
   if ((rc = upload(h, tb, &dt.leaf_coords, ht.leaf_coords))) return rc;
   if (ht.uniform) {
+    std::vector<int32_t> spread((size_t)ht.d * ht.M, 0);
+    for (int a = 0; a < ht.d; ++a)
+      for (int64_t c = 0; c < ht.M; ++c) {
+        int64_t v = 0, cc = c, mul = pow3(a);
+        for (int i = 0; i < ht.depth; ++i) {
+          v += (cc % 3) * mul;
+          cc /= 3;
+          mul *= ht.nch;
+        }
+        spread[(size_t)a * ht.M + c] = (int32_t)v;
+      }
+    if ((rc = upload(h, tb, &dt.spread, spread))) return rc;
     dt.ion_u64 = ht.ion_load[0];
     dt.ion_u32 = (float)ht.ion_load[0];
     dt.diag_u64 = ht.diag[0];
@@ -205,7 +217,11 @@ int alloc_state(pic_t h) {
     if ((rc = dalloc(h, sb, &p, fs * d * n))) return rc;
     h->vel[s] = p;
     if ((rc = dalloc(h, sb, &h->leaf[s], n))) return rc;
-    if ((rc = dalloc(h, sb, &h->key[s], n))) return rc;
+    if (h->scheme == PIC_PIT) {
+      h->key[s] = h->leaf[s];  // PIT keys are the leaves
+    } else if ((rc = dalloc(h, sb, &h->key[s], n))) {
+      return rc;
+    }
     if ((rc = dalloc(h, sb, &h->ids[s], n))) return rc;
   }
   if ((rc = dalloc(h, sb, &h->start_cur, nk + 1))) return rc;
@@ -333,7 +349,7 @@ int rebin_and_gather(pic_t h, const int32_t *old_start) {
     launch_gather_f64(h->perm, n, d, (const double *)h->vel[1], (double *)h->vel[0], s);
   }
   launch_gather_i32(h->perm, n, h->leaf[1], h->leaf[0], s);
-  launch_gather_i32(h->perm, n, h->key[1], h->key[0], s);
+  if (h->scheme != PIC_PIT) launch_gather_i32(h->perm, n, h->key[1], h->key[0], s);
   if (h->cfg.track_ids) {
     launch_gather_i32(h->perm, n, h->ids[0], h->ids[1], s);
     std::swap(h->ids[0], h->ids[1]);
@@ -392,6 +408,7 @@ int push_and_rebin(pic_t h, double dt) {
     a.E = (const float *)h->E;
     a.qmdt = (float)(h->cfg.qm * dt);
     a.dt = dt;
+    for (int l = 0; l <= 18; ++l) a.sl[l] = (float)(dt * (double)pow3(l));
     a.count = h->count;
     a.mover_words = h->mover_words;
     a.block_movers = h->block_movers;
