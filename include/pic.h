@@ -93,7 +93,11 @@ typedef struct {
   double omega;       /* Jacobi damping factor */
   int32_t track_ids;  /* 1: carry input particle ids through the re-bin (pic_bins) */
   void *stream;       /* cudaStream_t for every kernel of the handle; NULL = default */
+  int32_t path;       /* PIC_PATH_AUTO (brick path where it applies) or PIC_PATH_GENERIC */
 } pic_config;
+
+#define PIC_PATH_AUTO 0     /* uniform tree + PIT + split precision: two-pass brick kernels */
+#define PIC_PATH_GENERIC 1  /* per-particle push + counting-sort re-bin, any tree */
 
 /* Optional field-solve hook, called once per step with the vertex charges
  * Q[n_vertices] (FP64, or FP32 in split mode) and a buffer E[d][n_vertices]
@@ -110,6 +114,7 @@ typedef struct {
   int64_t n_buckets;     /* leaves (PIT) or PIDT owner vertices */
   int64_t n_keys;        /* sort keys: leaves (PIT) or owner vertex x 2^d quadrants (PIDT) */
   int32_t uniform;       /* 1 if every leaf is on `depth` */
+  int32_t brick;         /* 1 if steps run the brick path */
   int64_t device_bytes;  /* device memory held by the handle */
 } pic_info_t;
 

@@ -34,6 +34,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 
 static std::atomic<int64_t> g_launches{0};
 int64_t launches() { return g_launches.load(); }
+void count_launches(int64_t k) { g_launches.fetch_add(k); }
 #define COUNT(k) g_launches.fetch_add(k)
 
 static inline unsigned grid_for(int64_t n, int block = kBlock) {

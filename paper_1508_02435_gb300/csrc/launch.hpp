@@ -55,6 +55,58 @@ struct RebinArgs {
 // Kernels launched by this library so far (all handles of the process).
 int64_t launches();
 
+// Brick path (uniform trees, PIT, split precision): see brick.cu.
+struct BrickGeom {
+  int d, kb, B, LB, nbx, depth;  // B = 3^kb leaves per brick axis, LB = B^d, nbx bricks per axis
+  int64_t n_bricks;
+  const uint32_t *decodeL;       // local depth-first index -> x | y << 10 | z << 20
+};
+
+struct BrickPushArgs {
+  int64_t n;
+  const float *o, *v;
+  const int32_t *start;          // current leaf offsets
+  const int32_t *ids;            // NULL unless ids are tracked
+  const float *E;
+  float qmdt, sl;
+  float *to, *tv;
+  uint16_t *tcode;               // destination local leaf | stayer bit
+  int32_t *tids;
+  int32_t *cnt, *segoff;         // [n_bricks][28]
+  int32_t *far_n;
+  int32_t far_cap;
+  int32_t *far_tidx, *far_src, *far_dest;
+  int32_t *n_movers;
+  int32_t *err;
+};
+
+struct BrickPullArgs {
+  int64_t n;
+  const int32_t *old_start, *cnt, *segoff;
+  const int32_t *fstart;
+  int32_t *fstart_w;
+  const int32_t *far_tidx, *far_src;  // far arrivals sorted per destination brick
+  int32_t *far_tidx_w, *far_src_w;
+  int32_t *tot_w;
+  const int32_t *bstart;
+  int32_t *bstart_w;
+  const uint16_t *tcode;
+  const float *to, *tv;
+  const int32_t *tids;
+  float *o, *v;
+  int32_t *ids;
+  int32_t *new_start;
+  int32_t *max_bucket;
+  int32_t *err;
+};
+
+cudaError_t brick_configure(const BrickGeom &g);
+void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs &pa, cudaStream_t s);
+void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPushArgs &pa, const BrickPullArgs &qa,
+                       int32_t *fcount, int32_t *fcursor, int32_t *tile_sums, int32_t *scratch_total,
+                       cudaStream_t s);
+void launch_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf, cudaStream_t s);
+
 cudaError_t set_constants(cudaStream_t s);
 cudaError_t set_kref(int d, cudaStream_t s);
 int64_t scan_tiles_needed(int64_t n);

@@ -55,6 +55,16 @@ struct pic_s {
   int64_t step = 0;
   std::string last_error;
 
+  // brick path (uniform tree, PIT, split precision)
+  bool brick = false;
+  bool leaf_stale = false;  // leaf[0] not yet expanded from the offsets
+  BrickGeom bg{};
+  std::vector<DevBuf> brick_bufs;
+  uint16_t *tcode = nullptr;
+  int32_t *bcnt = nullptr, *bsegoff = nullptr, *far_n = nullptr, *far_tidx = nullptr, *far_src = nullptr;
+  int32_t *far_dest = nullptr, *far_stidx = nullptr, *far_ssrc = nullptr, *fcount = nullptr;
+  int32_t *fcursor = nullptr, *fstart = nullptr, *btot = nullptr, *bstart = nullptr;
+
   // per-phase event timing (pic_profile / pic_phase_times)
   struct Pending {
     int phase;
@@ -313,6 +323,135 @@ struct PhaseScope {
   }
 };
 
+// Buffers and tables of the brick path, when it applies.
+int setup_brick(pic_t h) {
+  free_bufs(h, h->brick_bufs);
+  h->brick = false;
+  const auto &t = h->ht;
+  if (h->cfg.path != PIC_PATH_AUTO || !t.uniform || h->scheme != PIC_PIT || !h->split || t.depth < 3) return PIC_OK;
+  BrickGeom g{};
+  g.d = t.d;
+  g.kb = 2;
+  g.B = 9;
+  g.LB = t.d == 3 ? 729 : 81;
+  g.depth = t.depth;
+  g.nbx = (int)pow3(t.depth - g.kb);
+  g.n_bricks = 1;
+  for (int a = 0; a < t.d; ++a) g.n_bricks *= g.nbx;
+  std::vector<uint32_t> dec(g.LB);
+  for (int l = 0; l < g.LB; ++l) {
+    uint32_t c[3] = {0, 0, 0};
+    int rest = l;
+    uint32_t p3i = 1;
+    for (int i = 0; i < g.kb; ++i) {
+      int dg = rest % t.nch;
+      rest /= t.nch;
+      c[0] += (uint32_t)(dg % 3) * p3i;
+      c[1] += (uint32_t)((dg / 3) % 3) * p3i;
+      c[2] += (uint32_t)(dg / 9) * p3i;
+      p3i *= 3;
+    }
+    dec[l] = c[0] | (c[1] << 10) | (c[2] << 20);
+  }
+  auto &bb = h->brick_bufs;
+  int rc;
+  if ((rc = upload(h, bb, &g.decodeL, dec))) return rc;
+  const int64_t n = h->n, nb = g.n_bricks;
+  if ((rc = dalloc(h, bb, &h->tcode, n))) return rc;
+  if ((rc = dalloc(h, bb, &h->bcnt, nb * 28))) return rc;
+  if ((rc = dalloc(h, bb, &h->bsegoff, nb * 28))) return rc;
+  if ((rc = dalloc(h, bb, &h->far_n, 2))) return rc;
+  if ((rc = dalloc(h, bb, &h->far_tidx, n))) return rc;
+  if ((rc = dalloc(h, bb, &h->far_src, n))) return rc;
+  if ((rc = dalloc(h, bb, &h->far_dest, n))) return rc;
+  if ((rc = dalloc(h, bb, &h->far_stidx, n))) return rc;
+  if ((rc = dalloc(h, bb, &h->far_ssrc, n))) return rc;
+  if ((rc = dalloc(h, bb, &h->fcount, nb))) return rc;
+  if ((rc = dalloc(h, bb, &h->fcursor, nb))) return rc;
+  if ((rc = dalloc(h, bb, &h->fstart, nb + 1))) return rc;
+  if ((rc = dalloc(h, bb, &h->btot, nb))) return rc;
+  if ((rc = dalloc(h, bb, &h->bstart, nb + 1))) return rc;
+  if (scan_tiles_needed(nb) + 1 > scan_tiles_needed(h->dt.n_keys) + 1)
+    return fail(h, PIC_EINVAL, "brick count exceeds scan scratch");
+  CK(brick_configure(g));
+  h->bg = g;
+  h->brick = true;
+  return PIC_OK;
+}
+
+int ensure_leaf(pic_t h) {
+  if (!h->leaf_stale) return PIC_OK;
+  launch_expand_leaves(h->start_cur, h->dt.n_leaves, h->leaf[0], h->stream);
+  CK(cudaGetLastError());
+  h->leaf_stale = false;
+  return PIC_OK;
+}
+
+int brick_push_and_rebin(pic_t h, double dt) {
+  cudaStream_t s = h->stream;
+  const int d = h->d;
+  BrickPushArgs pa{};
+  pa.n = h->n;
+  pa.o = (const float *)h->pos[0];
+  pa.v = (const float *)h->vel[0];
+  pa.start = h->start_cur;
+  pa.ids = h->cfg.track_ids ? h->ids[0] : nullptr;
+  pa.E = (const float *)h->E;
+  pa.qmdt = (float)(h->cfg.qm * dt);
+  pa.sl = (float)(dt * (double)pow3(h->ht.depth));
+  pa.to = (float *)h->pos[1];
+  pa.tv = (float *)h->vel[1];
+  pa.tcode = h->tcode;
+  pa.tids = h->ids[1];
+  pa.cnt = h->bcnt;
+  pa.segoff = h->bsegoff;
+  pa.far_n = h->far_n;
+  pa.far_cap = (int32_t)h->n;
+  pa.far_tidx = h->far_tidx;
+  pa.far_src = h->far_src;
+  pa.far_dest = h->far_dest;
+  pa.n_movers = h->scalars + 1;
+  pa.err = h->err;
+  BrickPullArgs qa{};
+  qa.n = h->n;
+  qa.old_start = h->start_cur;
+  qa.cnt = h->bcnt;
+  qa.segoff = h->bsegoff;
+  qa.fstart = h->fstart;
+  qa.fstart_w = h->fstart;
+  qa.far_tidx = h->far_stidx;
+  qa.far_src = h->far_ssrc;
+  qa.far_tidx_w = h->far_stidx;
+  qa.far_src_w = h->far_ssrc;
+  qa.tot_w = h->btot;
+  qa.bstart = h->bstart;
+  qa.bstart_w = h->bstart;
+  qa.tcode = h->tcode;
+  qa.to = (const float *)h->pos[1];
+  qa.tv = (const float *)h->vel[1];
+  qa.tids = pa.ids ? h->ids[1] : nullptr;
+  qa.o = (float *)h->pos[0];
+  qa.v = (float *)h->vel[0];
+  qa.ids = pa.ids ? h->ids[0] : nullptr;
+  qa.new_start = h->start_new;
+  qa.max_bucket = h->scalars + 2;
+  qa.err = h->err;
+  (void)d;
+  CK(cudaMemsetAsync(h->scalars + 1, 0, sizeof(int32_t) * 2, s));
+  {
+    PhaseScope ps(h, PIC_PHASE_PUSH);
+    launch_brick_push(h->dt, h->bg, pa, s);
+  }
+  {
+    PhaseScope ps(h, PIC_PHASE_REBIN);
+    launch_brick_pull(h->dt, h->bg, pa, qa, h->fcount, h->fcursor, h->tile_sums, h->scalars + 3, s);
+  }
+  CK(cudaGetLastError());
+  std::swap(h->start_cur, h->start_new);
+  h->leaf_stale = true;
+  return PIC_OK;
+}
+
 // Stable re-bin of the pushed state [1] into the current state [0].
 // old_start == NULL: fresh particles, every one counted as a mover.
 int rebin_and_gather(pic_t h, const int32_t *old_start) {
@@ -355,6 +494,7 @@ int rebin_and_gather(pic_t h, const int32_t *old_start) {
     std::swap(h->ids[0], h->ids[1]);
   }
   std::swap(h->start_cur, h->start_new);
+  h->leaf_stale = false;
   CK(cudaGetLastError());
   return PIC_OK;
 }
@@ -391,6 +531,9 @@ int field(pic_t h, pic_solve_fn hook, void *user) {
 }
 
 int push_and_rebin(pic_t h, double dt) {
+  if (h->brick) return brick_push_and_rebin(h, dt);
+  int rc0 = ensure_leaf(h);
+  if (rc0) return rc0;
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(h->count, 0, sizeof(int32_t) * h->dt.n_keys, s));
   PhaseScope *ps = new PhaseScope(h, PIC_PHASE_PUSH);
@@ -519,6 +662,7 @@ void pic_destroy(pic_t h) {
     cudaEventDestroy(p.b);
   }
   for (auto e : h->event_pool) cudaEventDestroy(e);
+  free_bufs(h, h->brick_bufs);
   free_bufs(h, h->state_bufs);
   free_bufs(h, h->tree_bufs);
   delete h;
@@ -554,6 +698,7 @@ int pic_create(pic_t *out, const pic_tree_desc *tree, const pic_particles_desc *
   e = set_kref(h->d, h->stream);
   if (e != cudaSuccess) { rc = cuda_fail(h, e, "set_kref"); pic_destroy(h); return rc; }
   if ((rc = alloc_state(h))) { pic_destroy(h); return rc; }
+  if ((rc = setup_brick(h))) { pic_destroy(h); return rc; }
   if (h->n > 0) {
     std::vector<int32_t> iota(h->n);
     for (int64_t i = 0; i < h->n; ++i) iota[i] = (int32_t)i;
@@ -580,6 +725,7 @@ int pic_info(pic_t h, pic_info_t *o) {
   o->n_buckets = h->scheme == PIC_PIT ? h->dt.n_leaves : h->dt.n_pv;
   o->n_keys = h->dt.n_keys;
   o->uniform = h->dt.uniform;
+  o->brick = h->brick ? 1 : 0;
   o->device_bytes = h->device_bytes;
   return PIC_OK;
 }
@@ -587,6 +733,7 @@ int pic_info(pic_t h, pic_info_t *o) {
 int pic_init_leapfrog(pic_t h, double dt, pic_solve_fn hook, void *user) {
   if (check_handle(h)) return PIC_EINVAL;
   int rc;
+  if ((rc = ensure_leaf(h))) return rc;
   if ((rc = deposit(h))) return rc;
   if ((rc = field(h, hook, user))) return rc;
   launch_gather_only(h->dt, h->split, h->pos[0], h->leaf[0], h->n, h->E, h->Ep, h->stream);
@@ -679,6 +826,8 @@ int pic_bins(pic_t h, int64_t *bucket_start, int32_t *perm, int32_t where) {
 
 int pic_keys(pic_t h, int32_t *keys, int32_t where) {
   if (check_handle(h) || !keys) return PIC_EINVAL;
+  int rc = ensure_leaf(h);
+  if (rc) return rc;
   return copy_out(h, keys, h->key[0], sizeof(int32_t) * h->n, where);
 }
 
@@ -686,6 +835,7 @@ int pic_get_particles(pic_t h, double *x, double *v, int32_t where) {
   if (check_handle(h)) return PIC_EINVAL;
   const int64_t m = h->n * h->d;
   int rc;
+  if ((rc = ensure_leaf(h))) return rc;
   if (h->split) {
     if (x) {
       launch_absolute_split(h->dt, h->leaf[0], (const float *)h->pos[0], h->n, (double *)h->Ep, h->stream);
@@ -703,6 +853,8 @@ int pic_get_particles(pic_t h, double *x, double *v, int32_t where) {
 
 int pic_get_state(pic_t h, int32_t *leaf, void *x_or_o, void *v, int32_t where) {
   if (check_handle(h)) return PIC_EINVAL;
+  int rc0 = ensure_leaf(h);
+  if (rc0) return rc0;
   const size_t fs = h->split ? sizeof(float) : sizeof(double);
   const size_t m = (size_t)h->n * h->d;
   cudaMemcpyKind kind = where == PIC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;

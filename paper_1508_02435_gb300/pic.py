@@ -14,6 +14,7 @@ import threading
 import numpy as np
 
 PIT, PIDT = 0, 1
+PATH_AUTO, PATH_GENERIC = 0, 1
 FP64, FP32_SPLIT = 0, 1
 HOST, DEVICE = 0, 1
 
@@ -42,14 +43,14 @@ class ParticlesDesc(C.Structure):
 class Config(C.Structure):
     _fields_ = [("scheme", C.c_int32), ("precision", C.c_int32), ("q", C.c_double), ("qm", C.c_double),
                 ("ion", C.c_double), ("sweeps", C.c_int32), ("omega", C.c_double),
-                ("track_ids", C.c_int32), ("stream", C.c_void_p)]
+                ("track_ids", C.c_int32), ("stream", C.c_void_p), ("path", C.c_int32)]
 
 
 class Info(C.Structure):
     _fields_ = [("d", C.c_int32), ("scheme", C.c_int32), ("precision", C.c_int32), ("depth", C.c_int32),
                 ("n_particles", C.c_int64), ("n_leaves", C.c_int64), ("n_vertices", C.c_int64),
                 ("n_buckets", C.c_int64), ("n_keys", C.c_int64), ("uniform", C.c_int32),
-                ("device_bytes", C.c_int64)]
+                ("brick", C.c_int32), ("device_bytes", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -133,7 +134,7 @@ class Pic:
 
     def __init__(self, d: int, flags: np.ndarray, x, v, *, scheme: int = PIT, precision: int = FP64,
                  q: float = -1.0, qm: float = -1.0, ion: float = 1.0, sweeps: int = 100,
-                 omega: float = 0.8, track_ids: bool = True, stream=None):
+                 omega: float = 0.8, track_ids: bool = True, stream=None, path: int = PATH_AUTO):
         self.lib = load()
         self.d = d
         flags = np.ascontiguousarray(flags, dtype=np.uint8)
@@ -148,7 +149,7 @@ class Pic:
         parts = ParticlesDesc(n, xp, vp, where)
         st = C.c_void_p(stream.cuda_stream) if stream is not None and hasattr(stream, "cuda_stream") else \
             C.c_void_p(stream)
-        self.cfg = Config(scheme, precision, q, qm, ion, sweeps, omega, 1 if track_ids else 0, st)
+        self.cfg = Config(scheme, precision, q, qm, ion, sweeps, omega, 1 if track_ids else 0, st, path)
         h = C.c_void_p()
         rc = self.lib.pic_create(C.byref(h), C.byref(tree), C.byref(parts), C.byref(self.cfg))
         if rc != 0:

@@ -44,6 +44,7 @@ TREES = [
     pytest.param(2, lambda: W.uniform_tree_flags(2, 3), id="2d-uniform-d3"),
     pytest.param(2, lambda: W.random_tree_flags(2, 5, 0.3, 5, min_depth=2), id="2d-adaptive-d5"),
     pytest.param(3, lambda: W.uniform_tree_flags(3, 2), id="3d-uniform-d2"),
+    pytest.param(3, lambda: W.uniform_tree_flags(3, 3), id="3d-uniform-d3"),
     pytest.param(3, lambda: W.random_tree_flags(3, 3, 0.3, 6, min_depth=1), id="3d-adaptive-d3"),
 ]
 
@@ -215,3 +216,34 @@ def test_device_inputs_and_determinism():
             assert np.array_equal(a, b)
         assert np.array_equal(o[1][1], outs[0][1][1])
         assert np.array_equal(o[2], outs[0][2])
+
+
+# ---------------------------------------------------------------------------
+# brick path (uniform trees, PIT, split) against the generic path
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,depth,n,vmax", [(2, 4, 150_001, 2.0), (3, 3, 120_001, 0.3),
+                                            (3, 4, 200_003, 2.0), (2, 3, 11_664, 0.05)])
+def test_brick_path_bit_identical_to_generic(d, depth, n, vmax):
+    """Same state, bucket offsets and ids after several steps, with particles
+    that stay, move to neighbour bricks and tunnel across several bricks."""
+    flags = W.uniform_tree_flags(d, depth)
+    x, v = W.random_particles(d, n, 31 + depth, vmax=vmax)
+    kw = dict(q=-1.0 / n, qm=-1.0, ion=1.0, sweeps=5, omega=0.8)
+    fast = make(d, flags, x, v, pic.PIT, pic.FP32_SPLIT, path=pic.PATH_AUTO, **kw)
+    slow = make(d, flags, x, v, pic.PIT, pic.FP32_SPLIT, path=pic.PATH_GENERIC, **kw)
+    assert fast.info().brick == 1 and slow.info().brick == 0
+    for step in range(3):
+        fast.step(0.1)
+        slow.step(0.1)
+        fast.sync()
+        slow.sync()
+        for a, b in zip(fast.get_state(), slow.get_state()):
+            assert np.array_equal(a, b), f"state differs at step {step}"
+        sf, idf = fast.bins()
+        ss, ids = slow.bins()
+        assert np.array_equal(sf, ss) and np.array_equal(idf, ids)
+        assert np.array_equal(fast.deposit(), slow.deposit())
+        assert fast.stats().movers == slow.stats().movers
+        assert fast.stats().max_bucket == slow.stats().max_bucket
+        assert fast.stats().error == 0
