@@ -536,6 +536,7 @@ int push_and_rebin(pic_t h, double dt) {
   if (rc0) return rc0;
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(h->count, 0, sizeof(int32_t) * h->dt.n_keys, s));
+  CK(cudaMemsetAsync(h->scalars + 2, 0, sizeof(int32_t), s));
   PhaseScope *ps = new PhaseScope(h, PIC_PHASE_PUSH);
   if (h->split) {
     Push32Args a{};
