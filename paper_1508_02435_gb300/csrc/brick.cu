@@ -35,7 +35,7 @@ constexpr uint16_t kStayBit = 0x8000;
 constexpr int kPushThreads = 512;
 constexpr int kPullThreads = 256;
 constexpr int kPullWarps = kPullThreads / 32;
-constexpr int kMaxPieces = 27 + 256; // neighbour segments + far arrivals per brick
+constexpr int kMaxPieces = 64;       // round-1 piece + 27 segments + 28 runs of far arrivals
 
 __device__ __forceinline__ int dir_delta(int dir, int a) {
   return a == 0 ? dir % 3 - 1 : (a == 1 ? (dir / 3) % 3 - 1 : dir / 9 - 1);
@@ -309,7 +309,8 @@ __global__ void k_brick_totals(DevTree t, BrickGeom g, const int32_t *cnt, const
 
 struct Piece {
   int32_t tstart, len, src;
-  int32_t round1;  // 1: keep stayers only; 0: keep movers only
+  int16_t round1;    // 1: keep stayers only; 0: keep movers only
+  int16_t indirect;  // 1: positions tstart.. index the sorted far arrivals
 };
 
 __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeom g, BrickPullArgs a) {
@@ -339,21 +340,24 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       }
       int32_t src = brick_of_coords(t, g, sc);
       int64_t k = (int64_t)src * kSlots + dir;
-      Piece pc{a.old_start[src * LB] + a.segoff[k], a.cnt[k], src, 0};
-      if (dir == kSelfDir) pieces[0] = Piece{pc.tstart, pc.len, src, 1};
+      Piece pc{a.old_start[src * LB] + a.segoff[k], a.cnt[k], src, 0, 0};
+      if (dir == kSelfDir) pieces[0] = Piece{pc.tstart, pc.len, src, 1, 0};
       int j = ns++;
       while (j > 0 && seg[j - 1].src > src) { seg[j] = seg[j - 1]; --j; }
       seg[j] = pc;
     }
+    // far arrivals (sorted by storage index, so by source brick) go between
+    // the neighbour segments as runs of the sorted far list
     int np = 1;
-    int32_t fb = a.fstart[b], fe = a.fstart[b + 1], fi = fb;
+    int32_t fi = a.fstart[b];
+    const int32_t fe = a.fstart[b + 1];
     for (int k = 0; k < ns; ++k) {
-      while (fi < fe && a.far_src[fi] < seg[k].src && np < kMaxPieces)
-        pieces[np++] = Piece{a.far_tidx[fi], 1, a.far_src[fi], 0}, ++fi;
+      int32_t f0 = fi;
+      while (fi < fe && a.far_src[fi] < seg[k].src) ++fi;
+      if (fi > f0) pieces[np++] = Piece{f0, fi - f0, -1, 0, 1};
       pieces[np++] = seg[k];
     }
-    while (fi < fe && np < kMaxPieces) pieces[np++] = Piece{a.far_tidx[fi], 1, a.far_src[fi], 0}, ++fi;
-    if (fi < fe) atomicOr(a.err, 4);
+    if (fi < fe) pieces[np++] = Piece{fi, fe - fi, -1, 0, 1};
     int32_t s = 0;
     for (int k = 0; k < np; ++k) { pfx[k] = s; s += pieces[k].len; }
     pfx[np] = s;
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       int leaf = -1;
       if (in) {
         const Piece &pc = pieces[kk];
-        tidx = pc.tstart + (r - pfx[kk]);
+        tidx = pc.indirect ? a.far_tidx[pc.tstart + (r - pfx[kk])] : pc.tstart + (r - pfx[kk]);
         uint16_t code = a.tcode[tidx];
         bool stay = (code & kStayBit) != 0;
         keep = pc.round1 ? stay : !stay;

@@ -767,7 +767,9 @@ int pic_sync(pic_t h) {
   int32_t err = 0;
   int rc = read_err(h, &err);
   if (rc) return rc;
-  return err ? fail(h, PIC_ERANGE, "non-finite position or velocity") : PIC_OK;
+  if (err & 1) return fail(h, PIC_ERANGE, "non-finite position or velocity");
+  if (err) return fail(h, PIC_ESTATE, "device-side capacity exceeded (error bits " + std::to_string(err) + ")");
+  return PIC_OK;
 }
 
 int pic_deposit(pic_t h, double *Q_out, int32_t where) {
@@ -900,7 +902,7 @@ int pic_stats(pic_t h, pic_stats_t *o) {
   o->max_bucket = sc[2];
   o->total_charge = tot;
   o->residual = std::sqrt(r2);
-  o->error = err ? PIC_ERANGE : PIC_OK;
+  o->error = (err & 1) ? PIC_ERANGE : (err ? PIC_ESTATE : PIC_OK);
   return PIC_OK;
 }
 
