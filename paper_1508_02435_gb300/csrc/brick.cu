@@ -36,52 +36,72 @@ constexpr int kPushThreads = 512;
 constexpr int kPullThreads = 256;
 constexpr int kPullWarps = kPullThreads / 32;
 constexpr int kMaxPieces = 64;       // round-1 piece + 27 segments + 28 runs of far arrivals
+constexpr int kLidxCap = 8192;       // particles per brick with a shared-memory leaf index
+constexpr int kInvCap = 10240;       // particles per brick staged for coalesced output
+
+// Compile-time brick shape: B = 9 leaves per axis (two levels).
+template <int D>
+struct BK {
+  static constexpr int B = 9, V1 = 10;
+  static constexpr int LB = D == 3 ? 729 : 81;
+  static constexpr int NVB = D == 3 ? 1000 : 100;
+  static constexpr int NC = 1 << D;
+};
 
 __device__ __forceinline__ int dir_delta(int dir, int a) {
   return a == 0 ? dir % 3 - 1 : (a == 1 ? (dir / 3) % 3 - 1 : dir / 9 - 1);
 }
 
-__device__ __forceinline__ int32_t brick_of_coords(const DevTree &t, const BrickGeom &g, const int32_t *bc) {
-  int32_t c[3] = {bc[0] * g.B, bc[1] * g.B, g.d == 3 ? bc[2] * g.B : 0};
-  return uniform_leaf_of_cell(t.spread, t.M, c, g.d) / g.LB;
+template <int D>
+__device__ __forceinline__ int32_t brick_of_coords(const DevTree &t, const int32_t *bc) {
+  int32_t c[3] = {bc[0] * 9, bc[1] * 9, D == 3 ? bc[2] * 9 : 0};
+  return uniform_leaf_of_cell(t.spread, t.M, c, D) / BK<D>::LB;
 }
 
 // ---------------------------------------------------------------------------
 // K1
 // ---------------------------------------------------------------------------
 
-struct PushOut {
-  int dir;
-  int32_t L2;
-  float o[3], v[3];
-};
-
-// Gather + kick + drift + re-location of one particle (the arithmetic of the
-// generic split push, field values from the staged brick field).
-__device__ __forceinline__ void brick_push_one(const DevTree &t, const BrickGeom &g, const BrickPushArgs &a,
-                                               int64_t p, const int32_t *lc, const int32_t *origin,
-                                               const int32_t *bc, const float *Eb, int nvb, PushOut &out,
-                                               bool &bad) {
-  const int d = g.d, nc = 1 << d, V1 = g.B + 1;
+// Gather + kick + drift + re-location of one particle -- the arithmetic of
+// the generic split push, field values from the staged brick field.  Returns
+// the destination direction slot.
+template <int D>
+__device__ __forceinline__ int brick_push_one(const DevTree &t, const BrickGeom &g, const BrickPushArgs &a,
+                                              int32_t p, const int32_t *lc, const int32_t *origin,
+                                              const int32_t *bc, const float *Eb, float *on, float *vn,
+                                              int32_t &L2, bool &bad) {
+  using K = BK<D>;
   const int64_t n = a.n;
-  float o[3] = {0.f, 0.f, 0.f};
-  for (int ax = 0; ax < d; ++ax) o[ax] = a.o[ax * n + p];
-  float E[3] = {0.f, 0.f, 0.f};
-  const int base = lc[0] + V1 * (lc[1] + (d == 3 ? V1 * lc[2] : 0));
-  for (int e = 0; e < nc; ++e) {
-    float w = shape<float>(o, e, d);
-    int lv = base + (e & 1) + ((e >> 1) & 1) * V1 + ((e >> 2) & 1) * V1 * V1;
-    for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * Eb[ax * nvb + lv];
+  float o[D], om[D];
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) {
+    o[ax] = a.o[ax * n + p];
+    om[ax] = 1.0f - o[ax];
+  }
+  float E[D];
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) E[ax] = 0.0f;
+  const int base = lc[0] + K::V1 * (lc[1] + (D == 3 ? K::V1 * lc[2] : 0));
+#pragma unroll
+  for (int e = 0; e < K::NC; ++e) {
+    float w = 1.0f;
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) w = w * (((e >> ax) & 1) ? o[ax] : om[ax]);
+    const int lv = base + (e & 1) + ((e >> 1) & 1) * K::V1 + ((e >> 2) & 1) * K::V1 * K::V1;
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) E[ax] = E[ax] + w * Eb[ax * K::NVB + lv];
   }
   int32_t I[3] = {0, 0, 0};
-  float f[3] = {0.f, 0.f, 0.f};
   const int32_t per = t.M;
-  for (int ax = 0; ax < d; ++ax) {
-    float vn = a.v[ax * n + p] + a.qmdt * E[ax];
-    float tt = o[ax] + vn * a.sl;
-    if (!isfinite(vn) || !isfinite(tt)) { bad = true; tt = 0.0f; }
+  int dir = 0, mul = 1;
+  bool far = false;
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) {
+    float v = a.v[ax * n + p] + a.qmdt * E[ax];
+    float tt = o[ax] + v * a.sl;
+    if (!isfinite(v) || !isfinite(tt)) { bad = true; tt = 0.0f; }
     float fl = floorf(tt);
-    f[ax] = tt - fl;
+    float f = tt - fl;
     int32_t c = origin[ax] + lc[ax], cc;
     if (fabsf(fl) < 1.0e9f) {
       cc = c + (int32_t)fl;
@@ -94,86 +114,83 @@ __device__ __forceinline__ void brick_push_one(const DevTree &t, const BrickGeom
       cc = (int32_t)(c64 < 0 ? c64 + per : c64);
     }
     I[ax] = cc;
-    out.v[ax] = vn;
-    out.o[ax] = clamp_off(f[ax]);
-  }
-  out.L2 = uniform_leaf_of_cell(t.spread, t.M, I, d);
-  int dir = 0, mul = 1;
-  bool far = false;
-  for (int ax = 0; ax < 3; ++ax) {
-    int dl = 0;
-    if (ax < d) {
-      int32_t db = I[ax] / g.B - bc[ax];
-      if (db < 0) db += g.nbx;
-      dl = db == 0 ? 0 : (db == 1 ? 1 : (db == g.nbx - 1 ? -1 : 2));
-      if (dl == 2) far = true;
-    }
+    vn[ax] = v;
+    on[ax] = clamp_off(f);
+    int32_t db = cc / K::B - bc[ax];
+    if (db < 0) db += g.nbx;
+    int dl = db == 0 ? 0 : (db == 1 ? 1 : (db == g.nbx - 1 ? -1 : 2));
+    far |= dl == 2;
     dir += (dl + 1) * mul;
     mul *= 3;
   }
-  out.dir = far ? kFarSlot : dir;
+  if (D == 2) dir += 9;
+  L2 = uniform_leaf_of_cell(t.spread, t.M, I, D);
+  return far ? kFarSlot : dir;
 }
 
+template <int D>
 __global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeom g, BrickPushArgs a) {
-  extern __shared__ int32_t sm[];
-  const int LB = g.LB, d = g.d, V1 = g.B + 1;
-  const int nvb = d == 3 ? V1 * V1 * V1 : V1 * V1;
-  int32_t *ls = sm;                                  // LB + 1 local leaf starts
-  uint32_t *dec = (uint32_t *)(ls + LB + 1);         // LB packed local coords
-  float *Eb = (float *)(dec + LB);                   // d * nvb staged field
-  int32_t *counters = (int32_t *)(Eb + d * nvb);     // kSlots
-  int32_t *seg = counters + kSlots;                  // kSlots
-  int32_t *run = seg + kSlots;                       // kSlots
-  int32_t *wcnt = run + kSlots;                      // warps * kSlots
+  using K = BK<D>;
+  __shared__ int32_t ls[K::LB + 1];
+  __shared__ uint32_t dec[K::LB];
+  __shared__ float Eb[D * K::NVB];
+  __shared__ uint16_t lidx[kLidxCap];
+  __shared__ int32_t counters[kSlots], seg[kSlots], run[kSlots];
+  __shared__ int32_t wcnt[(kPushThreads / 32) * kSlots];
   __shared__ int32_t s_movers;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
-  const int32_t b = blockIdx.x;
-  const int32_t L0 = b * LB;
+  const int32_t b = blockIdx.x, L0 = b * K::LB;
   int32_t origin[3] = {0, 0, 0}, bc[3] = {0, 0, 0};
-  for (int ax = 0; ax < d; ++ax) {
-    origin[ax] = t.leaf_coords[(int64_t)L0 * d + ax];
-    bc[ax] = origin[ax] / g.B;
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) {
+    origin[ax] = t.leaf_coords[(int64_t)L0 * D + ax];
+    bc[ax] = origin[ax] / K::B;
   }
-  const int32_t ps = a.start[L0], pe = a.start[L0 + LB], nb = pe - ps;
-  for (int i = tid; i <= LB; i += blockDim.x) ls[i] = a.start[L0 + i] - ps;
-  for (int i = tid; i < LB; i += blockDim.x) dec[i] = g.decodeL[i];
-  for (int i = tid; i < nvb; i += blockDim.x) {
-    int lx = i % V1, ly = (i / V1) % V1, lz = d == 3 ? i / (V1 * V1) : 0;
-    int32_t gx = origin[0] + lx, gy = origin[1] + ly, gz = d == 3 ? origin[2] + lz : 0;
+  const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nb = pe - ps;
+  for (int i = tid; i <= K::LB; i += blockDim.x) ls[i] = a.start[L0 + i] - ps;
+  for (int i = tid; i < K::LB; i += blockDim.x) dec[i] = g.decodeL[i];
+  for (int i = tid; i < K::NVB; i += blockDim.x) {
+    int lx = i % K::V1, ly = (i / K::V1) % K::V1, lz = D == 3 ? i / (K::V1 * K::V1) : 0;
+    int32_t gx = origin[0] + lx, gy = origin[1] + ly, gz = D == 3 ? origin[2] + lz : 0;
     if (gx >= t.M) gx -= t.M;
     if (gy >= t.M) gy -= t.M;
     if (gz >= t.M) gz -= t.M;
     int64_t vid = gx + (int64_t)t.M * (gy + (int64_t)t.M * gz);
-    for (int ax = 0; ax < d; ++ax) Eb[ax * nvb + i] = a.E[ax * t.n_vert + vid];
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) Eb[ax * K::NVB + i] = a.E[ax * t.n_vert + vid];
   }
   if (tid < kSlots) { counters[tid] = 0; run[tid] = 0; }
   if (tid == 0) s_movers = 0;
   __syncthreads();
-
-  auto local_leaf = [&](int32_t q) {  // upper_bound(ls, q) - 1
-    int lo = 0, hi = LB;
+  // particle -> local leaf index
+  for (int l = tid; l < K::LB; l += blockDim.x)
+    for (int32_t q = ls[l]; q < ls[l + 1] && q < kLidxCap; ++q) lidx[q] = (uint16_t)l;
+  __syncthreads();
+  auto local_leaf = [&](int32_t q) -> int {
+    if (q < kLidxCap) return lidx[q];
+    int lo = 0, hi = K::LB;
     while (hi - lo > 1) {
       int mid = (lo + hi) >> 1;
       if (ls[mid] <= q) lo = mid; else hi = mid;
     }
     return lo;
   };
-  auto coords_of = [&](int l, int32_t *lc) {
-    uint32_t pk = dec[l];
-    lc[0] = (int32_t)(pk & 1023u);
-    lc[1] = (int32_t)((pk >> 10) & 1023u);
-    lc[2] = (int32_t)(pk >> 20);
-  };
 
-  // pass A: destination counts
+  // pass A: destination counts (warp-aggregated)
   bool bad = false;
-  for (int32_t q = tid; q < nb; q += blockDim.x) {
-    int l = local_leaf(q);
-    int32_t lc[3];
-    coords_of(l, lc);
-    PushOut out;
-    brick_push_one(t, g, a, ps + q, lc, origin, bc, Eb, nvb, out, bad);
-    atomicAdd(&counters[out.dir], 1);
+  for (int32_t base = 0; base < nb; base += blockDim.x) {
+    const int32_t q = base + tid;
+    int dir = 255;
+    if (q < nb) {
+      const int l = local_leaf(q);
+      const uint32_t pk = dec[l];
+      const int32_t lc[3] = {(int32_t)(pk & 1023u), (int32_t)((pk >> 10) & 1023u), (int32_t)(pk >> 20)};
+      float on[D], vn[D];
+      int32_t L2;
+      dir = brick_push_one<D>(t, g, a, ps + q, lc, origin, bc, Eb, on, vn, L2, bad);
+    }
+    unsigned peers = __match_any_sync(0xffffffffu, dir);
+    if (dir != 255 && lane == __ffs(peers) - 1) atomicAdd(&counters[dir], __popc(peers));
   }
   __syncthreads();
   if (tid == 0) {
@@ -189,23 +206,24 @@ __global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeo
 
   // pass B: stable partition by direction
   int movers = 0;
+  const int64_t n = a.n;
   for (int32_t base = 0; base < nb; base += blockDim.x) {
     const int32_t q = base + tid;
     const bool act = q < nb;
     if (lane < kSlots) wcnt[w * kSlots + lane] = 0;
     __syncwarp();
-    PushOut out;
-    out.dir = 255;
-    int l = 0;
+    int dir = 255, l = 0;
+    float on[D], vn[D];
+    int32_t L2 = 0;
     if (act) {
       l = local_leaf(q);
-      int32_t lc[3];
-      coords_of(l, lc);
-      brick_push_one(t, g, a, ps + q, lc, origin, bc, Eb, nvb, out, bad);
+      const uint32_t pk = dec[l];
+      const int32_t lc[3] = {(int32_t)(pk & 1023u), (int32_t)((pk >> 10) & 1023u), (int32_t)(pk >> 20)};
+      dir = brick_push_one<D>(t, g, a, ps + q, lc, origin, bc, Eb, on, vn, L2, bad);
     }
-    unsigned peers = __match_any_sync(0xffffffffu, out.dir);
+    unsigned peers = __match_any_sync(0xffffffffu, dir);
     int rank = __popc(peers & ((1u << lane) - 1u));
-    if (act && rank == 0) wcnt[w * kSlots + out.dir] = __popc(peers);
+    if (act && rank == 0) wcnt[w * kSlots + dir] = __popc(peers);
     __syncthreads();
     if (tid < kSlots) {
       int s = run[tid];
@@ -218,22 +236,22 @@ __global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeo
     }
     __syncthreads();
     if (act) {
-      const int64_t n = a.n;
-      const int32_t pos = ps + seg[out.dir] + wcnt[w * kSlots + out.dir] + rank;
-      for (int ax = 0; ax < d; ++ax) {
-        a.to[ax * n + pos] = out.o[ax];
-        a.tv[ax * n + pos] = out.v[ax];
+      const int32_t pos = ps + seg[dir] + wcnt[w * kSlots + dir] + rank;
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        a.to[ax * n + pos] = on[ax];
+        a.tv[ax * n + pos] = vn[ax];
       }
-      const bool stay = out.L2 == L0 + l;
+      const bool stay = L2 == L0 + l;
       movers += !stay;
-      a.tcode[pos] = (uint16_t)(out.L2 % LB) | (stay ? kStayBit : 0);
+      a.tcode[pos] = (uint16_t)(L2 % K::LB) | (stay ? kStayBit : 0);
       if (a.ids) a.tids[pos] = a.ids[ps + q];
-      if (out.dir == kFarSlot) {
+      if (dir == kFarSlot) {
         int32_t k = atomicAdd(a.far_n, 1);
         if (k < a.far_cap) {
           a.far_tidx[k] = pos;
           a.far_src[k] = b;
-          a.far_dest[k] = out.L2 / LB;
+          a.far_dest[k] = L2 / K::LB;
         } else {
           atomicOr(a.err, 4);
         }
@@ -272,6 +290,7 @@ __global__ void k_far_scatter(const int32_t *far_n, int32_t far_cap, const int32
 
 // Per destination brick: far arrivals sorted by temporary index (storage
 // order), and the brick's total incoming count.
+template <int D>
 __global__ void k_brick_totals(DevTree t, BrickGeom g, const int32_t *cnt, const int32_t *fstart,
                                int32_t *sorted_tidx, int32_t *sorted_src, int32_t *tot) {
   int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -287,18 +306,18 @@ __global__ void k_brick_totals(DevTree t, BrickGeom g, const int32_t *cnt, const
     sorted_tidx[j + 1] = x;
     sorted_src[j + 1] = y;
   }
-  int32_t L0 = b * g.LB;
+  const int32_t L0 = b * BK<D>::LB;
   int32_t bc[3] = {0, 0, 0};
-  for (int ax = 0; ax < g.d; ++ax) bc[ax] = t.leaf_coords[(int64_t)L0 * g.d + ax] / g.B;
+  for (int ax = 0; ax < D; ++ax) bc[ax] = t.leaf_coords[(int64_t)L0 * D + ax] / 9;
   int32_t s = fe - fb;
   for (int dir = 0; dir < 27; ++dir) {
-    if (g.d == 2 && dir_delta(dir, 2) != 0) continue;
+    if (D == 2 && dir_delta(dir, 2) != 0) continue;
     int32_t sc[3] = {0, 0, 0};
-    for (int ax = 0; ax < g.d; ++ax) {
+    for (int ax = 0; ax < D; ++ax) {
       int32_t x = bc[ax] - dir_delta(dir, ax);
       sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
     }
-    s += cnt[(int64_t)brick_of_coords(t, g, sc) * kSlots + dir];
+    s += cnt[(int64_t)brick_of_coords<D>(t, sc) * kSlots + dir];
   }
   tot[b] = s;
 }
@@ -313,37 +332,48 @@ struct Piece {
   int16_t indirect;  // 1: positions tstart.. index the sorted far arrivals
 };
 
+template <int D>
 __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeom g, BrickPullArgs a) {
-  extern __shared__ int32_t sm[];
-  const int LB = g.LB, d = g.d;
-  int32_t *hist = sm;                                   // kPullWarps * LB
-  int32_t *lstart = hist + kPullWarps * LB;             // LB + 1
-  Piece *pieces = (Piece *)(lstart + LB + 1);           // kMaxPieces
-  int32_t *pfx = (int32_t *)(pieces + kMaxPieces);      // kMaxPieces + 1 raw prefix
+  using K = BK<D>;
+  extern __shared__ int32_t inv[];                      // kInvCap staged sources
+  __shared__ int32_t hist[kPullWarps * K::LB];
+  __shared__ int32_t lstart[K::LB + 1];
+  __shared__ Piece pieces[kMaxPieces];
+  __shared__ Piece sdesc[27];
+  __shared__ int32_t pfx[kMaxPieces + 1];
+  __shared__ int32_t wsum[kPullWarps];
   __shared__ int32_t s_np, s_tot, s_max;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int32_t b = blockIdx.x, L0 = b * LB;
+  const int32_t b = blockIdx.x, L0 = b * K::LB;
   const int64_t n = a.n;
 
+  // neighbour segment descriptors, one thread per direction
+  if (tid < 27) {
+    const int dir = tid;
+    Piece pc{0, 0, INT32_MAX, 0, 0};
+    if (!(D == 2 && dir_delta(dir, 2) != 0)) {
+      int32_t sc[3] = {0, 0, 0};
+      for (int ax = 0; ax < D; ++ax) {
+        int32_t x = t.leaf_coords[(int64_t)L0 * D + ax] / 9 - dir_delta(dir, ax);
+        sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
+      }
+      const int32_t src = brick_of_coords<D>(t, sc);
+      const int64_t k = (int64_t)src * kSlots + dir;
+      pc = Piece{a.old_start[src * K::LB] + a.segoff[k], a.cnt[k], src, 0, 0};
+    }
+    sdesc[dir] = pc;
+  }
+  for (int i = tid; i < kPullWarps * K::LB; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
   if (tid == 0) {
-    int32_t bc[3] = {0, 0, 0};
-    for (int ax = 0; ax < d; ++ax) bc[ax] = t.leaf_coords[(int64_t)L0 * d + ax] / g.B;
-    // neighbour segments sorted by source brick
     Piece seg[27];
     int ns = 0;
     for (int dir = 0; dir < 27; ++dir) {
-      if (d == 2 && dir_delta(dir, 2) != 0) continue;
-      int32_t sc[3] = {0, 0, 0};
-      for (int ax = 0; ax < d; ++ax) {
-        int32_t x = bc[ax] - dir_delta(dir, ax);
-        sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
-      }
-      int32_t src = brick_of_coords(t, g, sc);
-      int64_t k = (int64_t)src * kSlots + dir;
-      Piece pc{a.old_start[src * LB] + a.segoff[k], a.cnt[k], src, 0, 0};
-      if (dir == kSelfDir) pieces[0] = Piece{pc.tstart, pc.len, src, 1, 0};
+      const Piece pc = sdesc[dir];
+      if (pc.src == INT32_MAX) continue;
+      if (dir == kSelfDir) pieces[0] = Piece{pc.tstart, pc.len, pc.src, 1, 0};
       int j = ns++;
-      while (j > 0 && seg[j - 1].src > src) { seg[j] = seg[j - 1]; --j; }
+      while (j > 0 && seg[j - 1].src > pc.src) { seg[j] = seg[j - 1]; --j; }
       seg[j] = pc;
     }
     // far arrivals (sorted by storage index, so by source brick) go between
@@ -365,21 +395,19 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
     s_tot = s;
     s_max = 0;
   }
-  for (int i = tid; i < kPullWarps * LB; i += blockDim.x) hist[i] = 0;
   __syncthreads();
   const int np = s_np;
   const int32_t R = s_tot;
-  // contiguous raw range per warp
   const int32_t chunk = (R + kPullWarps - 1) / kPullWarps;
   const int32_t r0 = min(R, w * chunk), r1 = min(R, r0 + chunk);
 
-  // visit every raw position of this warp's range in order, 32 at a time
+  // visit this warp's raw range in order, 32 positions at a time
   auto walk = [&](auto fn) {
     int k = 0;
     while (k + 1 < np && pfx[k + 1] <= r0) ++k;
     for (int32_t base = r0; base < r1; base += 32) {
-      int32_t r = base + lane;
-      bool in = r < r1;
+      const int32_t r = base + lane;
+      const bool in = r < r1;
       int kk = k;
       if (in) while (kk + 1 < np && pfx[kk + 1] <= r) ++kk;
       int32_t tidx = 0;
@@ -388,20 +416,19 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       if (in) {
         const Piece &pc = pieces[kk];
         tidx = pc.indirect ? a.far_tidx[pc.tstart + (r - pfx[kk])] : pc.tstart + (r - pfx[kk]);
-        uint16_t code = a.tcode[tidx];
-        bool stay = (code & kStayBit) != 0;
+        const uint16_t code = a.tcode[tidx];
+        const bool stay = (code & kStayBit) != 0;
         keep = pc.round1 ? stay : !stay;
         leaf = code & 0x7fff;
       }
       fn(keep, keep ? leaf : -1, tidx);
-      // advance the piece cursor to the last lane's piece
-      int32_t rl = min(base + 31, r1 - 1);
+      const int32_t rl = min(base + 31, r1 - 1);
       while (k + 1 < np && pfx[k + 1] <= rl) ++k;
     }
   };
 
   // per-warp leaf histograms
-  int32_t *myh = hist + w * LB;
+  int32_t *myh = hist + w * K::LB;
   walk([&](bool keep, int leaf, int32_t) {
     unsigned peers = __match_any_sync(0xffffffffu, leaf);
     int rank = __popc(peers & ((1u << lane) - 1u));
@@ -410,50 +437,51 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
   });
   __syncthreads();
   // leaf totals -> local offsets (block scan), per-warp bases
-  {
-    int32_t carry = 0;
-    for (int base = 0; base < LB; base += blockDim.x) {
-      int l = base + tid;
-      int32_t tot = 0;
-      if (l < LB)
-        for (int k = 0; k < kPullWarps; ++k) tot += hist[k * LB + l];
-      // block exclusive scan of tot
-      __shared__ int32_t wsum[kPullWarps];
-      int32_t x = tot;
-      for (int o = 1; o < 32; o <<= 1) {
-        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-      }
-      if (lane == 31) wsum[w] = x;
-      __syncthreads();
-      int32_t before = 0, all = 0;
-      for (int k = 0; k < kPullWarps; ++k) {
-        if (k < w) before += wsum[k];
-        all += wsum[k];
-      }
-      int32_t ex = carry + before + x - tot;
-      if (l < LB) {
-        lstart[l] = ex;
-        if (tot > 0) atomicMax(&s_max, tot);
-        int32_t s = ex;
-        for (int k = 0; k < kPullWarps; ++k) {
-          int32_t c = hist[k * LB + l];
-          hist[k * LB + l] = s;
-          s += c;
-        }
-      }
-      carry += all;
-      __syncthreads();
+  int32_t carry = 0;
+  for (int base = 0; base < K::LB; base += blockDim.x) {
+    const int l = base + tid;
+    int32_t tot = 0;
+    if (l < K::LB)
+#pragma unroll
+      for (int k = 0; k < kPullWarps; ++k) tot += hist[k * K::LB + l];
+    int32_t x = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    if (tid == 0) lstart[LB] = carry;
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int32_t before = 0, all = 0;
+#pragma unroll
+    for (int k = 0; k < kPullWarps; ++k) {
+      if (k < w) before += wsum[k];
+      all += wsum[k];
+    }
+    const int32_t ex = carry + before + x - tot;
+    if (l < K::LB) {
+      lstart[l] = ex;
+      if (tot > 0) atomicMax(&s_max, tot);
+      int32_t s = ex;
+#pragma unroll
+      for (int k = 0; k < kPullWarps; ++k) {
+        const int32_t c = hist[k * K::LB + l];
+        hist[k * K::LB + l] = s;
+        s += c;
+      }
+    }
+    carry += all;
+    __syncthreads();
   }
+  if (tid == 0) lstart[K::LB] = carry;
   __syncthreads();
   const int32_t bstart = a.bstart[b];
-  for (int l = tid; l < LB; l += blockDim.x) a.new_start[L0 + l] = bstart + lstart[l];
-  if (b == g.n_bricks - 1 && tid == 0) a.new_start[(int64_t)g.n_bricks * LB] = bstart + lstart[LB];
+  const int32_t nin = lstart[K::LB];
+  for (int l = tid; l < K::LB; l += blockDim.x) a.new_start[L0 + l] = bstart + lstart[l];
+  if (b == g.n_bricks - 1 && tid == 0) a.new_start[(int64_t)g.n_bricks * K::LB] = bstart + nin;
   if (tid == 0 && s_max > 0) atomicMax(a.max_bucket, s_max);
+  const bool staged = nin <= kInvCap;
 
-  // rank and move
+  // rank; stage the source of every destination (or move directly)
   walk([&](bool keep, int leaf, int32_t tidx) {
     unsigned peers = __match_any_sync(0xffffffffu, leaf);
     int rank = __popc(peers & ((1u << lane) - 1u));
@@ -462,14 +490,32 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
     if (keep && rank == 0) myh[leaf] = basepos + __popc(peers);
     __syncwarp();
     if (keep) {
-      int32_t dst = bstart + basepos + rank;
-      for (int ax = 0; ax < d; ++ax) {
-        a.o[ax * n + dst] = a.to[ax * n + tidx];
-        a.v[ax * n + dst] = a.tv[ax * n + tidx];
+      const int32_t dl = basepos + rank;
+      if (staged) {
+        inv[dl] = tidx;
+      } else {
+        const int32_t dst = bstart + dl;
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+          a.o[ax * n + dst] = a.to[ax * n + tidx];
+          a.v[ax * n + dst] = a.tv[ax * n + tidx];
+        }
+        if (a.ids) a.ids[dst] = a.tids[tidx];
       }
-      if (a.ids) a.ids[dst] = a.tids[tidx];
     }
   });
+  if (!staged) return;
+  __syncthreads();
+  // coalesced writes in destination order
+  for (int32_t j = tid; j < nin; j += blockDim.x) {
+    const int32_t src = inv[j], dst = bstart + j;
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+      a.o[ax * n + dst] = a.to[ax * n + src];
+      a.v[ax * n + dst] = a.tv[ax * n + src];
+    }
+    if (a.ids) a.ids[dst] = a.tids[src];
+  }
 }
 
 // Leaf id of every particle from the bucket offsets (thread per leaf).
@@ -483,20 +529,12 @@ __global__ void k_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t 
 // launchers
 // ---------------------------------------------------------------------------
 
-size_t brick_push_smem(const BrickGeom &g) {
-  int V1 = g.B + 1;
-  int nvb = g.d == 3 ? V1 * V1 * V1 : V1 * V1;
-  return sizeof(int32_t) * ((g.LB + 1) + g.LB + g.d * nvb + 3 * kSlots + (kPushThreads / 32) * kSlots);
-}
-
-size_t brick_pull_smem(const BrickGeom &g) {
-  return sizeof(int32_t) * (kPullWarps * g.LB + g.LB + 1) + sizeof(Piece) * kMaxPieces +
-         sizeof(int32_t) * (kMaxPieces + 1);
-}
-
 void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs &pa, cudaStream_t s) {
   cudaMemsetAsync(pa.far_n, 0, sizeof(int32_t), s);
-  k_brick_push<<<(unsigned)g.n_bricks, kPushThreads, brick_push_smem(g), s>>>(t, g, pa);
+  if (g.d == 3)
+    k_brick_push<3><<<(unsigned)g.n_bricks, kPushThreads, 0, s>>>(t, g, pa);
+  else
+    k_brick_push<2><<<(unsigned)g.n_bricks, kPushThreads, 0, s>>>(t, g, pa);
   count_launches(1);
 }
 
@@ -504,16 +542,24 @@ void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPushArgs
                        int32_t *fcount, int32_t *fcursor, int32_t *tile_sums, int32_t *scratch_total,
                        cudaStream_t s) {
   const unsigned nb = (unsigned)g.n_bricks;
+  const size_t inv_bytes = sizeof(int32_t) * kInvCap;
   cudaMemsetAsync(fcount, 0, sizeof(int32_t) * g.n_bricks, s);
   cudaMemsetAsync(fcursor, 0, sizeof(int32_t) * g.n_bricks, s);
   k_far_count<<<64, 256, 0, s>>>(pa.far_n, pa.far_cap, pa.far_dest, fcount);
   launch_exclusive_scan(fcount, g.n_bricks, qa.fstart_w, tile_sums, scratch_total, s);
   k_far_scatter<<<64, 256, 0, s>>>(pa.far_n, pa.far_cap, pa.far_dest, pa.far_tidx, pa.far_src, qa.fstart,
                                    fcursor, qa.far_tidx_w, qa.far_src_w);
-  k_brick_totals<<<(nb + 255) / 256, 256, 0, s>>>(t, g, pa.cnt, qa.fstart, qa.far_tidx_w, qa.far_src_w,
-                                                  qa.tot_w);
+  if (g.d == 3)
+    k_brick_totals<3><<<(nb + 255) / 256, 256, 0, s>>>(t, g, pa.cnt, qa.fstart, qa.far_tidx_w, qa.far_src_w,
+                                                       qa.tot_w);
+  else
+    k_brick_totals<2><<<(nb + 255) / 256, 256, 0, s>>>(t, g, pa.cnt, qa.fstart, qa.far_tidx_w, qa.far_src_w,
+                                                       qa.tot_w);
   launch_exclusive_scan(qa.tot_w, g.n_bricks, qa.bstart_w, tile_sums, scratch_total, s);
-  k_brick_pull<<<nb, kPullThreads, brick_pull_smem(g), s>>>(t, g, qa);
+  if (g.d == 3)
+    k_brick_pull<3><<<nb, kPullThreads, inv_bytes, s>>>(t, g, qa);
+  else
+    k_brick_pull<2><<<nb, kPullThreads, inv_bytes, s>>>(t, g, qa);
   count_launches(4);  // far count, far scatter, totals, pull (the scans count themselves)
 }
 
@@ -523,11 +569,10 @@ void launch_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf,
 }
 
 cudaError_t brick_configure(const BrickGeom &g) {
-  cudaError_t e = cudaFuncSetAttribute(k_brick_push, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)brick_push_smem(g));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_brick_pull, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)brick_pull_smem(g));
+  const int bytes = (int)(sizeof(int32_t) * kInvCap);
+  cudaError_t e = g.d == 3 ? cudaFuncSetAttribute(k_brick_pull<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+                           : cudaFuncSetAttribute(k_brick_pull<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
 }
 
 }  // namespace pic
