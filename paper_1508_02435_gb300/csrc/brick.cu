@@ -37,7 +37,7 @@ constexpr int kPullThreads = 256;
 constexpr int kPullWarps = kPullThreads / 32;
 constexpr int kMaxPieces = 64;       // round-1 piece + 27 segments + 28 runs of far arrivals
 constexpr int kLidxCap = 8192;       // particles per brick with a shared-memory leaf index
-constexpr int kInvCap = 10240;       // particles per brick staged for coalesced output
+constexpr int kStageCap = 7680;      // particles per brick staged for coalesced output
 
 // Compile-time brick shape: B = 9 leaves per axis (two levels).
 template <int D>
@@ -335,14 +335,16 @@ struct Piece {
 template <int D>
 __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeom g, BrickPullArgs a) {
   using K = BK<D>;
-  extern __shared__ int32_t inv[];                      // kInvCap staged sources
+  extern __shared__ float stage[];                      // kStageCap staged values
+  uint16_t *map = (uint16_t *)(stage + kStageCap);      // destination -> stage index
   __shared__ int32_t hist[kPullWarps * K::LB];
   __shared__ int32_t lstart[K::LB + 1];
   __shared__ Piece pieces[kMaxPieces];
   __shared__ Piece sdesc[27];
   __shared__ int32_t pfx[kMaxPieces + 1];
+  __shared__ int32_t spfx[kMaxPieces + 1];              // stage offset of round-2 pieces
   __shared__ int32_t wsum[kPullWarps];
-  __shared__ int32_t s_np, s_tot, s_max;
+  __shared__ int32_t s_np, s_tot, s_max, s_self;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int32_t b = blockIdx.x, L0 = b * K::LB;
   const int64_t n = a.n;
@@ -385,12 +387,18 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       int32_t f0 = fi;
       while (fi < fe && a.far_src[fi] < seg[k].src) ++fi;
       if (fi > f0) pieces[np++] = Piece{f0, fi - f0, -1, 0, 1};
+      if (seg[k].src == b) s_self = np;
       pieces[np++] = seg[k];
     }
     if (fi < fe) pieces[np++] = Piece{fi, fe - fi, -1, 0, 1};
     int32_t s = 0;
-    for (int k = 0; k < np; ++k) { pfx[k] = s; s += pieces[k].len; }
+    for (int k = 0; k < np; ++k) {
+      pfx[k] = s;
+      spfx[k] = k == 0 ? 0 : s - pieces[0].len;
+      s += pieces[k].len;
+    }
     pfx[np] = s;
+    spfx[np] = s - pieces[0].len;
     s_np = np;
     s_tot = s;
     s_max = 0;
@@ -401,7 +409,8 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
   const int32_t chunk = (R + kPullWarps - 1) / kPullWarps;
   const int32_t r0 = min(R, w * chunk), r1 = min(R, r0 + chunk);
 
-  // visit this warp's raw range in order, 32 positions at a time
+  // visit this warp's raw range in order, 32 positions at a time:
+  // fn(keep, leaf, temporary index, stage index)
   auto walk = [&](auto fn) {
     int k = 0;
     while (k + 1 < np && pfx[k + 1] <= r0) ++k;
@@ -410,18 +419,20 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       const bool in = r < r1;
       int kk = k;
       if (in) while (kk + 1 < np && pfx[kk + 1] <= r) ++kk;
-      int32_t tidx = 0;
+      int32_t tidx = 0, si = 0;
       bool keep = false;
       int leaf = -1;
       if (in) {
         const Piece &pc = pieces[kk];
-        tidx = pc.indirect ? a.far_tidx[pc.tstart + (r - pfx[kk])] : pc.tstart + (r - pfx[kk]);
+        const int32_t off = r - pfx[kk];
+        tidx = pc.indirect ? a.far_tidx[pc.tstart + off] : pc.tstart + off;
+        si = (kk == 0 ? spfx[s_self] : spfx[kk]) + off;
         const uint16_t code = a.tcode[tidx];
         const bool stay = (code & kStayBit) != 0;
         keep = pc.round1 ? stay : !stay;
         leaf = code & 0x7fff;
       }
-      fn(keep, keep ? leaf : -1, tidx);
+      fn(keep, keep ? leaf : -1, tidx, si);
       const int32_t rl = min(base + 31, r1 - 1);
       while (k + 1 < np && pfx[k + 1] <= rl) ++k;
     }
@@ -429,7 +440,7 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
 
   // per-warp leaf histograms
   int32_t *myh = hist + w * K::LB;
-  walk([&](bool keep, int leaf, int32_t) {
+  walk([&](bool keep, int leaf, int32_t, int32_t) {
     unsigned peers = __match_any_sync(0xffffffffu, leaf);
     int rank = __popc(peers & ((1u << lane) - 1u));
     if (keep && rank == 0) myh[leaf] += __popc(peers);
@@ -479,10 +490,10 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
   for (int l = tid; l < K::LB; l += blockDim.x) a.new_start[L0 + l] = bstart + lstart[l];
   if (b == g.n_bricks - 1 && tid == 0) a.new_start[(int64_t)g.n_bricks * K::LB] = bstart + nin;
   if (tid == 0 && s_max > 0) atomicMax(a.max_bucket, s_max);
-  const bool staged = nin <= kInvCap;
+  const bool staged = nin <= kStageCap;
 
-  // rank; stage the source of every destination (or move directly)
-  walk([&](bool keep, int leaf, int32_t tidx) {
+  // rank: destination of every incoming particle
+  walk([&](bool keep, int leaf, int32_t tidx, int32_t si) {
     unsigned peers = __match_any_sync(0xffffffffu, leaf);
     int rank = __popc(peers & ((1u << lane) - 1u));
     int32_t basepos = keep ? myh[leaf] : 0;
@@ -492,7 +503,7 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
     if (keep) {
       const int32_t dl = basepos + rank;
       if (staged) {
-        inv[dl] = tidx;
+        map[dl] = (uint16_t)si;
       } else {
         const int32_t dst = bstart + dl;
 #pragma unroll
@@ -504,17 +515,50 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       }
     }
   });
-  if (!staged) return;
   __syncthreads();
-  // coalesced writes in destination order
-  for (int32_t j = tid; j < nin; j += blockDim.x) {
-    const int32_t src = inv[j], dst = bstart + j;
-#pragma unroll
-    for (int ax = 0; ax < D; ++ax) {
-      a.o[ax * n + dst] = a.to[ax * n + src];
-      a.v[ax * n + dst] = a.tv[ax * n + src];
+  if (staged) {
+    // one array at a time: coalesced reads of the incoming pieces into shared
+    // memory, coalesced writes in destination order
+    const int na = 2 * D + (a.ids ? 1 : 0);
+    for (int arr = 0; arr < na; ++arr) {
+      const float *src = arr < D ? a.to + arr * n : (arr < 2 * D ? a.tv + (arr - D) * n : (const float *)a.tids);
+      float *dst = arr < D ? a.o + arr * n : (arr < 2 * D ? a.v + (arr - D) * n : (float *)a.ids);
+      for (int k = 1; k < np; ++k) {
+        const Piece pc = pieces[k];
+        const int32_t so = spfx[k];
+        for (int32_t i = tid; i < pc.len; i += blockDim.x)
+          stage[so + i] = src[pc.indirect ? a.far_tidx[pc.tstart + i] : pc.tstart + i];
+      }
+      __syncthreads();
+      for (int32_t j = tid; j < nin; j += blockDim.x) dst[bstart + j] = stage[map[j]];
+      __syncthreads();
     }
-    if (a.ids) a.ids[dst] = a.tids[src];
+  }
+  // deposit partials of the new positions, per leaf in bucket order (the
+  // arithmetic and order of the generic per-leaf deposit)
+  if (a.part) {
+    for (int l = tid; l < K::LB; l += blockDim.x) {
+      float acc[K::NC];
+#pragma unroll
+      for (int e = 0; e < K::NC; ++e) acc[e] = 0.0f;
+      for (int32_t p = bstart + lstart[l]; p < bstart + lstart[l + 1]; ++p) {
+        float o[D], om[D];
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+          o[ax] = a.o[ax * n + p];
+          om[ax] = 1.0f - o[ax];
+        }
+#pragma unroll
+        for (int e = 0; e < K::NC; ++e) {
+          float wgt = 1.0f;
+#pragma unroll
+          for (int ax = 0; ax < D; ++ax) wgt = wgt * (((e >> ax) & 1) ? o[ax] : om[ax]);
+          acc[e] = acc[e] + wgt;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < K::NC; ++e) a.part[(int64_t)(L0 + l) * K::NC + e] = acc[e];
+    }
   }
 }
 
@@ -542,7 +586,7 @@ void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPushArgs
                        int32_t *fcount, int32_t *fcursor, int32_t *tile_sums, int32_t *scratch_total,
                        cudaStream_t s) {
   const unsigned nb = (unsigned)g.n_bricks;
-  const size_t inv_bytes = sizeof(int32_t) * kInvCap;
+  const size_t inv_bytes = (sizeof(float) + sizeof(uint16_t)) * kStageCap;
   cudaMemsetAsync(fcount, 0, sizeof(int32_t) * g.n_bricks, s);
   cudaMemsetAsync(fcursor, 0, sizeof(int32_t) * g.n_bricks, s);
   k_far_count<<<64, 256, 0, s>>>(pa.far_n, pa.far_cap, pa.far_dest, fcount);
@@ -569,7 +613,7 @@ void launch_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf,
 }
 
 cudaError_t brick_configure(const BrickGeom &g) {
-  const int bytes = (int)(sizeof(int32_t) * kInvCap);
+  const int bytes = (int)((sizeof(float) + sizeof(uint16_t)) * kStageCap);
   cudaError_t e = g.d == 3 ? cudaFuncSetAttribute(k_brick_pull<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
                            : cudaFuncSetAttribute(k_brick_pull<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   return e;

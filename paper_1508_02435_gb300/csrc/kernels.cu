@@ -801,18 +801,26 @@ void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *m
   { COUNT(1); k_count_all<<<grid_for(n), kBlock, 0, s>>>(key, n, count, mover_words, block_movers); }
 }
 
-void launch_deposit(const DevTree &t, bool split, const int32_t *start, const void *pos, int64_t n, void *part,
-                    double q, double ion, void *Q, double *block_sum, double *total, cudaStream_t s) {
+void launch_vertex_charge(const DevTree &t, bool split, const void *part, double q, double ion, void *Q,
+                          double *block_sum, double *total, cudaStream_t s) {
   if (split) {
-    { COUNT(1); k_leaf_partials<true><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part); }
     { COUNT(1); k_vertex_charge<float><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const float *)part, (float)q, (float)ion,
                                                                  (float *)Q, block_sum); }
   } else {
-    { COUNT(1); k_leaf_partials<false><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part); }
     { COUNT(1); k_vertex_charge<double><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const double *)part, q, ion, (double *)Q,
                                                                   block_sum); }
   }
   { COUNT(1); k_sum_blocks<<<1, 1024, 0, s>>>(block_sum, grid_for(t.n_vert), total); }
+}
+
+void launch_deposit(const DevTree &t, bool split, const int32_t *start, const void *pos, int64_t n, void *part,
+                    double q, double ion, void *Q, double *block_sum, double *total, cudaStream_t s) {
+  if (split) {
+    { COUNT(1); k_leaf_partials<true><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part); }
+  } else {
+    { COUNT(1); k_leaf_partials<false><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part); }
+  }
+  launch_vertex_charge(t, split, part, q, ion, Q, block_sum, total, s);
 }
 
 void launch_solve(const DevTree &t, bool split, const void *Q, const double *total, void *b, void *V, void *Vtmp,

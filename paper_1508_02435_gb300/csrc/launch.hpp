@@ -98,6 +98,7 @@ struct BrickPullArgs {
   int32_t *new_start;
   int32_t *max_bucket;
   int32_t *err;
+  float *part;                   // leaf-corner deposit partials of the new positions, or NULL
 };
 
 cudaError_t brick_configure(const BrickGeom &g);
@@ -119,6 +120,9 @@ void launch_rekey32(const DevTree &t, const int32_t *leaf, const float *o, int64
                     cudaStream_t s);
 void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *mover_words,
                       int32_t *block_movers, cudaStream_t s);
+// Vertex charges and FP64 total from leaf-corner partials already computed.
+void launch_vertex_charge(const DevTree &t, bool split, const void *part, double q, double ion, void *Q,
+                          double *block_sum, double *total, cudaStream_t s);
 void launch_deposit(const DevTree &t, bool split, const int32_t *start, const void *pos, int64_t n, void *part,
                     double q, double ion, void *Q, double *block_sum, double *total, cudaStream_t s);
 void launch_solve(const DevTree &t, bool split, const void *Q, const double *total, void *b, void *V, void *Vtmp,

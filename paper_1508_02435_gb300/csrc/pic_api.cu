@@ -58,6 +58,7 @@ struct pic_s {
   // brick path (uniform tree, PIT, split precision)
   bool brick = false;
   bool leaf_stale = false;  // leaf[0] not yet expanded from the offsets
+  bool q_valid = false;     // Q holds the charges of the current positions
   BrickGeom bg{};
   std::vector<DevBuf> brick_bufs;
   uint16_t *tcode = nullptr;
@@ -436,6 +437,7 @@ int brick_push_and_rebin(pic_t h, double dt) {
   qa.new_start = h->start_new;
   qa.max_bucket = h->scalars + 2;
   qa.err = h->err;
+  qa.part = (float *)h->part;
   (void)d;
   CK(cudaMemsetAsync(h->scalars + 1, 0, sizeof(int32_t) * 2, s));
   {
@@ -446,9 +448,15 @@ int brick_push_and_rebin(pic_t h, double dt) {
     PhaseScope ps(h, PIC_PHASE_REBIN);
     launch_brick_pull(h->dt, h->bg, pa, qa, h->fcount, h->fcursor, h->tile_sums, h->scalars + 3, s);
   }
+  {
+    // the pull also summed the deposit partials of the new positions
+    PhaseScope ps(h, PIC_PHASE_DEPOSIT);
+    launch_vertex_charge(h->dt, true, h->part, h->cfg.q, h->cfg.ion, h->Q, h->block_sum, h->total, s);
+  }
   CK(cudaGetLastError());
   std::swap(h->start_cur, h->start_new);
   h->leaf_stale = true;
+  h->q_valid = true;
   return PIC_OK;
 }
 
@@ -501,6 +509,7 @@ int rebin_and_gather(pic_t h, const int32_t *old_start) {
 
 // Keys of fresh state in [1] -> counts -> re-bin.
 int bin_fresh(pic_t h) {
+  h->q_valid = false;
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(h->count, 0, sizeof(int32_t) * h->dt.n_keys, s));
   launch_count_all(h->key[1], h->n, h->count, h->mover_words, h->block_movers, s);
@@ -508,7 +517,9 @@ int bin_fresh(pic_t h) {
 }
 
 int deposit(pic_t h) {
+  if (h->q_valid) return PIC_OK;
   PhaseScope ps(h, PIC_PHASE_DEPOSIT);
+  h->q_valid = true;
   launch_deposit(h->dt, h->split, h->start_cur, h->pos[0], h->n, h->part, h->cfg.q, h->cfg.ion, h->Q,
                  h->block_sum, h->total, h->stream);
   CK(cudaGetLastError());
@@ -534,6 +545,7 @@ int push_and_rebin(pic_t h, double dt) {
   if (h->brick) return brick_push_and_rebin(h, dt);
   int rc0 = ensure_leaf(h);
   if (rc0) return rc0;
+  h->q_valid = false;
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(h->count, 0, sizeof(int32_t) * h->dt.n_keys, s));
   CK(cudaMemsetAsync(h->scalars + 2, 0, sizeof(int32_t), s));
