@@ -37,7 +37,7 @@ constexpr int kPullThreads = 256;
 constexpr int kPullWarps = kPullThreads / 32;
 constexpr int kMaxPieces = 64;       // round-1 piece + 27 segments + 28 runs of far arrivals
 constexpr int kLidxCap = 8192;       // particles per brick with a shared-memory leaf index
-constexpr int kStageCap = 7680;      // particles per brick staged for coalesced output
+constexpr int kStageCap = 6144;      // particles per brick staged in shared memory
 
 // Compile-time brick shape: B = 9 leaves per axis (two levels).
 template <int D>
@@ -336,23 +336,24 @@ template <int D>
 __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeom g, BrickPullArgs a) {
   using K = BK<D>;
   extern __shared__ float stage[];                      // kStageCap staged values
-  uint16_t *map = (uint16_t *)(stage + kStageCap);      // destination -> stage index
-  __shared__ int32_t hist[kPullWarps * K::LB];
-  __shared__ int32_t lstart[K::LB + 1];
+  uint16_t *map = (uint16_t *)(stage + kStageCap);      // slot -> raw position -> stage index
+  __shared__ int32_t cnt[K::LB + 1];                    // counts, then offsets
+  __shared__ int32_t cur[K::LB];
   __shared__ Piece pieces[kMaxPieces];
   __shared__ Piece sdesc[27];
   __shared__ int32_t pfx[kMaxPieces + 1];
   __shared__ int32_t spfx[kMaxPieces + 1];              // stage offset of round-2 pieces
-  __shared__ int32_t wsum[kPullWarps];
-  __shared__ int32_t s_np, s_tot, s_max, s_self;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  __shared__ int32_t wsum[kPullThreads / 32];
+  __shared__ int32_t s_np, s_self, s_max;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
   const int32_t b = blockIdx.x, L0 = b * K::LB;
   const int64_t n = a.n;
 
-  // neighbour segment descriptors, one thread per direction
+  // neighbour segments, one thread per direction, placed by source-brick rank
+  __shared__ int32_t s_src[27];
+  Piece mine{0, 0, INT32_MAX, 0, 0};
   if (tid < 27) {
     const int dir = tid;
-    Piece pc{0, 0, INT32_MAX, 0, 0};
     if (!(D == 2 && dir_delta(dir, 2) != 0)) {
       int32_t sc[3] = {0, 0, 0};
       for (int ax = 0; ax < D; ++ax) {
@@ -361,34 +362,34 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       }
       const int32_t src = brick_of_coords<D>(t, sc);
       const int64_t k = (int64_t)src * kSlots + dir;
-      pc = Piece{a.old_start[src * K::LB] + a.segoff[k], a.cnt[k], src, 0, 0};
+      mine = Piece{a.old_start[src * K::LB] + a.segoff[k], a.cnt[k], src, 0, 0};
     }
-    sdesc[dir] = pc;
+    s_src[dir] = mine.src;
   }
-  for (int i = tid; i < kPullWarps * K::LB; i += blockDim.x) hist[i] = 0;
+  for (int i = tid; i < K::LB + 1; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  if (tid < 27 && mine.src != INT32_MAX) {
+    int rank = 0;
+    for (int k = 0; k < 27; ++k) rank += s_src[k] < mine.src;
+    sdesc[rank] = mine;
+    if (tid == kSelfDir) pieces[0] = Piece{mine.tstart, mine.len, mine.src, 1, 0};
+  }
   __syncthreads();
   if (tid == 0) {
-    Piece seg[27];
-    int ns = 0;
-    for (int dir = 0; dir < 27; ++dir) {
-      const Piece pc = sdesc[dir];
-      if (pc.src == INT32_MAX) continue;
-      if (dir == kSelfDir) pieces[0] = Piece{pc.tstart, pc.len, pc.src, 1, 0};
-      int j = ns++;
-      while (j > 0 && seg[j - 1].src > pc.src) { seg[j] = seg[j - 1]; --j; }
-      seg[j] = pc;
-    }
+    const int ns = D == 3 ? 27 : 9;
     // far arrivals (sorted by storage index, so by source brick) go between
     // the neighbour segments as runs of the sorted far list
     int np = 1;
     int32_t fi = a.fstart[b];
     const int32_t fe = a.fstart[b + 1];
     for (int k = 0; k < ns; ++k) {
-      int32_t f0 = fi;
-      while (fi < fe && a.far_src[fi] < seg[k].src) ++fi;
-      if (fi > f0) pieces[np++] = Piece{f0, fi - f0, -1, 0, 1};
-      if (seg[k].src == b) s_self = np;
-      pieces[np++] = seg[k];
+      if (fi < fe) {
+        int32_t f0 = fi;
+        while (fi < fe && a.far_src[fi] < sdesc[k].src) ++fi;
+        if (fi > f0) pieces[np++] = Piece{f0, fi - f0, -1, 0, 1};
+      }
+      if (sdesc[k].src == b) s_self = np;
+      pieces[np++] = sdesc[k];
     }
     if (fi < fe) pieces[np++] = Piece{fi, fe - fi, -1, 0, 1};
     int32_t s = 0;
@@ -398,64 +399,35 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       s += pieces[k].len;
     }
     pfx[np] = s;
-    spfx[np] = s - pieces[0].len;
     s_np = np;
-    s_tot = s;
     s_max = 0;
   }
   __syncthreads();
   const int np = s_np;
-  const int32_t R = s_tot;
-  const int32_t chunk = (R + kPullWarps - 1) / kPullWarps;
-  const int32_t r0 = min(R, w * chunk), r1 = min(R, r0 + chunk);
+  const int32_t self_stage = spfx[s_self];
 
-  // visit this warp's raw range in order, 32 positions at a time:
-  // fn(keep, leaf, temporary index, stage index)
-  auto walk = [&](auto fn) {
-    int k = 0;
-    while (k + 1 < np && pfx[k + 1] <= r0) ++k;
-    for (int32_t base = r0; base < r1; base += 32) {
-      const int32_t r = base + lane;
-      const bool in = r < r1;
-      int kk = k;
-      if (in) while (kk + 1 < np && pfx[kk + 1] <= r) ++kk;
-      int32_t tidx = 0, si = 0;
-      bool keep = false;
-      int leaf = -1;
-      if (in) {
-        const Piece &pc = pieces[kk];
-        const int32_t off = r - pfx[kk];
-        tidx = pc.indirect ? a.far_tidx[pc.tstart + off] : pc.tstart + off;
-        si = (kk == 0 ? spfx[s_self] : spfx[kk]) + off;
+  // every raw position of every piece: fn(raw position, temporary index, keep, leaf)
+  auto each = [&](auto fn) {
+    for (int k = 0; k < np; ++k) {
+      const Piece pc = pieces[k];
+      const int32_t r0 = pfx[k];
+      for (int32_t i = tid; i < pc.len; i += blockDim.x) {
+        const int32_t tidx = pc.indirect ? a.far_tidx[pc.tstart + i] : pc.tstart + i;
         const uint16_t code = a.tcode[tidx];
         const bool stay = (code & kStayBit) != 0;
-        keep = pc.round1 ? stay : !stay;
-        leaf = code & 0x7fff;
+        if (pc.round1 ? stay : !stay) fn(r0 + i, code & 0x7fff);
       }
-      fn(keep, keep ? leaf : -1, tidx, si);
-      const int32_t rl = min(base + 31, r1 - 1);
-      while (k + 1 < np && pfx[k + 1] <= rl) ++k;
     }
   };
-
-  // per-warp leaf histograms
-  int32_t *myh = hist + w * K::LB;
-  walk([&](bool keep, int leaf, int32_t, int32_t) {
-    unsigned peers = __match_any_sync(0xffffffffu, leaf);
-    int rank = __popc(peers & ((1u << lane) - 1u));
-    if (keep && rank == 0) myh[leaf] += __popc(peers);
-    __syncwarp();
-  });
+  // counts per leaf
+  each([&](int32_t, int leaf) { atomicAdd(&cnt[leaf], 1); });
   __syncthreads();
-  // leaf totals -> local offsets (block scan), per-warp bases
+  // exclusive scan of the counts (in place), cursors
   int32_t carry = 0;
   for (int base = 0; base < K::LB; base += blockDim.x) {
     const int l = base + tid;
-    int32_t tot = 0;
-    if (l < K::LB)
-#pragma unroll
-      for (int k = 0; k < kPullWarps; ++k) tot += hist[k * K::LB + l];
-    int32_t x = tot;
+    const int32_t c = l < K::LB ? cnt[l] : 0;
+    int32_t x = c;
     for (int o = 1; o < 32; o <<= 1) {
       int32_t y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
@@ -463,60 +435,45 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
     if (lane == 31) wsum[w] = x;
     __syncthreads();
     int32_t before = 0, all = 0;
-#pragma unroll
-    for (int k = 0; k < kPullWarps; ++k) {
+    for (int k = 0; k < nw; ++k) {
       if (k < w) before += wsum[k];
       all += wsum[k];
     }
-    const int32_t ex = carry + before + x - tot;
     if (l < K::LB) {
-      lstart[l] = ex;
-      if (tot > 0) atomicMax(&s_max, tot);
-      int32_t s = ex;
-#pragma unroll
-      for (int k = 0; k < kPullWarps; ++k) {
-        const int32_t c = hist[k * K::LB + l];
-        hist[k * K::LB + l] = s;
-        s += c;
-      }
+      cnt[l] = carry + before + x - c;
+      cur[l] = cnt[l];
+      if (c > 0) atomicMax(&s_max, c);
     }
     carry += all;
     __syncthreads();
   }
-  if (tid == 0) lstart[K::LB] = carry;
+  if (tid == 0) cnt[K::LB] = carry;
   __syncthreads();
   const int32_t bstart = a.bstart[b];
-  const int32_t nin = lstart[K::LB];
-  for (int l = tid; l < K::LB; l += blockDim.x) a.new_start[L0 + l] = bstart + lstart[l];
+  const int32_t nin = cnt[K::LB];
+  for (int l = tid; l < K::LB; l += blockDim.x) a.new_start[L0 + l] = bstart + cnt[l];
   if (b == g.n_bricks - 1 && tid == 0) a.new_start[(int64_t)g.n_bricks * K::LB] = bstart + nin;
   if (tid == 0 && s_max > 0) atomicMax(a.max_bucket, s_max);
-  const bool staged = nin <= kStageCap;
 
-  // rank: destination of every incoming particle
-  walk([&](bool keep, int leaf, int32_t tidx, int32_t si) {
-    unsigned peers = __match_any_sync(0xffffffffu, leaf);
-    int rank = __popc(peers & ((1u << lane) - 1u));
-    int32_t basepos = keep ? myh[leaf] : 0;
-    __syncwarp();
-    if (keep && rank == 0) myh[leaf] = basepos + __popc(peers);
-    __syncwarp();
-    if (keep) {
-      const int32_t dl = basepos + rank;
-      if (staged) {
-        map[dl] = (uint16_t)si;
-      } else {
-        const int32_t dst = bstart + dl;
-#pragma unroll
-        for (int ax = 0; ax < D; ++ax) {
-          a.o[ax * n + dst] = a.to[ax * n + tidx];
-          a.v[ax * n + dst] = a.tv[ax * n + tidx];
-        }
-        if (a.ids) a.ids[dst] = a.tids[tidx];
+  if (nin <= kStageCap) {
+    // slots (any order), then every leaf's slots sorted by raw position: the
+    // canonical order (stayers first, then movers in storage order)
+    each([&](int32_t r, int leaf) { map[atomicAdd(&cur[leaf], 1)] = (uint16_t)r; });
+    __syncthreads();
+    for (int l = tid; l < K::LB; l += blockDim.x) {
+      const int32_t lo = cnt[l], hi = cnt[l + 1];
+      for (int32_t i = lo + 1; i < hi; ++i) {
+        const uint16_t x = map[i];
+        int32_t j = i - 1;
+        while (j >= lo && map[j] > x) { map[j + 1] = map[j]; --j; }
+        map[j + 1] = x;
+      }
+      for (int32_t i = lo; i < hi; ++i) {  // raw position -> stage index
+        const int32_t r = map[i];
+        map[i] = (uint16_t)(r < pfx[1] ? self_stage + r : r - pfx[1]);
       }
     }
-  });
-  __syncthreads();
-  if (staged) {
+    __syncthreads();
     // one array at a time: coalesced reads of the incoming pieces into shared
     // memory, coalesced writes in destination order
     const int na = 2 * D + (a.ids ? 1 : 0);
@@ -533,6 +490,28 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       for (int32_t j = tid; j < nin; j += blockDim.x) dst[bstart + j] = stage[map[j]];
       __syncthreads();
     }
+  } else {
+    // large brick: one thread per leaf walks the raw positions in order
+    for (int l = tid; l < K::LB; l += blockDim.x) {
+      int32_t dl = cnt[l];
+      for (int k = 0; k < np; ++k) {
+        const Piece pc = pieces[k];
+        for (int32_t i = 0; i < pc.len; ++i) {
+          const int32_t tidx = pc.indirect ? a.far_tidx[pc.tstart + i] : pc.tstart + i;
+          const uint16_t code = a.tcode[tidx];
+          const bool stay = (code & kStayBit) != 0;
+          if (!(pc.round1 ? stay : !stay) || (code & 0x7fff) != l) continue;
+          const int32_t dst = bstart + dl++;
+#pragma unroll
+          for (int ax = 0; ax < D; ++ax) {
+            a.o[ax * n + dst] = a.to[ax * n + tidx];
+            a.v[ax * n + dst] = a.tv[ax * n + tidx];
+          }
+          if (a.ids) a.ids[dst] = a.tids[tidx];
+        }
+      }
+    }
+    __syncthreads();
   }
   // deposit partials of the new positions, per leaf in bucket order (the
   // arithmetic and order of the generic per-leaf deposit)
@@ -541,7 +520,7 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       float acc[K::NC];
 #pragma unroll
       for (int e = 0; e < K::NC; ++e) acc[e] = 0.0f;
-      for (int32_t p = bstart + lstart[l]; p < bstart + lstart[l + 1]; ++p) {
+      for (int32_t p = bstart + cnt[l]; p < bstart + cnt[l + 1]; ++p) {
         float o[D], om[D];
 #pragma unroll
         for (int ax = 0; ax < D; ++ax) {
