@@ -63,21 +63,18 @@ __device__ __forceinline__ int32_t brick_of_coords(const DevTree &t, const int32
 // ---------------------------------------------------------------------------
 
 // Gather + kick + drift + re-location of one particle -- the arithmetic of
-// the generic split push, field values from the staged brick field.  Returns
-// the destination direction slot.
+// the generic split push, field values from the staged brick field.  o and v
+// are the particle's offset and velocity; returns the destination direction
+// slot and writes the new offset, velocity and leaf.
 template <int D>
-__device__ __forceinline__ int brick_push_one(const DevTree &t, const BrickGeom &g, const BrickPushArgs &a,
-                                              int32_t p, const int32_t *lc, const int32_t *origin,
-                                              const int32_t *bc, const float *Eb, float *on, float *vn,
-                                              int32_t &L2, bool &bad) {
+__device__ __forceinline__ int push_core(const DevTree &t, const BrickGeom &g, const BrickPushArgs &a,
+                                         const float *o, const float *vin, const int32_t *lc,
+                                         const int32_t *origin, const int32_t *bc, const float *Eb, float *on,
+                                         float *vn, int32_t &L2, bool &bad) {
   using K = BK<D>;
-  const int64_t n = a.n;
-  float o[D], om[D];
+  float om[D];
 #pragma unroll
-  for (int ax = 0; ax < D; ++ax) {
-    o[ax] = a.o[ax * n + p];
-    om[ax] = 1.0f - o[ax];
-  }
+  for (int ax = 0; ax < D; ++ax) om[ax] = 1.0f - o[ax];
   float E[D];
 #pragma unroll
   for (int ax = 0; ax < D; ++ax) E[ax] = 0.0f;
@@ -97,7 +94,7 @@ __device__ __forceinline__ int brick_push_one(const DevTree &t, const BrickGeom 
   bool far = false;
 #pragma unroll
   for (int ax = 0; ax < D; ++ax) {
-    float v = a.v[ax * n + p] + a.qmdt * E[ax];
+    float v = vin[ax] + a.qmdt * E[ax];
     float tt = o[ax] + v * a.sl;
     if (!isfinite(v) || !isfinite(tt)) { bad = true; tt = 0.0f; }
     float fl = floorf(tt);
@@ -129,6 +126,196 @@ __device__ __forceinline__ int brick_push_one(const DevTree &t, const BrickGeom 
 }
 
 template <int D>
+__device__ __forceinline__ int brick_push_one(const DevTree &t, const BrickGeom &g, const BrickPushArgs &a,
+                                              int32_t p, const int32_t *lc, const int32_t *origin,
+                                              const int32_t *bc, const float *Eb, float *on, float *vn,
+                                              int32_t &L2, bool &bad) {
+  const int64_t n = a.n;
+  float o[D], v[D];
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) {
+    o[ax] = a.o[ax * n + p];
+    v[ax] = a.v[ax * n + p];
+  }
+  return push_core<D>(t, g, a, o, v, lc, origin, bc, Eb, on, vn, L2, bad);
+}
+
+// Stage the brick's vertex field: (B+1)^D vertices, periodic.
+template <int D>
+__device__ __forceinline__ void stage_field(const DevTree &t, const BrickPushArgs &a, const int32_t *origin,
+                                            float *Eb) {
+  using K = BK<D>;
+  for (int i = threadIdx.x; i < K::NVB; i += blockDim.x) {
+    int lx = i % K::V1, ly = (i / K::V1) % K::V1, lz = D == 3 ? i / (K::V1 * K::V1) : 0;
+    int32_t gx = origin[0] + lx, gy = origin[1] + ly, gz = D == 3 ? origin[2] + lz : 0;
+    if (gx >= t.M) gx -= t.M;
+    if (gy >= t.M) gy -= t.M;
+    if (gz >= t.M) gz -= t.M;
+    int64_t vid = gx + (int64_t)t.M * (gy + (int64_t)t.M * gz);
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) Eb[ax * K::NVB + i] = a.E[ax * t.n_vert + vid];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K1, shared-memory form: the brick's particles are loaded once, pushed once
+// and kept on chip until their partitioned positions are known.
+// ---------------------------------------------------------------------------
+
+constexpr int kStThreads = 1024;
+constexpr int kStCap = 7168;         // particles per brick held in shared memory
+
+template <int D>
+size_t push_st_smem() {
+  using K = BK<D>;
+  return sizeof(float) * 2 * D * kStCap + sizeof(uint16_t) * 2 * kStCap + sizeof(float) * D * K::NVB +
+         sizeof(int32_t) * (K::LB + 1) + sizeof(uint32_t) * K::LB + sizeof(int32_t) * (32 + 8 + 2) * kSlots;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, BrickGeom g, BrickPushArgs a) {
+  using K = BK<D>;
+  extern __shared__ float smf[];
+  float *so = smf;                                   // D * kStCap offsets
+  float *sv = so + D * kStCap;                       // D * kStCap velocities
+  uint16_t *code = (uint16_t *)(sv + D * kStCap);    // new local leaf | dir << 10 | stay << 15
+  uint16_t *pos = code + kStCap;                     // local leaf, then rank in (chunk, dir)
+  float *Eb = (float *)(pos + kStCap);               // D * NVB staged field
+  int32_t *ls = (int32_t *)(Eb + D * K::NVB);        // LB + 1
+  uint32_t *dec = (uint32_t *)(ls + K::LB + 1);      // LB
+  int32_t *wcnt = (int32_t *)(dec + K::LB);          // 32 * kSlots
+  int32_t *ctot = wcnt + 32 * kSlots;                // 8 * kSlots chunk totals, then offsets
+  int32_t *seg = ctot + 8 * kSlots;                  // kSlots
+  int32_t *dtot = seg + kSlots;                      // kSlots
+  __shared__ int32_t s_movers;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int32_t b = blockIdx.x, L0 = b * K::LB;
+  const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nb = pe - ps;
+  if (nb > kStCap) return;  // the recompute kernel takes this brick
+  const int64_t n = a.n;
+  int32_t origin[3] = {0, 0, 0}, bc[3] = {0, 0, 0};
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) {
+    origin[ax] = t.leaf_coords[(int64_t)L0 * D + ax];
+    bc[ax] = origin[ax] / K::B;
+  }
+  for (int i = tid; i <= K::LB; i += blockDim.x) ls[i] = a.start[L0 + i] - ps;
+  for (int i = tid; i < K::LB; i += blockDim.x) dec[i] = g.decodeL[i];
+  stage_field<D>(t, a, origin, Eb);
+  for (int32_t q = tid; q < nb; q += blockDim.x) {
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+      so[ax * kStCap + q] = a.o[ax * n + ps + q];
+      sv[ax * kStCap + q] = a.v[ax * n + ps + q];
+    }
+  }
+  if (tid == 0) s_movers = 0;
+  __syncthreads();
+  for (int l = tid; l < K::LB; l += blockDim.x)
+    for (int32_t q = ls[l]; q < ls[l + 1]; ++q) pos[q] = (uint16_t)l;
+  __syncthreads();
+
+  // push every particle once; ranks within (chunk of 1024, direction)
+  bool bad = false;
+  const int nchunk = (nb + kStThreads - 1) / kStThreads;
+  for (int c = 0; c < nchunk; ++c) {
+    const int32_t q = c * kStThreads + tid;
+    const bool act = q < nb;
+    if (lane < kSlots) wcnt[w * kSlots + lane] = 0;
+    __syncwarp();
+    int dir = 255;
+    if (act) {
+      const int l = pos[q];
+      const uint32_t pk = dec[l];
+      const int32_t lc[3] = {(int32_t)(pk & 1023u), (int32_t)((pk >> 10) & 1023u), (int32_t)(pk >> 20)};
+      float o[D], v[D], on[D], vn[D];
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        o[ax] = so[ax * kStCap + q];
+        v[ax] = sv[ax * kStCap + q];
+      }
+      int32_t L2;
+      dir = push_core<D>(t, g, a, o, v, lc, origin, bc, Eb, on, vn, L2, bad);
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        so[ax * kStCap + q] = on[ax];
+        sv[ax * kStCap + q] = vn[ax];
+      }
+      const bool stay = L2 == L0 + l;
+      code[q] = (uint16_t)((L2 % K::LB) | (dir << 10) | (stay ? kStayBit : 0));
+      if (dir == kFarSlot) a.far_scratch[ps + q] = L2 / K::LB;  // destination brick
+    }
+    unsigned peers = __match_any_sync(0xffffffffu, dir);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    if (act && rank == 0) wcnt[w * kSlots + dir] = __popc(peers);
+    __syncthreads();
+    if (tid < kSlots) {
+      int32_t sum = 0;
+      for (int k = 0; k < 32; ++k) {
+        const int32_t cv = wcnt[k * kSlots + tid];
+        wcnt[k * kSlots + tid] = sum;
+        sum += cv;
+      }
+      ctot[c * kSlots + tid] = sum;
+    }
+    __syncthreads();
+    if (act) pos[q] = (uint16_t)(wcnt[w * kSlots + dir] + rank);
+    __syncthreads();
+  }
+  // direction segments and chunk offsets
+  if (tid < kSlots) {
+    int32_t run = 0;
+    for (int c = 0; c < nchunk; ++c) {
+      const int32_t cv = ctot[c * kSlots + tid];
+      ctot[c * kSlots + tid] = run;
+      run += cv;
+    }
+    dtot[tid] = run;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int32_t sum = 0;
+    for (int k = 0; k < kSlots; ++k) {
+      seg[k] = sum;
+      a.cnt[(int64_t)b * kSlots + k] = dtot[k];
+      a.segoff[(int64_t)b * kSlots + k] = sum;
+      sum += dtot[k];
+    }
+  }
+  __syncthreads();
+  // partitioned writes
+  int movers = 0;
+  for (int32_t q = tid; q < nb; q += blockDim.x) {
+    const uint16_t cd = code[q];
+    const int dir = (cd >> 10) & 31;
+    const int32_t p = ps + seg[dir] + ctot[(q / kStThreads) * kSlots + dir] + pos[q];
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+      a.to[ax * n + p] = so[ax * kStCap + q];
+      a.tv[ax * n + p] = sv[ax * kStCap + q];
+    }
+    a.tcode[p] = (uint16_t)(cd & (kStayBit | 0x3ffu));
+    if (a.ids) a.tids[p] = a.ids[ps + q];
+    movers += !(cd & kStayBit);
+    if (dir == kFarSlot) {
+      int32_t k = atomicAdd(a.far_n, 1);
+      if (k < a.far_cap) {
+        a.far_tidx[k] = p;
+        a.far_src[k] = b;
+        a.far_dest[k] = a.far_scratch[ps + q];
+      } else {
+        atomicOr(a.err, 4);
+      }
+    }
+  }
+  if (bad) atomicOr(a.err, 1);
+  for (int o = 16; o > 0; o >>= 1) movers += __shfl_down_sync(0xffffffffu, movers, o);
+  if (lane == 0) atomicAdd(&s_movers, movers);
+  __syncthreads();
+  if (tid == 0 && s_movers) atomicAdd(a.n_movers, s_movers);
+}
+
+template <int D>
 __global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeom g, BrickPushArgs a) {
   using K = BK<D>;
   __shared__ int32_t ls[K::LB + 1];
@@ -147,6 +334,7 @@ __global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeo
     bc[ax] = origin[ax] / K::B;
   }
   const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nb = pe - ps;
+  if (nb <= kStCap) return;  // the shared-memory kernel took this brick
   for (int i = tid; i <= K::LB; i += blockDim.x) ls[i] = a.start[L0 + i] - ps;
   for (int i = tid; i < K::LB; i += blockDim.x) dec[i] = g.decodeL[i];
   for (int i = tid; i < K::NVB; i += blockDim.x) {
@@ -348,6 +536,7 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
   const int32_t b = blockIdx.x, L0 = b * K::LB;
   const int64_t n = a.n;
+  if (a.tot[b] <= kStCap) return;  // the shared-memory kernel took this brick
 
   // neighbour segments, one thread per direction, placed by source-brick rank
   __shared__ int32_t s_src[27];
@@ -541,6 +730,222 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
   }
 }
 
+// ---------------------------------------------------------------------------
+// K2, shared-memory form: every arrival is loaded once (coalesced), counted,
+// ordered, written in destination order and deposited from shared memory.
+// ---------------------------------------------------------------------------
+
+template <int D>
+size_t pull_st_smem() {
+  return sizeof(float) * 2 * D * kStCap + sizeof(uint16_t) * 2 * kStCap;
+}
+
+// Canonical position order inside the brick's incoming pieces: round-1 (the
+// stayers of the self segment) before round-2 (everything else in source
+// order); stage index = position among round-2 pieces.
+template <int D>
+__device__ __forceinline__ void build_pieces(const DevTree &t, const BrickGeom &g, const BrickPullArgs &a,
+                                             int32_t b, Piece *pieces, Piece *sdesc, int32_t *s_src,
+                                             int32_t *pfx, int32_t *spfx, int32_t *s_np, int32_t *s_self) {
+  using K = BK<D>;
+  const int tid = threadIdx.x;
+  const int32_t L0 = b * K::LB;
+  Piece mine{0, 0, INT32_MAX, 0, 0};
+  if (tid < 27) {
+    const int dir = tid;
+    if (!(D == 2 && dir_delta(dir, 2) != 0)) {
+      int32_t sc[3] = {0, 0, 0};
+      for (int ax = 0; ax < D; ++ax) {
+        int32_t x = t.leaf_coords[(int64_t)L0 * D + ax] / 9 - dir_delta(dir, ax);
+        sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
+      }
+      const int32_t src = brick_of_coords<D>(t, sc);
+      const int64_t k = (int64_t)src * kSlots + dir;
+      mine = Piece{a.old_start[src * K::LB] + a.segoff[k], a.cnt[k], src, 0, 0};
+    }
+    s_src[dir] = mine.src;
+  }
+  __syncthreads();
+  if (tid < 27 && mine.src != INT32_MAX) {
+    int rank = 0;
+    for (int k = 0; k < 27; ++k) rank += s_src[k] < mine.src;
+    sdesc[rank] = mine;
+    if (tid == kSelfDir) pieces[0] = Piece{mine.tstart, mine.len, mine.src, 1, 0};
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int ns = D == 3 ? 27 : 9;
+    int np = 1;
+    int32_t fi = a.fstart[b];
+    const int32_t fe = a.fstart[b + 1];
+    for (int k = 0; k < ns; ++k) {
+      if (fi < fe) {
+        int32_t f0 = fi;
+        while (fi < fe && a.far_src[fi] < sdesc[k].src) ++fi;
+        if (fi > f0) pieces[np++] = Piece{f0, fi - f0, -1, 0, 1};
+      }
+      if (sdesc[k].src == b) *s_self = np;
+      pieces[np++] = sdesc[k];
+    }
+    if (fi < fe) pieces[np++] = Piece{fi, fe - fi, -1, 0, 1};
+    int32_t sum = 0;
+    for (int k = 0; k < np; ++k) {
+      pfx[k] = sum;
+      spfx[k] = k == 0 ? 0 : sum - pieces[0].len;
+      sum += pieces[k].len;
+    }
+    pfx[np] = sum;
+    spfx[np] = sum - pieces[0].len;
+    *s_np = np;
+  }
+  __syncthreads();
+}
+
+template <int D>
+__global__ void __launch_bounds__(kStThreads, 1) k_brick_pull_st(DevTree t, BrickGeom g, BrickPullArgs a) {
+  using K = BK<D>;
+  extern __shared__ float smf[];
+  float *so = smf;                                   // D * kStCap
+  float *sv = so + D * kStCap;                       // D * kStCap
+  uint16_t *code = (uint16_t *)(sv + D * kStCap);    // kStCap tcode of every arrival (stage order)
+  uint16_t *map = code + kStCap;                     // kStCap slot -> key -> stage index
+  __shared__ int32_t cnt[K::LB + 1];
+  __shared__ int32_t cur[K::LB];
+  __shared__ Piece pieces[kMaxPieces];
+  __shared__ Piece sdesc[27];
+  __shared__ int32_t s_src[27];
+  __shared__ int32_t pfx[kMaxPieces + 1], spfx[kMaxPieces + 1];
+  __shared__ int32_t wsum[32];
+  __shared__ int32_t s_np, s_self, s_max;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+  const int32_t b = blockIdx.x, L0 = b * K::LB;
+  const int64_t n = a.n;
+  if (a.tot[b] > kStCap) return;  // the global-memory kernel takes this brick
+  if (tid == 0) s_max = 0;
+  for (int i = tid; i < K::LB + 1; i += blockDim.x) cnt[i] = 0;
+  build_pieces<D>(t, g, a, b, pieces, sdesc, s_src, pfx, spfx, &s_np, &s_self);
+  const int np = s_np;
+  const int32_t len0 = pieces[0].len, self_stage = spfx[s_self];
+  const int32_t nin = spfx[np];
+  // load every arrival once (round-2 pieces cover each exactly once)
+  for (int k = 1; k < np; ++k) {
+    const Piece pc = pieces[k];
+    const int32_t so0 = spfx[k];
+    for (int32_t i = tid; i < pc.len; i += blockDim.x) {
+      const int32_t tidx = pc.indirect ? a.far_tidx[pc.tstart + i] : pc.tstart + i;
+      const int32_t si = so0 + i;
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        so[ax * kStCap + si] = a.to[ax * n + tidx];
+        sv[ax * kStCap + si] = a.tv[ax * n + tidx];
+      }
+      const uint16_t cd = a.tcode[tidx];
+      code[si] = cd;
+      atomicAdd(&cnt[cd & 0x3ff], 1);
+    }
+  }
+  __syncthreads();
+  // exclusive scan of the leaf counts, cursors
+  int32_t carry = 0;
+  for (int base = 0; base < K::LB; base += blockDim.x) {
+    const int l = base + tid;
+    const int32_t c = l < K::LB ? cnt[l] : 0;
+    int32_t x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int32_t before = 0, all = 0;
+    for (int k = 0; k < nw; ++k) {
+      if (k < w) before += wsum[k];
+      all += wsum[k];
+    }
+    if (l < K::LB) {
+      cnt[l] = carry + before + x - c;
+      cur[l] = cnt[l];
+      if (c > 0) atomicMax(&s_max, c);
+    }
+    carry += all;
+    __syncthreads();
+  }
+  if (tid == 0) cnt[K::LB] = carry;
+  __syncthreads();
+  // slots in any order, keyed by canonical position
+  for (int32_t si = tid; si < nin; si += blockDim.x) {
+    const uint16_t cd = code[si];
+    const bool stay = (cd & kStayBit) != 0;
+    const int32_t key = stay ? si - self_stage : len0 + si;
+    map[atomicAdd(&cur[cd & 0x3ff], 1)] = (uint16_t)key;
+  }
+  __syncthreads();
+  const int32_t bstart = a.bstart[b];
+  for (int l = tid; l < K::LB; l += blockDim.x) {
+    a.new_start[L0 + l] = bstart + cnt[l];
+    const int32_t lo = cnt[l], hi = cnt[l + 1];
+    for (int32_t i = lo + 1; i < hi; ++i) {
+      const uint16_t x = map[i];
+      int32_t j = i - 1;
+      while (j >= lo && map[j] > x) { map[j + 1] = map[j]; --j; }
+      map[j + 1] = x;
+    }
+    for (int32_t i = lo; i < hi; ++i) {
+      const int32_t key = map[i];
+      map[i] = (uint16_t)(key < len0 ? self_stage + key : key - len0);
+    }
+  }
+  if (b == g.n_bricks - 1 && tid == 0) a.new_start[(int64_t)g.n_bricks * K::LB] = bstart + nin;
+  if (tid == 0 && s_max > 0) atomicMax(a.max_bucket, s_max);
+  __syncthreads();
+  // coalesced writes in destination order
+  for (int32_t j = tid; j < nin; j += blockDim.x) {
+    const int32_t si = map[j], dst = bstart + j;
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+      a.o[ax * n + dst] = so[ax * kStCap + si];
+      a.v[ax * n + dst] = sv[ax * kStCap + si];
+    }
+  }
+  if (a.ids) {
+    // ids: the source of stage index si is found in the round-2 pieces
+    for (int32_t j = tid; j < nin; j += blockDim.x) {
+      const int32_t si = map[j];
+      int k = 1;
+      while (k + 1 < np && spfx[k + 1] <= si) ++k;
+      const Piece pc = pieces[k];
+      const int32_t off = si - spfx[k];
+      a.ids[bstart + j] = a.tids[pc.indirect ? a.far_tidx[pc.tstart + off] : pc.tstart + off];
+    }
+  }
+  // deposit partials of the new positions, per leaf in bucket order
+  if (a.part) {
+    for (int l = tid; l < K::LB; l += blockDim.x) {
+      float acc[K::NC];
+#pragma unroll
+      for (int e = 0; e < K::NC; ++e) acc[e] = 0.0f;
+      for (int32_t j = cnt[l]; j < cnt[l + 1]; ++j) {
+        const int32_t si = map[j];
+        float o[D], om[D];
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+          o[ax] = so[ax * kStCap + si];
+          om[ax] = 1.0f - o[ax];
+        }
+#pragma unroll
+        for (int e = 0; e < K::NC; ++e) {
+          float wgt = 1.0f;
+#pragma unroll
+          for (int ax = 0; ax < D; ++ax) wgt = wgt * (((e >> ax) & 1) ? o[ax] : om[ax]);
+          acc[e] = acc[e] + wgt;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < K::NC; ++e) a.part[(int64_t)(L0 + l) * K::NC + e] = acc[e];
+    }
+  }
+}
+
 // Leaf id of every particle from the bucket offsets (thread per leaf).
 __global__ void k_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf) {
   int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -554,18 +959,22 @@ __global__ void k_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t 
 
 void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs &pa, cudaStream_t s) {
   cudaMemsetAsync(pa.far_n, 0, sizeof(int32_t), s);
-  if (g.d == 3)
-    k_brick_push<3><<<(unsigned)g.n_bricks, kPushThreads, 0, s>>>(t, g, pa);
-  else
-    k_brick_push<2><<<(unsigned)g.n_bricks, kPushThreads, 0, s>>>(t, g, pa);
-  count_launches(1);
+  const unsigned nb = (unsigned)g.n_bricks;
+  if (g.d == 3) {
+    k_brick_push_st<3><<<nb, kStThreads, push_st_smem<3>(), s>>>(t, g, pa);
+    k_brick_push<3><<<nb, kPushThreads, 0, s>>>(t, g, pa);
+  } else {
+    k_brick_push_st<2><<<nb, kStThreads, push_st_smem<2>(), s>>>(t, g, pa);
+    k_brick_push<2><<<nb, kPushThreads, 0, s>>>(t, g, pa);
+  }
+  count_launches(2);
 }
 
 void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPushArgs &pa, const BrickPullArgs &qa,
                        int32_t *fcount, int32_t *fcursor, int32_t *tile_sums, int32_t *scratch_total,
                        cudaStream_t s) {
   const unsigned nb = (unsigned)g.n_bricks;
-  const size_t inv_bytes = (sizeof(float) + sizeof(uint16_t)) * kStageCap;
+  const size_t stage_bytes = (sizeof(float) + sizeof(uint16_t)) * kStageCap;
   cudaMemsetAsync(fcount, 0, sizeof(int32_t) * g.n_bricks, s);
   cudaMemsetAsync(fcursor, 0, sizeof(int32_t) * g.n_bricks, s);
   k_far_count<<<64, 256, 0, s>>>(pa.far_n, pa.far_cap, pa.far_dest, fcount);
@@ -579,11 +988,14 @@ void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPushArgs
     k_brick_totals<2><<<(nb + 255) / 256, 256, 0, s>>>(t, g, pa.cnt, qa.fstart, qa.far_tidx_w, qa.far_src_w,
                                                        qa.tot_w);
   launch_exclusive_scan(qa.tot_w, g.n_bricks, qa.bstart_w, tile_sums, scratch_total, s);
-  if (g.d == 3)
-    k_brick_pull<3><<<nb, kPullThreads, inv_bytes, s>>>(t, g, qa);
-  else
-    k_brick_pull<2><<<nb, kPullThreads, inv_bytes, s>>>(t, g, qa);
-  count_launches(4);  // far count, far scatter, totals, pull (the scans count themselves)
+  if (g.d == 3) {
+    k_brick_pull_st<3><<<nb, kStThreads, pull_st_smem<3>(), s>>>(t, g, qa);
+    k_brick_pull<3><<<nb, kPullThreads, stage_bytes, s>>>(t, g, qa);
+  } else {
+    k_brick_pull_st<2><<<nb, kStThreads, pull_st_smem<2>(), s>>>(t, g, qa);
+    k_brick_pull<2><<<nb, kPullThreads, stage_bytes, s>>>(t, g, qa);
+  }
+  count_launches(5);  // far count, far scatter, totals, two pull kernels (the scans count themselves)
 }
 
 void launch_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf, cudaStream_t s) {
@@ -593,8 +1005,20 @@ void launch_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf,
 
 cudaError_t brick_configure(const BrickGeom &g) {
   const int bytes = (int)((sizeof(float) + sizeof(uint16_t)) * kStageCap);
-  cudaError_t e = g.d == 3 ? cudaFuncSetAttribute(k_brick_pull<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
-                           : cudaFuncSetAttribute(k_brick_pull<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaError_t e;
+  if (g.d == 3) {
+    e = cudaFuncSetAttribute(k_brick_pull<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_brick_push_st<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)push_st_smem<3>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_brick_pull_st<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pull_st_smem<3>());
+  } else {
+    e = cudaFuncSetAttribute(k_brick_pull<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_brick_push_st<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)push_st_smem<2>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_brick_pull_st<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pull_st_smem<2>());
+  }
   return e;
 }
 

@@ -76,6 +76,7 @@ struct BrickPushArgs {
   int32_t *far_n;
   int32_t far_cap;
   int32_t *far_tidx, *far_src, *far_dest;
+  int32_t *far_scratch;          // n entries: destination brick of a far mover by storage index
   int32_t *n_movers;
   int32_t *err;
 };
@@ -88,6 +89,7 @@ struct BrickPullArgs {
   const int32_t *far_tidx, *far_src;  // far arrivals sorted per destination brick
   int32_t *far_tidx_w, *far_src_w;
   int32_t *tot_w;
+  const int32_t *tot;            // incoming particles per destination brick
   const int32_t *bstart;
   int32_t *bstart_w;
   const uint16_t *tcode;

@@ -411,6 +411,7 @@ int brick_push_and_rebin(pic_t h, double dt) {
   pa.far_tidx = h->far_tidx;
   pa.far_src = h->far_src;
   pa.far_dest = h->far_dest;
+  pa.far_scratch = h->far_ssrc;  // free until the far list is sorted
   pa.n_movers = h->scalars + 1;
   pa.err = h->err;
   BrickPullArgs qa{};
@@ -425,6 +426,7 @@ int brick_push_and_rebin(pic_t h, double dt) {
   qa.far_tidx_w = h->far_stidx;
   qa.far_src_w = h->far_ssrc;
   qa.tot_w = h->btot;
+  qa.tot = h->btot;
   qa.bstart = h->bstart;
   qa.bstart_w = h->bstart;
   qa.tcode = h->tcode;
