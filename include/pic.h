@@ -204,12 +204,21 @@ PIC_API int pic_leaf_table(pic_t h, int32_t *level, int64_t *coords);
 PIC_API int pic_vertex_table(pic_t h, int64_t *pos);
 PIC_API int pic_pidt_table(pic_t h, int32_t *level, int64_t *j);
 
-/* Replace the tree (same d) and re-bin the particles into it. */
+/* Replace the tree (same d) and re-bin the particles into it.  FP64
+ * particles keep their positions; split particles are re-located with the
+ * integer lift/drop rule of the split push (zero displacement).  The solver's
+ * warm start and the field are reset.  Synchronous. */
 PIC_API int pic_retree(pic_t h, const pic_tree_desc *tree);
+
+/* Level-order refinement flags of the current tree: with flags == NULL only
+ * *n_nodes is written; else flags[n_nodes] (host memory). */
+PIC_API int pic_tree_flags(pic_t h, uint8_t *flags, int64_t *n_nodes);
 
 /* Re-refine by the particles-per-cell criterion: cell C on level m is refined
  * iff m < dmin, or m < dmax and C holds more than ppc particles (Section 6
- * setup: refine on overrun, coarsen when the union stays within ppc). */
+ * setup: refine on overrun, coarsen when the union stays within ppc).  Counts
+ * per level are taken on the device; dmax <= 6 in 3D, <= 10 in 2D.  Split
+ * positions below their leaf are resolved with the drop rule.  Synchronous. */
 PIC_API int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax);
 
 #ifdef __cplusplus

@@ -746,6 +746,90 @@ __global__ void k_gather_only32(DevTree t, const float *o, const int32_t *leaf, 
 }
 
 // ---------------------------------------------------------------------------
+// a9 re-refinement: depth-first cell index on the finest admissible level
+// ---------------------------------------------------------------------------
+
+// FP64: cell of the quantised position on level dmax.
+__global__ void k_fine_key64(DevTree t, const double *x, int64_t n, int dmax, uint32_t *key) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  uint32_t step = 2u * c_pow3[18 - dmax];
+  uint32_t c[3] = {0u, 0u, 0u};
+  for (int a = 0; a < t.d; ++a) c[a] = quantise(x[a * n + p]) / step;
+  key[p] = (uint32_t)local_index(c[0], c[1], c[2], t.d, dmax);
+}
+
+// Split: cell of leaf + offset on level dmax; below the leaf the offset
+// digits follow the drop rule of the split re-location.
+__global__ void k_fine_key32(DevTree t, const int32_t *leaf, const float *o, int64_t n, int dmax, uint32_t *key) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int32_t L = leaf[p];
+  const int lev = t.leaf_level[L];
+  uint32_t c[3] = {0u, 0u, 0u};
+  for (int a = 0; a < t.d; ++a) {
+    uint32_t I = (uint32_t)t.leaf_coords[(int64_t)L * t.d + a];
+    if (lev >= dmax) {
+      I /= c_pow3[lev - dmax];
+    } else {
+      float f = o[a * n + p];
+      for (int m = lev; m < dmax; ++m) {
+        float u = 3.0f * f;
+        int dg = (int)floorf(u);
+        dg = dg > 2 ? 2 : dg;
+        f = clamp_off(u - (float)dg);
+        I = 3u * I + (uint32_t)dg;
+      }
+    }
+    c[a] = I;
+  }
+  key[p] = (uint32_t)local_index(c[0], c[1], c[2], t.d, dmax);
+}
+
+// Particles per cell on one level (warp-aggregated).
+__global__ void k_level_count(const uint32_t *key, int64_t n, uint32_t div, int32_t *count) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = p < n;
+  const uint32_t c = act ? key[p] / div : 0xffffffffu;
+  const unsigned peers = __match_any_sync(0xffffffffu, c);
+  if (act && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&count[c], __popc(peers));
+}
+
+__global__ void k_threshold_bits(const int32_t *count, int64_t ncells, int64_t ppc, uint32_t *bits) {
+  int64_t wd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (wd * 32 >= ncells) return;
+  uint32_t b = 0;
+  for (int i = 0; i < 32; ++i) {
+    int64_t c = wd * 32 + i;
+    if (c < ncells && count[c] > ppc) b |= 1u << i;
+  }
+  bits[wd] = b;
+}
+
+// Split particles of tree `from` re-located in tree `to` (same positions):
+// the resolver of the split push with zero displacement.
+__global__ void k_relocate32(DevTree from, DevTree to, const int32_t *leaf, const float *o, const float *v,
+                             int64_t n, int32_t *leaf2, float *o2, float *v2) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int32_t L = leaf[p];
+  const int lev = from.leaf_level[L];
+  int32_t I[3] = {0, 0, 0};
+  float f[3] = {0.f, 0.f, 0.f};
+  for (int a = 0; a < from.d; ++a) {
+    I[a] = from.leaf_coords[(int64_t)L * from.d + a];
+    f[a] = o[a * n + p];
+  }
+  float on[3] = {0.f, 0.f, 0.f};
+  int lev2;
+  leaf2[p] = descend_split(to.tab, to.d, lev, I, f, on, &lev2);
+  for (int a = 0; a < from.d; ++a) {
+    o2[a * n + p] = on[a];
+    v2[a * n + p] = v[a * n + p];
+  }
+}
+
+// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 
@@ -799,6 +883,31 @@ void launch_rekey32(const DevTree &t, const int32_t *leaf, const float *o, int64
 void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *mover_words,
                       int32_t *block_movers, cudaStream_t s) {
   { COUNT(1); k_count_all<<<grid_for(n), kBlock, 0, s>>>(key, n, count, mover_words, block_movers); }
+}
+
+void launch_fine_keys(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n, int dmax,
+                      uint32_t *key, cudaStream_t s) {
+  if (n <= 0) return;
+  COUNT(1);
+  if (split)
+    k_fine_key32<<<grid_for(n), kBlock, 0, s>>>(t, leaf, (const float *)pos, n, dmax, key);
+  else
+    k_fine_key64<<<grid_for(n), kBlock, 0, s>>>(t, (const double *)pos, n, dmax, key);
+}
+
+void launch_level_bits(const uint32_t *key, int64_t n, uint32_t div, int32_t *count, int64_t ncells, int64_t ppc,
+                       uint32_t *bits, cudaStream_t s) {
+  cudaMemsetAsync(count, 0, sizeof(int32_t) * ncells, s);
+  if (n > 0) { COUNT(1); k_level_count<<<grid_for(n), kBlock, 0, s>>>(key, n, div, count); }
+  COUNT(1);
+  k_threshold_bits<<<grid_for((ncells + 31) / 32), kBlock, 0, s>>>(count, ncells, ppc, bits);
+}
+
+void launch_relocate32(const DevTree &from, const DevTree &to, const int32_t *leaf, const float *o, const float *v,
+                       int64_t n, int32_t *leaf2, float *o2, float *v2, cudaStream_t s) {
+  if (n <= 0) return;
+  COUNT(1);
+  k_relocate32<<<grid_for(n), kBlock, 0, s>>>(from, to, leaf, o, v, n, leaf2, o2, v2);
 }
 
 void launch_vertex_charge(const DevTree &t, bool split, const void *part, double q, double ion, void *Q,

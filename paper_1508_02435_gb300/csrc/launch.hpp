@@ -122,6 +122,15 @@ void launch_rekey32(const DevTree &t, const int32_t *leaf, const float *o, int64
                     cudaStream_t s);
 void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *mover_words,
                       int32_t *block_movers, cudaStream_t s);
+// Re-refinement: depth-first cell index on level dmax per particle; cells of
+// level m (index key / div) holding more than ppc particles as a bitmap.
+void launch_fine_keys(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n, int dmax,
+                      uint32_t *key, cudaStream_t s);
+void launch_level_bits(const uint32_t *key, int64_t n, uint32_t div, int32_t *count, int64_t ncells, int64_t ppc,
+                       uint32_t *bits, cudaStream_t s);
+void launch_relocate32(const DevTree &from, const DevTree &to, const int32_t *leaf, const float *o, const float *v,
+                       int64_t n, int32_t *leaf2, float *o2, float *v2, cudaStream_t s);
+
 // Vertex charges and FP64 total from leaf-corner partials already computed.
 void launch_vertex_charge(const DevTree &t, bool split, const void *part, double q, double ion, void *Q,
                           double *block_sum, double *total, cudaStream_t s);

@@ -132,8 +132,10 @@ int upload(pic_t h, std::vector<DevBuf> &bufs, const T **out, const std::vector<
 
 int64_t n_keys_of(const HostTree &t, int scheme) { return scheme == PIC_PIT ? t.n_leaves : t.n_pv * t.nc; }
 
-// Tabulate the tree on the host and upload the device view.
-int install_tree(pic_t h, const pic_tree_desc *tree) {
+// Tabulate the tree on the host and upload the device view.  The previous
+// tree's device buffers are handed back in *old (freed by the caller) so that
+// particles can still be re-located from it.
+int install_tree(pic_t h, const pic_tree_desc *tree, std::vector<DevBuf> *old = nullptr) {
   std::string err;
   HostTree ht;
   if (!tree || !tree->flags) return fail(h, PIC_EINVAL, "tree descriptor is NULL");
@@ -148,7 +150,8 @@ int install_tree(pic_t h, const pic_tree_desc *tree) {
   ht.build_grid();
   ht.build_pidt();
   if (n_keys_of(ht, h->scheme) >= INT32_MAX) return fail(h, PIC_EINVAL, "more than 2^31 sort keys");
-  free_bufs(h, h->tree_bufs);
+  std::vector<DevBuf> prev;
+  prev.swap(h->tree_bufs);
   DevTree dt{};
   dt.d = ht.d;
   dt.nch = ht.nch;
@@ -209,6 +212,10 @@ int install_tree(pic_t h, const pic_tree_desc *tree) {
   h->d = ht.d;
   h->ht = std::move(ht);
   h->dt = dt;
+  if (old)
+    old->swap(prev);
+  else
+    free_bufs(h, prev);
   return PIC_OK;
 }
 
@@ -988,13 +995,136 @@ int pic_pidt_table(pic_t h, int32_t *level, int64_t *j) {
 }
 
 int pic_retree(pic_t h, const pic_tree_desc *tree) {
-  (void)tree;
-  return fail(h, PIC_ESTATE, "pic_retree is not implemented yet");
+  if (check_handle(h) || !tree) return PIC_EINVAL;
+  if (tree->d != h->d) return fail(h, PIC_EINVAL, "tree dimension differs from the handle");
+  int rc;
+  if ((rc = ensure_leaf(h))) return rc;
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n;
+  const int d = h->d;
+  const size_t fs = h->split ? sizeof(float) : sizeof(double);
+  // keep the particles (storage order) while the buffers are rebuilt
+  std::vector<DevBuf> keep;
+  char *tpos, *tvel;
+  int32_t *tleaf, *tids;
+  if ((rc = dalloc(h, keep, &tpos, fs * d * n)) || (rc = dalloc(h, keep, &tvel, fs * d * n)) ||
+      (rc = dalloc(h, keep, &tleaf, n)) || (rc = dalloc(h, keep, &tids, n))) {
+    free_bufs(h, keep);
+    return rc;
+  }
+  CK(cudaMemcpyAsync(tpos, h->pos[0], fs * d * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(tvel, h->vel[0], fs * d * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(tleaf, h->leaf[0], sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(tids, h->ids[0], sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  const DevTree old_dt = h->dt;
+  std::vector<DevBuf> old_tree;
+  if ((rc = install_tree(h, tree, &old_tree))) {
+    free_bufs(h, keep);
+    return rc;
+  }
+  if ((rc = alloc_state(h))) {
+    free_bufs(h, old_tree);
+    free_bufs(h, keep);
+    return rc;
+  }
+  if (h->split) {
+    launch_relocate32(old_dt, h->dt, tleaf, (const float *)tpos, (const float *)tvel, n, h->leaf[1],
+                      (float *)h->pos[1], (float *)h->vel[1], s);
+    launch_rekey32(h->dt, h->leaf[1], (const float *)h->pos[1], n, h->key[1], h->err, s);
+  } else {
+    CK(cudaMemcpyAsync(h->pos[1], tpos, fs * d * n, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->vel[1], tvel, fs * d * n, cudaMemcpyDeviceToDevice, s));
+    launch_init64(h->dt, (double *)h->pos[1], n, h->leaf[1], h->key[1], h->err, s);
+  }
+  CK(cudaMemcpyAsync(h->ids[0], tids, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaGetLastError());
+  if ((rc = bin_fresh(h))) return rc;
+  CK(cudaStreamSynchronize(s));
+  free_bufs(h, old_tree);
+  free_bufs(h, keep);
+  h->leaf_stale = false;
+  h->q_valid = false;
+  return setup_brick(h);
 }
 
 int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax) {
-  (void)ppc; (void)dmin; (void)dmax;
-  return fail(h, PIC_ESTATE, "pic_adapt is not implemented yet");
+  if (check_handle(h)) return PIC_EINVAL;
+  const int d = h->d;
+  if (ppc < 0 || dmin < 0 || dmin > dmax || dmax > (d == 3 ? 6 : 10))
+    return fail(h, PIC_EINVAL, "adapt needs 0 <= dmin <= dmax <= 6 (3D) or 10 (2D)");
+  int rc;
+  if ((rc = ensure_leaf(h))) return rc;
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n;
+  uint32_t *key = (uint32_t *)h->perm;  // scratch until the re-bin
+  launch_fine_keys(h->dt, h->split, h->pos[0], h->leaf[0], n, dmax, key, s);
+  // refinement bitmaps of levels dmin .. dmax-1
+  std::vector<std::vector<uint32_t>> bits(dmax + 1);
+  if (dmax > dmin) {
+    const int64_t maxcells = pow3(d * (dmax - 1));
+    std::vector<DevBuf> tmp;
+    int32_t *count;
+    uint32_t *dbits;
+    if ((rc = dalloc(h, tmp, &count, maxcells)) || (rc = dalloc(h, tmp, &dbits, (maxcells + 31) / 32))) {
+      free_bufs(h, tmp);
+      return rc;
+    }
+    for (int m = dmin; m < dmax; ++m) {
+      const int64_t ncells = pow3(d * m);
+      const uint32_t div = (uint32_t)pow3(d * (dmax - m));
+      launch_level_bits(key, n, div, count, ncells, ppc, dbits, s);
+      bits[m].resize((ncells + 31) / 32);
+      cudaError_t e = cudaMemcpyAsync(bits[m].data(), dbits, sizeof(uint32_t) * bits[m].size(),
+                                      cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        free_bufs(h, tmp);
+        return cuda_fail(h, e, "adapt counts");
+      }
+    }
+    free_bufs(h, tmp);
+  }
+  // level-order flags: refined iff level < dmin, or level < dmax and the
+  // cell holds more than ppc particles
+  const int nch = (int)pow3(d);
+  std::vector<uint8_t> flags;
+  std::vector<int32_t> cur = {0, 0, 0}, nxt;
+  for (int m = 0; m <= dmax && !cur.empty(); ++m) {
+    nxt.clear();
+    for (size_t i = 0; i < cur.size(); i += 3) {
+      bool refine = m < dmin;
+      if (!refine && m < dmax) {
+        int64_t local = 0, mul = 1;
+        int32_t c[3] = {cur[i], cur[i + 1], cur[i + 2]};
+        for (int k = 0; k < m; ++k) {
+          int dg = c[0] % 3 + 3 * (c[1] % 3) + (d == 3 ? 9 * (c[2] % 3) : 0);
+          c[0] /= 3; c[1] /= 3; c[2] /= 3;
+          local += dg * mul;
+          mul *= nch;
+        }
+        refine = (bits[m][local >> 5] >> (local & 31)) & 1u;
+      }
+      flags.push_back(refine ? 1 : 0);
+      if (refine)
+        for (int ch = 0; ch < nch; ++ch) {
+          nxt.push_back(3 * cur[i] + ch % 3);
+          nxt.push_back(3 * cur[i + 1] + (ch / 3) % 3);
+          nxt.push_back(d == 3 ? 3 * cur[i + 2] + ch / 9 : 0);
+        }
+    }
+    cur.swap(nxt);
+  }
+  pic_tree_desc td{d, (int64_t)flags.size(), flags.data()};
+  return pic_retree(h, &td);
+}
+
+int pic_tree_flags(pic_t h, uint8_t *flags, int64_t *n_nodes) {
+  if (check_handle(h)) return PIC_EINVAL;
+  if (n_nodes) *n_nodes = h->ht.n_nodes;
+  if (flags)
+    for (int64_t i = 0; i < h->ht.n_nodes; ++i) flags[i] = h->ht.child0[i] >= 0 ? 1 : 0;
+  return PIC_OK;
 }
 
 }  // extern "C"

@@ -88,6 +88,7 @@ SIGNATURES = [
     ("pic_pidt_table", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_retree", C.c_int, [C.c_void_p, C.POINTER(TreeDesc)]),
     ("pic_adapt", C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32]),
+    ("pic_tree_flags", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
 ]
 
 
@@ -303,6 +304,13 @@ class Pic:
         self._check(self.lib.pic_retree(self.h, C.byref(tree)))
         self._flags = flags
         self._info = self.info()
+
+    def tree_flags(self) -> np.ndarray:
+        nn = C.c_int64(0)
+        self._check(self.lib.pic_tree_flags(self.h, None, C.byref(nn)))
+        out = np.zeros(nn.value, np.uint8)
+        self._check(self.lib.pic_tree_flags(self.h, _ptr(out)[0], None))
+        return out
 
     def adapt(self, ppc: int, dmin: int, dmax: int):
         self._check(self.lib.pic_adapt(self.h, ppc, dmin, dmax))

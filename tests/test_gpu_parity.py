@@ -249,3 +249,54 @@ def test_brick_path_bit_identical_to_generic(d, depth, n, vmax):
         assert fast.stats().movers == slow.stats().movers
         assert fast.stats().max_bucket == slow.stats().max_bucket
         assert fast.stats().error == 0
+
+
+# ---------------------------------------------------------------------------
+# a9 re-refinement by the ppc criterion
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scheme", [pic.PIT, pic.PIDT])
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_SPLIT])
+@pytest.mark.parametrize("d,base,ppc,dmin,dmax,n", [(2, 2, 40, 2, 5, 60_001), (3, 1, 30, 1, 3, 40_001)])
+def test_adapt_matches_oracle(d, base, ppc, dmin, dmax, n, scheme, precision):
+    rng = np.random.default_rng(d * 100 + ppc)
+    x = np.mod(0.5 + 0.12 * rng.standard_normal((d, n)), 1.0)
+    v = rng.uniform(-0.3, 0.3, (d, n))
+    flags0 = W.uniform_tree_flags(d, base)
+    g = make(d, flags0, x, v, scheme, precision, q=-1.0 / n, sweeps=5)
+    g.step(0.05)                       # move once on the base tree
+    g.adapt(ppc, dmin, dmax)
+    ot0 = oracle.Tree(d, flags0)
+    prm = oracle.Params(scheme=scheme, q=-1.0 / n, sweeps=5, omega=0.8)
+    if precision == pic.FP64:
+        st = oracle.State64(ot0, x, v, prm)
+        st.step(0.05)
+        expect = oracle.retree64(d, st.x, ppc, dmin, dmax)
+        assert np.array_equal(g.tree_flags(), expect)
+        ot1 = oracle.Tree(d, expect)
+        st1 = oracle.State64(ot1, st.x, st.v, prm, ids=st.ids)
+        xs, vs = g.particles()
+        assert np.array_equal(xs, st1.x) and np.array_equal(vs, st1.v)
+    else:
+        st = oracle.State32(ot0, x, v, prm)
+        st.step(0.05)
+        expect = oracle.retree32(ot0, st.leaf, st.o, ppc, dmin, dmax)
+        assert np.array_equal(g.tree_flags(), expect)
+        ot1 = oracle.Tree(d, expect)
+        leaf, o = st.leaf.copy(), st.o.copy()
+        ot0.rebin32_into(ot1, leaf, o)
+        key = ot1.keys32(scheme, leaf, o)
+        start, perm = oracle.stable_bucket(key, ot1.n_keys(scheme))
+        gl, go, gv = g.get_state()
+        assert np.array_equal(gl, leaf[perm]) and np.array_equal(go, o[:, perm])
+        assert np.array_equal(gv, st.v[:, perm])
+        st1_ids = st.ids[perm]
+        st1 = type("S", (), {"ids": st1_ids, "key": key[perm], "start": start})
+    start, ids = g.bins()
+    assert np.array_equal(ids, st1.ids)
+    assert np.array_equal(g.keys(), st1.key)
+    nb = 1 << d if scheme == pic.PIDT else 1
+    assert np.array_equal(start, st1.start[::nb])
+    # the adapted handle keeps stepping
+    g.step(0.05)
+    g.sync()
