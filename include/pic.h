@@ -115,6 +115,7 @@ typedef struct {
   int64_t n_keys;        /* sort keys: leaves (PIT) or owner vertex x 2^d quadrants (PIDT) */
   int32_t uniform;       /* 1 if every leaf is on `depth` */
   int32_t brick;         /* 1 if steps run the brick path */
+  int32_t n_instances;   /* independent plasmas in the handle (1 unless batched) */
   int64_t device_bytes;  /* device memory held by the handle */
 } pic_info_t;
 
@@ -135,6 +136,19 @@ PIC_API void pic_destroy(pic_t h);
 PIC_API const char *pic_strerror(int code);
 PIC_API const char *pic_last_error(pic_t h);
 PIC_API int pic_info(pic_t h, pic_info_t *out);
+
+/* Batch of n_inst independent plasmas of uneven size with uniform trees of
+ * any depth (same d): trees[i], parts[i], charge per particle q[i] (NULL:
+ * cfg->q for all).  Leaves, vertices, buckets and particles are concatenated
+ * instance by instance; every phase of a step is one launch over the whole
+ * batch.  Particle ids run over the batch in input order. */
+PIC_API int pic_create_batch(pic_t *out, int32_t n_inst, const pic_tree_desc *trees,
+                             const pic_particles_desc *parts, const double *q, const pic_config *cfg);
+
+/* Per-instance offsets into the concatenated particle storage, vertex arrays
+ * and bucket list; each array has n_instances + 1 entries (host memory, any
+ * may be NULL).  Particle ranges are fixed: no particle leaves its instance. */
+PIC_API int pic_instances(pic_t h, int64_t *particle_start, int64_t *vertex_start, int64_t *bucket_start);
 
 /* Leapfrog start: v_{-1/2} = v_0 - (q/m) E(x_0) dt/2 (deposit, solve, gather). */
 PIC_API int pic_init_leapfrog(pic_t h, double dt, pic_solve_fn hook, void *user);

@@ -15,8 +15,22 @@ namespace pic {
 
 __constant__ uint32_t c_pow3[21];
 
+// One plasma instance of a batch: its tree occupies the leaves, vertices and
+// sort keys [*_off, *_off + count) of the concatenated arrays.  A single
+// handle is a batch of one with every offset zero.
+struct InstInfo {
+  int32_t depth, M;            // uniform trees: level of every leaf, 3^depth
+  int32_t leaf_off, vert_off, key_off, spread_off, tab_root, n_vert;
+  int64_t poff;                // first particle of the instance in input order
+  double q, ion, ion_load, diag;
+  float q32, ion32, ion_load32, diag32;
+};
+
 struct DevTree {
   int d, nch, nc, depth, uniform, scheme;
+  int32_t n_inst;
+  const InstInfo *inst;
+  const int32_t *inst_of_leaf, *inst_of_vert;
   int64_t n_leaves, n_vert, n_pv, n_keys;
   int32_t M;  // 3^depth
   const TabEntry *tab;
@@ -73,9 +87,11 @@ __device__ __forceinline__ int32_t local_index(uint32_t J0, uint32_t J1, uint32_
   return local;
 }
 
-// Covering leaf of the quantised position Q (PIT owner, Theorem 1).
-__device__ __forceinline__ int32_t descend_q(const TabEntry *tab, int d, const uint32_t Q[3], int *lev_out) {
-  int ent = 0, lev = 0;
+// Covering leaf of the quantised position Q (PIT owner, Theorem 1), from the
+// table entry `root` of the instance's tree.
+__device__ __forceinline__ int32_t descend_q(const TabEntry *tab, int d, const uint32_t Q[3], int *lev_out,
+                                             int root = 0) {
+  int ent = root, lev = 0;
   for (;;) {
     TabEntry e = tab[ent];
     if (e.a < 0) {
@@ -113,8 +129,8 @@ __device__ __forceinline__ int drop_digit(float *f, int d) {
 // Split-precision re-location: the leaf covering integer cell I on level lev
 // plus fraction f.  Writes the leaf's offsets; returns the leaf id.
 __device__ __forceinline__ int32_t descend_split(const TabEntry *tab, int d, int lev, const int32_t I[3],
-                                                 float f[3], float o_out[3], int *lev_out) {
-  int ent = 0, m = 0, nch = d == 3 ? 27 : 9;
+                                                 float f[3], float o_out[3], int *lev_out, int root = 0) {
+  int ent = root, m = 0, nch = d == 3 ? 27 : 9;
   for (;;) {
     TabEntry e = tab[ent];
     if (e.a < 0) {
@@ -203,10 +219,13 @@ __device__ __forceinline__ T shape(const T *t, int e, int d) {
   return w;
 }
 
-// Incident leaf corners of uniform vertex v in ascending leaf-corner order.
-__device__ __forceinline__ int uniform_incidences(int64_t v, int d, int32_t M, const int32_t *spread, int32_t *lc) {
+// Incident leaf corners of uniform vertex v (global id) in ascending
+// leaf-corner order, for the instance I.
+__device__ __forceinline__ int uniform_incidences(int64_t v, int d, const InstInfo &I, const int32_t *spread,
+                                                  int32_t *lc) {
+  const int32_t M = I.M;
   int32_t j[3] = {0, 0, 0};
-  int64_t r = v;
+  int64_t r = v - I.vert_off;
   for (int a = 0; a < d; ++a) { j[a] = (int32_t)(r % M); r /= M; }
   int nc = 1 << d;
   for (int f = 0; f < nc; ++f) {
@@ -215,7 +234,7 @@ __device__ __forceinline__ int uniform_incidences(int64_t v, int d, int32_t M, c
       int32_t cc = j[a] - ((f >> a) & 1);
       c[a] = cc < 0 ? cc + M : cc;
     }
-    lc[f] = uniform_leaf_of_cell(spread, M, c, d) * nc + f;
+    lc[f] = (I.leaf_off + uniform_leaf_of_cell(spread + I.spread_off, M, c, d)) * nc + f;
   }
   for (int i = 1; i < nc; ++i) {  // insertion sort, at most 8 entries
     int32_t x = lc[i];

@@ -52,13 +52,26 @@ __device__ __forceinline__ void leaf_info(const DevTree &t, int32_t L, int *lev,
   for (int a = 0; a < t.d; ++a) c[a] = t.leaf_coords[(int64_t)L * t.d + a];
 }
 
+__device__ __forceinline__ const InstInfo &inst_of_leaf(const DevTree &t, int32_t L) {
+  return t.inst[t.n_inst > 1 ? t.inst_of_leaf[L] : 0];
+}
+__device__ __forceinline__ const InstInfo &inst_of_vertex(const DevTree &t, int64_t v) {
+  return t.inst[t.n_inst > 1 ? t.inst_of_vert[v] : 0];
+}
+
+// Global vertex ids of the corners of uniform-grid cell c of instance I.
+__device__ __forceinline__ void corner_vertices(const InstInfo &I, const int32_t *c, int d, int32_t *vid) {
+  uniform_corner_vertices(c, d, I.M, vid);
+  for (int e = 0; e < (1 << d); ++e) vid[e] += I.vert_off;
+}
+
 // PIDT owner vertex of corner a of leaf L (uniform grids: the FE vertex).
 __device__ __forceinline__ int32_t pidt_vertex(const DevTree &t, int32_t L, int a) {
   if (t.uniform) {
     int32_t c[3] = {0, 0, 0};
     for (int k = 0; k < t.d; ++k) c[k] = t.leaf_coords[(int64_t)L * t.d + k];
     int32_t vid[8];
-    uniform_corner_vertices(c, t.d, t.M, vid);
+    corner_vertices(inst_of_leaf(t, L), c, t.d, vid);
     return vid[a];
   }
   return t.corner_pv[(int64_t)L * t.nc + a];
@@ -75,7 +88,7 @@ __device__ __forceinline__ int32_t key_of(const DevTree &t, int32_t L, int a) {
 // from their masters, in ascending master order).
 __device__ __forceinline__ double corner_value(const DevTree &t, int32_t L, const int32_t *c, int e,
                                                const double *F) {
-  if (t.uniform) return F[uniform_corner_vertex(c, e, t.d, t.M)];
+  if (t.uniform) return F[inst_of_leaf(t, L).vert_off + uniform_corner_vertex(c, e, t.d, inst_of_leaf(t, L).M)];
   int64_t i = (int64_t)L * t.nc + e;
   double s = 0.0;
   for (int32_t j = t.cexp_ptr[i]; j < t.cexp_ptr[i + 1]; ++j) s = s + t.cexp_w64[j] * F[t.cexp_vid[j]];
@@ -84,7 +97,7 @@ __device__ __forceinline__ double corner_value(const DevTree &t, int32_t L, cons
 
 __device__ __forceinline__ float corner_value(const DevTree &t, int32_t L, const int32_t *c, int e,
                                               const float *F) {
-  if (t.uniform) return F[uniform_corner_vertex(c, e, t.d, t.M)];
+  if (t.uniform) return F[inst_of_leaf(t, L).vert_off + uniform_corner_vertex(c, e, t.d, inst_of_leaf(t, L).M)];
   int64_t i = (int64_t)L * t.nc + e;
   float s = 0.0f;
   for (int32_t j = t.cexp_ptr[i]; j < t.cexp_ptr[i + 1]; ++j) s = s + t.cexp_w32[j] * F[t.cexp_vid[j]];
@@ -96,16 +109,16 @@ __device__ __forceinline__ const float *inc_weights(const DevTree &t, float) { r
 __device__ __forceinline__ double kref_val(int e, int f, double) { return c_kref64[e][f]; }
 __device__ __forceinline__ float kref_val(int e, int f, float) { return c_kref32[e][f]; }
 __device__ __forceinline__ double ion_load(const DevTree &t, int64_t v, double) {
-  return t.uniform ? t.ion_u64 : t.ion64[v];
+  return t.uniform ? inst_of_vertex(t, v).ion_load : t.ion64[v];
 }
 __device__ __forceinline__ float ion_load(const DevTree &t, int64_t v, float) {
-  return t.uniform ? t.ion_u32 : t.ion32[v];
+  return t.uniform ? inst_of_vertex(t, v).ion_load32 : t.ion32[v];
 }
 __device__ __forceinline__ double diag_val(const DevTree &t, int64_t v, double) {
-  return t.uniform ? t.diag_u64 : t.diag64[v];
+  return t.uniform ? inst_of_vertex(t, v).diag : t.diag64[v];
 }
 __device__ __forceinline__ float diag_val(const DevTree &t, int64_t v, float) {
-  return t.uniform ? t.diag_u32 : t.diag32[v];
+  return t.uniform ? inst_of_vertex(t, v).diag32 : t.diag32[v];
 }
 
 // Visit the incident leaf corners (lc = leaf * 2^d + corner, ascending) of
@@ -114,7 +127,7 @@ template <typename T, typename Fn>
 __device__ __forceinline__ void for_incidences(const DevTree &t, int64_t v, Fn fn) {
   if (t.uniform) {
     int32_t lc[8];
-    int m = uniform_incidences(v, t.d, t.M, t.spread, lc);
+    int m = uniform_incidences(v, t.d, inst_of_vertex(t, v), t.spread, lc);
     for (int i = 0; i < m; ++i) fn(lc[i], (T)1);
   } else {
     const T *ww = inc_weights(t, (T)0);
@@ -210,15 +223,22 @@ __global__ void k_leaf_partials(DevTree t, const int32_t *__restrict__ start, co
 
 // Per vertex: S = sum of w * partial over incident leaf corners (ascending),
 // Q = q S + ion * integral(phi_v); block partial sums of Q in FP64.
+__device__ __forceinline__ double inst_q(const InstInfo &I, double) { return I.q; }
+__device__ __forceinline__ float inst_q(const InstInfo &I, float) { return I.q32; }
+__device__ __forceinline__ double inst_ion(const InstInfo &I, double) { return I.ion; }
+__device__ __forceinline__ float inst_ion(const InstInfo &I, float) { return I.ion32; }
+
 template <typename T>
-__global__ void k_vertex_charge(DevTree t, const T *__restrict__ part, T q, T ion, T *Q, double *block_sum) {
+__global__ void k_vertex_charge(DevTree t, const T *__restrict__ part, T *Q, double *block_sum) {
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double mine = 0.0;
   if (v < t.n_vert) {
+    const InstInfo &I = inst_of_vertex(t, v);
+    const T q = inst_q(I, (T)0), ion = inst_ion(I, (T)0);
     T S = (T)0;
     if (t.uniform) {
       int32_t lc[8];
-      int m = uniform_incidences(v, t.d, t.M, t.spread, lc);
+      int m = uniform_incidences(v, t.d, I, t.spread, lc);
       for (int i = 0; i < m; ++i) S = S + part[lc[i]];
     } else {
       const T *w = inc_weights(t, (T)0);
@@ -239,7 +259,7 @@ template <typename T>
 __global__ void k_rhs(DevTree t, const T *Q, const double *total, T *b) {
   int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= t.n_vert) return;
-  T tot = (T)(*total);
+  T tot = (T)(t.n_inst > 1 ? total[1 + t.inst_of_vert[v]] : *total);
   b[v] = Q[v] - tot * ion_load(t, v, (T)0);
 }
 
@@ -323,10 +343,21 @@ __device__ __forceinline__ int pidt_corner_o(const float *o, int d) {
   return a_idx;
 }
 
+// Instance of input particle p (binary search over the first particles).
+__device__ __forceinline__ int inst_of_particle(const DevTree &t, int64_t p) {
+  int lo = 0, hi = t.n_inst;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (t.inst[mid].poff <= p) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 // FP64: wrap x in place, covering leaf and key.
 __global__ void k_init64(DevTree t, double *x, int64_t n, int32_t *leaf, int32_t *key, int32_t *err) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
+  const int root = t.inst[inst_of_particle(t, p)].tab_root;
   uint32_t Q[3] = {0u, 0u, 0u};
   for (int a = 0; a < t.d; ++a) {
     double xa = x[a * n + p];
@@ -336,7 +367,7 @@ __global__ void k_init64(DevTree t, double *x, int64_t n, int32_t *leaf, int32_t
     Q[a] = quantise(y);
   }
   int lev;
-  int32_t L = descend_q(t.tab, t.d, Q, &lev);
+  int32_t L = descend_q(t.tab, t.d, Q, &lev, root);
   leaf[p] = L;
   key[p] = key_of(t, L, pidt_corner_q(Q, lev, t.d));
 }
@@ -346,6 +377,7 @@ __global__ void k_init32(DevTree t, const double *x, const double *v, int64_t n,
                          float *vf, int32_t *key, int32_t *err) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
+  const int root = t.inst[inst_of_particle(t, p)].tab_root;
   uint32_t Q[3] = {0u, 0u, 0u};
   double y[3] = {0.0, 0.0, 0.0};
   for (int a = 0; a < t.d; ++a) {
@@ -355,7 +387,7 @@ __global__ void k_init32(DevTree t, const double *x, const double *v, int64_t n,
     Q[a] = quantise(y[a]);
   }
   int lev;
-  int32_t L = descend_q(t.tab, t.d, Q, &lev);
+  int32_t L = descend_q(t.tab, t.d, Q, &lev, root);
   leaf[p] = L;
   double s = (double)c_pow3[lev];
   float oo[3] = {0.f, 0.f, 0.f};
@@ -422,9 +454,10 @@ __global__ void k_push64(DevTree t, Push64Args a) {
     double tl[3];
     local_coords(a.x, n, p, lev, c, d, tl);
     double E[3] = {0.0, 0.0, 0.0};
+    const InstInfo &I = inst_of_leaf(t, L);
     if (t.uniform) {
       int32_t vid[8];
-      uniform_corner_vertices(c, d, t.M, vid);
+      corner_vertices(I, c, d, vid);
       for (int e = 0; e < nc; ++e) {
         double w = shape<double>(tl, e, d);
         for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * a.E[ax * nv + vid[e]];
@@ -449,12 +482,12 @@ __global__ void k_push64(DevTree t, Push64Args a) {
     int lev2;
     int32_t L2;
     if (t.uniform) {
-      uint32_t step = 2u * c_pow3[18 - t.depth];
+      uint32_t step = 2u * c_pow3[18 - I.depth];
       int32_t cc[3] = {(int32_t)(Q[0] / step), (int32_t)(Q[1] / step), d == 3 ? (int32_t)(Q[2] / step) : 0};
-      L2 = uniform_leaf_of_cell(t.spread, t.M, cc, d);
-      lev2 = t.depth;
+      L2 = I.leaf_off + uniform_leaf_of_cell(t.spread + I.spread_off, I.M, cc, d);
+      lev2 = I.depth;
     } else {
-      L2 = descend_q(t.tab, d, Q, &lev2);
+      L2 = descend_q(t.tab, d, Q, &lev2, I.tab_root);
     }
     knew = key_of(t, L2, pidt_corner_q(Q, lev2, d));
     int32_t kold = t.scheme == 0 ? L : a.key[p];
@@ -480,9 +513,10 @@ __global__ void k_push32(DevTree t, Push32Args a) {
     float o[3] = {0.f, 0.f, 0.f};
     for (int ax = 0; ax < d; ++ax) o[ax] = a.o[ax * n + p];
     float E[3] = {0.f, 0.f, 0.f};
+    const InstInfo &Ins = inst_of_leaf(t, L);
     if (t.uniform) {
       int32_t vid[8];
-      uniform_corner_vertices(c, d, t.M, vid);
+      corner_vertices(Ins, c, d, vid);
       for (int e = 0; e < nc; ++e) {
         float w = shape<float>(o, e, d);
         for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * a.E[ax * nv + vid[e]];
@@ -522,11 +556,11 @@ __global__ void k_push32(DevTree t, Push32Args a) {
     float o2[3] = {0.f, 0.f, 0.f};
     int lev2;
     int32_t L2;
-    if (t.uniform) {  // the covering leaf is the cell I itself; o = f
-      L2 = uniform_leaf_of_cell(t.spread, t.M, I, d);
+    if (t.uniform) {  // the covering leaf is the target cell itself; o = f
+      L2 = Ins.leaf_off + uniform_leaf_of_cell(t.spread + Ins.spread_off, Ins.M, I, d);
       for (int ax = 0; ax < d; ++ax) o2[ax] = clamp_off(f[ax]);
     } else {
-      L2 = descend_split(t.tab, d, lev, I, f, o2, &lev2);
+      L2 = descend_split(t.tab, d, lev, I, f, o2, &lev2, Ins.tab_root);
     }
     for (int ax = 0; ax < d; ++ax) a.to[ax * n + p] = o2[ax];
     knew = key_of(t, L2, pidt_corner_o(o2, d));
@@ -910,26 +944,52 @@ void launch_relocate32(const DevTree &from, const DevTree &to, const int32_t *le
   k_relocate32<<<grid_for(n), kBlock, 0, s>>>(from, to, leaf, o, v, n, leaf2, o2, v2);
 }
 
-void launch_vertex_charge(const DevTree &t, bool split, const void *part, double q, double ion, void *Q,
-                          double *block_sum, double *total, cudaStream_t s) {
-  if (split) {
-    { COUNT(1); k_vertex_charge<float><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const float *)part, (float)q, (float)ion,
-                                                                 (float *)Q, block_sum); }
-  } else {
-    { COUNT(1); k_vertex_charge<double><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const double *)part, q, ion, (double *)Q,
-                                                                  block_sum); }
+// Per-instance FP64 sums of the vertex charges, one block per instance (fixed order).
+template <typename T>
+__global__ void k_inst_sum(DevTree t, const T *Q, double *out) {
+  const InstInfo &I = t.inst[blockIdx.x];
+  double v = 0.0;
+  for (int64_t i = threadIdx.x; i < I.n_vert; i += blockDim.x) v += (double)Q[I.vert_off + i];
+  __shared__ double sh[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) out[blockIdx.x] = v;
   }
-  { COUNT(1); k_sum_blocks<<<1, 1024, 0, s>>>(block_sum, grid_for(t.n_vert), total); }
+}
+
+void launch_vertex_charge(const DevTree &t, bool split, const void *part, void *Q, double *block_sum,
+                          double *total, cudaStream_t s) {
+  if (split) {
+    { COUNT(1); k_vertex_charge<float><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const float *)part, (float *)Q, block_sum); }
+  } else {
+    { COUNT(1); k_vertex_charge<double><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const double *)part, (double *)Q, block_sum); }
+  }
+  if (t.n_inst > 1) {
+    COUNT(2);
+    if (split)
+      k_inst_sum<float><<<t.n_inst, 256, 0, s>>>(t, (const float *)Q, total + 1);
+    else
+      k_inst_sum<double><<<t.n_inst, 256, 0, s>>>(t, (const double *)Q, total + 1);
+    k_sum_blocks<<<1, 1024, 0, s>>>(total + 1, t.n_inst, total);
+  } else {
+    COUNT(1);
+    k_sum_blocks<<<1, 1024, 0, s>>>(block_sum, grid_for(t.n_vert), total);
+  }
 }
 
 void launch_deposit(const DevTree &t, bool split, const int32_t *start, const void *pos, int64_t n, void *part,
-                    double q, double ion, void *Q, double *block_sum, double *total, cudaStream_t s) {
+                    void *Q, double *block_sum, double *total, cudaStream_t s) {
   if (split) {
     { COUNT(1); k_leaf_partials<true><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part); }
   } else {
     { COUNT(1); k_leaf_partials<false><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part); }
   }
-  launch_vertex_charge(t, split, part, q, ion, Q, block_sum, total, s);
+  launch_vertex_charge(t, split, part, Q, block_sum, total, s);
 }
 
 void launch_solve(const DevTree &t, bool split, const void *Q, const double *total, void *b, void *V, void *Vtmp,

@@ -132,10 +132,12 @@ void launch_relocate32(const DevTree &from, const DevTree &to, const int32_t *le
                        int64_t n, int32_t *leaf2, float *o2, float *v2, cudaStream_t s);
 
 // Vertex charges and FP64 total from leaf-corner partials already computed.
-void launch_vertex_charge(const DevTree &t, bool split, const void *part, double q, double ion, void *Q,
-                          double *block_sum, double *total, cudaStream_t s);
+void launch_vertex_charge(const DevTree &t, bool split, const void *part, void *Q, double *block_sum,
+                          double *total, cudaStream_t s);
+// Charges per instance: q and ion density come from the instance table;
+// total[0] is the FP64 sum over all vertices, total[1 + i] per instance.
 void launch_deposit(const DevTree &t, bool split, const int32_t *start, const void *pos, int64_t n, void *part,
-                    double q, double ion, void *Q, double *block_sum, double *total, cudaStream_t s);
+                    void *Q, double *block_sum, double *total, cudaStream_t s);
 void launch_solve(const DevTree &t, bool split, const void *Q, const double *total, void *b, void *V, void *Vtmp,
                   int sweeps, double omega, double *block_sum, double *resid2, cudaStream_t s);
 void launch_efield(const DevTree &t, bool split, const void *V, void *E, cudaStream_t s);

@@ -31,7 +31,9 @@ struct pic_s {
   pic_config cfg{};
   int d = 0, scheme = 0, split = 0;
   int64_t n = 0;
-  HostTree ht;
+  HostTree ht;                 // instance 0 (the only one unless batched)
+  std::vector<HostTree> hts;   // every instance
+  std::vector<InstInfo> inst;
   DevTree dt{};
   std::vector<DevBuf> tree_bufs, state_bufs;
   int64_t device_bytes = 0;
@@ -132,62 +134,126 @@ int upload(pic_t h, std::vector<DevBuf> &bufs, const T **out, const std::vector<
 
 int64_t n_keys_of(const HostTree &t, int scheme) { return scheme == PIC_PIT ? t.n_leaves : t.n_pv * t.nc; }
 
-// Tabulate the tree on the host and upload the device view.  The previous
-// tree's device buffers are handed back in *old (freed by the caller) so that
-// particles can still be re-located from it.
-int install_tree(pic_t h, const pic_tree_desc *tree, std::vector<DevBuf> *old = nullptr) {
-  std::string err;
-  HostTree ht;
-  if (!tree || !tree->flags) return fail(h, PIC_EINVAL, "tree descriptor is NULL");
-  if (ht.build(tree->d, tree->n_nodes, tree->flags, &err)) return fail(h, PIC_EINVAL, err);
-  if (h->d && tree->d != h->d) return fail(h, PIC_EINVAL, "tree dimension differs from the handle");
-  if (ht.depth > 12 && !ht.uniform) return fail(h, PIC_EINVAL, "adaptive trees deeper than level 12 are not supported");
-  {
+// Tabulate the trees of all instances on the host and upload the device view
+// (leaves, vertices and keys concatenated instance by instance).  The previous
+// device buffers are handed back in *old (freed by the caller) so particles
+// can still be re-located from them.
+int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const std::vector<double> &qs,
+                   std::vector<DevBuf> *old = nullptr) {
+  if (!trees || n_inst < 1) return fail(h, PIC_EINVAL, "tree descriptor is NULL");
+  std::vector<HostTree> hts(n_inst);
+  for (int32_t i = 0; i < n_inst; ++i) {
+    std::string err;
+    HostTree &ht = hts[i];
+    if (!trees[i].flags) return fail(h, PIC_EINVAL, "tree descriptor is NULL");
+    if (ht.build(trees[i].d, trees[i].n_nodes, trees[i].flags, &err))
+      return fail(h, PIC_EINVAL, "instance " + std::to_string(i) + ": " + err);
+    if ((h->d && trees[i].d != h->d) || trees[i].d != trees[0].d)
+      return fail(h, PIC_EINVAL, "tree dimension differs from the handle");
+    if (ht.depth > 12 && !ht.uniform) return fail(h, PIC_EINVAL, "adaptive trees deeper than level 12 are not supported");
+    if (n_inst > 1 && !ht.uniform) return fail(h, PIC_EINVAL, "batched instances must have uniform trees");
     int64_t mv = 1;
     for (int a = 0; a < ht.d; ++a) mv *= ht.M;
     if (mv > INT32_MAX) return fail(h, PIC_EINVAL, "finest level has more than 2^31 grid points");
+    ht.build_grid();
+    ht.build_pidt();
   }
-  ht.build_grid();
-  ht.build_pidt();
-  if (n_keys_of(ht, h->scheme) >= INT32_MAX) return fail(h, PIC_EINVAL, "more than 2^31 sort keys");
+  const HostTree &h0 = hts[0];
+  const int d = h0.d, nc = h0.nc;
+  int64_t nl = 0, nv = 0, npv = 0, ntab = 0, nspread = 0;
+  std::vector<InstInfo> inst(n_inst);
+  for (int32_t i = 0; i < n_inst; ++i) {
+    const HostTree &ht = hts[i];
+    InstInfo &I = inst[i];
+    I.depth = ht.depth;
+    I.M = (int32_t)ht.M;
+    I.leaf_off = (int32_t)nl;
+    I.vert_off = (int32_t)nv;
+    I.key_off = (int32_t)(h->scheme == PIC_PIT ? nl : npv * nc);
+    I.spread_off = (int32_t)nspread;
+    I.tab_root = (int32_t)ntab;
+    I.n_vert = (int32_t)ht.n_vert;
+    I.poff = 0;
+    I.q = qs[i];
+    I.ion = h->cfg.ion;
+    I.ion_load = ht.uniform ? ht.ion_load[0] : 0.0;
+    I.diag = ht.uniform ? ht.diag[0] : 0.0;
+    I.q32 = (float)I.q;
+    I.ion32 = (float)I.ion;
+    I.ion_load32 = (float)I.ion_load;
+    I.diag32 = (float)I.diag;
+    nl += ht.n_leaves;
+    nv += ht.n_vert;
+    npv += ht.n_pv;
+    ntab += (int64_t)ht.tab.size();
+    if (ht.uniform) nspread += (int64_t)d * ht.M;
+  }
+  const int64_t nkeys = h->scheme == PIC_PIT ? nl : npv * nc;
+  if (nl >= INT32_MAX / 8 || nv >= INT32_MAX || nkeys >= INT32_MAX)
+    return fail(h, PIC_EINVAL, "more than 2^31 leaves, vertices or sort keys");
+  std::vector<TabEntry> tab;
+  std::vector<uint8_t> leaf_level;
+  std::vector<int32_t> leaf_coords, spread, iol, iov;
+  tab.reserve(ntab);
+  leaf_level.reserve(nl);
+  leaf_coords.reserve(nl * d);
+  if (n_inst > 1) {
+    iol.reserve(nl);
+    iov.reserve(nv);
+  }
+  for (int32_t i = 0; i < n_inst; ++i) {
+    const HostTree &ht = hts[i];
+    const InstInfo &I = inst[i];
+    for (const TabEntry &e : ht.tab)
+      tab.push_back(e.a >= 0 ? TabEntry{e.a + I.tab_root, 0} : TabEntry{e.a, e.b + I.leaf_off});
+    leaf_level.insert(leaf_level.end(), ht.leaf_level.begin(), ht.leaf_level.end());
+    leaf_coords.insert(leaf_coords.end(), ht.leaf_coords.begin(), ht.leaf_coords.end());
+    if (ht.uniform)
+      for (int a = 0; a < d; ++a)
+        for (int64_t c = 0; c < ht.M; ++c) {
+          int64_t v = 0, cc = c, mul = pow3(a);
+          for (int k = 0; k < ht.depth; ++k) {
+            v += (cc % 3) * mul;
+            cc /= 3;
+            mul *= ht.nch;
+          }
+          spread.push_back((int32_t)v);
+        }
+    if (n_inst > 1) {
+      iol.insert(iol.end(), ht.n_leaves, i);
+      iov.insert(iov.end(), ht.n_vert, i);
+    }
+  }
   std::vector<DevBuf> prev;
   prev.swap(h->tree_bufs);
   DevTree dt{};
-  dt.d = ht.d;
-  dt.nch = ht.nch;
-  dt.nc = ht.nc;
-  dt.depth = ht.depth;
-  dt.uniform = ht.uniform ? 1 : 0;
+  dt.d = d;
+  dt.nch = h0.nch;
+  dt.nc = nc;
+  dt.depth = h0.depth;
+  dt.uniform = h0.uniform ? 1 : 0;
   dt.scheme = h->scheme;
-  dt.n_leaves = ht.n_leaves;
-  dt.n_vert = ht.n_vert;
-  dt.n_pv = ht.n_pv;
-  dt.n_keys = n_keys_of(ht, h->scheme);
-  dt.M = (int32_t)ht.M;
-  dt.n_tab = (int32_t)ht.tab.size();
+  dt.n_inst = n_inst;
+  dt.n_leaves = nl;
+  dt.n_vert = nv;
+  dt.n_pv = npv;
+  dt.n_keys = nkeys;
+  dt.M = (int32_t)h0.M;
+  dt.n_tab = (int32_t)tab.size();
   int rc;
   auto &tb = h->tree_bufs;
-  if ((rc = upload(h, tb, &dt.tab, ht.tab))) return rc;
-  if ((rc = upload(h, tb, &dt.leaf_level, ht.leaf_level))) return rc;
-  if ((rc = upload(h, tb, &dt.leaf_coords, ht.leaf_coords))) return rc;
-  if (ht.uniform) {
-    std::vector<int32_t> spread((size_t)ht.d * ht.M, 0);
-    for (int a = 0; a < ht.d; ++a)
-      for (int64_t c = 0; c < ht.M; ++c) {
-        int64_t v = 0, cc = c, mul = pow3(a);
-        for (int i = 0; i < ht.depth; ++i) {
-          v += (cc % 3) * mul;
-          cc /= 3;
-          mul *= ht.nch;
-        }
-        spread[(size_t)a * ht.M + c] = (int32_t)v;
-      }
+  if ((rc = upload(h, tb, &dt.tab, tab))) return rc;
+  if ((rc = upload(h, tb, &dt.leaf_level, leaf_level))) return rc;
+  if ((rc = upload(h, tb, &dt.leaf_coords, leaf_coords))) return rc;
+  if ((rc = upload(h, tb, &dt.inst, inst))) return rc;
+  if (n_inst > 1) {
+    if ((rc = upload(h, tb, &dt.inst_of_leaf, iol))) return rc;
+    if ((rc = upload(h, tb, &dt.inst_of_vert, iov))) return rc;
+  }
+  if (h0.uniform) {
     if ((rc = upload(h, tb, &dt.spread, spread))) return rc;
-    dt.ion_u64 = ht.ion_load[0];
-    dt.ion_u32 = (float)ht.ion_load[0];
-    dt.diag_u64 = ht.diag[0];
-    dt.diag_u32 = (float)ht.diag[0];
   } else {
+    const HostTree &ht = h0;
     std::vector<float> f;
     auto to32 = [&](const std::vector<double> &v) {
       f.assign(v.size(), 0.f);
@@ -209,13 +275,27 @@ int install_tree(pic_t h, const pic_tree_desc *tree, std::vector<DevBuf> *old = 
     if ((rc = upload(h, tb, &dt.dcnt, ht.direct_cnt))) return rc;
     if ((rc = upload(h, tb, &dt.corner_pv, ht.corner_pv))) return rc;
   }
-  h->d = ht.d;
-  h->ht = std::move(ht);
+  h->d = d;
+  h->inst = inst;
+  h->hts = std::move(hts);
+  h->ht = h->hts[0];
   h->dt = dt;
   if (old)
     old->swap(prev);
   else
     free_bufs(h, prev);
+  return PIC_OK;
+}
+
+int install_tree(pic_t h, const pic_tree_desc *tree, std::vector<DevBuf> *old = nullptr) {
+  std::vector<double> qs(1, h->cfg.q);
+  return install_forest(h, tree, 1, qs, old);
+}
+
+// Particle offsets of the instances (input order), uploaded into the table.
+int set_particle_offsets(pic_t h, const std::vector<int64_t> &poff) {
+  for (size_t i = 0; i < h->inst.size(); ++i) h->inst[i].poff = poff[i];
+  CK(cudaMemcpy((void *)h->dt.inst, h->inst.data(), sizeof(InstInfo) * h->inst.size(), cudaMemcpyHostToDevice));
   return PIC_OK;
 }
 
@@ -270,7 +350,7 @@ int alloc_state(pic_t h) {
   if ((rc = dalloc(h, sb, &p, fs * nv * d))) return rc;
   h->E = p;
   if ((rc = dalloc(h, sb, &h->block_sum, (nv + 255) / 256 + 1))) return rc;
-  if ((rc = dalloc(h, sb, &h->total, 2))) return rc;
+  if ((rc = dalloc(h, sb, &h->total, 2 + h->dt.n_inst))) return rc;
   if ((rc = dalloc(h, sb, &h->resid2, 2))) return rc;
   if ((rc = dalloc(h, sb, &p, sizeof(double) * d * n))) return rc;
   h->Ep = p;
@@ -279,7 +359,7 @@ int alloc_state(pic_t h) {
   CK(cudaMemsetAsync(h->E, 0, fs * nv * d, s));
   CK(cudaMemsetAsync(h->err, 0, sizeof(int32_t), s));
   CK(cudaMemsetAsync(h->scalars, 0, sizeof(int32_t) * 8, s));
-  CK(cudaMemsetAsync(h->total, 0, sizeof(double) * 2, s));
+  CK(cudaMemsetAsync(h->total, 0, sizeof(double) * (2 + h->dt.n_inst), s));
   CK(cudaMemsetAsync(h->resid2, 0, sizeof(double) * 2, s));
   return PIC_OK;
 }
@@ -336,7 +416,9 @@ int setup_brick(pic_t h) {
   free_bufs(h, h->brick_bufs);
   h->brick = false;
   const auto &t = h->ht;
-  if (h->cfg.path != PIC_PATH_AUTO || !t.uniform || h->scheme != PIC_PIT || !h->split || t.depth < 3) return PIC_OK;
+  if (h->cfg.path != PIC_PATH_AUTO || !t.uniform || h->scheme != PIC_PIT || !h->split || t.depth < 3 ||
+      h->dt.n_inst > 1)
+    return PIC_OK;
   BrickGeom g{};
   g.d = t.d;
   g.kb = 2;
@@ -460,7 +542,7 @@ int brick_push_and_rebin(pic_t h, double dt) {
   {
     // the pull also summed the deposit partials of the new positions
     PhaseScope ps(h, PIC_PHASE_DEPOSIT);
-    launch_vertex_charge(h->dt, true, h->part, h->cfg.q, h->cfg.ion, h->Q, h->block_sum, h->total, s);
+    launch_vertex_charge(h->dt, true, h->part, h->Q, h->block_sum, h->total, s);
   }
   CK(cudaGetLastError());
   std::swap(h->start_cur, h->start_new);
@@ -529,7 +611,7 @@ int deposit(pic_t h) {
   if (h->q_valid) return PIC_OK;
   PhaseScope ps(h, PIC_PHASE_DEPOSIT);
   h->q_valid = true;
-  launch_deposit(h->dt, h->split, h->start_cur, h->pos[0], h->n, h->part, h->cfg.q, h->cfg.ion, h->Q,
+  launch_deposit(h->dt, h->split, h->start_cur, h->pos[0], h->n, h->part, h->Q,
                  h->block_sum, h->total, h->stream);
   CK(cudaGetLastError());
   return PIC_OK;
@@ -625,26 +707,41 @@ int copy_in(pic_t h, void *dst, const void *src, size_t bytes, int32_t where) {
   return PIC_OK;
 }
 
-// Load FP64 particles (host or device) into state [1] and bin them.
-int load_particles64(pic_t h, const double *x, const double *v, int32_t where) {
+// Load FP64 particles (host or device, one piece per instance, concatenated
+// axis by axis) into state [1] and bin them.
+int load_particles64(pic_t h, const pic_particles_desc *parts, int32_t n_inst) {
   cudaStream_t s = h->stream;
-  const size_t bytes = sizeof(double) * h->d * h->n;
+  const int d = h->d;
+  const int64_t n = h->n;
   int rc;
+  double *xs, *vs;
+  std::vector<DevBuf> tmp;
   if (h->split) {
-    double *xs = (double *)h->Ep;
-    double *vs = nullptr;
-    std::vector<DevBuf> tmp;
-    if ((rc = dalloc(h, tmp, &vs, (size_t)h->d * h->n))) return rc;
-    if ((rc = copy_in(h, xs, x, bytes, where))) { free_bufs(h, tmp); return rc; }
-    if ((rc = copy_in(h, vs, v, bytes, where))) { free_bufs(h, tmp); return rc; }
-    launch_init32(h->dt, xs, vs, h->n, h->leaf[1], (float *)h->pos[1], (float *)h->vel[1], h->key[1], h->err, s);
+    xs = (double *)h->Ep;
+    if ((rc = dalloc(h, tmp, &vs, (size_t)d * n))) return rc;
+  } else {
+    xs = (double *)h->pos[1];
+    vs = (double *)h->vel[1];
+  }
+  int64_t off = 0;
+  for (int32_t i = 0; i < n_inst; ++i) {
+    const int64_t ni = parts[i].n;
+    for (int a = 0; a < d && ni > 0; ++a) {
+      if ((rc = copy_in(h, xs + a * n + off, parts[i].x + a * ni, sizeof(double) * ni, parts[i].where)) ||
+          (rc = copy_in(h, vs + a * n + off, parts[i].v + a * ni, sizeof(double) * ni, parts[i].where))) {
+        free_bufs(h, tmp);
+        return rc;
+      }
+    }
+    off += ni;
+  }
+  if (h->split) {
+    launch_init32(h->dt, xs, vs, n, h->leaf[1], (float *)h->pos[1], (float *)h->vel[1], h->key[1], h->err, s);
     cudaError_t e = cudaStreamSynchronize(s);
     free_bufs(h, tmp);
     if (e != cudaSuccess) return cuda_fail(h, e, "particle conversion");
   } else {
-    if ((rc = copy_in(h, h->pos[1], x, bytes, where))) return rc;
-    if ((rc = copy_in(h, h->vel[1], v, bytes, where))) return rc;
-    launch_init64(h->dt, (double *)h->pos[1], h->n, h->leaf[1], h->key[1], h->err, s);
+    launch_init64(h->dt, xs, n, h->leaf[1], h->key[1], h->err, s);
   }
   CK(cudaGetLastError());
   return bin_fresh(h);
@@ -690,33 +787,47 @@ void pic_destroy(pic_t h) {
   delete h;
 }
 
-int pic_create(pic_t *out, const pic_tree_desc *tree, const pic_particles_desc *parts, const pic_config *cfg) {
+// Common creation path: n_inst instances (a single handle is a batch of one).
+static int create_forest(pic_t *out, int32_t n_inst, const pic_tree_desc *trees, const pic_particles_desc *parts,
+                         const double *q, const pic_config *cfg) {
   if (!out) return PIC_EINVAL;
   *out = nullptr;
-  if (!tree || !parts || !cfg) return PIC_EINVAL;
+  if (n_inst < 1 || !trees || !parts || !cfg) return PIC_EINVAL;
   if (cfg->scheme != PIC_PIT && cfg->scheme != PIC_PIDT) return PIC_EINVAL;
   if (cfg->precision != PIC_FP64 && cfg->precision != PIC_FP32_SPLIT) return PIC_EINVAL;
-  if (parts->n < 0 || parts->n >= INT32_MAX || (parts->n > 0 && (!parts->x || !parts->v))) return PIC_EINVAL;
   if (cfg->sweeps < 0) return PIC_EINVAL;
-  if (parts->where != PIC_HOST && parts->where != PIC_DEVICE) return PIC_EINVAL;
-  if (parts->where == PIC_HOST) {
-    size_t m = (size_t)tree->d * parts->n;
-    if (tree->d == 2 || tree->d == 3)
-      for (size_t i = 0; i < m; ++i)
-        if (!std::isfinite(parts->x[i]) || !std::isfinite(parts->v[i])) return PIC_ERANGE;
+  int64_t n_total = 0;
+  std::vector<int64_t> poff(n_inst);
+  for (int32_t i = 0; i < n_inst; ++i) {
+    const pic_particles_desc &pp = parts[i];
+    if (pp.n < 0 || (pp.n > 0 && (!pp.x || !pp.v))) return PIC_EINVAL;
+    if (pp.where != PIC_HOST && pp.where != PIC_DEVICE) return PIC_EINVAL;
+    if (trees[i].d != 2 && trees[i].d != 3) return PIC_EINVAL;
+    if (pp.where == PIC_HOST) {
+      size_t m = (size_t)trees[i].d * pp.n;
+      for (size_t k = 0; k < m; ++k)
+        if (!std::isfinite(pp.x[k]) || !std::isfinite(pp.v[k])) return PIC_ERANGE;
+    }
+    poff[i] = n_total;
+    n_total += pp.n;
   }
+  if (n_total >= INT32_MAX) return PIC_EINVAL;
   pic_t h = new (std::nothrow) pic_s();
   if (!h) return PIC_ENOMEM;
   h->cfg = *cfg;
   h->scheme = cfg->scheme;
   h->split = cfg->precision == PIC_FP32_SPLIT;
-  h->n = parts->n;
+  h->n = n_total;
   h->stream = (cudaStream_t)cfg->stream;
   cudaGetDevice(&h->device);
   int rc;
   cudaError_t e = set_constants(h->stream);
   if (e != cudaSuccess) { rc = cuda_fail(h, e, "set_constants"); pic_destroy(h); return rc; }
-  if ((rc = install_tree(h, tree))) { pic_destroy(h); return rc; }
+  std::vector<double> qs(n_inst, cfg->q);
+  if (q)
+    for (int32_t i = 0; i < n_inst; ++i) qs[i] = q[i];
+  if ((rc = install_forest(h, trees, n_inst, qs))) { pic_destroy(h); return rc; }
+  if ((rc = set_particle_offsets(h, poff))) { pic_destroy(h); return rc; }
   e = set_kref(h->d, h->stream);
   if (e != cudaSuccess) { rc = cuda_fail(h, e, "set_kref"); pic_destroy(h); return rc; }
   if ((rc = alloc_state(h))) { pic_destroy(h); return rc; }
@@ -727,11 +838,33 @@ int pic_create(pic_t *out, const pic_tree_desc *tree, const pic_particles_desc *
     e = cudaMemcpy(h->ids[0], iota.data(), sizeof(int32_t) * h->n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { rc = cuda_fail(h, e, "ids"); pic_destroy(h); return rc; }
   }
-  if ((rc = load_particles64(h, parts->x, parts->v, parts->where))) { pic_destroy(h); return rc; }
+  if ((rc = load_particles64(h, parts, n_inst))) { pic_destroy(h); return rc; }
   int32_t err = 0;
   if ((rc = read_err(h, &err))) { pic_destroy(h); return rc; }
   if (err) { pic_destroy(h); return PIC_ERANGE; }
   *out = h;
+  return PIC_OK;
+}
+
+int pic_create(pic_t *out, const pic_tree_desc *tree, const pic_particles_desc *parts, const pic_config *cfg) {
+  return create_forest(out, 1, tree, parts, nullptr, cfg);
+}
+
+int pic_create_batch(pic_t *out, int32_t n_inst, const pic_tree_desc *trees, const pic_particles_desc *parts,
+                     const double *q, const pic_config *cfg) {
+  return create_forest(out, n_inst, trees, parts, q, cfg);
+}
+
+int pic_instances(pic_t h, int64_t *particle_start, int64_t *vertex_start, int64_t *bucket_start) {
+  if (check_handle(h)) return PIC_EINVAL;
+  const int32_t ni = h->dt.n_inst;
+  const int stride = h->scheme == PIC_PIT ? 1 : h->dt.nc;
+  for (int32_t i = 0; i <= ni; ++i) {
+    const bool end = i == ni;
+    if (particle_start) particle_start[i] = end ? h->n : h->inst[i].poff;
+    if (vertex_start) vertex_start[i] = end ? h->dt.n_vert : h->inst[i].vert_off;
+    if (bucket_start) bucket_start[i] = end ? h->dt.n_keys / stride : h->inst[i].key_off / stride;
+  }
   return PIC_OK;
 }
 
@@ -748,6 +881,7 @@ int pic_info(pic_t h, pic_info_t *o) {
   o->n_keys = h->dt.n_keys;
   o->uniform = h->dt.uniform;
   o->brick = h->brick ? 1 : 0;
+  o->n_instances = h->dt.n_inst;
   o->device_bytes = h->device_bytes;
   return PIC_OK;
 }
@@ -952,50 +1086,61 @@ int pic_phase_times(pic_t h, double *ms, int64_t *kernels) {
 
 int pic_leaf_table(pic_t h, int32_t *level, int64_t *coords) {
   if (check_handle(h)) return PIC_EINVAL;
-  const auto &t = h->ht;
-  for (int64_t l = 0; l < t.n_leaves; ++l) {
-    if (level) level[l] = t.leaf_level[l];
-    if (coords)
-      for (int a = 0; a < t.d; ++a) coords[l * t.d + a] = t.leaf_coords[l * t.d + a];
+  int64_t base = 0;
+  for (const auto &t : h->hts) {
+    for (int64_t l = 0; l < t.n_leaves; ++l) {
+      if (level) level[base + l] = t.leaf_level[l];
+      if (coords)
+        for (int a = 0; a < t.d; ++a) coords[(base + l) * t.d + a] = t.leaf_coords[l * t.d + a];
+    }
+    base += t.n_leaves;
   }
   return PIC_OK;
 }
 
 int pic_vertex_table(pic_t h, int64_t *pos) {
   if (check_handle(h) || !pos) return PIC_EINVAL;
-  const auto &t = h->ht;
-  for (int64_t v = 0; v < t.n_vert; ++v) {
-    int64_t k = t.uniform ? v : t.vert_key[v];
-    for (int a = 0; a < t.d; ++a) {
-      pos[a * t.n_vert + v] = k % t.M;
-      k /= t.M;
+  const int64_t nv = h->dt.n_vert;
+  int64_t base = 0;
+  for (const auto &t : h->hts) {
+    for (int64_t v = 0; v < t.n_vert; ++v) {
+      int64_t k = t.uniform ? v : t.vert_key[v];
+      for (int a = 0; a < t.d; ++a) {
+        pos[a * nv + base + v] = k % t.M;
+        k /= t.M;
+      }
     }
+    base += t.n_vert;
   }
   return PIC_OK;
 }
 
 int pic_pidt_table(pic_t h, int32_t *level, int64_t *j) {
   if (check_handle(h)) return PIC_EINVAL;
-  const auto &t = h->ht;
-  for (int64_t v = 0; v < t.n_pv; ++v) {
-    if (t.uniform) {
-      if (level) level[v] = t.depth;
-      int64_t k = v;
-      for (int a = 0; a < t.d; ++a) {
-        if (j) j[v * t.d + a] = k % t.M;
-        k /= t.M;
+  int64_t base = 0;
+  for (const auto &t : h->hts) {
+    for (int64_t v = 0; v < t.n_pv; ++v) {
+      if (t.uniform) {
+        if (level) level[base + v] = t.depth;
+        int64_t k = v;
+        for (int a = 0; a < t.d; ++a) {
+          if (j) j[(base + v) * t.d + a] = k % t.M;
+          k /= t.M;
+        }
+      } else {
+        if (level) level[base + v] = t.pv_level[v];
+        if (j)
+          for (int a = 0; a < t.d; ++a) j[(base + v) * t.d + a] = t.pv_j[v * t.d + a];
       }
-    } else {
-      if (level) level[v] = t.pv_level[v];
-      if (j)
-        for (int a = 0; a < t.d; ++a) j[v * t.d + a] = t.pv_j[v * t.d + a];
     }
+    base += t.n_pv;
   }
   return PIC_OK;
 }
 
 int pic_retree(pic_t h, const pic_tree_desc *tree) {
   if (check_handle(h) || !tree) return PIC_EINVAL;
+  if (h->dt.n_inst > 1) return fail(h, PIC_ESTATE, "re-tree of batched handles is not supported");
   if (tree->d != h->d) return fail(h, PIC_EINVAL, "tree dimension differs from the handle");
   int rc;
   if ((rc = ensure_leaf(h))) return rc;
@@ -1050,6 +1195,7 @@ int pic_retree(pic_t h, const pic_tree_desc *tree) {
 
 int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax) {
   if (check_handle(h)) return PIC_EINVAL;
+  if (h->dt.n_inst > 1) return fail(h, PIC_ESTATE, "re-refinement of batched handles is not supported");
   const int d = h->d;
   if (ppc < 0 || dmin < 0 || dmin > dmax || dmax > (d == 3 ? 6 : 10))
     return fail(h, PIC_EINVAL, "adapt needs 0 <= dmin <= dmax <= 6 (3D) or 10 (2D)");
@@ -1121,9 +1267,13 @@ int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax) {
 
 int pic_tree_flags(pic_t h, uint8_t *flags, int64_t *n_nodes) {
   if (check_handle(h)) return PIC_EINVAL;
-  if (n_nodes) *n_nodes = h->ht.n_nodes;
-  if (flags)
-    for (int64_t i = 0; i < h->ht.n_nodes; ++i) flags[i] = h->ht.child0[i] >= 0 ? 1 : 0;
+  int64_t total = 0;
+  for (const auto &t : h->hts) {
+    if (flags)
+      for (int64_t i = 0; i < t.n_nodes; ++i) flags[total + i] = t.child0[i] >= 0 ? 1 : 0;
+    total += t.n_nodes;
+  }
+  if (n_nodes) *n_nodes = total;
   return PIC_OK;
 }
 

@@ -50,7 +50,7 @@ class Info(C.Structure):
     _fields_ = [("d", C.c_int32), ("scheme", C.c_int32), ("precision", C.c_int32), ("depth", C.c_int32),
                 ("n_particles", C.c_int64), ("n_leaves", C.c_int64), ("n_vertices", C.c_int64),
                 ("n_buckets", C.c_int64), ("n_keys", C.c_int64), ("uniform", C.c_int32),
-                ("brick", C.c_int32), ("device_bytes", C.c_int64)]
+                ("brick", C.c_int32), ("n_instances", C.c_int32), ("device_bytes", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -65,6 +65,9 @@ SIGNATURES = [
     ("pic_create", C.c_int, [C.POINTER(C.c_void_p), C.POINTER(TreeDesc), C.POINTER(ParticlesDesc),
                              C.POINTER(Config)]),
     ("pic_destroy", None, [C.c_void_p]),
+    ("pic_create_batch", C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(TreeDesc),
+                                   C.POINTER(ParticlesDesc), C.c_void_p, C.POINTER(Config)]),
+    ("pic_instances", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_strerror", C.c_char_p, [C.c_int]),
     ("pic_last_error", C.c_char_p, [C.c_void_p]),
     ("pic_info", C.c_int, [C.c_void_p, C.POINTER(Info)]),
@@ -160,6 +163,59 @@ class Pic:
         self.scheme = scheme
         self.precision = precision
         self._info = self.info()
+
+    @classmethod
+    def batch(cls, d: int, flags_list, xs, vs, qs=None, *, scheme: int = PIT, precision: int = FP64,
+              q: float = -1.0, qm: float = -1.0, ion: float = 1.0, sweeps: int = 100, omega: float = 0.8,
+              track_ids: bool = True, stream=None, path: int = PATH_AUTO) -> "Pic":
+        """Several independent plasmas (uniform trees) in one handle."""
+        self = cls.__new__(cls)
+        self.lib = load()
+        self.d = d
+        n_inst = len(flags_list)
+        self._keep = []
+        trees = (TreeDesc * n_inst)()
+        parts = (ParticlesDesc * n_inst)()
+        for i in range(n_inst):
+            f = np.ascontiguousarray(flags_list[i], dtype=np.uint8)
+            x = xs[i]
+            v = vs[i]
+            if isinstance(x, np.ndarray):
+                x = np.ascontiguousarray(x, dtype=np.float64)
+                v = np.ascontiguousarray(v, dtype=np.float64)
+            self._keep += [f, x, v]
+            trees[i] = TreeDesc(d, len(f), f.ctypes.data_as(C.c_void_p))
+            xp, where = _ptr(x)
+            vp, _ = _ptr(v)
+            parts[i] = ParticlesDesc(int(x.shape[1]), xp, vp, where)
+        qarr = None
+        if qs is not None:
+            qarr = np.ascontiguousarray(qs, dtype=np.float64)
+            self._keep.append(qarr)
+        st = C.c_void_p(stream.cuda_stream) if stream is not None and hasattr(stream, "cuda_stream") else \
+            C.c_void_p(stream)
+        self.cfg = Config(scheme, precision, q, qm, ion, sweeps, omega, 1 if track_ids else 0, st, path)
+        h = C.c_void_p()
+        rc = self.lib.pic_create_batch(C.byref(h), n_inst, trees, parts,
+                                       None if qarr is None else qarr.ctypes.data_as(C.c_void_p),
+                                       C.byref(self.cfg))
+        if rc != 0:
+            raise PicError(rc, self.lib.pic_strerror(rc).decode())
+        self.h = h
+        self.n = sum(int(p.n) for p in parts)
+        self.scheme = scheme
+        self.precision = precision
+        self._info = self.info()
+        return self
+
+    def instances(self):
+        """(particle_start, vertex_start, bucket_start), each n_instances + 1 long."""
+        ni = int(self._info.n_instances)
+        ps = np.zeros(ni + 1, np.int64)
+        vs = np.zeros(ni + 1, np.int64)
+        bs = np.zeros(ni + 1, np.int64)
+        self._check(self.lib.pic_instances(self.h, _ptr(ps)[0], _ptr(vs)[0], _ptr(bs)[0]))
+        return ps, vs, bs
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

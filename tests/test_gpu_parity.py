@@ -300,3 +300,44 @@ def test_adapt_matches_oracle(d, base, ppc, dmin, dmax, n, scheme, precision):
     # the adapted handle keeps stepping
     g.step(0.05)
     g.sync()
+
+
+# ---------------------------------------------------------------------------
+# a10 batches of independent instances
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scheme", [pic.PIT, pic.PIDT])
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_SPLIT])
+def test_batch_equals_single_instances(scheme, precision):
+    """Uneven instances (particle counts, depths 3-5) in one handle give the
+    same keys, buckets, charges and states as separate handles."""
+    insts = W.batched_langmuir(n_inst=7, n_min=300, n_max=30_000)
+    kw = dict(scheme=scheme, precision=precision, sweeps=20, omega=0.8)
+    g = pic.Pic.batch(2, [w.flags for w in insts], [w.x for w in insts], [w.v for w in insts],
+                      qs=[w.q for w in insts], **kw)
+    assert g.info().n_instances == len(insts)
+    singles = [pic.Pic(2, w.flags, w.x, w.v, q=w.q, **kw) for w in insts]
+    for _ in range(3):
+        g.step(0.1)
+        for s1 in singles:
+            s1.step(0.1)
+    g.sync()
+    ps, vs, bs = g.instances()
+    gstate = g.get_state()
+    gstart, gids = g.bins()
+    gkeys = g.keys()
+    gQ = g.deposit()
+    for i, s1 in enumerate(singles):
+        sl = slice(ps[i], ps[i + 1])
+        st1 = s1.get_state()
+        tol = 0.0 if precision == pic.FP32_SPLIT else 1e-12
+        if precision == pic.FP32_SPLIT:
+            assert np.array_equal(gstate[0][sl] - 0, st1[0] + (gstate[0][sl][0] - st1[0][0]))
+        for a, b in zip(gstate[1:], st1[1:]):
+            assert np.allclose(a[:, sl], b, rtol=tol, atol=tol)
+        start1, ids1 = s1.bins()
+        assert np.array_equal(gstart[bs[i]:bs[i + 1] + 1] - ps[i], start1)
+        assert np.array_equal(gids[sl] - ps[i], ids1)
+        k1 = s1.keys()
+        assert np.array_equal(gkeys[sl] - gkeys[sl].min() + k1.min(), k1)
+        assert np.allclose(gQ[vs[i]:vs[i + 1]], s1.deposit(), rtol=1e-6 if tol == 0 else 1e-12, atol=1e-12)
