@@ -331,8 +331,8 @@ def test_batch_equals_single_instances(scheme, precision):
         sl = slice(ps[i], ps[i + 1])
         st1 = s1.get_state()
         tol = 0.0 if precision == pic.FP32_SPLIT else 1e-12
-        if precision == pic.FP32_SPLIT:
-            assert np.array_equal(gstate[0][sl] - 0, st1[0] + (gstate[0][sl][0] - st1[0][0]))
+        loff = gstate[0][sl][0] - st1[0][0]            # the instance's first leaf in the batch
+        assert np.array_equal(gstate[0][sl] - loff, st1[0])
         for a, b in zip(gstate[1:], st1[1:]):
             assert np.allclose(a[:, sl], b, rtol=tol, atol=tol)
         start1, ids1 = s1.bins()
