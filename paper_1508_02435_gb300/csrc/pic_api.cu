@@ -2,6 +2,7 @@
 // orchestration of one PIT/PIDT particle step on the handle's stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -352,7 +353,8 @@ int alloc_state(pic_t h) {
   if ((rc = dalloc(h, sb, &h->block_sum, (nv + 255) / 256 + 1))) return rc;
   if ((rc = dalloc(h, sb, &h->total, 2 + h->dt.n_inst))) return rc;
   if ((rc = dalloc(h, sb, &h->resid2, 2))) return rc;
-  if ((rc = dalloc(h, sb, &p, sizeof(double) * d * n))) return rc;
+  // FP64 staging: particle arrays (d * n) and widened vertex fields (d * n_vert)
+  if ((rc = dalloc(h, sb, &p, sizeof(double) * d * std::max(n, nv)))) return rc;
   h->Ep = p;
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(h->V, 0, fs * nv, s));
