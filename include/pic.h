@@ -161,6 +161,27 @@ PIC_API int pic_step(pic_t h, double dt, pic_solve_fn hook, void *user);
  * solve: deposit of the current positions, gather + push + key, re-bin. */
 PIC_API int pic_step_fixed_field(pic_t h, double dt);
 
+/* Capture the fixed-field step (deposit when due, gather + push + key,
+ * re-bin) as CUDA graphs after one ordinary step; the handle's stream must
+ * not be the legacy default stream.  Two graphs are kept because a step
+ * swaps ping-pong buffers.  Any call that rebuilds buffers (re-tree, tuning)
+ * drops them. */
+PIC_API int pic_graph_capture(pic_t h, double dt);
+
+/* Replay `steps` captured steps on the handle's stream (asynchronous). */
+PIC_API int pic_graph_launch(pic_t h, int32_t steps);
+
+/* Tuning = {path (1 brick, 0 generic), threads per block of the push, of
+ * the per-leaf deposit, of the per-vertex kernels}.  pic_autotune times
+ * every candidate for `trials` fixed-field steps on the handle's own
+ * particles, keeps the fastest and restores the particle state; the chosen
+ * values go to tuned[4] (may be NULL).  pic_set_tuning applies stored values
+ * (for example from a cache); pic_get_tuning reads the current ones. */
+PIC_API int pic_autotune(pic_t h, double dt, int32_t trials, int32_t *tuned);
+PIC_API int pic_set_tuning(pic_t h, const int32_t *tuned);
+PIC_API int pic_get_tuning(pic_t h, int32_t *tuned);
+
+/* Wait for the handle's stream; returns the sticky device error if any. */
 /* Wait for the handle's stream; returns the sticky device error if any. */
 PIC_API int pic_sync(pic_t h);
 

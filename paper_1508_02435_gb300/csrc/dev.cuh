@@ -29,6 +29,7 @@ struct InstInfo {
 struct DevTree {
   int d, nch, nc, depth, uniform, scheme;
   int32_t n_inst;
+  int32_t block_push, block_leaf, block_vert;  // threads per block (autotuned; 0 = 256)
   const InstInfo *inst;
   const int32_t *inst_of_leaf, *inst_of_vert;
   int64_t n_leaves, n_vert, n_pv, n_keys;

@@ -37,6 +37,8 @@ int64_t launches() { return g_launches.load(); }
 void count_launches(int64_t k) { g_launches.fetch_add(k); }
 #define COUNT(k) g_launches.fetch_add(k)
 
+static inline int bsz(int32_t b) { return b > 0 ? b : kBlock; }
+
 static inline unsigned grid_for(int64_t n, int block = kBlock) {
   int64_t g = (n + block - 1) / block;
   if (g < 1) g = 1;
@@ -915,8 +917,8 @@ void launch_rekey32(const DevTree &t, const int32_t *leaf, const float *o, int64
 }
 
 void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *mover_words,
-                      int32_t *block_movers, cudaStream_t s) {
-  { COUNT(1); k_count_all<<<grid_for(n), kBlock, 0, s>>>(key, n, count, mover_words, block_movers); }
+                      int32_t *block_movers, int block, cudaStream_t s) {
+  { COUNT(1); k_count_all<<<grid_for(n, block), block, 0, s>>>(key, n, count, mover_words, block_movers); }
 }
 
 void launch_fine_keys(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n, int dmax,
@@ -965,9 +967,9 @@ __global__ void k_inst_sum(DevTree t, const T *Q, double *out) {
 void launch_vertex_charge(const DevTree &t, bool split, const void *part, void *Q, double *block_sum,
                           double *total, cudaStream_t s) {
   if (split) {
-    { COUNT(1); k_vertex_charge<float><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const float *)part, (float *)Q, block_sum); }
+    { COUNT(1); k_vertex_charge<float><<<grid_for(t.n_vert, bsz(t.block_vert)), bsz(t.block_vert), 0, s>>>(t, (const float *)part, (float *)Q, block_sum); }
   } else {
-    { COUNT(1); k_vertex_charge<double><<<grid_for(t.n_vert), kBlock, 0, s>>>(t, (const double *)part, (double *)Q, block_sum); }
+    { COUNT(1); k_vertex_charge<double><<<grid_for(t.n_vert, bsz(t.block_vert)), bsz(t.block_vert), 0, s>>>(t, (const double *)part, (double *)Q, block_sum); }
   }
   if (t.n_inst > 1) {
     COUNT(2);
@@ -978,16 +980,16 @@ void launch_vertex_charge(const DevTree &t, bool split, const void *part, void *
     k_sum_blocks<<<1, 1024, 0, s>>>(total + 1, t.n_inst, total);
   } else {
     COUNT(1);
-    k_sum_blocks<<<1, 1024, 0, s>>>(block_sum, grid_for(t.n_vert), total);
+    k_sum_blocks<<<1, 1024, 0, s>>>(block_sum, grid_for(t.n_vert, bsz(t.block_vert)), total);
   }
 }
 
 void launch_deposit(const DevTree &t, bool split, const int32_t *start, const void *pos, int64_t n, void *part,
                     void *Q, double *block_sum, double *total, cudaStream_t s) {
   if (split) {
-    { COUNT(1); k_leaf_partials<true><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part); }
+    { COUNT(1); k_leaf_partials<true><<<grid_for(t.n_leaves, bsz(t.block_leaf)), bsz(t.block_leaf), 0, s>>>(t, start, pos, n, part); }
   } else {
-    { COUNT(1); k_leaf_partials<false><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, pos, n, part); }
+    { COUNT(1); k_leaf_partials<false><<<grid_for(t.n_leaves, bsz(t.block_leaf)), bsz(t.block_leaf), 0, s>>>(t, start, pos, n, part); }
   }
   launch_vertex_charge(t, split, part, Q, block_sum, total, s);
 }
@@ -1025,11 +1027,11 @@ void launch_efield(const DevTree &t, bool split, const void *V, void *E, cudaStr
 }
 
 void launch_push64(const DevTree &t, const Push64Args &a, cudaStream_t s) {
-  { COUNT(1); k_push64<<<grid_for(a.n), kBlock, 0, s>>>(t, a); }
+  { COUNT(1); k_push64<<<grid_for(a.n, bsz(t.block_push)), bsz(t.block_push), 0, s>>>(t, a); }
 }
 
 void launch_push32(const DevTree &t, const Push32Args &a, cudaStream_t s) {
-  { COUNT(1); k_push32<<<grid_for(a.n), kBlock, 0, s>>>(t, a); }
+  { COUNT(1); k_push32<<<grid_for(a.n, bsz(t.block_push)), bsz(t.block_push), 0, s>>>(t, a); }
 }
 
 int64_t scan_tiles_needed(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
@@ -1047,16 +1049,17 @@ void launch_rebin(const RebinArgs &r, cudaStream_t s) {
   // bucket offsets
   launch_exclusive_scan(r.count, r.n_keys, r.new_start, r.tile_sums, r.scalars + 0, s);
   // mover list in storage order
-  unsigned gp = grid_for(r.n);
+  const int bp = bsz(r.block);
+  unsigned gp = grid_for(r.n, bp);
   launch_exclusive_scan(r.block_movers, gp, r.block_offsets, r.tile_sums2, r.scalars + 1, s);
   if (r.old_start)
     { COUNT(1); k_stayers<<<grid_for(r.n_keys), kBlock, 0, s>>>(r.old_start, r.keyn, r.new_start, r.n_keys, r.perm, r.n_stay,
                                                     r.scalars + 2); }
   else
     cudaMemsetAsync(r.n_stay, 0, sizeof(int32_t) * r.n_keys, s);
-  { COUNT(1); k_compact_movers<<<gp, kBlock, 0, s>>>(r.mover_words, r.block_offsets, r.n, r.movers); }
+  { COUNT(1); k_compact_movers<<<gp, bp, 0, s>>>(r.mover_words, r.block_offsets, r.n, r.movers); }
   cudaMemsetAsync(r.cursor, 0, sizeof(int32_t) * r.n_keys, s);
-  { COUNT(1); k_mover_slots<<<gp, kBlock, 0, s>>>(r.movers, r.scalars + 1, r.keyn, r.new_start, r.n_stay, r.cursor, r.perm); }
+  { COUNT(1); k_mover_slots<<<gp, bp, 0, s>>>(r.movers, r.scalars + 1, r.keyn, r.new_start, r.n_stay, r.cursor, r.perm); }
   { COUNT(1); k_sort_segments<<<grid_for(r.n_keys), kBlock, 0, s>>>(r.new_start, r.n_stay, r.n_keys, r.perm); }
 }
 

@@ -50,10 +50,12 @@ struct RebinArgs {
   int32_t *block_offsets, *movers, *n_stay, *cursor, *perm;
   int32_t *tile_sums, *tile_sums2;
   int32_t *scalars;             // [0] n, [1] movers, [2] max bucket
+  int block;                     // threads per block of the push (ballot words, block counts)
 };
 
 // Kernels launched by this library so far (all handles of the process).
 int64_t launches();
+void count_launches(int64_t k);
 
 // Brick path (uniform trees, PIT, split precision): see brick.cu.
 struct BrickGeom {
@@ -121,7 +123,7 @@ void launch_init32(const DevTree &t, const double *x, const double *v, int64_t n
 void launch_rekey32(const DevTree &t, const int32_t *leaf, const float *o, int64_t n, int32_t *key, int32_t *err,
                     cudaStream_t s);
 void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *mover_words,
-                      int32_t *block_movers, cudaStream_t s);
+                      int32_t *block_movers, int block, cudaStream_t s);
 // Re-refinement: depth-first cell index on level dmax per particle; cells of
 // level m (index key / div) holding more than ppc particles as a bitmap.
 void launch_fine_keys(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n, int dmax,

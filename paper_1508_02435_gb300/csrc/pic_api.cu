@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -60,8 +61,19 @@ struct pic_s {
 
   // brick path (uniform tree, PIT, split precision)
   bool brick = false;
+  bool brick_ok = false;    // the brick path applies (its buffers exist)
   bool leaf_stale = false;  // leaf[0] not yet expanded from the offsets
   bool q_valid = false;     // Q holds the charges of the current positions
+
+  // CUDA graphs of one fixed-field step: [0] from the current buffer
+  // assignment, [1] from the swapped one (the step alternates ping-pong offsets)
+  struct HostView {  // host-side buffer assignment a step swaps
+    int32_t *start_cur, *start_new, *ids0, *ids1;
+    bool leaf_stale, q_valid;
+  };
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  HostView graph_pre[2]{}, graph_post[2]{};
+  int64_t graph_kernels = 0;
   BrickGeom bg{};
   std::vector<DevBuf> brick_bufs;
   uint16_t *tcode = nullptr;
@@ -307,7 +319,7 @@ int alloc_state(pic_t h) {
   const int64_t n = h->n, d = h->d;
   const size_t fs = h->split ? sizeof(float) : sizeof(double);
   const int64_t nk = h->dt.n_keys, nv = h->dt.n_vert, nl = h->dt.n_leaves;
-  const int64_t nblk = (n + 255) / 256 + 1;
+  const int64_t nblk = (n + 127) / 128 + 1;  // blocks of the smallest tuned block size
   int rc;
   for (int s = 0; s < 2; ++s) {
     char *p;
@@ -332,7 +344,7 @@ int alloc_state(pic_t h) {
   if ((rc = dalloc(h, sb, &h->movers, n))) return rc;
   if ((rc = dalloc(h, sb, &h->block_movers, nblk))) return rc;
   if ((rc = dalloc(h, sb, &h->block_offsets, nblk + 1))) return rc;
-  if ((rc = dalloc(h, sb, &h->mover_words, nblk * 8))) return rc;
+  if ((rc = dalloc(h, sb, &h->mover_words, (n + 31) / 32 + 64))) return rc;
   if ((rc = dalloc(h, sb, &h->tile_sums, scan_tiles_needed(nk) + 1))) return rc;
   if ((rc = dalloc(h, sb, &h->tile_sums2, scan_tiles_needed(nblk) + 1))) return rc;
   if ((rc = dalloc(h, sb, &h->scalars, 8))) return rc;
@@ -350,7 +362,7 @@ int alloc_state(pic_t h) {
   h->Vtmp = p;
   if ((rc = dalloc(h, sb, &p, fs * nv * d))) return rc;
   h->E = p;
-  if ((rc = dalloc(h, sb, &h->block_sum, (nv + 255) / 256 + 1))) return rc;
+  if ((rc = dalloc(h, sb, &h->block_sum, (nv + 127) / 128 + 1))) return rc;
   if ((rc = dalloc(h, sb, &h->total, 2 + h->dt.n_inst))) return rc;
   if ((rc = dalloc(h, sb, &h->resid2, 2))) return rc;
   // FP64 staging: particle arrays (d * n) and widened vertex fields (d * n_vert)
@@ -417,6 +429,7 @@ struct PhaseScope {
 int setup_brick(pic_t h) {
   free_bufs(h, h->brick_bufs);
   h->brick = false;
+  h->brick_ok = false;
   const auto &t = h->ht;
   if (h->cfg.path != PIC_PATH_AUTO || !t.uniform || h->scheme != PIC_PIT || !h->split || t.depth < 3 ||
       h->dt.n_inst > 1)
@@ -468,6 +481,7 @@ int setup_brick(pic_t h) {
   CK(brick_configure(g));
   h->bg = g;
   h->brick = true;
+  h->brick_ok = true;
   return PIC_OK;
 }
 
@@ -575,6 +589,7 @@ int rebin_and_gather(pic_t h, const int32_t *old_start) {
   r.tile_sums = h->tile_sums;
   r.tile_sums2 = h->tile_sums2;
   r.scalars = h->scalars;
+  r.block = h->dt.block_push;
   {
     PhaseScope ps(h, PIC_PHASE_REBIN);
     launch_rebin(r, s);
@@ -605,7 +620,7 @@ int bin_fresh(pic_t h) {
   h->q_valid = false;
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(h->count, 0, sizeof(int32_t) * h->dt.n_keys, s));
-  launch_count_all(h->key[1], h->n, h->count, h->mover_words, h->block_movers, s);
+  launch_count_all(h->key[1], h->n, h->count, h->mover_words, h->block_movers, h->dt.block_push, s);
   return rebin_and_gather(h, nullptr);
 }
 
@@ -689,6 +704,14 @@ int push_and_rebin(pic_t h, double dt) {
 }
 
 int check_handle(pic_t h) { return h ? PIC_OK : PIC_EINVAL; }
+
+void drop_graphs(pic_t h) {
+  for (auto &g : h->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
 
 
 
@@ -783,6 +806,7 @@ void pic_destroy(pic_t h) {
     cudaEventDestroy(p.b);
   }
   for (auto e : h->event_pool) cudaEventDestroy(e);
+  drop_graphs(h);
   free_bufs(h, h->brick_bufs);
   free_bufs(h, h->state_bufs);
   free_bufs(h, h->tree_bufs);
@@ -919,6 +943,202 @@ int pic_step_fixed_field(pic_t h, double dt) {
   return PIC_OK;
 }
 
+pic_s::HostView host_view(pic_t h) {
+  return {h->start_cur, h->start_new, h->ids[0], h->ids[1], h->leaf_stale, h->q_valid};
+}
+
+void set_host_view(pic_t h, const pic_s::HostView &v) {
+  h->start_cur = v.start_cur;
+  h->start_new = v.start_new;
+  h->ids[0] = v.ids0;
+  h->ids[1] = v.ids1;
+  h->leaf_stale = v.leaf_stale;
+  h->q_valid = v.q_valid;
+}
+
+int pic_graph_capture(pic_t h, double dt) {
+  if (check_handle(h)) return PIC_EINVAL;
+  if (!h->stream) return fail(h, PIC_ESTATE, "graph capture needs a non-default stream");
+  if (h->prof) return fail(h, PIC_ESTATE, "stop profiling before capturing");
+  drop_graphs(h);
+  int rc;
+  // one ordinary step first, so that the captured steps start from the state
+  // every later step starts from (brick path: charges already deposited)
+  if ((rc = deposit(h)) || (rc = push_and_rebin(h, dt))) return rc;
+  h->step++;
+  if ((rc = ensure_leaf(h))) return rc;  // generic path: no expansion inside the graph
+  CK(cudaStreamSynchronize(h->stream));
+  const pic_s::HostView start = host_view(h);
+  const int64_t k0 = launches();
+  for (int g = 0; g < 2; ++g) {
+    h->graph_pre[g] = host_view(h);
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    rc = deposit(h);
+    if (!rc) rc = push_and_rebin(h, dt);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    h->graph_post[g] = host_view(h);
+    if (!rc && e == cudaSuccess) e = cudaGraphInstantiate(&h->graph[g], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc || e != cudaSuccess) {
+      drop_graphs(h);
+      set_host_view(h, start);  // nothing captured ran
+      return rc ? rc : cuda_fail(h, e, "graph capture");
+    }
+  }
+  set_host_view(h, start);
+  h->graph_kernels = (launches() - k0) / 2;
+  return PIC_OK;
+}
+
+int pic_graph_launch(pic_t h, int32_t steps) {
+  if (check_handle(h) || steps < 0) return PIC_EINVAL;
+  if (!h->graph[0]) return fail(h, PIC_ESTATE, "no captured step (pic_graph_capture)");
+  for (int32_t i = 0; i < steps; ++i) {
+    int rc;
+    if (!h->graph_pre[0].leaf_stale && (rc = ensure_leaf(h))) return rc;
+    const auto cur = host_view(h);
+    int g = -1;
+    for (int k = 0; k < 2; ++k) {
+      const auto &p = h->graph_pre[k];
+      if (p.start_cur == cur.start_cur && p.ids0 == cur.ids0 && (p.q_valid || !cur.q_valid)) g = k;
+    }
+    if (g < 0) return fail(h, PIC_ESTATE, "the state no longer matches the captured step; capture again");
+    PhaseScope ps(h, PIC_PHASE_PUSH);
+    CK(cudaGraphLaunch(h->graph[g], h->stream));
+    count_launches(h->graph_kernels);
+    set_host_view(h, h->graph_post[g]);
+    h->step++;
+  }
+  return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuning: path (brick or generic) and threads per block
+// ---------------------------------------------------------------------------
+
+struct Snapshot {
+  std::vector<DevBuf> bufs;
+  void *pos = nullptr, *vel = nullptr;
+  int32_t *leaf = nullptr, *key = nullptr, *ids = nullptr, *start = nullptr;
+};
+
+int snapshot_take(pic_t h, Snapshot &sn) {
+  const size_t fs = h->split ? sizeof(float) : sizeof(double);
+  const int64_t n = h->n, m = n * h->d, nk = h->dt.n_keys;
+  char *p, *q;
+  int rc;
+  if ((rc = dalloc(h, sn.bufs, &p, fs * m)) || (rc = dalloc(h, sn.bufs, &q, fs * m)) ||
+      (rc = dalloc(h, sn.bufs, &sn.leaf, n)) || (rc = dalloc(h, sn.bufs, &sn.key, n)) ||
+      (rc = dalloc(h, sn.bufs, &sn.ids, n)) || (rc = dalloc(h, sn.bufs, &sn.start, nk + 1)))
+    return rc;
+  sn.pos = p;
+  sn.vel = q;
+  cudaStream_t s = h->stream;
+  CK(cudaMemcpyAsync(sn.pos, h->pos[0], fs * m, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(sn.vel, h->vel[0], fs * m, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(sn.leaf, h->leaf[0], sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(sn.key, h->key[0], sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(sn.ids, h->ids[0], sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(sn.start, h->start_cur, sizeof(int32_t) * (nk + 1), cudaMemcpyDeviceToDevice, s));
+  return PIC_OK;
+}
+
+int snapshot_restore(pic_t h, const Snapshot &sn) {
+  const size_t fs = h->split ? sizeof(float) : sizeof(double);
+  const int64_t n = h->n, m = n * h->d, nk = h->dt.n_keys;
+  cudaStream_t s = h->stream;
+  CK(cudaMemcpyAsync(h->pos[0], sn.pos, fs * m, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->vel[0], sn.vel, fs * m, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->leaf[0], sn.leaf, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->key[0], sn.key, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->ids[0], sn.ids, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->start_cur, sn.start, sizeof(int32_t) * (nk + 1), cudaMemcpyDeviceToDevice, s));
+  h->leaf_stale = false;
+  h->q_valid = false;
+  return PIC_OK;
+}
+
+int apply_tuning(pic_t h, const int32_t *t) {
+  if (t[0] == 1 && !h->brick_ok) return fail(h, PIC_EINVAL, "the brick path does not apply to this handle");
+  for (int i = 1; i < 4; ++i)
+    if (t[i] != 128 && t[i] != 256 && t[i] != 512) return fail(h, PIC_EINVAL, "block sizes are 128, 256 or 512");
+  int rc;
+  if ((rc = ensure_leaf(h))) return rc;
+  drop_graphs(h);
+  h->brick = t[0] == 1;
+  h->dt.block_push = t[1];
+  h->dt.block_leaf = t[2];
+  h->dt.block_vert = t[3];
+  return PIC_OK;
+}
+
+int pic_set_tuning(pic_t h, const int32_t *tuned) {
+  if (check_handle(h) || !tuned) return PIC_EINVAL;
+  return apply_tuning(h, tuned);
+}
+
+int pic_get_tuning(pic_t h, int32_t *tuned) {
+  if (check_handle(h) || !tuned) return PIC_EINVAL;
+  tuned[0] = h->brick ? 1 : 0;
+  tuned[1] = h->dt.block_push > 0 ? h->dt.block_push : 256;
+  tuned[2] = h->dt.block_leaf > 0 ? h->dt.block_leaf : 256;
+  tuned[3] = h->dt.block_vert > 0 ? h->dt.block_vert : 256;
+  return PIC_OK;
+}
+
+int pic_autotune(pic_t h, double dt, int32_t trials, int32_t *tuned) {
+  if (check_handle(h)) return PIC_EINVAL;
+  if (trials < 1) trials = 1;
+  int rc;
+  if ((rc = ensure_leaf(h))) return rc;
+  const bool prof = h->prof;
+  h->prof = false;
+  Snapshot sn;
+  if ((rc = snapshot_take(h, sn))) {
+    free_bufs(h, sn.bufs);
+    h->prof = prof;
+    return rc;
+  }
+  std::vector<std::array<int32_t, 4>> cands;
+  if (h->brick_ok) cands.push_back({1, 256, 256, 256});
+  for (int32_t bp : {128, 256, 512})
+    for (int32_t bl : {128, 256})
+      cands.push_back({0, bp, bl, 256});
+  cudaEvent_t e0 = take_event(h), e1 = take_event(h);
+  float best = 1e30f;
+  std::array<int32_t, 4> pick = cands[0];
+  for (const auto &c : cands) {
+    if ((rc = apply_tuning(h, c.data())) || (rc = snapshot_restore(h, sn))) break;
+    if ((rc = deposit(h)) || (rc = push_and_rebin(h, dt))) break;  // warm-up
+    CK(cudaEventRecord(e0, h->stream));
+    for (int32_t i = 0; i < trials && !rc; ++i) {
+      rc = deposit(h);
+      if (!rc) rc = push_and_rebin(h, dt);
+    }
+    if (rc) break;
+    CK(cudaEventRecord(e1, h->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  h->event_pool.push_back(e0);
+  h->event_pool.push_back(e1);
+  int rc2 = apply_tuning(h, pick.data());
+  if (!rc2) rc2 = snapshot_restore(h, sn);
+  if (!rc2) rc2 = cudaStreamSynchronize(h->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+  free_bufs(h, sn.bufs);
+  h->prof = prof;
+  if (rc) return rc;
+  if (rc2) return rc2;
+  if (tuned) std::copy(pick.begin(), pick.end(), tuned);
+  return PIC_OK;
+}
+
 int pic_sync(pic_t h) {
   if (check_handle(h)) return PIC_EINVAL;
   int32_t err = 0;
@@ -1027,6 +1247,7 @@ int pic_get_state(pic_t h, int32_t *leaf, void *x_or_o, void *v, int32_t where) 
 
 int pic_set_state(pic_t h, const int32_t *leaf, const void *x_or_o, const void *v, int32_t where) {
   if (check_handle(h) || !x_or_o || !v) return PIC_EINVAL;
+  drop_graphs(h);
   if (h->split && !leaf) return fail(h, PIC_EINVAL, "split state needs the leaf array");
   const size_t fs = h->split ? sizeof(float) : sizeof(double);
   const size_t m = (size_t)h->n * h->d;
@@ -1143,6 +1364,7 @@ int pic_pidt_table(pic_t h, int32_t *level, int64_t *j) {
 int pic_retree(pic_t h, const pic_tree_desc *tree) {
   if (check_handle(h) || !tree) return PIC_EINVAL;
   if (h->dt.n_inst > 1) return fail(h, PIC_ESTATE, "re-tree of batched handles is not supported");
+  drop_graphs(h);
   if (tree->d != h->d) return fail(h, PIC_EINVAL, "tree dimension differs from the handle");
   int rc;
   if ((rc = ensure_leaf(h))) return rc;

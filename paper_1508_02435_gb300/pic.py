@@ -85,6 +85,11 @@ SIGNATURES = [
     ("pic_set_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
     ("pic_stats", C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     ("pic_profile", C.c_int, [C.c_void_p, C.c_int32]),
+    ("pic_graph_capture", C.c_int, [C.c_void_p, C.c_double]),
+    ("pic_graph_launch", C.c_int, [C.c_void_p, C.c_int32]),
+    ("pic_autotune", C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p]),
+    ("pic_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("pic_get_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
     ("pic_phase_times", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_leaf_table", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_vertex_table", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -154,6 +159,7 @@ class Pic:
         st = C.c_void_p(stream.cuda_stream) if stream is not None and hasattr(stream, "cuda_stream") else \
             C.c_void_p(stream)
         self.cfg = Config(scheme, precision, q, qm, ion, sweeps, omega, 1 if track_ids else 0, st, path)
+        self._stream = stream  # the handle launches on it: keep it alive
         h = C.c_void_p()
         rc = self.lib.pic_create(C.byref(h), C.byref(tree), C.byref(parts), C.byref(self.cfg))
         if rc != 0:
@@ -195,6 +201,7 @@ class Pic:
         st = C.c_void_p(stream.cuda_stream) if stream is not None and hasattr(stream, "cuda_stream") else \
             C.c_void_p(stream)
         self.cfg = Config(scheme, precision, q, qm, ion, sweeps, omega, 1 if track_ids else 0, st, path)
+        self._stream = stream
         h = C.c_void_p()
         rc = self.lib.pic_create_batch(C.byref(h), n_inst, trees, parts,
                                        None if qarr is None else qarr.ctypes.data_as(C.c_void_p),
@@ -322,6 +329,47 @@ class Pic:
         self._check(self.lib.pic_set_state(self.h, lp, pp, vp, w))
 
     PHASES = ("deposit", "solve", "push", "rebin", "permute")
+
+    def graph_capture(self, dt: float):
+        self._check(self.lib.pic_graph_capture(self.h, dt))
+
+    def graph_launch(self, steps: int):
+        self._check(self.lib.pic_graph_launch(self.h, steps))
+
+    def tuning(self):
+        out = np.zeros(4, np.int32)
+        self._check(self.lib.pic_get_tuning(self.h, _ptr(out)[0]))
+        return [int(x) for x in out]
+
+    def set_tuning(self, tuned):
+        arr = np.ascontiguousarray(tuned, dtype=np.int32)
+        self._check(self.lib.pic_set_tuning(self.h, _ptr(arr)[0]))
+
+    def autotune(self, dt: float, trials: int = 3, cache: str | None = None):
+        """Pick the path and block shapes by timing them on this handle's own
+        particles (state restored afterwards).  With `cache`, results are kept
+        in that JSON file keyed by the workload's shape."""
+        import json
+        info = self.info()
+        key = json.dumps([int(info.d), int(info.depth), int(info.n_instances), int(info.n_particles),
+                          int(info.scheme), int(info.precision), int(info.uniform)])
+        store = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                store = json.load(f)
+        if key in store:
+            self.set_tuning(store[key])
+            return store[key]
+        out = np.zeros(4, np.int32)
+        self._check(self.lib.pic_autotune(self.h, dt, trials, _ptr(out)[0]))
+        tuned = [int(x) for x in out]
+        if cache:
+            store[key] = tuned
+            tmp = cache + f".tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(store, f, indent=1)
+            os.replace(tmp, cache)
+        return tuned
 
     def profile(self, enable: bool = True):
         self._check(self.lib.pic_profile(self.h, 1 if enable else 0))
