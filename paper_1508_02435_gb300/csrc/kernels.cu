@@ -918,7 +918,8 @@ void launch_rekey32(const DevTree &t, const int32_t *leaf, const float *o, int64
 
 void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *mover_words,
                       int32_t *block_movers, int block, cudaStream_t s) {
-  { COUNT(1); k_count_all<<<grid_for(n, block), block, 0, s>>>(key, n, count, mover_words, block_movers); }
+  const int b = bsz(block);
+  { COUNT(1); k_count_all<<<grid_for(n, b), b, 0, s>>>(key, n, count, mover_words, block_movers); }
 }
 
 void launch_fine_keys(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n, int dmax,
