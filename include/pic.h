@@ -256,6 +256,40 @@ PIC_API int pic_tree_flags(pic_t h, uint8_t *flags, int64_t *n_nodes);
  * positions below their leaf are resolved with the drop rule.  Synchronous. */
 PIC_API int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax);
 
+/* ---- no-allocation entry point -------------------------------------------
+ * The paper has no counterpart to this call: it is a library utility.  It is
+ * the stable counting sort of the re-bin (Section 4) for the fresh-particle
+ * case, on caller-owned device keys, for callers that must not allocate
+ * device memory at that point: a thread that runs while another thread holds
+ * a global-mode stream capture (cudaMalloc is refused there), a pipeline
+ * that cannot afford cudaFree's implicit device synchronisation between
+ * steps, or a process whose memory a caching allocator has already reserved.
+ *
+ * keys[n] (device): bucket of each element, in [0, n_keys).  Outputs (device,
+ * caller-owned, no initialisation needed): start[n_keys + 1] exclusive bucket
+ * offsets, start[n_keys] = number of valid keys; perm[n] the input index at
+ * each sorted position, ascending inside every bucket (stable).  Keys outside
+ * [0, n_keys) are skipped, so start[n_keys] < n reports them and perm past
+ * start[n_keys] is left untouched.
+ *
+ * Work is queued on `stream` (a cudaStream_t; NULL = legacy default stream)
+ * and the call returns without synchronising.  Scratch is one file-scope
+ * device array of PIC_NOALLOC_MAX_KEYS + 192 int32 words per device
+ * (4 MiB); the call clears the part it uses on `stream`, so nothing must be
+ * zero on entry.  No device memory is allocated or freed.  That array is
+ * shared by every caller in the process: calls on one device that overlap in
+ * time (different streams or host threads) race and must be serialised by
+ * the caller.  The first call on each device looks the array's address up
+ * (cudaGetSymbolAddress); make that first call outside any stream capture.
+ * No statement is made about capturing later calls in a CUDA graph.
+ *
+ * Returns PIC_EINVAL for n < 0, n > INT32_MAX, n_keys < 1, NULL pointers, or
+ * n_keys > PIC_NOALLOC_MAX_KEYS (nothing is launched); PIC_ECUDA if a CUDA
+ * call fails. */
+#define PIC_NOALLOC_MAX_KEYS (1 << 20)
+PIC_API int pic_bucket_noalloc(const int32_t *keys, int64_t n, int64_t n_keys, int32_t *start, int32_t *perm,
+                               void *stream);
+
 #ifdef __cplusplus
 }
 #endif

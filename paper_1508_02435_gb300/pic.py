@@ -86,6 +86,7 @@ SIGNATURES = [
     ("pic_stats", C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     ("pic_profile", C.c_int, [C.c_void_p, C.c_int32]),
     ("pic_graph_capture", C.c_int, [C.c_void_p, C.c_double]),
+    ("pic_bucket_noalloc", C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_graph_launch", C.c_int, [C.c_void_p, C.c_int32]),
     ("pic_autotune", C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p]),
     ("pic_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -136,6 +137,24 @@ def _ptr(a):
         assert a.is_contiguous()
         return C.c_void_p(a.data_ptr()), DEVICE if a.is_cuda else HOST
     raise TypeError(f"unsupported array type {type(a)}")
+
+
+NOALLOC_MAX_KEYS = 1 << 20
+
+
+def bucket_noalloc(keys, n_keys: int, start, perm, stream=None):
+    """Stable bucket sort of device int32 `keys` into the caller's device
+    tensors start[n_keys + 1] and perm[len(keys)], with no device allocation
+    inside the library (pic_bucket_noalloc).  Queued on `stream`."""
+    lib = load()
+    n = int(keys.numel())
+    if n_keys > NOALLOC_MAX_KEYS:
+        raise PicError(-1, f"n_keys = {n_keys} is above the fixed scratch of {NOALLOC_MAX_KEYS} buckets")
+    st = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+    rc = lib.pic_bucket_noalloc(C.c_void_p(keys.data_ptr()), n, int(n_keys), C.c_void_p(start.data_ptr()),
+                                C.c_void_p(perm.data_ptr()), C.c_void_p(st))
+    if rc != 0:
+        raise PicError(rc, lib.pic_strerror(rc).decode())
 
 
 class Pic:
