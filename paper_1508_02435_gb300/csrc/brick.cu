@@ -48,6 +48,14 @@ struct BK {
   static constexpr int NC = 1 << D;
 };
 
+// Asynchronous 4-byte global -> shared copies (no register round trip); the
+// issuing thread waits for all of its copies with cp_async_wait_all().
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __device__ __forceinline__ int dir_delta(int dir, int a) {
   return a == 0 ? dir % 3 - 1 : (a == 1 ? (dir / 3) % 3 - 1 : dir / 9 - 1);
 }
@@ -163,28 +171,97 @@ __device__ __forceinline__ void stage_field(const DevTree &t, const BrickPushArg
 // ---------------------------------------------------------------------------
 
 constexpr int kStThreads = 1024;
+constexpr int kLoadBatch = 4;        // particles whose loads one thread keeps in flight
 constexpr int kStCap = 7168;         // particles per brick held in shared memory
+
+// Staged field entry of one vertex: the D components side by side, so one
+// vector shared-memory load serves a corner.
+template <int D> struct EVec;
+template <> struct EVec<3> { using T = float4; };
+template <> struct EVec<2> { using T = float2; };
+
+__device__ __forceinline__ float ecomp(const float4 &e, int ax) { return ax == 0 ? e.x : (ax == 1 ? e.y : e.z); }
+__device__ __forceinline__ float ecomp(const float2 &e, int ax) { return ax == 0 ? e.x : e.y; }
+
+// Contribution of local cell coordinate x (0 <= x < 9) on axis ax to the
+// depth-first index of a leaf inside its brick (two base-3 digits per axis).
+template <int D>
+__device__ __forceinline__ int lidx_axis(int x, int ax) {
+  const int hi = (x * 11) >> 5, lo = x - 3 * hi;  // x / 3 and x % 3 for 0 <= x < 9
+  const int p = ax == 0 ? 1 : (ax == 1 ? 3 : 9);
+  return (lo + hi * (D == 3 ? 27 : 9)) * p;
+}
+
+// Re-location when some axis leaves the [-9, 18) window around the brick
+// (wrap-around, tunnelling): global cell, brick delta modulo the brick grid.
+struct SlowIn {
+  int32_t lc[3], origin[3], bc[3];
+  float fl[3];
+};
+struct SlowOut {
+  int dir, lidx;
+  int32_t dest;
+};
+
+template <int D>
+__device__ __noinline__ SlowOut relocate_slow(const DevTree &t, const BrickGeom &g, const SlowIn in) {
+  const int32_t *lc = in.lc, *origin = in.origin, *bc = in.bc;
+  const float *fl = in.fl;
+  const int32_t per = t.M;
+  int dir = 0, mul = 1, li = 0;
+  bool far = false;
+  int32_t dbc[3] = {0, 0, 0};
+#pragma unroll
+  for (int ax = 0; ax < D; ++ax) {
+    const int32_t c = origin[ax] + lc[ax];
+    int32_t cc;
+    if (fabsf(fl[ax]) < 1.0e9f) {
+      cc = c + (int32_t)fl[ax];
+      if (cc < 0 || cc >= per) {
+        cc %= per;
+        if (cc < 0) cc += per;
+      }
+    } else {
+      const int64_t c64 = ((int64_t)c + (int64_t)fminf(fmaxf(fl[ax], -1.0e15f), 1.0e15f)) % per;
+      cc = (int32_t)(c64 < 0 ? c64 + per : c64);
+    }
+    dbc[ax] = cc / 9;
+    li += lidx_axis<D>(cc - 9 * dbc[ax], ax);
+    int32_t db = dbc[ax] - bc[ax];
+    if (db < 0) db += g.nbx;
+    const int dl = db == 0 ? 0 : (db == 1 ? 1 : (db == g.nbx - 1 ? -1 : 2));
+    far |= dl == 2;
+    dir += (dl + 1) * mul;
+    mul *= 3;
+  }
+  if (D == 2) dir += 9;
+  return SlowOut{far ? kFarSlot : dir, li, brick_of_coords<D>(t, dbc)};
+}
 
 template <int D>
 size_t push_st_smem() {
   using K = BK<D>;
-  return sizeof(float) * 2 * D * kStCap + sizeof(uint16_t) * 2 * kStCap + sizeof(float) * D * K::NVB +
-         sizeof(int32_t) * (K::LB + 1) + sizeof(uint32_t) * K::LB + sizeof(int32_t) * (32 + 8 + 2) * kSlots;
+  return sizeof(float) * 2 * D * kStCap + sizeof(uint16_t) * 2 * kStCap + sizeof(typename EVec<D>::T) * K::NVB +
+         sizeof(int32_t) * (K::LB + 1) + sizeof(uint32_t) * K::LB + sizeof(int32_t) * (64 + 8 + 2) * kSlots;
 }
 
+// K1, shared-memory form.  Same arithmetic as push_core (gather in corner
+// order, kick, drift, split re-location), with the brick's field staged as
+// one vector per vertex and the destination found from the brick-local cell.
 template <int D>
 __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, BrickGeom g, BrickPushArgs a) {
   using K = BK<D>;
+  using EV = typename EVec<D>::T;
   extern __shared__ float smf[];
   float *so = smf;                                   // D * kStCap offsets
   float *sv = so + D * kStCap;                       // D * kStCap velocities
   uint16_t *code = (uint16_t *)(sv + D * kStCap);    // new local leaf | dir << 10 | stay << 15
-  uint16_t *pos = code + kStCap;                     // local leaf, then rank in (chunk, dir)
-  float *Eb = (float *)(pos + kStCap);               // D * NVB staged field
-  int32_t *ls = (int32_t *)(Eb + D * K::NVB);        // LB + 1
+  uint16_t *pos = code + kStCap;                     // local leaf, rank in (chunk, dir), then inverse map
+  EV *Eb = (EV *)(pos + kStCap);                     // NVB staged field vectors
+  int32_t *ls = (int32_t *)(Eb + K::NVB);            // LB + 1 leaf offsets (absolute until rebased)
   uint32_t *dec = (uint32_t *)(ls + K::LB + 1);      // LB
-  int32_t *wcnt = (int32_t *)(dec + K::LB);          // 32 * kSlots
-  int32_t *ctot = wcnt + 32 * kSlots;                // 8 * kSlots chunk totals, then offsets
+  int32_t *wcnt = (int32_t *)(dec + K::LB);          // 2 x 32 * kSlots (alternating chunks)
+  int32_t *ctot = wcnt + 64 * kSlots;                // 8 * kSlots chunk totals, then offsets
   int32_t *seg = ctot + 8 * kSlots;                  // kSlots
   int32_t *dtot = seg + kSlots;                      // kSlots
   __shared__ int32_t s_movers;
@@ -199,69 +276,137 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
     origin[ax] = t.leaf_coords[(int64_t)L0 * D + ax];
     bc[ax] = origin[ax] / K::B;
   }
-  for (int i = tid; i <= K::LB; i += blockDim.x) ls[i] = a.start[L0 + i] - ps;
-  for (int i = tid; i < K::LB; i += blockDim.x) dec[i] = g.decodeL[i];
-  stage_field<D>(t, a, origin, Eb);
-  for (int32_t q = tid; q < nb; q += blockDim.x) {
+  // every global -> shared copy of the brick is issued before any is awaited
+  for (int i = tid; i <= K::LB; i += blockDim.x) cp_async4(ls + i, a.start + L0 + i);
+  for (int i = tid; i < K::LB; i += blockDim.x) cp_async4(dec + i, g.decodeL + i);
+  for (int i = tid; i < K::NVB; i += blockDim.x) {
+    int lx = i % K::V1, ly = (i / K::V1) % K::V1, lz = D == 3 ? i / (K::V1 * K::V1) : 0;
+    int32_t gx = origin[0] + lx, gy = origin[1] + ly, gz = D == 3 ? origin[2] + lz : 0;
+    if (gx >= t.M) gx -= t.M;
+    if (gy >= t.M) gy -= t.M;
+    if (gz >= t.M) gz -= t.M;
+    const int64_t vid = gx + (int64_t)t.M * (gy + (int64_t)t.M * gz);
+    float *slot = (float *)(Eb + i);
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) cp_async4(slot + ax, a.E + ax * t.n_vert + vid);
+  }
+  {
+    const float *gO[D], *gV[D];
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
-      so[ax * kStCap + q] = a.o[ax * n + ps + q];
-      sv[ax * kStCap + q] = a.v[ax * n + ps + q];
+      gO[ax] = a.o + ax * n + ps;
+      gV[ax] = a.v + ax * n + ps;
+    }
+    for (int32_t q = tid; q < nb; q += blockDim.x) {
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        cp_async4(so + ax * kStCap + q, gO[ax] + q);
+        cp_async4(sv + ax * kStCap + q, gV[ax] + q);
+      }
     }
   }
   if (tid == 0) s_movers = 0;
+  cp_async_wait_all();
   __syncthreads();
   for (int l = tid; l < K::LB; l += blockDim.x)
-    for (int32_t q = ls[l]; q < ls[l + 1]; ++q) pos[q] = (uint16_t)l;
+    for (int32_t q = ls[l] - ps; q < ls[l + 1] - ps; ++q) pos[q] = (uint16_t)l;
   __syncthreads();
 
   // push every particle once; ranks within (chunk of 1024, direction)
   bool bad = false;
   const int nchunk = (nb + kStThreads - 1) / kStThreads;
   for (int c = 0; c < nchunk; ++c) {
+    int32_t *wc = wcnt + (c & 1) * 32 * kSlots;
     const int32_t q = c * kStThreads + tid;
     const bool act = q < nb;
-    if (lane < kSlots) wcnt[w * kSlots + lane] = 0;
+    if (lane < kSlots) wc[w * kSlots + lane] = 0;
     __syncwarp();
     int dir = 255;
     if (act) {
       const int l = pos[q];
       const uint32_t pk = dec[l];
       const int32_t lc[3] = {(int32_t)(pk & 1023u), (int32_t)((pk >> 10) & 1023u), (int32_t)(pk >> 20)};
-      float o[D], v[D], on[D], vn[D];
+      float o[D], om[D], E[D];
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
         o[ax] = so[ax * kStCap + q];
-        v[ax] = sv[ax * kStCap + q];
+        om[ax] = 1.0f - o[ax];
+        E[ax] = 0.0f;
       }
-      int32_t L2;
-      dir = push_core<D>(t, g, a, o, v, lc, origin, bc, Eb, on, vn, L2, bad);
+      const int base = lc[0] + K::V1 * (lc[1] + (D == 3 ? K::V1 * lc[2] : 0));
+#pragma unroll
+      for (int e = 0; e < K::NC; ++e) {
+        float wgt = 1.0f;
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) wgt = wgt * (((e >> ax) & 1) ? o[ax] : om[ax]);
+        const EV ev = Eb[base + (e & 1) + ((e >> 1) & 1) * K::V1 + ((e >> 2) & 1) * K::V1 * K::V1];
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) E[ax] = E[ax] + wgt * ecomp(ev, ax);
+      }
+      float fl[D];
+      int32_t loc[D];
+      bool win = true;
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
-        so[ax * kStCap + q] = on[ax];
-        sv[ax * kStCap + q] = vn[ax];
+        const float vv = sv[ax * kStCap + q] + a.qmdt * E[ax];
+        float tt = o[ax] + vv * a.sl;
+        if (!isfinite(vv) || !isfinite(tt)) {
+          bad = true;
+          tt = 0.0f;
+        }
+        fl[ax] = floorf(tt);
+        so[ax * kStCap + q] = clamp_off(tt - fl[ax]);
+        sv[ax * kStCap + q] = vv;
+        loc[ax] = lc[ax] + (int32_t)fmaxf(fminf(fl[ax], 64.0f), -64.0f);
+        win &= loc[ax] >= -K::B && loc[ax] < 2 * K::B;
       }
-      const bool stay = L2 == L0 + l;
-      code[q] = (uint16_t)((L2 % K::LB) | (dir << 10) | (stay ? kStayBit : 0));
-      if (dir == kFarSlot) a.far_scratch[ps + q] = L2 / K::LB;  // destination brick
+      int lidx = 0;
+      if (win) {
+        dir = D == 2 ? 9 : 0;
+        int mul = 1;
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+          const int dl = (loc[ax] >= K::B) - (loc[ax] < 0);
+          dir += (dl + 1) * mul;
+          mul *= 3;
+          lidx += lidx_axis<D>(loc[ax] - K::B * dl, ax);
+        }
+      } else {
+        SlowIn in{};
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+          in.lc[ax] = lc[ax];
+          in.origin[ax] = origin[ax];
+          in.bc[ax] = bc[ax];
+          in.fl[ax] = fl[ax];
+        }
+        const SlowOut r = relocate_slow<D>(t, g, in);
+        dir = r.dir;
+        lidx = r.lidx;
+        if (dir == kFarSlot) a.far_scratch[ps + q] = r.dest;
+      }
+      const bool stay = dir == kSelfDir && lidx == l;
+      code[q] = (uint16_t)(lidx | (dir << 10) | (stay ? kStayBit : 0));
     }
-    unsigned peers = __match_any_sync(0xffffffffu, dir);
+    const unsigned peers = __match_any_sync(0xffffffffu, dir);
     const int rank = __popc(peers & ((1u << lane) - 1u));
-    if (act && rank == 0) wcnt[w * kSlots + dir] = __popc(peers);
+    if (act && rank == 0) wc[w * kSlots + dir] = __popc(peers);
     __syncthreads();
-    if (tid < kSlots) {
-      int32_t sum = 0;
-      for (int k = 0; k < 32; ++k) {
-        const int32_t cv = wcnt[k * kSlots + tid];
-        wcnt[k * kSlots + tid] = sum;
-        sum += cv;
+    if (w < kSlots) {  // warp `w` scans direction w over the 32 warps' counts
+      const int32_t cv = wc[lane * kSlots + w];
+      int32_t x = cv;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
-      ctot[c * kSlots + tid] = sum;
+      wc[lane * kSlots + w] = x - cv;
+      if (lane == 31) ctot[c * kSlots + w] = x;
     }
     __syncthreads();
-    if (act) pos[q] = (uint16_t)(wcnt[w * kSlots + dir] + rank);
-    __syncthreads();
+    if (act) pos[q] = (uint16_t)(wc[w * kSlots + dir] + rank);
   }
+  __syncthreads();
   // direction segments and chunk offsets
   if (tid < kSlots) {
     int32_t run = 0;
@@ -283,29 +428,54 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
     }
   }
   __syncthreads();
-  // partitioned writes
+  // final position of every particle (registers), then the inverse map in
+  // pos[] so that the writes walk the destination order (coalesced)
+  constexpr int kPer = (kStCap + kStThreads - 1) / kStThreads;
+  int32_t fin[kPer];
   int movers = 0;
-  for (int32_t q = tid; q < nb; q += blockDim.x) {
-    const uint16_t cd = code[q];
-    const int dir = (cd >> 10) & 31;
-    const int32_t p = ps + seg[dir] + ctot[(q / kStThreads) * kSlots + dir] + pos[q];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int32_t q = u * kStThreads + tid;
+    fin[u] = -1;
+    if (q < nb) {
+      const uint16_t cd = code[q];
+      const int dir = (cd >> 10) & 31;
+      fin[u] = seg[dir] + ctot[u * kSlots + dir] + pos[q];
+      movers += !(cd & kStayBit);
+      if (dir == kFarSlot) {
+        int32_t k = atomicAdd(a.far_n, 1);
+        if (k < a.far_cap) {
+          a.far_tidx[k] = ps + fin[u];
+          a.far_src[k] = b;
+          a.far_dest[k] = a.far_scratch[ps + q];
+        } else {
+          atomicOr(a.err, 4);
+        }
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kPer; ++u)
+    if (fin[u] >= 0) pos[fin[u]] = (uint16_t)(u * kStThreads + tid);
+  __syncthreads();
+  {
+    float *tO[D], *tV[D];
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
-      a.to[ax * n + p] = so[ax * kStCap + q];
-      a.tv[ax * n + p] = sv[ax * kStCap + q];
+      tO[ax] = a.to + ax * n + ps;
+      tV[ax] = a.tv + ax * n + ps;
     }
-    a.tcode[p] = (uint16_t)(cd & (kStayBit | 0x3ffu));
-    if (a.ids) a.tids[p] = a.ids[ps + q];
-    movers += !(cd & kStayBit);
-    if (dir == kFarSlot) {
-      int32_t k = atomicAdd(a.far_n, 1);
-      if (k < a.far_cap) {
-        a.far_tidx[k] = p;
-        a.far_src[k] = b;
-        a.far_dest[k] = a.far_scratch[ps + q];
-      } else {
-        atomicOr(a.err, 4);
+    uint16_t *tC = a.tcode + ps;
+    for (int32_t p = tid; p < nb; p += blockDim.x) {
+      const int32_t q = pos[p];
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        tO[ax][p] = so[ax * kStCap + q];
+        tV[ax][p] = sv[ax * kStCap + q];
       }
+      tC[p] = (uint16_t)(code[q] & (kStayBit | 0x3ffu));
+      if (a.ids) a.tids[ps + p] = a.ids[ps + q];
     }
   }
   if (bad) atomicOr(a.err, 1);
@@ -479,35 +649,46 @@ __global__ void k_far_scatter(const int32_t *far_n, int32_t far_cap, const int32
 // Per destination brick: far arrivals sorted by temporary index (storage
 // order), and the brick's total incoming count.
 template <int D>
-__global__ void k_brick_totals(DevTree t, BrickGeom g, const int32_t *cnt, const int32_t *fstart,
-                               int32_t *sorted_tidx, int32_t *sorted_src, int32_t *tot) {
-  int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_brick_totals(DevTree t, BrickGeom g, const int32_t *cnt, const int32_t *segoff,
+                               const int32_t *old_start, const int32_t *fstart, int32_t *sorted_tidx,
+                               int32_t *sorted_src, int32_t *tot, int4 *bpiece) {
+  // one warp per destination brick, lane = direction of the source brick
+  const int lane = threadIdx.x & 31;
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (b >= g.n_bricks) return;
-  int32_t fb = fstart[b], fe = fstart[b + 1];
-  for (int32_t i = fb + 1; i < fe; ++i) {
-    int32_t x = sorted_tidx[i], y = sorted_src[i], j = i - 1;
-    while (j >= fb && sorted_tidx[j] > x) {
-      sorted_tidx[j + 1] = sorted_tidx[j];
-      sorted_src[j + 1] = sorted_src[j];
-      --j;
+  const int32_t fb = fstart[b], fe = fstart[b + 1];
+  if (lane == 0)
+    for (int32_t i = fb + 1; i < fe; ++i) {
+      int32_t x = sorted_tidx[i], y = sorted_src[i], j = i - 1;
+      while (j >= fb && sorted_tidx[j] > x) {
+        sorted_tidx[j + 1] = sorted_tidx[j];
+        sorted_src[j + 1] = sorted_src[j];
+        --j;
+      }
+      sorted_tidx[j + 1] = x;
+      sorted_src[j + 1] = y;
     }
-    sorted_tidx[j + 1] = x;
-    sorted_src[j + 1] = y;
-  }
-  const int32_t L0 = b * BK<D>::LB;
-  int32_t bc[3] = {0, 0, 0};
-  for (int ax = 0; ax < D; ++ax) bc[ax] = t.leaf_coords[(int64_t)L0 * D + ax] / 9;
-  int32_t s = fe - fb;
-  for (int dir = 0; dir < 27; ++dir) {
-    if (D == 2 && dir_delta(dir, 2) != 0) continue;
-    int32_t sc[3] = {0, 0, 0};
-    for (int ax = 0; ax < D; ++ax) {
-      int32_t x = bc[ax] - dir_delta(dir, ax);
-      sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
+  const int32_t L0 = (int32_t)b * BK<D>::LB;
+  int32_t len = 0;
+  if (lane < 27) {
+    const int dir = lane;
+    int4 pc = make_int4(0, 0, INT32_MAX, 0);
+    if (!(D == 2 && dir_delta(dir, 2) != 0)) {
+      int32_t sc[3] = {0, 0, 0};
+      for (int ax = 0; ax < D; ++ax) {
+        const int32_t x = t.leaf_coords[(int64_t)L0 * D + ax] / 9 - dir_delta(dir, ax);
+        sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
+      }
+      const int32_t src = brick_of_coords<D>(t, sc);
+      const int64_t k = (int64_t)src * kSlots + dir;
+      len = cnt[k];
+      pc = make_int4(old_start[(int64_t)src * BK<D>::LB] + segoff[k], len, src, 0);
     }
-    s += cnt[(int64_t)brick_of_coords<D>(t, sc) * kSlots + dir];
+    bpiece[b * 27 + dir] = pc;
   }
-  tot[b] = s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) len += __shfl_down_sync(0xffffffffu, len, o);
+  if (lane == 0) tot[b] = len + (fe - fb);
 }
 
 // ---------------------------------------------------------------------------
@@ -519,6 +700,18 @@ struct Piece {
   int16_t round1;    // 1: keep stayers only; 0: keep movers only
   int16_t indirect;  // 1: positions tstart.. index the sorted far arrivals
 };
+
+// Round-2 piece holding stage index si: the largest k in [1, np) with
+// spfx[k] <= si (empty pieces share their successor's prefix).
+__device__ __forceinline__ int piece_of(const int32_t *spfx, int np, int32_t si) {
+  int lo = 1, hi = np - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (spfx[mid] <= si) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 template <int D>
 __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeom g, BrickPullArgs a) {
@@ -542,18 +735,9 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
   __shared__ int32_t s_src[27];
   Piece mine{0, 0, INT32_MAX, 0, 0};
   if (tid < 27) {
-    const int dir = tid;
-    if (!(D == 2 && dir_delta(dir, 2) != 0)) {
-      int32_t sc[3] = {0, 0, 0};
-      for (int ax = 0; ax < D; ++ax) {
-        int32_t x = t.leaf_coords[(int64_t)L0 * D + ax] / 9 - dir_delta(dir, ax);
-        sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
-      }
-      const int32_t src = brick_of_coords<D>(t, sc);
-      const int64_t k = (int64_t)src * kSlots + dir;
-      mine = Piece{a.old_start[src * K::LB] + a.segoff[k], a.cnt[k], src, 0, 0};
-    }
-    s_src[dir] = mine.src;
+    const int4 pc = a.bpiece[(int64_t)b * 27 + tid];
+    mine = Piece{pc.x, pc.y, pc.z, 0, 0};
+    s_src[tid] = mine.src;
   }
   for (int i = tid; i < K::LB + 1; i += blockDim.x) cnt[i] = 0;
   __syncthreads();
@@ -752,18 +936,9 @@ __device__ __forceinline__ void build_pieces(const DevTree &t, const BrickGeom &
   const int32_t L0 = b * K::LB;
   Piece mine{0, 0, INT32_MAX, 0, 0};
   if (tid < 27) {
-    const int dir = tid;
-    if (!(D == 2 && dir_delta(dir, 2) != 0)) {
-      int32_t sc[3] = {0, 0, 0};
-      for (int ax = 0; ax < D; ++ax) {
-        int32_t x = t.leaf_coords[(int64_t)L0 * D + ax] / 9 - dir_delta(dir, ax);
-        sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
-      }
-      const int32_t src = brick_of_coords<D>(t, sc);
-      const int64_t k = (int64_t)src * kSlots + dir;
-      mine = Piece{a.old_start[src * K::LB] + a.segoff[k], a.cnt[k], src, 0, 0};
-    }
-    s_src[dir] = mine.src;
+    const int4 pc = a.bpiece[(int64_t)b * 27 + tid];
+    mine = Piece{pc.x, pc.y, pc.z, 0, 0};
+    s_src[tid] = mine.src;
   }
   __syncthreads();
   if (tid < 27 && mine.src != INT32_MAX) {
@@ -801,6 +976,32 @@ __device__ __forceinline__ void build_pieces(const DevTree &t, const BrickGeom &
   __syncthreads();
 }
 
+// Sorts the m <= kNet canonical keys of one leaf (ascending) with a bitonic
+// network in registers and replaces each by its stage index.
+constexpr int kNet = 16;
+__device__ __forceinline__ void sort_keys_net(uint16_t *keys, int m, int32_t len0, int32_t self_stage) {
+  uint32_t r[kNet];
+#pragma unroll
+  for (int i = 0; i < kNet; ++i) r[i] = i < m ? keys[i] : 0xffffu;
+#pragma unroll
+  for (int k = 2; k <= kNet; k <<= 1)
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+      for (int i = 0; i < kNet; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint32_t x = r[i], y = r[l];
+          const bool up = (i & k) == 0;
+          r[i] = up ? min(x, y) : max(x, y);
+          r[l] = up ? max(x, y) : min(x, y);
+        }
+      }
+#pragma unroll
+  for (int i = 0; i < kNet; ++i)
+    if (i < m) keys[i] = (uint16_t)((int32_t)r[i] < len0 ? self_stage + (int32_t)r[i] : (int32_t)r[i] - len0);
+}
+
 template <int D>
 __global__ void __launch_bounds__(kStThreads, 1) k_brick_pull_st(DevTree t, BrickGeom g, BrickPullArgs a) {
   using K = BK<D>;
@@ -827,23 +1028,46 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_pull_st(DevTree t, Bric
   const int np = s_np;
   const int32_t len0 = pieces[0].len, self_stage = spfx[s_self];
   const int32_t nin = spfx[np];
-  // load every arrival once (round-2 pieces cover each exactly once)
-  for (int k = 1; k < np; ++k) {
-    const Piece pc = pieces[k];
-    const int32_t so0 = spfx[k];
-    for (int32_t i = tid; i < pc.len; i += blockDim.x) {
-      const int32_t tidx = pc.indirect ? a.far_tidx[pc.tstart + i] : pc.tstart + i;
-      const int32_t si = so0 + i;
+  // load every arrival once (round-2 pieces cover each exactly once): one
+  // thread per arrival over all pieces; payload by asynchronous copies, the
+  // codes through registers for the leaf counts
+  {
+    const float *gO[D], *gV[D];
 #pragma unroll
-      for (int ax = 0; ax < D; ++ax) {
-        so[ax * kStCap + si] = a.to[ax * n + tidx];
-        sv[ax * kStCap + si] = a.tv[ax * n + tidx];
+    for (int ax = 0; ax < D; ++ax) {
+      gO[ax] = a.to + ax * n;
+      gV[ax] = a.tv + ax * n;
+    }
+    int kp = tid < nin ? piece_of(spfx, np, tid) : 1;  // arrivals only move forward
+    for (int32_t base = 0; base < nin; base += kLoadBatch * kStThreads) {
+      uint16_t rc[kLoadBatch];
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int32_t si = base + u * kStThreads + tid;
+        if (si < nin) {
+          while (kp + 1 < np && spfx[kp + 1] <= si) ++kp;
+          const Piece pc = pieces[kp];
+          const int32_t off = si - spfx[kp];
+          const int32_t tx = pc.indirect ? a.far_tidx[pc.tstart + off] : pc.tstart + off;
+#pragma unroll
+          for (int ax = 0; ax < D; ++ax) {
+            cp_async4(so + ax * kStCap + si, gO[ax] + tx);
+            cp_async4(sv + ax * kStCap + si, gV[ax] + tx);
+          }
+          rc[u] = __ldg(a.tcode + tx);
+        }
       }
-      const uint16_t cd = a.tcode[tidx];
-      code[si] = cd;
-      atomicAdd(&cnt[cd & 0x3ff], 1);
+#pragma unroll
+      for (int u = 0; u < kLoadBatch; ++u) {
+        const int32_t si = base + u * kStThreads + tid;
+        if (si < nin) {
+          code[si] = rc[u];
+          atomicAdd(&cnt[rc[u] & 0x3ff], 1);
+        }
+      }
     }
   }
+  cp_async_wait_all();
   __syncthreads();
   // exclusive scan of the leaf counts, cursors
   int32_t carry = 0;
@@ -884,6 +1108,10 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_pull_st(DevTree t, Bric
   for (int l = tid; l < K::LB; l += blockDim.x) {
     a.new_start[L0 + l] = bstart + cnt[l];
     const int32_t lo = cnt[l], hi = cnt[l + 1];
+    if (hi - lo <= kNet) {
+      sort_keys_net(map + lo, hi - lo, len0, self_stage);
+      continue;
+    }
     for (int32_t i = lo + 1; i < hi; ++i) {
       const uint16_t x = map[i];
       int32_t j = i - 1;
@@ -899,20 +1127,27 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_pull_st(DevTree t, Bric
   if (tid == 0 && s_max > 0) atomicMax(a.max_bucket, s_max);
   __syncthreads();
   // coalesced writes in destination order
-  for (int32_t j = tid; j < nin; j += blockDim.x) {
-    const int32_t si = map[j], dst = bstart + j;
+  {
+    float *gO[D], *gV[D];
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
-      a.o[ax * n + dst] = so[ax * kStCap + si];
-      a.v[ax * n + dst] = sv[ax * kStCap + si];
+      gO[ax] = a.o + ax * n + bstart;
+      gV[ax] = a.v + ax * n + bstart;
+    }
+    for (int32_t j = tid; j < nin; j += blockDim.x) {
+      const int32_t si = map[j];
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        gO[ax][j] = so[ax * kStCap + si];
+        gV[ax][j] = sv[ax * kStCap + si];
+      }
     }
   }
   if (a.ids) {
     // ids: the source of stage index si is found in the round-2 pieces
     for (int32_t j = tid; j < nin; j += blockDim.x) {
       const int32_t si = map[j];
-      int k = 1;
-      while (k + 1 < np && spfx[k + 1] <= si) ++k;
+      const int k = piece_of(spfx, np, si);
       const Piece pc = pieces[k];
       const int32_t off = si - spfx[k];
       a.ids[bstart + j] = a.tids[pc.indirect ? a.far_tidx[pc.tstart + off] : pc.tstart + off];
@@ -982,11 +1217,11 @@ void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPushArgs
   k_far_scatter<<<64, 256, 0, s>>>(pa.far_n, pa.far_cap, pa.far_dest, pa.far_tidx, pa.far_src, qa.fstart,
                                    fcursor, qa.far_tidx_w, qa.far_src_w);
   if (g.d == 3)
-    k_brick_totals<3><<<(nb + 255) / 256, 256, 0, s>>>(t, g, pa.cnt, qa.fstart, qa.far_tidx_w, qa.far_src_w,
-                                                       qa.tot_w);
+    k_brick_totals<3><<<(nb + 7) / 8, 256, 0, s>>>(t, g, pa.cnt, pa.segoff, qa.old_start, qa.fstart,
+                                                   qa.far_tidx_w, qa.far_src_w, qa.tot_w, qa.bpiece_w);
   else
-    k_brick_totals<2><<<(nb + 255) / 256, 256, 0, s>>>(t, g, pa.cnt, qa.fstart, qa.far_tidx_w, qa.far_src_w,
-                                                       qa.tot_w);
+    k_brick_totals<2><<<(nb + 7) / 8, 256, 0, s>>>(t, g, pa.cnt, pa.segoff, qa.old_start, qa.fstart,
+                                                   qa.far_tidx_w, qa.far_src_w, qa.tot_w, qa.bpiece_w);
   launch_exclusive_scan(qa.tot_w, g.n_bricks, qa.bstart_w, tile_sums, scratch_total, s);
   if (g.d == 3) {
     k_brick_pull_st<3><<<nb, kStThreads, pull_st_smem<3>(), s>>>(t, g, qa);

@@ -226,8 +226,12 @@ __device__ __forceinline__ int uniform_incidences(int64_t v, int d, const InstIn
                                                   int32_t *lc) {
   const int32_t M = I.M;
   int32_t j[3] = {0, 0, 0};
-  int64_t r = v - I.vert_off;
-  for (int a = 0; a < d; ++a) { j[a] = (int32_t)(r % M); r /= M; }
+  int32_t r = (int32_t)(v - I.vert_off);  // < 3^(d depth) <= 3^18
+  for (int a = 0; a < d; ++a) {
+    const int32_t qt = r / M;
+    j[a] = r - qt * M;
+    r = qt;
+  }
   int nc = 1 << d;
   for (int f = 0; f < nc; ++f) {
     int32_t c[3] = {0, 0, 0};

@@ -103,6 +103,8 @@ struct BrickPullArgs {
   int32_t *max_bucket;
   int32_t *err;
   float *part;                   // leaf-corner deposit partials of the new positions, or NULL
+  const int4 *bpiece;            // [n_bricks][27] incoming segment {start, length, source brick}
+  int4 *bpiece_w;
 };
 
 cudaError_t brick_configure(const BrickGeom &g);

@@ -80,6 +80,7 @@ struct pic_s {
   int32_t *bcnt = nullptr, *bsegoff = nullptr, *far_n = nullptr, *far_tidx = nullptr, *far_src = nullptr;
   int32_t *far_dest = nullptr, *far_stidx = nullptr, *far_ssrc = nullptr, *fcount = nullptr;
   int32_t *fcursor = nullptr, *fstart = nullptr, *btot = nullptr, *bstart = nullptr;
+  int4 *bpiece = nullptr;
 
   // per-phase event timing (pic_profile / pic_phase_times)
   struct Pending {
@@ -476,6 +477,7 @@ int setup_brick(pic_t h) {
   if ((rc = dalloc(h, bb, &h->fstart, nb + 1))) return rc;
   if ((rc = dalloc(h, bb, &h->btot, nb))) return rc;
   if ((rc = dalloc(h, bb, &h->bstart, nb + 1))) return rc;
+  if ((rc = dalloc(h, bb, &h->bpiece, nb * 27))) return rc;
   if (scan_tiles_needed(nb) + 1 > scan_tiles_needed(h->dt.n_keys) + 1)
     return fail(h, PIC_EINVAL, "brick count exceeds scan scratch");
   CK(brick_configure(g));
@@ -545,6 +547,8 @@ int brick_push_and_rebin(pic_t h, double dt) {
   qa.max_bucket = h->scalars + 2;
   qa.err = h->err;
   qa.part = (float *)h->part;
+  qa.bpiece = h->bpiece;
+  qa.bpiece_w = h->bpiece;
   (void)d;
   CK(cudaMemsetAsync(h->scalars + 1, 0, sizeof(int32_t) * 2, s));
   {
