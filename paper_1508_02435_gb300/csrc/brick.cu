@@ -931,75 +931,98 @@ template <int D>
 __device__ __forceinline__ void build_pieces(const DevTree &t, const BrickGeom &g, const BrickPullArgs &a,
                                              int32_t b, Piece *pieces, Piece *sdesc, int32_t *s_src,
                                              int32_t *pfx, int32_t *spfx, int32_t *s_np, int32_t *s_self) {
-  using K = BK<D>;
-  const int tid = threadIdx.x;
-  const int32_t L0 = b * K::LB;
-  Piece mine{0, 0, INT32_MAX, 0, 0};
-  if (tid < 27) {
-    const int4 pc = a.bpiece[(int64_t)b * 27 + tid];
-    mine = Piece{pc.x, pc.y, pc.z, 0, 0};
-    s_src[tid] = mine.src;
-  }
-  __syncthreads();
-  if (tid < 27 && mine.src != INT32_MAX) {
-    int rank = 0;
-    for (int k = 0; k < 27; ++k) rank += s_src[k] < mine.src;
-    sdesc[rank] = mine;
-    if (tid == kSelfDir) pieces[0] = Piece{mine.tstart, mine.len, mine.src, 1, 0};
-  }
-  __syncthreads();
-  if (tid == 0) {
+  (void)t;
+  (void)g;
+  (void)s_src;
+  const int tid = threadIdx.x, lane = tid & 31;
+  constexpr unsigned kAll = 0xffffffffu;
+  if (tid < 32) {  // warp 0: lane = direction of the source brick
+    Piece mine{0, 0, INT32_MAX, 0, 0};
+    if (lane < 27) {
+      const int4 pc = a.bpiece[(int64_t)b * 27 + lane];
+      mine = Piece{pc.x, pc.y, pc.z, 0, 0};
+    }
+    const int32_t fi0 = a.fstart[b], fe = a.fstart[b + 1];
+    int rank = 0;  // sources in ascending brick order = storage order
+    for (int k = 0; k < 27; ++k) rank += __shfl_sync(kAll, mine.src, k) < mine.src;
+    const bool valid = lane < 27 && mine.src != INT32_MAX;
     const int ns = D == 3 ? 27 : 9;
-    int np = 1;
-    int32_t fi = a.fstart[b];
-    const int32_t fe = a.fstart[b + 1];
-    for (int k = 0; k < ns; ++k) {
-      if (fi < fe) {
-        int32_t f0 = fi;
-        while (fi < fe && a.far_src[fi] < sdesc[k].src) ++fi;
-        if (fi > f0) pieces[np++] = Piece{f0, fi - f0, -1, 0, 1};
+    if (lane == kSelfDir) pieces[0] = Piece{mine.tstart, mine.len, mine.src, 1, 0};
+    if (fi0 == fe) {
+      // no far arrivals: the neighbour segments in source order, in parallel
+      if (valid) {
+        pieces[1 + rank] = mine;
+        if (mine.src == b) *s_self = 1 + rank;
       }
-      if (sdesc[k].src == b) *s_self = np;
-      pieces[np++] = sdesc[k];
+      __syncwarp();
+      const int32_t len0 = __shfl_sync(kAll, mine.len, kSelfDir);
+      const int32_t x = lane < ns ? pieces[1 + lane].len : 0;
+      int32_t incl = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(kAll, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane < ns) {
+        pfx[1 + lane] = len0 + incl - x;
+        spfx[1 + lane] = incl - x;
+      }
+      if (lane == 0) pfx[0] = spfx[0] = 0;
+      if (lane == ns - 1) {
+        pfx[ns + 1] = len0 + incl;
+        spfx[ns + 1] = incl;
+        *s_np = ns + 1;
+      }
+    } else {
+      if (valid) sdesc[rank] = mine;
+      __syncwarp();
+      if (lane == 0) {
+        // far arrivals (sorted by storage index, so by source brick) go
+        // between the neighbour segments as runs of the sorted far list
+        int np = 1;
+        int32_t fi = fi0;
+        for (int k = 0; k < ns; ++k) {
+          if (fi < fe) {
+            int32_t f0 = fi;
+            while (fi < fe && a.far_src[fi] < sdesc[k].src) ++fi;
+            if (fi > f0) pieces[np++] = Piece{f0, fi - f0, -1, 0, 1};
+          }
+          if (sdesc[k].src == b) *s_self = np;
+          pieces[np++] = sdesc[k];
+        }
+        if (fi < fe) pieces[np++] = Piece{fi, fe - fi, -1, 0, 1};
+        int32_t sum = 0;
+        for (int k = 0; k < np; ++k) {
+          pfx[k] = sum;
+          spfx[k] = k == 0 ? 0 : sum - pieces[0].len;
+          sum += pieces[k].len;
+        }
+        pfx[np] = sum;
+        spfx[np] = sum - pieces[0].len;
+        *s_np = np;
+      }
     }
-    if (fi < fe) pieces[np++] = Piece{fi, fe - fi, -1, 0, 1};
-    int32_t sum = 0;
-    for (int k = 0; k < np; ++k) {
-      pfx[k] = sum;
-      spfx[k] = k == 0 ? 0 : sum - pieces[0].len;
-      sum += pieces[k].len;
-    }
-    pfx[np] = sum;
-    spfx[np] = sum - pieces[0].len;
-    *s_np = np;
   }
   __syncthreads();
 }
 
-// Sorts the m <= kNet canonical keys of one leaf (ascending) with a bitonic
+// Sorts the m <= N canonical keys of one leaf (ascending) with a bitonic
 // network in registers and replaces each by its stage index.
-constexpr int kNet = 16;
+template <int N>
 __device__ __forceinline__ void sort_keys_net(uint16_t *keys, int m, int32_t len0, int32_t self_stage) {
-  uint32_t r[kNet];
+  uint32_t r[N];
 #pragma unroll
-  for (int i = 0; i < kNet; ++i) r[i] = i < m ? keys[i] : 0xffffu;
+  for (int i = 0; i < N; ++i) r[i] = i < m ? keys[i] : 0xffffu;
+  bitonic_sort<N>(r);
 #pragma unroll
-  for (int k = 2; k <= kNet; k <<= 1)
-#pragma unroll
-    for (int j = k >> 1; j > 0; j >>= 1)
-#pragma unroll
-      for (int i = 0; i < kNet; ++i) {
-        const int l = i ^ j;
-        if (l > i) {
-          const uint32_t x = r[i], y = r[l];
-          const bool up = (i & k) == 0;
-          r[i] = up ? min(x, y) : max(x, y);
-          r[l] = up ? max(x, y) : min(x, y);
-        }
-      }
-#pragma unroll
-  for (int i = 0; i < kNet; ++i)
+  for (int i = 0; i < N; ++i)
     if (i < m) keys[i] = (uint16_t)((int32_t)r[i] < len0 ? self_stage + (int32_t)r[i] : (int32_t)r[i] - len0);
+}
+
+// Leaves with 17..32 keys (rare): out of line, so that the 32-entry network
+// does not raise the register demand of the calling kernel.
+__device__ __noinline__ void sort_keys_net32(uint16_t *keys, int m, int32_t len0, int32_t self_stage) {
+  sort_keys_net<32>(keys, m, len0, self_stage);
 }
 
 template <int D>
@@ -1108,8 +1131,12 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_pull_st(DevTree t, Bric
   for (int l = tid; l < K::LB; l += blockDim.x) {
     a.new_start[L0 + l] = bstart + cnt[l];
     const int32_t lo = cnt[l], hi = cnt[l + 1];
-    if (hi - lo <= kNet) {
-      sort_keys_net(map + lo, hi - lo, len0, self_stage);
+    if (hi - lo <= 16) {
+      sort_keys_net<16>(map + lo, hi - lo, len0, self_stage);
+      continue;
+    }
+    if (hi - lo <= 32) {
+      sort_keys_net32(map + lo, hi - lo, len0, self_stage);
       continue;
     }
     for (int32_t i = lo + 1; i < hi; ++i) {
@@ -1153,19 +1180,31 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_pull_st(DevTree t, Bric
       a.ids[bstart + j] = a.tids[pc.indirect ? a.far_tidx[pc.tstart + off] : pc.tstart + off];
     }
   }
-  // deposit partials of the new positions, per leaf in bucket order
+  // deposit partials of the new positions, per leaf in bucket order; the
+  // next particle's offsets are fetched while the current one is summed
   if (a.part) {
     for (int l = tid; l < K::LB; l += blockDim.x) {
       float acc[K::NC];
 #pragma unroll
       for (int e = 0; e < K::NC; ++e) acc[e] = 0.0f;
-      for (int32_t j = cnt[l]; j < cnt[l + 1]; ++j) {
-        const int32_t si = map[j];
+      const int32_t lo = cnt[l], hi = cnt[l + 1];
+      float on[D];
+      if (lo < hi) {
+        const int32_t si = map[lo];
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) on[ax] = so[ax * kStCap + si];
+      }
+      for (int32_t j = lo; j < hi; ++j) {
         float o[D], om[D];
 #pragma unroll
         for (int ax = 0; ax < D; ++ax) {
-          o[ax] = so[ax * kStCap + si];
+          o[ax] = on[ax];
           om[ax] = 1.0f - o[ax];
+        }
+        if (j + 1 < hi) {
+          const int32_t si = map[j + 1];
+#pragma unroll
+          for (int ax = 0; ax < D; ++ax) on[ax] = so[ax * kStCap + si];
         }
 #pragma unroll
         for (int e = 0; e < K::NC; ++e) {
@@ -1175,8 +1214,9 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_pull_st(DevTree t, Bric
           acc[e] = acc[e] + wgt;
         }
       }
+      float *gp = a.part + (int64_t)(L0 + l) * K::NC;
 #pragma unroll
-      for (int e = 0; e < K::NC; ++e) a.part[(int64_t)(L0 + l) * K::NC + e] = acc[e];
+      for (int e = 0; e < K::NC; ++e) gp[e] = acc[e];
     }
   }
 }

@@ -220,34 +220,64 @@ __device__ __forceinline__ T shape(const T *t, int e, int d) {
   return w;
 }
 
+// Ascending bitonic sorting network over N register values (N a power of two).
+template <int N, typename T>
+__device__ __forceinline__ void bitonic_sort(T *r) {
+#pragma unroll
+  for (int k = 2; k <= N; k <<= 1)
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        const int l = i ^ j;
+        if (l > i) {
+          const T x = r[i], y = r[l];
+          const bool up = (i & k) == 0;
+          r[i] = up ? (x < y ? x : y) : (x < y ? y : x);
+          r[l] = up ? (x < y ? y : x) : (x < y ? x : y);
+        }
+      }
+}
+
 // Incident leaf corners of uniform vertex v (global id) in ascending
-// leaf-corner order, for the instance I.
+// leaf-corner order, for the instance I.  The cell of corner f is
+// j - bits(f) per axis (periodic); its leaf id is a sum of per-axis spread values.
+template <int D>
+__device__ __forceinline__ void uniform_incidences_d(int64_t v, const InstInfo &I, const int32_t *spread,
+                                                     int32_t *lc) {
+  const int32_t M = I.M;
+  int32_t r = (int32_t)(v - I.vert_off);  // < 3^(d depth) <= 3^18
+  int32_t s_hi[3] = {0, 0, 0}, s_lo[3] = {0, 0, 0};
+  const int32_t *sp = spread + I.spread_off;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int32_t qt = r / M, j = r - qt * M;
+    r = qt;
+    s_hi[a] = __ldg(sp + a * M + j);
+    s_lo[a] = __ldg(sp + a * M + (j == 0 ? M - 1 : j - 1));
+  }
+  constexpr int NC = 1 << D;
+  int32_t k[NC];
+#pragma unroll
+  for (int f = 0; f < NC; ++f) {
+    int32_t leaf = I.leaf_off;
+#pragma unroll
+    for (int a = 0; a < D; ++a) leaf += ((f >> a) & 1) ? s_lo[a] : s_hi[a];
+    k[f] = leaf * NC + f;
+  }
+  bitonic_sort<NC>(k);
+#pragma unroll
+  for (int f = 0; f < NC; ++f) lc[f] = k[f];
+}
+
 __device__ __forceinline__ int uniform_incidences(int64_t v, int d, const InstInfo &I, const int32_t *spread,
                                                   int32_t *lc) {
-  const int32_t M = I.M;
-  int32_t j[3] = {0, 0, 0};
-  int32_t r = (int32_t)(v - I.vert_off);  // < 3^(d depth) <= 3^18
-  for (int a = 0; a < d; ++a) {
-    const int32_t qt = r / M;
-    j[a] = r - qt * M;
-    r = qt;
+  if (d == 3) {
+    uniform_incidences_d<3>(v, I, spread, lc);
+    return 8;
   }
-  int nc = 1 << d;
-  for (int f = 0; f < nc; ++f) {
-    int32_t c[3] = {0, 0, 0};
-    for (int a = 0; a < d; ++a) {
-      int32_t cc = j[a] - ((f >> a) & 1);
-      c[a] = cc < 0 ? cc + M : cc;
-    }
-    lc[f] = (I.leaf_off + uniform_leaf_of_cell(spread + I.spread_off, M, c, d)) * nc + f;
-  }
-  for (int i = 1; i < nc; ++i) {  // insertion sort, at most 8 entries
-    int32_t x = lc[i];
-    int k = i - 1;
-    while (k >= 0 && lc[k] > x) { lc[k + 1] = lc[k]; --k; }
-    lc[k + 1] = x;
-  }
-  return nc;
+  uniform_incidences_d<2>(v, I, spread, lc);
+  return 4;
 }
 
 }  // namespace pic
