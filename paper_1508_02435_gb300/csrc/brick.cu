@@ -56,6 +56,40 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// One-dimensional bulk copies (TMA) global -> shared, completed on an
+// mbarrier: both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// Bounded wait for phase `parity` of the mbarrier: false if it did not
+// complete within about `cycles` SM clocks.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long cycles) {
+  const long long t0 = clock64();
+  unsigned done = 0;
+  do {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+  } while (!done && clock64() - t0 < cycles);
+  return done != 0;
+}
+constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at the maximum SM clock
+constexpr int kErrTimeout = 8;                   // error bit: a bounded device wait gave up
+
 __device__ __forceinline__ int dir_delta(int dir, int a) {
   return a == 0 ? dir % 3 - 1 : (a == 1 ? (dir / 3) % 3 - 1 : dir / 9 - 1);
 }
@@ -173,6 +207,7 @@ __device__ __forceinline__ void stage_field(const DevTree &t, const BrickPushArg
 constexpr int kStThreads = 1024;
 constexpr int kLoadBatch = 4;        // particles whose loads one thread keeps in flight
 constexpr int kStCap = 7168;         // particles per brick held in shared memory
+constexpr int kStS = kStCap + 8;     // shared row stride of the K1 stash (room for a 16-byte aligned head)
 
 // Staged field entry of one vertex: the D components side by side, so one
 // vector shared-memory load serves a corner.
@@ -241,7 +276,7 @@ __device__ __noinline__ SlowOut relocate_slow(const DevTree &t, const BrickGeom 
 template <int D>
 size_t push_st_smem() {
   using K = BK<D>;
-  return sizeof(float) * 2 * D * kStCap + sizeof(uint16_t) * 2 * kStCap + sizeof(typename EVec<D>::T) * K::NVB +
+  return sizeof(float) * 2 * D * kStS + sizeof(uint16_t) * 2 * kStCap + sizeof(typename EVec<D>::T) * K::NVB +
          sizeof(int32_t) * (K::LB + 1) + sizeof(uint32_t) * K::LB + sizeof(int32_t) * (64 + 8 + 2) * kSlots;
 }
 
@@ -253,9 +288,9 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
   using K = BK<D>;
   using EV = typename EVec<D>::T;
   extern __shared__ float smf[];
-  float *so = smf;                                   // D * kStCap offsets
-  float *sv = so + D * kStCap;                       // D * kStCap velocities
-  uint16_t *code = (uint16_t *)(sv + D * kStCap);    // new local leaf | dir << 10 | stay << 15
+  float *so = smf;                                   // D rows of kStS offsets
+  float *sv = so + D * kStS;                         // D rows of kStS velocities
+  uint16_t *code = (uint16_t *)(sv + D * kStS);      // new local leaf | dir << 10 | stay << 15
   uint16_t *pos = code + kStCap;                     // local leaf, rank in (chunk, dir), then inverse map
   EV *Eb = (EV *)(pos + kStCap);                     // NVB staged field vectors
   int32_t *ls = (int32_t *)(Eb + K::NVB);            // LB + 1 leaf offsets (absolute until rebased)
@@ -265,6 +300,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
   int32_t *seg = ctot + 8 * kSlots;                  // kSlots
   int32_t *dtot = seg + kSlots;                      // kSlots
   __shared__ int32_t s_movers;
+  __shared__ uint64_t s_bar;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int32_t b = blockIdx.x, L0 = b * K::LB;
   const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nb = pe - ps;
@@ -290,24 +326,45 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) cp_async4(slot + ax, a.E + ax * t.n_vert + vid);
   }
-  {
-    const float *gO[D], *gV[D];
+  // the brick's particle rows: one bulk copy per row from the 16-byte
+  // boundary at or below its first particle; row r holds particle q at
+  // shared index off[r] + q
+  int32_t offO[D], offV[D];
 #pragma unroll
-    for (int ax = 0; ax < D; ++ax) {
-      gO[ax] = a.o + ax * n + ps;
-      gV[ax] = a.v + ax * n + ps;
-    }
-    for (int32_t q = tid; q < nb; q += blockDim.x) {
+  for (int r = 0; r < 2 * D; ++r) {
+    const float *src = (r < D ? a.o + r * n : a.v + (r - D) * n) + ps;
+    const int32_t head = (int32_t)(((uintptr_t)src & 15u) >> 2);
+    if (r < D) offO[r] = r * kStS + head;
+    else offV[r - D] = (r - D) * kStS + head;
+  }
+  if (tid == 0) {
+    s_movers = 0;
+    if (nb > 0) {
+      mbar_init(&s_bar, 1);
+      uint32_t total = 0, bytes[2 * D];
+      const float *src[2 * D];
 #pragma unroll
-      for (int ax = 0; ax < D; ++ax) {
-        cp_async4(so + ax * kStCap + q, gO[ax] + q);
-        cp_async4(sv + ax * kStCap + q, gV[ax] + q);
+      for (int r = 0; r < 2 * D; ++r) {
+        const float *p = (r < D ? a.o + r * n : a.v + (r - D) * n) + ps;
+        const uintptr_t a0 = (uintptr_t)p & ~(uintptr_t)15;
+        src[r] = (const float *)a0;
+        bytes[r] = (uint32_t)(((uintptr_t)(p + nb) - a0 + 15u) & ~(uintptr_t)15);
+        total += bytes[r];
       }
+      mbar_expect_tx(&s_bar, total);
+#pragma unroll
+      for (int r = 0; r < 2 * D; ++r)
+        bulk_g2s(r < D ? so + r * kStS : sv + (r - D) * kStS, src[r], bytes[r], &s_bar);
     }
   }
-  if (tid == 0) s_movers = 0;
   cp_async_wait_all();
-  __syncthreads();
+  __syncthreads();  // the barrier is initialised and armed before anyone waits on it
+  const bool landed = nb == 0 || mbar_wait(&s_bar, 0, kWaitCycles);
+  if (__syncthreads_or(!landed)) {
+    if (!landed) mbar_wait(&s_bar, 0, kWaitCycles);  // let copies in flight land before leaving
+    if (tid == 0) atomicOr(a.err, kErrTimeout);
+    return;
+  }
   for (int l = tid; l < K::LB; l += blockDim.x)
     for (int32_t q = ls[l] - ps; q < ls[l + 1] - ps; ++q) pos[q] = (uint16_t)l;
   __syncthreads();
@@ -329,7 +386,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
       float o[D], om[D], E[D];
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
-        o[ax] = so[ax * kStCap + q];
+        o[ax] = so[offO[ax] + q];
         om[ax] = 1.0f - o[ax];
         E[ax] = 0.0f;
       }
@@ -348,15 +405,15 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
       bool win = true;
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
-        const float vv = sv[ax * kStCap + q] + a.qmdt * E[ax];
+        const float vv = sv[offV[ax] + q] + a.qmdt * E[ax];
         float tt = o[ax] + vv * a.sl;
         if (!isfinite(vv) || !isfinite(tt)) {
           bad = true;
           tt = 0.0f;
         }
         fl[ax] = floorf(tt);
-        so[ax * kStCap + q] = clamp_off(tt - fl[ax]);
-        sv[ax * kStCap + q] = vv;
+        so[offO[ax] + q] = clamp_off(tt - fl[ax]);
+        sv[offV[ax] + q] = vv;
         loc[ax] = lc[ax] + (int32_t)fmaxf(fminf(fl[ax], 64.0f), -64.0f);
         win &= loc[ax] >= -K::B && loc[ax] < 2 * K::B;
       }
@@ -471,8 +528,8 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
       const int32_t q = pos[p];
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
-        tO[ax][p] = so[ax * kStCap + q];
-        tV[ax][p] = sv[ax * kStCap + q];
+        tO[ax][p] = so[offO[ax] + q];
+        tV[ax][p] = sv[offV[ax] + q];
       }
       tC[p] = (uint16_t)(code[q] & (kStayBit | 0x3ffu));
       if (a.ids) a.tids[ps + p] = a.ids[ps + q];

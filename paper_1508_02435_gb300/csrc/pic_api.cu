@@ -324,9 +324,10 @@ int alloc_state(pic_t h) {
   int rc;
   for (int s = 0; s < 2; ++s) {
     char *p;
-    if ((rc = dalloc(h, sb, &p, fs * d * n))) return rc;
+    // + 64 bytes: bulk copies read whole 16-byte units around a particle range
+    if ((rc = dalloc(h, sb, &p, fs * d * n + 64))) return rc;
     h->pos[s] = p;
-    if ((rc = dalloc(h, sb, &p, fs * d * n))) return rc;
+    if ((rc = dalloc(h, sb, &p, fs * d * n + 64))) return rc;
     h->vel[s] = p;
     if ((rc = dalloc(h, sb, &h->leaf[s], n))) return rc;
     if (h->scheme == PIC_PIT) {
@@ -1149,6 +1150,7 @@ int pic_sync(pic_t h) {
   int rc = read_err(h, &err);
   if (rc) return rc;
   if (err & 1) return fail(h, PIC_ERANGE, "non-finite position or velocity");
+  if (err & 8) return fail(h, PIC_ETIMEOUT, "a bounded device wait gave up");
   if (err) return fail(h, PIC_ESTATE, "device-side capacity exceeded (error bits " + std::to_string(err) + ")");
   return PIC_OK;
 }
