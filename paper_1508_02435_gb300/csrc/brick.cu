@@ -287,7 +287,7 @@ template <int D>
 __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, BrickGeom g, BrickPushArgs a) {
   using K = BK<D>;
   using EV = typename EVec<D>::T;
-  extern __shared__ float smf[];
+  extern __shared__ __align__(128) float smf[];
   float *so = smf;                                   // D rows of kStS offsets
   float *sv = so + D * kStS;                         // D rows of kStS velocities
   uint16_t *code = (uint16_t *)(sv + D * kStS);      // new local leaf | dir << 10 | stay << 15
@@ -1085,7 +1085,7 @@ __device__ __noinline__ void sort_keys_net32(uint16_t *keys, int m, int32_t len0
 template <int D>
 __global__ void __launch_bounds__(kStThreads, 1) k_brick_pull_st(DevTree t, BrickGeom g, BrickPullArgs a) {
   using K = BK<D>;
-  extern __shared__ float smf[];
+  extern __shared__ __align__(128) float smf[];
   float *so = smf;                                   // D * kStCap
   float *sv = so + D * kStCap;                       // D * kStCap
   uint16_t *code = (uint16_t *)(sv + D * kStCap);    // kStCap tcode of every arrival (stage order)

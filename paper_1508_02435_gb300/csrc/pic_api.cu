@@ -464,7 +464,7 @@ int setup_brick(pic_t h) {
   int rc;
   if ((rc = upload(h, bb, &g.decodeL, dec))) return rc;
   const int64_t n = h->n, nb = g.n_bricks;
-  if ((rc = dalloc(h, bb, &h->tcode, n))) return rc;
+  if ((rc = dalloc(h, bb, &h->tcode, n + 32))) return rc;  // bulk copies read whole 16-byte units
   if ((rc = dalloc(h, bb, &h->bcnt, nb * 28))) return rc;
   if ((rc = dalloc(h, bb, &h->bsegoff, nb * 28))) return rc;
   if ((rc = dalloc(h, bb, &h->far_n, 2))) return rc;
