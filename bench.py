@@ -38,6 +38,45 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 at 16 particles per cell.
 STEP_BYTES = {(3, 1): 70.0, (3, 0): 132.0, (2, 1): 48.5, (2, 0): 89.0}
 
+# DRAM bytes per particle that ncu measured for the dominant kernel (read +
+# write, one launch, divided by the particles it moved), valid only for the
+# kernel sources whose digest is stored beside it; see profiles/.
+MEASURED_TRAFFIC = {}
+KERNEL_SOURCES = ("paper_1508_02435_gb300/csrc/brick.cu", "paper_1508_02435_gb300/csrc/dev.cuh")
+
+
+def kernel_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def brick_bytes(d: int, ppc: float, track_ids: bool) -> dict:
+    """Compulsory bytes per particle of each phase of the brick path (uniform
+    tree, PIT, FP32 split), bricks of 9^d leaves: what each kernel must read
+    and write given its inputs and outputs.
+      push   (k_brick_push_st): offsets + velocities in, the brick's staged
+             field ((9+1)^d vertices x d x 4 B) and leaf offsets, pushed
+             offsets + velocities + 2-byte direction code out;
+      rebin  (k_brick_pull_st + helpers): the pushed state and codes in, the
+             bucket-ordered state, leaf offsets and 2^d corner partials per
+             leaf out;
+      deposit (k_vertex_charge): corner partials in, vertex charge out."""
+    st = 2 * d * 4 + (8 if track_ids else 0)
+    leaves = 9 ** d
+    per_brick = leaves * ppc
+    field = (10 ** d) * d * 4 / per_brick
+    nc = 1 << d
+    return {
+        "push": st + field + 4 / ppc + st + 2,
+        "rebin": st + 2 + st + 4 / ppc + nc * 4 / ppc,
+        "deposit": nc * 4 / ppc + 4 / ppc,
+        "permute": 0.0,
+    }
+
 
 def kernel_bytes(d: int, split: bool, ppc: float) -> dict:
     """Algorithmic bytes per particle of each phase as the kernels implement it:
@@ -115,21 +154,38 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_workload(name: str):
+def workload_config(name: str) -> dict:
+    n3 = {"langmuir3d": 243 ** 3 * 8, "langmuir3d-small": 81 ** 3 * 8}
     if name == "langmuir3d":
-        w = W.langmuir(3, 5, 8, vth=0.05, dt=0.1, steps=200)
-        return w, {"workload": "3D uniform Langmuir, depth 5 (243^3 leaves), 8 ppc, "
-                               f"{w.n} particles, vth=0.05, omega_p dt=0.1",
-                   "precision": "fp32_split", "scheme": "PIT", "d": 3, "ppc": 8}
+        return {"workload": "3D uniform Langmuir, depth 5 (243^3 leaves), 8 ppc, "
+                            f"{n3[name]} particles, vth=0.05, omega_p dt=0.1",
+                "precision": "fp32_split", "scheme": "PIT", "d": 3, "ppc": 8}
     if name == "langmuir3d-small":
-        w = W.langmuir(3, 4, 8, vth=0.05, dt=0.1, steps=200)
-        return w, {"workload": "3D uniform Langmuir, depth 4 (81^3 leaves), 8 ppc, "
-                               f"{w.n} particles (profiling case)",
-                   "precision": "fp32_split", "scheme": "PIT", "d": 3, "ppc": 8}
+        return {"workload": "3D uniform Langmuir, depth 4 (81^3 leaves), 8 ppc, "
+                            f"{n3[name]} particles (profiling case)",
+                "precision": "fp32_split", "scheme": "PIT", "d": 3, "ppc": 8}
+    if name == "langmuir3d-octant":
+        return {"workload": "3D Langmuir, depth 5 (243^3 leaves), 8 ppc in the octant [0,1/2)^3 only "
+                            "(profiling case: the same bricks, an eighth of them populated)",
+                "precision": "fp32_split", "scheme": "PIT", "d": 3, "ppc": 8}
     if name == "langmuir2d":
-        w = W.langmuir(2, 3, 16)
-        return w, {"workload": f"2D uniform Langmuir, depth 3 (27^2 leaves), 16 ppc, {w.n} particles",
-                   "precision": "fp64", "scheme": "PIT", "d": 2, "ppc": 16}
+        return {"workload": "2D uniform Langmuir, depth 3 (27^2 leaves), 16 ppc, 11664 particles",
+                "precision": "fp64", "scheme": "PIT", "d": 2, "ppc": 16}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def build_workload(name: str):
+    if name == "langmuir3d-octant":
+        w = W.langmuir(3, 5, 8, vth=0.05, dt=0.1, steps=200)
+        keep = np.all(w.x < 0.5, axis=0)
+        w.x, w.v = np.ascontiguousarray(w.x[:, keep]), np.ascontiguousarray(w.v[:, keep])
+        return w, workload_config(name)
+    if name == "langmuir3d":
+        return W.langmuir(3, 5, 8, vth=0.05, dt=0.1, steps=200), workload_config(name)
+    if name == "langmuir3d-small":
+        return W.langmuir(3, 4, 8, vth=0.05, dt=0.1, steps=200), workload_config(name)
+    if name == "langmuir2d":
+        return W.langmuir(2, 3, 16), workload_config(name)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -169,19 +225,21 @@ def run_reference(args):
     w_name = args.workload
     d = 3 if w_name.startswith("langmuir3d") else 2
     split = d == 3
-    rates = []
+    rates, secs = [], []
     for _ in range(args.warmup):
         oracle_rate(d, split, 0, 1.0)
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         r, info = oracle_rate(d, split, 0, max(2.0, 20.0 / max(args.steps, 1)))
+        secs.append(time.perf_counter() - t0)
         rates.append(r)
     value = statistics.median(rates)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-updates/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-           "higher_is_better": True, "dtype": "f32" if split else "f64", "data": "synthetic",
-           "config": {"workload": "3D uniform Langmuir (bounded oracle sample: depth 3, 8 ppc)" if d == 3
-                      else "2D uniform Langmuir depth 3", "scheme": "PIT",
-                      "precision": "fp32_split" if split else "fp64"},
+           "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32" if split else "f64", "data": "synthetic",
+           "config": {**workload_config(w_name), "field": "held fixed (solve timed apart)",
+                      "parallelism": "1 GPU"},
            "cpu_baseline": {"value": value, "unit": "particle-updates/s", **info},
            "e2e": {"value": value, "unit": "particle-updates/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
@@ -194,7 +252,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="langmuir3d", choices=["langmuir3d", "langmuir3d-small", "langmuir2d"])
+    ap.add_argument("--workload", default="langmuir3d",
+                    choices=["langmuir3d", "langmuir3d-small", "langmuir3d-octant", "langmuir2d"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
@@ -284,12 +343,23 @@ def main():
 
     peaks, peak_kind = load_peaks()
     hbm = float(peaks["hbm_gbs"])
-    kb = kernel_bytes(d, split, cfg["ppc"])
+    info = g.info()
+    if info.brick:
+        kb = brick_bytes(d, cfg["ppc"], track_ids=False)
+        names = {"push": "k_brick_push_st (gather + kick + drift + re-location + direction partition)",
+                 "rebin": "k_brick_pull_st (+ far-list and brick-offset helpers): canonical re-bin + corner partials",
+                 "deposit": "k_vertex_charge (vertex sums of the corner partials)"}
+    else:
+        kb = kernel_bytes(d, split, cfg["ppc"])
+        names = {}
     dom = max(("deposit", "push", "rebin", "permute"), key=lambda k: phases[k][0])
     dom_ms = phases[dom][0] / args.steps
     achieved = kb[dom] * n / (dom_ms / 1e3) / 1e9
     step_bytes = STEP_BYTES[(d, 1 if split else 0)]
     traffic = None
+    mt = MEASURED_TRAFFIC.get((args.workload, dom))
+    if mt and mt["digest"] == kernel_digest():
+        traffic = mt["bytes_per_particle"] * n
     launches = sum(k for _, k in phases.values())
     out = {
         "metric": METRIC, "value": value, "unit": "particle-updates/s", "n_gpus": world,
@@ -298,9 +368,9 @@ def main():
         "config": {**cfg, "n_particles": n, "field": "held fixed (solve timed apart)",
                    "l2": "inputs larger than L2 (state > 3 GB)",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
-                     "algorithmic_bytes_per_particle": kb[dom]},
+        "roofline": {"bound": "hbm", "kernel": names.get(dom, dom), "achieved": achieved, "peak": hbm,
+                     "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_particle": kb[dom], "launch_ms": dom_ms},
         "step_roofline": {"bytes_per_particle": step_bytes,
                           "achieved_gbs": step_bytes * n / (ms_step / 1e3) / 1e9,
                           "frac": step_bytes * n / (ms_step / 1e3) / 1e9 / hbm},
