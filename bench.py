@@ -41,7 +41,11 @@ STEP_BYTES = {(3, 1): 70.0, (3, 0): 132.0, (2, 1): 48.5, (2, 0): 89.0}
 # DRAM bytes per particle that ncu measured for the dominant kernel (read +
 # write, one launch, divided by the particles it moved), valid only for the
 # kernel sources whose digest is stored beside it; see profiles/.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("langmuir3d", "push"): {"bytes_per_particle": 52.21, "digest": "db8f1cb4187503b8"},
+    ("langmuir3d", "rebin"): {"bytes_per_particle": 54.76, "digest": "db8f1cb4187503b8"},
+    ("langmuir3d", "deposit"): {"bytes_per_particle": 4.48, "digest": "db8f1cb4187503b8"},
+}
 KERNEL_SOURCES = ("paper_1508_02435_gb300/csrc/brick.cu", "paper_1508_02435_gb300/csrc/dev.cuh")
 
 
@@ -164,10 +168,6 @@ def workload_config(name: str) -> dict:
         return {"workload": "3D uniform Langmuir, depth 4 (81^3 leaves), 8 ppc, "
                             f"{n3[name]} particles (profiling case)",
                 "precision": "fp32_split", "scheme": "PIT", "d": 3, "ppc": 8}
-    if name == "langmuir3d-octant":
-        return {"workload": "3D Langmuir, depth 5 (243^3 leaves), 8 ppc in the octant [0,1/2)^3 only "
-                            "(profiling case: the same bricks, an eighth of them populated)",
-                "precision": "fp32_split", "scheme": "PIT", "d": 3, "ppc": 8}
     if name == "langmuir2d":
         return {"workload": "2D uniform Langmuir, depth 3 (27^2 leaves), 16 ppc, 11664 particles",
                 "precision": "fp64", "scheme": "PIT", "d": 2, "ppc": 16}
@@ -175,11 +175,6 @@ def workload_config(name: str) -> dict:
 
 
 def build_workload(name: str):
-    if name == "langmuir3d-octant":
-        w = W.langmuir(3, 5, 8, vth=0.05, dt=0.1, steps=200)
-        keep = np.all(w.x < 0.5, axis=0)
-        w.x, w.v = np.ascontiguousarray(w.x[:, keep]), np.ascontiguousarray(w.v[:, keep])
-        return w, workload_config(name)
     if name == "langmuir3d":
         return W.langmuir(3, 5, 8, vth=0.05, dt=0.1, steps=200), workload_config(name)
     if name == "langmuir3d-small":
@@ -253,7 +248,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="langmuir3d",
-                    choices=["langmuir3d", "langmuir3d-small", "langmuir3d-octant", "langmuir2d"])
+                    choices=["langmuir3d", "langmuir3d-small", "langmuir2d"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
