@@ -35,7 +35,7 @@ constexpr uint16_t kStayBit = 0x8000;
 constexpr int kPushThreads = 512;
 constexpr int kPullThreads = 256;
 constexpr int kPullWarps = kPullThreads / 32;
-constexpr int kMaxPieces = 64;       // round-1 piece + 27 segments + 28 runs of far arrivals
+constexpr int kMaxPieces = 128;      // round-1 pieces + 2 x 27 segments + 55 runs of far arrivals
 constexpr int kLidxCap = 8192;       // particles per brick with a shared-memory leaf index
 constexpr int kStageCap = 6144;      // particles per brick staged in shared memory
 
@@ -209,6 +209,16 @@ constexpr int kLoadBatch = 4;        // particles whose loads one thread keeps i
 constexpr int kStCap = 7168;         // particles per brick held in shared memory
 constexpr int kStS = kStCap + 8;     // shared row stride of the K1 stash (room for a 16-byte aligned head)
 
+// Two independent FP32 products in one instruction, each rounded to nearest.
+__device__ __forceinline__ float2 mul2_rn(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mul.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}\n"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+
 // Staged field entry of one vertex: the D components side by side, so one
 // vector shared-memory load serves a corner.
 template <int D> struct EVec;
@@ -273,38 +283,61 @@ __device__ __noinline__ SlowOut relocate_slow(const DevTree &t, const BrickGeom 
   return SlowOut{far ? kFarSlot : dir, li, brick_of_coords<D>(t, dbc)};
 }
 
+// K1 runs two CTAs per SM: each takes one half of a brick's particles
+// (storage order) and partitions that half by direction on its own, so a
+// brick's segment towards one neighbour is two runs, half 0 then half 1.
+constexpr int kHThreads = 512;
+constexpr int kHalfCap = 3040;       // particles of one half held in shared memory
+constexpr int kHS = kHalfCap + 8;    // shared row stride (room for a 16-byte aligned head)
+constexpr int kHChunks = (kHalfCap + kHThreads - 1) / kHThreads;
+constexpr int kH32 = (kHalfCap + 31) / 32;  // 32-particle chunks of one half
+
+// First storage offset (within the brick) of half h of a brick holding nb
+// particles: halves of the shared-memory kernel, or everything in half 0 for
+// bricks that the global-memory kernel takes.
+__host__ __device__ __forceinline__ int32_t half_start(int32_t nb, int h) {
+  if (h == 0) return 0;
+  return nb <= 2 * kHalfCap ? (nb + 1) / 2 : nb;
+}
+
 template <int D>
 size_t push_st_smem() {
   using K = BK<D>;
-  return sizeof(float) * 2 * D * kStS + sizeof(uint16_t) * 2 * kStCap + sizeof(typename EVec<D>::T) * K::NVB +
-         sizeof(int32_t) * (K::LB + 1) + sizeof(uint32_t) * K::LB + sizeof(int32_t) * (64 + 8 + 2) * kSlots;
+  return sizeof(float) * 2 * D * kHS + sizeof(uint16_t) * 2 * kHalfCap + sizeof(typename EVec<D>::T) * K::NVB +
+         sizeof(int32_t) * (K::LB + 1) + sizeof(uint32_t) * K::LB + sizeof(uint16_t) * kH32 * kSlots +
+         sizeof(int32_t) * 2 * kSlots + sizeof(int32_t) * 3 * 32;
 }
 
-// K1, shared-memory form.  Same arithmetic as push_core (gather in corner
-// order, kick, drift, split re-location), with the brick's field staged as
-// one vector per vertex and the destination found from the brick-local cell.
-template <int D>
-__global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, BrickGeom g, BrickPushArgs a) {
+// K1, shared-memory form, one CTA per half brick.  Same arithmetic as
+// push_core (gather in corner order, kick, drift, split re-location), with
+// the brick's field staged as one vector per vertex and the destination found
+// from the brick-local cell through a per-axis table.
+template <int D, bool kAligned>
+__global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, BrickGeom g, BrickPushArgs a) {
   using K = BK<D>;
   using EV = typename EVec<D>::T;
+  constexpr int kW = kHThreads / 32;
   extern __shared__ __align__(128) float smf[];
-  float *so = smf;                                   // D rows of kStS offsets
-  float *sv = so + D * kStS;                         // D rows of kStS velocities
-  uint16_t *code = (uint16_t *)(sv + D * kStS);      // new local leaf | dir << 10 | stay << 15
-  uint16_t *pos = code + kStCap;                     // local leaf, rank in (chunk, dir), then inverse map
-  EV *Eb = (EV *)(pos + kStCap);                     // NVB staged field vectors
-  int32_t *ls = (int32_t *)(Eb + K::NVB);            // LB + 1 leaf offsets (absolute until rebased)
+  float *so = smf;                                   // D rows of kHS offsets
+  float *sv = so + D * kHS;                          // D rows of kHS velocities
+  uint16_t *code = (uint16_t *)(sv + D * kHS);       // new local leaf | dir << 10 | stay << 15
+  uint16_t *pos = code + kHalfCap;                   // local leaf, rank in (chunk, dir), then inverse map
+  EV *Eb = (EV *)(pos + kHalfCap);                   // NVB staged field vectors
+  int32_t *ls = (int32_t *)(Eb + K::NVB);            // LB + 1 absolute leaf offsets
   uint32_t *dec = (uint32_t *)(ls + K::LB + 1);      // LB
-  int32_t *wcnt = (int32_t *)(dec + K::LB);          // 2 x 32 * kSlots (alternating chunks)
-  int32_t *ctot = wcnt + 64 * kSlots;                // 8 * kSlots chunk totals, then offsets
-  int32_t *seg = ctot + 8 * kSlots;                  // kSlots
+  uint16_t *cw = (uint16_t *)(dec + K::LB);          // kH32 x kSlots: per 32-particle chunk and
+                                                     // direction counts, then exclusive offsets
+  int32_t *seg = (int32_t *)(cw + kH32 * kSlots);    // kSlots
   int32_t *dtot = seg + kSlots;                      // kSlots
+  int32_t *rel = dtot + kSlots;                      // 3 x 32: per-axis direction | leaf-index parts
   __shared__ int32_t s_movers;
   __shared__ uint64_t s_bar;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int32_t b = blockIdx.x, L0 = b * K::LB;
-  const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nb = pe - ps;
-  if (nb > kStCap) return;  // the recompute kernel takes this brick
+  const int32_t b = blockIdx.x >> 1, h = blockIdx.x & 1, L0 = b * K::LB;
+  const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nbr = pe - ps;
+  if (nbr > 2 * kHalfCap) return;  // the global-memory kernel takes this brick
+  const int32_t q0 = half_start(nbr, h), q1 = h ? nbr : half_start(nbr, 1), nb = q1 - q0;
+  const int32_t hs = ps + q0;  // storage index of this half's first particle
   const int64_t n = a.n;
   int32_t origin[3] = {0, 0, 0}, bc[3] = {0, 0, 0};
 #pragma unroll
@@ -312,7 +345,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
     origin[ax] = t.leaf_coords[(int64_t)L0 * D + ax];
     bc[ax] = origin[ax] / K::B;
   }
-  // every global -> shared copy of the brick is issued before any is awaited
+  // every global -> shared copy is issued before any is awaited
   for (int i = tid; i <= K::LB; i += blockDim.x) cp_async4(ls + i, a.start + L0 + i);
   for (int i = tid; i < K::LB; i += blockDim.x) cp_async4(dec + i, g.decodeL + i);
   for (int i = tid; i < K::NVB; i += blockDim.x) {
@@ -326,17 +359,28 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) cp_async4(slot + ax, a.E + ax * t.n_vert + vid);
   }
-  // the brick's particle rows: one bulk copy per row from the 16-byte
-  // boundary at or below its first particle; row r holds particle q at
-  // shared index off[r] + q
+  if (tid < 3 * 27) {  // local cell l - 9 on axis tid / 27: (direction digit + 1) 3^axis << 16 | leaf part
+    const int ax = tid / 27, loc = tid % 27 - K::B;
+    const int dl = (loc >= K::B) - (loc < 0);
+    const int p3 = ax == 0 ? 1 : (ax == 1 ? 3 : 9);
+    rel[ax * 32 + tid % 27] = ((dl + 1) * p3 << 16) | lidx_axis<D>(loc - K::B * dl, ax);
+  }
+  for (int i = tid; i < kH32 * kSlots / 2; i += blockDim.x) reinterpret_cast<uint32_t *>(cw)[i] = 0u;
+  // the half's particle rows: one bulk copy per row from the 16-byte boundary
+  // at or below its first particle; row r holds particle q at index off[r] + q
   int32_t offO[D], offV[D];
 #pragma unroll
   for (int r = 0; r < 2 * D; ++r) {
-    const float *src = (r < D ? a.o + r * n : a.v + (r - D) * n) + ps;
+    const float *src = (r < D ? a.o + r * n : a.v + (r - D) * n) + hs;
     const int32_t head = (int32_t)(((uintptr_t)src & 15u) >> 2);
-    if (r < D) offO[r] = r * kStS + head;
-    else offV[r - D] = (r - D) * kStS + head;
+    if (r < D) offO[r] = r * kHS + head;
+    else offV[r - D] = (r - D) * kHS + head;
   }
+  // with n a multiple of 4 every row has the same head, so row ax of particle
+  // q sits a compile-time distance from row 0
+  const int32_t h0 = offO[0];
+  auto O = [&](int ax, int32_t q) -> float & { return kAligned ? so[ax * kHS + h0 + q] : so[offO[ax] + q]; };
+  auto V = [&](int ax, int32_t q) -> float & { return kAligned ? sv[ax * kHS + h0 + q] : sv[offV[ax] + q]; };
   if (tid == 0) {
     s_movers = 0;
     if (nb > 0) {
@@ -345,7 +389,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
       const float *src[2 * D];
 #pragma unroll
       for (int r = 0; r < 2 * D; ++r) {
-        const float *p = (r < D ? a.o + r * n : a.v + (r - D) * n) + ps;
+        const float *p = (r < D ? a.o + r * n : a.v + (r - D) * n) + hs;
         const uintptr_t a0 = (uintptr_t)p & ~(uintptr_t)15;
         src[r] = (const float *)a0;
         bytes[r] = (uint32_t)(((uintptr_t)(p + nb) - a0 + 15u) & ~(uintptr_t)15);
@@ -354,7 +398,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
       mbar_expect_tx(&s_bar, total);
 #pragma unroll
       for (int r = 0; r < 2 * D; ++r)
-        bulk_g2s(r < D ? so + r * kStS : sv + (r - D) * kStS, src[r], bytes[r], &s_bar);
+        bulk_g2s(r < D ? so + r * kHS : sv + (r - D) * kHS, src[r], bytes[r], &s_bar);
     }
   }
   cp_async_wait_all();
@@ -365,69 +409,88 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
     if (tid == 0) atomicOr(a.err, kErrTimeout);
     return;
   }
-  for (int l = tid; l < K::LB; l += blockDim.x)
-    for (int32_t q = ls[l] - ps; q < ls[l + 1] - ps; ++q) pos[q] = (uint16_t)l;
+  for (int l = tid; l < K::LB; l += blockDim.x) {
+    const int32_t lo = max(ls[l] - hs, 0), hi = min(ls[l + 1] - hs, nb);
+    for (int32_t q = lo; q < hi; ++q) pos[q] = (uint16_t)l;
+  }
   __syncthreads();
 
-  // push every particle once; ranks within (chunk of 1024, direction)
+  // push every particle once, warp by warp over chunks of 32 consecutive
+  // particles: rank within (chunk, direction) by a warp match, chunk counts
+  // into cw[]; no block barrier until every particle is pushed
   bool bad = false;
-  const int nchunk = (nb + kStThreads - 1) / kStThreads;
-  for (int c = 0; c < nchunk; ++c) {
-    int32_t *wc = wcnt + (c & 1) * 32 * kSlots;
-    const int32_t q = c * kStThreads + tid;
+  const int nc32 = (nb + 31) >> 5;
+  for (int c = w; c < nc32; c += kW) {
+    const int32_t q = c * 32 + lane;
     const bool act = q < nb;
-    if (lane < kSlots) wc[w * kSlots + lane] = 0;
-    __syncwarp();
     int dir = 255;
     if (act) {
       const int l = pos[q];
       const uint32_t pk = dec[l];
       const int32_t lc[3] = {(int32_t)(pk & 1023u), (int32_t)((pk >> 10) & 1023u), (int32_t)(pk >> 20)};
-      float o[D], om[D], E[D];
+      float o[D], om[D];
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
-        o[ax] = so[offO[ax] + q];
+        o[ax] = O(ax, q);
         om[ax] = 1.0f - o[ax];
-        E[ax] = 0.0f;
       }
       const int base = lc[0] + K::V1 * (lc[1] + (D == 3 ? K::V1 * lc[2] : 0));
+      // corner weights (1 * f0) * f1 [* f2], f = o or 1 - o by corner bit,
+      // two corners per paired multiply; then E = sum over corners of w * E_corner
+      // in corner order.  (Paired adds are not used: the compiler fuses a paired
+      // multiply and add into one rounding, which would change the result.)
+      float wgt[K::NC];
+      {
+        const float2 f0 = make_float2(om[0], o[0]);
+        const float2 a01 = mul2_rn(f0, make_float2(om[1], om[1]));  // corners 0, 1
+        const float2 a23 = mul2_rn(f0, make_float2(o[1], o[1]));    // corners 2, 3
+        if constexpr (D == 3) {
+          const float2 w01 = mul2_rn(a01, make_float2(om[2], om[2]));
+          const float2 w23 = mul2_rn(a23, make_float2(om[2], om[2]));
+          const float2 w45 = mul2_rn(a01, make_float2(o[2], o[2]));
+          const float2 w67 = mul2_rn(a23, make_float2(o[2], o[2]));
+          wgt[0] = w01.x; wgt[1] = w01.y; wgt[2] = w23.x; wgt[3] = w23.y;
+          wgt[4] = w45.x; wgt[5] = w45.y; wgt[6] = w67.x; wgt[7] = w67.y;
+        } else {
+          wgt[0] = a01.x; wgt[1] = a01.y; wgt[2] = a23.x; wgt[3] = a23.y;
+        }
+      }
+      float E[D];
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) E[ax] = 0.0f;
 #pragma unroll
       for (int e = 0; e < K::NC; ++e) {
-        float wgt = 1.0f;
-#pragma unroll
-        for (int ax = 0; ax < D; ++ax) wgt = wgt * (((e >> ax) & 1) ? o[ax] : om[ax]);
         const EV ev = Eb[base + (e & 1) + ((e >> 1) & 1) * K::V1 + ((e >> 2) & 1) * K::V1 * K::V1];
 #pragma unroll
-        for (int ax = 0; ax < D; ++ax) E[ax] = E[ax] + wgt * ecomp(ev, ax);
+        for (int ax = 0; ax < D; ++ax) E[ax] = E[ax] + wgt[e] * ecomp(ev, ax);
+      }
+      // kick and drift: v += (q/m) dt E, t = o + v s_l
+      float vv[D], tt[D];
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        vv[ax] = V(ax, q) + a.qmdt * E[ax];
+        tt[ax] = o[ax] + vv[ax] * a.sl;
       }
       float fl[D];
-      int32_t loc[D];
+      int32_t packed = D == 2 ? (9 << 16) : 0;
       bool win = true;
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
-        const float vv = sv[offV[ax] + q] + a.qmdt * E[ax];
-        float tt = o[ax] + vv * a.sl;
-        if (!isfinite(vv) || !isfinite(tt)) {
+        if (!isfinite(vv[ax]) || !isfinite(tt[ax])) {
           bad = true;
-          tt = 0.0f;
+          tt[ax] = 0.0f;
         }
-        fl[ax] = floorf(tt);
-        so[offO[ax] + q] = clamp_off(tt - fl[ax]);
-        sv[offV[ax] + q] = vv;
-        loc[ax] = lc[ax] + (int32_t)fmaxf(fminf(fl[ax], 64.0f), -64.0f);
-        win &= loc[ax] >= -K::B && loc[ax] < 2 * K::B;
+        fl[ax] = floorf(tt[ax]);
+        O(ax, q) = clamp_off(tt[ax] - fl[ax]);
+        V(ax, q) = vv[ax];
+        const uint32_t li = (uint32_t)(lc[ax] + K::B + (int32_t)fmaxf(fminf(fl[ax], 64.0f), -64.0f));
+        win &= li < 3u * K::B;
+        packed += rel[ax * 32 + (li < 3u * K::B ? li : 0u)];
       }
-      int lidx = 0;
+      int lidx;
       if (win) {
-        dir = D == 2 ? 9 : 0;
-        int mul = 1;
-#pragma unroll
-        for (int ax = 0; ax < D; ++ax) {
-          const int dl = (loc[ax] >= K::B) - (loc[ax] < 0);
-          dir += (dl + 1) * mul;
-          mul *= 3;
-          lidx += lidx_axis<D>(loc[ax] - K::B * dl, ax);
-        }
+        dir = packed >> 16;
+        lidx = packed & 0xffff;
       } else {
         SlowIn in{};
 #pragma unroll
@@ -440,71 +503,67 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
         const SlowOut r = relocate_slow<D>(t, g, in);
         dir = r.dir;
         lidx = r.lidx;
-        if (dir == kFarSlot) a.far_scratch[ps + q] = r.dest;
+        if (dir == kFarSlot) a.far_scratch[hs + q] = r.dest;
       }
       const bool stay = dir == kSelfDir && lidx == l;
       code[q] = (uint16_t)(lidx | (dir << 10) | (stay ? kStayBit : 0));
     }
     const unsigned peers = __match_any_sync(0xffffffffu, dir);
     const int rank = __popc(peers & ((1u << lane) - 1u));
-    if (act && rank == 0) wc[w * kSlots + dir] = __popc(peers);
-    __syncthreads();
-    if (w < kSlots) {  // warp `w` scans direction w over the 32 warps' counts
-      const int32_t cv = wc[lane * kSlots + w];
-      int32_t x = cv;
+    if (act) {
+      pos[q] = (uint16_t)rank;
+      if (rank == 0) cw[c * kSlots + dir] = (uint16_t)__popc(peers);
+    }
+  }
+  __syncthreads();
+  // exclusive offsets of every (chunk, direction) over the chunks; direction totals
+  for (int d = w; d < kSlots; d += kW) {
+    int32_t carry = 0;
+    for (int c0 = 0; c0 < nc32; c0 += 32) {
+      const int c = c0 + lane;
+      const int32_t v = c < nc32 ? cw[c * kSlots + d] : 0;
+      int32_t x = v;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
       }
-      wc[lane * kSlots + w] = x - cv;
-      if (lane == 31) ctot[c * kSlots + w] = x;
+      if (c < nc32) cw[c * kSlots + d] = (uint16_t)(carry + x - v);
+      carry += __shfl_sync(0xffffffffu, x, 31);
     }
-    __syncthreads();
-    if (act) pos[q] = (uint16_t)(wc[w * kSlots + dir] + rank);
-  }
-  __syncthreads();
-  // direction segments and chunk offsets
-  if (tid < kSlots) {
-    int32_t run = 0;
-    for (int c = 0; c < nchunk; ++c) {
-      const int32_t cv = ctot[c * kSlots + tid];
-      ctot[c * kSlots + tid] = run;
-      run += cv;
-    }
-    dtot[tid] = run;
+    if (lane == 0) dtot[d] = carry;
   }
   __syncthreads();
   if (tid == 0) {
     int32_t sum = 0;
+    const int64_t row = ((int64_t)b * 2 + h) * kSlots;
     for (int k = 0; k < kSlots; ++k) {
       seg[k] = sum;
-      a.cnt[(int64_t)b * kSlots + k] = dtot[k];
-      a.segoff[(int64_t)b * kSlots + k] = sum;
+      a.cnt[row + k] = dtot[k];
+      a.segoff[row + k] = sum;
       sum += dtot[k];
     }
   }
   __syncthreads();
   // final position of every particle (registers), then the inverse map in
   // pos[] so that the writes walk the destination order (coalesced)
-  constexpr int kPer = (kStCap + kStThreads - 1) / kStThreads;
-  int32_t fin[kPer];
+  int32_t fin[kHChunks];
   int movers = 0;
 #pragma unroll
-  for (int u = 0; u < kPer; ++u) {
-    const int32_t q = u * kStThreads + tid;
+  for (int u = 0; u < kHChunks; ++u) {
+    const int32_t q = u * kHThreads + tid;
     fin[u] = -1;
     if (q < nb) {
       const uint16_t cd = code[q];
       const int dir = (cd >> 10) & 31;
-      fin[u] = seg[dir] + ctot[u * kSlots + dir] + pos[q];
+      fin[u] = seg[dir] + cw[(q >> 5) * kSlots + dir] + pos[q];
       movers += !(cd & kStayBit);
       if (dir == kFarSlot) {
         int32_t k = atomicAdd(a.far_n, 1);
         if (k < a.far_cap) {
-          a.far_tidx[k] = ps + fin[u];
+          a.far_tidx[k] = hs + fin[u];
           a.far_src[k] = b;
-          a.far_dest[k] = a.far_scratch[ps + q];
+          a.far_dest[k] = a.far_scratch[hs + q];
         } else {
           atomicOr(a.err, 4);
         }
@@ -513,26 +572,51 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_push_st(DevTree t, Bric
   }
   __syncthreads();
 #pragma unroll
-  for (int u = 0; u < kPer; ++u)
-    if (fin[u] >= 0) pos[fin[u]] = (uint16_t)(u * kStThreads + tid);
+  for (int u = 0; u < kHChunks; ++u)
+    if (fin[u] >= 0) pos[fin[u]] = (uint16_t)(u * kHThreads + tid);
   __syncthreads();
   {
     float *tO[D], *tV[D];
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
-      tO[ax] = a.to + ax * n + ps;
-      tV[ax] = a.tv + ax * n + ps;
+      tO[ax] = a.to + ax * n + hs;
+      tV[ax] = a.tv + ax * n + hs;
     }
-    uint16_t *tC = a.tcode + ps;
-    for (int32_t p = tid; p < nb; p += blockDim.x) {
+    uint16_t *tC = a.tcode + hs;
+    auto put = [&](int32_t p) {
       const int32_t q = pos[p];
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
-        tO[ax][p] = so[offO[ax] + q];
-        tV[ax][p] = sv[offV[ax] + q];
+        tO[ax][p] = O(ax, q);
+        tV[ax][p] = V(ax, q);
       }
       tC[p] = (uint16_t)(code[q] & (kStayBit | 0x3ffu));
-      if (a.ids) a.tids[ps + p] = a.ids[ps + q];
+      if (a.ids) a.tids[hs + p] = a.ids[hs + q];
+    };
+    if (kAligned && !a.ids) {
+      // 16-byte stores: positions p with hs + p a multiple of 4 start a group
+      const int32_t p0 = min((int32_t)((4 - (hs & 3)) & 3), nb);
+      const int32_t ng = (nb - p0) >> 2;
+      if (tid < p0) put(tid);
+      for (int32_t gi = tid; gi < ng; gi += blockDim.x) {
+        const int32_t p = p0 + 4 * gi;
+        int32_t qq[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) qq[k] = pos[p + k];
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+          *reinterpret_cast<float4 *>(tO[ax] + p) = make_float4(O(ax, qq[0]), O(ax, qq[1]), O(ax, qq[2]), O(ax, qq[3]));
+          *reinterpret_cast<float4 *>(tV[ax] + p) = make_float4(V(ax, qq[0]), V(ax, qq[1]), V(ax, qq[2]), V(ax, qq[3]));
+        }
+        const uint32_t c01 = (uint32_t)(code[qq[0]] & (kStayBit | 0x3ffu)) |
+                             ((uint32_t)(code[qq[1]] & (kStayBit | 0x3ffu)) << 16);
+        const uint32_t c23 = (uint32_t)(code[qq[2]] & (kStayBit | 0x3ffu)) |
+                             ((uint32_t)(code[qq[3]] & (kStayBit | 0x3ffu)) << 16);
+        *reinterpret_cast<uint2 *>(tC + p) = make_uint2(c01, c23);
+      }
+      for (int32_t p = p0 + 4 * ng + tid; p < nb; p += blockDim.x) put(p);
+    } else {
+      for (int32_t p = tid; p < nb; p += blockDim.x) put(p);
     }
   }
   if (bad) atomicOr(a.err, 1);
@@ -561,7 +645,7 @@ __global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeo
     bc[ax] = origin[ax] / K::B;
   }
   const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nb = pe - ps;
-  if (nb <= kStCap) return;  // the shared-memory kernel took this brick
+  if (nb <= 2 * kHalfCap) return;  // the shared-memory kernel took this brick (in halves)
   for (int i = tid; i <= K::LB; i += blockDim.x) ls[i] = a.start[L0 + i] - ps;
   for (int i = tid; i < K::LB; i += blockDim.x) dec[i] = g.decodeL[i];
   for (int i = tid; i < K::NVB; i += blockDim.x) {
@@ -608,12 +692,14 @@ __global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeo
     if (dir != 255 && lane == __ffs(peers) - 1) atomicAdd(&counters[dir], __popc(peers));
   }
   __syncthreads();
-  if (tid == 0) {
+  if (tid == 0) {  // the whole brick is half 0; half 1 is empty
     int s = 0;
     for (int k = 0; k < kSlots; ++k) {
       seg[k] = s;
-      a.cnt[(int64_t)b * kSlots + k] = counters[k];
-      a.segoff[(int64_t)b * kSlots + k] = s;
+      a.cnt[(int64_t)b * 2 * kSlots + k] = counters[k];
+      a.segoff[(int64_t)b * 2 * kSlots + k] = s;
+      a.cnt[((int64_t)b * 2 + 1) * kSlots + k] = 0;
+      a.segoff[((int64_t)b * 2 + 1) * kSlots + k] = s;
       s += counters[k];
     }
   }
@@ -729,7 +815,7 @@ __global__ void k_brick_totals(DevTree t, BrickGeom g, const int32_t *cnt, const
   int32_t len = 0;
   if (lane < 27) {
     const int dir = lane;
-    int4 pc = make_int4(0, 0, INT32_MAX, 0);
+    int4 pc0 = make_int4(0, 0, INT32_MAX, 0), pc1 = make_int4(0, 0, INT32_MAX, 1);
     if (!(D == 2 && dir_delta(dir, 2) != 0)) {
       int32_t sc[3] = {0, 0, 0};
       for (int ax = 0; ax < D; ++ax) {
@@ -737,11 +823,15 @@ __global__ void k_brick_totals(DevTree t, BrickGeom g, const int32_t *cnt, const
         sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
       }
       const int32_t src = brick_of_coords<D>(t, sc);
-      const int64_t k = (int64_t)src * kSlots + dir;
-      len = cnt[k];
-      pc = make_int4(old_start[(int64_t)src * BK<D>::LB] + segoff[k], len, src, 0);
+      const int32_t s0 = old_start[(int64_t)src * BK<D>::LB];
+      const int32_t nbs = old_start[(int64_t)(src + 1) * BK<D>::LB] - s0;
+      const int64_t k0 = (int64_t)src * 2 * kSlots + dir, k1 = k0 + kSlots;
+      pc0 = make_int4(s0 + segoff[k0], cnt[k0], src, 0);
+      pc1 = make_int4(s0 + half_start(nbs, 1) + segoff[k1], cnt[k1], src, 1);
+      len = pc0.y + pc1.y;
     }
-    bpiece[b * 27 + dir] = pc;
+    bpiece[((int64_t)b * 27 + dir) * 2] = pc0;
+    bpiece[((int64_t)b * 27 + dir) * 2 + 1] = pc1;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) len += __shfl_down_sync(0xffffffffu, len, o);
@@ -778,7 +868,7 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
   __shared__ int32_t cnt[K::LB + 1];                    // counts, then offsets
   __shared__ int32_t cur[K::LB];
   __shared__ Piece pieces[kMaxPieces];
-  __shared__ Piece sdesc[27];
+  __shared__ Piece sdesc[54];
   __shared__ int32_t pfx[kMaxPieces + 1];
   __shared__ int32_t spfx[kMaxPieces + 1];              // stage offset of round-2 pieces
   __shared__ int32_t wsum[kPullThreads / 32];
@@ -788,28 +878,34 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
   const int64_t n = a.n;
   if (a.tot[b] <= kStCap) return;  // the shared-memory kernel took this brick
 
-  // neighbour segments, one thread per direction, placed by source-brick rank
+  // neighbour segments (two halves each), one thread per direction, placed by
+  // source-brick rank; round 1 = the stayers of this brick's own two halves
   __shared__ int32_t s_src[27];
-  Piece mine{0, 0, INT32_MAX, 0, 0};
+  Piece m0{0, 0, INT32_MAX, 0, 0}, m1{0, 0, INT32_MAX, 0, 0};
   if (tid < 27) {
-    const int4 pc = a.bpiece[(int64_t)b * 27 + tid];
-    mine = Piece{pc.x, pc.y, pc.z, 0, 0};
-    s_src[tid] = mine.src;
+    const int4 p0 = a.bpiece[((int64_t)b * 27 + tid) * 2], p1 = a.bpiece[((int64_t)b * 27 + tid) * 2 + 1];
+    m0 = Piece{p0.x, p0.y, p0.z, 0, 0};
+    m1 = Piece{p1.x, p1.y, p1.z, 0, 0};
+    s_src[tid] = m0.src;
   }
   for (int i = tid; i < K::LB + 1; i += blockDim.x) cnt[i] = 0;
   __syncthreads();
-  if (tid < 27 && mine.src != INT32_MAX) {
+  if (tid < 27 && m0.src != INT32_MAX) {
     int rank = 0;
-    for (int k = 0; k < 27; ++k) rank += s_src[k] < mine.src;
-    sdesc[rank] = mine;
-    if (tid == kSelfDir) pieces[0] = Piece{mine.tstart, mine.len, mine.src, 1, 0};
+    for (int k = 0; k < 27; ++k) rank += s_src[k] < m0.src;
+    sdesc[2 * rank] = m0;
+    sdesc[2 * rank + 1] = m1;
+    if (tid == kSelfDir) {
+      pieces[0] = Piece{m0.tstart, m0.len, m0.src, 1, 0};
+      pieces[1] = Piece{m1.tstart, m1.len, m1.src, 1, 0};
+    }
   }
   __syncthreads();
   if (tid == 0) {
-    const int ns = D == 3 ? 27 : 9;
+    const int ns = 2 * (D == 3 ? 27 : 9);
     // far arrivals (sorted by storage index, so by source brick) go between
     // the neighbour segments as runs of the sorted far list
-    int np = 1;
+    int np = 2;
     int32_t fi = a.fstart[b];
     const int32_t fe = a.fstart[b + 1];
     for (int k = 0; k < ns; ++k) {
@@ -818,14 +914,14 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
         while (fi < fe && a.far_src[fi] < sdesc[k].src) ++fi;
         if (fi > f0) pieces[np++] = Piece{f0, fi - f0, -1, 0, 1};
       }
-      if (sdesc[k].src == b) s_self = np;
+      if (sdesc[k].src == b && (k & 1) == 0) s_self = np;
       pieces[np++] = sdesc[k];
     }
     if (fi < fe) pieces[np++] = Piece{fi, fe - fi, -1, 0, 1};
     int32_t s = 0;
     for (int k = 0; k < np; ++k) {
       pfx[k] = s;
-      spfx[k] = k == 0 ? 0 : s - pieces[0].len;
+      spfx[k] = k < 2 ? 0 : s - pieces[0].len - pieces[1].len;
       s += pieces[k].len;
     }
     pfx[np] = s;
@@ -900,7 +996,7 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       }
       for (int32_t i = lo; i < hi; ++i) {  // raw position -> stage index
         const int32_t r = map[i];
-        map[i] = (uint16_t)(r < pfx[1] ? self_stage + r : r - pfx[1]);
+        map[i] = (uint16_t)(r < pfx[2] ? self_stage + r : r - pfx[2]);
       }
     }
     __syncthreads();
@@ -910,7 +1006,7 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
     for (int arr = 0; arr < na; ++arr) {
       const float *src = arr < D ? a.to + arr * n : (arr < 2 * D ? a.tv + (arr - D) * n : (const float *)a.tids);
       float *dst = arr < D ? a.o + arr * n : (arr < 2 * D ? a.v + (arr - D) * n : (float *)a.ids);
-      for (int k = 1; k < np; ++k) {
+      for (int k = 2; k < np; ++k) {
         const Piece pc = pieces[k];
         const int32_t so = spfx[k];
         for (int32_t i = tid; i < pc.len; i += blockDim.x)
@@ -993,45 +1089,55 @@ __device__ __forceinline__ void build_pieces(const DevTree &t, const BrickGeom &
   (void)s_src;
   const int tid = threadIdx.x, lane = tid & 31;
   constexpr unsigned kAll = 0xffffffffu;
-  if (tid < 32) {  // warp 0: lane = direction of the source brick
-    Piece mine{0, 0, INT32_MAX, 0, 0};
+  if (tid < 32) {  // warp 0: lane = direction of the source brick, two halves each
+    Piece m0{0, 0, INT32_MAX, 0, 0}, m1{0, 0, INT32_MAX, 0, 0};
     if (lane < 27) {
-      const int4 pc = a.bpiece[(int64_t)b * 27 + lane];
-      mine = Piece{pc.x, pc.y, pc.z, 0, 0};
+      const int4 p0 = a.bpiece[((int64_t)b * 27 + lane) * 2], p1 = a.bpiece[((int64_t)b * 27 + lane) * 2 + 1];
+      m0 = Piece{p0.x, p0.y, p0.z, 0, 0};
+      m1 = Piece{p1.x, p1.y, p1.z, 0, 0};
     }
     const int32_t fi0 = a.fstart[b], fe = a.fstart[b + 1];
     int rank = 0;  // sources in ascending brick order = storage order
-    for (int k = 0; k < 27; ++k) rank += __shfl_sync(kAll, mine.src, k) < mine.src;
-    const bool valid = lane < 27 && mine.src != INT32_MAX;
-    const int ns = D == 3 ? 27 : 9;
-    if (lane == kSelfDir) pieces[0] = Piece{mine.tstart, mine.len, mine.src, 1, 0};
+    for (int k = 0; k < 27; ++k) rank += __shfl_sync(kAll, m0.src, k) < m0.src;
+    const bool valid = lane < 27 && m0.src != INT32_MAX;
+    const int ns = 2 * (D == 3 ? 27 : 9);
+    const int32_t len0 = __shfl_sync(kAll, m0.len + m1.len, kSelfDir);  // stayers come from both halves
+    if (lane == 0) pieces[0] = Piece{0, len0, b, 1, 0};
     if (fi0 == fe) {
-      // no far arrivals: the neighbour segments in source order, in parallel
+      // no far arrivals: the neighbour segments in (source, half) order, in parallel
       if (valid) {
-        pieces[1 + rank] = mine;
-        if (mine.src == b) *s_self = 1 + rank;
+        pieces[1 + 2 * rank] = m0;
+        pieces[2 + 2 * rank] = m1;
+        if (m0.src == b) *s_self = 1 + 2 * rank;
       }
       __syncwarp();
-      const int32_t len0 = __shfl_sync(kAll, mine.len, kSelfDir);
-      const int32_t x = lane < ns ? pieces[1 + lane].len : 0;
+      const int32_t x0 = 2 * lane < ns ? pieces[1 + 2 * lane].len : 0;
+      const int32_t x1 = 2 * lane < ns ? pieces[2 + 2 * lane].len : 0;
+      const int32_t x = x0 + x1;
       int32_t incl = x;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int32_t y = __shfl_up_sync(kAll, incl, o);
         if (lane >= o) incl += y;
       }
-      if (lane < ns) {
-        pfx[1 + lane] = len0 + incl - x;
-        spfx[1 + lane] = incl - x;
+      if (2 * lane < ns) {
+        const int32_t ex = incl - x;
+        pfx[1 + 2 * lane] = len0 + ex;
+        spfx[1 + 2 * lane] = ex;
+        pfx[2 + 2 * lane] = len0 + ex + x0;
+        spfx[2 + 2 * lane] = ex + x0;
       }
       if (lane == 0) pfx[0] = spfx[0] = 0;
-      if (lane == ns - 1) {
+      if (2 * lane == ns - 2) {
         pfx[ns + 1] = len0 + incl;
         spfx[ns + 1] = incl;
         *s_np = ns + 1;
       }
     } else {
-      if (valid) sdesc[rank] = mine;
+      if (valid) {
+        sdesc[2 * rank] = m0;
+        sdesc[2 * rank + 1] = m1;
+      }
       __syncwarp();
       if (lane == 0) {
         // far arrivals (sorted by storage index, so by source brick) go
@@ -1044,7 +1150,7 @@ __device__ __forceinline__ void build_pieces(const DevTree &t, const BrickGeom &
             while (fi < fe && a.far_src[fi] < sdesc[k].src) ++fi;
             if (fi > f0) pieces[np++] = Piece{f0, fi - f0, -1, 0, 1};
           }
-          if (sdesc[k].src == b) *s_self = np;
+          if (sdesc[k].src == b && (k & 1) == 0) *s_self = np;
           pieces[np++] = sdesc[k];
         }
         if (fi < fe) pieces[np++] = Piece{fi, fe - fi, -1, 0, 1};
@@ -1093,7 +1199,7 @@ __global__ void __launch_bounds__(kStThreads, 1) k_brick_pull_st(DevTree t, Bric
   __shared__ int32_t cnt[K::LB + 1];
   __shared__ int32_t cur[K::LB];
   __shared__ Piece pieces[kMaxPieces];
-  __shared__ Piece sdesc[27];
+  __shared__ Piece sdesc[54];
   __shared__ int32_t s_src[27];
   __shared__ int32_t pfx[kMaxPieces + 1], spfx[kMaxPieces + 1];
   __shared__ int32_t wsum[32];
@@ -1293,10 +1399,16 @@ void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs
   cudaMemsetAsync(pa.far_n, 0, sizeof(int32_t), s);
   const unsigned nb = (unsigned)g.n_bricks;
   if (g.d == 3) {
-    k_brick_push_st<3><<<nb, kStThreads, push_st_smem<3>(), s>>>(t, g, pa);
+    if (pa.n % 4 == 0)
+      k_brick_push_st<3, true><<<2 * nb, kHThreads, push_st_smem<3>(), s>>>(t, g, pa);
+    else
+      k_brick_push_st<3, false><<<2 * nb, kHThreads, push_st_smem<3>(), s>>>(t, g, pa);
     k_brick_push<3><<<nb, kPushThreads, 0, s>>>(t, g, pa);
   } else {
-    k_brick_push_st<2><<<nb, kStThreads, push_st_smem<2>(), s>>>(t, g, pa);
+    if (pa.n % 4 == 0)
+      k_brick_push_st<2, true><<<2 * nb, kHThreads, push_st_smem<2>(), s>>>(t, g, pa);
+    else
+      k_brick_push_st<2, false><<<2 * nb, kHThreads, push_st_smem<2>(), s>>>(t, g, pa);
     k_brick_push<2><<<nb, kPushThreads, 0, s>>>(t, g, pa);
   }
   count_launches(2);
@@ -1340,14 +1452,18 @@ cudaError_t brick_configure(const BrickGeom &g) {
   cudaError_t e;
   if (g.d == 3) {
     e = cudaFuncSetAttribute(k_brick_pull<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_brick_push_st<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)push_st_smem<3>());
+    for (auto fn : {k_brick_push_st<3, true>, k_brick_push_st<3, false>}) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)push_st_smem<3>());
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_brick_pull_st<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pull_st_smem<3>());
   } else {
     e = cudaFuncSetAttribute(k_brick_pull<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_brick_push_st<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)push_st_smem<2>());
+    for (auto fn : {k_brick_push_st<2, true>, k_brick_push_st<2, false>}) {
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)push_st_smem<2>());
+      if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_brick_pull_st<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pull_st_smem<2>());
   }

@@ -74,7 +74,7 @@ struct BrickPushArgs {
   float *to, *tv;
   uint16_t *tcode;               // destination local leaf | stayer bit
   int32_t *tids;
-  int32_t *cnt, *segoff;         // [n_bricks][28]
+  int32_t *cnt, *segoff;         // [n_bricks][2 halves][28]
   int32_t *far_n;
   int32_t far_cap;
   int32_t *far_tidx, *far_src, *far_dest;
@@ -103,7 +103,7 @@ struct BrickPullArgs {
   int32_t *max_bucket;
   int32_t *err;
   float *part;                   // leaf-corner deposit partials of the new positions, or NULL
-  const int4 *bpiece;            // [n_bricks][27] incoming segment {start, length, source brick}
+  const int4 *bpiece;            // [n_bricks][27][2 halves] incoming segment {start, length, source brick, half}
   int4 *bpiece_w;
 };
 

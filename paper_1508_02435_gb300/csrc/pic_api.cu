@@ -465,8 +465,8 @@ int setup_brick(pic_t h) {
   if ((rc = upload(h, bb, &g.decodeL, dec))) return rc;
   const int64_t n = h->n, nb = g.n_bricks;
   if ((rc = dalloc(h, bb, &h->tcode, n + 32))) return rc;  // bulk copies read whole 16-byte units
-  if ((rc = dalloc(h, bb, &h->bcnt, nb * 28))) return rc;
-  if ((rc = dalloc(h, bb, &h->bsegoff, nb * 28))) return rc;
+  if ((rc = dalloc(h, bb, &h->bcnt, nb * 2 * 28))) return rc;  // [brick][half][direction]
+  if ((rc = dalloc(h, bb, &h->bsegoff, nb * 2 * 28))) return rc;
   if ((rc = dalloc(h, bb, &h->far_n, 2))) return rc;
   if ((rc = dalloc(h, bb, &h->far_tidx, n))) return rc;
   if ((rc = dalloc(h, bb, &h->far_src, n))) return rc;
@@ -478,7 +478,7 @@ int setup_brick(pic_t h) {
   if ((rc = dalloc(h, bb, &h->fstart, nb + 1))) return rc;
   if ((rc = dalloc(h, bb, &h->btot, nb))) return rc;
   if ((rc = dalloc(h, bb, &h->bstart, nb + 1))) return rc;
-  if ((rc = dalloc(h, bb, &h->bpiece, nb * 27))) return rc;
+  if ((rc = dalloc(h, bb, &h->bpiece, nb * 27 * 2))) return rc;
   if (scan_tiles_needed(nb) + 1 > scan_tiles_needed(h->dt.n_keys) + 1)
     return fail(h, PIC_EINVAL, "brick count exceeds scan scratch");
   CK(brick_configure(g));
