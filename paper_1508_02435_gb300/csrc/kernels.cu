@@ -922,6 +922,17 @@ void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *m
   { COUNT(1); k_count_all<<<grid_for(n, b), b, 0, s>>>(key, n, count, mover_words, block_movers); }
 }
 
+// Flag = 1 if keys are not in ascending order.
+__global__ void k_check_sorted(const int32_t *key, int64_t n, int32_t *flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool bad = i + 1 < n && key[i] > key[i + 1];
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+void launch_check_sorted(const int32_t *key, int64_t n, int32_t *flag, cudaStream_t s) {
+  if (n > 1) { COUNT(1); k_check_sorted<<<grid_for(n), kBlock, 0, s>>>(key, n, flag); }
+}
+
 void launch_fine_keys(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n, int dmax,
                       uint32_t *key, cudaStream_t s) {
   if (n <= 0) return;

@@ -124,6 +124,7 @@ void launch_init32(const DevTree &t, const double *x, const double *v, int64_t n
                    float *vf, int32_t *key, int32_t *err, cudaStream_t s);
 void launch_rekey32(const DevTree &t, const int32_t *leaf, const float *o, int64_t n, int32_t *key, int32_t *err,
                     cudaStream_t s);
+void launch_check_sorted(const int32_t *key, int64_t n, int32_t *flag, cudaStream_t s);
 void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *mover_words,
                       int32_t *block_movers, int block, cudaStream_t s);
 // Re-refinement: depth-first cell index on level dmax per particle; cells of

@@ -620,13 +620,34 @@ int rebin_and_gather(pic_t h, const int32_t *old_start) {
   return PIC_OK;
 }
 
-// Keys of fresh state in [1] -> counts -> re-bin.
+// Keys of fresh state in [1] -> counts -> re-bin.  Fresh particles are all
+// movers, so the canonical order is the stable order by key; when the keys
+// already ascend (a state read back by pic_get_state, for example) that is the
+// input order and only the bucket offsets are computed.
 int bin_fresh(pic_t h) {
   h->q_valid = false;
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(h->count, 0, sizeof(int32_t) * h->dt.n_keys, s));
   launch_count_all(h->key[1], h->n, h->count, h->mover_words, h->block_movers, h->dt.block_push, s);
-  return rebin_and_gather(h, nullptr);
+  CK(cudaMemsetAsync(h->scalars + 6, 0, sizeof(int32_t), s));
+  launch_check_sorted(h->key[1], h->n, h->scalars + 6, s);
+  int32_t unsorted = 1;
+  CK(cudaMemcpyAsync(&unsorted, h->scalars + 6, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (unsorted) return rebin_and_gather(h, nullptr);
+  launch_exclusive_scan(h->count, h->dt.n_keys, h->start_new, h->tile_sums, h->scalars + 0, s);
+  std::swap(h->pos[0], h->pos[1]);
+  std::swap(h->vel[0], h->vel[1]);
+  std::swap(h->leaf[0], h->leaf[1]);
+  if (h->key[0] != h->leaf[1]) std::swap(h->key[0], h->key[1]);  // PIT keys alias the leaves
+  else {
+    h->key[0] = h->leaf[0];
+    h->key[1] = h->leaf[1];
+  }
+  std::swap(h->start_cur, h->start_new);
+  h->leaf_stale = false;
+  CK(cudaGetLastError());
+  return PIC_OK;
 }
 
 int deposit(pic_t h) {

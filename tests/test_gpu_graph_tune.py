@@ -136,3 +136,40 @@ def test_tuning_rejects_bad_values():
         g.set_tuning([1, 256, 256, 256])   # no brick path on an adaptive tree
     with pytest.raises(pic.PicError):
         g.set_tuning([0, 96, 256, 256])
+
+
+@pytest.mark.parametrize("scheme", [pic.PIT, pic.PIDT])
+def test_set_state_sorted_and_shuffled(scheme):
+    """A state read back by get_state (keys ascending) re-enters unchanged and
+    without a re-sort; the same particles shuffled go through the full re-bin,
+    whose result is the stable sort of the shuffled input by key."""
+    flags, x, v = case(3, "uniform", 50_000)
+    kw = dict(scheme=scheme, precision=pic.FP32_SPLIT, q=-2e-5, qm=-1.0, ion=1.0, sweeps=5)
+    a = pic.Pic(3, flags, x, v, **kw)
+    b = pic.Pic(3, flags, x, v, **kw)
+    a.step(0.05)
+    b.step(0.05)
+    leaf, o, vv = a.get_state()
+    keys = a.keys()
+    start0, _ = a.bins(with_ids=False)
+    a.set_state(leaf, o, vv)                       # ascending keys: fast path
+    a.sync()
+    for u, w in zip(a.get_state(), (leaf, o, vv)):
+        assert np.array_equal(u, w)
+    assert np.array_equal(a.bins(with_ids=False)[0], start0) and np.array_equal(a.keys(), keys)
+    perm = np.random.default_rng(1).permutation(leaf.size)
+    b.set_state(np.ascontiguousarray(leaf[perm]), np.ascontiguousarray(o[:, perm]),
+                np.ascontiguousarray(vv[:, perm]))  # shuffled: full re-bin
+    b.sync()
+    order = perm[np.argsort(keys[perm], kind="stable")]
+    lb, ob, vb = b.get_state()
+    assert np.array_equal(lb, leaf[order]) and np.array_equal(ob, o[:, order]) and np.array_equal(vb, vv[:, order])
+    assert np.array_equal(b.bins(with_ids=False)[0], start0)
+    # the fast path keeps stepping like an untouched handle
+    c = pic.Pic(3, flags, x, v, **kw)
+    c.step(0.05)
+    for _ in range(2):
+        a.step(0.05)
+        c.step(0.05)
+    for u, w in zip(a.get_state(), c.get_state()):
+        assert np.array_equal(u, w)
