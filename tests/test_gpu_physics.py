@@ -79,3 +79,44 @@ def test_langmuir_frequency_3d_brick_path():
     target = kinetic_root(2 * math.pi * 0.05)
     assert abs(om / target - 1) < 0.03, (om, target)
     assert g.stats().error == 0
+
+
+@pytest.mark.parametrize("d,depth,ppc", [(2, 3, 16), (3, 3, 8)])
+def test_split_precision_error_per_result(d, depth, ppc):
+    """FP32 split (int32 leaf + FP32 offset) against FP64 on the GPU after 50
+    steps of the Langmuir set-up, per result: deposited density, field,
+    positions and velocities (the same errors as the two oracles give:
+    about 2e-6 relative for density and field, 3e-7 L for positions)."""
+    w = W.langmuir(d, depth, ppc, vth=0.05)
+    kw = dict(scheme=pic.PIT, q=w.q, qm=w.qm, ion=w.ion, sweeps=50, omega=0.8)
+    a = pic.Pic(d, w.flags, w.x, w.v, precision=pic.FP64, **kw)
+    b = pic.Pic(d, w.flags, w.x, w.v, precision=pic.FP32_SPLIT, **kw)
+    for g in (a, b):
+        g.init_leapfrog(w.dt)
+    for _ in range(50):
+        a.step(w.dt)
+        b.step(w.dt)
+    rel = lambda x, y: float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
+    assert rel(b.deposit(), a.deposit()) < 1e-5
+    assert rel(b.field(), a.field()) < 1e-5
+    xa, va = a.particles()
+    xb, vb = b.particles()
+    ia, ib = np.argsort(a.bins()[1]), np.argsort(b.bins()[1])
+    dx = np.abs(xa[:, ia] - xb[:, ib])
+    dx = np.minimum(dx, 1.0 - dx)
+    assert dx.max() < 2e-6
+    assert rel(vb[:, ib], va[:, ia]) < 5e-6
+
+
+def test_split_precision_frequency():
+    """Measured Langmuir frequency, FP32 split against FP64 (same workload):
+    within 0.1% of each other."""
+    pytest.importorskip("scipy")
+    w = W.langmuir(2, 3, 64, vth=0.05)
+    om = []
+    for prec in (pic.FP64, pic.FP32_SPLIT):
+        g = pic.Pic(2, w.flags, w.x, w.v, scheme=pic.PIT, precision=prec, q=w.q, qm=w.qm, ion=w.ion,
+                    sweeps=400, omega=1.0)
+        g.init_leapfrog(w.dt)
+        om.append(measure_omega(g, w, 200, 6.0))
+    assert abs(om[1] / om[0] - 1) < 1e-3, om
