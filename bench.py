@@ -251,6 +251,7 @@ def main():
                     choices=["langmuir3d", "langmuir3d-small", "langmuir2d"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -280,8 +281,30 @@ def main():
     g = pic.Pic(d, w.flags, w.x, w.v, scheme=pic.PIT, precision=pic.FP32_SPLIT if split else pic.FP64,
                 q=w.q, qm=w.qm, ion=w.ion, sweeps=10, omega=0.8, track_ids=False, stream=stream)
     n = g.n
-    del w.x, w.v
     g.init_leapfrog(w.dt)
+    fp64 = None
+    if split and not args.no_fp64 and world == 1:
+        # the same workload in FP64 (generic kernels), timed apart: the metric
+        # compares FP32 split with FP64
+        g64 = pic.Pic(d, w.flags, w.x, w.v, scheme=pic.PIT, precision=pic.FP64, q=w.q, qm=w.qm, ion=w.ion,
+                      sweeps=10, omega=0.8, track_ids=False, stream=stream)
+        g64.init_leapfrog(w.dt)
+        for _ in range(3):
+            g64.step_fixed_field(w.dt)
+        g64.sync()
+        k64 = max(5, min(args.steps, 20))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k64):
+            g64.step_fixed_field(w.dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / k64
+        fp64 = {"value": n / (ms64 / 1e3), "unit": "particle-updates/s", "ms_per_step": ms64, "steps": k64,
+                "path": "generic kernels (FP64 positions and velocities, 132 B per particle-step)",
+                "step_roofline_frac": STEP_BYTES[(d, 0)] * n / (ms64 / 1e3) / 1e9 / float(load_peaks()[0]["hbm_gbs"])}
+        g64.close()
+    del w.x, w.v
     for _ in range(max(args.warmup, 3)):
         g.step_fixed_field(w.dt)
     g.sync()
@@ -375,6 +398,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": "particle-updates/s", "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes, "steps": args.e2e_steps},
     }
+    if fp64 is not None:
+        out["fp64"] = fp64
     if world == 1 and not args.no_cpu_baseline:
         rate, info = oracle_rate(d, split, 0, args.oracle_seconds)
         out["cpu_baseline"] = {"value": rate, "unit": "particle-updates/s", **info}
