@@ -241,6 +241,53 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_batch(args):
+    """256 independent 2D Langmuir instances of uneven size (particle counts
+    log-uniform 1e3..1e6, depths 3..5) in one handle: one launch per phase over
+    all instances, the fixed-field step captured in a CUDA graph after the
+    autotuner picked the block shapes; FP32 split, and FP64 for comparison."""
+    import torch
+    from paper_1508_02435_gb300 import pic
+
+    insts = W.batched_langmuir(256, 1000, 1_000_000)
+    n = sum(w.n for w in insts)
+    out = {"metric": METRIC, "unit": "particle-updates/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "data": "synthetic",
+           "config": {"workload": f"batch of 256 2D Langmuir instances, {n} particles, depths 3-5, "
+                                  "particle counts log-uniform 1e3..1e6",
+                      "scheme": "PIT", "d": 2, "parallelism": "1 GPU",
+                      "l2": "inputs larger than L2 (state > 1 GB)", "field": "held fixed (solve timed apart)"}}
+    res = {}
+    for prec, name in ((pic.FP32_SPLIT, "fp32_split"), (pic.FP64, "fp64")):
+        stream = torch.cuda.Stream()
+        g = pic.Pic.batch(2, [w.flags for w in insts], [w.x for w in insts], [w.v for w in insts],
+                          qs=[w.q for w in insts], scheme=pic.PIT, precision=prec, sweeps=10, omega=0.8,
+                          track_ids=False, stream=stream)
+        g.init_leapfrog(0.1)
+        tuned = g.autotune(0.1, trials=2)
+        g.graph_capture(0.1)
+        g.graph_launch(max(args.warmup, 3))
+        g.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.graph_launch(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        if g.stats().error:
+            raise SystemExit("device reported non-finite particle state")
+        res[name] = {"value": n / (ms / 1e3), "ms_per_step": ms, "tuning": tuned,
+                     "step_roofline_frac": STEP_BYTES[(2, 1 if prec == pic.FP32_SPLIT else 0)] * n
+                     / (ms / 1e3) / 1e9 / float(load_peaks()[0]["hbm_gbs"])}
+        g.close()
+    out.update(value=res["fp32_split"]["value"], ms_per_step=res["fp32_split"]["ms_per_step"], dtype="f32",
+               fp64=res["fp64"], tuning=res["fp32_split"]["tuning"],
+               step_roofline={"bytes_per_particle": STEP_BYTES[(2, 1)],
+                              "frac": res["fp32_split"]["step_roofline_frac"]})
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -248,7 +295,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="langmuir3d",
-                    choices=["langmuir3d", "langmuir3d-small", "langmuir2d"])
+                    choices=["langmuir3d", "langmuir3d-small", "langmuir2d", "batch256"])
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
@@ -256,6 +303,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch256":
+        return run_batch(args)
 
     import torch
 
