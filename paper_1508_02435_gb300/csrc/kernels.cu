@@ -692,10 +692,19 @@ __global__ void k_mover_slots(const int32_t *movers, const int32_t *n_movers, co
 }
 
 // The movers of every bucket in storage order (undoes the atomic slot order).
-__global__ void k_sort_segments(const int32_t *new_start, const int32_t *n_stay, int64_t n_keys, int32_t *perm) {
+// Segments longer than kSmallSeg are listed for k_sort_large.
+constexpr int kSmallSeg = 32;
+constexpr int kLargeSeg = 16384;     // longest segment sorted in shared memory
+constexpr int kLargeThreads = 256;
+__global__ void k_sort_segments(const int32_t *new_start, const int32_t *n_stay, int64_t n_keys, int32_t *perm,
+                                int32_t *large, int32_t *n_large) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_keys) return;
   int32_t b = new_start[k] + n_stay[k], e = new_start[k + 1];
+  if (e - b > kSmallSeg) {
+    large[atomicAdd(n_large, 1)] = (int32_t)k;
+    return;
+  }
   for (int32_t i = b + 1; i < e; ++i) {
     int32_t x = perm[i];
     int32_t j = i - 1;
@@ -704,6 +713,55 @@ __global__ void k_sort_segments(const int32_t *new_start, const int32_t *n_stay,
       --j;
     }
     perm[j + 1] = x;
+  }
+}
+
+// One block per long segment (grid-stride over the list): a bitonic sort in
+// shared memory, padded to a power of two; longer than kLargeSeg, one thread
+// sorts by insertion.
+__global__ void __launch_bounds__(kLargeThreads) k_sort_large(const int32_t *new_start, const int32_t *n_stay,
+                                                              const int32_t *large, const int32_t *n_large,
+                                                              int32_t *perm) {
+  extern __shared__ int32_t sv[];
+  const int nl = *n_large;
+  for (int li = blockIdx.x; li < nl; li += gridDim.x) {
+    const int32_t k = large[li];
+    const int32_t b = new_start[k] + n_stay[k], m = new_start[k + 1] - b;
+    if (m > kLargeSeg) {
+      if (threadIdx.x == 0)
+        for (int32_t i = b + 1; i < b + m; ++i) {
+          const int32_t x = perm[i];
+          int32_t j = i - 1;
+          while (j >= b && perm[j] > x) {
+            perm[j + 1] = perm[j];
+            --j;
+          }
+          perm[j + 1] = x;
+        }
+      __syncthreads();
+      continue;
+    }
+    int P = 1;
+    while (P < m) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sv[i] = i < m ? perm[b + i] : INT32_MAX;
+    __syncthreads();
+    for (int kk = 2; kk <= P; kk <<= 1)
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+          const int l = i ^ jj;
+          if (l > i) {
+            const int32_t x = sv[i], y = sv[l];
+            const bool up = (i & kk) == 0;
+            if ((x > y) == up) {
+              sv[i] = y;
+              sv[l] = x;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[b + i] = sv[i];
+    __syncthreads();
   }
 }
 
@@ -873,6 +931,9 @@ cudaError_t set_constants(cudaStream_t s) {
   uint32_t p3[21];
   p3[0] = 1;
   for (int i = 1; i < 21; ++i) p3[i] = p3[i - 1] * 3u;
+  cudaError_t e = cudaFuncSetAttribute(k_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(sizeof(int32_t) * kLargeSeg));
+  if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbolAsync(c_pow3, p3, sizeof(p3), 0, cudaMemcpyHostToDevice, s);
 }
 
@@ -1072,7 +1133,11 @@ void launch_rebin(const RebinArgs &r, cudaStream_t s) {
   { COUNT(1); k_compact_movers<<<gp, bp, 0, s>>>(r.mover_words, r.block_offsets, r.n, r.movers); }
   cudaMemsetAsync(r.cursor, 0, sizeof(int32_t) * r.n_keys, s);
   { COUNT(1); k_mover_slots<<<gp, bp, 0, s>>>(r.movers, r.scalars + 1, r.keyn, r.new_start, r.n_stay, r.cursor, r.perm); }
-  { COUNT(1); k_sort_segments<<<grid_for(r.n_keys), kBlock, 0, s>>>(r.new_start, r.n_stay, r.n_keys, r.perm); }
+  cudaMemsetAsync(r.scalars + 5, 0, sizeof(int32_t), s);
+  { COUNT(1); k_sort_segments<<<grid_for(r.n_keys), kBlock, 0, s>>>(r.new_start, r.n_stay, r.n_keys, r.perm, r.cursor,
+                                                                      r.scalars + 5); }
+  { COUNT(1); k_sort_large<<<304, kLargeThreads, sizeof(int32_t) * kLargeSeg, s>>>(r.new_start, r.n_stay, r.cursor,
+                                                                                  r.scalars + 5, r.perm); }
 }
 
 void launch_gather_f64(const int32_t *perm, int64_t n, int d, const double *src, double *dst, cudaStream_t s) {

@@ -342,3 +342,27 @@ def test_batch_equals_single_instances(scheme, precision):
         k1 = s1.keys()
         assert np.array_equal(gkeys[sl] - gkeys[sl].min() + k1.min(), k1)
         assert np.allclose(gQ[vs[i]:vs[i + 1]], s1.deposit(), rtol=1e-6 if tol == 0 else 1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", [pic.PIT, pic.PIDT])
+def test_crowded_buckets_match_oracle(scheme):
+    """Thousands of particles per leaf, most of them moving: long mover
+    segments (sorted in shared memory) and one over the in-memory limit keep
+    the canonical order bit-exactly."""
+    d = 2
+    flags = W.uniform_tree_flags(d, 2)           # 81 leaves
+    rng = np.random.default_rng(7)
+    n = 160_000
+    x = rng.random((d, n))
+    x[:, :20_000] = 0.5 + 0.01 * rng.random((d, 20_000))   # one crowded corner: > 16384 in a bucket
+    v = rng.uniform(-0.3, 0.3, (d, n))
+    prm = oracle.Params(scheme=scheme, q=-1.0 / n, sweeps=5, omega=0.8)
+    st = oracle.State64(oracle.Tree(d, flags), x, v, prm)
+    g = make(d, flags, x, v, scheme, pic.FP64, q=-1.0 / n, sweeps=5, omega=0.8)
+    for step in range(2):
+        st.step(0.05)
+        g.step(0.05)
+        g.sync()
+        start, ids = g.bins()
+        assert np.array_equal(ids, st.ids), f"storage order step {step}"
+        assert np.array_equal(g.keys(), st.key)
