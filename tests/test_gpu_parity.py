@@ -366,3 +366,70 @@ def test_crowded_buckets_match_oracle(scheme):
         start, ids = g.bins()
         assert np.array_equal(ids, st.ids), f"storage order step {step}"
         assert np.array_equal(g.keys(), st.key)
+
+
+# ---------------------------------------------------------------------------
+# the adaptive configurations, scaled down: steps with periodic re-refinement
+# ---------------------------------------------------------------------------
+
+def _retarget(st, tree, split):
+    """Oracle state moved onto a new tree as fresh particles (all movers,
+    stable by key in storage order), solver warm start reset."""
+    if split:
+        st.tree.rebin32_into(tree, st.leaf, st.o)
+        st.tree = tree
+        st.V = np.zeros(tree.n_vertices, np.float32)
+    else:
+        st.tree = tree
+        st.V = np.zeros(tree.n_vertices)
+    if hasattr(st, "key"):
+        del st.key
+    st.rebin()
+
+
+def _run_adaptive(w, scheme, precision, ppc, dmin, dmax, every, steps):
+    d = w.d
+    prm = oracle.Params(scheme=scheme, q=w.q, qm=w.qm, ion=w.ion, sweeps=10, omega=0.8)
+    tree = oracle.Tree(d, w.flags)
+    split = precision == pic.FP32_SPLIT
+    st = (oracle.State32 if split else oracle.State64)(tree, w.x, w.v, prm)
+    g = make(d, w.flags, w.x, w.v, scheme, precision, q=w.q, qm=w.qm, ion=w.ion, sweeps=10, omega=0.8)
+    for s in range(steps):
+        if s % every == 0:
+            g.adapt(ppc, dmin, dmax)
+            flags = (oracle.retree32(st.tree, st.leaf, st.o, ppc, dmin, dmax) if split
+                     else oracle.retree64(d, st.x, ppc, dmin, dmax))
+            assert np.array_equal(g.tree_flags(), flags), f"tree at step {s}"
+            _retarget(st, oracle.Tree(d, flags), split)
+        st.step(w.dt)
+        g.step(w.dt)
+        g.sync()
+        start, ids = g.bins()
+        assert np.array_equal(ids, st.ids), f"storage order step {s}"
+        assert np.array_equal(g.keys(), st.key), f"keys step {s}"
+        if split:
+            leaf, o, v = g.get_state()
+            assert np.array_equal(leaf, st.leaf) and np.array_equal(o, st.o) and np.array_equal(v, st.v)
+        else:
+            x, v = g.particles()
+            xs = st.x[:, np.argsort(st.ids)]
+            xg = x[:, np.argsort(ids)]
+            assert rel_err(xg, xs) <= REL64
+
+
+@pytest.mark.parametrize("scheme", [pic.PIT, pic.PIDT])
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_SPLIT])
+def test_gaussian_bump_with_rerefinement(scheme, precision):
+    """2D Gaussian bump with a clipped Cauchy tail (tunnelling several cells),
+    refined where a cell holds more than 64 particles, re-refined every 3
+    steps: trees, keys, buckets and states match the oracle."""
+    w = W.gaussian_bump(n=60_000, d=2, base_depth=3, finest_depth=5)
+    _run_adaptive(w, scheme, precision, ppc=64, dmin=3, dmax=5, every=3, steps=7)
+
+
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_SPLIT])
+def test_two_stream_pidt_with_rerefinement(precision):
+    """3D two-stream (beams at +-8 cells per step), PIDT, refined above 32
+    particles per cell, re-refined every 2 steps."""
+    w = W.two_stream(n=60_000, d=3, base_depth=2)
+    _run_adaptive(w, pic.PIDT, precision, ppc=32, dmin=2, dmax=3, every=2, steps=5)
