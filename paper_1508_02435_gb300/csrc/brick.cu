@@ -5,21 +5,25 @@
 // contiguous in the bucket-sorted particle arrays.  One step re-bins every
 // particle (PIT, Algorithm 1 end state) in two passes over the particles:
 //
-//   K1 k_brick_push   one CTA per source brick: stage the brick's vertex
-//                     field in shared memory, gather + kick + drift every
-//                     particle, re-locate it (integer arithmetic, split rule),
-//                     and stably partition it by destination brick direction
-//                     (27 neighbours + "far") into a temporary array.
-//   K2 k_brick_pull   one CTA per destination brick: pull the 27 incoming
-//                     segments (+ far arrivals) in canonical order -- stayers
-//                     first in storage order, then movers in storage order --
-//                     rank them per leaf with per-warp histograms, write the
-//                     new bucket order and the leaf offsets.
+//   K1 k_brick_push_st  two CTAs per SM, one per half brick: the half's
+//                       particle rows land in shared memory by bulk copies,
+//                       the brick's vertex field is staged, every particle is
+//                       gathered, kicked, drifted and re-located (integer
+//                       arithmetic, split rule) and appended to the staging
+//                       area of its destination brick (warp-aggregated slot),
+//                       with its canonical key: moved bit, storage index.
+//   K2 k_brick_pull_st  one CTA per destination brick: its staging area lands
+//                       by bulk copies; leaf counts, scan, slots, and a per-leaf
+//                       sort by key restore the canonical order -- stayers
+//                       first, then movers, each in storage order -- before the
+//                       coalesced writes of the new bucket order and the
+//                       leaf-corner deposit partials.
 //
-// The result is bit-identical to the generic path (same arithmetic, same
-// canonical bucket order), with each particle read twice and written twice
-// and no global atomics on the hot path.
+// Bricks over the shared-memory capacity take global-memory kernels with the
+// same arithmetic.  The result is bit-identical to the generic path.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "dev.cuh"
 #include "launch.hpp"
@@ -28,16 +32,12 @@ namespace pic {
 
 void count_launches(int64_t k);
 
-constexpr int kSlots = 28;           // 27 neighbour directions + far
 constexpr int kFarSlot = 27;
 constexpr int kSelfDir = 13;         // (0, 0, 0)
 constexpr uint16_t kStayBit = 0x8000;
+constexpr uint16_t kMoverCode = 0;   // leaf code flags of an arrival from another leaf
 constexpr int kPushThreads = 512;
 constexpr int kPullThreads = 256;
-constexpr int kPullWarps = kPullThreads / 32;
-constexpr int kMaxPieces = 128;      // round-1 pieces + 2 x 27 segments + 55 runs of far arrivals
-constexpr int kLidxCap = 8192;       // particles per brick with a shared-memory leaf index
-constexpr int kStageCap = 6144;      // particles per brick staged in shared memory
 
 // Compile-time brick shape: B = 9 leaves per axis (two levels).
 template <int D>
@@ -46,7 +46,13 @@ struct BK {
   static constexpr int LB = D == 3 ? 729 : 81;
   static constexpr int NVB = D == 3 ? 1000 : 100;
   static constexpr int NC = 1 << D;
+  static constexpr int LH = (LB + 1) / 2;  // leaves of the first destination half (local leaves [0, LH))
 };
+
+// Destination unit of local leaf lidx of brick b: the brick's leaves are split
+// in two halves, each re-binned by its own CTA.
+template <int D>
+__device__ __forceinline__ int32_t unit_of(int32_t b, int lidx) { return 2 * b + (lidx >= BK<D>::LH); }
 
 // Asynchronous 4-byte global -> shared copies (no register round trip); the
 // issuing thread waits for all of its copies with cp_async_wait_all().
@@ -89,6 +95,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long l
 }
 constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at the maximum SM clock
 constexpr int kErrTimeout = 8;                   // error bit: a bounded device wait gave up
+constexpr int kErrCode = 16;                     // error bit: a staged leaf code outside its brick
 
 __device__ __forceinline__ int dir_delta(int dir, int a) {
   return a == 0 ? dir % 3 - 1 : (a == 1 ? (dir / 3) % 3 - 1 : dir / 9 - 1);
@@ -200,14 +207,8 @@ __device__ __forceinline__ void stage_field(const DevTree &t, const BrickPushArg
 }
 
 // ---------------------------------------------------------------------------
-// K1, shared-memory form: the brick's particles are loaded once, pushed once
-// and kept on chip until their partitioned positions are known.
+// K1, shared-memory form
 // ---------------------------------------------------------------------------
-
-constexpr int kStThreads = 1024;
-constexpr int kLoadBatch = 4;        // particles whose loads one thread keeps in flight
-constexpr int kStCap = 7168;         // particles per brick held in shared memory
-constexpr int kStS = kStCap + 8;     // shared row stride of the K1 stash (room for a 16-byte aligned head)
 
 // Two independent FP32 products in one instruction, each rounded to nearest.
 __device__ __forceinline__ float2 mul2_rn(float2 a, float2 b) {
@@ -283,29 +284,80 @@ __device__ __noinline__ SlowOut relocate_slow(const DevTree &t, const BrickGeom 
   return SlowOut{far ? kFarSlot : dir, li, brick_of_coords<D>(t, dbc)};
 }
 
-// K1 runs two CTAs per SM: each takes one half of a brick's particles
-// (storage order) and partitions that half by direction on its own, so a
-// brick's segment towards one neighbour is two runs, half 0 then half 1.
+// K1 runs two CTAs per SM, each on one half of a brick's particles (storage
+// order); bricks with more than 2 kHalfCap particles take k_brick_push.
 constexpr int kHThreads = 512;
+constexpr int kUnitSlots = 56;       // destination units by direction: 27 neighbour bricks x 2 halves (+ pad)
 constexpr int kHalfCap = 3040;       // particles of one half held in shared memory
 constexpr int kHS = kHalfCap + 8;    // shared row stride (room for a 16-byte aligned head)
-constexpr int kHChunks = (kHalfCap + kHThreads - 1) / kHThreads;
-constexpr int kH32 = (kHalfCap + 31) / 32;  // 32-particle chunks of one half
 
-// First storage offset (within the brick) of half h of a brick holding nb
-// particles: halves of the shared-memory kernel, or everything in half 0 for
-// bricks that the global-memory kernel takes.
-__host__ __device__ __forceinline__ int32_t half_start(int32_t nb, int h) {
-  if (h == 0) return 0;
-  return nb <= 2 * kHalfCap ? (nb + 1) / 2 : nb;
-}
+// First storage offset (within the brick) of half h of a brick holding nb particles.
+__host__ __device__ __forceinline__ int32_t half_start(int32_t nb, int h) { return h == 0 ? 0 : (nb + 1) / 2; }
 
 template <int D>
 size_t push_st_smem() {
   using K = BK<D>;
-  return sizeof(float) * 2 * D * kHS + sizeof(uint16_t) * 2 * kHalfCap + sizeof(typename EVec<D>::T) * K::NVB +
-         sizeof(int32_t) * (K::LB + 1) + sizeof(uint32_t) * K::LB + sizeof(uint16_t) * kH32 * kSlots +
-         sizeof(int32_t) * 2 * kSlots + sizeof(int32_t) * 3 * 32;
+  return sizeof(float) * 2 * D * kHS + sizeof(uint16_t) * kHalfCap + sizeof(typename EVec<D>::T) * K::NVB +
+         sizeof(int32_t) * (K::LB + 1) + sizeof(uint32_t) * K::LB + sizeof(int32_t) * (3 * 32 + 32) +
+         sizeof(uint8_t) * kHalfCap + sizeof(int32_t) * (kHThreads / 32) * kUnitSlots;
+}
+
+// Writes one arrival into slot `slot` of brick dest's staging area, or into
+// the overflow list when the area is full.
+template <int D>
+__device__ __forceinline__ void stage_put(const BrickStage &st, int32_t dest, int32_t slot, const float *on,
+                                          const float *vn, uint16_t code, uint32_t key, int32_t id, bool with_id,
+                                          int32_t *err) {
+  if (slot < st.cap) {
+    const int64_t at = (int64_t)dest * st.cap + slot;
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+      st.o[ax * st.row + at] = on[ax];
+      st.v[ax * st.row + at] = vn[ax];
+    }
+    st.code[at] = code;
+    st.key[at] = key;
+    if (with_id) st.id[at] = id;
+  } else {
+    const int32_t k = atomicAdd(st.ovf_n, 1);
+    if (k >= st.ovf_cap) {
+      atomicOr(err, 4);
+      return;
+    }
+    st.ovf_dest[k] = dest;
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+      st.ovf_o[ax * (int64_t)st.ovf_cap + k] = on[ax];
+      st.ovf_v[ax * (int64_t)st.ovf_cap + k] = vn[ax];
+    }
+    st.ovf_code[k] = code;
+    st.ovf_key[k] = key;
+    if (with_id) st.ovf_id[k] = id;
+  }
+}
+
+// Appends the pushed particles of one warp to the staging areas of their
+// destination bricks: one global atomic per distinct destination of the warp,
+// lanes in lane order; arrivals beyond the area's capacity go to the overflow
+// list.  Inactive lanes pass dest < 0.
+template <int D>
+__device__ __forceinline__ void stage_append(const BrickStage &st, int32_t dest, const float *on, const float *vn,
+                                             uint16_t code, uint32_t key, int32_t id, bool with_id,
+                                             int32_t *err) {
+  const int lane = threadIdx.x & 31;
+  unsigned todo = __ballot_sync(0xffffffffu, dest >= 0);
+  int32_t slot = -1;
+  while (todo) {
+    const int leader = __ffs(todo) - 1;
+    const int32_t dd = __shfl_sync(0xffffffffu, dest, leader);
+    const unsigned m = __ballot_sync(0xffffffffu, dest == dd);
+    int32_t base = 0;
+    if (lane == leader) base = atomicAdd(&st.fill[dd], __popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (dest == dd) slot = base + __popc(m & ((1u << lane) - 1u));
+    todo &= ~m;
+  }
+  if (dest >= 0) stage_put<D>(st, dest, slot, on, vn, code, key, id, with_id, err);
 }
 
 // K1, shared-memory form, one CTA per half brick.  Same arithmetic as
@@ -320,23 +372,22 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
   extern __shared__ __align__(128) float smf[];
   float *so = smf;                                   // D rows of kHS offsets
   float *sv = so + D * kHS;                          // D rows of kHS velocities
-  uint16_t *code = (uint16_t *)(sv + D * kHS);       // new local leaf | dir << 10 | stay << 15
-  uint16_t *pos = code + kHalfCap;                   // local leaf, rank in (chunk, dir), then inverse map
+  uint16_t *pos = (uint16_t *)(sv + D * kHS);        // local leaf of every particle of the half
   EV *Eb = (EV *)(pos + kHalfCap);                   // NVB staged field vectors
   int32_t *ls = (int32_t *)(Eb + K::NVB);            // LB + 1 absolute leaf offsets
   uint32_t *dec = (uint32_t *)(ls + K::LB + 1);      // LB
-  uint16_t *cw = (uint16_t *)(dec + K::LB);          // kH32 x kSlots: per 32-particle chunk and
-                                                     // direction counts, then exclusive offsets
-  int32_t *seg = (int32_t *)(cw + kH32 * kSlots);    // kSlots
-  int32_t *dtot = seg + kSlots;                      // kSlots
-  int32_t *rel = dtot + kSlots;                      // 3 x 32: per-axis direction | leaf-index parts
+  int32_t *rel = (int32_t *)(dec + K::LB);           // 3 x 32: per-axis direction | leaf-index parts
+  int32_t *nbr = rel + 3 * 32;                       // 27 neighbour bricks by direction
+  int32_t *wc = nbr + 32;                            // [warp][unit slot] arrivals, then offsets
+  uint8_t *lslot = (uint8_t *)(wc + kW * kUnitSlots); // rank within (warp, unit slot)
+  __shared__ int32_t dbase[kUnitSlots];              // first reserved staging slot per unit slot
   __shared__ int32_t s_movers;
   __shared__ uint64_t s_bar;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int32_t b = blockIdx.x >> 1, h = blockIdx.x & 1, L0 = b * K::LB;
-  const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nbr = pe - ps;
-  if (nbr > 2 * kHalfCap) return;  // the global-memory kernel takes this brick
-  const int32_t q0 = half_start(nbr, h), q1 = h ? nbr : half_start(nbr, 1), nb = q1 - q0;
+  const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nbr_n = pe - ps;
+  if (nbr_n > 2 * kHalfCap) return;  // the global-memory kernel takes this brick
+  const int32_t q0 = half_start(nbr_n, h), q1 = h ? nbr_n : half_start(nbr_n, 1), nb = q1 - q0;
   const int32_t hs = ps + q0;  // storage index of this half's first particle
   const int64_t n = a.n;
   int32_t origin[3] = {0, 0, 0}, bc[3] = {0, 0, 0};
@@ -364,8 +415,15 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
     const int dl = (loc >= K::B) - (loc < 0);
     const int p3 = ax == 0 ? 1 : (ax == 1 ? 3 : 9);
     rel[ax * 32 + tid % 27] = ((dl + 1) * p3 << 16) | lidx_axis<D>(loc - K::B * dl, ax);
+  } else if (tid >= 128 && tid < 128 + 27) {  // neighbour brick in direction tid - 128
+    const int dir = tid - 128;
+    int32_t sc[3] = {0, 0, 0};
+    for (int ax = 0; ax < D; ++ax) {
+      const int32_t x = bc[ax] + dir_delta(dir, ax);
+      sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
+    }
+    nbr[dir] = (D == 2 && dir_delta(dir, 2) != 0) ? -1 : brick_of_coords<D>(t, sc);
   }
-  for (int i = tid; i < kH32 * kSlots / 2; i += blockDim.x) reinterpret_cast<uint32_t *>(cw)[i] = 0u;
   // the half's particle rows: one bulk copy per row from the 16-byte boundary
   // at or below its first particle; row r holds particle q at index off[r] + q
   int32_t offO[D], offV[D];
@@ -376,11 +434,10 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
     if (r < D) offO[r] = r * kHS + head;
     else offV[r - D] = (r - D) * kHS + head;
   }
-  // with n a multiple of 4 every row has the same head, so row ax of particle
-  // q sits a compile-time distance from row 0
   const int32_t h0 = offO[0];
   auto O = [&](int ax, int32_t q) -> float & { return kAligned ? so[ax * kHS + h0 + q] : so[offO[ax] + q]; };
   auto V = [&](int ax, int32_t q) -> float & { return kAligned ? sv[ax * kHS + h0 + q] : sv[offV[ax] + q]; };
+  for (int i = tid; i < kW * kUnitSlots; i += blockDim.x) wc[i] = 0;
   if (tid == 0) {
     s_movers = 0;
     if (nb > 0) {
@@ -415,16 +472,22 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
   }
   __syncthreads();
 
-  // push every particle once, warp by warp over chunks of 32 consecutive
-  // particles: rank within (chunk, direction) by a warp match, chunk counts
-  // into cw[]; no block barrier until every particle is pushed
+  // pass A: push every particle once; the new state goes back to its shared
+  // slot and its leaf code gains the destination direction (bits 10-14).  Its
+  // unit slot (direction, destination half) and its rank among the arrivals
+  // of its warp for that slot are noted; per-warp counts go to wc[].  The
+  // pull restores the canonical order, so any order of the slots will do.
+  // Arrivals beyond the neighbour bricks are appended at once.
   bool bad = false;
+  int movers = 0;
   const int nc32 = (nb + 31) >> 5;
   for (int c = w; c < nc32; c += kW) {
     const int32_t q = c * 32 + lane;
     const bool act = q < nb;
-    int dir = 255;
+    int uslot = -1;  // unit slot 2 direction + destination half; -1: none (idle lane, far arrival)
     if (act) {
+      float on[D], vn[D];
+      int dir;
       const int l = pos[q];
       const uint32_t pk = dec[l];
       const int32_t lc[3] = {(int32_t)(pk & 1023u), (int32_t)((pk >> 10) & 1023u), (int32_t)(pk >> 20)};
@@ -465,29 +528,25 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
         for (int ax = 0; ax < D; ++ax) E[ax] = E[ax] + wgt[e] * ecomp(ev, ax);
       }
       // kick and drift: v += (q/m) dt E, t = o + v s_l
-      float vv[D], tt[D];
-#pragma unroll
-      for (int ax = 0; ax < D; ++ax) {
-        vv[ax] = V(ax, q) + a.qmdt * E[ax];
-        tt[ax] = o[ax] + vv[ax] * a.sl;
-      }
       float fl[D];
       int32_t packed = D == 2 ? (9 << 16) : 0;
       bool win = true;
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
-        if (!isfinite(vv[ax]) || !isfinite(tt[ax])) {
+        vn[ax] = V(ax, q) + a.qmdt * E[ax];
+        float tt = o[ax] + vn[ax] * a.sl;
+        if (!isfinite(vn[ax]) || !isfinite(tt)) {
           bad = true;
-          tt[ax] = 0.0f;
+          tt = 0.0f;
         }
-        fl[ax] = floorf(tt[ax]);
-        O(ax, q) = clamp_off(tt[ax] - fl[ax]);
-        V(ax, q) = vv[ax];
+        fl[ax] = floorf(tt);
+        on[ax] = clamp_off(tt - fl[ax]);
         const uint32_t li = (uint32_t)(lc[ax] + K::B + (int32_t)fmaxf(fminf(fl[ax], 64.0f), -64.0f));
         win &= li < 3u * K::B;
         packed += rel[ax * 32 + (li < 3u * K::B ? li : 0u)];
       }
       int lidx;
+      int32_t dest = -1;
       if (win) {
         dir = packed >> 16;
         lidx = packed & 0xffff;
@@ -503,121 +562,74 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
         const SlowOut r = relocate_slow<D>(t, g, in);
         dir = r.dir;
         lidx = r.lidx;
-        if (dir == kFarSlot) a.far_scratch[hs + q] = r.dest;
+        dest = r.dest;
       }
       const bool stay = dir == kSelfDir && lidx == l;
-      code[q] = (uint16_t)(lidx | (dir << 10) | (stay ? kStayBit : 0));
-    }
-    const unsigned peers = __match_any_sync(0xffffffffu, dir);
-    const int rank = __popc(peers & ((1u << lane) - 1u));
-    if (act) {
-      pos[q] = (uint16_t)rank;
-      if (rank == 0) cw[c * kSlots + dir] = (uint16_t)__popc(peers);
-    }
-  }
-  __syncthreads();
-  // exclusive offsets of every (chunk, direction) over the chunks; direction totals
-  for (int d = w; d < kSlots; d += kW) {
-    int32_t carry = 0;
-    for (int c0 = 0; c0 < nc32; c0 += 32) {
-      const int c = c0 + lane;
-      const int32_t v = c < nc32 ? cw[c * kSlots + d] : 0;
-      int32_t x = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+      movers += !stay;
+      if (dir == kFarSlot) {  // beyond the neighbour bricks: its own slot now
+        const int32_t u = unit_of<D>(dest, lidx);
+        const int32_t slot = atomicAdd(&a.st.fill[u], 1);
+        stage_put<D>(a.st, u, slot, on, vn, (uint16_t)(lidx | kMoverCode), 0x80000000u | (uint32_t)(hs + q),
+                     a.ids ? a.ids[hs + q] : 0, a.ids != nullptr, a.err);
       }
-      if (c < nc32) cw[c * kSlots + d] = (uint16_t)(carry + x - v);
-      carry += __shfl_sync(0xffffffffu, x, 31);
-    }
-    if (lane == 0) dtot[d] = carry;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    int32_t sum = 0;
-    const int64_t row = ((int64_t)b * 2 + h) * kSlots;
-    for (int k = 0; k < kSlots; ++k) {
-      seg[k] = sum;
-      a.cnt[row + k] = dtot[k];
-      a.segoff[row + k] = sum;
-      sum += dtot[k];
-    }
-  }
-  __syncthreads();
-  // final position of every particle (registers), then the inverse map in
-  // pos[] so that the writes walk the destination order (coalesced)
-  int32_t fin[kHChunks];
-  int movers = 0;
-#pragma unroll
-  for (int u = 0; u < kHChunks; ++u) {
-    const int32_t q = u * kHThreads + tid;
-    fin[u] = -1;
-    if (q < nb) {
-      const uint16_t cd = code[q];
-      const int dir = (cd >> 10) & 31;
-      fin[u] = seg[dir] + cw[(q >> 5) * kSlots + dir] + pos[q];
-      movers += !(cd & kStayBit);
-      if (dir == kFarSlot) {
-        int32_t k = atomicAdd(a.far_n, 1);
-        if (k < a.far_cap) {
-          a.far_tidx[k] = hs + fin[u];
-          a.far_src[k] = b;
-          a.far_dest[k] = a.far_scratch[hs + q];
-        } else {
-          atomicOr(a.err, 4);
-        }
-      }
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int u = 0; u < kHChunks; ++u)
-    if (fin[u] >= 0) pos[fin[u]] = (uint16_t)(u * kHThreads + tid);
-  __syncthreads();
-  {
-    float *tO[D], *tV[D];
-#pragma unroll
-    for (int ax = 0; ax < D; ++ax) {
-      tO[ax] = a.to + ax * n + hs;
-      tV[ax] = a.tv + ax * n + hs;
-    }
-    uint16_t *tC = a.tcode + hs;
-    auto put = [&](int32_t p) {
-      const int32_t q = pos[p];
 #pragma unroll
       for (int ax = 0; ax < D; ++ax) {
-        tO[ax][p] = O(ax, q);
-        tV[ax][p] = V(ax, q);
+        O(ax, q) = on[ax];
+        V(ax, q) = vn[ax];
       }
-      tC[p] = (uint16_t)(code[q] & (kStayBit | 0x3ffu));
-      if (a.ids) a.tids[hs + p] = a.ids[hs + q];
-    };
-    if (kAligned && !a.ids) {
-      // 16-byte stores: positions p with hs + p a multiple of 4 start a group
-      const int32_t p0 = min((int32_t)((4 - (hs & 3)) & 3), nb);
-      const int32_t ng = (nb - p0) >> 2;
-      if (tid < p0) put(tid);
-      for (int32_t gi = tid; gi < ng; gi += blockDim.x) {
-        const int32_t p = p0 + 4 * gi;
-        int32_t qq[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) qq[k] = pos[p + k];
-#pragma unroll
-        for (int ax = 0; ax < D; ++ax) {
-          *reinterpret_cast<float4 *>(tO[ax] + p) = make_float4(O(ax, qq[0]), O(ax, qq[1]), O(ax, qq[2]), O(ax, qq[3]));
-          *reinterpret_cast<float4 *>(tV[ax] + p) = make_float4(V(ax, qq[0]), V(ax, qq[1]), V(ax, qq[2]), V(ax, qq[3]));
-        }
-        const uint32_t c01 = (uint32_t)(code[qq[0]] & (kStayBit | 0x3ffu)) |
-                             ((uint32_t)(code[qq[1]] & (kStayBit | 0x3ffu)) << 16);
-        const uint32_t c23 = (uint32_t)(code[qq[2]] & (kStayBit | 0x3ffu)) |
-                             ((uint32_t)(code[qq[3]] & (kStayBit | 0x3ffu)) << 16);
-        *reinterpret_cast<uint2 *>(tC + p) = make_uint2(c01, c23);
-      }
-      for (int32_t p = p0 + 4 * ng + tid; p < nb; p += blockDim.x) put(p);
-    } else {
-      for (int32_t p = tid; p < nb; p += blockDim.x) put(p);
+      pos[q] = (uint16_t)(lidx | (dir << 10) | (stay ? kStayBit : 0));
+      if (dir != kFarSlot) uslot = 2 * dir + (lidx >= K::LH);
     }
+    // lanes of the chunk with the same unit slot agree in all six bits of it
+    unsigned peers = __ballot_sync(0xffffffffu, uslot >= 0);
+#pragma unroll
+    for (int bit = 0; bit < 6; ++bit) {
+      const bool x = (uslot >> bit) & 1;
+      const unsigned bb = __ballot_sync(0xffffffffu, x);
+      peers &= x ? bb : ~bb;
+    }
+    const int leader = uslot >= 0 ? __ffs(peers) - 1 : lane;
+    int32_t r0 = 0;
+    if (uslot >= 0 && lane == leader) {  // one leader per distinct slot: distinct words
+      r0 = wc[w * kUnitSlots + uslot];
+      wc[w * kUnitSlots + uslot] = r0 + __popc(peers);
+    }
+    r0 = __shfl_sync(0xffffffffu, r0, leader);
+    if (uslot >= 0) lslot[q] = (uint8_t)(r0 + __popc(peers & ((1u << lane) - 1u)));
+    __syncwarp();  // the counts are read by other lanes in the next chunk
+  }
+  __syncthreads();
+  // per unit slot: offsets of the warps' runs, then one reservation in the
+  // destination unit's staging area
+  if (tid < 54) {
+    int32_t sum = 0;
+    for (int k = 0; k < kW; ++k) {
+      const int32_t c = wc[k * kUnitSlots + tid];
+      wc[k * kUnitSlots + tid] = sum;
+      sum += c;
+    }
+    dbase[tid] = sum > 0 ? atomicAdd(&a.st.fill[2 * nbr[tid >> 1] + (tid & 1)], sum) : 0;
+  }
+  __syncthreads();
+  // pass B: every arrival to its reserved slot (consecutive particles of a
+  // warp hold consecutive ranks, so the stores coalesce)
+  for (int32_t q = tid; q < nb; q += blockDim.x) {
+    const uint16_t cd = pos[q];
+    const int dir = (cd >> 10) & 31;
+    if (dir == kFarSlot) continue;
+    const int hh = (cd & 0x3ff) >= K::LH;
+    const int us = 2 * dir + hh;
+    const int32_t slot = dbase[us] + wc[((q >> 5) % kW) * kUnitSlots + us] + lslot[q];
+    float on[D], vn[D];
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+      on[ax] = O(ax, q);
+      vn[ax] = V(ax, q);
+    }
+    const bool stay = (cd & kStayBit) != 0;
+    stage_put<D>(a.st, 2 * nbr[dir] + hh, slot, on, vn, (uint16_t)(cd & (kStayBit | 0x3ff)),
+                 (stay ? 0u : 0x80000000u) | (uint32_t)(hs + q), a.ids ? a.ids[hs + q] : 0, a.ids != nullptr,
+                 a.err);
   }
   if (bad) atomicOr(a.err, 1);
   for (int o = 16; o > 0; o >>= 1) movers += __shfl_down_sync(0xffffffffu, movers, o);
@@ -626,139 +638,58 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
   if (tid == 0 && s_movers) atomicAdd(a.n_movers, s_movers);
 }
 
+// K1 for bricks over 2 kHalfCap particles: the same arithmetic (push_core),
+// particles and field read from global memory, one thread per particle.
 template <int D>
 __global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeom g, BrickPushArgs a) {
   using K = BK<D>;
   __shared__ int32_t ls[K::LB + 1];
   __shared__ uint32_t dec[K::LB];
   __shared__ float Eb[D * K::NVB];
-  __shared__ uint16_t lidx[kLidxCap];
-  __shared__ int32_t counters[kSlots], seg[kSlots], run[kSlots];
-  __shared__ int32_t wcnt[(kPushThreads / 32) * kSlots];
   __shared__ int32_t s_movers;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
   const int32_t b = blockIdx.x, L0 = b * K::LB;
+  const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nb = pe - ps;
+  if (nb <= 2 * kHalfCap) return;  // the shared-memory kernel took this brick
   int32_t origin[3] = {0, 0, 0}, bc[3] = {0, 0, 0};
-#pragma unroll
   for (int ax = 0; ax < D; ++ax) {
     origin[ax] = t.leaf_coords[(int64_t)L0 * D + ax];
     bc[ax] = origin[ax] / K::B;
   }
-  const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nb = pe - ps;
-  if (nb <= 2 * kHalfCap) return;  // the shared-memory kernel took this brick (in halves)
   for (int i = tid; i <= K::LB; i += blockDim.x) ls[i] = a.start[L0 + i] - ps;
   for (int i = tid; i < K::LB; i += blockDim.x) dec[i] = g.decodeL[i];
-  for (int i = tid; i < K::NVB; i += blockDim.x) {
-    int lx = i % K::V1, ly = (i / K::V1) % K::V1, lz = D == 3 ? i / (K::V1 * K::V1) : 0;
-    int32_t gx = origin[0] + lx, gy = origin[1] + ly, gz = D == 3 ? origin[2] + lz : 0;
-    if (gx >= t.M) gx -= t.M;
-    if (gy >= t.M) gy -= t.M;
-    if (gz >= t.M) gz -= t.M;
-    int64_t vid = gx + (int64_t)t.M * (gy + (int64_t)t.M * gz);
-#pragma unroll
-    for (int ax = 0; ax < D; ++ax) Eb[ax * K::NVB + i] = a.E[ax * t.n_vert + vid];
-  }
-  if (tid < kSlots) { counters[tid] = 0; run[tid] = 0; }
+  stage_field<D>(t, a, origin, Eb);
   if (tid == 0) s_movers = 0;
   __syncthreads();
-  // particle -> local leaf index
-  for (int l = tid; l < K::LB; l += blockDim.x)
-    for (int32_t q = ls[l]; q < ls[l + 1] && q < kLidxCap; ++q) lidx[q] = (uint16_t)l;
-  __syncthreads();
-  auto local_leaf = [&](int32_t q) -> int {
-    if (q < kLidxCap) return lidx[q];
-    int lo = 0, hi = K::LB;
-    while (hi - lo > 1) {
-      int mid = (lo + hi) >> 1;
-      if (ls[mid] <= q) lo = mid; else hi = mid;
-    }
-    return lo;
-  };
-
-  // pass A: destination counts (warp-aggregated)
   bool bad = false;
-  for (int32_t base = 0; base < nb; base += blockDim.x) {
-    const int32_t q = base + tid;
-    int dir = 255;
-    if (q < nb) {
-      const int l = local_leaf(q);
-      const uint32_t pk = dec[l];
-      const int32_t lc[3] = {(int32_t)(pk & 1023u), (int32_t)((pk >> 10) & 1023u), (int32_t)(pk >> 20)};
-      float on[D], vn[D];
-      int32_t L2;
-      dir = brick_push_one<D>(t, g, a, ps + q, lc, origin, bc, Eb, on, vn, L2, bad);
-    }
-    unsigned peers = __match_any_sync(0xffffffffu, dir);
-    if (dir != 255 && lane == __ffs(peers) - 1) atomicAdd(&counters[dir], __popc(peers));
-  }
-  __syncthreads();
-  if (tid == 0) {  // the whole brick is half 0; half 1 is empty
-    int s = 0;
-    for (int k = 0; k < kSlots; ++k) {
-      seg[k] = s;
-      a.cnt[(int64_t)b * 2 * kSlots + k] = counters[k];
-      a.segoff[(int64_t)b * 2 * kSlots + k] = s;
-      a.cnt[((int64_t)b * 2 + 1) * kSlots + k] = 0;
-      a.segoff[((int64_t)b * 2 + 1) * kSlots + k] = s;
-      s += counters[k];
-    }
-  }
-  __syncthreads();
-
-  // pass B: stable partition by direction
   int movers = 0;
-  const int64_t n = a.n;
   for (int32_t base = 0; base < nb; base += blockDim.x) {
     const int32_t q = base + tid;
     const bool act = q < nb;
-    if (lane < kSlots) wcnt[w * kSlots + lane] = 0;
-    __syncwarp();
-    int dir = 255, l = 0;
+    int32_t dest = -1;
     float on[D], vn[D];
-    int32_t L2 = 0;
+    uint16_t code = 0;
+    uint32_t key = 0;
     if (act) {
-      l = local_leaf(q);
+      int lo = 0, hi = K::LB - 1;  // leaf of storage position q: last l with ls[l] <= q
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ls[mid] <= q) lo = mid;
+        else hi = mid - 1;
+      }
+      const int l = lo;
       const uint32_t pk = dec[l];
       const int32_t lc[3] = {(int32_t)(pk & 1023u), (int32_t)((pk >> 10) & 1023u), (int32_t)(pk >> 20)};
-      dir = brick_push_one<D>(t, g, a, ps + q, lc, origin, bc, Eb, on, vn, L2, bad);
-    }
-    unsigned peers = __match_any_sync(0xffffffffu, dir);
-    int rank = __popc(peers & ((1u << lane) - 1u));
-    if (act && rank == 0) wcnt[w * kSlots + dir] = __popc(peers);
-    __syncthreads();
-    if (tid < kSlots) {
-      int s = run[tid];
-      for (int k = 0; k < nw; ++k) {
-        int c = wcnt[k * kSlots + tid];
-        wcnt[k * kSlots + tid] = s;
-        s += c;
-      }
-      run[tid] = s;
-    }
-    __syncthreads();
-    if (act) {
-      const int32_t pos = ps + seg[dir] + wcnt[w * kSlots + dir] + rank;
-#pragma unroll
-      for (int ax = 0; ax < D; ++ax) {
-        a.to[ax * n + pos] = on[ax];
-        a.tv[ax * n + pos] = vn[ax];
-      }
+      int32_t L2;
+      const int dir = brick_push_one<D>(t, g, a, ps + q, lc, origin, bc, Eb, on, vn, L2, bad);
+      (void)dir;
       const bool stay = L2 == L0 + l;
       movers += !stay;
-      a.tcode[pos] = (uint16_t)(L2 % K::LB) | (stay ? kStayBit : 0);
-      if (a.ids) a.tids[pos] = a.ids[ps + q];
-      if (dir == kFarSlot) {
-        int32_t k = atomicAdd(a.far_n, 1);
-        if (k < a.far_cap) {
-          a.far_tidx[k] = pos;
-          a.far_src[k] = b;
-          a.far_dest[k] = L2 / K::LB;
-        } else {
-          atomicOr(a.err, 4);
-        }
-      }
+      dest = unit_of<D>(L2 / K::LB, L2 % K::LB);
+      code = (uint16_t)((L2 % K::LB) | (stay ? kStayBit : 0));
+      key = (stay ? 0u : 0x80000000u) | (uint32_t)(ps + q);
     }
-    __syncthreads();
+    stage_append<D>(a.st, dest, on, vn, code, key, (a.ids && act) ? a.ids[ps + q] : 0, a.ids != nullptr, a.err);
   }
   if (bad) atomicOr(a.err, 1);
   for (int o = 16; o > 0; o >>= 1) movers += __shfl_down_sync(0xffffffffu, movers, o);
@@ -768,191 +699,267 @@ __global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeo
 }
 
 // ---------------------------------------------------------------------------
-// far arrivals: sorted per destination brick by temporary index
+// between K1 and K2: overflow arrivals grouped by destination, brick totals
 // ---------------------------------------------------------------------------
 
-__global__ void k_far_count(const int32_t *far_n, int32_t far_cap, const int32_t *far_dest, int32_t *fcount) {
-  int32_t nf = min(*far_n, far_cap);
+__global__ void k_ovf_count(const int32_t *ovf_n, int32_t ovf_cap, const int32_t *ovf_dest, int32_t *fcount) {
+  const int32_t nf = min(*ovf_n, ovf_cap);
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x)
-    atomicAdd(&fcount[far_dest[i]], 1);
+    atomicAdd(&fcount[ovf_dest[i]], 1);
 }
 
-__global__ void k_far_scatter(const int32_t *far_n, int32_t far_cap, const int32_t *far_dest,
-                              const int32_t *far_tidx, const int32_t *far_src, const int32_t *fstart,
-                              int32_t *fcursor, int32_t *sorted_tidx, int32_t *sorted_src) {
-  int32_t nf = min(*far_n, far_cap);
+__global__ void k_ovf_scatter(const int32_t *ovf_n, int32_t ovf_cap, const int32_t *ovf_dest, const int32_t *fstart,
+                              int32_t *fcursor, int32_t *sorted) {
+  const int32_t nf = min(*ovf_n, ovf_cap);
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
-    int32_t db = far_dest[i];
-    int32_t k = fstart[db] + atomicAdd(&fcursor[db], 1);
-    sorted_tidx[k] = far_tidx[i];
-    sorted_src[k] = far_src[i];
+    const int32_t db = ovf_dest[i];
+    sorted[fstart[db] + atomicAdd(&fcursor[db], 1)] = i;
   }
 }
 
-// Per destination brick: far arrivals sorted by temporary index (storage
-// order), and the brick's total incoming count.
+__global__ void k_brick_totals(int64_t n_units, int32_t cap, const int32_t *fill, const int32_t *fstart,
+                               int32_t *tot) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n_units) return;
+  tot[u] = min(fill[u], cap) + (fstart[u + 1] - fstart[u]);
+}
+
+// ---------------------------------------------------------------------------
+// K2: one CTA per destination unit (half brick), two CTAs per SM
+// ---------------------------------------------------------------------------
+
+constexpr int kStThreads = 512;
+constexpr int kStCap = 3456;  // arrivals per unit held in shared memory (the largest staging capacity)
+
 template <int D>
-__global__ void k_brick_totals(DevTree t, BrickGeom g, const int32_t *cnt, const int32_t *segoff,
-                               const int32_t *old_start, const int32_t *fstart, int32_t *sorted_tidx,
-                               int32_t *sorted_src, int32_t *tot, int4 *bpiece) {
-  // one warp per destination brick, lane = direction of the source brick
-  const int lane = threadIdx.x & 31;
-  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (b >= g.n_bricks) return;
-  const int32_t fb = fstart[b], fe = fstart[b + 1];
-  if (lane == 0)
-    for (int32_t i = fb + 1; i < fe; ++i) {
-      int32_t x = sorted_tidx[i], y = sorted_src[i], j = i - 1;
-      while (j >= fb && sorted_tidx[j] > x) {
-        sorted_tidx[j + 1] = sorted_tidx[j];
-        sorted_src[j + 1] = sorted_src[j];
-        --j;
-      }
-      sorted_tidx[j + 1] = x;
-      sorted_src[j + 1] = y;
-    }
-  const int32_t L0 = (int32_t)b * BK<D>::LB;
-  int32_t len = 0;
-  if (lane < 27) {
-    const int dir = lane;
-    int4 pc0 = make_int4(0, 0, INT32_MAX, 0), pc1 = make_int4(0, 0, INT32_MAX, 1);
-    if (!(D == 2 && dir_delta(dir, 2) != 0)) {
-      int32_t sc[3] = {0, 0, 0};
-      for (int ax = 0; ax < D; ++ax) {
-        const int32_t x = t.leaf_coords[(int64_t)L0 * D + ax] / 9 - dir_delta(dir, ax);
-        sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
-      }
-      const int32_t src = brick_of_coords<D>(t, sc);
-      const int32_t s0 = old_start[(int64_t)src * BK<D>::LB];
-      const int32_t nbs = old_start[(int64_t)(src + 1) * BK<D>::LB] - s0;
-      const int64_t k0 = (int64_t)src * 2 * kSlots + dir, k1 = k0 + kSlots;
-      pc0 = make_int4(s0 + segoff[k0], cnt[k0], src, 0);
-      pc1 = make_int4(s0 + half_start(nbs, 1) + segoff[k1], cnt[k1], src, 1);
-      len = pc0.y + pc1.y;
-    }
-    bpiece[((int64_t)b * 27 + dir) * 2] = pc0;
-    bpiece[((int64_t)b * 27 + dir) * 2 + 1] = pc1;
-  }
+size_t pull_st_smem() {
+  return (sizeof(float) * 2 * D + sizeof(uint32_t) + 2 * sizeof(uint16_t)) * kStCap;
+}
+
+// Exclusive scan of c over the first nl <= blockDim.x threads of the block
+// (c = 0 beyond); returns this thread's offset.  wsum holds one word per warp.
+__device__ __forceinline__ int32_t block_excl_scan(int32_t c, int32_t *wsum) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int32_t x = c;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) len += __shfl_down_sync(0xffffffffu, len, o);
-  if (lane == 0) tot[b] = len + (fe - fb);
-}
-
-// ---------------------------------------------------------------------------
-// K2
-// ---------------------------------------------------------------------------
-
-struct Piece {
-  int32_t tstart, len, src;
-  int16_t round1;    // 1: keep stayers only; 0: keep movers only
-  int16_t indirect;  // 1: positions tstart.. index the sorted far arrivals
-};
-
-// Round-2 piece holding stage index si: the largest k in [1, np) with
-// spfx[k] <= si (empty pieces share their successor's prefix).
-__device__ __forceinline__ int piece_of(const int32_t *spfx, int np, int32_t si) {
-  int lo = 1, hi = np - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (spfx[mid] <= si) lo = mid;
-    else hi = mid - 1;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-  return lo;
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  int32_t before = 0;
+  for (int k = 0; k < nw; ++k)
+    if (k < w) before += wsum[k];
+  return before + x - c;
 }
 
+template <int D>
+__global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, BrickGeom g, BrickPullArgs a) {
+  using K = BK<D>;
+  extern __shared__ __align__(128) float smf[];
+  float *so = smf;                                   // D rows of kStCap offsets (arrival order)
+  float *sv = so + D * kStCap;                       // D rows of velocities
+  uint32_t *key = (uint32_t *)(sv + D * kStCap);     // canonical keys
+  uint16_t *code = (uint16_t *)(key + kStCap);       // local leaf | stayer bit; later the final position
+  uint16_t *map = code + kStCap;                     // bucket position -> arrival
+  __shared__ int32_t cnt[K::LH + 1];
+  __shared__ int32_t cur[K::LH];
+  __shared__ int32_t wsum[kStThreads / 32];
+  __shared__ int32_t s_max;
+  __shared__ uint64_t s_bar;
+  const int tid = threadIdx.x;
+  const BrickStage &st = a.st;
+  const int32_t u = blockIdx.x, b = u >> 1;
+  const int lf0 = (u & 1) ? K::LH : 0, nlf = (u & 1) ? K::LB - K::LH : K::LH;
+  const int32_t L0 = b * K::LB + lf0;  // first leaf of the unit
+  const int64_t n = a.n;
+  const int32_t nin = st.fill[u];
+  if (nin > st.cap) return;  // the global-memory kernel takes this unit
+  const int64_t at = (int64_t)u * st.cap;
+  if (tid == 0) {
+    s_max = 0;
+    if (nin > 0) {
+      mbar_init(&s_bar, 1);
+      const uint32_t rb = (uint32_t)((nin * 4 + 15) & ~15), cb = (uint32_t)((nin * 2 + 15) & ~15);
+      mbar_expect_tx(&s_bar, 2u * D * rb + rb + cb);
+      for (int ax = 0; ax < D; ++ax) {
+        bulk_g2s(so + ax * kStCap, st.o + ax * st.row + at, rb, &s_bar);
+        bulk_g2s(sv + ax * kStCap, st.v + ax * st.row + at, rb, &s_bar);
+      }
+      bulk_g2s(key, st.key + at, rb, &s_bar);
+      bulk_g2s(code, st.code + at, cb, &s_bar);
+    }
+  }
+  for (int i = tid; i <= nlf; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();  // the barrier is initialised and armed before anyone waits on it
+  {
+    const bool landed = nin == 0 || mbar_wait(&s_bar, 0, kWaitCycles);
+    if (__syncthreads_or(!landed)) {
+      if (!landed) mbar_wait(&s_bar, 0, kWaitCycles);  // let copies in flight land before leaving
+      if (tid == 0) atomicOr(a.err, kErrTimeout);
+      return;
+    }
+  }
+  // leaf counts: four consecutive arrivals per thread, one shared atomic per run
+  bool badc = false;
+  for (int32_t r0 = 4 * tid; r0 < nin; r0 += 4 * kStThreads) {
+    int leaf = -1, run = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (r0 + k >= nin) break;
+      const int lf = (code[r0 + k] & 0x3ff) - lf0;
+      if (lf < 0 || lf >= nlf) {
+        badc = true;
+        continue;
+      }
+      if (lf == leaf) {
+        ++run;
+      } else {
+        if (run) atomicAdd(&cnt[leaf], run);
+        leaf = lf;
+        run = 1;
+      }
+    }
+    if (run) atomicAdd(&cnt[leaf], run);
+  }
+  if (__syncthreads_or(badc)) {  // a staged code names no leaf of the unit
+    if (tid == 0) atomicOr(a.err, kErrCode);
+    return;
+  }
+  // leaf offsets (nlf <= blockDim.x), cursors
+  {
+    const int32_t c = tid < nlf ? cnt[tid] : 0;
+    const int32_t off = block_excl_scan(c, wsum);
+    if (tid < nlf) {
+      cnt[tid] = off;
+      cur[tid] = off;
+      if (c > 0) atomicMax(&s_max, c);
+    }
+    if (tid == 0) cnt[nlf] = nin;
+  }
+  __syncthreads();
+  // bucket positions in any order
+  for (int32_t i = tid; i < nin; i += blockDim.x) map[atomicAdd(&cur[(code[i] & 0x3ff) - lf0], 1)] = (uint16_t)i;
+  __syncthreads();
+  // canonical position of every arrival: its leaf's offset plus the number
+  // of arrivals of the leaf with a smaller key (keys are distinct)
+  for (int32_t j = tid; j < nin; j += blockDim.x) {
+    const int32_t i = map[j];
+    const int lf = (code[i] & 0x3ff) - lf0;
+    const int32_t lo = cnt[lf], hi = cnt[lf + 1];
+    int32_t r = 0;
+    if (hi - lo > 1) {
+      const uint32_t kx = key[i];
+      for (int32_t j2 = lo; j2 < hi; ++j2) r += key[map[j2]] < kx;
+    }
+    code[i] = (uint16_t)(lo + r);
+  }
+  __syncthreads();
+  for (int32_t i = tid; i < nin; i += blockDim.x) map[code[i]] = (uint16_t)i;
+  const int32_t bstart = a.bstart[u];
+  for (int l = tid; l < nlf; l += blockDim.x) a.new_start[L0 + l] = bstart + cnt[l];
+  if (u == 2 * g.n_bricks - 1 && tid == 0) a.new_start[(int64_t)g.n_bricks * K::LB] = bstart + nin;
+  if (tid == 0 && s_max > 0) atomicMax(a.max_bucket, s_max);
+  __syncthreads();
+  // coalesced writes in destination order
+  {
+    float *gO[D], *gV[D];
+#pragma unroll
+    for (int ax = 0; ax < D; ++ax) {
+      gO[ax] = a.o + ax * n + bstart;
+      gV[ax] = a.v + ax * n + bstart;
+    }
+    for (int32_t j = tid; j < nin; j += blockDim.x) {
+      const int32_t i = map[j];
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        gO[ax][j] = so[ax * kStCap + i];
+        gV[ax][j] = sv[ax * kStCap + i];
+      }
+    }
+    if (a.ids)
+      for (int32_t j = tid; j < nin; j += blockDim.x) a.ids[bstart + j] = st.id[at + map[j]];
+  }
+  // deposit partials of the new positions, per leaf in bucket order; the
+  // next particle's offsets are fetched while the current one is summed
+  if (a.part) {
+    for (int l = tid; l < nlf; l += blockDim.x) {
+      float acc[K::NC];
+#pragma unroll
+      for (int e = 0; e < K::NC; ++e) acc[e] = 0.0f;
+      const int32_t lo = cnt[l], hi = cnt[l + 1];
+      float on[D];
+      if (lo < hi) {
+        const int32_t i = map[lo];
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) on[ax] = so[ax * kStCap + i];
+      }
+      for (int32_t j = lo; j < hi; ++j) {
+        float o[D], om[D];
+#pragma unroll
+        for (int ax = 0; ax < D; ++ax) {
+          o[ax] = on[ax];
+          om[ax] = 1.0f - o[ax];
+        }
+        if (j + 1 < hi) {
+          const int32_t i = map[j + 1];
+#pragma unroll
+          for (int ax = 0; ax < D; ++ax) on[ax] = so[ax * kStCap + i];
+        }
+#pragma unroll
+        for (int e = 0; e < K::NC; ++e) {
+          float wgt = 1.0f;
+#pragma unroll
+          for (int ax = 0; ax < D; ++ax) wgt = wgt * (((e >> ax) & 1) ? o[ax] : om[ax]);
+          acc[e] = acc[e] + wgt;
+        }
+      }
+      float *gp = a.part + (int64_t)(L0 + l) * K::NC;
+#pragma unroll
+      for (int e = 0; e < K::NC; ++e) gp[e] = acc[e];
+    }
+  }
+}
+
+// K2 for units over their staging capacity: the staging area (first cap
+// arrivals) and the unit's overflow arrivals; a counting sort by leaf in
+// global scratch (fb_key / fb_idx at the unit's output range), per-leaf
+// insertion sort by key, then gathers in bucket order.  Arrival r < cap is
+// staging slot r, arrival cap + k the unit's k-th overflow entry.
 template <int D>
 __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeom g, BrickPullArgs a) {
   using K = BK<D>;
-  extern __shared__ float stage[];                      // kStageCap staged values
-  uint16_t *map = (uint16_t *)(stage + kStageCap);      // slot -> raw position -> stage index
-  __shared__ int32_t cnt[K::LB + 1];                    // counts, then offsets
-  __shared__ int32_t cur[K::LB];
-  __shared__ Piece pieces[kMaxPieces];
-  __shared__ Piece sdesc[54];
-  __shared__ int32_t pfx[kMaxPieces + 1];
-  __shared__ int32_t spfx[kMaxPieces + 1];              // stage offset of round-2 pieces
+  __shared__ int32_t cnt[K::LH + 1];
+  __shared__ int32_t cur[K::LH];
   __shared__ int32_t wsum[kPullThreads / 32];
-  __shared__ int32_t s_np, s_self, s_max;
+  __shared__ int32_t s_max;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
-  const int32_t b = blockIdx.x, L0 = b * K::LB;
+  const BrickStage &st = a.st;
+  const int32_t u = blockIdx.x, b = u >> 1;
+  const int lf0 = (u & 1) ? K::LH : 0, nlf = (u & 1) ? K::LB - K::LH : K::LH;
+  const int32_t L0 = b * K::LB + lf0;
   const int64_t n = a.n;
-  if (a.tot[b] <= kStCap) return;  // the shared-memory kernel took this brick
-
-  // neighbour segments (two halves each), one thread per direction, placed by
-  // source-brick rank; round 1 = the stayers of this brick's own two halves
-  __shared__ int32_t s_src[27];
-  Piece m0{0, 0, INT32_MAX, 0, 0}, m1{0, 0, INT32_MAX, 0, 0};
-  if (tid < 27) {
-    const int4 p0 = a.bpiece[((int64_t)b * 27 + tid) * 2], p1 = a.bpiece[((int64_t)b * 27 + tid) * 2 + 1];
-    m0 = Piece{p0.x, p0.y, p0.z, 0, 0};
-    m1 = Piece{p1.x, p1.y, p1.z, 0, 0};
-    s_src[tid] = m0.src;
-  }
-  for (int i = tid; i < K::LB + 1; i += blockDim.x) cnt[i] = 0;
-  __syncthreads();
-  if (tid < 27 && m0.src != INT32_MAX) {
-    int rank = 0;
-    for (int k = 0; k < 27; ++k) rank += s_src[k] < m0.src;
-    sdesc[2 * rank] = m0;
-    sdesc[2 * rank + 1] = m1;
-    if (tid == kSelfDir) {
-      pieces[0] = Piece{m0.tstart, m0.len, m0.src, 1, 0};
-      pieces[1] = Piece{m1.tstart, m1.len, m1.src, 1, 0};
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    const int ns = 2 * (D == 3 ? 27 : 9);
-    // far arrivals (sorted by storage index, so by source brick) go between
-    // the neighbour segments as runs of the sorted far list
-    int np = 2;
-    int32_t fi = a.fstart[b];
-    const int32_t fe = a.fstart[b + 1];
-    for (int k = 0; k < ns; ++k) {
-      if (fi < fe) {
-        int32_t f0 = fi;
-        while (fi < fe && a.far_src[fi] < sdesc[k].src) ++fi;
-        if (fi > f0) pieces[np++] = Piece{f0, fi - f0, -1, 0, 1};
-      }
-      if (sdesc[k].src == b && (k & 1) == 0) s_self = np;
-      pieces[np++] = sdesc[k];
-    }
-    if (fi < fe) pieces[np++] = Piece{fi, fe - fi, -1, 0, 1};
-    int32_t s = 0;
-    for (int k = 0; k < np; ++k) {
-      pfx[k] = s;
-      spfx[k] = k < 2 ? 0 : s - pieces[0].len - pieces[1].len;
-      s += pieces[k].len;
-    }
-    pfx[np] = s;
-    s_np = np;
-    s_max = 0;
-  }
-  __syncthreads();
-  const int np = s_np;
-  const int32_t self_stage = spfx[s_self];
-
-  // every raw position of every piece: fn(raw position, temporary index, keep, leaf)
-  auto each = [&](auto fn) {
-    for (int k = 0; k < np; ++k) {
-      const Piece pc = pieces[k];
-      const int32_t r0 = pfx[k];
-      for (int32_t i = tid; i < pc.len; i += blockDim.x) {
-        const int32_t tidx = pc.indirect ? a.far_tidx[pc.tstart + i] : pc.tstart + i;
-        const uint16_t code = a.tcode[tidx];
-        const bool stay = (code & kStayBit) != 0;
-        if (pc.round1 ? stay : !stay) fn(r0 + i, code & 0x7fff);
-      }
-    }
+  if (st.fill[u] <= st.cap) return;  // the shared-memory kernel took this unit
+  const int32_t nf = st.cap;
+  const int32_t f0 = a.fstart[u], nov = a.fstart[u + 1] - f0, nin = nf + nov;
+  const int64_t at = (int64_t)u * st.cap;
+  auto code_of = [&](int32_t r) -> uint16_t {
+    return r < nf ? st.code[at + r] : st.ovf_code[a.ovf_sorted[f0 + r - nf]];
   };
-  // counts per leaf
-  each([&](int32_t, int leaf) { atomicAdd(&cnt[leaf], 1); });
+  auto key_of = [&](int32_t r) -> uint32_t {
+    return r < nf ? st.key[at + r] : st.ovf_key[a.ovf_sorted[f0 + r - nf]];
+  };
+  auto leaf_of = [&](int32_t r) -> int { return min(max((code_of(r) & 0x3ff) - lf0, 0), nlf - 1); };
+  for (int i = tid; i <= nlf; i += blockDim.x) cnt[i] = 0;
+  if (tid == 0) s_max = 0;
   __syncthreads();
-  // exclusive scan of the counts (in place), cursors
+  for (int32_t r = tid; r < nin; r += blockDim.x) atomicAdd(&cnt[leaf_of(r)], 1);
+  __syncthreads();
   int32_t carry = 0;
-  for (int base = 0; base < K::LB; base += blockDim.x) {
+  for (int base = 0; base < nlf; base += blockDim.x) {
     const int l = base + tid;
-    const int32_t c = l < K::LB ? cnt[l] : 0;
+    const int32_t c = l < nlf ? cnt[l] : 0;
     int32_t x = c;
     for (int o = 1; o < 32; o <<= 1) {
       int32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -965,7 +972,7 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       if (k < w) before += wsum[k];
       all += wsum[k];
     }
-    if (l < K::LB) {
+    if (l < nlf) {
       cnt[l] = carry + before + x - c;
       cur[l] = cnt[l];
       if (c > 0) atomicMax(&s_max, c);
@@ -973,76 +980,58 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
     carry += all;
     __syncthreads();
   }
-  if (tid == 0) cnt[K::LB] = carry;
+  if (tid == 0) cnt[nlf] = carry;
   __syncthreads();
-  const int32_t bstart = a.bstart[b];
-  const int32_t nin = cnt[K::LB];
-  for (int l = tid; l < K::LB; l += blockDim.x) a.new_start[L0 + l] = bstart + cnt[l];
-  if (b == g.n_bricks - 1 && tid == 0) a.new_start[(int64_t)g.n_bricks * K::LB] = bstart + nin;
-  if (tid == 0 && s_max > 0) atomicMax(a.max_bucket, s_max);
-
-  if (nin <= kStageCap) {
-    // slots (any order), then every leaf's slots sorted by raw position: the
-    // canonical order (stayers first, then movers in storage order)
-    each([&](int32_t r, int leaf) { map[atomicAdd(&cur[leaf], 1)] = (uint16_t)r; });
-    __syncthreads();
-    for (int l = tid; l < K::LB; l += blockDim.x) {
-      const int32_t lo = cnt[l], hi = cnt[l + 1];
-      for (int32_t i = lo + 1; i < hi; ++i) {
-        const uint16_t x = map[i];
-        int32_t j = i - 1;
-        while (j >= lo && map[j] > x) { map[j + 1] = map[j]; --j; }
-        map[j + 1] = x;
-      }
-      for (int32_t i = lo; i < hi; ++i) {  // raw position -> stage index
-        const int32_t r = map[i];
-        map[i] = (uint16_t)(r < pfx[2] ? self_stage + r : r - pfx[2]);
-      }
-    }
-    __syncthreads();
-    // one array at a time: coalesced reads of the incoming pieces into shared
-    // memory, coalesced writes in destination order
-    const int na = 2 * D + (a.ids ? 1 : 0);
-    for (int arr = 0; arr < na; ++arr) {
-      const float *src = arr < D ? a.to + arr * n : (arr < 2 * D ? a.tv + (arr - D) * n : (const float *)a.tids);
-      float *dst = arr < D ? a.o + arr * n : (arr < 2 * D ? a.v + (arr - D) * n : (float *)a.ids);
-      for (int k = 2; k < np; ++k) {
-        const Piece pc = pieces[k];
-        const int32_t so = spfx[k];
-        for (int32_t i = tid; i < pc.len; i += blockDim.x)
-          stage[so + i] = src[pc.indirect ? a.far_tidx[pc.tstart + i] : pc.tstart + i];
-      }
-      __syncthreads();
-      for (int32_t j = tid; j < nin; j += blockDim.x) dst[bstart + j] = stage[map[j]];
-      __syncthreads();
-    }
-  } else {
-    // large brick: one thread per leaf walks the raw positions in order
-    for (int l = tid; l < K::LB; l += blockDim.x) {
-      int32_t dl = cnt[l];
-      for (int k = 0; k < np; ++k) {
-        const Piece pc = pieces[k];
-        for (int32_t i = 0; i < pc.len; ++i) {
-          const int32_t tidx = pc.indirect ? a.far_tidx[pc.tstart + i] : pc.tstart + i;
-          const uint16_t code = a.tcode[tidx];
-          const bool stay = (code & kStayBit) != 0;
-          if (!(pc.round1 ? stay : !stay) || (code & 0x7fff) != l) continue;
-          const int32_t dst = bstart + dl++;
-#pragma unroll
-          for (int ax = 0; ax < D; ++ax) {
-            a.o[ax * n + dst] = a.to[ax * n + tidx];
-            a.v[ax * n + dst] = a.tv[ax * n + tidx];
-          }
-          if (a.ids) a.ids[dst] = a.tids[tidx];
-        }
-      }
-    }
-    __syncthreads();
+  const int32_t bstart = a.bstart[u];
+  for (int32_t r = tid; r < nin; r += blockDim.x) {
+    const int32_t p = bstart + atomicAdd(&cur[leaf_of(r)], 1);
+    a.fb_key[p] = key_of(r);
+    a.fb_idx[p] = r;
   }
-  // deposit partials of the new positions, per leaf in bucket order (the
-  // arithmetic and order of the generic per-leaf deposit)
+  __syncthreads();
+  for (int l = tid; l < nlf; l += blockDim.x) {
+    a.new_start[L0 + l] = bstart + cnt[l];
+    const int32_t lo = bstart + cnt[l], hi = bstart + cnt[l + 1];
+    for (int32_t i = lo + 1; i < hi; ++i) {
+      const uint32_t kx = a.fb_key[i];
+      const int32_t vx = a.fb_idx[i];
+      int32_t j = i - 1;
+      while (j >= lo && a.fb_key[j] > kx) {
+        a.fb_key[j + 1] = a.fb_key[j];
+        a.fb_idx[j + 1] = a.fb_idx[j];
+        --j;
+      }
+      a.fb_key[j + 1] = kx;
+      a.fb_idx[j + 1] = vx;
+    }
+  }
+  if (u == 2 * g.n_bricks - 1 && tid == 0) a.new_start[(int64_t)g.n_bricks * K::LB] = bstart + nin;
+  if (tid == 0 && s_max > 0) atomicMax(a.max_bucket, s_max);
+  __syncthreads();
+  for (int32_t j = tid; j < nin; j += blockDim.x) {
+    const int32_t r = a.fb_idx[bstart + j];
+    const int32_t dst = bstart + j;
+    if (r < nf) {
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        a.o[ax * n + dst] = st.o[ax * st.row + at + r];
+        a.v[ax * n + dst] = st.v[ax * st.row + at + r];
+      }
+      if (a.ids) a.ids[dst] = st.id[at + r];
+    } else {
+      const int32_t k = a.ovf_sorted[f0 + r - nf];
+#pragma unroll
+      for (int ax = 0; ax < D; ++ax) {
+        a.o[ax * n + dst] = st.ovf_o[ax * (int64_t)st.ovf_cap + k];
+        a.v[ax * n + dst] = st.ovf_v[ax * (int64_t)st.ovf_cap + k];
+      }
+      if (a.ids) a.ids[dst] = st.ovf_id[k];
+    }
+  }
+  __syncthreads();
+  // deposit partials of the new positions, per leaf in bucket order
   if (a.part) {
-    for (int l = tid; l < K::LB; l += blockDim.x) {
+    for (int l = tid; l < nlf; l += blockDim.x) {
       float acc[K::NC];
 #pragma unroll
       for (int e = 0; e < K::NC; ++e) acc[e] = 0.0f;
@@ -1067,324 +1056,6 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
   }
 }
 
-// ---------------------------------------------------------------------------
-// K2, shared-memory form: every arrival is loaded once (coalesced), counted,
-// ordered, written in destination order and deposited from shared memory.
-// ---------------------------------------------------------------------------
-
-template <int D>
-size_t pull_st_smem() {
-  return sizeof(float) * 2 * D * kStCap + sizeof(uint16_t) * 2 * kStCap;
-}
-
-// Canonical position order inside the brick's incoming pieces: round-1 (the
-// stayers of the self segment) before round-2 (everything else in source
-// order); stage index = position among round-2 pieces.
-template <int D>
-__device__ __forceinline__ void build_pieces(const DevTree &t, const BrickGeom &g, const BrickPullArgs &a,
-                                             int32_t b, Piece *pieces, Piece *sdesc, int32_t *s_src,
-                                             int32_t *pfx, int32_t *spfx, int32_t *s_np, int32_t *s_self) {
-  (void)t;
-  (void)g;
-  (void)s_src;
-  const int tid = threadIdx.x, lane = tid & 31;
-  constexpr unsigned kAll = 0xffffffffu;
-  if (tid < 32) {  // warp 0: lane = direction of the source brick, two halves each
-    Piece m0{0, 0, INT32_MAX, 0, 0}, m1{0, 0, INT32_MAX, 0, 0};
-    if (lane < 27) {
-      const int4 p0 = a.bpiece[((int64_t)b * 27 + lane) * 2], p1 = a.bpiece[((int64_t)b * 27 + lane) * 2 + 1];
-      m0 = Piece{p0.x, p0.y, p0.z, 0, 0};
-      m1 = Piece{p1.x, p1.y, p1.z, 0, 0};
-    }
-    const int32_t fi0 = a.fstart[b], fe = a.fstart[b + 1];
-    int rank = 0;  // sources in ascending brick order = storage order
-    for (int k = 0; k < 27; ++k) rank += __shfl_sync(kAll, m0.src, k) < m0.src;
-    const bool valid = lane < 27 && m0.src != INT32_MAX;
-    const int ns = 2 * (D == 3 ? 27 : 9);
-    const int32_t len0 = __shfl_sync(kAll, m0.len + m1.len, kSelfDir);  // stayers come from both halves
-    if (lane == 0) pieces[0] = Piece{0, len0, b, 1, 0};
-    if (fi0 == fe) {
-      // no far arrivals: the neighbour segments in (source, half) order, in parallel
-      if (valid) {
-        pieces[1 + 2 * rank] = m0;
-        pieces[2 + 2 * rank] = m1;
-        if (m0.src == b) *s_self = 1 + 2 * rank;
-      }
-      __syncwarp();
-      const int32_t x0 = 2 * lane < ns ? pieces[1 + 2 * lane].len : 0;
-      const int32_t x1 = 2 * lane < ns ? pieces[2 + 2 * lane].len : 0;
-      const int32_t x = x0 + x1;
-      int32_t incl = x;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int32_t y = __shfl_up_sync(kAll, incl, o);
-        if (lane >= o) incl += y;
-      }
-      if (2 * lane < ns) {
-        const int32_t ex = incl - x;
-        pfx[1 + 2 * lane] = len0 + ex;
-        spfx[1 + 2 * lane] = ex;
-        pfx[2 + 2 * lane] = len0 + ex + x0;
-        spfx[2 + 2 * lane] = ex + x0;
-      }
-      if (lane == 0) pfx[0] = spfx[0] = 0;
-      if (2 * lane == ns - 2) {
-        pfx[ns + 1] = len0 + incl;
-        spfx[ns + 1] = incl;
-        *s_np = ns + 1;
-      }
-    } else {
-      if (valid) {
-        sdesc[2 * rank] = m0;
-        sdesc[2 * rank + 1] = m1;
-      }
-      __syncwarp();
-      if (lane == 0) {
-        // far arrivals (sorted by storage index, so by source brick) go
-        // between the neighbour segments as runs of the sorted far list
-        int np = 1;
-        int32_t fi = fi0;
-        for (int k = 0; k < ns; ++k) {
-          if (fi < fe) {
-            int32_t f0 = fi;
-            while (fi < fe && a.far_src[fi] < sdesc[k].src) ++fi;
-            if (fi > f0) pieces[np++] = Piece{f0, fi - f0, -1, 0, 1};
-          }
-          if (sdesc[k].src == b && (k & 1) == 0) *s_self = np;
-          pieces[np++] = sdesc[k];
-        }
-        if (fi < fe) pieces[np++] = Piece{fi, fe - fi, -1, 0, 1};
-        int32_t sum = 0;
-        for (int k = 0; k < np; ++k) {
-          pfx[k] = sum;
-          spfx[k] = k == 0 ? 0 : sum - pieces[0].len;
-          sum += pieces[k].len;
-        }
-        pfx[np] = sum;
-        spfx[np] = sum - pieces[0].len;
-        *s_np = np;
-      }
-    }
-  }
-  __syncthreads();
-}
-
-// Sorts the m <= N canonical keys of one leaf (ascending) with a bitonic
-// network in registers and replaces each by its stage index.
-template <int N>
-__device__ __forceinline__ void sort_keys_net(uint16_t *keys, int m, int32_t len0, int32_t self_stage) {
-  uint32_t r[N];
-#pragma unroll
-  for (int i = 0; i < N; ++i) r[i] = i < m ? keys[i] : 0xffffu;
-  bitonic_sort<N>(r);
-#pragma unroll
-  for (int i = 0; i < N; ++i)
-    if (i < m) keys[i] = (uint16_t)((int32_t)r[i] < len0 ? self_stage + (int32_t)r[i] : (int32_t)r[i] - len0);
-}
-
-// Leaves with 17..32 keys (rare): out of line, so that the 32-entry network
-// does not raise the register demand of the calling kernel.
-__device__ __noinline__ void sort_keys_net32(uint16_t *keys, int m, int32_t len0, int32_t self_stage) {
-  sort_keys_net<32>(keys, m, len0, self_stage);
-}
-
-template <int D>
-__global__ void __launch_bounds__(kStThreads, 1) k_brick_pull_st(DevTree t, BrickGeom g, BrickPullArgs a) {
-  using K = BK<D>;
-  extern __shared__ __align__(128) float smf[];
-  float *so = smf;                                   // D * kStCap
-  float *sv = so + D * kStCap;                       // D * kStCap
-  uint16_t *code = (uint16_t *)(sv + D * kStCap);    // kStCap tcode of every arrival (stage order)
-  uint16_t *map = code + kStCap;                     // kStCap slot -> key -> stage index
-  __shared__ int32_t cnt[K::LB + 1];
-  __shared__ int32_t cur[K::LB];
-  __shared__ Piece pieces[kMaxPieces];
-  __shared__ Piece sdesc[54];
-  __shared__ int32_t s_src[27];
-  __shared__ int32_t pfx[kMaxPieces + 1], spfx[kMaxPieces + 1];
-  __shared__ int32_t wsum[32];
-  __shared__ int32_t s_np, s_self, s_max;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
-  const int32_t b = blockIdx.x, L0 = b * K::LB;
-  const int64_t n = a.n;
-  if (a.tot[b] > kStCap) return;  // the global-memory kernel takes this brick
-  if (tid == 0) s_max = 0;
-  for (int i = tid; i < K::LB + 1; i += blockDim.x) cnt[i] = 0;
-  build_pieces<D>(t, g, a, b, pieces, sdesc, s_src, pfx, spfx, &s_np, &s_self);
-  const int np = s_np;
-  const int32_t len0 = pieces[0].len, self_stage = spfx[s_self];
-  const int32_t nin = spfx[np];
-  // load every arrival once (round-2 pieces cover each exactly once): one
-  // thread per arrival over all pieces; payload by asynchronous copies, the
-  // codes through registers for the leaf counts
-  {
-    const float *gO[D], *gV[D];
-#pragma unroll
-    for (int ax = 0; ax < D; ++ax) {
-      gO[ax] = a.to + ax * n;
-      gV[ax] = a.tv + ax * n;
-    }
-    int kp = tid < nin ? piece_of(spfx, np, tid) : 1;  // arrivals only move forward
-    for (int32_t base = 0; base < nin; base += kLoadBatch * kStThreads) {
-      uint16_t rc[kLoadBatch];
-#pragma unroll
-      for (int u = 0; u < kLoadBatch; ++u) {
-        const int32_t si = base + u * kStThreads + tid;
-        if (si < nin) {
-          while (kp + 1 < np && spfx[kp + 1] <= si) ++kp;
-          const Piece pc = pieces[kp];
-          const int32_t off = si - spfx[kp];
-          const int32_t tx = pc.indirect ? a.far_tidx[pc.tstart + off] : pc.tstart + off;
-#pragma unroll
-          for (int ax = 0; ax < D; ++ax) {
-            cp_async4(so + ax * kStCap + si, gO[ax] + tx);
-            cp_async4(sv + ax * kStCap + si, gV[ax] + tx);
-          }
-          rc[u] = __ldg(a.tcode + tx);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < kLoadBatch; ++u) {
-        const int32_t si = base + u * kStThreads + tid;
-        if (si < nin) {
-          code[si] = rc[u];
-          atomicAdd(&cnt[rc[u] & 0x3ff], 1);
-        }
-      }
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // exclusive scan of the leaf counts, cursors
-  int32_t carry = 0;
-  for (int base = 0; base < K::LB; base += blockDim.x) {
-    const int l = base + tid;
-    const int32_t c = l < K::LB ? cnt[l] : 0;
-    int32_t x = c;
-    for (int o = 1; o < 32; o <<= 1) {
-      int32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[w] = x;
-    __syncthreads();
-    int32_t before = 0, all = 0;
-    for (int k = 0; k < nw; ++k) {
-      if (k < w) before += wsum[k];
-      all += wsum[k];
-    }
-    if (l < K::LB) {
-      cnt[l] = carry + before + x - c;
-      cur[l] = cnt[l];
-      if (c > 0) atomicMax(&s_max, c);
-    }
-    carry += all;
-    __syncthreads();
-  }
-  if (tid == 0) cnt[K::LB] = carry;
-  __syncthreads();
-  // slots in any order, keyed by canonical position
-  for (int32_t si = tid; si < nin; si += blockDim.x) {
-    const uint16_t cd = code[si];
-    const bool stay = (cd & kStayBit) != 0;
-    const int32_t key = stay ? si - self_stage : len0 + si;
-    map[atomicAdd(&cur[cd & 0x3ff], 1)] = (uint16_t)key;
-  }
-  __syncthreads();
-  const int32_t bstart = a.bstart[b];
-  for (int l = tid; l < K::LB; l += blockDim.x) {
-    a.new_start[L0 + l] = bstart + cnt[l];
-    const int32_t lo = cnt[l], hi = cnt[l + 1];
-    if (hi - lo <= 16) {
-      sort_keys_net<16>(map + lo, hi - lo, len0, self_stage);
-      continue;
-    }
-    if (hi - lo <= 32) {
-      sort_keys_net32(map + lo, hi - lo, len0, self_stage);
-      continue;
-    }
-    for (int32_t i = lo + 1; i < hi; ++i) {
-      const uint16_t x = map[i];
-      int32_t j = i - 1;
-      while (j >= lo && map[j] > x) { map[j + 1] = map[j]; --j; }
-      map[j + 1] = x;
-    }
-    for (int32_t i = lo; i < hi; ++i) {
-      const int32_t key = map[i];
-      map[i] = (uint16_t)(key < len0 ? self_stage + key : key - len0);
-    }
-  }
-  if (b == g.n_bricks - 1 && tid == 0) a.new_start[(int64_t)g.n_bricks * K::LB] = bstart + nin;
-  if (tid == 0 && s_max > 0) atomicMax(a.max_bucket, s_max);
-  __syncthreads();
-  // coalesced writes in destination order
-  {
-    float *gO[D], *gV[D];
-#pragma unroll
-    for (int ax = 0; ax < D; ++ax) {
-      gO[ax] = a.o + ax * n + bstart;
-      gV[ax] = a.v + ax * n + bstart;
-    }
-    for (int32_t j = tid; j < nin; j += blockDim.x) {
-      const int32_t si = map[j];
-#pragma unroll
-      for (int ax = 0; ax < D; ++ax) {
-        gO[ax][j] = so[ax * kStCap + si];
-        gV[ax][j] = sv[ax * kStCap + si];
-      }
-    }
-  }
-  if (a.ids) {
-    // ids: the source of stage index si is found in the round-2 pieces
-    for (int32_t j = tid; j < nin; j += blockDim.x) {
-      const int32_t si = map[j];
-      const int k = piece_of(spfx, np, si);
-      const Piece pc = pieces[k];
-      const int32_t off = si - spfx[k];
-      a.ids[bstart + j] = a.tids[pc.indirect ? a.far_tidx[pc.tstart + off] : pc.tstart + off];
-    }
-  }
-  // deposit partials of the new positions, per leaf in bucket order; the
-  // next particle's offsets are fetched while the current one is summed
-  if (a.part) {
-    for (int l = tid; l < K::LB; l += blockDim.x) {
-      float acc[K::NC];
-#pragma unroll
-      for (int e = 0; e < K::NC; ++e) acc[e] = 0.0f;
-      const int32_t lo = cnt[l], hi = cnt[l + 1];
-      float on[D];
-      if (lo < hi) {
-        const int32_t si = map[lo];
-#pragma unroll
-        for (int ax = 0; ax < D; ++ax) on[ax] = so[ax * kStCap + si];
-      }
-      for (int32_t j = lo; j < hi; ++j) {
-        float o[D], om[D];
-#pragma unroll
-        for (int ax = 0; ax < D; ++ax) {
-          o[ax] = on[ax];
-          om[ax] = 1.0f - o[ax];
-        }
-        if (j + 1 < hi) {
-          const int32_t si = map[j + 1];
-#pragma unroll
-          for (int ax = 0; ax < D; ++ax) on[ax] = so[ax * kStCap + si];
-        }
-#pragma unroll
-        for (int e = 0; e < K::NC; ++e) {
-          float wgt = 1.0f;
-#pragma unroll
-          for (int ax = 0; ax < D; ++ax) wgt = wgt * (((e >> ax) & 1) ? o[ax] : om[ax]);
-          acc[e] = acc[e] + wgt;
-        }
-      }
-      float *gp = a.part + (int64_t)(L0 + l) * K::NC;
-#pragma unroll
-      for (int e = 0; e < K::NC; ++e) gp[e] = acc[e];
-    }
-  }
-}
-
-// Leaf id of every particle from the bucket offsets (thread per leaf).
 __global__ void k_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf) {
   int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n_leaves) return;
@@ -1396,7 +1067,8 @@ __global__ void k_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t 
 // ---------------------------------------------------------------------------
 
 void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs &pa, cudaStream_t s) {
-  cudaMemsetAsync(pa.far_n, 0, sizeof(int32_t), s);
+  cudaMemsetAsync(pa.st.fill, 0, sizeof(int32_t) * 2 * g.n_bricks, s);
+  cudaMemsetAsync(pa.st.ovf_n, 0, sizeof(int32_t), s);
   const unsigned nb = (unsigned)g.n_bricks;
   if (g.d == 3) {
     if (pa.n % 4 == 0)
@@ -1414,32 +1086,24 @@ void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs
   count_launches(2);
 }
 
-void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPushArgs &pa, const BrickPullArgs &qa,
-                       int32_t *fcount, int32_t *fcursor, int32_t *tile_sums, int32_t *scratch_total,
-                       cudaStream_t s) {
-  const unsigned nb = (unsigned)g.n_bricks;
-  const size_t stage_bytes = (sizeof(float) + sizeof(uint16_t)) * kStageCap;
-  cudaMemsetAsync(fcount, 0, sizeof(int32_t) * g.n_bricks, s);
-  cudaMemsetAsync(fcursor, 0, sizeof(int32_t) * g.n_bricks, s);
-  k_far_count<<<64, 256, 0, s>>>(pa.far_n, pa.far_cap, pa.far_dest, fcount);
-  launch_exclusive_scan(fcount, g.n_bricks, qa.fstart_w, tile_sums, scratch_total, s);
-  k_far_scatter<<<64, 256, 0, s>>>(pa.far_n, pa.far_cap, pa.far_dest, pa.far_tidx, pa.far_src, qa.fstart,
-                                   fcursor, qa.far_tidx_w, qa.far_src_w);
-  if (g.d == 3)
-    k_brick_totals<3><<<(nb + 7) / 8, 256, 0, s>>>(t, g, pa.cnt, pa.segoff, qa.old_start, qa.fstart,
-                                                   qa.far_tidx_w, qa.far_src_w, qa.tot_w, qa.bpiece_w);
-  else
-    k_brick_totals<2><<<(nb + 7) / 8, 256, 0, s>>>(t, g, pa.cnt, pa.segoff, qa.old_start, qa.fstart,
-                                                   qa.far_tidx_w, qa.far_src_w, qa.tot_w, qa.bpiece_w);
-  launch_exclusive_scan(qa.tot_w, g.n_bricks, qa.bstart_w, tile_sums, scratch_total, s);
+void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPullArgs &qa, int32_t *fcount,
+                       int32_t *fcursor, int32_t *tile_sums, int32_t *scratch_total, cudaStream_t s) {
+  const int64_t nu = 2 * g.n_bricks;  // destination units
+  cudaMemsetAsync(fcount, 0, sizeof(int32_t) * nu, s);
+  cudaMemsetAsync(fcursor, 0, sizeof(int32_t) * nu, s);
+  k_ovf_count<<<64, 256, 0, s>>>(qa.st.ovf_n, qa.st.ovf_cap, qa.st.ovf_dest, fcount);
+  launch_exclusive_scan(fcount, nu, qa.fstart_w, tile_sums, scratch_total, s);
+  k_ovf_scatter<<<64, 256, 0, s>>>(qa.st.ovf_n, qa.st.ovf_cap, qa.st.ovf_dest, qa.fstart, fcursor, qa.ovf_sorted_w);
+  k_brick_totals<<<(unsigned)((nu + 255) / 256), 256, 0, s>>>(nu, qa.st.cap, qa.st.fill, qa.fstart, qa.tot_w);
+  launch_exclusive_scan(qa.tot_w, nu, qa.bstart_w, tile_sums, scratch_total, s);
   if (g.d == 3) {
-    k_brick_pull_st<3><<<nb, kStThreads, pull_st_smem<3>(), s>>>(t, g, qa);
-    k_brick_pull<3><<<nb, kPullThreads, stage_bytes, s>>>(t, g, qa);
+    k_brick_pull_st<3><<<(unsigned)nu, kStThreads, pull_st_smem<3>(), s>>>(t, g, qa);
+    k_brick_pull<3><<<(unsigned)nu, kPullThreads, 0, s>>>(t, g, qa);
   } else {
-    k_brick_pull_st<2><<<nb, kStThreads, pull_st_smem<2>(), s>>>(t, g, qa);
-    k_brick_pull<2><<<nb, kPullThreads, stage_bytes, s>>>(t, g, qa);
+    k_brick_pull_st<2><<<(unsigned)nu, kStThreads, pull_st_smem<2>(), s>>>(t, g, qa);
+    k_brick_pull<2><<<(unsigned)nu, kPullThreads, 0, s>>>(t, g, qa);
   }
-  count_launches(5);  // far count, far scatter, totals, two pull kernels (the scans count themselves)
+  count_launches(5);  // overflow count, overflow scatter, totals, two pull kernels (the scans count themselves)
 }
 
 void launch_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf, cudaStream_t s) {
@@ -1447,25 +1111,34 @@ void launch_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf,
   count_launches(1);
 }
 
+int32_t brick_stage_cap(int64_t n, int64_t n_units) {
+  // four times the mean arrivals per unit and some slack, a multiple of 8
+  // (every unit's area then starts on a 16-byte boundary in each row), at most
+  // what the shared-memory kernel holds; fuller units take the overflow list
+  const int64_t want = 4 * (n / (n_units > 0 ? n_units : 1)) + 256;
+  return (int32_t)std::min<int64_t>(kStCap, (want + 7) & ~(int64_t)7);
+}
+
 cudaError_t brick_configure(const BrickGeom &g) {
-  const int bytes = (int)((sizeof(float) + sizeof(uint16_t)) * kStageCap);
-  cudaError_t e;
+  cudaError_t e = cudaSuccess;
   if (g.d == 3) {
-    e = cudaFuncSetAttribute(k_brick_pull<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     for (auto fn : {k_brick_push_st<3, true>, k_brick_push_st<3, false>}) {
       if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)push_st_smem<3>());
       if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_brick_pull_st<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pull_st_smem<3>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_brick_pull_st<3>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   } else {
-    e = cudaFuncSetAttribute(k_brick_pull<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     for (auto fn : {k_brick_push_st<2, true>, k_brick_push_st<2, false>}) {
       if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)push_st_smem<2>());
       if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_brick_pull_st<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pull_st_smem<2>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_brick_pull_st<2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   }
   return e;
 }

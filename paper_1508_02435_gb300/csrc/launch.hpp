@@ -64,6 +64,27 @@ struct BrickGeom {
   const uint32_t *decodeL;       // local depth-first index -> x | y << 10 | z << 20
 };
 
+// Staging between K1 and K2: every pushed particle is appended to the area of
+// its destination unit U (half a brick: local leaves below or from (LB+1)/2),
+// slots [U cap, U cap + cap) of each row; arrivals beyond cap go to an
+// overflow list.
+struct BrickStage {
+  int32_t cap;                   // slots per destination unit (a multiple of 8)
+  int64_t row;                   // elements per row (2 n_bricks cap, padded)
+  float *o, *v;                  // D rows each
+  uint16_t *code;                // destination local leaf | stayer bit
+  uint32_t *key;                 // moved << 31 | storage index before the step (canonical order)
+  int32_t *id;                   // particle ids (tracked ids only)
+  int32_t *fill;                 // [2 n_bricks] arrivals per destination unit (may exceed cap)
+  int32_t *ovf_n;                // overflow count
+  int32_t ovf_cap;
+  int32_t *ovf_dest;             // [ovf_cap] destination unit
+  float *ovf_o, *ovf_v;          // [D][ovf_cap]
+  uint16_t *ovf_code;
+  uint32_t *ovf_key;
+  int32_t *ovf_id;
+};
+
 struct BrickPushArgs {
   int64_t n;
   const float *o, *v;
@@ -71,47 +92,37 @@ struct BrickPushArgs {
   const int32_t *ids;            // NULL unless ids are tracked
   const float *E;
   float qmdt, sl;
-  float *to, *tv;
-  uint16_t *tcode;               // destination local leaf | stayer bit
-  int32_t *tids;
-  int32_t *cnt, *segoff;         // [n_bricks][2 halves][28]
-  int32_t *far_n;
-  int32_t far_cap;
-  int32_t *far_tidx, *far_src, *far_dest;
-  int32_t *far_scratch;          // n entries: destination brick of a far mover by storage index
+  BrickStage st;
   int32_t *n_movers;
   int32_t *err;
 };
 
 struct BrickPullArgs {
   int64_t n;
-  const int32_t *old_start, *cnt, *segoff;
-  const int32_t *fstart;
+  BrickStage st;
+  const int32_t *fstart;         // overflow arrivals sorted per destination brick
   int32_t *fstart_w;
-  const int32_t *far_tidx, *far_src;  // far arrivals sorted per destination brick
-  int32_t *far_tidx_w, *far_src_w;
+  const int32_t *ovf_sorted;     // overflow list positions, grouped by destination brick
+  int32_t *ovf_sorted_w;
   int32_t *tot_w;
   const int32_t *tot;            // incoming particles per destination brick
   const int32_t *bstart;
   int32_t *bstart_w;
-  const uint16_t *tcode;
-  const float *to, *tv;
-  const int32_t *tids;
   float *o, *v;
   int32_t *ids;
   int32_t *new_start;
   int32_t *max_bucket;
   int32_t *err;
   float *part;                   // leaf-corner deposit partials of the new positions, or NULL
-  const int4 *bpiece;            // [n_bricks][27][2 halves] incoming segment {start, length, source brick, half}
-  int4 *bpiece_w;
+  uint32_t *fb_key;              // [n] scratch of the global-memory kernel
+  int32_t *fb_idx;
 };
 
 cudaError_t brick_configure(const BrickGeom &g);
+int32_t brick_stage_cap(int64_t n, int64_t n_units);  // staging slots per destination unit
 void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs &pa, cudaStream_t s);
-void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPushArgs &pa, const BrickPullArgs &qa,
-                       int32_t *fcount, int32_t *fcursor, int32_t *tile_sums, int32_t *scratch_total,
-                       cudaStream_t s);
+void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPullArgs &qa, int32_t *fcount,
+                       int32_t *fcursor, int32_t *tile_sums, int32_t *scratch_total, cudaStream_t s);
 void launch_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf, cudaStream_t s);
 
 cudaError_t set_constants(cudaStream_t s);

@@ -76,11 +76,10 @@ struct pic_s {
   int64_t graph_kernels = 0;
   BrickGeom bg{};
   std::vector<DevBuf> brick_bufs;
-  uint16_t *tcode = nullptr;
-  int32_t *bcnt = nullptr, *bsegoff = nullptr, *far_n = nullptr, *far_tidx = nullptr, *far_src = nullptr;
-  int32_t *far_dest = nullptr, *far_stidx = nullptr, *far_ssrc = nullptr, *fcount = nullptr;
-  int32_t *fcursor = nullptr, *fstart = nullptr, *btot = nullptr, *bstart = nullptr;
-  int4 *bpiece = nullptr;
+  BrickStage stage{};      // per-destination staging between the two brick kernels
+  int32_t *fcount = nullptr, *fcursor = nullptr, *fstart = nullptr, *ovf_sorted = nullptr;
+  int32_t *btot = nullptr, *bstart = nullptr, *fb_idx = nullptr;
+  uint32_t *fb_key = nullptr;
 
   // per-phase event timing (pic_profile / pic_phase_times)
   struct Pending {
@@ -463,23 +462,37 @@ int setup_brick(pic_t h) {
   auto &bb = h->brick_bufs;
   int rc;
   if ((rc = upload(h, bb, &g.decodeL, dec))) return rc;
-  const int64_t n = h->n, nb = g.n_bricks;
-  if ((rc = dalloc(h, bb, &h->tcode, n + 32))) return rc;  // bulk copies read whole 16-byte units
-  if ((rc = dalloc(h, bb, &h->bcnt, nb * 2 * 28))) return rc;  // [brick][half][direction]
-  if ((rc = dalloc(h, bb, &h->bsegoff, nb * 2 * 28))) return rc;
-  if ((rc = dalloc(h, bb, &h->far_n, 2))) return rc;
-  if ((rc = dalloc(h, bb, &h->far_tidx, n))) return rc;
-  if ((rc = dalloc(h, bb, &h->far_src, n))) return rc;
-  if ((rc = dalloc(h, bb, &h->far_dest, n))) return rc;
-  if ((rc = dalloc(h, bb, &h->far_stidx, n))) return rc;
-  if ((rc = dalloc(h, bb, &h->far_ssrc, n))) return rc;
-  if ((rc = dalloc(h, bb, &h->fcount, nb))) return rc;
-  if ((rc = dalloc(h, bb, &h->fcursor, nb))) return rc;
-  if ((rc = dalloc(h, bb, &h->fstart, nb + 1))) return rc;
-  if ((rc = dalloc(h, bb, &h->btot, nb))) return rc;
-  if ((rc = dalloc(h, bb, &h->bstart, nb + 1))) return rc;
-  if ((rc = dalloc(h, bb, &h->bpiece, nb * 27 * 2))) return rc;
-  if (scan_tiles_needed(nb) + 1 > scan_tiles_needed(h->dt.n_keys) + 1)
+  const int64_t n = h->n, nu = 2 * g.n_bricks;  // destination units: half bricks
+  // staging rows: cap slots per destination unit (a multiple of 8, so every
+  // unit's area starts on a 16-byte boundary in each row), plus a tail for the
+  // bulk copies of the last unit, which read whole 16-byte units
+  BrickStage &st = h->stage;
+  st = BrickStage{};
+  st.cap = brick_stage_cap(n, nu);
+  st.row = nu * st.cap + 16;
+  if ((rc = dalloc(h, bb, &st.o, st.row * t.d))) return rc;
+  if ((rc = dalloc(h, bb, &st.v, st.row * t.d))) return rc;
+  if ((rc = dalloc(h, bb, &st.code, st.row))) return rc;
+  if ((rc = dalloc(h, bb, &st.key, st.row))) return rc;
+  if (h->cfg.track_ids && (rc = dalloc(h, bb, &st.id, st.row))) return rc;
+  if ((rc = dalloc(h, bb, &st.fill, nu))) return rc;
+  if ((rc = dalloc(h, bb, &st.ovf_n, 1))) return rc;
+  // overflow list: one entry per particle at most; offsets, velocities and
+  // ids in the pushed-state rows, which the brick step leaves unused (set per
+  // step)
+  st.ovf_cap = (int32_t)n;
+  if ((rc = dalloc(h, bb, &st.ovf_dest, n))) return rc;
+  if ((rc = dalloc(h, bb, &st.ovf_code, n))) return rc;
+  if ((rc = dalloc(h, bb, &st.ovf_key, n))) return rc;
+  if ((rc = dalloc(h, bb, &h->ovf_sorted, n))) return rc;
+  if ((rc = dalloc(h, bb, &h->fb_key, n))) return rc;
+  if ((rc = dalloc(h, bb, &h->fb_idx, n))) return rc;
+  if ((rc = dalloc(h, bb, &h->fcount, nu))) return rc;
+  if ((rc = dalloc(h, bb, &h->fcursor, nu))) return rc;
+  if ((rc = dalloc(h, bb, &h->fstart, nu + 1))) return rc;
+  if ((rc = dalloc(h, bb, &h->btot, nu))) return rc;
+  if ((rc = dalloc(h, bb, &h->bstart, nu + 1))) return rc;
+  if (scan_tiles_needed(nu) + 1 > scan_tiles_needed(h->dt.n_keys) + 1)
     return fail(h, PIC_EINVAL, "brick count exceeds scan scratch");
   CK(brick_configure(g));
   h->bg = g;
@@ -498,7 +511,6 @@ int ensure_leaf(pic_t h) {
 
 int brick_push_and_rebin(pic_t h, double dt) {
   cudaStream_t s = h->stream;
-  const int d = h->d;
   BrickPushArgs pa{};
   pa.n = h->n;
   pa.o = (const float *)h->pos[0];
@@ -508,39 +520,25 @@ int brick_push_and_rebin(pic_t h, double dt) {
   pa.E = (const float *)h->E;
   pa.qmdt = (float)(h->cfg.qm * dt);
   pa.sl = (float)(dt * (double)pow3(h->ht.depth));
-  pa.to = (float *)h->pos[1];
-  pa.tv = (float *)h->vel[1];
-  pa.tcode = h->tcode;
-  pa.tids = h->ids[1];
-  pa.cnt = h->bcnt;
-  pa.segoff = h->bsegoff;
-  pa.far_n = h->far_n;
-  pa.far_cap = (int32_t)h->n;
-  pa.far_tidx = h->far_tidx;
-  pa.far_src = h->far_src;
-  pa.far_dest = h->far_dest;
-  pa.far_scratch = h->far_ssrc;  // free until the far list is sorted
+  pa.st = h->stage;
+  pa.st.ovf_o = (float *)h->pos[1];  // the current assignment: re-bins elsewhere swap the rows
+  pa.st.ovf_v = (float *)h->vel[1];
+  pa.st.ovf_id = h->ids[1];
   pa.n_movers = h->scalars + 1;
   pa.err = h->err;
+  // the pull reads only the staging area and the overflow list, so the new
+  // bucket order is written over the current state in place
   BrickPullArgs qa{};
   qa.n = h->n;
-  qa.old_start = h->start_cur;
-  qa.cnt = h->bcnt;
-  qa.segoff = h->bsegoff;
+  qa.st = pa.st;
   qa.fstart = h->fstart;
   qa.fstart_w = h->fstart;
-  qa.far_tidx = h->far_stidx;
-  qa.far_src = h->far_ssrc;
-  qa.far_tidx_w = h->far_stidx;
-  qa.far_src_w = h->far_ssrc;
+  qa.ovf_sorted = h->ovf_sorted;
+  qa.ovf_sorted_w = h->ovf_sorted;
   qa.tot_w = h->btot;
   qa.tot = h->btot;
   qa.bstart = h->bstart;
   qa.bstart_w = h->bstart;
-  qa.tcode = h->tcode;
-  qa.to = (const float *)h->pos[1];
-  qa.tv = (const float *)h->vel[1];
-  qa.tids = pa.ids ? h->ids[1] : nullptr;
   qa.o = (float *)h->pos[0];
   qa.v = (float *)h->vel[0];
   qa.ids = pa.ids ? h->ids[0] : nullptr;
@@ -548,9 +546,8 @@ int brick_push_and_rebin(pic_t h, double dt) {
   qa.max_bucket = h->scalars + 2;
   qa.err = h->err;
   qa.part = (float *)h->part;
-  qa.bpiece = h->bpiece;
-  qa.bpiece_w = h->bpiece;
-  (void)d;
+  qa.fb_key = h->fb_key;
+  qa.fb_idx = h->fb_idx;
   CK(cudaMemsetAsync(h->scalars + 1, 0, sizeof(int32_t) * 2, s));
   {
     PhaseScope ps(h, PIC_PHASE_PUSH);
@@ -558,7 +555,7 @@ int brick_push_and_rebin(pic_t h, double dt) {
   }
   {
     PhaseScope ps(h, PIC_PHASE_REBIN);
-    launch_brick_pull(h->dt, h->bg, pa, qa, h->fcount, h->fcursor, h->tile_sums, h->scalars + 3, s);
+    launch_brick_pull(h->dt, h->bg, qa, h->fcount, h->fcursor, h->tile_sums, h->scalars + 3, s);
   }
   {
     // the pull also summed the deposit partials of the new positions
