@@ -62,21 +62,22 @@ def brick_bytes(d: int, ppc: float, track_ids: bool) -> dict:
     """Compulsory bytes per particle of each phase of the brick path (uniform
     tree, PIT, FP32 split), bricks of 9^d leaves: what each kernel must read
     and write given its inputs and outputs.
-      push   (k_brick_push_st): offsets + velocities in, the brick's staged
-             field ((9+1)^d vertices x d x 4 B) and leaf offsets, pushed
-             offsets + velocities + 2-byte direction code out;
-      rebin  (k_brick_pull_st + helpers): the pushed state and codes in, the
-             bucket-ordered state, leaf offsets and 2^d corner partials per
-             leaf out;
+      push   (k_brick_push_st): offsets + velocities (+ id) in, the brick's
+             staged field ((9+1)^d vertices x d x 4 B) and leaf offsets, the
+             pushed offsets + velocities (+ id), a 2-byte leaf code and a
+             4-byte canonical key out to the destination's staging area;
+      rebin  (k_brick_pull_st + helpers): the staged arrivals in, the
+             bucket-ordered state (+ id), leaf offsets and 2^d corner partials
+             per leaf out;
       deposit (k_vertex_charge): corner partials in, vertex charge out."""
-    st = 2 * d * 4 + (8 if track_ids else 0)
-    leaves = 9 ** d
-    per_brick = leaves * ppc
-    field = (10 ** d) * d * 4 / per_brick
+    s0 = 2 * d * 4
+    idb = 4 if track_ids else 0
+    staged = s0 + idb + 2 + 4
+    field = (10 ** d) * d * 4 / ((9 ** d) * ppc)
     nc = 1 << d
     return {
-        "push": st + field + 4 / ppc + st + 2,
-        "rebin": st + 2 + st + 4 / ppc + nc * 4 / ppc,
+        "push": s0 + idb + field + 4 / ppc + staged,
+        "rebin": staged + s0 + idb + 4 / ppc + nc * 4 / ppc,
         "deposit": nc * 4 / ppc + 4 / ppc,
         "permute": 0.0,
     }
@@ -413,8 +414,8 @@ def main():
     info = g.info()
     if info.brick:
         kb = brick_bytes(d, cfg["ppc"], track_ids=False)
-        names = {"push": "k_brick_push_st (gather + kick + drift + re-location + direction partition)",
-                 "rebin": "k_brick_pull_st (+ far-list and brick-offset helpers): canonical re-bin + corner partials",
+        names = {"push": "k_brick_push_st (gather + kick + drift + re-location + append to the destination's staging area)",
+                 "rebin": "k_brick_pull_st (+ overflow and unit-offset helpers): canonical re-bin + corner partials",
                  "deposit": "k_vertex_charge (vertex sums of the corner partials)"}
     else:
         kb = kernel_bytes(d, split, cfg["ppc"])

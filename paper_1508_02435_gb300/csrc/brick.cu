@@ -378,9 +378,8 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
   uint32_t *dec = (uint32_t *)(ls + K::LB + 1);      // LB
   int32_t *rel = (int32_t *)(dec + K::LB);           // 3 x 32: per-axis direction | leaf-index parts
   int32_t *nbr = rel + 3 * 32;                       // 27 neighbour bricks by direction
-  int32_t *wc = nbr + 32;                            // [warp][unit slot] arrivals, then offsets
+  int32_t *wc = nbr + 32;                            // [warp][unit slot] arrivals, then first slot
   uint8_t *lslot = (uint8_t *)(wc + kW * kUnitSlots); // rank within (warp, unit slot)
-  __shared__ int32_t dbase[kUnitSlots];              // first reserved staging slot per unit slot
   __shared__ int32_t s_movers;
   __shared__ uint64_t s_bar;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -598,28 +597,25 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
     if (uslot >= 0) lslot[q] = (uint8_t)(r0 + __popc(peers & ((1u << lane) - 1u)));
     __syncwarp();  // the counts are read by other lanes in the next chunk
   }
-  __syncthreads();
-  // per unit slot: offsets of the warps' runs, then one reservation in the
-  // destination unit's staging area
-  if (tid < 54) {
-    int32_t sum = 0;
-    for (int k = 0; k < kW; ++k) {
-      const int32_t c = wc[k * kUnitSlots + tid];
-      wc[k * kUnitSlots + tid] = sum;
-      sum += c;
-    }
-    dbase[tid] = sum > 0 ? atomicAdd(&a.st.fill[2 * nbr[tid >> 1] + (tid & 1)], sum) : 0;
+  // the warp reserves its runs in the destination units' staging areas (one
+  // atomic per unit it sends to; the count becomes the run's first slot)
+  for (int us = lane; us < 54; us += 32) {
+    const int32_t c = wc[w * kUnitSlots + us];
+    if (c > 0) wc[w * kUnitSlots + us] = atomicAdd(&a.st.fill[2 * nbr[us >> 1] + (us & 1)], c);
   }
-  __syncthreads();
-  // pass B: every arrival to its reserved slot (consecutive particles of a
-  // warp hold consecutive ranks, so the stores coalesce)
-  for (int32_t q = tid; q < nb; q += blockDim.x) {
+  __syncwarp();
+  // pass B, the warp's own chunks: every arrival to its reserved slot
+  // (consecutive particles of a chunk hold consecutive ranks, so the stores
+  // coalesce)
+  for (int c = w; c < nc32; c += kW) {
+    const int32_t q = c * 32 + lane;
+    if (q >= nb) break;
     const uint16_t cd = pos[q];
     const int dir = (cd >> 10) & 31;
     if (dir == kFarSlot) continue;
     const int hh = (cd & 0x3ff) >= K::LH;
     const int us = 2 * dir + hh;
-    const int32_t slot = dbase[us] + wc[((q >> 5) % kW) * kUnitSlots + us] + lslot[q];
+    const int32_t slot = wc[w * kUnitSlots + us] + lslot[q];
     float on[D], vn[D];
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
@@ -827,15 +823,16 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
     if (tid == 0) atomicOr(a.err, kErrCode);
     return;
   }
-  // leaf offsets (nlf <= blockDim.x), cursors
+  // leaf offsets (nlf <= blockDim.x), cursors, largest leaf count
   {
     const int32_t c = tid < nlf ? cnt[tid] : 0;
     const int32_t off = block_excl_scan(c, wsum);
     if (tid < nlf) {
       cnt[tid] = off;
       cur[tid] = off;
-      if (c > 0) atomicMax(&s_max, c);
     }
+    const int32_t wmax = __reduce_max_sync(0xffffffffu, c);
+    if ((tid & 31) == 0 && wmax > 0) atomicMax(&s_max, wmax);
     if (tid == 0) cnt[nlf] = nin;
   }
   __syncthreads();
