@@ -579,14 +579,8 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
       pos[q] = (uint16_t)(lidx | (dir << 10) | (stay ? kStayBit : 0));
       if (dir != kFarSlot) uslot = 2 * dir + (lidx >= K::LH);
     }
-    // lanes of the chunk with the same unit slot agree in all six bits of it
-    unsigned peers = __ballot_sync(0xffffffffu, uslot >= 0);
-#pragma unroll
-    for (int bit = 0; bit < 6; ++bit) {
-      const bool x = (uslot >> bit) & 1;
-      const unsigned bb = __ballot_sync(0xffffffffu, x);
-      peers &= x ? bb : ~bb;
-    }
+    // lanes of the chunk with the same unit slot
+    const unsigned peers = __match_any_sync(0xffffffffu, uslot);
     const int leader = uslot >= 0 ? __ffs(peers) - 1 : lane;
     int32_t r0 = 0;
     if (uslot >= 0 && lane == leader) {  // one leader per distinct slot: distinct words
@@ -732,6 +726,44 @@ size_t pull_st_smem() {
   return (sizeof(float) * 2 * D + sizeof(uint32_t) + 2 * sizeof(uint16_t)) * kStCap;
 }
 
+// Sorts the m <= N arrival indices mp[0..m) of one leaf by their keys
+// (distinct) with a bitonic network over (key, index) pairs in registers.
+template <int N>
+__device__ __forceinline__ void sort_leaf_net(uint16_t *mp, int m, const uint32_t *key) {
+  uint32_t k[N], v[N];
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    v[t] = t < m ? mp[t] : 0u;
+    k[t] = t < m ? key[v[t]] : 0xffffffffu;
+  }
+#pragma unroll
+  for (int kk = 2; kk <= N; kk <<= 1)
+#pragma unroll
+    for (int j = kk >> 1; j > 0; j >>= 1)
+#pragma unroll
+      for (int t = 0; t < N; ++t) {
+        const int u = t ^ j;
+        if (u > t) {
+          const bool up = (t & kk) == 0;
+          const bool sw = up ? k[t] > k[u] : k[t] < k[u];
+          const uint32_t tk = k[t], tv = v[t];
+          k[t] = sw ? k[u] : tk;
+          v[t] = sw ? v[u] : tv;
+          k[u] = sw ? tk : k[u];
+          v[u] = sw ? tv : v[u];
+        }
+      }
+#pragma unroll
+  for (int t = 0; t < N; ++t)
+    if (t < m) mp[t] = (uint16_t)v[t];
+}
+
+// Size class of a leaf's sort: -1 nothing to sort, 0..2 networks of 4, 8
+// and 16, 3 a warp.
+__device__ __forceinline__ int leaf_class(int32_t m) {
+  return m <= 1 ? -1 : (m <= 4 ? 0 : (m <= 8 ? 1 : (m <= 16 ? 2 : 3)));
+}
+
 // Exclusive scan of c over the first nl <= blockDim.x threads of the block
 // (c = 0 beyond); returns this thread's offset.  wsum holds one word per warp.
 __device__ __forceinline__ int32_t block_excl_scan(int32_t c, int32_t *wsum) {
@@ -762,9 +794,9 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
   __shared__ int32_t cnt[K::LH + 1];
   __shared__ int32_t cur[K::LH];
   __shared__ int32_t wsum[kStThreads / 32];
-  __shared__ int32_t s_max;
+  __shared__ int32_t s_max, s_ccount[4];
   __shared__ uint64_t s_bar;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const BrickStage &st = a.st;
   const int32_t u = blockIdx.x, b = u >> 1;
   const int lf0 = (u & 1) ? K::LH : 0, nlf = (u & 1) ? K::LB - K::LH : K::LH;
@@ -773,6 +805,7 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
   const int32_t nin = st.fill[u];
   if (nin > st.cap) return;  // the global-memory kernel takes this unit
   const int64_t at = (int64_t)u * st.cap;
+  if (tid < 4) s_ccount[tid] = 0;
   if (tid == 0) {
     s_max = 0;
     if (nin > 0) {
@@ -823,7 +856,9 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
     if (tid == 0) atomicOr(a.err, kErrCode);
     return;
   }
-  // leaf offsets (nlf <= blockDim.x), cursors, largest leaf count
+  // leaf offsets (nlf <= blockDim.x), cursors, largest leaf count; the
+  // thread of leaf tid notes its sort class and its rank within the class
+  int cls = -1, crank = 0;
   {
     const int32_t c = tid < nlf ? cnt[tid] : 0;
     const int32_t off = block_excl_scan(c, wsum);
@@ -832,28 +867,58 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
       cur[tid] = off;
     }
     const int32_t wmax = __reduce_max_sync(0xffffffffu, c);
-    if ((tid & 31) == 0 && wmax > 0) atomicMax(&s_max, wmax);
+    if (lane == 0 && wmax > 0) atomicMax(&s_max, wmax);
     if (tid == 0) cnt[nlf] = nin;
+    cls = leaf_class(c);
+    const unsigned peers = __match_any_sync(0xffffffffu, cls);
+    const int leader = __ffs(peers) - 1;
+    int32_t base = 0;
+    if (cls >= 0 && lane == leader) base = atomicAdd(&s_ccount[cls], __popc(peers));
+    crank = __shfl_sync(0xffffffffu, base, leader) + __popc(peers & ((1u << lane) - 1u));
   }
   __syncthreads();
   // bucket positions in any order
   for (int32_t i = tid; i < nin; i += blockDim.x) map[atomicAdd(&cur[(code[i] & 0x3ff) - lf0], 1)] = (uint16_t)i;
   __syncthreads();
-  // canonical position of every arrival: its leaf's offset plus the number
-  // of arrivals of the leaf with a smaller key (keys are distinct)
-  for (int32_t j = tid; j < nin; j += blockDim.x) {
-    const int32_t i = map[j];
-    const int lf = (code[i] & 0x3ff) - lf0;
-    const int32_t lo = cnt[lf], hi = cnt[lf + 1];
-    int32_t r = 0;
-    if (hi - lo > 1) {
-      const uint32_t kx = key[i];
-      for (int32_t j2 = lo; j2 < hi; ++j2) r += key[map[j2]] < kx;
-    }
-    code[i] = (uint16_t)(lo + r);
-  }
+  // leaves to sort, grouped by size class (the cursors are free now), so that
+  // the threads of a warp run the same network
+  uint16_t *list = (uint16_t *)cur;
+  const int32_t nA = s_ccount[0], nB = s_ccount[1], nC = s_ccount[2], nD = s_ccount[3];
+  if (cls >= 0) list[(cls > 0 ? nA : 0) + (cls > 1 ? nB : 0) + (cls > 2 ? nC : 0) + crank] = (uint16_t)tid;
   __syncthreads();
-  for (int32_t i = tid; i < nin; i += blockDim.x) map[code[i]] = (uint16_t)i;
+  // every leaf's arrivals sorted by canonical key, in place
+  const int32_t nABC = nA + nB + nC;
+  for (int32_t t = tid; t < nABC; t += blockDim.x) {
+    const int lf = list[t];
+    const int32_t lo = cnt[lf], m = cnt[lf + 1] - lo;
+    if (m <= 4) sort_leaf_net<4>(map + lo, m, key);
+    else if (m <= 8) sort_leaf_net<8>(map + lo, m, key);
+    else sort_leaf_net<16>(map + lo, m, key);
+  }
+  for (int32_t dd = w; dd < nD; dd += blockDim.x >> 5) {  // a warp per leaf over 16 arrivals
+    const int lf = list[nABC + dd];
+    const int32_t lo = cnt[lf], m = cnt[lf + 1] - lo;
+    if (m <= 32) {
+      const int32_t i = lane < m ? map[lo + lane] : 0;
+      const uint32_t kx = lane < m ? key[i] : 0xffffffffu;
+      int32_t r = 0;
+      for (int t2 = 0; t2 < m; ++t2) r += __shfl_sync(0xffffffffu, kx, t2) < kx;
+      __syncwarp();
+      if (lane < m) map[lo + r] = (uint16_t)i;
+    } else if (lane == 0) {  // insertion sort by one thread (crowded leaves only)
+      for (int32_t x = lo + 1; x < lo + m; ++x) {
+        const uint16_t v = map[x];
+        const uint32_t kv = key[v];
+        int32_t y = x - 1;
+        while (y >= lo && key[map[y]] > kv) {
+          map[y + 1] = map[y];
+          --y;
+        }
+        map[y + 1] = v;
+      }
+    }
+    __syncwarp();
+  }
   const int32_t bstart = a.bstart[u];
   for (int l = tid; l < nlf; l += blockDim.x) a.new_start[L0 + l] = bstart + cnt[l];
   if (u == 2 * g.n_bricks - 1 && tid == 0) a.new_start[(int64_t)g.n_bricks * K::LB] = bstart + nin;
@@ -904,12 +969,20 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
 #pragma unroll
           for (int ax = 0; ax < D; ++ax) on[ax] = so[ax * kStCap + i];
         }
-#pragma unroll
-        for (int e = 0; e < K::NC; ++e) {
-          float wgt = 1.0f;
-#pragma unroll
-          for (int ax = 0; ax < D; ++ax) wgt = wgt * (((e >> ax) & 1) ? o[ax] : om[ax]);
-          acc[e] = acc[e] + wgt;
+        // corner weights (f0 * f1) [* f2] as in the push, two corners per
+        // paired multiply, then summed per corner in bucket order
+        const float2 f0 = make_float2(om[0], o[0]);
+        const float2 a01 = mul2_rn(f0, make_float2(om[1], om[1]));
+        const float2 a23 = mul2_rn(f0, make_float2(o[1], o[1]));
+        if constexpr (D == 3) {
+          const float2 w01 = mul2_rn(a01, make_float2(om[2], om[2]));
+          const float2 w23 = mul2_rn(a23, make_float2(om[2], om[2]));
+          const float2 w45 = mul2_rn(a01, make_float2(o[2], o[2]));
+          const float2 w67 = mul2_rn(a23, make_float2(o[2], o[2]));
+          acc[0] = acc[0] + w01.x; acc[1] = acc[1] + w01.y; acc[2] = acc[2] + w23.x; acc[3] = acc[3] + w23.y;
+          acc[4] = acc[4] + w45.x; acc[5] = acc[5] + w45.y; acc[6] = acc[6] + w67.x; acc[7] = acc[7] + w67.y;
+        } else {
+          acc[0] = acc[0] + a01.x; acc[1] = acc[1] + a01.y; acc[2] = acc[2] + a23.x; acc[3] = acc[3] + a23.y;
         }
       }
       float *gp = a.part + (int64_t)(L0 + l) * K::NC;
