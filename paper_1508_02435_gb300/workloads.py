@@ -33,6 +33,7 @@ __all__ = [
     "batched_langmuir",
     "random_tree_flags",
     "random_particles",
+    "random_field",
 ]
 
 
@@ -266,3 +267,10 @@ def random_particles(d: int, n: int, seed: int, vmax: float = 1.0) -> tuple[np.n
     x = rng.random((d, n))
     v = rng.uniform(-vmax, vmax, (d, n))
     return x, v
+
+
+def random_field(d: int, n_vertices: int, seed: int, amp: float) -> np.ndarray:
+    """A seeded vertex field for tests that hold E fixed: FP32 values uniform
+    in [-amp, amp), shape (d, n_vertices) in the vertex numbering of the tree."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-amp, amp, (d, n_vertices)).astype(np.float32)

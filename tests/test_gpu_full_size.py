@@ -1,0 +1,155 @@
+"""The 3D uniform Langmuir configuration at its full size (243^3 leaves, 8
+particles per cell, 114,791,256 particles) through the brick path in the
+launch configuration the bench times (FP32 split, PIT, no id tracking,
+field held fixed between steps).
+
+The field is a seeded vertex field set through the solve hook, so that it is
+an input of both sides.  A second handle with id tracking runs the same
+steps; its state must equal the bench-configuration handle's bit for bit,
+and the ids let the test check, for every particle, that each bucket holds
+its particles in the canonical order (stayers first, then arrivals, each in
+storage order; Section 4 bookkeeping, Algorithm 1 end state), and that
+sampled particles, pushed one by one by the oracle from the same inputs, end
+in the same leaf with the same offsets and velocities.  The deposit after the
+steps is checked at sampled vertices against an FP64 re-sum of the particles'
+cloud-in-cell weights (Section 3 item 1) within FP32 accumulation error."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1508_02435_gb300 import pic
+from paper_1508_02435_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU hosts
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+
+class _DevArray:
+    """Zero-copy view of a device buffer the library hands to the solve hook."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None, "stream": None}
+
+
+def _inverse(perm):
+    inv = np.empty(len(perm), np.int64)
+    inv[perm] = np.arange(len(perm), dtype=np.int64)
+    return inv
+
+
+def _check_canonical(leaf, old_index, old_leaf):
+    """Bucket order = (leaf, moved, storage index before the step), strictly
+    increasing over the whole array; moved = leaf changed."""
+    moved = (leaf != old_leaf[old_index]).astype(np.int64)
+    comp = (leaf.astype(np.int64) << 33) | (moved << 32) | old_index
+    assert np.all(comp[1:] > comp[:-1]), "bucket order is not canonical"
+    return int(moved.sum())
+
+
+def _check_offsets(start, leaf, n_leaves):
+    expect = np.zeros(n_leaves + 1, np.int64)
+    np.cumsum(np.bincount(leaf, minlength=n_leaves), out=expect[1:])
+    assert np.array_equal(np.asarray(start, np.int64), expect), "bucket offsets disagree with the leaves"
+
+
+def test_langmuir3d_full_size_bench_configuration():
+    w = W.langmuir(3, 5, 8, vth=0.05, dt=0.1)
+    n = w.n
+    assert n == 114_791_256
+    tree = oracle.Tree(3, w.flags)
+    nv = tree.n_vertices
+    nl = tree.n_leaves
+    E = W.random_field(3, nv, seed=7, amp=0.05)
+    E_dev = torch.from_numpy(E).cuda()
+    stream = torch.cuda.Stream()
+
+    def set_field(user, q_dev, e_dev, n_vertices, precision, st):
+        assert precision == pic.FP32_SPLIT and n_vertices == nv
+        dst = torch.as_tensor(_DevArray(e_dev, (3, nv), "<f4"), device="cuda")
+        with torch.cuda.stream(torch.cuda.ExternalStream(st)):
+            dst.copy_(E_dev)
+        return 0
+
+    hook = pic.SOLVE_FN(set_field)
+    kw = dict(scheme=pic.PIT, precision=pic.FP32_SPLIT, q=w.q, qm=w.qm, ion=w.ion, sweeps=10, omega=0.8,
+              stream=stream)
+    ga = pic.Pic(3, w.flags, w.x, w.v, track_ids=False, **kw)   # the bench's configuration
+    gb = pic.Pic(3, w.flags, w.x, w.v, track_ids=True, **kw)    # the same steps, with ids
+    assert ga.info().brick == 1 and gb.info().brick == 1, "brick path not selected"
+
+    leaf0, _, _ = gb.get_state()
+    start0, ids0 = gb.bins()
+    _check_offsets(start0, leaf0, nl)
+    # creation: every particle counts as arriving, in input order
+    comp0 = (leaf0.astype(np.int64) << 32) | ids0.astype(np.int64)
+    assert np.all(comp0[1:] > comp0[:-1]), "initial bucket order is not canonical"
+    pos0 = _inverse(ids0)
+    del comp0
+
+    for g in (ga, gb):
+        g.step(w.dt, hook=hook)
+    ga.sync()
+    gb.sync()
+    leaf1, _, _ = gb.get_state()
+    start1, ids1 = gb.bins()
+    _check_offsets(start1, leaf1, nl)
+    movers1 = _check_canonical(leaf1, pos0[ids1], leaf0)
+    pos1 = _inverse(ids1)
+    del leaf0, pos0
+
+    for g in (ga, gb):
+        g.step_fixed_field(w.dt)
+    ga.sync()
+    gb.sync()
+    leaf2, o2, v2 = gb.get_state()
+    start2, ids2 = gb.bins()
+    _check_offsets(start2, leaf2, nl)
+    movers2 = _check_canonical(leaf2, pos1[ids2], leaf1)
+    assert movers1 > n // 2 and movers2 > n // 2  # thermal speed: most particles change leaf each step
+    del leaf1, pos1, ids1
+
+    la, oa, va = ga.get_state()
+    assert np.array_equal(la, leaf2) and np.array_equal(oa, o2) and np.array_equal(va, v2), \
+        "the bench configuration differs from the id-tracking handle"
+    del la, oa, va
+
+    # sampled particles pushed one by one by the oracle from the same inputs
+    rng = np.random.default_rng(11)
+    sid = np.unique(rng.integers(0, n, 70_000))[:65_536]
+    lf, o, v = tree.split_from64(np.ascontiguousarray(w.x[:, sid]), np.ascontiguousarray(w.v[:, sid]))
+    for _ in range(2):
+        tree.push32(lf, o, v, E, w.qm, w.dt)
+    p = _inverse(ids2)[sid]
+    assert np.array_equal(leaf2[p], lf), "sampled leaves differ from the oracle"
+    assert np.array_equal(o2[:, p], o) and np.array_equal(v2[:, p], v), "sampled particle state differs"
+
+    # deposit at sampled vertices against an FP64 re-sum of the particles'
+    # cloud-in-cell weights (ion background from the oracle's vertex loads)
+    Q = ga.deposit()
+    ion_load, _ = tree.vertex_aux()
+    vpos = tree.vertex_pos()                                   # (3, nv), units 3^-5
+    lev, co = tree.leaf_info()
+    M = 3 ** 5
+    cell_leaf = np.empty(M ** 3, np.int64)
+    cell_leaf[co[:, 0] + M * (co[:, 1] + M * co[:, 2])] = np.arange(nl)
+    vs = rng.choice(nv, 4096, replace=False)
+    for vid in vs:
+        s = 0.0
+        for e in range(8):
+            eb = [(e >> a) & 1 for a in range(3)]
+            c = [(int(vpos[a, vid]) - eb[a]) % M for a in range(3)]
+            L = cell_leaf[c[0] + M * (c[1] + M * c[2])]
+            oo = o2[:, start2[L]:start2[L + 1]].astype(np.float64)
+            wgt = np.ones(oo.shape[1])
+            for a in range(3):
+                wgt *= oo[a] if eb[a] else 1.0 - oo[a]
+            s += wgt.sum()
+        expect = w.q * s + w.ion * ion_load[vid]
+        scale = abs(w.q) * s + abs(w.ion * ion_load[vid])
+        assert abs(Q[vid] - expect) <= 2e-6 * scale + 1e-12, f"deposit at vertex {vid} differs"
