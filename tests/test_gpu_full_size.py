@@ -153,3 +153,57 @@ def test_langmuir3d_full_size_bench_configuration():
         expect = w.q * s + w.ion * ion_load[vid]
         scale = abs(w.q) * s + abs(w.ion * ion_load[vid])
         assert abs(Q[vid] - expect) <= 2e-6 * scale + 1e-12, f"deposit at vertex {vid} differs"
+
+
+@pytest.mark.parametrize("precision", [pic.FP32_SPLIT, pic.FP64])
+def test_batch256_full_size_sampled_instances(precision):
+    """The batched configuration at its full size (256 2D Langmuir instances,
+    particle counts log-uniform 1e3..1e6, depths 3..5) as the bench runs it:
+    one handle, leapfrog start, autotuned shapes, the fixed-field step
+    captured in a CUDA graph (one ordinary step) and replayed twice.  The
+    instances are independent, so the oracle runs sampled instances whole —
+    the largest, the smallest and four drawn at random — and their states
+    must match (split: bit for bit; FP64: within 1e-12 relative)."""
+    insts = W.batched_langmuir(256, 1000, 1_000_000)
+    stream = torch.cuda.Stream()
+    g = pic.Pic.batch(2, [w.flags for w in insts], [w.x for w in insts], [w.v for w in insts],
+                      qs=[w.q for w in insts], scheme=pic.PIT, precision=precision, sweeps=10, omega=0.8,
+                      track_ids=False, stream=stream)
+    dt = 0.1
+    g.init_leapfrog(dt)
+    g.autotune(dt, trials=2)
+    g.graph_capture(dt)
+    g.graph_launch(2)
+    g.sync()
+    assert g.stats().error == 0
+    ps, vs, bs = g.instances()
+    split = precision == pic.FP32_SPLIT
+    state = g.get_state() if split else g.particles()
+    sizes = np.array([w.n for w in insts])
+    rng = np.random.default_rng(5)
+    pick = sorted({int(np.argmax(sizes)), int(np.argmin(sizes))} | set(rng.choice(256, 4, replace=False).tolist()))
+    for i in pick:
+        w = insts[i]
+        tree = oracle.Tree(2, w.flags)
+        prm = oracle.Params(scheme=oracle.PIT, q=w.q, qm=w.qm, ion=w.ion, sweeps=10, omega=0.8)
+        sl = slice(ps[i], ps[i + 1])
+        if split:
+            st = oracle.State32(tree, w.x, w.v, prm)
+            st.init_leapfrog(dt)
+            E = tree.efield32(st.V)
+            for _ in range(3):
+                tree.push32(st.leaf, st.o, st.v, E, w.qm, dt)
+                st.rebin()
+            leaf, o, v = state
+            assert np.array_equal(leaf[sl] - bs[i], st.leaf), f"instance {i}: leaves"
+            assert np.array_equal(o[:, sl], st.o) and np.array_equal(v[:, sl], st.v), f"instance {i}: state"
+        else:
+            st = oracle.State64(tree, w.x, w.v, prm)
+            st.init_leapfrog(dt)
+            E = tree.efield64(st.V)
+            for _ in range(3):
+                tree.push64(st.x, st.v, E, w.qm, dt)
+                st.rebin()
+            x, v = state
+            for a, b in ((x[:, sl], st.x), (v[:, sl], st.v)):
+                assert np.max(np.abs(a - b)) <= 1e-12 * max(np.max(np.abs(b)), 1e-300), f"instance {i}"
