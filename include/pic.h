@@ -290,6 +290,24 @@ PIC_API int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax);
 PIC_API int pic_bucket_noalloc(const int32_t *keys, int64_t n, int64_t n_keys, int32_t *start, int32_t *perm,
                                void *stream);
 
+/* Stream-like particle update, the calibration ceiling of the paper's
+ * memory-throughput experiment (Section 6, "Memory throughput"): `steps`
+ * passes over the particles, each advancing every position by one explicit
+ * Euler step x += v dt and reflecting it at the walls of the unit box
+ * (x < 0 -> -x, x > 1 -> 2 - x, the velocity component negated), written back
+ * in place.  No grid, no keys, no reordering.  Not part of the particle step:
+ * it bounds what a particle update can reach on the same memory system.
+ *
+ * d = 2 or 3; precision PIC_FP64 (double arrays) or PIC_FP32_SPLIT (float
+ * arrays, FP32 arithmetic with separate roundings of the product and the
+ * sum); x[d][n] and v[d][n] are device arrays, structure of arrays, owned by
+ * the caller and updated in place.  Work is queued on `stream` (a
+ * cudaStream_t; NULL = legacy default stream), one kernel per pass; the call
+ * does not synchronise.  Returns PIC_EINVAL for a bad d, precision, n < 0,
+ * steps < 0 or NULL arrays with n > 0; PIC_ECUDA if a launch fails. */
+PIC_API int pic_stream_step(int32_t d, int32_t precision, void *x, void *v, int64_t n, double dt, int32_t steps,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,8 @@ SIGNATURES = [
     ("pic_profile", C.c_int, [C.c_void_p, C.c_int32]),
     ("pic_graph_capture", C.c_int, [C.c_void_p, C.c_double]),
     ("pic_bucket_noalloc", C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pic_stream_step", C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int32,
+                                  C.c_void_p]),
     ("pic_graph_launch", C.c_int, [C.c_void_p, C.c_int32]),
     ("pic_autotune", C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p]),
     ("pic_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -140,6 +142,20 @@ def _ptr(a):
 
 
 NOALLOC_MAX_KEYS = 1 << 20
+
+
+def stream_step(x, v, dt: float, steps: int = 1, stream=None):
+    """Stream-like calibration update (pic_stream_step): `steps` passes of
+    x += v dt with reflection at the unit-box walls, in place on the device
+    tensors x[d][n], v[d][n] (float32 or float64).  Queued on `stream`."""
+    lib = load()
+    d, n = int(x.shape[0]), int(x.shape[1])
+    prec = FP64 if str(x.dtype) == "torch.float64" else FP32_SPLIT
+    st = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+    rc = lib.pic_stream_step(d, prec, C.c_void_p(x.data_ptr()), C.c_void_p(v.data_ptr()), n, float(dt), int(steps),
+                             C.c_void_p(st))
+    if rc != 0:
+        raise PicError(rc, lib.pic_strerror(rc).decode())
 
 
 def bucket_noalloc(keys, n_keys: int, start, perm, stream=None):
