@@ -138,9 +138,13 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.reader = threading.Thread(target=self._read, daemon=True)
             self.reader.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 3.0:  # sampling runs before the timed region starts
+                time.sleep(0.01)
+            self.lines.clear()
         except Exception:
             self.proc = None
         return self
