@@ -2,6 +2,8 @@
 #include "tree.hpp"
 
 #include <algorithm>
+#include <memory>
+#include <thread>
 #include <unordered_map>
 
 namespace pic {
@@ -121,11 +123,53 @@ double kref(int d, int e, int f) {
   return k3[diff];
 }
 
-struct GridPoint {
-  int state = 0;  // 0 new, 2 resolved
-  bool hanging = false;
-  std::vector<std::pair<int32_t, double>> ex;  // (point index, weight)
-};
+// Runs fn(t, lo, hi) on nt threads over [0, n) split into equal chunks.
+template <typename F>
+void parallel_chunks(int64_t n, unsigned nt, F fn) {
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t) {
+    const int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
+    th.emplace_back([=, &fn] { fn(t, lo, hi); });
+  }
+  for (auto &x : th) x.join();
+}
+
+unsigned host_threads() {
+  const unsigned hw = std::thread::hardware_concurrency();
+  return std::max(1u, std::min(hw == 0 ? 1u : hw, 32u));
+}
+
+// Stable LSD radix sort of records by the 64-bit value key(rec), 16 bits a
+// pass, passes on host threads over contiguous chunks (counts per chunk, then
+// bucket-major offsets, so equal keys keep their order).
+template <typename Rec, typename Key>
+void radix_sort(std::unique_ptr<Rec[]> &r, int64_t n, uint64_t key_max, Key key) {
+  constexpr int kBits = 16;
+  constexpr size_t kBuckets = size_t(1) << kBits;
+  const unsigned nt = host_threads();
+  std::unique_ptr<Rec[]> tmp(new Rec[n > 0 ? n : 1]);
+  std::vector<int64_t> cnt((size_t)nt * kBuckets);
+  for (int shift = 0; shift < 64 && (shift == 0 || (key_max >> shift) != 0); shift += kBits) {
+    auto digit = [&](const Rec &x) { return (size_t)((key(x) >> shift) & (kBuckets - 1)); };
+    parallel_chunks(n, nt, [&](unsigned t, int64_t lo, int64_t hi) {
+      int64_t *c = cnt.data() + (size_t)t * kBuckets;
+      std::fill(c, c + kBuckets, 0);
+      for (int64_t i = lo; i < hi; ++i) c[digit(r[i])]++;
+    });
+    int64_t run = 0;
+    for (size_t k = 0; k < kBuckets; ++k)
+      for (unsigned t = 0; t < nt; ++t) {
+        const int64_t v = cnt[(size_t)t * kBuckets + k];
+        cnt[(size_t)t * kBuckets + k] = run;
+        run += v;
+      }
+    parallel_chunks(n, nt, [&](unsigned t, int64_t lo, int64_t hi) {
+      int64_t *c = cnt.data() + (size_t)t * kBuckets;
+      for (int64_t i = lo; i < hi; ++i) tmp[c[digit(r[i])]++] = r[i];
+    });
+    r.swap(tmp);
+  }
+}
 
 }  // namespace
 
@@ -156,28 +200,51 @@ void HostTree::build_grid() {
     for (int a = 0; a < d; ++a) { k += p[a] * m; m *= M; }
     return k;
   };
-  std::unordered_map<int64_t, int32_t> index;
-  index.reserve((size_t)n_leaves * 2);
-  std::vector<GridPoint> pts;
-  std::vector<int64_t> pkey;
-  auto point = [&](const int64_t p[3]) -> int32_t {
-    int64_t k = key_of(p);
-    auto it = index.find(k);
-    if (it != index.end()) return it->second;
-    int32_t id = (int32_t)pts.size();
-    index.emplace(k, id);
-    pts.emplace_back();
-    pkey.push_back(k);
-    return id;
+  const unsigned nt = host_threads();
+  const int64_t nlc = n_leaves * nc;
+  // grid points: the distinct leaf corners, by row-major key on the finest
+  // level (sorted keys; a corner's point is its key's rank)
+  struct KC {
+    uint64_t key;
+    int64_t lc;
   };
-  // resolve: non-hanging iff it is a corner of the coarsest leaf whose closure
-  // holds it; else the d-linear interpolant of that leaf's corners
-  std::vector<int32_t> work;
-  auto resolve = [&](int32_t root_id) {
-    work.push_back(root_id);
-    while (!work.empty()) {
-      int32_t id = work.back();
-      if (pts[id].state == 2) { work.pop_back(); continue; }
+  std::unique_ptr<KC[]> kc(new KC[nlc > 0 ? nlc : 1]);
+  parallel_chunks(n_leaves, nt, [&](unsigned, int64_t lo, int64_t hi) {
+    for (int64_t l = lo; l < hi; ++l) {
+      const int32_t nd = leaf_node[l];
+      const int64_t s = pow3(depth - level[nd]);
+      for (int e = 0; e < nc; ++e) {
+        int64_t q[3] = {0, 0, 0};
+        for (int a = 0; a < d; ++a) {
+          q[a] = (coords[nd * 3 + a] + ((e >> a) & 1)) * s;
+          if (q[a] >= M) q[a] -= M;
+        }
+        kc[l * nc + e] = {(uint64_t)key_of(q), l * nc + e};
+      }
+    }
+  });
+  uint64_t key_max = 1;
+  for (int a = 0; a < d; ++a) key_max *= (uint64_t)M;
+  radix_sort(kc, nlc, key_max, [](const KC &x) { return x.key; });
+  std::vector<int64_t> pkey;
+  std::vector<int32_t> corner_pt(nlc);
+  for (int64_t i = 0; i < nlc; ++i) {
+    if (i == 0 || kc[i].key != kc[i - 1].key) pkey.push_back((int64_t)kc[i].key);
+    corner_pt[kc[i].lc] = (int32_t)(pkey.size() - 1);
+  }
+  kc.reset();
+  const int64_t np = (int64_t)pkey.size();
+  auto point = [&](const int64_t q[3]) -> int32_t {  // an existing point (a leaf corner)
+    const int64_t k = key_of(q);
+    return (int32_t)(std::lower_bound(pkey.begin(), pkey.end(), k) - pkey.begin());
+  };
+  // every point: the coarsest leaf whose closure holds it; non-hanging iff it
+  // is a corner of that leaf, else (hanging) the d-linear interpolant of the
+  // leaf's corners (weights by the point's place in the leaf)
+  std::vector<uint8_t> hanging(np, 0);
+  std::vector<int32_t> best_of(np, -1);
+  parallel_chunks(np, nt, [&](unsigned, int64_t lo, int64_t hi) {
+    for (int64_t id = lo; id < hi; ++id) {
       int64_t p[3] = {0, 0, 0}, k = pkey[id];
       for (int a = 0; a < d; ++a) { p[a] = k % M; k /= M; }
       int32_t best = -1;
@@ -190,23 +257,37 @@ void HostTree::build_grid() {
         int32_t nd = leaf_at(Q);
         if (best < 0 || level[nd] < level[best]) best = nd;
       }
-      int64_t s = pow3(depth - level[best]);
-      int64_t r[3] = {0, 0, 0};
+      const int64_t s = pow3(depth - level[best]);
       bool corner = true;
       for (int a = 0; a < d; ++a) {
         int64_t rr = p[a] - coords[best * 3 + a] * s;
         if (rr < 0) rr += M;
-        r[a] = rr;
         if (rr != 0 && rr != s) corner = false;
       }
-      if (corner) {
-        pts[id].hanging = false;
-        pts[id].ex = {{id, 1.0}};
-        pts[id].state = 2;
-        work.pop_back();
-        continue;
+      hanging[id] = corner ? 0 : 1;
+      best_of[id] = best;
+    }
+  });
+  // expansions of hanging points onto non-hanging ones, masters first
+  // (memoised; the masters of a hanging point are corners of a coarser leaf)
+  std::vector<int32_t> hslot(np, -1);
+  std::vector<std::vector<std::pair<int32_t, double>>> hex;
+  std::vector<int32_t> work;
+  auto resolve = [&](int32_t root_id) {
+    work.push_back(root_id);
+    while (!work.empty()) {
+      const int32_t id = work.back();
+      if (!hanging[id] || hslot[id] >= 0) { work.pop_back(); continue; }
+      int64_t p[3] = {0, 0, 0}, k = pkey[id];
+      for (int a = 0; a < d; ++a) { p[a] = k % M; k /= M; }
+      const int32_t best = best_of[id];
+      const int64_t s = pow3(depth - level[best]);
+      int64_t r[3] = {0, 0, 0};
+      for (int a = 0; a < d; ++a) {
+        int64_t rr = p[a] - coords[best * 3 + a] * s;
+        if (rr < 0) rr += M;
+        r[a] = rr;
       }
-      // the masters first
       bool ready = true;
       int32_t cid[8];
       double cw[8];
@@ -220,7 +301,7 @@ void HostTree::build_grid() {
         }
         cw[e] = w;
         cid[e] = w == 0.0 ? -1 : point(q);
-        if (cid[e] >= 0 && pts[cid[e]].state != 2) {
+        if (cid[e] >= 0 && hanging[cid[e]] && hslot[cid[e]] < 0) {
           ready = false;
           work.push_back(cid[e]);
         }
@@ -229,56 +310,60 @@ void HostTree::build_grid() {
       std::vector<std::pair<int32_t, double>> ex;
       for (int e = 0; e < nc; ++e) {
         if (cid[e] < 0) continue;
-        for (auto &pr : pts[cid[e]].ex) {
-          bool merged = false;
+        auto merge = [&](int32_t pid, double wt) {
           for (auto &q : ex)
-            if (q.first == pr.first) { q.second += cw[e] * pr.second; merged = true; break; }
-          if (!merged) ex.push_back({pr.first, cw[e] * pr.second});
-        }
+            if (q.first == pid) { q.second += cw[e] * wt; return; }
+          ex.push_back({pid, cw[e] * wt});
+        };
+        if (!hanging[cid[e]]) merge(cid[e], 1.0);
+        else for (auto &pr : hex[hslot[cid[e]]]) merge(pr.first, pr.second);
       }
-      pts[id].hanging = true;
-      pts[id].ex = std::move(ex);
-      pts[id].state = 2;
+      hslot[id] = (int32_t)hex.size();
+      hex.push_back(std::move(ex));
       work.pop_back();
     }
   };
-  const int64_t nlc = n_leaves * nc;
-  std::vector<int32_t> corner_pt(nlc);
-  for (int64_t l = 0; l < n_leaves; ++l) {
-    int32_t nd = leaf_node[l];
-    int64_t s = pow3(depth - level[nd]);
-    for (int e = 0; e < nc; ++e) {
-      int64_t q[3] = {0, 0, 0};
-      for (int a = 0; a < d; ++a) q[a] = ((coords[nd * 3 + a] + ((e >> a) & 1)) * s) % M;
-      corner_pt[l * nc + e] = point(q);
-    }
-  }
-  for (int64_t i = 0; i < nlc; ++i) resolve(corner_pt[i]);
-  // vertex ids by row-major key
+  for (int64_t id = 0; id < np; ++id)
+    if (hanging[id]) resolve((int32_t)id);
+  // vertex ids: the non-hanging points in key order
   vert_key.clear();
-  for (size_t i = 0; i < pts.size(); ++i)
-    if (!pts[i].hanging) vert_key.push_back(pkey[i]);
-  std::sort(vert_key.begin(), vert_key.end());
+  std::vector<int32_t> vid_of_point(np, -1);
+  for (int64_t id = 0; id < np; ++id)
+    if (!hanging[id]) {
+      vid_of_point[id] = (int32_t)vert_key.size();
+      vert_key.push_back(pkey[id]);
+    }
   n_vert = (int64_t)vert_key.size();
-  std::vector<int32_t> vid_of_point(pts.size(), -1);
-  for (size_t i = 0; i < pts.size(); ++i)
-    if (!pts[i].hanging)
-      vid_of_point[i] = (int32_t)(std::lower_bound(vert_key.begin(), vert_key.end(), pkey[i]) -
-                                  vert_key.begin());
+  // leaf corner -> (vertex, weight), ascending vertex
   cexp_ptr.assign(nlc + 1, 0);
-  cexp_vid.clear();
-  cexp_w.clear();
   for (int64_t i = 0; i < nlc; ++i) {
-    cexp_ptr[i] = (int32_t)cexp_vid.size();
-    std::vector<std::pair<int32_t, double>> ex;
-    for (auto &pr : pts[corner_pt[i]].ex) ex.push_back({vid_of_point[pr.first], pr.second});
-    std::sort(ex.begin(), ex.end(),
-              [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
-                return a.first < b.first;
-              });
-    for (auto &pr : ex) { cexp_vid.push_back(pr.first); cexp_w.push_back(pr.second); }
+    const int32_t pt = corner_pt[i];
+    cexp_ptr[i + 1] = cexp_ptr[i] + (hanging[pt] ? (int32_t)hex[hslot[pt]].size() : 1);
   }
-  cexp_ptr[nlc] = (int32_t)cexp_vid.size();
+  cexp_vid.assign(cexp_ptr[nlc], 0);
+  cexp_w.assign(cexp_ptr[nlc], 0.0);
+  parallel_chunks(nlc, nt, [&](unsigned, int64_t lo, int64_t hi) {
+    std::vector<std::pair<int32_t, double>> ex;
+    for (int64_t i = lo; i < hi; ++i) {
+      const int32_t pt = corner_pt[i];
+      const int32_t o = cexp_ptr[i];
+      if (!hanging[pt]) {
+        cexp_vid[o] = vid_of_point[pt];
+        cexp_w[o] = 1.0;
+        continue;
+      }
+      ex.clear();
+      for (auto &pr : hex[hslot[pt]]) ex.push_back({vid_of_point[pr.first], pr.second});
+      std::sort(ex.begin(), ex.end(),
+                [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
+                  return a.first < b.first;
+                });
+      for (size_t j = 0; j < ex.size(); ++j) {
+        cexp_vid[o + j] = ex[j].first;
+        cexp_w[o + j] = ex[j].second;
+      }
+    }
+  });
   // transpose, stable in leaf-corner order
   inc_ptr.assign(n_vert + 1, 0);
   for (int32_t v : cexp_vid) inc_ptr[v + 1]++;
@@ -303,10 +388,28 @@ void HostTree::build_grid() {
     double vol = 1.0;
     for (int a = 0; a < d; ++a) vol *= h;
     double cint = vol / (double)nc, hs = d == 2 ? 1.0 : h;
+    // a leaf whose corners are distinct vertices (one entry each): only the
+    // (e, e) pairs meet, so the sums below reduce to these, in the same order
+    bool simple = true;
+    for (int e = 0; e < nc && simple; ++e) {
+      const int64_t i = l * nc + e;
+      simple = cexp_ptr[i + 1] - cexp_ptr[i] == 1 && cexp_w[cexp_ptr[i]] == 1.0;
+      for (int f = 0; f < e && simple; ++f) simple = cexp_vid[cexp_ptr[l * nc + f]] != cexp_vid[cexp_ptr[i]];
+    }
+    if (simple) {
+      for (int e = 0; e < nc; ++e) {
+        const int64_t i = l * nc + e;
+        const int32_t v = cexp_vid[cexp_ptr[i]];
+        ion_load[v] += cexp_w[cexp_ptr[i]] * cint;
+        if (!hanging[corner_pt[i]]) direct_cnt[v]++;
+        diag[v] += kref(d, e, e) * hs * cexp_w[cexp_ptr[i]] * cexp_w[cexp_ptr[i]];
+      }
+      continue;
+    }
     for (int e = 0; e < nc; ++e) {
       int64_t i = l * nc + e;
       for (int32_t j = cexp_ptr[i]; j < cexp_ptr[i + 1]; ++j) ion_load[cexp_vid[j]] += cexp_w[j] * cint;
-      if (cexp_ptr[i + 1] - cexp_ptr[i] == 1 && !pts[corner_pt[i]].hanging) direct_cnt[cexp_vid[cexp_ptr[i]]]++;
+      if (cexp_ptr[i + 1] - cexp_ptr[i] == 1 && !hanging[corner_pt[i]]) direct_cnt[cexp_vid[cexp_ptr[i]]]++;
       for (int f = 0; f < nc; ++f) {
         int64_t jf = l * nc + f;
         double kef = kref(d, e, f) * hs;
@@ -318,43 +421,58 @@ void HostTree::build_grid() {
   }
 }
 
+
 void HostTree::build_pidt() {
   if (uniform) {
     n_pv = 1;
     for (int a = 0; a < d; ++a) n_pv *= M;
     return;
   }
+  // every leaf corner as (level, row-major index on that level, leaf corner);
+  // owner vertices are the distinct (level, index) pairs in that order, and a
+  // corner's owner is its pair's rank.  A stable LSD radix sort by the index,
+  // then by the level, keeps equal pairs in leaf-corner order; its passes run
+  // on host threads over contiguous chunks (counts per chunk, then offsets).
   struct Rec {
-    int64_t lev, rm, lc;
+    uint64_t rm;
+    int32_t lc;
+    int32_t lev;
   };
   const int64_t nlc = n_leaves * nc;
-  std::vector<Rec> r(nlc);
-  for (int64_t l = 0; l < n_leaves; ++l) {
-    int32_t nd = leaf_node[l];
-    int lev = level[nd];
-    int64_t per = pow3(lev);
-    for (int e = 0; e < nc; ++e) {
-      int64_t rm = 0, m = 1;
-      for (int a = 0; a < d; ++a) {
-        rm += ((coords[nd * 3 + a] + ((e >> a) & 1)) % per) * m;
-        m *= per;
+  std::unique_ptr<Rec[]> r(new Rec[nlc > 0 ? nlc : 1]);
+  const unsigned nt = host_threads();
+  std::vector<uint64_t> rm_max_t(nt, 0);
+  parallel_chunks(n_leaves, nt, [&](unsigned t, int64_t lo, int64_t hi) {
+    uint64_t mx = 0;
+    for (int64_t l = lo; l < hi; ++l) {
+      const int32_t nd = leaf_node[l];
+      const int lev = level[nd];
+      const int64_t per = pow3(lev);
+      for (int e = 0; e < nc; ++e) {
+        int64_t rm = 0, m = 1;
+        for (int a = 0; a < d; ++a) {
+          int64_t c = coords[nd * 3 + a] + ((e >> a) & 1);  // below per, or per itself (periodic wrap)
+          if (c == per) c = 0;
+          rm += c * m;
+          m *= per;
+        }
+        r[l * nc + e] = {(uint64_t)rm, (int32_t)(l * nc + e), lev};
+        mx = std::max(mx, (uint64_t)rm);
       }
-      r[l * nc + e] = {lev, rm, l * nc + e};
     }
-  }
-  std::sort(r.begin(), r.end(), [](const Rec &a, const Rec &b) {
-    if (a.lev != b.lev) return a.lev < b.lev;
-    if (a.rm != b.rm) return a.rm < b.rm;
-    return a.lc < b.lc;
+    rm_max_t[t] = mx;
   });
+  const uint64_t rm_max = *std::max_element(rm_max_t.begin(), rm_max_t.end());
+  radix_sort(r, nlc, rm_max, [](const Rec &x) { return x.rm; });
+  radix_sort(r, nlc, 31, [](const Rec &x) { return (uint64_t)x.lev; });
   corner_pv.assign(nlc, 0);
   pv_level.clear();
   pv_j.clear();
   int64_t nv = 0;
   for (int64_t i = 0; i < nlc; ++i) {
     if (i == 0 || r[i].lev != r[i - 1].lev || r[i].rm != r[i - 1].rm) {
-      pv_level.push_back((int32_t)r[i].lev);
-      int64_t per = pow3((int)r[i].lev), rm = r[i].rm;
+      pv_level.push_back(r[i].lev);
+      int64_t per = pow3(r[i].lev), rm = (int64_t)r[i].rm;
       for (int a = 0; a < d; ++a) { pv_j.push_back(rm % per); rm /= per; }
       ++nv;
     }
