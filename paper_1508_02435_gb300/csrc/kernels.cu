@@ -523,6 +523,14 @@ __global__ void k_push32(DevTree t, Push32Args a) {
         float w = shape<float>(o, e, d);
         for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * a.E[ax * nv + vid[e]];
       }
+    } else if (a.Ec) {  // the corner values, expanded once per field
+      const float4 *ec = a.Ec + (int64_t)L * nc;
+      for (int e = 0; e < nc; ++e) {
+        float w = shape<float>(o, e, d);
+        const float4 q = ec[e];
+        const float qv[3] = {q.x, q.y, q.z};
+        for (int ax = 0; ax < d; ++ax) E[ax] = E[ax] + w * qv[ax];
+      }
     } else {
       for (int e = 0; e < nc; ++e) {
         float w = shape<float>(o, e, d);
@@ -1101,6 +1109,26 @@ void launch_efield(const DevTree &t, bool split, const void *V, void *E, cudaStr
 
 void launch_push64(const DevTree &t, const Push64Args &a, cudaStream_t s) {
   { COUNT(1); k_push64<<<grid_for(a.n, bsz(t.block_push)), bsz(t.block_push), 0, s>>>(t, a); }
+}
+
+// Field at every leaf corner: the same expansion sums the push would form
+// per particle (corner_value), once per leaf corner.
+__global__ void k_corner_field32(DevTree t, const float *__restrict__ E, float4 *__restrict__ Ec) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= t.n_leaves * t.nc) return;
+  const int32_t L = (int32_t)(i / t.nc);
+  const int e = (int)(i - (int64_t)L * t.nc);
+  int lev;
+  int32_t c[3] = {0, 0, 0};
+  leaf_info(t, L, &lev, c);
+  float q[3] = {0.f, 0.f, 0.f};
+  for (int ax = 0; ax < t.d; ++ax) q[ax] = corner_value(t, L, c, e, E + ax * t.n_vert);
+  Ec[i] = make_float4(q[0], q[1], q[2], 0.f);
+}
+
+void launch_corner_field32(const DevTree &t, const float *E, float4 *Ec, cudaStream_t s) {
+  const int64_t m = t.n_leaves * t.nc;
+  { COUNT(1); k_corner_field32<<<grid_for(m, 256), 256, 0, s>>>(t, E, Ec); }
 }
 
 void launch_push32(const DevTree &t, const Push32Args &a, cudaStream_t s) {

@@ -30,6 +30,7 @@ struct Push32Args {
   float *to, *tv;
   int32_t *tleaf, *keyn;
   const float *E;
+  const float4 *Ec;             // field at every leaf corner [leaf][corner] (adaptive trees), or NULL
   float qmdt;
   double dt;
   float sl[19];                 // RN32(dt * 3^level) per level
@@ -159,6 +160,9 @@ void launch_solve(const DevTree &t, bool split, const void *Q, const double *tot
 void launch_efield(const DevTree &t, bool split, const void *V, void *E, cudaStream_t s);
 void launch_push64(const DevTree &t, const Push64Args &a, cudaStream_t s);
 void launch_push32(const DevTree &t, const Push32Args &a, cudaStream_t s);
+// Field at every leaf corner, the corner expansion applied once per field:
+// Ec[L nc + e] = (E_x, E_y, E_z, 0) at corner e of leaf L (adaptive trees).
+void launch_corner_field32(const DevTree &t, const float *E, float4 *Ec, cudaStream_t s);
 void launch_exclusive_scan(const int32_t *in, int64_t n, int32_t *out, int32_t *tile_sums, int32_t *total,
                            cudaStream_t s);
 void launch_rebin(const RebinArgs &r, cudaStream_t s);

@@ -55,6 +55,8 @@ struct pic_s {
   void *part = nullptr, *Q = nullptr, *b = nullptr, *V = nullptr, *Vtmp = nullptr, *E = nullptr;
   double *block_sum = nullptr, *total = nullptr, *resid2 = nullptr;
   void *Ep = nullptr;  // d * n scratch (gather at the particles, FP64 staging)
+  float4 *ecorner = nullptr;  // split, adaptive: field at every leaf corner
+  bool ecorner_valid = false; // ecorner holds the corners of the current E
 
   int64_t step = 0;
   std::string last_error;
@@ -369,6 +371,9 @@ int alloc_state(pic_t h) {
   // FP64 staging: particle arrays (d * n) and widened vertex fields (d * n_vert)
   if ((rc = dalloc(h, sb, &p, sizeof(double) * d * std::max(n, nv)))) return rc;
   h->Ep = p;
+  h->ecorner = nullptr;
+  h->ecorner_valid = false;
+  if (h->split && !h->dt.uniform && (rc = dalloc(h, sb, &h->ecorner, nl * h->dt.nc))) return rc;
   cudaStream_t s = h->stream;
   CK(cudaMemsetAsync(h->V, 0, fs * nv, s));
   CK(cudaMemsetAsync(h->E, 0, fs * nv * d, s));
@@ -660,6 +665,7 @@ int deposit(pic_t h) {
 int field(pic_t h, pic_solve_fn hook, void *user) {
   PhaseScope ps(h, PIC_PHASE_SOLVE);
   cudaStream_t s = h->stream;
+  h->ecorner_valid = false;  // E changes below
   if (hook) {
     int r = hook(user, h->Q, h->E, h->dt.n_vert, h->split ? PIC_FP32_SPLIT : PIC_FP64, (void *)s);
     if (r != 0) return fail(h, PIC_EHOOK, "field-solve hook returned " + std::to_string(r));
@@ -693,6 +699,13 @@ int push_and_rebin(pic_t h, double dt) {
     a.tleaf = h->leaf[1];
     a.keyn = h->key[1];
     a.E = (const float *)h->E;
+    if (h->ecorner) {
+      if (!h->ecorner_valid) {
+        launch_corner_field32(h->dt, (const float *)h->E, h->ecorner, s);
+        h->ecorner_valid = true;
+      }
+      a.Ec = h->ecorner;
+    }
     a.qmdt = (float)(h->cfg.qm * dt);
     a.dt = dt;
     for (int l = 0; l <= 18; ++l) a.sl[l] = (float)(dt * (double)pow3(l));
