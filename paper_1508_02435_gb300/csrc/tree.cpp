@@ -226,11 +226,25 @@ void HostTree::build_grid() {
   uint64_t key_max = 1;
   for (int a = 0; a < d; ++a) key_max *= (uint64_t)M;
   radix_sort(kc, nlc, key_max, [](const KC &x) { return x.key; });
-  std::vector<int64_t> pkey;
   std::vector<int32_t> corner_pt(nlc);
-  for (int64_t i = 0; i < nlc; ++i) {
-    if (i == 0 || kc[i].key != kc[i - 1].key) pkey.push_back((int64_t)kc[i].key);
-    corner_pt[kc[i].lc] = (int32_t)(pkey.size() - 1);
+  std::vector<int64_t> pkey;
+  {
+    // ranks of the distinct keys: new keys counted per chunk, then offsets
+    std::vector<int64_t> first(nt + 1, 0);
+    parallel_chunks(nlc, nt, [&](unsigned t, int64_t lo, int64_t hi) {
+      int64_t c = 0;
+      for (int64_t i = lo; i < hi; ++i) c += (i == 0 || kc[i].key != kc[i - 1].key);
+      first[t + 1] = c;
+    });
+    for (unsigned t = 0; t < nt; ++t) first[t + 1] += first[t];
+    pkey.assign(first[nt], 0);
+    parallel_chunks(nlc, nt, [&](unsigned t, int64_t lo, int64_t hi) {
+      int64_t r = first[t] - 1;
+      for (int64_t i = lo; i < hi; ++i) {
+        if (i == 0 || kc[i].key != kc[i - 1].key) pkey[++r] = (int64_t)kc[i].key;
+        corner_pt[kc[i].lc] = (int32_t)r;
+      }
+    });
   }
   kc.reset();
   const int64_t np = (int64_t)pkey.size();
@@ -364,61 +378,67 @@ void HostTree::build_grid() {
       }
     }
   });
-  // transpose, stable in leaf-corner order
+  // transpose, stable in leaf-corner order (stable radix sort by vertex)
+  const int64_t nnz = (int64_t)cexp_vid.size();
+  struct VE {
+    int32_t v, lc;
+    double w;
+  };
+  std::unique_ptr<VE[]> ve(new VE[nnz > 0 ? nnz : 1]);
+  parallel_chunks(nlc, nt, [&](unsigned, int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i)
+      for (int32_t j = cexp_ptr[i]; j < cexp_ptr[i + 1]; ++j) ve[j] = {cexp_vid[j], (int32_t)i, cexp_w[j]};
+  });
+  radix_sort(ve, nnz, (uint64_t)std::max<int64_t>(n_vert, 1), [](const VE &x) { return (uint64_t)x.v; });
   inc_ptr.assign(n_vert + 1, 0);
-  for (int32_t v : cexp_vid) inc_ptr[v + 1]++;
-  for (int64_t v = 0; v < n_vert; ++v) inc_ptr[v + 1] += inc_ptr[v];
-  inc_lc.assign(cexp_vid.size(), 0);
-  inc_w.assign(cexp_vid.size(), 0.0);
-  {
-    std::vector<int32_t> cur(inc_ptr.begin(), inc_ptr.end() - 1);
-    for (int64_t i = 0; i < nlc; ++i)
-      for (int32_t j = cexp_ptr[i]; j < cexp_ptr[i + 1]; ++j) {
-        int32_t v = cexp_vid[j];
-        inc_lc[cur[v]] = (int32_t)i;
-        inc_w[cur[v]] = cexp_w[j];
-        cur[v]++;
-      }
-  }
+  inc_lc.assign(nnz, 0);
+  inc_w.assign(nnz, 0.0);
+  parallel_chunks(nnz, nt, [&](unsigned, int64_t lo, int64_t hi) {
+    for (int64_t j = lo; j < hi; ++j) {
+      inc_lc[j] = ve[j].lc;
+      inc_w[j] = ve[j].w;
+      if (j == 0 || ve[j].v != ve[j - 1].v)
+        for (int32_t v = j == 0 ? 0 : ve[j - 1].v + 1; v <= ve[j].v; ++v) inc_ptr[v] = (int32_t)j;
+    }
+  });
+  for (int32_t v = nnz == 0 ? 0 : ve[nnz - 1].v + 1; v <= n_vert; ++v) inc_ptr[v] = (int32_t)nnz;
+  ve.reset();
+  // per vertex: the ion load, the number of corners that are the vertex
+  // itself, and the diagonal of the stiffness matrix -- summed over the
+  // vertex's incident leaf corners in leaf-corner order, pairs of corners of
+  // one leaf in (e, f) order: the order of a loop over leaves and corners
   ion_load.assign(n_vert, 0.0);
   diag.assign(n_vert, 0.0);
   direct_cnt.assign(n_vert, 0);
-  for (int64_t l = 0; l < n_leaves; ++l) {
-    double h = 1.0 / (double)pow3(level[leaf_node[l]]);
-    double vol = 1.0;
-    for (int a = 0; a < d; ++a) vol *= h;
-    double cint = vol / (double)nc, hs = d == 2 ? 1.0 : h;
-    // a leaf whose corners are distinct vertices (one entry each): only the
-    // (e, e) pairs meet, so the sums below reduce to these, in the same order
-    bool simple = true;
-    for (int e = 0; e < nc && simple; ++e) {
-      const int64_t i = l * nc + e;
-      simple = cexp_ptr[i + 1] - cexp_ptr[i] == 1 && cexp_w[cexp_ptr[i]] == 1.0;
-      for (int f = 0; f < e && simple; ++f) simple = cexp_vid[cexp_ptr[l * nc + f]] != cexp_vid[cexp_ptr[i]];
-    }
-    if (simple) {
-      for (int e = 0; e < nc; ++e) {
-        const int64_t i = l * nc + e;
-        const int32_t v = cexp_vid[cexp_ptr[i]];
-        ion_load[v] += cexp_w[cexp_ptr[i]] * cint;
-        if (!hanging[corner_pt[i]]) direct_cnt[v]++;
-        diag[v] += kref(d, e, e) * hs * cexp_w[cexp_ptr[i]] * cexp_w[cexp_ptr[i]];
+  parallel_chunks(n_vert, nt, [&](unsigned, int64_t lo, int64_t hi) {
+    for (int64_t v = lo; v < hi; ++v) {
+      double ion = 0.0, dg = 0.0;
+      int32_t dc = 0;
+      for (int32_t j = inc_ptr[v]; j < inc_ptr[v + 1];) {
+        const int64_t leaf = inc_lc[j] / nc;
+        int32_t k = j;
+        while (k < inc_ptr[v + 1] && inc_lc[k] / nc == leaf) ++k;  // this leaf's corners at v
+        const double h = 1.0 / (double)pow3(level[leaf_node[leaf]]);
+        double vol = 1.0;
+        for (int a = 0; a < d; ++a) vol *= h;
+        const double cint = vol / (double)nc, hs = d == 2 ? 1.0 : h;
+        for (int32_t a1 = j; a1 < k; ++a1) {
+          const int64_t i = inc_lc[a1];
+          ion += inc_w[a1] * cint;
+          if (cexp_ptr[i + 1] - cexp_ptr[i] == 1 && !hanging[corner_pt[i]]) ++dc;
+          const int e = (int)(i % nc);
+          for (int32_t a2 = j; a2 < k; ++a2) {
+            const int f = (int)(inc_lc[a2] % nc);
+            dg += kref(d, e, f) * hs * inc_w[a1] * inc_w[a2];
+          }
+        }
+        j = k;
       }
-      continue;
+      ion_load[v] = ion;
+      diag[v] = dg;
+      direct_cnt[v] = dc;
     }
-    for (int e = 0; e < nc; ++e) {
-      int64_t i = l * nc + e;
-      for (int32_t j = cexp_ptr[i]; j < cexp_ptr[i + 1]; ++j) ion_load[cexp_vid[j]] += cexp_w[j] * cint;
-      if (cexp_ptr[i + 1] - cexp_ptr[i] == 1 && !hanging[corner_pt[i]]) direct_cnt[cexp_vid[cexp_ptr[i]]]++;
-      for (int f = 0; f < nc; ++f) {
-        int64_t jf = l * nc + f;
-        double kef = kref(d, e, f) * hs;
-        for (int32_t a1 = cexp_ptr[i]; a1 < cexp_ptr[i + 1]; ++a1)
-          for (int32_t a2 = cexp_ptr[jf]; a2 < cexp_ptr[jf + 1]; ++a2)
-            if (cexp_vid[a1] == cexp_vid[a2]) diag[cexp_vid[a1]] += kef * cexp_w[a1] * cexp_w[a2];
-      }
-    }
-  }
+  });
 }
 
 
