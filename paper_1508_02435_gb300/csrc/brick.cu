@@ -95,7 +95,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long l
 }
 constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at the maximum SM clock
 constexpr int kErrTimeout = 8;                   // error bit: a bounded device wait gave up
-constexpr int kErrCode = 16;                     // error bit: a staged leaf code outside its brick
+constexpr int kErrCode = 16;                     // error bit: a staged leaf code outside its unit, or counts that disagree
 
 __device__ __forceinline__ int dir_delta(int dir, int a) {
   return a == 0 ? dir % 3 - 1 : (a == 1 ? (dir / 3) % 3 - 1 : dir / 9 - 1);
