@@ -147,8 +147,6 @@ int upload(pic_t h, std::vector<DevBuf> &bufs, const T **out, const std::vector<
   return PIC_OK;
 }
 
-int64_t n_keys_of(const HostTree &t, int scheme) { return scheme == PIC_PIT ? t.n_leaves : t.n_pv * t.nc; }
-
 // Tabulate the trees of all instances on the host and upload the device view
 // (leaves, vertices and keys concatenated instance by instance).  The previous
 // device buffers are handed back in *old (freed by the caller) so particles
