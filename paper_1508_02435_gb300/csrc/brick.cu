@@ -727,7 +727,8 @@ size_t pull_st_smem() {
 }
 
 // Sorts the m <= N arrival indices mp[0..m) of one leaf by their keys
-// (distinct) with a bitonic network over (key, index) pairs in registers.
+// (distinct) with Batcher's odd-even merge network (5, 19 and 63 comparators
+// for N = 4, 8, 16) over (key, index) pairs in registers.
 template <int N>
 __device__ __forceinline__ void sort_leaf_net(uint16_t *mp, int m, const uint32_t *key) {
   uint32_t k[N], v[N];
@@ -737,22 +738,22 @@ __device__ __forceinline__ void sort_leaf_net(uint16_t *mp, int m, const uint32_
     k[t] = t < m ? key[v[t]] : 0xffffffffu;
   }
 #pragma unroll
-  for (int kk = 2; kk <= N; kk <<= 1)
+  for (int p = 1; p < N; p <<= 1)
 #pragma unroll
-    for (int j = kk >> 1; j > 0; j >>= 1)
+    for (int c = p; c >= 1; c >>= 1)
 #pragma unroll
-      for (int t = 0; t < N; ++t) {
-        const int u = t ^ j;
-        if (u > t) {
-          const bool up = (t & kk) == 0;
-          const bool sw = up ? k[t] > k[u] : k[t] < k[u];
-          const uint32_t tk = k[t], tv = v[t];
-          k[t] = sw ? k[u] : tk;
-          v[t] = sw ? v[u] : tv;
-          k[u] = sw ? tk : k[u];
-          v[u] = sw ? tv : v[u];
-        }
-      }
+      for (int j = c % p; j + c < N; j += 2 * c)
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+          if (i < c && i < N - j - c && (i + j) / (2 * p) == (i + j + c) / (2 * p)) {
+            const int x = i + j, y = i + j + c;
+            const bool sw = k[x] > k[y];
+            const uint32_t tk = k[x], tv = v[x];
+            k[x] = sw ? k[y] : tk;
+            v[x] = sw ? v[y] : tv;
+            k[y] = sw ? tk : k[y];
+            v[y] = sw ? tv : v[y];
+          }
 #pragma unroll
   for (int t = 0; t < N; ++t)
     if (t < m) mp[t] = (uint16_t)v[t];
