@@ -290,6 +290,29 @@ PIC_API int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax);
 PIC_API int pic_bucket_noalloc(const int32_t *keys, int64_t n, int64_t n_keys, int32_t *start, int32_t *perm,
                                void *stream);
 
+/* Host-only tabulation of a spacetree given as level-order refinement flags
+ * (Section 4: the tree, its d-linear finite-element grid with hanging-vertex
+ * constraints, and the PIDT owner vertices), without a handle and without
+ * any device work, so it can run where there is no GPU.  Call once with
+ * every array NULL to learn the sizes, then again with caller-owned host
+ * arrays of those sizes; any array may be NULL.
+ *   vertex_pos[d][n_vertices]   non-hanging vertices in units of 3^-depth
+ *   pidt_level[n_pidt_vertices], pidt_j[n_pidt_vertices][d]  PIDT owners
+ * and, for trees that are not uniform (sizes->uniform == 0; uniform trees
+ * use closed forms and leave these untouched):
+ *   ion_load[n_vertices], diag[n_vertices]  load of a unit density and the
+ *                                           stiffness diagonal per vertex
+ *   cexp_ptr[n_leaves 2^d + 1], cexp_vid[n_corner_entries],
+ *   cexp_w[n_corner_entries]    every leaf corner expanded onto vertices
+ * Returns PIC_EINVAL for a NULL sizes pointer or a malformed tree. */
+typedef struct {
+  int32_t d, depth, uniform, reserved;
+  int64_t n_leaves, n_vertices, n_corner_entries, n_pidt_vertices;
+} pic_tree_sizes_t;
+PIC_API int pic_tree_tabulate(int32_t d, const uint8_t *flags, int64_t n_flags, pic_tree_sizes_t *sizes,
+                              int64_t *vertex_pos, double *ion_load, double *diag, int32_t *cexp_ptr,
+                              int32_t *cexp_vid, double *cexp_w, int32_t *pidt_level, int64_t *pidt_j);
+
 /* Stream-like particle update, the calibration ceiling of the paper's
  * memory-throughput experiment (Section 6, "Memory throughput"): `steps`
  * passes over the particles, each advancing every position by one explicit

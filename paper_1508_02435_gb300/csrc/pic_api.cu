@@ -1373,6 +1373,51 @@ int pic_vertex_table(pic_t h, int64_t *pos) {
   return PIC_OK;
 }
 
+int pic_tree_tabulate(int32_t d, const uint8_t *flags, int64_t n_flags, pic_tree_sizes_t *sizes,
+                      int64_t *vertex_pos, double *ion_load, double *diag, int32_t *cexp_ptr, int32_t *cexp_vid,
+                      double *cexp_w, int32_t *pidt_level, int64_t *pidt_j) {
+  if (!sizes || !flags || n_flags < 1) return PIC_EINVAL;
+  HostTree t;
+  std::string err;
+  if (t.build(d, n_flags, flags, &err)) return PIC_EINVAL;
+  t.build_grid();
+  t.build_pidt();
+  sizes->d = t.d;
+  sizes->depth = t.depth;
+  sizes->uniform = t.uniform ? 1 : 0;
+  sizes->reserved = 0;
+  sizes->n_leaves = t.n_leaves;
+  sizes->n_vertices = t.n_vert;
+  sizes->n_corner_entries = t.uniform ? 0 : (int64_t)t.cexp_vid.size();
+  sizes->n_pidt_vertices = t.n_pv;
+  const int64_t nv = t.n_vert;
+  if (vertex_pos)
+    for (int64_t v = 0; v < nv; ++v) {
+      int64_t k = t.uniform ? v : t.vert_key[v];
+      for (int a = 0; a < t.d; ++a) {
+        vertex_pos[a * nv + v] = k % t.M;
+        k /= t.M;
+      }
+    }
+  for (int64_t v = 0; v < t.n_pv; ++v) {
+    int64_t k = v;
+    if (pidt_level) pidt_level[v] = t.uniform ? t.depth : t.pv_level[v];
+    if (pidt_j)
+      for (int a = 0; a < t.d; ++a) {
+        pidt_j[v * t.d + a] = t.uniform ? k % t.M : t.pv_j[v * t.d + a];
+        k /= t.M;
+      }
+  }
+  if (!t.uniform) {
+    if (ion_load) std::copy(t.ion_load.begin(), t.ion_load.end(), ion_load);
+    if (diag) std::copy(t.diag.begin(), t.diag.end(), diag);
+    if (cexp_ptr) std::copy(t.cexp_ptr.begin(), t.cexp_ptr.end(), cexp_ptr);
+    if (cexp_vid) std::copy(t.cexp_vid.begin(), t.cexp_vid.end(), cexp_vid);
+    if (cexp_w) std::copy(t.cexp_w.begin(), t.cexp_w.end(), cexp_w);
+  }
+  return PIC_OK;
+}
+
 int pic_pidt_table(pic_t h, int32_t *level, int64_t *j) {
   if (check_handle(h)) return PIC_EINVAL;
   int64_t base = 0;

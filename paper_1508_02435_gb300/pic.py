@@ -89,6 +89,7 @@ SIGNATURES = [
     ("pic_bucket_noalloc", C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_stream_step", C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int32,
                                   C.c_void_p]),
+    ("pic_tree_tabulate", C.c_int, [C.c_int32, C.c_void_p, C.c_int64, C.c_void_p] + [C.c_void_p] * 8),
     ("pic_graph_launch", C.c_int, [C.c_void_p, C.c_int32]),
     ("pic_autotune", C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p]),
     ("pic_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -142,6 +143,40 @@ def _ptr(a):
 
 
 NOALLOC_MAX_KEYS = 1 << 20
+
+
+class TreeSizes(C.Structure):
+    _fields_ = [("d", C.c_int32), ("depth", C.c_int32), ("uniform", C.c_int32), ("reserved", C.c_int32),
+                ("n_leaves", C.c_int64), ("n_vertices", C.c_int64), ("n_corner_entries", C.c_int64),
+                ("n_pidt_vertices", C.c_int64)]
+
+
+def tree_tables(d: int, flags) -> dict:
+    """Host tabulation of a tree (pic_tree_tabulate; no GPU needed): vertex
+    positions (d, n_vertices), PIDT owner levels and coordinates, and for
+    non-uniform trees the vertex ion loads and stiffness diagonals and the
+    leaf-corner expansions (ptr, vid, w)."""
+    lib = load()
+    fl = np.ascontiguousarray(flags, dtype=np.uint8)
+    sz = TreeSizes()
+    p = lambda a: C.c_void_p(a.ctypes.data) if a is not None else None  # noqa: E731
+    rc = lib.pic_tree_tabulate(d, p(fl), len(fl), C.byref(sz), *([None] * 8))
+    if rc != 0:
+        raise PicError(rc, lib.pic_strerror(rc).decode())
+    nv, npv, nlc = sz.n_vertices, sz.n_pidt_vertices, sz.n_leaves * (1 << d)
+    out = {"uniform": bool(sz.uniform), "depth": int(sz.depth), "n_leaves": int(sz.n_leaves),
+           "vertex_pos": np.zeros((d, nv), np.int64), "pidt_level": np.zeros(npv, np.int32),
+           "pidt_j": np.zeros((npv, d), np.int64)}
+    adaptive = not sz.uniform
+    if adaptive:
+        out.update(ion_load=np.zeros(nv), diag=np.zeros(nv), cexp_ptr=np.zeros(nlc + 1, np.int32),
+                   cexp_vid=np.zeros(sz.n_corner_entries, np.int32), cexp_w=np.zeros(sz.n_corner_entries))
+    g = lambda k: p(out[k]) if k in out else None  # noqa: E731
+    rc = lib.pic_tree_tabulate(d, p(fl), len(fl), C.byref(sz), g("vertex_pos"), g("ion_load"), g("diag"),
+                               g("cexp_ptr"), g("cexp_vid"), g("cexp_w"), g("pidt_level"), g("pidt_j"))
+    if rc != 0:
+        raise PicError(rc, lib.pic_strerror(rc).decode())
+    return out
 
 
 def stream_step(x, v, dt: float, steps: int = 1, stream=None):
