@@ -350,9 +350,22 @@ void HostTree::build_grid() {
   n_vert = (int64_t)vert_key.size();
   // leaf corner -> (vertex, weight), ascending vertex
   cexp_ptr.assign(nlc + 1, 0);
-  for (int64_t i = 0; i < nlc; ++i) {
-    const int32_t pt = corner_pt[i];
-    cexp_ptr[i + 1] = cexp_ptr[i] + (hanging[pt] ? (int32_t)hex[hslot[pt]].size() : 1);
+  {
+    // entries per corner, offsets by chunk sums
+    std::vector<int64_t> part(nt + 1, 0);
+    parallel_chunks(nlc, nt, [&](unsigned t, int64_t lo, int64_t hi) {
+      int64_t run = 0;
+      for (int64_t i = lo; i < hi; ++i) {
+        const int32_t pt = corner_pt[i];
+        run += hanging[pt] ? (int64_t)hex[hslot[pt]].size() : 1;
+        cexp_ptr[i + 1] = (int32_t)run;
+      }
+      part[t + 1] = run;
+    });
+    for (unsigned t = 0; t < nt; ++t) part[t + 1] += part[t];
+    parallel_chunks(nlc, nt, [&](unsigned t, int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi; ++i) cexp_ptr[i + 1] += (int32_t)part[t];
+    });
   }
   cexp_vid.assign(cexp_ptr[nlc], 0);
   cexp_w.assign(cexp_ptr[nlc], 0.0);
