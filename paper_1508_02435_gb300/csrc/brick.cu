@@ -9,18 +9,20 @@
 //                       particle rows land in shared memory by bulk copies,
 //                       the brick's vertex field is staged, every particle is
 //                       gathered, kicked, drifted and re-located (integer
-//                       arithmetic, split rule) and appended to the staging
-//                       area of its destination brick (warp-aggregated slot),
-//                       with its canonical key: moved bit, storage index.
-//   K2 k_brick_pull_st  one CTA per destination brick: its staging area lands
-//                       by bulk copies; leaf counts, scan, slots, and a per-leaf
-//                       sort by key restore the canonical order -- stayers
-//                       first, then movers, each in storage order -- before the
-//                       coalesced writes of the new bucket order and the
-//                       leaf-corner deposit partials.
+//                       arithmetic, split rule); each warp then reserves one
+//                       run per destination unit (half brick) it sends to and
+//                       appends its particles there, with their canonical
+//                       key: moved bit, storage index.
+//   K2 k_brick_pull_st  two CTAs per SM, one per destination unit: its
+//                       staging area lands by bulk copies; leaf counts, scan,
+//                       slots, and a per-leaf sort by key restore the canonical
+//                       order -- stayers first, then movers, each in storage
+//                       order -- before the coalesced writes of the new bucket
+//                       order and the leaf-corner deposit partials.
 //
-// Bricks over the shared-memory capacity take global-memory kernels with the
-// same arithmetic.  The result is bit-identical to the generic path.
+// Bricks over the shared-memory capacity (K1) and units over their staging
+// capacity (K2) take global-memory kernels with the same arithmetic.  The
+// result is bit-identical to the generic path.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -337,9 +339,9 @@ __device__ __forceinline__ void stage_put(const BrickStage &st, int32_t dest, in
 }
 
 // Appends the pushed particles of one warp to the staging areas of their
-// destination bricks: one global atomic per distinct destination of the warp,
-// lanes in lane order; arrivals beyond the area's capacity go to the overflow
-// list.  Inactive lanes pass dest < 0.
+// destination units (the global-memory K1): one global atomic per distinct
+// destination of the warp, lanes in lane order; arrivals beyond the area's
+// capacity go to the overflow list.  Inactive lanes pass dest < 0.
 template <int D>
 __device__ __forceinline__ void stage_append(const BrickStage &st, int32_t dest, const float *on, const float *vn,
                                              uint16_t code, uint32_t key, int32_t id, bool with_id,
