@@ -1,6 +1,6 @@
-"""The multi-rank logic of the bench on CPU: two gloo ranks (one per GPU on
-a GPU machine, replicas with no data-path collective) must agree on the job's
-time — the slowest rank's — and on the whole-job rate."""
+"""The multi-rank logic of the bench on CPU: two gloo ranks (one per GPU in a
+multi-GPU run, replicas with no data-path collective) must agree on the
+job's time — the slowest rank's — and on the whole-job rate."""
 from __future__ import annotations
 
 import os
