@@ -473,6 +473,9 @@ int setup_brick(pic_t h) {
   st = BrickStage{};
   st.cap = brick_stage_cap(n, nu);
   st.row = nu * st.cap + 16;
+  // a tree with many more bricks than particles would spend more memory on
+  // empty staging areas than on the particles: the generic path serves it
+  if (nu * st.cap > 16 * n + (int64_t(1) << 24)) return PIC_OK;
   if ((rc = dalloc(h, bb, &st.o, st.row * t.d))) return rc;
   if ((rc = dalloc(h, bb, &st.v, st.row * t.d))) return rc;
   if ((rc = dalloc(h, bb, &st.code, st.row))) return rc;
