@@ -2,9 +2,9 @@
 #include "tree.hpp"
 
 #include <algorithm>
+#include <cstdlib>
 #include <memory>
 #include <thread>
-#include <unordered_map>
 
 namespace pic {
 
@@ -134,7 +134,13 @@ void parallel_chunks(int64_t n, unsigned nt, F fn) {
   for (auto &x : th) x.join();
 }
 
+// Host threads for the tabulation: PIC_HOST_THREADS if set (1..64), else the
+// hardware concurrency (at most 32).  The tables do not depend on it.
 unsigned host_threads() {
+  if (const char *env = std::getenv("PIC_HOST_THREADS")) {
+    const long v = std::strtol(env, nullptr, 10);
+    if (v >= 1 && v <= 64) return (unsigned)v;
+  }
   const unsigned hw = std::thread::hardware_concurrency();
   return std::max(1u, std::min(hw == 0 ? 1u : hw, 32u));
 }

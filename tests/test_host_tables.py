@@ -55,3 +55,18 @@ def test_host_tables_reject_malformed_tree():
     _lib_or_skip()
     with pytest.raises(pic.PicError):
         pic.tree_tables(3, np.array([1, 0, 0], np.uint8))  # a refined root without 27 children
+
+
+@pytest.mark.parametrize("d,flags_fn", [TREES[2], TREES[5]])
+def test_host_tables_do_not_depend_on_thread_count(d, flags_fn, monkeypatch):
+    """The threaded tabulation (radix sorts, chunked passes) gives the same
+    tables with one host thread as with several."""
+    _lib_or_skip()
+    flags = flags_fn()
+    monkeypatch.setenv("PIC_HOST_THREADS", "1")
+    one = pic.tree_tables(d, flags)
+    monkeypatch.setenv("PIC_HOST_THREADS", "7")
+    seven = pic.tree_tables(d, flags)
+    assert one.keys() == seven.keys()
+    for k in one:
+        assert np.array_equal(np.asarray(one[k]), np.asarray(seven[k])), k
