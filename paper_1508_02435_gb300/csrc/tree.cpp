@@ -190,17 +190,6 @@ void HostTree::build_grid() {
     diag.assign(1, (double)nc * kref(d, 0, 0) * hs);
     return;
   }
-  const int64_t qs = 2 * pow3(kMaxLevel - depth);
-  auto leaf_at = [&](const int64_t Q[3]) {
-    int32_t nd = 0;
-    while (child0[nd] >= 0) {
-      int64_t step = 2 * pow3(kMaxLevel - (level[nd] + 1));
-      int digit = 0, mul = 1;
-      for (int a = 0; a < d; ++a) { digit += (int)((Q[a] / step) % 3) * mul; mul *= 3; }
-      nd = child0[nd] + digit;
-    }
-    return nd;
-  };
   auto key_of = [&](const int64_t p[3]) {
     int64_t k = 0, m = 1;
     for (int a = 0; a < d; ++a) { k += p[a] * m; m *= M; }
@@ -267,14 +256,28 @@ void HostTree::build_grid() {
     for (int64_t id = lo; id < hi; ++id) {
       int64_t p[3] = {0, 0, 0}, k = pkey[id];
       for (int a = 0; a < d; ++a) { p[a] = k % M; k /= M; }
+      // the leaf holding the finest cell just below (corner bit 0) or at
+      // (bit 1) the point on every axis, by the base-3 digits of those cells
+      // (most significant first): the descent of the quantised positions
+      // p qs - 1 and p qs without their divisions
+      uint8_t dig[2][3][kMaxLevel];
+      for (int a = 0; a < d; ++a)
+        for (int b = 0; b < 2; ++b) {
+          int64_t c = b ? p[a] : (p[a] == 0 ? M - 1 : p[a] - 1);
+          for (int l = depth - 1; l >= 0; --l) {
+            dig[b][a][l] = (uint8_t)(c % 3);
+            c /= 3;
+          }
+        }
       int32_t best = -1;
       for (int e = 0; e < nc; ++e) {
-        int64_t Q[3] = {0, 0, 0};
-        for (int a = 0; a < d; ++a) {
-          int64_t q = p[a] * qs - (((e >> a) & 1) ? 0 : 1);
-          Q[a] = q < 0 ? q + (int64_t)kQSteps : q;
+        int32_t nd = 0;
+        while (child0[nd] >= 0) {
+          const int lv = level[nd];
+          int digit = 0, mul = 1;
+          for (int a = 0; a < d; ++a) { digit += dig[(e >> a) & 1][a][lv] * mul; mul *= 3; }
+          nd = child0[nd] + digit;
         }
-        int32_t nd = leaf_at(Q);
         if (best < 0 || level[nd] < level[best]) best = nd;
       }
       const int64_t s = pow3(depth - level[best]);
