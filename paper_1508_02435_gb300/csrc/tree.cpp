@@ -349,13 +349,25 @@ void HostTree::build_grid() {
   for (int64_t id = 0; id < np; ++id)
     if (hanging[id]) resolve((int32_t)id);
   // vertex ids: the non-hanging points in key order
-  vert_key.clear();
   std::vector<int32_t> vid_of_point(np, -1);
-  for (int64_t id = 0; id < np; ++id)
-    if (!hanging[id]) {
-      vid_of_point[id] = (int32_t)vert_key.size();
-      vert_key.push_back(pkey[id]);
-    }
+  {
+    std::vector<int64_t> first(nt + 1, 0);  // non-hanging points per chunk, then offsets
+    parallel_chunks(np, nt, [&](unsigned t, int64_t lo, int64_t hi) {
+      int64_t c = 0;
+      for (int64_t id = lo; id < hi; ++id) c += !hanging[id];
+      first[t + 1] = c;
+    });
+    for (unsigned t = 0; t < nt; ++t) first[t + 1] += first[t];
+    vert_key.assign(first[nt], 0);
+    parallel_chunks(np, nt, [&](unsigned t, int64_t lo, int64_t hi) {
+      int64_t r = first[t];
+      for (int64_t id = lo; id < hi; ++id)
+        if (!hanging[id]) {
+          vid_of_point[id] = (int32_t)r;
+          vert_key[r++] = pkey[id];
+        }
+    });
+  }
   n_vert = (int64_t)vert_key.size();
   // leaf corner -> (vertex, weight), ascending vertex
   cexp_ptr.assign(nlc + 1, 0);
