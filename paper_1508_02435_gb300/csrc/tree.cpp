@@ -519,19 +519,31 @@ void HostTree::build_pidt() {
   const uint64_t rm_max = *std::max_element(rm_max_t.begin(), rm_max_t.end());
   radix_sort(r, nlc, rm_max, [](const Rec &x) { return x.rm; });
   radix_sort(r, nlc, 31, [](const Rec &x) { return (uint64_t)x.lev; });
+  // distinct pairs in order: new pairs counted per chunk, then offsets
+  auto is_new = [&](int64_t i) { return i == 0 || r[i].lev != r[i - 1].lev || r[i].rm != r[i - 1].rm; };
+  std::vector<int64_t> first(nt + 1, 0);
+  parallel_chunks(nlc, nt, [&](unsigned t, int64_t lo, int64_t hi) {
+    int64_t c = 0;
+    for (int64_t i = lo; i < hi; ++i) c += is_new(i);
+    first[t + 1] = c;
+  });
+  for (unsigned t = 0; t < nt; ++t) first[t + 1] += first[t];
+  const int64_t nv = first[nt];
   corner_pv.assign(nlc, 0);
-  pv_level.clear();
-  pv_j.clear();
-  int64_t nv = 0;
-  for (int64_t i = 0; i < nlc; ++i) {
-    if (i == 0 || r[i].lev != r[i - 1].lev || r[i].rm != r[i - 1].rm) {
-      pv_level.push_back(r[i].lev);
-      int64_t per = pow3(r[i].lev), rm = (int64_t)r[i].rm;
-      for (int a = 0; a < d; ++a) { pv_j.push_back(rm % per); rm /= per; }
-      ++nv;
+  pv_level.assign(nv, 0);
+  pv_j.assign(nv * d, 0);
+  parallel_chunks(nlc, nt, [&](unsigned t, int64_t lo, int64_t hi) {
+    int64_t id = first[t] - 1;
+    for (int64_t i = lo; i < hi; ++i) {
+      if (is_new(i)) {
+        ++id;
+        pv_level[id] = r[i].lev;
+        int64_t per = pow3(r[i].lev), rm = (int64_t)r[i].rm;
+        for (int a = 0; a < d; ++a) { pv_j[id * d + a] = rm % per; rm /= per; }
+      }
+      corner_pv[r[i].lc] = (int32_t)id;
     }
-    corner_pv[r[i].lc] = (int32_t)(nv - 1);
-  }
+  });
   n_pv = nv;
 }
 
