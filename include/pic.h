@@ -23,7 +23,8 @@
  *     pointer it was given; inputs are copied, outputs are written before the
  *     call returns (host) or are stream-ordered on the handle's stream (device).
  *   - Every call returns PIC_OK (0) or a negative PIC_E* code; no exception or
- *     signal crosses the ABI.  pic_last_error() gives a message per handle.
+ *     signal crosses the ABI.  pic_last_error() gives a message per handle
+ *     (with NULL: the last failed pic_load of the calling thread).
  *   - Leaves are numbered in depth-first pre-order (children in digit order);
  *     finite-element vertices (non-hanging grid points) by row-major position
  *     on the finest level; PIDT owner vertices by (level, row-major index).
@@ -54,6 +55,7 @@ extern "C" {
 #define PIC_ETIMEOUT (-5)  /* a bounded device wait gave up */
 #define PIC_ECUDA (-6)     /* a CUDA runtime call failed */
 #define PIC_ESTATE (-7)    /* call not valid in the handle's state */
+#define PIC_EIO (-8)       /* checkpoint file missing, unreadable, truncated or corrupt */
 
 #define PIC_PIT 0
 #define PIC_PIDT 1
@@ -182,7 +184,6 @@ PIC_API int pic_set_tuning(pic_t h, const int32_t *tuned);
 PIC_API int pic_get_tuning(pic_t h, int32_t *tuned);
 
 /* Wait for the handle's stream; returns the sticky device error if any. */
-/* Wait for the handle's stream; returns the sticky device error if any. */
 PIC_API int pic_sync(pic_t h);
 
 /* Vertex charges Q[n_vertices] of the current positions (FP64 values, also in
@@ -248,6 +249,42 @@ PIC_API int pic_retree(pic_t h, const pic_tree_desc *tree);
 /* Level-order refinement flags of the current tree: with flags == NULL only
  * *n_nodes is written; else flags[n_nodes] (host memory). */
 PIC_API int pic_tree_flags(pic_t h, uint8_t *flags, int64_t *n_nodes);
+
+/* ---- checkpoint / resume ----------------------------------------------------
+ * The paper has no counterpart to these calls: they are library utilities.
+ * pic_save writes what the next step reads: the refinement flags of every
+ * instance, the particle state in storage order and native precision (split:
+ * leaf ids, FP32 offsets, FP32 velocities; FP64: positions, velocities), the
+ * particle ids (track_ids), the potential V (the warm start of the built-in
+ * solve), the field E, the step counter, the configuration (everything in
+ * pic_config but the stream) and the launch tuning.  Velocities are saved as
+ * they are, so a leapfrog run resumes at its half step.  Synchronous; the file
+ * is overwritten.  PIC_ESTATE if the handle holds a sticky device error,
+ * PIC_EIO if the file cannot be written.
+ *
+ * pic_load creates a new handle (*out, on `stream`) from such a file.  Steps
+ * of the loaded handle give the same bits as steps of the saved one: sort
+ * keys, bucket offsets and vertex charges are recomputed from the saved
+ * state, which stays in its saved order.  PIC_EIO: the file is missing,
+ * unreadable, not a checkpoint, of another format version, truncated, or its
+ * checksum does not match.  PIC_EINVAL: its trees are malformed or a particle
+ * value is out of range (a non-finite value, an offset or FP64 position
+ * outside [0, 1), a leaf outside the particle's instance, ids that are not a
+ * permutation of [0, n)).  Every such check runs on the host before the first
+ * device call.  On failure *out is NULL and pic_last_error(NULL) says why.
+ *
+ * File layout (little-endian; each section zero-padded to 8 bytes):
+ *   magic "PICSNAP\0", u32 version 1, u32 meta bytes, u64 checksum of all
+ *   bytes after these 24; meta: i32 d, scheme, precision, sweeps, track_ids,
+ *   path, n_inst, 0; f64 q, qm, ion, omega; i64 step, n, n_vertices;
+ *   i32 tuning[4]; per instance i64 n_flags, i64 n_particles, f64 q; then
+ *   flags u8[], leaf i32[n] (split only), pos[d][n], vel[d][n] (f32 split,
+ *   f64 otherwise), ids i32[n] (track_ids only), V[n_vertices],
+ *   E[d][n_vertices].  The checksum folds the 64-bit words w in order:
+ *   c = 0x243f6a8885a308d3 initially, then c = (c ^ w) * 0x9e3779b97f4a7c15
+ *   and c ^= c >> 29 (arithmetic mod 2^64). */
+PIC_API int pic_save(pic_t h, const char *path);
+PIC_API int pic_load(pic_t *out, const char *path, void *stream);
 
 /* Re-refine by the particles-per-cell criterion: cell C on level m is refined
  * iff m < dmin, or m < dmax and C holds more than ppc particles (Section 6

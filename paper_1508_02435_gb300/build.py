@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic.so")
-SOURCES = ["kernels.cu", "brick.cu", "pic_api.cu", "noalloc.cu", "calibrate.cu", "tree.cpp"]
+SOURCES = ["kernels.cu", "brick.cu", "pic_api.cu", "noalloc.cu", "calibrate.cu", "tree.cpp", "snapshot.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -14,6 +14,7 @@
 #include "../../include/pic.h"
 #include "dev.cuh"
 #include "launch.hpp"
+#include "snapshot.hpp"
 #include "tree.hpp"
 
 using namespace pic;
@@ -829,11 +830,18 @@ const char *pic_strerror(int code) {
     case PIC_ETIMEOUT: return "device wait timed out";
     case PIC_ECUDA: return "CUDA runtime error";
     case PIC_ESTATE: return "call not valid in this state";
+    case PIC_EIO: return "checkpoint file missing, unreadable, truncated or corrupt";
     default: return "unknown error";
   }
 }
 
-const char *pic_last_error(pic_t h) { return h ? h->last_error.c_str() : "NULL handle"; }
+// Message of the last failed handle-less call (pic_load) on this thread.
+static thread_local std::string t_last_error;
+
+const char *pic_last_error(pic_t h) {
+  if (h) return h->last_error.c_str();
+  return t_last_error.empty() ? "NULL handle" : t_last_error.c_str();
+}
 
 void pic_destroy(pic_t h) {
   if (!h) return;
@@ -1581,6 +1589,153 @@ int pic_tree_flags(pic_t h, uint8_t *flags, int64_t *n_nodes) {
     total += t.n_nodes;
   }
   if (n_nodes) *n_nodes = total;
+  return PIC_OK;
+}
+
+int pic_save(pic_t h, const char *path) {
+  if (check_handle(h) || !path) return PIC_EINVAL;
+  int rc;
+  int32_t err = 0;
+  if ((rc = read_err(h, &err))) return rc;
+  if (err) return fail(h, PIC_ESTATE, "the handle holds a sticky device error; nothing was saved");
+  SnapshotMeta m;
+  m.d = h->d;
+  m.scheme = h->scheme;
+  m.precision = h->split ? PIC_FP32_SPLIT : PIC_FP64;
+  m.sweeps = h->cfg.sweeps;
+  m.track_ids = h->cfg.track_ids ? 1 : 0;
+  m.path = h->cfg.path == PIC_PATH_GENERIC ? PIC_PATH_GENERIC : PIC_PATH_AUTO;
+  m.n_inst = (int32_t)h->hts.size();
+  m.q = h->cfg.q;
+  m.qm = h->cfg.qm;
+  m.ion = h->cfg.ion;
+  m.omega = h->cfg.omega;
+  m.step = h->step;
+  m.n = h->n;
+  m.n_vert = h->dt.n_vert;
+  if ((rc = pic_get_tuning(h, m.tuned))) return rc;
+  for (int32_t i = 0; i < m.n_inst; ++i) {
+    m.inst_flags.push_back(h->hts[i].n_nodes);
+    const int64_t end = i + 1 < m.n_inst ? h->inst[i + 1].poff : h->n;
+    m.inst_n.push_back(end - h->inst[i].poff);
+    m.inst_q.push_back(h->inst[i].q);
+  }
+  SnapshotArrays a;
+  int64_t n_nodes = 0;
+  if ((rc = pic_tree_flags(h, nullptr, &n_nodes))) return rc;
+  a.flags.resize(n_nodes);
+  if ((rc = pic_tree_flags(h, a.flags.data(), nullptr))) return rc;
+  const size_t fs = h->split ? sizeof(float) : sizeof(double);
+  const size_t n = (size_t)h->n, d = (size_t)h->d, nv = (size_t)h->dt.n_vert;
+  a.pos.resize(fs * d * n);
+  a.vel.resize(fs * d * n);
+  if (h->split) a.leaf.resize(n);
+  if ((rc = pic_get_state(h, h->split ? a.leaf.data() : nullptr, a.pos.data(), a.vel.data(), PIC_HOST))) return rc;
+  if (m.track_ids) {
+    a.ids.resize(n);
+    if ((rc = copy_out(h, a.ids.data(), h->ids[0], sizeof(int32_t) * n, PIC_HOST))) return rc;
+  }
+  a.V.resize(fs * nv);
+  a.E.resize(fs * d * nv);
+  if ((rc = copy_out(h, a.V.data(), h->V, a.V.size(), PIC_HOST)) ||
+      (rc = copy_out(h, a.E.data(), h->E, a.E.size(), PIC_HOST)))
+    return rc;
+  std::string msg;
+  if ((rc = snapshot_write(path, m, a, &msg))) return fail(h, rc, msg);
+  return PIC_OK;
+}
+
+static int load_fail(int rc, const std::string &msg) {
+  t_last_error = msg;
+  return rc;
+}
+
+int pic_load(pic_t *out, const char *path, void *stream) {
+  if (!out) return PIC_EINVAL;
+  *out = nullptr;
+  t_last_error.clear();
+  SnapshotMeta m;
+  SnapshotArrays a;
+  std::string msg;
+  int rc = snapshot_read(path, m, a, &msg);
+  if (rc) return load_fail(rc, msg);
+  const bool split = m.precision == PIC_FP32_SPLIT;
+  const int d = m.d;
+  const int64_t n = m.n;
+  // Trees, and a creation position for every particle.  The creation
+  // positions only size and order the new handle: the saved state replaces
+  // them below.  FP64: the saved positions themselves.  Split: the centre of
+  // the particle's leaf.  Velocities at creation are zero, likewise replaced.
+  std::vector<pic_tree_desc> trees(m.n_inst);
+  std::vector<pic_particles_desc> parts(m.n_inst);
+  std::vector<int64_t> leaf_off(m.n_inst + 1, 0);
+  std::vector<double> x0((size_t)d * n), v0((size_t)d * n, 0.0);
+  int64_t foff = 0, poff = 0;
+  for (int32_t i = 0; i < m.n_inst; ++i) {
+    const int64_t ni = m.inst_n[i];
+    trees[i] = {d, m.inst_flags[i], a.flags.data() + foff};
+    double *xi = x0.data() + (size_t)d * poff;
+    parts[i] = {ni, xi, v0.data() + (size_t)d * poff, PIC_HOST};
+    if (split) {
+      HostTree t;
+      std::string terr;
+      if (t.build(d, m.inst_flags[i], a.flags.data() + foff, &terr))
+        return load_fail(PIC_EINVAL, "instance " + std::to_string(i) + ": " + terr);
+      leaf_off[i + 1] = leaf_off[i] + t.n_leaves;
+      for (int64_t k = 0; k < ni; ++k) {
+        const int64_t L = a.leaf[poff + k] - leaf_off[i];
+        if (L < 0 || L >= t.n_leaves)
+          return load_fail(PIC_EINVAL, "particle " + std::to_string(poff + k) + " names a leaf outside its instance");
+        const double w = std::pow(3.0, -(double)t.leaf_level[L]);
+        for (int ax = 0; ax < d; ++ax) xi[ax * ni + k] = ((double)t.leaf_coords[L * d + ax] + 0.5) * w;
+      }
+    } else {
+      const double *x = (const double *)a.pos.data();
+      for (int ax = 0; ax < d; ++ax)
+        for (int64_t k = 0; k < ni; ++k) xi[ax * ni + k] = x[ax * n + poff + k];
+    }
+    foff += m.inst_flags[i];
+    poff += ni;
+  }
+  if (split && (rc = snapshot_check_leaves(m, a, leaf_off, &msg))) return load_fail(rc, msg);
+  pic_config cfg{};
+  cfg.scheme = m.scheme;
+  cfg.precision = m.precision;
+  cfg.q = m.q;
+  cfg.qm = m.qm;
+  cfg.ion = m.ion;
+  cfg.sweeps = m.sweeps;
+  cfg.omega = m.omega;
+  cfg.track_ids = m.track_ids;
+  cfg.stream = stream;
+  cfg.path = m.path;
+  pic_t h = nullptr;
+  rc = create_forest(&h, m.n_inst, trees.data(), parts.data(), m.inst_q.data(), &cfg);
+  std::vector<double>().swap(x0);
+  std::vector<double>().swap(v0);
+  if (rc) return load_fail(rc, "creating the handle from the checkpoint failed");
+  auto bail = [&](int code, const std::string &why) {
+    t_last_error = why.empty() ? h->last_error : why;
+    pic_destroy(h);
+    return code;
+  };
+  if (h->n != n || h->dt.n_vert != m.n_vert) return bail(PIC_EIO, "the checkpoint does not match its own tree");
+  // ids first: pic_set_state permutes them along with the particles if the
+  // saved order is not already bucket order
+  if (m.track_ids && n > 0 && (rc = copy_in(h, h->ids[0], a.ids.data(), sizeof(int32_t) * n, PIC_HOST)))
+    return bail(rc, "");
+  if (n > 0 && (rc = pic_set_state(h, split ? a.leaf.data() : nullptr, a.pos.data(), a.vel.data(), PIC_HOST)))
+    return bail(rc, "");
+  if ((rc = copy_in(h, h->V, a.V.data(), a.V.size(), PIC_HOST)) ||
+      (rc = copy_in(h, h->E, a.E.data(), a.E.size(), PIC_HOST)))
+    return bail(rc, "");
+  h->ecorner_valid = false;
+  if ((rc = apply_tuning(h, m.tuned))) return bail(rc, "");
+  h->step = m.step;
+  int32_t err = 0;
+  if ((rc = read_err(h, &err))) return bail(rc, "");
+  if (err) return bail(PIC_EINVAL, "the saved particle state is out of range for its tree");
+  *out = h;
   return PIC_OK;
 }
 

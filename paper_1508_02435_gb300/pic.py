@@ -19,7 +19,7 @@ FP64, FP32_SPLIT = 0, 1
 HOST, DEVICE = 0, 1
 
 ERRORS = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ERANGE", -4: "PIC_EHOOK",
-          -5: "PIC_ETIMEOUT", -6: "PIC_ECUDA", -7: "PIC_ESTATE"}
+          -5: "PIC_ETIMEOUT", -6: "PIC_ECUDA", -7: "PIC_ESTATE", -8: "PIC_EIO"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _lock = threading.Lock()
@@ -101,6 +101,8 @@ SIGNATURES = [
     ("pic_retree", C.c_int, [C.c_void_p, C.POINTER(TreeDesc)]),
     ("pic_adapt", C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32]),
     ("pic_tree_flags", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pic_save", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("pic_load", C.c_int, [C.POINTER(C.c_void_p), C.c_char_p, C.c_void_p]),
 ]
 
 
@@ -284,6 +286,32 @@ class Pic:
         self.precision = precision
         self._info = self.info()
         return self
+
+    @classmethod
+    def load(cls, path, stream=None) -> "Pic":
+        """A handle restored from a checkpoint file written by :meth:`save`
+        (pic_load), launching on `stream`."""
+        self = cls.__new__(cls)
+        self.lib = load()
+        st = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+        self._stream = stream
+        h = C.c_void_p()
+        rc = self.lib.pic_load(C.byref(h), os.fsencode(path), C.c_void_p(st))
+        if rc != 0:
+            raise PicError(rc, self.lib.pic_last_error(None).decode())
+        self.h = h
+        info = self.info()
+        self.d = int(info.d)
+        self.n = int(info.n_particles)
+        self.scheme = int(info.scheme)
+        self.precision = int(info.precision)
+        self._info = info
+        self._flags = self.tree_flags()
+        return self
+
+    def save(self, path):
+        """Write a checkpoint of the handle to `path` (pic_save)."""
+        self._check(self.lib.pic_save(self.h, os.fsencode(path)))
 
     def instances(self):
         """(particle_start, vertex_start, bucket_start), each n_instances + 1 long."""
