@@ -28,12 +28,14 @@
  *   - Leaves are numbered in depth-first pre-order (children in digit order);
  *     finite-element vertices (non-hanging grid points) by row-major position
  *     on the finest level; PIDT owner vertices by (level, row-major index).
- *   - The library owns all device memory it allocates (cudaMalloc at create
- *     and at re-tree); pic_destroy frees it.
+ *   - The library owns all device memory it allocates (at create, re-tree,
+ *     re-refinement, autotuning); pic_destroy frees it.  It is taken with
+ *     cudaMalloc, or from the caller's allocator set by pic_set_allocator.
  */
 #ifndef PIC_H
 #define PIC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -129,6 +131,21 @@ typedef struct {
   double residual;       /* FP64 2-norm of b - A V after the last built-in solve */
   int32_t error;         /* sticky device error: PIC_ERANGE if a non-finite value was seen */
 } pic_stats_t;
+
+/* Device memory through the caller's allocator, for example PyTorch's caching
+ * allocator.  alloc(user, bytes, stream) returns device memory of the current
+ * device, aligned to 256 bytes, or NULL (the calling function then fails with
+ * PIC_ENOMEM); free_fn(user, ptr, bytes, stream) returns it.  `stream` is the
+ * handle's stream: the library synchronises it after each allocation (a
+ * recycled block may still be in use by work queued before) and before
+ * returning blocks, so a stream-ordered pool may hand a block to the next
+ * user on that stream at once.  The setting is process-wide and
+ * taken by handles created afterwards, which keep it for all their later
+ * allocations and frees; both NULL restores cudaMalloc / cudaFree.  Only one
+ * of the two NULL: PIC_EINVAL.  Host only; no device call. */
+typedef void *(*pic_alloc_fn)(void *user, size_t bytes, void *stream);
+typedef void (*pic_free_fn)(void *user, void *ptr, size_t bytes, void *stream);
+PIC_API int pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_fn, void *user);
 
 /* Create a handle on the current CUDA device: validate and tabulate the tree,
  * copy the particles, bin them (initial key + stable bucket sort). */

@@ -6,7 +6,9 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -32,6 +34,11 @@ struct pic_s {
   int device = 0;
   cudaStream_t stream = nullptr;
   pic_config cfg{};
+  // device memory through the caller's allocator (pic_set_allocator at
+  // creation); NULL: cudaMalloc / cudaFree
+  pic_alloc_fn alloc_fn = nullptr;
+  pic_free_fn free_fn = nullptr;
+  void *alloc_user = nullptr;
   int d = 0, scheme = 0, split = 0;
   int64_t n = 0;
   HostTree ht;                 // instance 0 (the only one unless batched)
@@ -115,14 +122,35 @@ int cuda_fail(pic_t h, cudaError_t e, const char *what) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
   } while (0)
 
+// Process-wide allocator that handles created from now on adopt.
+std::mutex g_alloc_mu;
+pic_alloc_fn g_alloc_fn = nullptr;
+pic_free_fn g_free_fn = nullptr;
+void *g_alloc_user = nullptr;
+
 template <typename T>
 int dalloc(pic_t h, std::vector<DevBuf> &bufs, T **out, size_t count) {
   size_t bytes = sizeof(T) * (count ? count : 1);
   void *p = nullptr;
-  cudaError_t e = cudaMalloc(&p, bytes);
-  if (e != cudaSuccess) {
-    *out = nullptr;
-    return fail(h, PIC_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed");
+  *out = nullptr;
+  if (h->alloc_fn) {
+    p = h->alloc_fn(h->alloc_user, bytes, (void *)h->stream);
+    if (!p) return fail(h, PIC_ENOMEM, "the caller's allocator failed for " + std::to_string(bytes) + " bytes");
+    if ((uintptr_t)p & 255u) {
+      h->free_fn(h->alloc_user, p, bytes, (void *)h->stream);
+      return fail(h, PIC_ENOMEM, "the caller's allocator returned a pointer not aligned to 256 bytes");
+    }
+    // a recycled block may still be in use by work queued on the stream
+    // before it was handed over; some uploads copy outside the stream
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      h->free_fn(h->alloc_user, p, bytes, (void *)h->stream);
+      return cuda_fail(h, e, "cudaStreamSynchronize");
+    }
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess)
+      return fail(h, PIC_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed");
   }
   bufs.push_back({p, bytes});
   h->device_bytes += (int64_t)bytes;
@@ -131,8 +159,14 @@ int dalloc(pic_t h, std::vector<DevBuf> &bufs, T **out, size_t count) {
 }
 
 void free_bufs(pic_t h, std::vector<DevBuf> &bufs) {
+  // blocks go back to the caller's allocator only once the stream is done
+  // with them (cudaFree synchronises the device itself)
+  if (h->free_fn && !bufs.empty()) cudaStreamSynchronize(h->stream);
   for (auto &b : bufs) {
-    cudaFree(b.p);
+    if (h->free_fn)
+      h->free_fn(h->alloc_user, b.p, b.bytes, (void *)h->stream);
+    else
+      cudaFree(b.p);
     h->device_bytes -= (int64_t)b.bytes;
   }
   bufs.clear();
@@ -890,6 +924,12 @@ static int create_forest(pic_t *out, int32_t n_inst, const pic_tree_desc *trees,
   h->split = cfg->precision == PIC_FP32_SPLIT;
   h->n = n_total;
   h->stream = (cudaStream_t)cfg->stream;
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    h->alloc_fn = g_alloc_fn;
+    h->free_fn = g_free_fn;
+    h->alloc_user = g_alloc_user;
+  }
   cudaGetDevice(&h->device);
   int rc;
   cudaError_t e = set_constants(h->stream);
@@ -1589,6 +1629,15 @@ int pic_tree_flags(pic_t h, uint8_t *flags, int64_t *n_nodes) {
     total += t.n_nodes;
   }
   if (n_nodes) *n_nodes = total;
+  return PIC_OK;
+}
+
+int pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_fn, void *user) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return PIC_EINVAL;
+  std::lock_guard<std::mutex> lock(g_alloc_mu);
+  g_alloc_fn = alloc;
+  g_free_fn = free_fn;
+  g_alloc_user = alloc ? user : nullptr;
   return PIC_OK;
 }
 

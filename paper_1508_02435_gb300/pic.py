@@ -59,6 +59,8 @@ class Stats(C.Structure):
 
 
 SOLVE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 
 # (name, restype, argtypes) of every entry point declared in include/pic.h
 SIGNATURES = [
@@ -101,6 +103,7 @@ SIGNATURES = [
     ("pic_retree", C.c_int, [C.c_void_p, C.POINTER(TreeDesc)]),
     ("pic_adapt", C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32]),
     ("pic_tree_flags", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pic_set_allocator", C.c_int, [ALLOC_FN, FREE_FN, C.c_void_p]),
     ("pic_save", C.c_int, [C.c_void_p, C.c_char_p]),
     ("pic_load", C.c_int, [C.POINTER(C.c_void_p), C.c_char_p, C.c_void_p]),
 ]
@@ -179,6 +182,39 @@ def tree_tables(d: int, flags) -> dict:
     if rc != 0:
         raise PicError(rc, lib.pic_strerror(rc).decode())
     return out
+
+
+def _torch_alloc(user, nbytes, stream):
+    try:
+        import torch
+        return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+    except Exception:  # out of memory or no CUDA: the library reports PIC_ENOMEM
+        return None
+
+
+def _torch_free(user, ptr, nbytes, stream):
+    try:
+        import torch
+        torch.cuda.caching_allocator_delete(int(ptr))
+    except Exception:  # interpreter shutdown
+        pass
+
+
+# the callbacks must outlive every handle created while they are set
+_TORCH_CALLBACKS = (ALLOC_FN(_torch_alloc), FREE_FN(_torch_free))
+
+
+def use_torch_allocator(enable: bool = True):
+    """Take the device memory of handles created from now on from PyTorch's
+    caching allocator (pic_set_allocator); False restores cudaMalloc.  Handles
+    keep the allocator they were created with."""
+    lib = load()
+    if enable:
+        rc = lib.pic_set_allocator(_TORCH_CALLBACKS[0], _TORCH_CALLBACKS[1], None)
+    else:
+        rc = lib.pic_set_allocator(ALLOC_FN(), FREE_FN(), None)
+    if rc != 0:
+        raise PicError(rc, lib.pic_strerror(rc).decode())
 
 
 def stream_step(x, v, dt: float, steps: int = 1, stream=None):

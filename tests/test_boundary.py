@@ -41,3 +41,15 @@ def test_strerror_is_host_only():
     lib = pic.load()
     assert lib.pic_strerror(0) == b"ok"
     assert b"malformed" in lib.pic_strerror(-1)
+
+
+def test_set_allocator_takes_both_callbacks_or_neither():
+    lib = pic.load()
+    alloc, free = pic._TORCH_CALLBACKS
+    try:
+        assert lib.pic_set_allocator(alloc, pic.FREE_FN(), None) == -1
+        assert lib.pic_set_allocator(pic.ALLOC_FN(), free, None) == -1
+        pic.use_torch_allocator(True)
+    finally:
+        pic.use_torch_allocator(False)
+    assert lib.pic_set_allocator(pic.ALLOC_FN(), pic.FREE_FN(), None) == 0
