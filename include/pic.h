@@ -232,6 +232,21 @@ PIC_API int pic_set_state(pic_t h, const int32_t *leaf, const void *x_or_o, cons
 
 PIC_API int pic_stats(pic_t h, pic_stats_t *out);
 
+/* Lift and drop counts of Algorithm 1 (the paper's cost measure for particle
+ * handling, Section 6: lifting a particle n levels counts as n lifts).  With
+ * counting on, every pic_step / pic_step_fixed_field adds, for each particle
+ * that went from leaf L1 to leaf L2, lifts = level(L1) - m and
+ * drops = level(L2) - m, m the level of the deepest common ancestor of L1 and
+ * L2 (a particle is lifted out of every cell that no longer covers it and
+ * dropped into every cell that does; stayers add nothing).  Two extra
+ * kernels per step; PIT handles with track_ids only (PIC_ESTATE otherwise);
+ * graph capture is refused while counting.  pic_count_lifts(h, 1) starts (or
+ * restarts) from zero, (h, 0) stops and frees the counters.  pic_lift_counts
+ * returns the totals and the steps counted since the start (synchronous;
+ * PIC_ESTATE when counting is off); any pointer may be NULL. */
+PIC_API int pic_count_lifts(pic_t h, int32_t enable);
+PIC_API int pic_lift_counts(pic_t h, int64_t *lifts, int64_t *drops, int64_t *steps);
+
 /* Phases of a step for pic_phase_times. */
 #define PIC_PHASE_DEPOSIT 0  /* leaf partial sums + vertex charges + FP64 total */
 #define PIC_PHASE_SOLVE 1    /* built-in Jacobi sweeps + vertex field (or the hook) */

@@ -143,6 +143,28 @@ class Tree:
         self._lib.or_leaf_info(self._h, _p(lev), _p(co))
         return lev, co
 
+    def pit_lifts(self, old_leaf: np.ndarray, new_leaf: np.ndarray):
+        """Lifts and drops of Algorithm 1 for particles that go from leaf
+        old_leaf[i] to leaf new_leaf[i]: a particle is lifted out of every cell
+        from its old leaf up to the deepest ancestor that also contains its new
+        leaf, then dropped cell by cell down to the new leaf; lifting (or
+        dropping) n levels counts as n lifts (drops), as the paper counts them
+        (Section 6).  Returns (lifts, drops), int64 per particle."""
+        lev, co = self.leaf_info()
+        old_leaf = np.asarray(old_leaf, np.int64)
+        new_leaf = np.asarray(new_leaf, np.int64)
+        l1, l2 = lev[old_leaf].astype(np.int64), lev[new_leaf].astype(np.int64)
+        c1, c2 = co[old_leaf], co[new_leaf]
+        low = np.minimum(l1, l2)
+        common = np.zeros(len(old_leaf), np.int64)  # level of the deepest common ancestor
+        for m in range(1, int(low.max(initial=0)) + 1):
+            on = low >= m
+            a1 = c1 // (3 ** np.where(on, l1 - m, 0))[:, None]
+            a2 = c2 // (3 ** np.where(on, l2 - m, 0))[:, None]
+            same = on & np.all(a1 == a2, axis=1)
+            common = np.where(same, m, common)
+        return l1 - common, l2 - common
+
     # ---- keys -----------------------------------------------------------
     def pit_owner(self, x: np.ndarray) -> np.ndarray:
         x = _c(x, np.float64)

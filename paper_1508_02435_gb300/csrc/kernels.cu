@@ -1197,6 +1197,69 @@ void launch_gather_only(const DevTree &t, bool split, const void *pos, const int
                                                    (double *)Ep); }
 }
 
+// ---------------------------------------------------------------------------
+// Lift and drop counts of Algorithm 1 (diagnostic, PIT)
+// ---------------------------------------------------------------------------
+
+// The leaf of every particle before a step, by particle id.
+__global__ void k_scatter_by_id(const int32_t *ids, const int32_t *leaf, int64_t n, int32_t *by_id) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int32_t id = ids[p];
+  if (id >= 0 && id < n) by_id[id] = leaf[p];
+}
+
+// A particle that went from leaf L1 (level l1, coordinates c1) to leaf L2 is
+// lifted out of every cell from L1 up to the deepest ancestor that contains
+// L2, then dropped down to L2: lifts = l1 - m, drops = l2 - m with m the level
+// of that ancestor (levels and coordinates of one instance's tree).  Warp sums
+// go to counts[0] (lifts) and counts[1] (drops).
+__global__ void k_lift_drop(DevTree t, const int32_t *ids, const int32_t *leaf, const int32_t *old_by_id, int64_t n,
+                            unsigned long long *counts) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned lifts = 0, drops = 0;
+  if (p < n) {
+    const int32_t id = ids[p];
+    const int32_t L2 = leaf[p];
+    const int32_t L1 = (id >= 0 && id < n) ? old_by_id[id] : -1;
+    if (L1 >= 0 && L1 < t.n_leaves && L2 >= 0 && L2 < t.n_leaves) {
+      const int l1 = t.leaf_level[L1], l2 = t.leaf_level[L2];
+      int m = l1 < l2 ? l1 : l2;
+      uint32_t a1[3] = {0u, 0u, 0u}, a2[3] = {0u, 0u, 0u};
+      for (int a = 0; a < t.d; ++a) {
+        a1[a] = (uint32_t)t.leaf_coords[(int64_t)L1 * t.d + a] / c_pow3[l1 - m];
+        a2[a] = (uint32_t)t.leaf_coords[(int64_t)L2 * t.d + a] / c_pow3[l2 - m];
+      }
+      while (m > 0 && (a1[0] != a2[0] || a1[1] != a2[1] || a1[2] != a2[2])) {
+        for (int a = 0; a < 3; ++a) {
+          a1[a] /= 3u;
+          a2[a] /= 3u;
+        }
+        --m;
+      }
+      lifts = (unsigned)(l1 - m);
+      drops = (unsigned)(l2 - m);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    lifts += __shfl_down_sync(0xffffffffu, lifts, off);
+    drops += __shfl_down_sync(0xffffffffu, drops, off);
+  }
+  if ((threadIdx.x & 31) == 0 && (lifts | drops)) {
+    atomicAdd(&counts[0], (unsigned long long)lifts);
+    atomicAdd(&counts[1], (unsigned long long)drops);
+  }
+}
+
+void launch_scatter_by_id(const int32_t *ids, const int32_t *leaf, int64_t n, int32_t *by_id, cudaStream_t s) {
+  if (n > 0) { COUNT(1); k_scatter_by_id<<<grid_for(n), kBlock, 0, s>>>(ids, leaf, n, by_id); }
+}
+
+void launch_lift_drop(const DevTree &t, const int32_t *ids, const int32_t *leaf, const int32_t *old_by_id, int64_t n,
+                      unsigned long long *counts, cudaStream_t s) {
+  if (n > 0) { COUNT(1); k_lift_drop<<<grid_for(n), kBlock, 0, s>>>(t, ids, leaf, old_by_id, n, counts); }
+}
+
 void launch_half_kick(bool split, const void *Ep, int64_t n_total, double c, void *v, cudaStream_t s) {
   if (n_total <= 0) return;
   if (split)

@@ -69,6 +69,13 @@ struct pic_s {
   int64_t step = 0;
   std::string last_error;
 
+  // lift and drop counts of the steps (pic_count_lifts; PIT, tracked ids)
+  bool count_lifts = false;
+  int32_t *lift_old = nullptr;             // leaf before the step, by particle id
+  unsigned long long *lift_counts = nullptr;  // [0] lifts, [1] drops
+  int64_t lift_steps = 0;
+  std::vector<DevBuf> diag_bufs;
+
   // brick path (uniform tree, PIT, split precision)
   bool brick = false;
   bool brick_ok = false;    // the brick path applies (its buffers exist)
@@ -886,6 +893,7 @@ void pic_destroy(pic_t h) {
   }
   for (auto e : h->event_pool) cudaEventDestroy(e);
   drop_graphs(h);
+  free_bufs(h, h->diag_bufs);
   free_bufs(h, h->brick_bufs);
   free_bufs(h, h->state_bufs);
   free_bufs(h, h->tree_bufs);
@@ -1009,12 +1017,39 @@ int pic_init_leapfrog(pic_t h, double dt, pic_solve_fn hook, void *user) {
   return PIC_OK;
 }
 
+// Lift and drop counting around the push and re-bin of a step: the leaf of
+// every particle by id before, the per-particle counts after.
+static int lift_before(pic_t h) {
+  int rc;
+  if ((rc = ensure_leaf(h))) return rc;
+  launch_scatter_by_id(h->ids[0], h->leaf[0], h->n, h->lift_old, h->stream);
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+static int lift_after(pic_t h) {
+  int rc;
+  if ((rc = ensure_leaf(h))) return rc;
+  launch_lift_drop(h->dt, h->ids[0], h->leaf[0], h->lift_old, h->n, h->lift_counts, h->stream);
+  CK(cudaGetLastError());
+  h->lift_steps++;
+  return PIC_OK;
+}
+
+static int counted_push_and_rebin(pic_t h, double dt) {
+  int rc;
+  if (h->count_lifts && (rc = lift_before(h))) return rc;
+  if ((rc = push_and_rebin(h, dt))) return rc;
+  if (h->count_lifts && (rc = lift_after(h))) return rc;
+  return PIC_OK;
+}
+
 int pic_step(pic_t h, double dt, pic_solve_fn hook, void *user) {
   if (check_handle(h)) return PIC_EINVAL;
   int rc;
   if ((rc = deposit(h))) return rc;
   if ((rc = field(h, hook, user))) return rc;
-  if ((rc = push_and_rebin(h, dt))) return rc;
+  if ((rc = counted_push_and_rebin(h, dt))) return rc;
   h->step++;
   return PIC_OK;
 }
@@ -1023,8 +1058,48 @@ int pic_step_fixed_field(pic_t h, double dt) {
   if (check_handle(h)) return PIC_EINVAL;
   int rc;
   if ((rc = deposit(h))) return rc;
-  if ((rc = push_and_rebin(h, dt))) return rc;
+  if ((rc = counted_push_and_rebin(h, dt))) return rc;
   h->step++;
+  return PIC_OK;
+}
+
+int pic_count_lifts(pic_t h, int32_t enable) {
+  if (check_handle(h)) return PIC_EINVAL;
+  if (!enable) {
+    h->count_lifts = false;
+    free_bufs(h, h->diag_bufs);
+    h->lift_old = nullptr;
+    h->lift_counts = nullptr;
+    return PIC_OK;
+  }
+  if (h->scheme != PIC_PIT) return fail(h, PIC_ESTATE, "lift and drop counts are kept for PIT handles only");
+  if (!h->cfg.track_ids) return fail(h, PIC_ESTATE, "lift and drop counts need track_ids = 1");
+  drop_graphs(h);
+  int rc;
+  if (!h->count_lifts) {
+    if ((rc = dalloc(h, h->diag_bufs, &h->lift_old, h->n)) ||
+        (rc = dalloc(h, h->diag_bufs, &h->lift_counts, 2))) {
+      free_bufs(h, h->diag_bufs);
+      h->lift_old = nullptr;
+      h->lift_counts = nullptr;
+      return rc;
+    }
+  }
+  CK(cudaMemsetAsync(h->lift_counts, 0, 2 * sizeof(unsigned long long), h->stream));
+  h->lift_steps = 0;
+  h->count_lifts = true;
+  return PIC_OK;
+}
+
+int pic_lift_counts(pic_t h, int64_t *lifts, int64_t *drops, int64_t *steps) {
+  if (check_handle(h)) return PIC_EINVAL;
+  if (!h->count_lifts) return fail(h, PIC_ESTATE, "lift counting is off (pic_count_lifts)");
+  unsigned long long c[2] = {0, 0};
+  CK(cudaMemcpyAsync(c, h->lift_counts, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (lifts) *lifts = (int64_t)c[0];
+  if (drops) *drops = (int64_t)c[1];
+  if (steps) *steps = h->lift_steps;
   return PIC_OK;
 }
 
@@ -1044,6 +1119,7 @@ void set_host_view(pic_t h, const pic_s::HostView &v) {
 int pic_graph_capture(pic_t h, double dt) {
   if (check_handle(h)) return PIC_EINVAL;
   if (!h->stream) return fail(h, PIC_ESTATE, "graph capture needs a non-default stream");
+  if (h->count_lifts) return fail(h, PIC_ESTATE, "lift counting is on; captured steps would not count");
   if (h->prof) return fail(h, PIC_ESTATE, "stop profiling before capturing");
   drop_graphs(h);
   int rc;

@@ -104,6 +104,8 @@ SIGNATURES = [
     ("pic_adapt", C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32]),
     ("pic_tree_flags", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_set_allocator", C.c_int, [ALLOC_FN, FREE_FN, C.c_void_p]),
+    ("pic_count_lifts", C.c_int, [C.c_void_p, C.c_int32]),
+    ("pic_lift_counts", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_save", C.c_int, [C.c_void_p, C.c_char_p]),
     ("pic_load", C.c_int, [C.POINTER(C.c_void_p), C.c_char_p, C.c_void_p]),
 ]
@@ -390,6 +392,17 @@ class Pic:
 
     def sync(self):
         self._check(self.lib.pic_sync(self.h))
+
+    def count_lifts(self, enable: bool = True):
+        """Start (from zero) or stop counting the lifts and drops of every
+        step (pic_count_lifts; PIT handles with tracked ids)."""
+        self._check(self.lib.pic_count_lifts(self.h, 1 if enable else 0))
+
+    def lift_counts(self):
+        """(lifts, drops, steps) since counting started (pic_lift_counts)."""
+        lifts, drops, steps = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+        self._check(self.lib.pic_lift_counts(self.h, C.byref(lifts), C.byref(drops), C.byref(steps)))
+        return lifts.value, drops.value, steps.value
 
     def stats(self) -> Stats:
         out = Stats()

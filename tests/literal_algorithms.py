@@ -75,10 +75,18 @@ def dual_contains(level: int, j, Q) -> bool:
 # Algorithm 1: particle in tree
 # --------------------------------------------------------------------------
 
-def pit_literal(d, flags, Q_old, Q_new, max_traversals=8):
+def pit_literal(d, flags, Q_old, Q_new, max_traversals=8, counts=None):
     """Particles start in the leaf covering Q_old; the move replaces the
     position by Q_new in the first traversal.  Traversals repeat until no
-    particle is lifted or dropped.  Returns {particle: (level, coords)}."""
+    particle is lifted or dropped.  Returns {particle: (level, coords)}.
+    With a dict `counts`, counts["lifts"][m] and counts["drops"][m] receive
+    the lift and drop events of particle m during the traversals (the initial
+    placement is not counted)."""
+    lifts = [0] * len(Q_old)
+    drops = [0] * len(Q_old)
+    if counts is not None:
+        counts["lifts"] = lifts
+        counts["drops"] = drops
     root = parse_tree(d, flags)
     assoc = {id(root): list(range(len(Q_old)))}
     cells = {id(root): root}
@@ -112,6 +120,7 @@ def pit_literal(d, flags, Q_old, Q_new, max_traversals=8):
                         assoc.setdefault(id(ch), []).append(m)
                         mine.remove(m)
                         state["changes"] += 1
+                        drops[m] += 1
                         break
         else:                                   # move
             if state["moving"]:
@@ -127,6 +136,7 @@ def pit_literal(d, flags, Q_old, Q_new, max_traversals=8):
                     assoc.setdefault(id(cell.parent), []).append(m)
                     mine.remove(m)
                     state["changes"] += 1
+                    lifts[m] += 1
 
     for t in range(max_traversals):
         state["changes"] = 0

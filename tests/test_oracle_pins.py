@@ -120,6 +120,59 @@ def test_pit_equals_literal_algorithm1(d, depth, p, seed, vmax):
         assert lit[pi] == (lev[leaf[pi]], tuple(int(c) for c in co[leaf[pi]]))
 
 
+@pytest.mark.parametrize("d,depth,p,seed,vmax", [(2, 4, 0.4, 11, 0.3), (2, 5, 0.3, 12, 0.05),
+                                                 (3, 3, 0.35, 13, 0.4), (2, 5, 0.5, 14, 0.8)])
+def test_pit_lift_counts_equal_literal_algorithm1(d, depth, p, seed, vmax):
+    """The oracle's lift and drop counts per particle (old leaf up to the
+    deepest common ancestor, down to the new leaf) equal the lift and drop
+    events of Algorithm 1 executed on a depth-first traversal."""
+    flags = random_tree(d, depth, p, seed)
+    t = oracle.Tree(d, flags)
+    x0, v = W.random_particles(d, 300, seed, vmax=vmax)
+    x1 = np.mod(x0 + v, 1.0)
+    Q0, Q1 = quantise_np(x0).T.tolist(), quantise_np(x1).T.tolist()
+    counts = {}
+    LA.pit_literal(d, flags, Q0, Q1, counts=counts)
+    lifts, drops = t.pit_lifts(t.pit_owner(x0), t.pit_owner(x1))
+    assert np.array_equal(lifts, counts["lifts"])
+    assert np.array_equal(drops, counts["drops"])
+    assert lifts.sum() > 0 and (lifts == 0).any()
+
+
+def test_pit_lift_counts_closed_form_on_a_uniform_tree():
+    """2D, depth 3 (27 x 27 leaves, leaf id = depth-first): a move to the
+    neighbour inside the same parent is one lift and one drop; across a
+    level-2 face two of each; across a level-1 face (or the periodic seam)
+    three; a stayer none."""
+    d, D = 2, 3
+    t = oracle.Tree(d, W.uniform_tree_flags(d, D))
+    lev, co = t.leaf_info()
+    leaf_of = {tuple(int(c) for c in co[i]): i for i in range(len(lev))}
+    pairs = [((4, 4), (4, 4), 0), ((0, 0), (1, 0), 1), ((2, 0), (3, 0), 2), ((8, 5), (9, 5), 3),
+             ((26, 3), (0, 3), 3), ((4, 4), (5, 5), 1), ((4, 4), (13, 22), 3), ((1, 1), (0, 2), 1)]
+    old = [leaf_of[a] for a, _, _ in pairs]
+    new = [leaf_of[b] for _, b, _ in pairs]
+    lifts, drops = t.pit_lifts(np.array(old), np.array(new))
+    expect = np.array([k for _, _, k in pairs])
+    assert np.array_equal(lifts, expect) and np.array_equal(drops, expect)
+
+
+def test_pit_lift_counts_across_levels():
+    """From a leaf on level 3 to a leaf on level 1 in another level-1 cell:
+    three lifts to the root, one drop; and the reverse."""
+    d = 2
+    flags = np.zeros(1 + 9 + 9 + 9, np.uint8)
+    flags[0] = 1          # root
+    flags[1] = 1          # level-1 cell (0, 0)
+    flags[10] = 1         # its first child, level-2 cell (0, 0)
+    t = oracle.Tree(d, flags)
+    lev, co = t.leaf_info()
+    deep = int(np.flatnonzero(lev == 3)[0])
+    coarse = [i for i in range(len(lev)) if lev[i] == 1 and tuple(co[i]) == (2, 2)][0]
+    lifts, drops = t.pit_lifts(np.array([deep, coarse]), np.array([coarse, deep]))
+    assert list(lifts) == [3, 1] and list(drops) == [1, 3]
+
+
 # ---------------------------------------------------------------------------
 # a2 PIDT owner
 # ---------------------------------------------------------------------------
