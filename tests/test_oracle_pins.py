@@ -173,6 +173,63 @@ def test_pit_lift_counts_across_levels():
     assert list(lifts) == [3, 1] and list(drops) == [1, 3]
 
 
+def _unit_speed_particles(d, n, seed):
+    """Uniform positions; velocities of uniform random direction and speed in
+    [0, 1] (the particle workload of the paper's Section 6)."""
+    rng = np.random.default_rng(seed)
+    x = rng.random((d, n))
+    g = rng.standard_normal((d, n))
+    v = g / np.linalg.norm(g, axis=0) * rng.random(n)
+    return x, v
+
+
+def _mean_lifts(t, x, v, dt):
+    li, dr = t.pit_lifts(t.pit_owner(x), t.pit_owner(np.mod(x + v * dt, 1.0)))
+    return li.mean(), dr.mean()
+
+
+@pytest.mark.parametrize("d,n", [(2, 20_000), (3, 30_000)])
+def test_lifts_grow_with_the_time_step(d, n):
+    """On a tree refined to a particles-per-cell bound, lifts per particle
+    grow with the time step and, for small steps, in proportion to it (a
+    particle leaves its cell with probability ~ |v| dt / h)."""
+    x, v = _unit_speed_particles(d, n, 5)
+    t = oracle.Tree(d, oracle.retree64(d, x, 30, 1, 8 if d == 2 else 5))
+    lifts = [_mean_lifts(t, x, v, dt)[0] for dt in (1e-4, 1e-3, 1e-2, 1e-1)]
+    assert all(a < b for a, b in zip(lifts, lifts[1:])), lifts
+    assert 0.04 < lifts[1] / lifts[2] < 0.2, lifts
+
+
+@pytest.mark.parametrize("d,n,ppcs", [(2, 20_000, (10, 30, 100, 300)), (3, 30_000, (4, 12, 40))])
+def test_more_particles_per_cell_fewer_lifts(d, n, ppcs):
+    """Section 6: the more particles a cell may hold before it is refined, the
+    coarser the tree and the fewer lifts per particle at a fixed time step."""
+    x, v = _unit_speed_particles(d, n, 6)
+    lifts = []
+    for ppc in ppcs:
+        t = oracle.Tree(d, oracle.retree64(d, x, ppc, 1, 8 if d == 2 else 5))
+        lifts.append(_mean_lifts(t, x, v, 1e-2)[0])
+    assert all(a > b for a, b in zip(lifts, lifts[1:])), lifts
+
+
+def test_lifts_of_stayers_movers_and_uniform_trees():
+    """Stayers are neither lifted nor dropped, every particle that changes
+    leaf is lifted at least once, and on a uniform tree every lift is matched
+    by a drop."""
+    d = 2
+    x, v = _unit_speed_particles(d, 5000, 7)
+    for flags, uniform in ((W.uniform_tree_flags(d, 4), True), (random_tree(d, 5, 0.35, 8), False)):
+        t = oracle.Tree(d, flags)
+        old, new = t.pit_owner(x), t.pit_owner(np.mod(x + 0.02 * v, 1.0))
+        li, dr = t.pit_lifts(old, new)
+        assert np.all((li == 0) == (old == new)) and np.all((dr == 0) == (old == new))
+        assert (li > 0).any()
+        if uniform:
+            assert np.array_equal(li, dr)
+        else:
+            assert not np.array_equal(li, dr)  # moves between levels
+
+
 # ---------------------------------------------------------------------------
 # a2 PIDT owner
 # ---------------------------------------------------------------------------
