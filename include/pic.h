@@ -230,6 +230,9 @@ PIC_API int pic_get_state(pic_t h, int32_t *leaf, void *x_or_o, void *v, int32_t
 PIC_API int pic_set_state(pic_t h, const int32_t *leaf, const void *x_or_o, const void *v,
                   int32_t where);
 
+/* Counters of the last step (movers, largest bucket), the FP64 charge total
+ * of the last deposit (neutrality check), the residual norm of the last
+ * built-in solve, the step count and the sticky device error.  Synchronous. */
 PIC_API int pic_stats(pic_t h, pic_stats_t *out);
 
 /* Lift and drop counts of Algorithm 1 (the paper's cost measure for particle
