@@ -187,6 +187,11 @@ PIC_API int pic_step_fixed_field(pic_t h, double dt);
  * drops them. */
 PIC_API int pic_graph_capture(pic_t h, double dt);
 
+/* The same for the whole time step with the built-in solve (no hook): deposit
+ * when due, Jacobi sweeps + vertex field, gather + push + key, re-bin.  A
+ * replay is one pic_step(h, dt, NULL, NULL), bit for bit. */
+PIC_API int pic_graph_capture_step(pic_t h, double dt);
+
 /* Replay `steps` captured steps on the handle's stream (asynchronous). */
 PIC_API int pic_graph_launch(pic_t h, int32_t steps);
 

@@ -1116,7 +1116,16 @@ void set_host_view(pic_t h, const pic_s::HostView &v) {
   h->q_valid = v.q_valid;
 }
 
-int pic_graph_capture(pic_t h, double dt) {
+// The captured step: deposit when due, the built-in solve if with_solve,
+// gather + push + key, re-bin.
+static int captured_step(pic_t h, double dt, bool with_solve) {
+  int rc;
+  if ((rc = deposit(h))) return rc;
+  if (with_solve && (rc = field(h, nullptr, nullptr))) return rc;
+  return push_and_rebin(h, dt);
+}
+
+static int graph_capture(pic_t h, double dt, bool with_solve) {
   if (check_handle(h)) return PIC_EINVAL;
   if (!h->stream) return fail(h, PIC_ESTATE, "graph capture needs a non-default stream");
   if (h->count_lifts) return fail(h, PIC_ESTATE, "lift counting is on; captured steps would not count");
@@ -1125,7 +1134,7 @@ int pic_graph_capture(pic_t h, double dt) {
   int rc;
   // one ordinary step first, so that the captured steps start from the state
   // every later step starts from (brick path: charges already deposited)
-  if ((rc = deposit(h)) || (rc = push_and_rebin(h, dt))) return rc;
+  if ((rc = captured_step(h, dt, with_solve))) return rc;
   h->step++;
   if ((rc = ensure_leaf(h))) return rc;  // generic path: no expansion inside the graph
   CK(cudaStreamSynchronize(h->stream));
@@ -1135,8 +1144,7 @@ int pic_graph_capture(pic_t h, double dt) {
     h->graph_pre[g] = host_view(h);
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    rc = deposit(h);
-    if (!rc) rc = push_and_rebin(h, dt);
+    rc = captured_step(h, dt, with_solve);
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     h->graph_post[g] = host_view(h);
     if (!rc && e == cudaSuccess) e = cudaGraphInstantiate(&h->graph[g], graph, 0);
@@ -1151,6 +1159,10 @@ int pic_graph_capture(pic_t h, double dt) {
   h->graph_kernels = (launches() - k0) / 2;
   return PIC_OK;
 }
+
+int pic_graph_capture(pic_t h, double dt) { return graph_capture(h, dt, false); }
+
+int pic_graph_capture_step(pic_t h, double dt) { return graph_capture(h, dt, true); }
 
 int pic_graph_launch(pic_t h, int32_t steps) {
   if (check_handle(h) || steps < 0) return PIC_EINVAL;

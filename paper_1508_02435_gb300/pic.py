@@ -93,6 +93,7 @@ SIGNATURES = [
                                   C.c_void_p]),
     ("pic_tree_tabulate", C.c_int, [C.c_int32, C.c_void_p, C.c_int64, C.c_void_p] + [C.c_void_p] * 8),
     ("pic_graph_launch", C.c_int, [C.c_void_p, C.c_int32]),
+    ("pic_graph_capture_step", C.c_int, [C.c_void_p, C.c_double]),
     ("pic_autotune", C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_void_p]),
     ("pic_set_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
     ("pic_get_tuning", C.c_int, [C.c_void_p, C.c_void_p]),
@@ -479,6 +480,10 @@ class Pic:
 
     def graph_capture(self, dt: float):
         self._check(self.lib.pic_graph_capture(self.h, dt))
+
+    def graph_capture_step(self, dt: float):
+        """Capture the whole step with the built-in solve (pic_graph_capture_step)."""
+        self._check(self.lib.pic_graph_capture_step(self.h, dt))
 
     def graph_launch(self, steps: int):
         self._check(self.lib.pic_graph_launch(self.h, steps))
