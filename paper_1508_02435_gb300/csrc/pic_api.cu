@@ -179,8 +179,8 @@ void free_bufs(pic_t h, std::vector<DevBuf> &bufs) {
   bufs.clear();
 }
 
-template <typename T>
-int upload(pic_t h, std::vector<DevBuf> &bufs, const T **out, const std::vector<T> &v) {
+template <typename T, typename A>
+int upload(pic_t h, std::vector<DevBuf> &bufs, const T **out, const std::vector<T, A> &v) {
   T *p = nullptr;
   int rc = dalloc(h, bufs, &p, v.size());
   if (rc) return rc;
@@ -310,7 +310,7 @@ int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const st
   } else {
     const HostTree &ht = h0;
     std::vector<float> f;
-    auto to32 = [&](const std::vector<double> &v) {
+    auto to32 = [&](const table<double> &v) {
       f.assign(v.size(), 0.f);
       for (size_t i = 0; i < v.size(); ++i) f[i] = (float)v[i];
       return f;

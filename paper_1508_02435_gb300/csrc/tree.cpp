@@ -221,8 +221,9 @@ void HostTree::build_grid() {
   uint64_t key_max = 1;
   for (int a = 0; a < d; ++a) key_max *= (uint64_t)M;
   radix_sort(kc, nlc, key_max, [](const KC &x) { return x.key; });
-  std::vector<int32_t> corner_pt(nlc);
-  std::vector<int64_t> pkey;
+  table<int32_t> corner_pt;
+  corner_pt.resize(nlc);  // every corner written below
+  table<int64_t> pkey;
   {
     // ranks of the distinct keys: new keys counted per chunk, then offsets
     std::vector<int64_t> first(nt + 1, 0);
@@ -232,7 +233,7 @@ void HostTree::build_grid() {
       first[t + 1] = c;
     });
     for (unsigned t = 0; t < nt; ++t) first[t + 1] += first[t];
-    pkey.assign(first[nt], 0);
+    pkey.resize(first[nt]);
     parallel_chunks(nlc, nt, [&](unsigned t, int64_t lo, int64_t hi) {
       int64_t r = first[t] - 1;
       for (int64_t i = lo; i < hi; ++i) {
@@ -250,8 +251,10 @@ void HostTree::build_grid() {
   // every point: the coarsest leaf whose closure holds it; non-hanging iff it
   // is a corner of that leaf, else (hanging) the d-linear interpolant of the
   // leaf's corners (weights by the point's place in the leaf)
-  std::vector<uint8_t> hanging(np, 0);
-  std::vector<int32_t> best_of(np, -1);
+  table<uint8_t> hanging;
+  table<int32_t> best_of;
+  hanging.resize(np);  // both written for every point below
+  best_of.resize(np);
   parallel_chunks(np, nt, [&](unsigned, int64_t lo, int64_t hi) {
     for (int64_t id = lo; id < hi; ++id) {
       int64_t p[3] = {0, 0, 0}, k = pkey[id];
@@ -358,7 +361,7 @@ void HostTree::build_grid() {
       first[t + 1] = c;
     });
     for (unsigned t = 0; t < nt; ++t) first[t + 1] += first[t];
-    vert_key.assign(first[nt], 0);
+    vert_key.resize(first[nt]);
     parallel_chunks(np, nt, [&](unsigned t, int64_t lo, int64_t hi) {
       int64_t r = first[t];
       for (int64_t id = lo; id < hi; ++id)
@@ -370,7 +373,8 @@ void HostTree::build_grid() {
   }
   n_vert = (int64_t)vert_key.size();
   // leaf corner -> (vertex, weight), ascending vertex
-  cexp_ptr.assign(nlc + 1, 0);
+  cexp_ptr.resize(nlc + 1);  // entries 1..nlc written below
+  cexp_ptr[0] = 0;
   {
     // entries per corner, offsets by chunk sums
     std::vector<int64_t> part(nt + 1, 0);
@@ -388,8 +392,8 @@ void HostTree::build_grid() {
       for (int64_t i = lo; i < hi; ++i) cexp_ptr[i + 1] += (int32_t)part[t];
     });
   }
-  cexp_vid.assign(cexp_ptr[nlc], 0);
-  cexp_w.assign(cexp_ptr[nlc], 0.0);
+  cexp_vid.resize(cexp_ptr[nlc]);  // every entry written below
+  cexp_w.resize(cexp_ptr[nlc]);
   parallel_chunks(nlc, nt, [&](unsigned, int64_t lo, int64_t hi) {
     std::vector<std::pair<int32_t, double>> ex;
     for (int64_t i = lo; i < hi; ++i) {
@@ -424,9 +428,9 @@ void HostTree::build_grid() {
       for (int32_t j = cexp_ptr[i]; j < cexp_ptr[i + 1]; ++j) ve[j] = {cexp_vid[j], (int32_t)i, cexp_w[j]};
   });
   radix_sort(ve, nnz, (uint64_t)std::max<int64_t>(n_vert, 1), [](const VE &x) { return (uint64_t)x.v; });
-  inc_ptr.assign(n_vert + 1, 0);
-  inc_lc.assign(nnz, 0);
-  inc_w.assign(nnz, 0.0);
+  inc_ptr.resize(n_vert + 1);  // every entry written below
+  inc_lc.resize(nnz);
+  inc_w.resize(nnz);
   parallel_chunks(nnz, nt, [&](unsigned, int64_t lo, int64_t hi) {
     for (int64_t j = lo; j < hi; ++j) {
       inc_lc[j] = ve[j].lc;
@@ -441,9 +445,9 @@ void HostTree::build_grid() {
   // itself, and the diagonal of the stiffness matrix -- summed over the
   // vertex's incident leaf corners in leaf-corner order, pairs of corners of
   // one leaf in (e, f) order: the order of a loop over leaves and corners
-  ion_load.assign(n_vert, 0.0);
-  diag.assign(n_vert, 0.0);
-  direct_cnt.assign(n_vert, 0);
+  ion_load.resize(n_vert);  // every vertex written below
+  diag.resize(n_vert);
+  direct_cnt.resize(n_vert);
   parallel_chunks(n_vert, nt, [&](unsigned, int64_t lo, int64_t hi) {
     for (int64_t v = lo; v < hi; ++v) {
       double ion = 0.0, dg = 0.0;
@@ -529,9 +533,9 @@ void HostTree::build_pidt() {
   });
   for (unsigned t = 0; t < nt; ++t) first[t + 1] += first[t];
   const int64_t nv = first[nt];
-  corner_pv.assign(nlc, 0);
-  pv_level.assign(nv, 0);
-  pv_j.assign(nv * d, 0);
+  corner_pv.resize(nlc);  // every corner and owner written below
+  pv_level.resize(nv);
+  pv_j.resize(nv * d);
   parallel_chunks(nlc, nt, [&](unsigned t, int64_t lo, int64_t hi) {
     int64_t id = first[t] - 1;
     for (int64_t i = lo; i < hi; ++i) {

@@ -5,10 +5,38 @@
 // vertices.
 #pragma once
 #include <cstdint>
+#include <memory>
+#include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace pic {
+
+// Allocator whose value-less construct leaves plain values uninitialised, so
+// that resize(n) of a large table costs no serial zero fill: the threads that
+// fill the table touch its pages first, in parallel.
+template <typename T>
+struct NoInitAllocator : std::allocator<T> {
+  using value_type = T;
+  template <typename U>
+  struct rebind {
+    using other = NoInitAllocator<U>;
+  };
+  NoInitAllocator() = default;
+  template <typename U>
+  NoInitAllocator(const NoInitAllocator<U> &) noexcept {}
+  template <typename U>
+  void construct(U *p) noexcept {
+    ::new ((void *)p) U;
+  }
+  template <typename U, typename... Args>
+  void construct(U *p, Args &&...args) {
+    ::new ((void *)p) U(std::forward<Args>(args)...);
+  }
+};
+template <typename T>
+using table = std::vector<T, NoInitAllocator<T>>;
 
 constexpr int kMaxLevel = 18;
 constexpr uint32_t kQSteps = 774840978u;  // 2 * 3^18 integer steps per axis
@@ -43,17 +71,17 @@ struct HostTree {
   // finite-element grid
   int64_t M = 1;       // 3^depth
   int64_t n_vert = 0;  // non-hanging grid points
-  std::vector<int64_t> vert_key;  // row-major key on the finest level (adaptive only)
+  table<int64_t> vert_key;  // row-major key on the finest level (adaptive only)
   // adaptive only: leaf corner -> (vertex, weight); vertex -> (leaf corner, weight)
-  std::vector<int32_t> cexp_ptr, cexp_vid, inc_ptr, inc_lc;
-  std::vector<double> cexp_w, inc_w;
-  std::vector<double> ion_load, diag;  // per vertex (adaptive), or one value (uniform)
-  std::vector<int32_t> direct_cnt;     // adaptive only
+  table<int32_t> cexp_ptr, cexp_vid, inc_ptr, inc_lc;
+  table<double> cexp_w, inc_w;
+  table<double> ion_load, diag;  // per vertex (adaptive), or one value (uniform)
+  table<int32_t> direct_cnt;     // adaptive only
 
   // PIDT owner vertices (adaptive only; uniform trees use the FE vertices)
   int64_t n_pv = 0;
-  std::vector<int32_t> corner_pv, pv_level;
-  std::vector<int64_t> pv_j;  // d per vertex
+  table<int32_t> corner_pv, pv_level;
+  table<int64_t> pv_j;  // d per vertex
 
   int build(int d_, int64_t n_flags, const uint8_t *flags, std::string *err);
   void build_grid();
