@@ -1519,6 +1519,7 @@ int pic_tree_tabulate(int32_t d, const uint8_t *flags, int64_t n_flags, pic_tree
   HostTree t;
   std::string err;
   if (t.build(d, n_flags, flags, &err)) return PIC_EINVAL;
+  if (t.depth > 12 && !t.uniform) return PIC_EINVAL;  // as pic_create
   t.build_grid();
   t.build_pidt();
   sizes->d = t.d;

@@ -520,9 +520,15 @@ void HostTree::build_pidt() {
     }
     rm_max_t[t] = mx;
   });
+  // one stable sort by level * (rm_max + 1) + rm: the order of a sort by rm
+  // followed by a stable sort by level, in fewer passes (adaptive trees have
+  // at most 12 levels, so rm < 3^36 and the key stays below 2^61)
   const uint64_t rm_max = *std::max_element(rm_max_t.begin(), rm_max_t.end());
-  radix_sort(r, nlc, rm_max, [](const Rec &x) { return x.rm; });
-  radix_sort(r, nlc, 31, [](const Rec &x) { return (uint64_t)x.lev; });
+  const uint64_t span = rm_max + 1;
+  int lev_max = 0;
+  for (int64_t l = 0; l < n_leaves; ++l) lev_max = std::max(lev_max, (int)level[leaf_node[l]]);
+  radix_sort(r, nlc, (uint64_t)lev_max * span + rm_max,
+             [span](const Rec &x) { return (uint64_t)x.lev * span + x.rm; });
   // distinct pairs in order: new pairs counted per chunk, then offsets
   auto is_new = [&](int64_t i) { return i == 0 || r[i].lev != r[i - 1].lev || r[i].rm != r[i - 1].rm; };
   std::vector<int64_t> first(nt + 1, 0);

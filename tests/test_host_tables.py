@@ -70,3 +70,14 @@ def test_host_tables_do_not_depend_on_thread_count(d, flags_fn, monkeypatch):
     assert one.keys() == seven.keys()
     for k in one:
         assert np.array_equal(np.asarray(one[k]), np.asarray(seven[k])), k
+
+
+def test_host_tables_reject_adaptive_trees_deeper_than_level_12():
+    _lib_or_skip()
+    # a chain of first children refined down to level 13 in 2D
+    flags = []
+    for level in range(13):
+        flags += [1] + [0] * (8 if level else 0)
+    flags += [0] * 9
+    with pytest.raises(pic.PicError):
+        pic.tree_tables(2, np.array(flags, np.uint8))
