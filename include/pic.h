@@ -147,10 +147,22 @@ typedef void *(*pic_alloc_fn)(void *user, size_t bytes, void *stream);
 typedef void (*pic_free_fn)(void *user, void *ptr, size_t bytes, void *stream);
 PIC_API int pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_fn, void *user);
 
-/* Create a handle on the current CUDA device: validate and tabulate the tree,
- * copy the particles, bin them (initial key + stable bucket sort). */
+/* Create a handle on the current CUDA device: the problem statement of
+ * Section 3 (particles with positions and velocities in a domain covered by
+ * a spacetree, Section 4) and of Section 5's introduction (every particle held
+ * by the leaf, PIT, or the vertex, PIDT, that covers it).  Validates and
+ * tabulates the tree (refined nodes with 3^d children, depth <= 18, d in
+ * {2, 3}; else PIC_EINVAL), copies the particles (host or device per
+ * parts->where; non-finite values: PIC_ERANGE), and bins them: initial key
+ * (Theorem 1 / Theorem 2 end state) and stable bucket sort (every particle
+ * counts as moved, so buckets keep input order).  *out receives the handle,
+ * NULL on failure.  Memory: PIC_ENOMEM; CUDA failures: PIC_ECUDA. */
 PIC_API int pic_create(pic_t *out, const pic_tree_desc *tree, const pic_particles_desc *parts,
                const pic_config *cfg);
+/* Free every device buffer of the handle (through the allocator it was
+ * created with) after its stream has drained; NULL is ignored.  The paper's
+ * grid and particle containers have no counterpart to release: a library
+ * utility. */
 PIC_API void pic_destroy(pic_t h);
 PIC_API const char *pic_strerror(int code);
 PIC_API const char *pic_last_error(pic_t h);
@@ -205,26 +217,57 @@ PIC_API int pic_autotune(pic_t h, double dt, int32_t trials, int32_t *tuned);
 PIC_API int pic_set_tuning(pic_t h, const int32_t *tuned);
 PIC_API int pic_get_tuning(pic_t h, int32_t *tuned);
 
-/* Wait for the handle's stream; returns the sticky device error if any. */
+/* Wait for the handle's stream; returns the sticky device error if any
+ * (PIC_ERANGE, PIC_ETIMEOUT when a bounded device wait gave up). */
 PIC_API int pic_sync(pic_t h);
 
-/* Vertex charges Q[n_vertices] of the current positions (FP64 values, also in
- * split mode) and the field E[d][n_vertices] of the last solve. */
+/* Failure detection of device waits (no counterpart in the paper; a library
+ * safeguard).  Every device-side wait of the library is bounded: the brick
+ * kernels wait for their bulk copies at most `cycles` SM clocks (default 4e9,
+ * about two seconds), then record PIC_ETIMEOUT (reported by pic_sync) and
+ * return after the copies in flight have landed, leaving the context usable.
+ * pic_set_wait_limit sets the limit of the handle's later steps (1e3 <=
+ * cycles <= 2^40, else PIC_EINVAL) and drops captured graphs.
+ * pic_wait_selftest runs, on `stream`, one CTA whose barrier expects 16 bytes
+ * that are never sent and waits for them with the same bounded wait: it
+ * returns PIC_ETIMEOUT when the wait gave up and the kernel returned (the
+ * expected outcome), PIC_OK if the barrier completed, PIC_ECUDA on a CUDA
+ * error.  Synchronous; allocates one 4-byte flag. */
+PIC_API int pic_set_wait_limit(pic_t h, int64_t cycles);
+PIC_API int pic_wait_selftest(int64_t cycles, void *stream);
+
+/* Vertex charges Q[n_vertices] of the current positions: Section 3 item 1,
+ * rho = sum_i R(x_i) with d-linear R on the leaf that covers x_i, as the
+ * finite-element load Q_v = q sum_i phi_v(x_i) + ion integral(phi_v) (hanging
+ * vertices pass their share to the vertices of the coarse face).  FP64 values
+ * in both precisions, summed in a fixed order (no floating-point atomics), so
+ * the result is run-to-run identical.  Q_out is caller-owned, host or device
+ * per `where`.  Computes the deposit if the positions changed since the last
+ * one.  pic_field / pic_potential return E[d][n_vertices] and V[n_vertices]
+ * of the last solve (Section 3 items 2-3). */
 PIC_API int pic_deposit(pic_t h, double *Q_out, int32_t where);
 PIC_API int pic_field(pic_t h, double *E_out, int32_t where);
 PIC_API int pic_potential(pic_t h, double *V_out, int32_t where);
 
-/* Buckets after the last re-bin: bucket_start[n_buckets + 1] offsets into the
- * storage order and perm[n] the input particle id stored at each position
- * (needs track_ids; else perm may be NULL). */
+/* Buckets after the last re-bin -- the association of particles with leaves
+ * (PIT, Section 5.1) or dual cells of vertices (PIDT, Section 5.2), stored as
+ * the paper's per-cell particle arrays (Section 4.2) in one CSR layout:
+ * bucket_start[n_keys + 1] offsets into the storage order (PIT: one bucket
+ * per leaf; PIDT: per owner vertex and quadrant, key = vertex 2^d + quadrant)
+ * and perm[n] the input particle id stored at each position (needs
+ * track_ids, else PIC_ESTATE when perm is not NULL).  Caller-owned, host or
+ * device per `where`. */
 PIC_API int pic_bins(pic_t h, int64_t *bucket_start, int32_t *perm, int32_t where);
 
 /* Sort keys per particle in storage order (leaf id, or owner vertex * 2^d +
  * quadrant for PIDT). */
 PIC_API int pic_keys(pic_t h, int32_t *keys, int32_t where);
 
-/* Particles in storage order: absolute FP64 positions (split mode:
- * (c + o) / 3^level) and FP64 velocities, [d][n]. */
+/* Particles in storage order: absolute FP64 positions x[d][n] in [0, 1)^d
+ * (split mode: (c + o) / 3^level from the leaf coordinates c and the cell
+ * offset o) and FP64 velocities v[d][n] -- the particle state of Section 3
+ * (position and velocity per particle).  Caller-owned, host or device per
+ * `where`; either pointer may be NULL. */
 PIC_API int pic_get_particles(pic_t h, double *x, double *v, int32_t where);
 
 /* Native state in storage order, for checkpoints and host round trips.
@@ -235,9 +278,12 @@ PIC_API int pic_get_state(pic_t h, int32_t *leaf, void *x_or_o, void *v, int32_t
 PIC_API int pic_set_state(pic_t h, const int32_t *leaf, const void *x_or_o, const void *v,
                   int32_t where);
 
-/* Counters of the last step (movers, largest bucket), the FP64 charge total
- * of the last deposit (neutrality check), the residual norm of the last
- * built-in solve, the step count and the sticky device error.  Synchronous. */
+/* Counters of the last step: movers (particles whose key changed -- the
+ * PIDT `moved` flag of Section 5.2, for PIT the particles that left their
+ * leaf), the largest bucket, the FP64 charge total of the last deposit (the
+ * neutrality check of Section 3 item 1 against the ion background of
+ * Appendix A), the residual norm of the last built-in solve (item 2), the
+ * step count and the sticky device error.  Synchronous. */
 PIC_API int pic_stats(pic_t h, pic_stats_t *out);
 
 /* Lift and drop counts of Algorithm 1 (the paper's cost measure for particle
@@ -280,10 +326,14 @@ PIC_API int pic_leaf_table(pic_t h, int32_t *level, int64_t *coords);
 PIC_API int pic_vertex_table(pic_t h, int64_t *pos);
 PIC_API int pic_pidt_table(pic_t h, int32_t *level, int64_t *j);
 
-/* Replace the tree (same d) and re-bin the particles into it.  FP64
- * particles keep their positions; split particles are re-located with the
- * integer lift/drop rule of the split push (zero displacement).  The solver's
- * warm start and the field are reset.  Synchronous. */
+/* Replace the tree (same d) and re-bin the particles into it: the dynamic
+ * adaptivity of Section 5's introduction (the grid changes between steps and
+ * every particle is lifted and dropped into the leaf or dual cell of the new
+ * grid that covers it; Theorems 1 and 2 hold for any tree).  FP64 particles
+ * keep their positions; split particles are re-located with the integer
+ * lift/drop rule of the split push (zero displacement).  The solver's warm
+ * start and the field are reset.  Malformed tree or other d: PIC_EINVAL.
+ * Synchronous. */
 PIC_API int pic_retree(pic_t h, const pic_tree_desc *tree);
 
 /* Level-order refinement flags of the current tree: with flags == NULL only
@@ -357,8 +407,11 @@ PIC_API int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax);
  * shared by every caller in the process: calls on one device that overlap in
  * time (different streams or host threads) race and must be serialised by
  * the caller.  The first call on each device looks the array's address up
- * (cudaGetSymbolAddress); make that first call outside any stream capture.
- * No statement is made about capturing later calls in a CUDA graph.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call outside any stream capture, and make no call on a device after
+ * cudaDeviceReset() on it (the module, and with it the array, is reloaded at
+ * another address).  No statement is made about capturing later calls in a
+ * CUDA graph.  Crowded buckets cost O(m log^2 m) for a bucket of m elements.
  *
  * Returns PIC_EINVAL for n < 0, n > INT32_MAX, n_keys < 1, NULL pointers, or
  * n_keys > PIC_NOALLOC_MAX_KEYS (nothing is launched); PIC_ECUDA if a CUDA

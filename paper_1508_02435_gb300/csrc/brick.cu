@@ -29,6 +29,7 @@
 
 #include "dev.cuh"
 #include "launch.hpp"
+#include "segsort.cuh"
 
 namespace pic {
 
@@ -95,7 +96,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long l
   } while (!done && clock64() - t0 < cycles);
   return done != 0;
 }
-constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at the maximum SM clock
+// Limit of the wait that lets copies still in flight land before a CTA that
+// gave up returns (its shared memory must outlive them): about two seconds at
+// the maximum SM clock, whatever limit the first wait had.
+constexpr long long kWaitCycles = 4000000000LL;
 constexpr int kErrTimeout = 8;                   // error bit: a bounded device wait gave up
 constexpr int kErrCode = 16;                     // error bit: a staged leaf code outside its unit, or counts that disagree
 
@@ -461,7 +465,7 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
   }
   cp_async_wait_all();
   __syncthreads();  // the barrier is initialised and armed before anyone waits on it
-  const bool landed = nb == 0 || mbar_wait(&s_bar, 0, kWaitCycles);
+  const bool landed = nb == 0 || mbar_wait(&s_bar, 0, a.wait_cycles);
   if (__syncthreads_or(!landed)) {
     if (!landed) mbar_wait(&s_bar, 0, kWaitCycles);  // let copies in flight land before leaving
     if (tid == 0) atomicOr(a.err, kErrTimeout);
@@ -826,7 +830,7 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
   for (int i = tid; i <= nlf; i += blockDim.x) cnt[i] = 0;
   __syncthreads();  // the barrier is initialised and armed before anyone waits on it
   {
-    const bool landed = nin == 0 || mbar_wait(&s_bar, 0, kWaitCycles);
+    const bool landed = nin == 0 || mbar_wait(&s_bar, 0, a.wait_cycles);
     if (__syncthreads_or(!landed)) {
       if (!landed) mbar_wait(&s_bar, 0, kWaitCycles);  // let copies in flight land before leaving
       if (tid == 0) atomicOr(a.err, kErrTimeout);
@@ -908,17 +912,8 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
       for (int t2 = 0; t2 < m; ++t2) r += __shfl_sync(0xffffffffu, kx, t2) < kx;
       __syncwarp();
       if (lane < m) map[lo + r] = (uint16_t)i;
-    } else if (lane == 0) {  // insertion sort by one thread (crowded leaves only)
-      for (int32_t x = lo + 1; x < lo + m; ++x) {
-        const uint16_t v = map[x];
-        const uint32_t kv = key[v];
-        int32_t y = x - 1;
-        while (y >= lo && key[map[y]] > kv) {
-          map[y + 1] = map[y];
-          --y;
-        }
-        map[y + 1] = v;
-      }
+    } else {  // crowded leaves: the warp runs a bitonic network over the leaf's slots
+      warp_sort_indirect<uint16_t, uint32_t>(map + lo, m, key);
     }
     __syncwarp();
   }
@@ -997,12 +992,18 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
 
 // K2 for units over their staging capacity: the staging area (first cap
 // arrivals) and the unit's overflow arrivals; a counting sort by leaf in
-// global scratch (fb_key / fb_idx at the unit's output range), per-leaf
-// insertion sort by key, then gathers in bucket order.  Arrival r < cap is
+// global scratch (fb_key / fb_idx at the unit's output range), a per-leaf
+// sort by key (insertion by one thread up to kPullSmallLeaf arrivals, the
+// block's bitonic network above), then gathers in bucket order.  Arrival r < cap is
 // staging slot r, arrival cap + k the unit's k-th overflow entry.
+constexpr int kPullSmallLeaf = 32;  // leaves up to this many arrivals: one thread's insertion sort
+constexpr int kPullChunk = 2048;    // (key, index) pairs of a crowded leaf sorted at once in shared memory
+
 template <int D>
 __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeom g, BrickPullArgs a) {
   using K = BK<D>;
+  __shared__ uint32_t sk[kPullChunk];
+  __shared__ int32_t sv[kPullChunk];
   __shared__ int32_t cnt[K::LH + 1];
   __shared__ int32_t cur[K::LH];
   __shared__ int32_t wsum[kPullThreads / 32];
@@ -1065,6 +1066,7 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
   for (int l = tid; l < nlf; l += blockDim.x) {
     a.new_start[L0 + l] = bstart + cnt[l];
     const int32_t lo = bstart + cnt[l], hi = bstart + cnt[l + 1];
+    if (hi - lo > kPullSmallLeaf) continue;  // crowded: sorted by the whole block below
     for (int32_t i = lo + 1; i < hi; ++i) {
       const uint32_t kx = a.fb_key[i];
       const int32_t vx = a.fb_idx[i];
@@ -1077,6 +1079,11 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
       a.fb_key[j + 1] = kx;
       a.fb_idx[j + 1] = vx;
     }
+  }
+  __syncthreads();
+  for (int l = 0; l < nlf; ++l) {  // crowded leaves, one at a time, by the whole block
+    const int32_t lo = bstart + cnt[l], m = cnt[l + 1] - cnt[l];
+    if (m > kPullSmallLeaf) block_sort_global<uint32_t, int32_t>(a.fb_key + lo, a.fb_idx + lo, m, sk, sv, kPullChunk);
   }
   if (u == 2 * g.n_bricks - 1 && tid == 0) a.new_start[(int64_t)g.n_bricks * K::LB] = bstart + nin;
   if (tid == 0 && s_max > 0) atomicMax(a.max_bucket, s_max);
@@ -1177,6 +1184,28 @@ void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPullArgs
     k_brick_pull<2><<<(unsigned)nu, kPullThreads, 0, s>>>(t, g, qa);
   }
   count_launches(5);  // overflow count, overflow scatter, totals, two pull kernels (the scans count themselves)
+}
+
+// Self-test of the bounded wait: the barrier expects 16 bytes and no copy is
+// ever issued, so the wait must give up after `cycles` and the kernel return.
+__global__ void k_wait_selftest(long long cycles, int32_t *flag) {
+  __shared__ uint64_t s_bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    mbar_expect_tx(&s_bar, 16);
+  }
+  __syncthreads();  // initialised and armed before anyone waits
+  const bool done = mbar_wait(&s_bar, 0, cycles);
+  if (__syncthreads_or(!done)) {
+    if (threadIdx.x == 0) *flag = 1;
+  } else if (threadIdx.x == 0) {
+    *flag = 2;
+  }
+}
+
+void launch_wait_selftest(long long cycles, int32_t *flag, cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(cycles, flag);
+  count_launches(1);
 }
 
 void launch_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf, cudaStream_t s) {

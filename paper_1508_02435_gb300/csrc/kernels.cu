@@ -21,6 +21,7 @@
 
 #include "dev.cuh"
 #include "launch.hpp"
+#include "segsort.cuh"
 
 namespace pic {
 
@@ -31,6 +32,7 @@ constexpr int kBlock = 256;
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
+static_assert(kScanTile == kScanTileElems, "scan tile size disagrees with launch.hpp");
 
 static std::atomic<int64_t> g_launches{0};
 int64_t launches() { return g_launches.load(); }
@@ -702,8 +704,8 @@ __global__ void k_mover_slots(const int32_t *movers, const int32_t *n_movers, co
 // The movers of every bucket in storage order (undoes the atomic slot order).
 // Segments longer than kSmallSeg are listed for k_sort_large.
 constexpr int kSmallSeg = 32;
-constexpr int kLargeSeg = 16384;     // longest segment sorted in shared memory
-constexpr int kLargeThreads = 256;
+constexpr int kLargeSeg = 16384;     // chunk of a long segment sorted in shared memory
+constexpr int kLargeThreads = 1024;
 __global__ void k_sort_segments(const int32_t *new_start, const int32_t *n_stay, int64_t n_keys, int32_t *perm,
                                 int32_t *large, int32_t *n_large) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -724,9 +726,9 @@ __global__ void k_sort_segments(const int32_t *new_start, const int32_t *n_stay,
   }
 }
 
-// One block per long segment (grid-stride over the list): a bitonic sort in
-// shared memory, padded to a power of two; longer than kLargeSeg, one thread
-// sorts by insertion.
+// One block per long segment (grid-stride over the list): the in-place
+// bitonic network of segsort.cuh, chunks of kLargeSeg in shared memory, so a
+// bucket of any size sorts in O(m log^2 m).
 __global__ void __launch_bounds__(kLargeThreads) k_sort_large(const int32_t *new_start, const int32_t *n_stay,
                                                               const int32_t *large, const int32_t *n_large,
                                                               int32_t *perm) {
@@ -735,40 +737,7 @@ __global__ void __launch_bounds__(kLargeThreads) k_sort_large(const int32_t *new
   for (int li = blockIdx.x; li < nl; li += gridDim.x) {
     const int32_t k = large[li];
     const int32_t b = new_start[k] + n_stay[k], m = new_start[k + 1] - b;
-    if (m > kLargeSeg) {
-      if (threadIdx.x == 0)
-        for (int32_t i = b + 1; i < b + m; ++i) {
-          const int32_t x = perm[i];
-          int32_t j = i - 1;
-          while (j >= b && perm[j] > x) {
-            perm[j + 1] = perm[j];
-            --j;
-          }
-          perm[j + 1] = x;
-        }
-      __syncthreads();
-      continue;
-    }
-    int P = 1;
-    while (P < m) P <<= 1;
-    for (int i = threadIdx.x; i < P; i += blockDim.x) sv[i] = i < m ? perm[b + i] : INT32_MAX;
-    __syncthreads();
-    for (int kk = 2; kk <= P; kk <<= 1)
-      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        for (int i = threadIdx.x; i < P; i += blockDim.x) {
-          const int l = i ^ jj;
-          if (l > i) {
-            const int32_t x = sv[i], y = sv[l];
-            const bool up = (i & kk) == 0;
-            if ((x > y) == up) {
-              sv[i] = y;
-              sv[l] = x;
-            }
-          }
-        }
-        __syncthreads();
-      }
-    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[b + i] = sv[i];
+    block_sort_global<int32_t, int32_t>(perm + b, nullptr, m, sv, nullptr, kLargeSeg);
     __syncthreads();
   }
 }

@@ -54,6 +54,10 @@ struct RebinArgs {
   int block;                     // threads per block of the push (ballot words, block counts)
 };
 
+// Elements per tile of launch_exclusive_scan: a scan of n elements writes
+// scan_tiles_needed(n) = ceil(n / kScanTileElems) tile sums.
+constexpr int64_t kScanTileElems = 8192;
+
 // Kernels launched by this library so far (all handles of the process).
 int64_t launches();
 void count_launches(int64_t k);
@@ -96,6 +100,7 @@ struct BrickPushArgs {
   BrickStage st;
   int32_t *n_movers;
   int32_t *err;
+  long long wait_cycles;         // limit of the bounded wait for the bulk copies (SM clocks)
 };
 
 struct BrickPullArgs {
@@ -117,6 +122,7 @@ struct BrickPullArgs {
   float *part;                   // leaf-corner deposit partials of the new positions, or NULL
   uint32_t *fb_key;              // [n] scratch of the global-memory kernel
   int32_t *fb_idx;
+  long long wait_cycles;         // limit of the bounded wait for the bulk copies (SM clocks)
 };
 
 cudaError_t brick_configure(const BrickGeom &g);
@@ -125,6 +131,10 @@ void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs
 void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPullArgs &qa, int32_t *fcount,
                        int32_t *fcursor, int32_t *tile_sums, int32_t *scratch_total, cudaStream_t s);
 void launch_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf, cudaStream_t s);
+// One CTA arms an mbarrier for 16 bytes that are never sent and waits for it
+// with the bounded wait of the brick kernels (limit `cycles`); *flag becomes
+// 1 when the wait gave up (the expected outcome), 2 if it completed.
+void launch_wait_selftest(long long cycles, int32_t *flag, cudaStream_t s);
 
 cudaError_t set_constants(cudaStream_t s);
 cudaError_t set_kref(int d, cudaStream_t s);

@@ -3,12 +3,13 @@
 // every particle is a mover) on scratch that lives in a file-scope device
 // array instead of memory obtained from the allocator.
 //
-// Scratch layout (int32 words, 256-byte aligned): the per-bucket counts, which
-// become the per-bucket fill cursors after the scan, then the scan's tile
-// sums, then its total.  The call clears the counts itself on the caller's
-// stream before using them, so nothing has to be zero on entry.  One array
-// per device serves every caller of the process: calls that overlap in time
-// (different streams or host threads on one device) race on it.
+// The call clears every part of the scratch it reads before using it, on the
+// caller's stream, so nothing has to be zero on entry.  One array per device
+// serves every caller of the process: calls that overlap in time (different
+// streams or host threads on one device) race on it.  Buckets are put in
+// input order by a per-thread insertion sort up to 32 elements and by an
+// in-place bitonic network above (O(m log^2 m), no extra memory), so a call
+// with few keys and many elements stays fast.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -17,13 +18,16 @@
 
 #include "../../include/pic.h"
 #include "launch.hpp"
+#include "segsort.cuh"
 
 namespace pic {
 namespace {
 
-constexpr int64_t kTileWords = 8192;  // elements per scan tile of launch_exclusive_scan
-constexpr int64_t kMaxTiles = (PIC_NOALLOC_MAX_KEYS + kTileWords - 1) / kTileWords;
-constexpr int64_t kScratchWords = PIC_NOALLOC_MAX_KEYS + kMaxTiles + 64;
+// Scratch layout: counts (later fill cursors, later the list of crowded
+// buckets) | scan tile sums | scan total | crowded-bucket count | spare.
+constexpr int64_t kMaxTiles = (PIC_NOALLOC_MAX_KEYS + kScanTileElems - 1) / kScanTileElems;
+constexpr int64_t kScratchWords = PIC_NOALLOC_MAX_KEYS + 192;
+static_assert(kMaxTiles + 2 < 192, "scan tile sums and totals overrun the scratch tail");
 
 static __device__ __align__(256) int32_t g_bucket_scratch[kScratchWords];
 
@@ -60,11 +64,18 @@ __global__ void k_na_fill(const int32_t *keys, int64_t n, int64_t n_keys, const 
   }
 }
 
-// Restores input order inside every bucket (the fill's atomic order is arbitrary).
-__global__ void k_na_order(const int32_t *start, int64_t n_keys, int32_t *perm) {
+// Restores input order inside every bucket (the fill's atomic order is
+// arbitrary): buckets of at most kSmallBucket elements by one thread, longer
+// ones are listed for k_na_order_large.
+constexpr int kSmallBucket = 32;
+__global__ void k_na_order(const int32_t *start, int64_t n_keys, int32_t *perm, int32_t *large, int32_t *n_large) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_keys) return;
   const int32_t b = start[k], e = start[k + 1];
+  if (e - b > kSmallBucket) {
+    large[atomicAdd(n_large, 1)] = (int32_t)k;
+    return;
+  }
   for (int32_t i = b + 1; i < e; ++i) {
     int32_t x = perm[i], j = i - 1;
     while (j >= b && perm[j] > x) {
@@ -72,6 +83,23 @@ __global__ void k_na_order(const int32_t *start, int64_t n_keys, int32_t *perm) 
       --j;
     }
     perm[j + 1] = x;
+  }
+}
+
+// One block per crowded bucket (grid-stride over the list): in-place bitonic
+// network, chunks of kOrderChunk in shared memory; O(m log^2 m) for a bucket
+// of m elements, no memory beyond the bucket's own range of perm.
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderChunk = 8192;
+__global__ void __launch_bounds__(kOrderThreads) k_na_order_large(const int32_t *start, const int32_t *large,
+                                                                  const int32_t *n_large, int32_t *perm) {
+  __shared__ int32_t sk[kOrderChunk];
+  const int nl = *n_large;
+  for (int li = blockIdx.x; li < nl; li += gridDim.x) {
+    const int32_t k = large[li];
+    const int32_t b = start[k], m = start[k + 1] - b;
+    block_sort_global<int32_t, int32_t>(perm + b, nullptr, m, sk, nullptr, kOrderChunk);
+    __syncthreads();
   }
 }
 
@@ -89,7 +117,8 @@ extern "C" int pic_bucket_noalloc(const int32_t *keys, int64_t n, int64_t n_keys
   if (rc) return rc;
   int32_t *count = scratch;
   int32_t *tile_sums = scratch + PIC_NOALLOC_MAX_KEYS;
-  int32_t *total = tile_sums + kMaxTiles + 1;
+  int32_t *total = tile_sums + kMaxTiles;
+  int32_t *n_large = total + 1;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int threads = 256;
   const unsigned grid = (unsigned)(n > 0 ? std::min<int64_t>((n + threads - 1) / threads, 152 * 8) : 1);
@@ -98,7 +127,9 @@ extern "C" int pic_bucket_noalloc(const int32_t *keys, int64_t n, int64_t n_keys
   launch_exclusive_scan(count, n_keys, start, tile_sums, total, s);
   if (cudaMemsetAsync(count, 0, sizeof(int32_t) * n_keys, s) != cudaSuccess) return PIC_ECUDA;
   k_na_fill<<<grid, threads, 0, s>>>(keys, n, n_keys, start, count, perm);
-  k_na_order<<<(unsigned)((n_keys + threads - 1) / threads), threads, 0, s>>>(start, n_keys, perm);
-  count_launches(3);
+  if (cudaMemsetAsync(n_large, 0, sizeof(int32_t), s) != cudaSuccess) return PIC_ECUDA;
+  k_na_order<<<(unsigned)((n_keys + threads - 1) / threads), threads, 0, s>>>(start, n_keys, perm, count, n_large);
+  k_na_order_large<<<152, kOrderThreads, 0, s>>>(start, count, n_large, perm);
+  count_launches(4);
   return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }

@@ -68,6 +68,7 @@ struct pic_s {
 
   int64_t step = 0;
   std::string last_error;
+  long long wait_cycles = 4000000000LL;  // bounded device waits of the brick kernels (pic_set_wait_limit)
 
   // lift and drop counts of the steps (pic_count_lifts; PIT, tracked ids)
   bool count_lifts = false;
@@ -574,6 +575,7 @@ int brick_push_and_rebin(pic_t h, double dt) {
   pa.st.ovf_id = h->ids[1];
   pa.n_movers = h->scalars + 1;
   pa.err = h->err;
+  pa.wait_cycles = h->wait_cycles;
   // the pull reads only the staging area and the overflow list, so the new
   // bucket order is written over the current state in place
   BrickPullArgs qa{};
@@ -596,6 +598,7 @@ int brick_push_and_rebin(pic_t h, double dt) {
   qa.part = (float *)h->part;
   qa.fb_key = h->fb_key;
   qa.fb_idx = h->fb_idx;
+  qa.wait_cycles = h->wait_cycles;
   CK(cudaMemsetAsync(h->scalars + 1, 0, sizeof(int32_t) * 2, s));
   {
     PhaseScope ps(h, PIC_PHASE_PUSH);
@@ -1310,6 +1313,34 @@ int pic_autotune(pic_t h, double dt, int32_t trials, int32_t *tuned) {
   if (rc2) return rc2;
   if (tuned) std::copy(pick.begin(), pick.end(), tuned);
   return PIC_OK;
+}
+
+int pic_set_wait_limit(pic_t h, int64_t cycles) {
+  if (check_handle(h)) return PIC_EINVAL;
+  if (cycles < 1000 || cycles > (int64_t)1 << 40) return fail(h, PIC_EINVAL, "wait limit outside [1e3, 2^40] cycles");
+  h->wait_cycles = (long long)cycles;
+  drop_graphs(h);  // captured launches carry the old limit
+  return PIC_OK;
+}
+
+int pic_wait_selftest(int64_t cycles, void *stream) {
+  if (cycles < 1 || cycles > (int64_t)1 << 40) return PIC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int32_t *flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(int32_t)) != cudaSuccess) return PIC_ENOMEM;
+  int32_t got = 0;
+  int rc = PIC_OK;
+  if (cudaMemsetAsync(flag, 0, sizeof(int32_t), s) != cudaSuccess) rc = PIC_ECUDA;
+  if (!rc) {
+    launch_wait_selftest((long long)cycles, flag, s);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&got, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = PIC_ECUDA;
+  }
+  cudaFree(flag);
+  if (rc) return rc;
+  return got == 1 ? PIC_ETIMEOUT : (got == 2 ? PIC_OK : PIC_ECUDA);
 }
 
 int pic_sync(pic_t h) {

@@ -109,6 +109,8 @@ SIGNATURES = [
     ("pic_lift_counts", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_save", C.c_int, [C.c_void_p, C.c_char_p]),
     ("pic_load", C.c_int, [C.POINTER(C.c_void_p), C.c_char_p, C.c_void_p]),
+    ("pic_set_wait_limit", C.c_int, [C.c_void_p, C.c_int64]),
+    ("pic_wait_selftest", C.c_int, [C.c_int64, C.c_void_p]),
 ]
 
 
@@ -234,6 +236,13 @@ def stream_step(x, v, dt: float, steps: int = 1, stream=None):
         raise PicError(rc, lib.pic_strerror(rc).decode())
 
 
+def wait_selftest(cycles: int, stream=None) -> int:
+    """Run the bounded-wait self-test kernel (pic_wait_selftest); returns the
+    library's code: PIC_ETIMEOUT (-5) when the wait gave up as designed."""
+    st = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
+    return int(load().pic_wait_selftest(int(cycles), C.c_void_p(st)))
+
+
 def bucket_noalloc(keys, n_keys: int, start, perm, stream=None):
     """Stable bucket sort of device int32 `keys` into the caller's device
     tensors start[n_keys + 1] and perm[len(keys)], with no device allocation
@@ -242,6 +251,20 @@ def bucket_noalloc(keys, n_keys: int, start, perm, stream=None):
     n = int(keys.numel())
     if n_keys > NOALLOC_MAX_KEYS:
         raise PicError(-1, f"n_keys = {n_keys} is above the fixed scratch of {NOALLOC_MAX_KEYS} buckets")
+    # the kernels write start[0..n_keys] and perm[0..n) through raw pointers:
+    # check every tensor before anything is launched
+    import torch
+    for name, t in (("keys", keys), ("start", start), ("perm", perm)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.int32 or not t.is_cuda or not t.is_contiguous():
+            raise PicError(-1, f"{name} must be a contiguous int32 CUDA tensor")
+        if t.device != keys.device:
+            raise PicError(-1, f"{name} is on {t.device}, keys on {keys.device}")
+    if keys.device.index != torch.cuda.current_device():
+        raise PicError(-1, f"keys are on {keys.device}, the current device is cuda:{torch.cuda.current_device()}")
+    if start.numel() < n_keys + 1:
+        raise PicError(-1, f"start holds {start.numel()} entries, n_keys + 1 = {n_keys + 1} needed")
+    if perm.numel() < n:
+        raise PicError(-1, f"perm holds {perm.numel()} entries, len(keys) = {n} needed")
     st = stream.cuda_stream if stream is not None and hasattr(stream, "cuda_stream") else stream
     rc = lib.pic_bucket_noalloc(C.c_void_p(keys.data_ptr()), n, int(n_keys), C.c_void_p(start.data_ptr()),
                                 C.c_void_p(perm.data_ptr()), C.c_void_p(st))
@@ -393,6 +416,10 @@ class Pic:
 
     def sync(self):
         self._check(self.lib.pic_sync(self.h))
+
+    def set_wait_limit(self, cycles: int):
+        """Limit (SM clocks) of the bounded device waits of later steps."""
+        self._check(self.lib.pic_set_wait_limit(self.h, int(cycles)))
 
     def count_lifts(self, enable: bool = True):
         """Start (from zero) or stop counting the lifts and drops of every

@@ -53,3 +53,16 @@ def test_set_allocator_takes_both_callbacks_or_neither():
     finally:
         pic.use_torch_allocator(False)
     assert lib.pic_set_allocator(pic.ALLOC_FN(), pic.FREE_FN(), None) == 0
+
+
+def test_bucket_noalloc_checks_tensors_on_the_host():
+    """Host tensors, a wrong dtype or short outputs are refused by the binding
+    before the library is called (no device needed)."""
+    torch = pytest.importorskip("torch")
+    keys = torch.zeros(10, dtype=torch.int32)
+    start = torch.zeros(5, dtype=torch.int32)
+    perm = torch.zeros(10, dtype=torch.int32)
+    for k, s, p in ((keys, start, perm), (keys.to(torch.int64), start, perm), (keys, start[:2], perm)):
+        with pytest.raises(pic.PicError) as e:
+            pic.bucket_noalloc(k, 4, s, p)
+        assert e.value.code == -1
