@@ -48,6 +48,8 @@ struct BK {
   static constexpr int B = 9, V1 = 10;
   static constexpr int LB = D == 3 ? 729 : 81;
   static constexpr int NVB = D == 3 ? 1000 : 100;
+  static constexpr int LSW = (LB + 4 + 3) & ~3;   // leaf-offset words in shared memory (head + LB + 1)
+  static constexpr int DECW = (LB + 3) & ~3;      // decode-table words (a multiple of four)
   static constexpr int NC = 1 << D;
   static constexpr int LH = (LB + 1) / 2;  // leaves of the first destination half (local leaves [0, LH))
 };
@@ -100,6 +102,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long l
 // gave up returns (its shared memory must outlive them): about two seconds at
 // the maximum SM clock, whatever limit the first wait had.
 constexpr long long kWaitCycles = 4000000000LL;
+
 constexpr int kErrTimeout = 8;                   // error bit: a bounded device wait gave up
 constexpr int kErrCode = 16;                     // error bit: a staged leaf code outside its unit, or counts that disagree
 
@@ -300,11 +303,20 @@ constexpr int kHS = kHalfCap + 8;    // shared row stride (room for a 16-byte al
 // First storage offset (within the brick) of half h of a brick holding nb particles.
 __host__ __device__ __forceinline__ int32_t half_start(int32_t nb, int h) { return h == 0 ? 0 : (nb + 1) / 2; }
 
+// Shared-memory offsets of K1's bulk-copy targets must be multiples of 16 bytes.
+template <int D>
+constexpr size_t push_st_off_field() { return sizeof(float) * 2 * D * kHS + sizeof(uint16_t) * kHalfCap; }
+static_assert(push_st_off_field<3>() % 16 == 0 && push_st_off_field<2>() % 16 == 0, "field staging misaligned");
+static_assert((push_st_off_field<3>() + 16 * BK<3>::NVB) % 16 == 0 && (push_st_off_field<2>() + 8 * BK<2>::NVB) % 16 == 0,
+              "leaf offsets misaligned");
+static_assert(BK<3>::LSW % 4 == 0 && BK<2>::LSW % 4 == 0 && BK<3>::DECW % 4 == 0 && BK<2>::DECW % 4 == 0,
+              "decode table misaligned");
+
 template <int D>
 size_t push_st_smem() {
   using K = BK<D>;
   return sizeof(float) * 2 * D * kHS + sizeof(uint16_t) * kHalfCap + sizeof(typename EVec<D>::T) * K::NVB +
-         sizeof(int32_t) * (K::LB + 1) + sizeof(uint32_t) * K::LB + sizeof(int32_t) * (3 * 32 + 32) +
+         sizeof(int32_t) * K::LSW + sizeof(uint32_t) * K::DECW + sizeof(int32_t) * (3 * 32 + 32) +
          sizeof(uint8_t) * kHalfCap + sizeof(int32_t) * (kHThreads / 32) * kUnitSlots;
 }
 
@@ -366,127 +378,46 @@ __device__ __forceinline__ void stage_append(const BrickStage &st, int32_t dest,
   if (dest >= 0) stage_put<D>(st, dest, slot, on, vn, code, key, id, with_id, err);
 }
 
-// K1, shared-memory form, one CTA per half brick.  Same arithmetic as
+// A half brick in shared memory, as one warp of K1 sees it.
+template <int D>
+struct HalfView {
+  float *so, *sv;                   // offset and velocity rows (row r starts at so + r kHS)
+  int32_t offO[D], offV[D];         // index of the half's particle 0 in each row
+  uint16_t *pos;                    // local leaf of every particle, then its destination code
+  uint8_t *lslot;                   // rank within (warp, unit slot)
+  const typename EVec<D>::T *Eb;    // the brick's field, one vector per vertex
+  const uint32_t *dec;              // local leaf -> x | y << 10 | z << 20
+  const int32_t *rel, *nbr;         // per-axis re-location table; neighbour bricks by direction
+  int32_t nb, hs;                   // particles of the half; storage index of its first
+  int32_t origin[3], bc[3];         // first leaf cell of the brick; brick coordinates
+};
+
+// One warp's share of a half brick in K1: pass A pushes the warp's chunks
+// (chunk c = first, first + stride, ...), pass B appends them to the
+// destination units' staging areas after one reservation per unit.  wc holds
+// the warp's kUnitSlots counters (zero on entry).  Same arithmetic as
 // push_core (gather in corner order, kick, drift, split re-location), with
-// the brick's field staged as one vector per vertex and the destination found
-// from the brick-local cell through a per-axis table.
+// the destination found from the brick-local cell through a per-axis table.
 template <int D, bool kAligned>
-__global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, BrickGeom g, BrickPushArgs a) {
+__device__ __forceinline__ void push_half_warp(const DevTree &t, const BrickGeom &g, const BrickPushArgs &a,
+                                               const HalfView<D> &hv, int first, int stride, int32_t *wc,
+                                               bool &bad, int &movers) {
   using K = BK<D>;
   using EV = typename EVec<D>::T;
-  constexpr int kW = kHThreads / 32;
-  extern __shared__ __align__(128) float smf[];
-  float *so = smf;                                   // D rows of kHS offsets
-  float *sv = so + D * kHS;                          // D rows of kHS velocities
-  uint16_t *pos = (uint16_t *)(sv + D * kHS);        // local leaf of every particle of the half
-  EV *Eb = (EV *)(pos + kHalfCap);                   // NVB staged field vectors
-  int32_t *ls = (int32_t *)(Eb + K::NVB);            // LB + 1 absolute leaf offsets
-  uint32_t *dec = (uint32_t *)(ls + K::LB + 1);      // LB
-  int32_t *rel = (int32_t *)(dec + K::LB);           // 3 x 32: per-axis direction | leaf-index parts
-  int32_t *nbr = rel + 3 * 32;                       // 27 neighbour bricks by direction
-  int32_t *wc = nbr + 32;                            // [warp][unit slot] arrivals, then first slot
-  uint8_t *lslot = (uint8_t *)(wc + kW * kUnitSlots); // rank within (warp, unit slot)
-  __shared__ int32_t s_movers;
-  __shared__ uint64_t s_bar;
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int32_t b = blockIdx.x >> 1, h = blockIdx.x & 1, L0 = b * K::LB;
-  const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nbr_n = pe - ps;
-  if (nbr_n > 2 * kHalfCap) return;  // the global-memory kernel takes this brick
-  const int32_t q0 = half_start(nbr_n, h), q1 = h ? nbr_n : half_start(nbr_n, 1), nb = q1 - q0;
-  const int32_t hs = ps + q0;  // storage index of this half's first particle
-  const int64_t n = a.n;
-  int32_t origin[3] = {0, 0, 0}, bc[3] = {0, 0, 0};
-#pragma unroll
-  for (int ax = 0; ax < D; ++ax) {
-    origin[ax] = t.leaf_coords[(int64_t)L0 * D + ax];
-    bc[ax] = origin[ax] / K::B;
-  }
-  // every global -> shared copy is issued before any is awaited
-  for (int i = tid; i <= K::LB; i += blockDim.x) cp_async4(ls + i, a.start + L0 + i);
-  for (int i = tid; i < K::LB; i += blockDim.x) cp_async4(dec + i, g.decodeL + i);
-  for (int i = tid; i < K::NVB; i += blockDim.x) {
-    int lx = i % K::V1, ly = (i / K::V1) % K::V1, lz = D == 3 ? i / (K::V1 * K::V1) : 0;
-    int32_t gx = origin[0] + lx, gy = origin[1] + ly, gz = D == 3 ? origin[2] + lz : 0;
-    if (gx >= t.M) gx -= t.M;
-    if (gy >= t.M) gy -= t.M;
-    if (gz >= t.M) gz -= t.M;
-    const int64_t vid = gx + (int64_t)t.M * (gy + (int64_t)t.M * gz);
-    float *slot = (float *)(Eb + i);
-#pragma unroll
-    for (int ax = 0; ax < D; ++ax) cp_async4(slot + ax, a.E + ax * t.n_vert + vid);
-  }
-  if (tid < 3 * 27) {  // local cell l - 9 on axis tid / 27: (direction digit + 1) 3^axis << 16 | leaf part
-    const int ax = tid / 27, loc = tid % 27 - K::B;
-    const int dl = (loc >= K::B) - (loc < 0);
-    const int p3 = ax == 0 ? 1 : (ax == 1 ? 3 : 9);
-    rel[ax * 32 + tid % 27] = ((dl + 1) * p3 << 16) | lidx_axis<D>(loc - K::B * dl, ax);
-  } else if (tid >= 128 && tid < 128 + 27) {  // neighbour brick in direction tid - 128
-    const int dir = tid - 128;
-    int32_t sc[3] = {0, 0, 0};
-    for (int ax = 0; ax < D; ++ax) {
-      const int32_t x = bc[ax] + dir_delta(dir, ax);
-      sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
-    }
-    nbr[dir] = (D == 2 && dir_delta(dir, 2) != 0) ? -1 : brick_of_coords<D>(t, sc);
-  }
-  // the half's particle rows: one bulk copy per row from the 16-byte boundary
-  // at or below its first particle; row r holds particle q at index off[r] + q
-  int32_t offO[D], offV[D];
-#pragma unroll
-  for (int r = 0; r < 2 * D; ++r) {
-    const float *src = (r < D ? a.o + r * n : a.v + (r - D) * n) + hs;
-    const int32_t head = (int32_t)(((uintptr_t)src & 15u) >> 2);
-    if (r < D) offO[r] = r * kHS + head;
-    else offV[r - D] = (r - D) * kHS + head;
-  }
-  const int32_t h0 = offO[0];
-  auto O = [&](int ax, int32_t q) -> float & { return kAligned ? so[ax * kHS + h0 + q] : so[offO[ax] + q]; };
-  auto V = [&](int ax, int32_t q) -> float & { return kAligned ? sv[ax * kHS + h0 + q] : sv[offV[ax] + q]; };
-  for (int i = tid; i < kW * kUnitSlots; i += blockDim.x) wc[i] = 0;
-  if (tid == 0) {
-    s_movers = 0;
-    if (nb > 0) {
-      mbar_init(&s_bar, 1);
-      uint32_t total = 0, bytes[2 * D];
-      const float *src[2 * D];
-#pragma unroll
-      for (int r = 0; r < 2 * D; ++r) {
-        const float *p = (r < D ? a.o + r * n : a.v + (r - D) * n) + hs;
-        const uintptr_t a0 = (uintptr_t)p & ~(uintptr_t)15;
-        src[r] = (const float *)a0;
-        bytes[r] = (uint32_t)(((uintptr_t)(p + nb) - a0 + 15u) & ~(uintptr_t)15);
-        total += bytes[r];
-      }
-      mbar_expect_tx(&s_bar, total);
-#pragma unroll
-      for (int r = 0; r < 2 * D; ++r)
-        bulk_g2s(r < D ? so + r * kHS : sv + (r - D) * kHS, src[r], bytes[r], &s_bar);
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();  // the barrier is initialised and armed before anyone waits on it
-  const bool landed = nb == 0 || mbar_wait(&s_bar, 0, a.wait_cycles);
-  if (__syncthreads_or(!landed)) {
-    if (!landed) mbar_wait(&s_bar, 0, kWaitCycles);  // let copies in flight land before leaving
-    if (tid == 0) atomicOr(a.err, kErrTimeout);
-    return;
-  }
-  for (int l = tid; l < K::LB; l += blockDim.x) {
-    const int32_t lo = max(ls[l] - hs, 0), hi = min(ls[l + 1] - hs, nb);
-    for (int32_t q = lo; q < hi; ++q) pos[q] = (uint16_t)l;
-  }
-  __syncthreads();
-
+  const int lane = threadIdx.x & 31;
+  const int32_t nb = hv.nb, hs = hv.hs;
+  const int32_t h0 = hv.offO[0];
+  auto O = [&](int ax, int32_t q) -> float & { return kAligned ? hv.so[ax * kHS + h0 + q] : hv.so[hv.offO[ax] + q]; };
+  auto V = [&](int ax, int32_t q) -> float & { return kAligned ? hv.sv[ax * kHS + h0 + q] : hv.sv[hv.offV[ax] + q]; };
+  uint16_t *pos = hv.pos;
   // pass A: push every particle once; the new state goes back to its shared
   // slot and its leaf code gains the destination direction (bits 10-14).  Its
   // unit slot (direction, destination half) and its rank among the arrivals
   // of its warp for that slot are noted; per-warp counts go to wc[].  The
   // pull restores the canonical order, so any order of the slots will do.
   // Arrivals beyond the neighbour bricks are appended at once.
-  bool bad = false;
-  int movers = 0;
   const int nc32 = (nb + 31) >> 5;
-  for (int c = w; c < nc32; c += kW) {
+  for (int c = first; c < nc32; c += stride) {
     const int32_t q = c * 32 + lane;
     const bool act = q < nb;
     int uslot = -1;  // unit slot 2 direction + destination half; -1: none (idle lane, far arrival)
@@ -494,7 +425,7 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
       float on[D], vn[D];
       int dir;
       const int l = pos[q];
-      const uint32_t pk = dec[l];
+      const uint32_t pk = hv.dec[l];
       const int32_t lc[3] = {(int32_t)(pk & 1023u), (int32_t)((pk >> 10) & 1023u), (int32_t)(pk >> 20)};
       float o[D], om[D];
 #pragma unroll
@@ -528,11 +459,12 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
       for (int ax = 0; ax < D; ++ax) E[ax] = 0.0f;
 #pragma unroll
       for (int e = 0; e < K::NC; ++e) {
-        const EV ev = Eb[base + (e & 1) + ((e >> 1) & 1) * K::V1 + ((e >> 2) & 1) * K::V1 * K::V1];
+        const EV ev = hv.Eb[base + (e & 1) + ((e >> 1) & 1) * K::V1 + ((e >> 2) & 1) * K::V1 * K::V1];
 #pragma unroll
         for (int ax = 0; ax < D; ++ax) E[ax] = E[ax] + wgt[e] * ecomp(ev, ax);
       }
-      // kick and drift: v += (q/m) dt E, t = o + v s_l
+      // kick and drift: v += (q/m) dt E, t = o + v s_l.  t is non-finite
+      // whenever the new velocity is (s_l is finite), so checking t suffices.
       float fl[D];
       int32_t packed = D == 2 ? (9 << 16) : 0;
       bool win = true;
@@ -540,7 +472,7 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
       for (int ax = 0; ax < D; ++ax) {
         vn[ax] = V(ax, q) + a.qmdt * E[ax];
         float tt = o[ax] + vn[ax] * a.sl;
-        if (!isfinite(vn[ax]) || !isfinite(tt)) {
+        if (!isfinite(tt)) {
           bad = true;
           tt = 0.0f;
         }
@@ -548,7 +480,7 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
         on[ax] = clamp_off(tt - fl[ax]);
         const uint32_t li = (uint32_t)(lc[ax] + K::B + (int32_t)fmaxf(fminf(fl[ax], 64.0f), -64.0f));
         win &= li < 3u * K::B;
-        packed += rel[ax * 32 + (li < 3u * K::B ? li : 0u)];
+        packed += hv.rel[ax * 32 + (li < 3u * K::B ? li : 0u)];
       }
       int lidx;
       int32_t dest = -1;
@@ -560,8 +492,8 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
 #pragma unroll
         for (int ax = 0; ax < D; ++ax) {
           in.lc[ax] = lc[ax];
-          in.origin[ax] = origin[ax];
-          in.bc[ax] = bc[ax];
+          in.origin[ax] = hv.origin[ax];
+          in.bc[ax] = hv.bc[ax];
           in.fl[ax] = fl[ax];
         }
         const SlowOut r = relocate_slow<D>(t, g, in);
@@ -590,24 +522,24 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
     const int leader = uslot >= 0 ? __ffs(peers) - 1 : lane;
     int32_t r0 = 0;
     if (uslot >= 0 && lane == leader) {  // one leader per distinct slot: distinct words
-      r0 = wc[w * kUnitSlots + uslot];
-      wc[w * kUnitSlots + uslot] = r0 + __popc(peers);
+      r0 = wc[uslot];
+      wc[uslot] = r0 + __popc(peers);
     }
     r0 = __shfl_sync(0xffffffffu, r0, leader);
-    if (uslot >= 0) lslot[q] = (uint8_t)(r0 + __popc(peers & ((1u << lane) - 1u)));
+    if (uslot >= 0) hv.lslot[q] = (uint8_t)(r0 + __popc(peers & ((1u << lane) - 1u)));
     __syncwarp();  // the counts are read by other lanes in the next chunk
   }
   // the warp reserves its runs in the destination units' staging areas (one
   // atomic per unit it sends to; the count becomes the run's first slot)
   for (int us = lane; us < 54; us += 32) {
-    const int32_t c = wc[w * kUnitSlots + us];
-    if (c > 0) wc[w * kUnitSlots + us] = atomicAdd(&a.st.fill[2 * nbr[us >> 1] + (us & 1)], c);
+    const int32_t c = wc[us];
+    if (c > 0) wc[us] = atomicAdd(&a.st.fill[2 * hv.nbr[us >> 1] + (us & 1)], c);
   }
   __syncwarp();
   // pass B, the warp's own chunks: every arrival to its reserved slot
   // (consecutive particles of a chunk hold consecutive ranks, so the stores
   // coalesce)
-  for (int c = w; c < nc32; c += kW) {
+  for (int c = first; c < nc32; c += stride) {
     const int32_t q = c * 32 + lane;
     if (q >= nb) break;
     const uint16_t cd = pos[q];
@@ -615,7 +547,7 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
     if (dir == kFarSlot) continue;
     const int hh = (cd & 0x3ff) >= K::LH;
     const int us = 2 * dir + hh;
-    const int32_t slot = wc[w * kUnitSlots + us] + lslot[q];
+    const int32_t slot = wc[us] + hv.lslot[q];
     float on[D], vn[D];
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
@@ -623,10 +555,144 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
       vn[ax] = V(ax, q);
     }
     const bool stay = (cd & kStayBit) != 0;
-    stage_put<D>(a.st, 2 * nbr[dir] + hh, slot, on, vn, (uint16_t)(cd & (kStayBit | 0x3ff)),
+    stage_put<D>(a.st, 2 * hv.nbr[dir] + hh, slot, on, vn, (uint16_t)(cd & (kStayBit | 0x3ff)),
                  (stay ? 0u : 0x80000000u) | (uint32_t)(hs + q), a.ids ? a.ids[hs + q] : 0, a.ids != nullptr,
                  a.err);
   }
+  __syncwarp();
+  for (int us = lane; us < kUnitSlots; us += 32) wc[us] = 0;  // ready for the warp's next half brick
+  __syncwarp();
+}
+
+// Per-axis re-location table of K1: for local cell l - 9 (l = 0 .. 26) on
+// axis ax, (direction digit + 1) 3^ax << 16 | the cell's part of the leaf
+// index; computed by threads 0 .. 80.
+template <int D>
+__device__ __forceinline__ void fill_rel(int32_t *rel, int tid) {
+  using K = BK<D>;
+  if (tid < 3 * 27) {
+    const int ax = tid / 27, loc = tid % 27 - K::B;
+    const int dl = (loc >= K::B) - (loc < 0);
+    const int p3 = ax == 0 ? 1 : (ax == 1 ? 3 : 9);
+    rel[ax * 32 + tid % 27] = ((dl + 1) * p3 << 16) | lidx_axis<D>(loc - K::B * dl, ax);
+  }
+}
+
+// Neighbour brick of brick coordinates bc in direction dir (-1 for the
+// directions a 2D brick does not have).
+template <int D>
+__device__ __forceinline__ int32_t neighbour_brick(const DevTree &t, const BrickGeom &g, const int32_t *bc, int dir) {
+  int32_t sc[3] = {0, 0, 0};
+  for (int ax = 0; ax < D; ++ax) {
+    const int32_t x = bc[ax] + dir_delta(dir, ax);
+    sc[ax] = x < 0 ? x + g.nbx : (x >= g.nbx ? x - g.nbx : x);
+  }
+  return (D == 2 && dir_delta(dir, 2) != 0) ? -1 : brick_of_coords<D>(t, sc);
+}
+
+// K1, shared-memory form, one CTA per half brick: its copies land, the leaf
+// map is built, and every warp pushes its share (push_half_warp).
+template <int D, bool kAligned>
+__global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, BrickGeom g, BrickPushArgs a) {
+  using K = BK<D>;
+  using EV = typename EVec<D>::T;
+  constexpr int kW = kHThreads / 32;
+  extern __shared__ __align__(128) float smf[];
+  float *so = smf;                                   // D rows of kHS offsets
+  float *sv = so + D * kHS;                          // D rows of kHS velocities
+  uint16_t *pos = (uint16_t *)(sv + D * kHS);        // local leaf of every particle of the half
+  EV *Eb = (EV *)(pos + kHalfCap);                   // NVB staged field vectors (16-byte aligned)
+  int32_t *lsb = (int32_t *)(Eb + K::NVB);           // LB + 1 absolute leaf offsets after a head of < 4
+  uint32_t *dec = (uint32_t *)(lsb + K::LSW);        // LB (padded to DECW words)
+  int32_t *rel = (int32_t *)(dec + K::DECW);         // 3 x 32: per-axis direction | leaf-index parts
+  int32_t *nbr = rel + 3 * 32;                       // 27 neighbour bricks by direction
+  int32_t *wc = nbr + 32;                            // [warp][unit slot] arrivals, then first slot
+  uint8_t *lslot = (uint8_t *)(wc + kW * kUnitSlots); // rank within (warp, unit slot)
+  __shared__ int32_t s_movers;
+  __shared__ uint64_t s_bar;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int32_t b = blockIdx.x >> 1, h = blockIdx.x & 1, L0 = b * K::LB;
+  const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nbr_n = pe - ps;
+  if (nbr_n > 2 * kHalfCap) return;  // the global-memory kernel takes this brick
+  const int32_t q0 = half_start(nbr_n, h), q1 = h ? nbr_n : half_start(nbr_n, 1), nb = q1 - q0;
+  const int32_t hs = ps + q0;  // storage index of this half's first particle
+  const int64_t n = a.n;
+  if (nb == 0) return;  // an empty half: nothing to push
+  HalfView<D> hv;
+  hv.so = so;
+  hv.sv = sv;
+  hv.pos = pos;
+  hv.lslot = lslot;
+  hv.Eb = Eb;
+  hv.dec = dec;
+  hv.rel = rel;
+  hv.nbr = nbr;
+  hv.nb = nb;
+  hv.hs = hs;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    hv.origin[ax] = ax < D ? t.leaf_coords[(int64_t)L0 * D + ax] : 0;
+    hv.bc[ax] = hv.origin[ax] / K::B;
+  }
+  fill_rel<D>(rel, tid);
+  if (tid >= 128 && tid < 128 + 27) nbr[tid - 128] = neighbour_brick<D>(t, g, hv.bc, tid - 128);
+  // the half's particle rows: one bulk copy per row from the 16-byte boundary
+  // at or below its first particle; row r holds particle q at index off[r] + q
+#pragma unroll
+  for (int r = 0; r < 2 * D; ++r) {
+    const float *src = (r < D ? a.o + r * n : a.v + (r - D) * n) + hs;
+    const int32_t head = (int32_t)(((uintptr_t)src & 15u) >> 2);
+    if (r < D) hv.offO[r] = r * kHS + head;
+    else hv.offV[r - D] = (r - D) * kHS + head;
+  }
+  // the brick's leaf offsets start at the 16-byte boundary at or below L0
+  const int32_t lhead = (int32_t)(((uintptr_t)(a.start + L0) & 15u) >> 2);
+  const int32_t *ls = lsb + lhead;
+  for (int i = tid; i < kW * kUnitSlots; i += blockDim.x) wc[i] = 0;
+  if (tid == 0) {
+    // every global -> shared copy is one bulk copy, issued before any is
+    // awaited: the particle rows of the half, the brick's leaf offsets, the
+    // local-leaf decode table and the brick's field (one vector per vertex,
+    // laid out brick by brick when the field was set)
+    s_movers = 0;
+    mbar_init(&s_bar, 1);
+    uint32_t total = 0, bytes[2 * D];
+    const float *src[2 * D];
+#pragma unroll
+    for (int r = 0; r < 2 * D; ++r) {
+      const float *p = (r < D ? a.o + r * n : a.v + (r - D) * n) + hs;
+      const uintptr_t a0 = (uintptr_t)p & ~(uintptr_t)15;
+      src[r] = (const float *)a0;
+      bytes[r] = (uint32_t)(((uintptr_t)(p + nb) - a0 + 15u) & ~(uintptr_t)15);
+      total += bytes[r];
+    }
+    const int32_t *ls0 = a.start + L0 - lhead;
+    const uint32_t lbytes = (uint32_t)(((lhead + K::LB + 1) * 4 + 15) & ~15);
+    constexpr uint32_t dbytes = K::DECW * 4, ebytes = K::NVB * sizeof(EV);
+    total += lbytes + dbytes + ebytes;
+    mbar_expect_tx(&s_bar, total);
+#pragma unroll
+    for (int r = 0; r < 2 * D; ++r)
+      bulk_g2s(r < D ? so + r * kHS : sv + (r - D) * kHS, src[r], bytes[r], &s_bar);
+    bulk_g2s(lsb, ls0, lbytes, &s_bar);
+    bulk_g2s(dec, g.decodeL, dbytes, &s_bar);
+    bulk_g2s(Eb, (const EV *)a.Ebrick + (int64_t)b * K::NVB, ebytes, &s_bar);
+  }
+  __syncthreads();  // the barrier is initialised and armed before anyone waits on it
+  const bool landed = mbar_wait(&s_bar, 0, a.wait_cycles);
+  if (__syncthreads_or(!landed)) {
+    if (!landed) mbar_wait(&s_bar, 0, kWaitCycles);  // let copies in flight land before leaving
+    if (tid == 0) atomicOr(a.err, kErrTimeout);
+    return;
+  }
+  for (int l = tid; l < K::LB; l += blockDim.x) {
+    const int32_t lo = max(ls[l] - hs, 0), hi = min(ls[l + 1] - hs, nb);
+    for (int32_t q = lo; q < hi; ++q) pos[q] = (uint16_t)l;
+  }
+  __syncthreads();
+  bool bad = false;
+  int movers = 0;
+  push_half_warp<D, kAligned>(t, g, a, hv, w, kW, wc + w * kUnitSlots, bad, movers);
   if (bad) atomicOr(a.err, 1);
   for (int o = 16; o > 0; o >>= 1) movers += __shfl_down_sync(0xffffffffu, movers, o);
   if (lane == 0) atomicAdd(&s_movers, movers);
@@ -1150,19 +1216,16 @@ void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs
   cudaMemsetAsync(pa.st.fill, 0, sizeof(int32_t) * 2 * g.n_bricks, s);
   cudaMemsetAsync(pa.st.ovf_n, 0, sizeof(int32_t), s);
   const unsigned nb = (unsigned)g.n_bricks;
+  const bool al = pa.n % 4 == 0;
   if (g.d == 3) {
-    if (pa.n % 4 == 0)
-      k_brick_push_st<3, true><<<2 * nb, kHThreads, push_st_smem<3>(), s>>>(t, g, pa);
-    else
-      k_brick_push_st<3, false><<<2 * nb, kHThreads, push_st_smem<3>(), s>>>(t, g, pa);
-    k_brick_push<3><<<nb, kPushThreads, 0, s>>>(t, g, pa);
+    if (al) k_brick_push_st<3, true><<<2 * nb, kHThreads, push_st_smem<3>(), s>>>(t, g, pa);
+    else k_brick_push_st<3, false><<<2 * nb, kHThreads, push_st_smem<3>(), s>>>(t, g, pa);
   } else {
-    if (pa.n % 4 == 0)
-      k_brick_push_st<2, true><<<2 * nb, kHThreads, push_st_smem<2>(), s>>>(t, g, pa);
-    else
-      k_brick_push_st<2, false><<<2 * nb, kHThreads, push_st_smem<2>(), s>>>(t, g, pa);
-    k_brick_push<2><<<nb, kPushThreads, 0, s>>>(t, g, pa);
+    if (al) k_brick_push_st<2, true><<<2 * nb, kHThreads, push_st_smem<2>(), s>>>(t, g, pa);
+    else k_brick_push_st<2, false><<<2 * nb, kHThreads, push_st_smem<2>(), s>>>(t, g, pa);
   }
+  if (g.d == 3) k_brick_push<3><<<nb, kPushThreads, 0, s>>>(t, g, pa);
+  else k_brick_push<2><<<nb, kPushThreads, 0, s>>>(t, g, pa);
   count_launches(2);
 }
 
@@ -1205,6 +1268,38 @@ __global__ void k_wait_selftest(long long cycles, int32_t *flag) {
 
 void launch_wait_selftest(long long cycles, int32_t *flag, cudaStream_t s) {
   k_wait_selftest<<<1, 32, 0, s>>>(cycles, flag);
+  count_launches(1);
+}
+
+template <int D>
+__global__ void k_brick_field(DevTree t, BrickGeom g, const float *__restrict__ E,
+                              typename EVec<D>::T *__restrict__ out) {
+  using K = BK<D>;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.n_bricks * K::NVB) return;
+  const int64_t b = i / K::NVB;
+  const int v = (int)(i - b * K::NVB);
+  const int lx = v % K::V1, ly = (v / K::V1) % K::V1, lz = D == 3 ? v / (K::V1 * K::V1) : 0;
+  const int64_t L0 = b * K::LB;
+  int32_t gx = t.leaf_coords[L0 * D + 0] + lx, gy = t.leaf_coords[L0 * D + 1] + ly;
+  int32_t gz = D == 3 ? t.leaf_coords[L0 * D + 2] + lz : 0;
+  if (gx >= t.M) gx -= t.M;
+  if (gy >= t.M) gy -= t.M;
+  if (gz >= t.M) gz -= t.M;
+  const int64_t vid = gx + (int64_t)t.M * (gy + (int64_t)t.M * gz);
+  if constexpr (D == 3)
+    out[i] = make_float4(E[vid], E[t.n_vert + vid], E[2 * t.n_vert + vid], 0.0f);
+  else
+    out[i] = make_float2(E[vid], E[t.n_vert + vid]);
+}
+
+void launch_brick_field(const DevTree &t, const BrickGeom &g, const float *E, float *Ebrick, cudaStream_t s) {
+  const int64_t m = g.n_bricks * (g.d == 3 ? BK<3>::NVB : BK<2>::NVB);
+  const unsigned grid = (unsigned)((m + 255) / 256);
+  if (g.d == 3)
+    k_brick_field<3><<<grid, 256, 0, s>>>(t, g, E, (float4 *)Ebrick);
+  else
+    k_brick_field<2><<<grid, 256, 0, s>>>(t, g, E, (float2 *)Ebrick);
   count_launches(1);
 }
 

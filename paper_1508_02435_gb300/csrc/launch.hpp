@@ -96,6 +96,7 @@ struct BrickPushArgs {
   const int32_t *start;          // current leaf offsets
   const int32_t *ids;            // NULL unless ids are tracked
   const float *E;
+  const void *Ebrick;            // the field brick by brick: (9+1)^d vertices per brick, float4 (3D) / float2 (2D)
   float qmdt, sl;
   BrickStage st;
   int32_t *n_movers;
@@ -131,6 +132,10 @@ void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs
 void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPullArgs &qa, int32_t *fcount,
                        int32_t *fcursor, int32_t *tile_sums, int32_t *scratch_total, cudaStream_t s);
 void launch_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf, cudaStream_t s);
+// The vertex field E[d][n_vert] re-laid brick by brick for K1: brick b holds
+// the (9+1)^d vertices from its origin on (periodic), x fastest, one vector
+// (E_x, E_y[, E_z, 0]) per vertex.
+void launch_brick_field(const DevTree &t, const BrickGeom &g, const float *E, float *Ebrick, cudaStream_t s);
 // One CTA arms an mbarrier for 16 bytes that are never sent and waits for it
 // with the bounded wait of the brick kernels (limit `cycles`); *flag becomes
 // 1 when the wait gave up (the expected outcome), 2 if it completed.

@@ -65,6 +65,8 @@ struct pic_s {
   void *Ep = nullptr;  // d * n scratch (gather at the particles, FP64 staging)
   float4 *ecorner = nullptr;  // split, adaptive: field at every leaf corner
   bool ecorner_valid = false; // ecorner holds the corners of the current E
+  float *ebrick = nullptr;    // brick path: the field brick by brick (float4 / float2 per vertex)
+  bool ebrick_valid = false;  // ebrick holds the current E
 
   int64_t step = 0;
   std::string last_error;
@@ -379,8 +381,9 @@ int alloc_state(pic_t h) {
     }
     if ((rc = dalloc(h, sb, &h->ids[s], n))) return rc;
   }
-  if ((rc = dalloc(h, sb, &h->start_cur, nk + 1))) return rc;
-  if ((rc = dalloc(h, sb, &h->start_new, nk + 1))) return rc;
+  // bucket offsets, padded: the brick kernels copy whole 16-byte units of them
+  if ((rc = dalloc(h, sb, &h->start_cur, nk + 8))) return rc;
+  if ((rc = dalloc(h, sb, &h->start_new, nk + 8))) return rc;
   if ((rc = dalloc(h, sb, &h->count, nk))) return rc;
   if ((rc = dalloc(h, sb, &h->n_stay, nk))) return rc;
   if ((rc = dalloc(h, sb, &h->cursor, nk))) return rc;
@@ -490,7 +493,7 @@ int setup_brick(pic_t h) {
   g.nbx = (int)pow3(t.depth - g.kb);
   g.n_bricks = 1;
   for (int a = 0; a < t.d; ++a) g.n_bricks *= g.nbx;
-  std::vector<uint32_t> dec(g.LB);
+  std::vector<uint32_t> dec((g.LB + 3) & ~3, 0u);  // padded to whole 16-byte units (one bulk copy)
   for (int l = 0; l < g.LB; ++l) {
     uint32_t c[3] = {0, 0, 0};
     int rest = l;
@@ -525,6 +528,10 @@ int setup_brick(pic_t h) {
   if ((rc = dalloc(h, bb, &st.key, st.row))) return rc;
   if (h->cfg.track_ids && (rc = dalloc(h, bb, &st.id, st.row))) return rc;
   if ((rc = dalloc(h, bb, &st.fill, nu))) return rc;
+  // the field laid out brick by brick, one vector per vertex of the brick
+  // and its upper faces ((9+1)^d vertices), refreshed whenever E changes
+  if ((rc = dalloc(h, bb, &h->ebrick, g.n_bricks * (t.d == 3 ? 1000 * 4 : 100 * 2)))) return rc;
+  h->ebrick_valid = false;
   if ((rc = dalloc(h, bb, &st.ovf_n, 1))) return rc;
   // overflow list: one entry per particle at most; offsets, velocities and
   // ids in the pushed-state rows, which the brick step leaves unused (set per
@@ -567,6 +574,11 @@ int brick_push_and_rebin(pic_t h, double dt) {
   pa.start = h->start_cur;
   pa.ids = h->cfg.track_ids ? h->ids[0] : nullptr;
   pa.E = (const float *)h->E;
+  if (!h->ebrick_valid) {
+    launch_brick_field(h->dt, h->bg, (const float *)h->E, h->ebrick, s);
+    h->ebrick_valid = true;
+  }
+  pa.Ebrick = h->ebrick;
   pa.qmdt = (float)(h->cfg.qm * dt);
   pa.sl = (float)(dt * (double)pow3(h->ht.depth));
   pa.st = h->stage;
@@ -712,6 +724,7 @@ int field(pic_t h, pic_solve_fn hook, void *user) {
   PhaseScope ps(h, PIC_PHASE_SOLVE);
   cudaStream_t s = h->stream;
   h->ecorner_valid = false;  // E changes below
+  h->ebrick_valid = false;
   if (hook) {
     int r = hook(user, h->Q, h->E, h->dt.n_vert, h->split ? PIC_FP32_SPLIT : PIC_FP64, (void *)s);
     if (r != 0) return fail(h, PIC_EHOOK, "field-solve hook returned " + std::to_string(r));
@@ -1236,6 +1249,7 @@ int snapshot_restore(pic_t h, const Snapshot &sn) {
 }
 
 int apply_tuning(pic_t h, const int32_t *t) {
+  if (t[0] != 0 && t[0] != 1) return fail(h, PIC_EINVAL, "path is 0 (generic) or 1 (brick)");
   if (t[0] == 1 && !h->brick_ok) return fail(h, PIC_EINVAL, "the brick path does not apply to this handle");
   for (int i = 1; i < 4; ++i)
     if (t[i] != 128 && t[i] != 256 && t[i] != 512) return fail(h, PIC_EINVAL, "block sizes are 128, 256 or 512");
@@ -1899,6 +1913,7 @@ int pic_load(pic_t *out, const char *path, void *stream) {
       (rc = copy_in(h, h->E, a.E.data(), a.E.size(), PIC_HOST)))
     return bail(rc, "");
   h->ecorner_valid = false;
+  h->ebrick_valid = false;
   if ((rc = apply_tuning(h, m.tuned))) return bail(rc, "");
   h->step = m.step;
   int32_t err = 0;
