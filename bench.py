@@ -38,18 +38,15 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 at 16 particles per cell.
 STEP_BYTES = {(3, 1): 70.0, (3, 0): 132.0, (2, 1): 48.5, (2, 0): 89.0}
 
-# DRAM bytes per particle that ncu measured for the dominant kernel (read +
-# write, one launch, divided by the particles it moved), valid only for the
-# kernel sources whose digest is stored beside it; see profiles/.  The push
-# and vertex-sum kernels are unchanged since the counters were taken; the
-# re-bin kernel's leaf sort changed since (its entry keeps the older digest,
-# so it reads as unmeasured).
-MEASURED_TRAFFIC = {
-    ("langmuir3d", "push"): {"bytes_per_particle": 57.68, "digest": "48217a120c57b8ac"},
-    ("langmuir3d", "rebin"): {"bytes_per_particle": 58.22, "digest": "de2c87e1b8a0272b"},
-    ("langmuir3d", "deposit"): {"bytes_per_particle": 4.48, "digest": "48217a120c57b8ac"},
-}
-KERNEL_SOURCES = ("paper_1508_02435_gb300/csrc/brick.cu", "paper_1508_02435_gb300/csrc/dev.cuh")
+# DRAM traffic that ncu measured per launch of each brick kernel, stored in
+# profiles/ as CSV by `bench.py --ingest-ncu` together with the digest of the
+# kernel sources at capture time; a row whose digest differs from the current
+# sources is stale and reads as unmeasured.
+TRAFFIC_CSV = os.path.join(ROOT, "profiles", "dram_traffic_langmuir3d_243cubed_8ppc.csv")
+KERNEL_SOURCES = ("paper_1508_02435_gb300/csrc/brick.cu", "paper_1508_02435_gb300/csrc/dev.cuh",
+                  "paper_1508_02435_gb300/csrc/segsort.cuh", "paper_1508_02435_gb300/csrc/kernels.cu",
+                  "paper_1508_02435_gb300/csrc/launch.hpp")
+PHASE_KERNEL = {"push": "k_brick_push_st", "rebin": "k_brick_pull_st", "deposit": "k_vertex_charge"}
 
 
 def kernel_digest() -> str:
@@ -59,6 +56,55 @@ def kernel_digest() -> str:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def measured_traffic(workload: str, kernel: str):
+    """(bytes per launch, row) of the kernel from the committed CSV when it
+    was captured from the current sources, else (None, row or None)."""
+    import csv
+    try:
+        rows = [r for r in csv.DictReader(ln for ln in open(TRAFFIC_CSV) if not ln.startswith("#"))]
+    except OSError:
+        return None, None
+    for r in rows:
+        if r["workload"] == workload and r["kernel"] == kernel:
+            if r["sources_digest"] != kernel_digest():
+                return None, r
+            return (float(r["read_bytes"]) + float(r["write_bytes"])) / float(r["launches"]), r
+    return None, None
+
+
+def ingest_ncu(path: str, workload: str, particles: int) -> str:
+    """CSV rows (one per brick kernel) from an ncu --csv log of the metrics
+    dram__bytes_read.sum, dram__bytes_write.sum and gpu__time_duration.sum,
+    stamped with the digest of the current kernel sources."""
+    import csv
+    acc = {}
+    lines = [ln for ln in open(path) if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        name = r.get("Kernel Name", "")
+        for k in PHASE_KERNEL.values():
+            if name.startswith("void pic::" + k + "<") or name.startswith(k + "<") or name.startswith("void " + k) \
+                    or ("::" + k + "<") in name or name.startswith(k + "("):
+                d = acc.setdefault(k, {"ids": set(), "read": 0.0, "write": 0.0, "ns": 0.0})
+                d["ids"].add(r["ID"])
+                v = float(r["Metric Value"].replace(",", ""))
+                unit = r.get("Metric Unit", "")
+                scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1, "usecond": 1e3,
+                         "msecond": 1e6}.get(unit, 1)
+                if r["Metric Name"] == "dram__bytes_read.sum":
+                    d["read"] += v * scale
+                elif r["Metric Name"] == "dram__bytes_write.sum":
+                    d["write"] += v * scale
+                elif r["Metric Name"] == "gpu__time_duration.sum":
+                    d["ns"] += v * scale
+    out = ["# DRAM bytes of the brick kernels per ncu capture (dram__bytes_read.sum + dram__bytes_write.sum,",
+           "# --clock-control none); written by bench.py --ingest-ncu from the capture's CSV log",
+           "workload,kernel,launches,read_bytes,write_bytes,duration_ns,particles,sources_digest"]
+    for k, d in acc.items():
+        out.append(f"{workload},{k},{len(d['ids'])},{d['read']:.0f},{d['write']:.0f},{d['ns']:.0f},{particles},"
+                   f"{kernel_digest()}")
+    return "\n".join(out) + "\n"
 
 
 def brick_bytes(d: int, ppc: float, track_ids: bool) -> dict:
@@ -86,19 +132,25 @@ def brick_bytes(d: int, ppc: float, track_ids: bool) -> dict:
     }
 
 
-def kernel_bytes(d: int, split: bool, ppc: float) -> dict:
-    """Algorithmic bytes per particle of each phase as the kernels implement it:
-    what each phase must read and write, grid arrays amortised over ppc."""
+def step_shares(d: int, split: bool, ppc: float, brick: bool) -> dict:
+    """Each phase's share of the algorithmic bytes of one particle-step (the
+    STEP_BYTES of the method: deposit read of the positions, state read,
+    state write, grid terms amortised over ppc), by which phase moves them.
+      brick path: push reads the state and the field (K1), rebin writes the
+        state and sums the deposit partials of the new positions from shared
+        memory (K2: the deposit's read of the positions happens there),
+        deposit sums the partials into vertex charges;
+      generic path: deposit reads the positions, push reads the state and
+        the field, permute writes the state; the re-bin bookkeeping moves no
+        algorithmic bytes."""
     f = 4 if split else 8
-    state = (d * 2 * f + 4)                       # position/offset + velocity + leaf
-    grid_e = d * f / ppc                          # vertex field, read once
-    nc = 1 << d
-    return {
-        "deposit": d * f + (nc * f) / ppc * 2 + f / ppc,   # offsets + leaf partials w/r + Q
-        "push": state + grid_e + state + 4,                # state in, field, state out, key
-        "rebin": 4 + 4 + 4 + 4 + 4,                        # keys, perm, mover list
-        "permute": 4 + state + state + 4,                  # perm, gather in, scatter out, key
-    }
+    pos = d * f                                   # positions (split: cell offsets; leaf implicit)
+    state = 2 * d * f + 4                         # positions + velocities + leaf
+    field = d * f / ppc                           # vertex field, read once
+    charge = f / ppc                              # vertex charge, written once
+    if brick:
+        return {"push": state + field, "rebin": state + pos, "deposit": charge, "permute": 0.0}
+    return {"deposit": pos + charge, "push": state + field, "rebin": 0.0, "permute": state}
 
 
 def max_over_ranks(x: float, dist, device: str) -> float:
@@ -209,51 +261,110 @@ def build_workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-def oracle_rate(d: int, split: bool, scheme: int, budget_s: float):
-    """The CPU oracle, as it stands, timed on a bounded sample of the workload:
-    the same 3D Langmuir plasma on a depth-3 tree (27^3 leaves, 8 ppc, 157,464
-    particles), deposit + gather/push + re-bin with the field held fixed."""
-    import oracle
+_ORACLE = {}
 
-    w = W.langmuir(d, 3, 8 if d == 3 else 16, vth=0.05)
+
+def _oracle_init(d, depth, split, scheme):
+    """Per host process: the CPU oracle, as it stands, on its own copy of the
+    sample (the 3D Langmuir plasma on a depth-4 tree, 8 particles per cell),
+    with the field of the start positions held fixed."""
+    import oracle
+    w = W.langmuir(d, depth, 8 if d == 3 else 16, vth=0.05, dt=0.1)
     tree = oracle.Tree(d, w.flags)
     prm = oracle.Params(scheme=scheme, q=w.q, qm=w.qm, ion=w.ion, sweeps=10, omega=0.8)
     st = oracle.State32(tree, w.x, w.v, prm) if split else oracle.State64(tree, w.x, w.v, prm)
     Q, tot, res, E = st.field()
+    _ORACLE.update(w=w, tree=tree, st=st, E=E, split=split, scheme=scheme)
+
+
+def _oracle_steps(budget_s):
+    """Oracle steps (deposit + gather/push + re-bin) for at least one step and
+    about budget_s seconds; returns (particle-updates, seconds, steps, n)."""
+    o = _ORACLE
+    w, tree, st, E = o["w"], o["tree"], o["st"], o["E"]
     steps, t0 = 0, time.perf_counter()
     while True:
-        if split:
-            tree.deposit32(scheme, st.leaf, st.o, np.float32(w.q), np.float32(w.ion))
+        if o["split"]:
+            tree.deposit32(o["scheme"], st.leaf, st.o, np.float32(w.q), np.float32(w.ion))
             tree.push32(st.leaf, st.o, st.v, E, w.qm, w.dt)
         else:
-            tree.deposit64(scheme, st.x, w.q, w.ion)
+            tree.deposit64(o["scheme"], st.x, w.q, w.ion)
             tree.push64(st.x, st.v, E, w.qm, w.dt)
         st.rebin()
         steps += 1
         el = time.perf_counter() - t0
         if el >= budget_s:
             break
-    return w.n * steps / el, {"kind": "oracle", "cores": 1,
-                              "sample": f"{steps} steps of the depth-3 3D Langmuir sample ({w.n} particles), "
-                                        "single-threaded C oracle, field fixed"}
+    return w.n * steps, el, steps, w.n
+
+
+class OraclePool:
+    """The CPU oracle on every host core at once: one spawned process per core,
+    each stepping its own copy of a bounded sample of the bench workload."""
+
+    def __init__(self, d: int, split: bool, scheme: int = 0, cores: int | None = None):
+        import multiprocessing as mp
+
+        import oracle
+        oracle.build()
+        self.cores = cores or (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
+        self.d, self.depth = d, (4 if d == 3 else 5)
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init,
+                                                  initargs=(d, self.depth, split, scheme))
+
+    def run(self, budget_s: float):
+        """(particle-updates/s of all cores together, wall seconds, steps, n)."""
+        res = self.pool.map(_oracle_steps, [budget_s] * self.cores, chunksize=1)
+        secs = max(r[1] for r in res)
+        return sum(r[0] for r in res) / secs, secs, min(r[2] for r in res), res[0][3]
+
+    def info(self, steps: int, n: int) -> dict:
+        return {"kind": "oracle", "cores": self.cores,
+                "sample": f"{self.cores} processes, one per host core, each stepping ({steps}+ steps) its own "
+                          f"depth-{self.depth} {self.d}D Langmuir sample ({n} particles, 8 ppc: the bench "
+                          "workload's density and velocities on a coarser tree) with the single-threaded C "
+                          "oracle, field fixed"}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_rate(d: int, split: bool, scheme: int, budget_s: float, cores: int | None = None):
+    """The CPU oracle as it stands, timed on every host core at once for about
+    budget_s seconds (OraclePool); returns (rate, cpu_baseline info)."""
+    pool = OraclePool(d, split, scheme, cores)
+    try:
+        rate, _, steps, n = pool.run(budget_s)
+        return rate, pool.info(steps, n)
+    finally:
+        pool.close()
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on every host core,
+    each timed step one oracle step of every core's own sample of the bench
+    workload (OraclePool)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w_name = args.workload
     d = 3 if w_name.startswith("langmuir3d") else 2
     split = d == 3
-    rates, secs = [], []
-    for _ in range(args.warmup):
-        oracle_rate(d, split, 0, 1.0)
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        r, info = oracle_rate(d, split, 0, max(2.0, 20.0 / max(args.steps, 1)))
-        secs.append(time.perf_counter() - t0)
-        rates.append(r)
-    value = statistics.median(rates)
+    pool = OraclePool(d, split)
+    try:
+        for _ in range(args.warmup):
+            pool.run(0.0)
+        rates, secs = [], []
+        steps, n = 0, 0
+        for _ in range(args.steps):
+            r, sec, steps, n = pool.run(0.0)
+            rates.append(r)
+            secs.append(sec)
+        info = pool.info(args.steps, n)
+    finally:
+        pool.close()
+    value = sum(r * t for r, t in zip(rates, secs)) / sum(secs)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-updates/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True, "scaling": "weak",
@@ -310,7 +421,7 @@ def run_batch(args):
                fp64=res["fp64"], tuning=res["fp32_split"]["tuning"],
                step_roofline={"bytes_per_particle": STEP_BYTES[(2, 1)],
                               "frac": res["fp32_split"]["step_roofline_frac"]})
-    print(json.dumps(out))
+    return out
 
 
 def run_twostream(args):
@@ -364,7 +475,8 @@ def run_twostream(args):
            "step_roofline": {"bytes_per_particle": STEP_BYTES[(3, 1)],
                              "frac": STEP_BYTES[(3, 1)] * n / (ms / 1e3) / 1e9 / hbm},
            "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()}}
-    print(json.dumps(out))
+    g.close()
+    return out
 
 
 def main():
@@ -379,13 +491,24 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
+    ap.add_argument("--only-main", action="store_true",
+                    help="skip the other configurations (3D adaptive two-stream PIDT, batch of 256)")
+    ap.add_argument("--ingest-ncu", default=None,
+                    help="write the DRAM-traffic CSV of the brick kernels from an ncu --csv log and exit")
+    ap.add_argument("--particles", type=int, default=243 ** 3 * 8,
+                    help="particles of the captured workload (with --ingest-ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch256":
-        return run_batch(args)
+        print(json.dumps(run_batch(args)))
+        return
     if args.workload == "twostream3d":
-        return run_twostream(args)
+        print(json.dumps(run_twostream(args)))
+        return
+    if args.ingest_ncu:
+        sys.stdout.write(ingest_ncu(args.ingest_ncu, args.workload, args.particles))
+        return
 
     import torch
 
@@ -551,22 +674,17 @@ def main():
     peaks, peak_kind = load_peaks()
     hbm = float(peaks["hbm_gbs"])
     info = g.info()
-    if info.brick:
-        kb = brick_bytes(d, cfg["ppc"], track_ids=False)
-        names = {"push": "k_brick_push_st (gather + kick + drift + re-location + append to the destination's staging area)",
-                 "rebin": "k_brick_pull_st (+ overflow and unit-offset helpers): canonical re-bin + corner partials",
-                 "deposit": "k_vertex_charge (vertex sums of the corner partials)"}
-    else:
-        kb = kernel_bytes(d, split, cfg["ppc"])
-        names = {}
+    shares = step_shares(d, split, cfg["ppc"], bool(info.brick))
+    names = {"push": "k_brick_push_st (gather + kick + drift + re-location + append to the destination's staging area)",
+             "rebin": "k_brick_pull_st (+ overflow and unit-offset helpers): canonical re-bin + corner partials",
+             "deposit": "k_vertex_charge (vertex sums of the corner partials)"} if info.brick else {}
     dom = max(("deposit", "push", "rebin", "permute"), key=lambda k: phases[k][0])
     dom_ms = phases[dom][0] / args.steps
-    achieved = kb[dom] * n / (dom_ms / 1e3) / 1e9
+    achieved = shares[dom] * n / (dom_ms / 1e3) / 1e9
     step_bytes = STEP_BYTES[(d, 1 if split else 0)]
-    traffic = None
-    mt = MEASURED_TRAFFIC.get((args.workload, dom))
-    if mt and mt["digest"] == kernel_digest():
-        traffic = mt["bytes_per_particle"] * n
+    traffic, trow = (measured_traffic(args.workload, PHASE_KERNEL[dom]) if info.brick and dom in PHASE_KERNEL
+                     else (None, None))
+    staged = brick_bytes(d, cfg["ppc"], track_ids=False) if info.brick else None
     launches = sum(k for _, k in phases.values())
     out = {
         "metric": METRIC, "value": value, "unit": "particle-updates/s", "n_gpus": world,
@@ -577,7 +695,22 @@ def main():
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "roofline": {"bound": "hbm", "kernel": names.get(dom, dom), "achieved": achieved, "peak": hbm,
                      "unit": "GB/s", "frac": achieved / hbm, "peak_kind": peak_kind, "traffic": traffic,
-                     "algorithmic_bytes_per_particle": kb[dom], "launch_ms": dom_ms},
+                     "algorithmic_bytes_per_particle": shares[dom],
+                     "algorithmic_bytes": f"the kernel's share of the {step_bytes:g} B particle-step "
+                                          "(state read + field read, grid terms over ppc)" if dom == "push" else
+                                          f"the kernel's share of the {step_bytes:g} B particle-step",
+                     "traffic_source": (f"ncu capture of these sources ({trow['launches']} launches), "
+                                        "profiles/dram_traffic_langmuir3d_243cubed_8ppc.csv") if traffic else
+                                       ("stale: the kernel changed since the committed capture" if trow else None),
+                     "design_bytes_per_particle": staged[dom] if staged else None,
+                     "launch_ms": dom_ms},
+        "phase_roofline": {k: {"algorithmic_bytes_per_particle": shares[k],
+                               "achieved_gbs": shares[k] * n / (phases[k][0] / args.steps / 1e3) / 1e9
+                               if phases[k][0] > 0 else None,
+                               "frac": shares[k] * n / (phases[k][0] / args.steps / 1e3) / 1e9 / hbm
+                               if phases[k][0] > 0 else None,
+                               "ms": phases[k][0] / args.steps}
+                           for k in ("deposit", "push", "rebin", "permute") if shares[k] > 0},
         "step_roofline": {"bytes_per_particle": step_bytes,
                           "achieved_gbs": step_bytes * n / (ms_step / 1e3) / 1e9,
                           "frac": step_bytes * n / (ms_step / 1e3) / 1e9 / hbm},
@@ -595,6 +728,13 @@ def main():
     out["calibration"] = calib
     if fp64 is not None:
         out["fp64"] = fp64
+    if world == 1 and not args.only_main and args.workload == "langmuir3d":
+        # the other configurations, each timed on its own (their handles are
+        # created after the main handles are closed)
+        g.close()
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        out["workloads"] = {"twostream3d": run_twostream(args), "batch256": run_batch(args)}
     if world == 1 and not args.no_cpu_baseline:
         rate, info = oracle_rate(d, split, 0, args.oracle_seconds)
         out["cpu_baseline"] = {"value": rate, "unit": "particle-updates/s", **info}

@@ -702,17 +702,22 @@ __global__ void k_mover_slots(const int32_t *movers, const int32_t *n_movers, co
 }
 
 // The movers of every bucket in storage order (undoes the atomic slot order).
-// Segments longer than kSmallSeg are listed for k_sort_large.
+// Segments of kSmallSeg movers or fewer are sorted here by one thread; longer
+// ones are listed for k_sort_medium (up to kMedSeg: one warp each) or
+// k_sort_large (one block each).
 constexpr int kSmallSeg = 32;
+constexpr int kMedSeg = 2048;        // longest segment one warp sorts in shared memory
+constexpr int kMedThreads = 256;
 constexpr int kLargeSeg = 16384;     // chunk of a long segment sorted in shared memory
 constexpr int kLargeThreads = 1024;
 __global__ void k_sort_segments(const int32_t *new_start, const int32_t *n_stay, int64_t n_keys, int32_t *perm,
-                                int32_t *large, int32_t *n_large) {
+                                int32_t *large, int32_t *n_large, int32_t *med, int32_t *n_med) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n_keys) return;
   int32_t b = new_start[k] + n_stay[k], e = new_start[k + 1];
   if (e - b > kSmallSeg) {
-    large[atomicAdd(n_large, 1)] = (int32_t)k;
+    if (e - b <= kMedSeg) med[atomicAdd(n_med, 1)] = (int32_t)k;
+    else large[atomicAdd(n_large, 1)] = (int32_t)k;
     return;
   }
   for (int32_t i = b + 1; i < e; ++i) {
@@ -723,6 +728,27 @@ __global__ void k_sort_segments(const int32_t *new_start, const int32_t *n_stay,
       --j;
     }
     perm[j + 1] = x;
+  }
+}
+
+// One warp per listed segment of at most kMedSeg movers (grid-stride over the
+// list): the segment is copied into the warp's shared slice, sorted by the
+// bitonic network of segsort.cuh and copied back.
+__global__ void __launch_bounds__(kMedThreads) k_sort_medium(const int32_t *new_start, const int32_t *n_stay,
+                                                             const int32_t *med, const int32_t *n_med,
+                                                             int32_t *perm) {
+  extern __shared__ int32_t sw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = kMedThreads / 32;
+  int32_t *v = sw + wib * kMedSeg;
+  const int nm = *n_med;
+  for (int li = blockIdx.x * wpb + wib; li < nm; li += gridDim.x * wpb) {
+    const int32_t k = med[li];
+    const int32_t b = new_start[k] + n_stay[k], m = new_start[k + 1] - b;
+    for (int i = lane; i < m; i += 32) v[i] = perm[b + i];
+    __syncwarp();
+    warp_sort_direct<int32_t>(v, m);
+    for (int i = lane; i < m; i += 32) perm[b + i] = v[i];
+    __syncwarp();
   }
 }
 
@@ -910,6 +936,9 @@ cudaError_t set_constants(cudaStream_t s) {
   for (int i = 1; i < 21; ++i) p3[i] = p3[i - 1] * 3u;
   cudaError_t e = cudaFuncSetAttribute(k_sort_large, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)(sizeof(int32_t) * kLargeSeg));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_sort_medium, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(int32_t) * kMedSeg * (kMedThreads / 32)));
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbolAsync(c_pow3, p3, sizeof(p3), 0, cudaMemcpyHostToDevice, s);
 }
@@ -1131,8 +1160,12 @@ void launch_rebin(const RebinArgs &r, cudaStream_t s) {
   cudaMemsetAsync(r.cursor, 0, sizeof(int32_t) * r.n_keys, s);
   { COUNT(1); k_mover_slots<<<gp, bp, 0, s>>>(r.movers, r.scalars + 1, r.keyn, r.new_start, r.n_stay, r.cursor, r.perm); }
   cudaMemsetAsync(r.scalars + 5, 0, sizeof(int32_t), s);
+  cudaMemsetAsync(r.scalars + 7, 0, sizeof(int32_t), s);
+  // the mover list is no longer needed: it holds the list of medium segments
   { COUNT(1); k_sort_segments<<<grid_for(r.n_keys), kBlock, 0, s>>>(r.new_start, r.n_stay, r.n_keys, r.perm, r.cursor,
-                                                                      r.scalars + 5); }
+                                                                      r.scalars + 5, r.movers, r.scalars + 7); }
+  { COUNT(1); k_sort_medium<<<456, kMedThreads, sizeof(int32_t) * kMedSeg * (kMedThreads / 32), s>>>(
+      r.new_start, r.n_stay, r.movers, r.scalars + 7, r.perm); }
   { COUNT(1); k_sort_large<<<304, kLargeThreads, sizeof(int32_t) * kLargeSeg, s>>>(r.new_start, r.n_stay, r.cursor,
                                                                                   r.scalars + 5, r.perm); }
 }

@@ -50,6 +50,32 @@ __device__ void warp_sort_indirect(Idx *idx, int m, const Key *key) {
     }
 }
 
+// One warp sorts v[0..m) (shared memory) ascending; the values are distinct.
+// All 32 lanes must call it.
+template <typename T>
+__device__ void warp_sort_direct(T *v, int m) {
+  if (m <= 1) return;
+  const int lane = threadIdx.x & 31;
+  int P = 1;
+  while (P < m) P <<= 1;
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      // comparator c reaches l >= 2c - j + 2: none past (m + j) / 2 has both positions valid
+      for (int c = lane; c <= (m + j) / 2; c += 32) {
+        int64_t i, l;
+        bitonic_pair(c, k, j, &i, &l);
+        if (l < m) {
+          const T a = v[i], b = v[l];
+          if (b < a) {
+            v[i] = b;
+            v[l] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+}
+
 // Compare-exchange of positions i < l of (key, val) arrays; val may be null.
 template <typename K, typename V>
 __device__ __forceinline__ void cmpx(K *key, V *val, int64_t i, int64_t l) {
