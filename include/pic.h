@@ -129,7 +129,11 @@ typedef struct {
   int64_t max_bucket;    /* largest bucket after the last re-bin */
   double total_charge;   /* FP64 sum of the vertex charges of the last deposit */
   double residual;       /* FP64 2-norm of b - A V after the last built-in solve */
-  int32_t error;         /* sticky device error: PIC_ERANGE if a non-finite value was seen */
+  int32_t error;         /* sticky device error: PIC_ERANGE if a non-finite value was seen,
+                            PIC_ETIMEOUT if a bounded device wait gave up */
+  int64_t tunnellers;    /* with lift counting on (pic_count_lifts): particles whose new leaf
+                            does not touch their old leaf (moved two cells or more on the finer
+                            level), summed over the counted steps; -1 when counting is off */
 } pic_stats_t;
 
 /* Device memory through the caller's allocator, for example PyTorch's caching
@@ -286,20 +290,29 @@ PIC_API int pic_set_state(pic_t h, const int32_t *leaf, const void *x_or_o, cons
  * step count and the sticky device error.  Synchronous. */
 PIC_API int pic_stats(pic_t h, pic_stats_t *out);
 
-/* Lift and drop counts of Algorithm 1 (the paper's cost measure for particle
- * handling, Section 6: lifting a particle n levels counts as n lifts).  With
- * counting on, every pic_step / pic_step_fixed_field adds, for each particle
- * that went from leaf L1 to leaf L2, lifts = level(L1) - m and
- * drops = level(L2) - m, m the level of the deepest common ancestor of L1 and
- * L2 (a particle is lifted out of every cell that no longer covers it and
- * dropped into every cell that does; stayers add nothing).  Two extra
- * kernels per step; PIT handles with track_ids only (PIC_ESTATE otherwise);
+/* Lift and drop counts (the paper's cost measure for particle handling,
+ * Section 6: lifting a particle n levels counts as n lifts).  With counting
+ * on, every pic_step / pic_step_fixed_field adds per particle:
+ *   PIT (Algorithm 1): for a particle that went from leaf L1 to leaf L2,
+ *     lifts = level(L1) - m and drops = level(L2) - m, m the level of the
+ *     deepest common ancestor of L1 and L2 (it is lifted out of every cell
+ *     that no longer covers it and dropped into every cell that does);
+ *   PIDT (Algorithms 2-3, read as a count): none for a particle whose new
+ *     owner vertex is a vertex of its old leaf on that leaf's level (handed
+ *     over inside the cell); otherwise lifts from the old owner vertex to the
+ *     deepest vertex of the dual tree whose dual cell holds both owners' dual
+ *     cells (the dual parent of (l, j) is (l - 1, (j + 1) div 3)) and drops
+ *     from there to the new owner;
+ *   both: a tunneller when L2 does not touch L1 (the closed boxes share no
+ *     point, periodic).
+ * Stayers add nothing.  Two or three extra kernels per step; handles with
+ * track_ids only, PIDT ones with a single instance (PIC_ESTATE otherwise);
  * graph capture is refused while counting.  pic_count_lifts(h, 1) starts (or
  * restarts) from zero, (h, 0) stops and frees the counters.  pic_lift_counts
  * returns the totals and the steps counted since the start (synchronous;
  * PIC_ESTATE when counting is off); any pointer may be NULL. */
 PIC_API int pic_count_lifts(pic_t h, int32_t enable);
-PIC_API int pic_lift_counts(pic_t h, int64_t *lifts, int64_t *drops, int64_t *steps);
+PIC_API int pic_lift_counts(pic_t h, int64_t *lifts, int64_t *drops, int64_t *tunnellers, int64_t *steps);
 
 /* Phases of a step for pic_phase_times. */
 #define PIC_PHASE_DEPOSIT 0  /* leaf partial sums + vertex charges + FP64 total */

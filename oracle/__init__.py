@@ -165,6 +165,68 @@ class Tree:
             common = np.where(same, m, common)
         return l1 - common, l2 - common
 
+    def pidt_lifts(self, old_leaf, old_key, new_key):
+        """Lifts and drops of a PIDT particle whose owner went from the vertex
+        of old_key to the vertex of new_key (key = vertex 2^d + quadrant) while
+        its leaf before the move was old_leaf.  Reading of Algorithms 2-3 as a
+        count: a particle that ends at a vertex of its old leaf on that leaf's
+        level is handed over between the cell's vertices (no lift, no drop);
+        any other particle is lifted from its old vertex to the deepest
+        vertex of the dual tree whose dual cell holds both owners' dual cells
+        and dropped from there to the new owner -- the dual parent of vertex
+        (l, j) being the vertex (l - 1, (j + 1) div 3) whose dual cell contains
+        its dual cell (k = 3).  Returns (lifts, drops), int64 per particle."""
+        d = self.d
+        nc = 1 << d
+        lev, co = self.leaf_info()
+        pv_lev, pv_j = self.pidt_vertices()
+        old_leaf = np.asarray(old_leaf, np.int64)
+        k1 = np.asarray(old_key, np.int64) // nc
+        k2 = np.asarray(new_key, np.int64) // nc
+        l1, l2 = pv_lev[k1].astype(np.int64), pv_lev[k2].astype(np.int64)
+        j1, j2 = pv_j[k1].astype(np.int64), pv_j[k2].astype(np.int64)
+        ll, cl = lev[old_leaf].astype(np.int64), co[old_leaf]
+        per = 3 ** ll
+        rel = np.mod(j2 - cl, per[:, None])
+        handed = (l2 == ll) & np.all(rel <= 1, axis=1)
+        m = np.minimum(l1, l2)
+
+        def up(j, lfrom, lto):
+            j = j.copy()
+            lcur = lfrom.copy()
+            while np.any(lcur > lto):
+                go = lcur > lto
+                j[go] = np.mod((j[go] + 1) // 3, (3 ** (lcur[go] - 1))[:, None])
+                lcur[go] -= 1
+            return j
+
+        a1, a2 = up(j1, l1, m), up(j2, l2, m)
+        while True:
+            differ = (m > 0) & np.any(a1 != a2, axis=1)
+            if not np.any(differ):
+                break
+            a1[differ] = np.mod((a1[differ] + 1) // 3, (3 ** (m[differ] - 1))[:, None])
+            a2[differ] = np.mod((a2[differ] + 1) // 3, (3 ** (m[differ] - 1))[:, None])
+            m = np.where(differ, m - 1, m)
+        same = k1 == k2
+        zero = handed | same
+        return np.where(zero, 0, l1 - m), np.where(zero, 0, l2 - m)
+
+    def tunnellers(self, old_leaf, new_leaf):
+        """True for a particle whose new leaf does not touch its old leaf (the
+        closed boxes, periodic, share no point): it moved two cells or more,
+        counted on the finer of the two levels."""
+        lev, co = self.leaf_info()
+        old_leaf = np.asarray(old_leaf, np.int64)
+        new_leaf = np.asarray(new_leaf, np.int64)
+        l1, l2 = lev[old_leaf].astype(np.int64), lev[new_leaf].astype(np.int64)
+        lm = np.maximum(l1, l2)
+        s1, s2 = (3 ** (lm - l1))[:, None], (3 ** (lm - l2))[:, None]
+        P = (3 ** lm)[:, None]
+        lo1, lo2 = co[old_leaf] * s1, co[new_leaf] * s2
+        touch = (np.mod(lo2 - lo1, P) <= s1) | (np.mod(lo1 - lo2, P) <= s2)
+        return ~np.all(touch, axis=1)
+
     # ---- keys -----------------------------------------------------------
     def pit_owner(self, x: np.ndarray) -> np.ndarray:
         x = _c(x, np.float64)

@@ -1211,15 +1211,47 @@ __global__ void k_scatter_by_id(const int32_t *ids, const int32_t *leaf, int64_t
   if (id >= 0 && id < n) by_id[id] = leaf[p];
 }
 
+// True when the closed boxes of leaves L1 and L2 share a point (periodic),
+// compared on the finer of the two levels.
+__device__ __forceinline__ bool leaves_touch(const DevTree &t, int32_t L1, int32_t L2) {
+  const int l1 = t.leaf_level[L1], l2 = t.leaf_level[L2];
+  const int lm = l1 > l2 ? l1 : l2;
+  const int64_t s1 = c_pow3[lm - l1], s2 = c_pow3[lm - l2], P = c_pow3[lm];
+  for (int a = 0; a < t.d; ++a) {
+    const int64_t lo1 = (int64_t)t.leaf_coords[(int64_t)L1 * t.d + a] * s1;
+    const int64_t lo2 = (int64_t)t.leaf_coords[(int64_t)L2 * t.d + a] * s2;
+    int64_t d12 = (lo2 - lo1) % P, d21 = (lo1 - lo2) % P;
+    if (d12 < 0) d12 += P;
+    if (d21 < 0) d21 += P;
+    if (d12 > s1 && d21 > s2) return false;
+  }
+  return true;
+}
+
+// Warp sums of (lifts, drops, tunnellers) into counts[0..2].
+__device__ __forceinline__ void add_counts(unsigned lifts, unsigned drops, unsigned tun, unsigned long long *counts) {
+  for (int off = 16; off > 0; off >>= 1) {
+    lifts += __shfl_down_sync(0xffffffffu, lifts, off);
+    drops += __shfl_down_sync(0xffffffffu, drops, off);
+    tun += __shfl_down_sync(0xffffffffu, tun, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (lifts) atomicAdd(&counts[0], (unsigned long long)lifts);
+    if (drops) atomicAdd(&counts[1], (unsigned long long)drops);
+    if (tun) atomicAdd(&counts[2], (unsigned long long)tun);
+  }
+}
+
 // A particle that went from leaf L1 (level l1, coordinates c1) to leaf L2 is
 // lifted out of every cell from L1 up to the deepest ancestor that contains
 // L2, then dropped down to L2: lifts = l1 - m, drops = l2 - m with m the level
-// of that ancestor (levels and coordinates of one instance's tree).  Warp sums
-// go to counts[0] (lifts) and counts[1] (drops).
+// of that ancestor (levels and coordinates of one instance's tree).  It
+// tunnelled when L2 does not touch L1.  Warp sums go to counts[0] (lifts),
+// counts[1] (drops) and counts[2] (tunnellers).
 __global__ void k_lift_drop(DevTree t, const int32_t *ids, const int32_t *leaf, const int32_t *old_by_id, int64_t n,
                             unsigned long long *counts) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned lifts = 0, drops = 0;
+  unsigned lifts = 0, drops = 0, tun = 0;
   if (p < n) {
     const int32_t id = ids[p];
     const int32_t L2 = leaf[p];
@@ -1241,16 +1273,81 @@ __global__ void k_lift_drop(DevTree t, const int32_t *ids, const int32_t *leaf, 
       }
       lifts = (unsigned)(l1 - m);
       drops = (unsigned)(l2 - m);
+      tun = leaves_touch(t, L1, L2) ? 0u : 1u;
     }
   }
-  for (int off = 16; off > 0; off >>= 1) {
-    lifts += __shfl_down_sync(0xffffffffu, lifts, off);
-    drops += __shfl_down_sync(0xffffffffu, drops, off);
+  add_counts(lifts, drops, tun, counts);
+}
+
+// Owner vertex (level, j) of PIDT key k (owner vertex id = k / 2^d): the
+// finite-element vertex of a uniform tree (row-major on the finest level),
+// else the owner-vertex table.
+__device__ __forceinline__ int pidt_owner(const DevTree &t, const int32_t *pv_level, const int32_t *pv_j, int32_t k,
+                                          int64_t *j) {
+  const int32_t pv = k / t.nc;
+  if (t.uniform) {
+    int64_t v = pv;
+    for (int a = 0; a < t.d; ++a) {
+      j[a] = v % t.M;
+      v /= t.M;
+    }
+    return t.depth;
   }
-  if ((threadIdx.x & 31) == 0 && (lifts | drops)) {
-    atomicAdd(&counts[0], (unsigned long long)lifts);
-    atomicAdd(&counts[1], (unsigned long long)drops);
+  for (int a = 0; a < t.d; ++a) j[a] = pv_j[(int64_t)pv * t.d + a];
+  return pv_level[pv];
+}
+
+// Lifts and drops of PIDT (reading of Algorithms 2-3 as a count): a particle
+// whose new owner is a vertex of its old leaf on that leaf's level is handed
+// over inside the cell (none); any other is lifted from its old vertex to the
+// deepest dual ancestor whose dual cell holds both owners' dual cells and
+// dropped to the new owner, the dual parent of (l, j) being
+// (l - 1, (j + 1) div 3).  Tunnellers as for PIT, from the leaves.
+__global__ void k_lift_drop_pidt(DevTree t, const int32_t *pv_level, const int32_t *pv_j, const int32_t *ids,
+                                 const int32_t *leaf, const int32_t *key, const int32_t *old_leaf_by_id,
+                                 const int32_t *old_key_by_id, int64_t n, unsigned long long *counts) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned lifts = 0, drops = 0, tun = 0;
+  if (p < n) {
+    const int32_t id = ids[p];
+    const int32_t L2 = leaf[p], k2 = key[p];
+    const bool ok = id >= 0 && id < n;
+    const int32_t L1 = ok ? old_leaf_by_id[id] : -1, k1 = ok ? old_key_by_id[id] : -1;
+    if (L1 >= 0 && L1 < t.n_leaves && L2 >= 0 && L2 < t.n_leaves && k1 >= 0 && k1 < t.n_keys && k2 >= 0 &&
+        k2 < t.n_keys) {
+      tun = leaves_touch(t, L1, L2) ? 0u : 1u;
+      if (k1 / t.nc != k2 / t.nc) {
+        int64_t j1[3] = {0, 0, 0}, j2[3] = {0, 0, 0};
+        const int l1 = pidt_owner(t, pv_level, pv_j, k1, j1);
+        const int l2 = pidt_owner(t, pv_level, pv_j, k2, j2);
+        const int ll = t.leaf_level[L1];
+        const int64_t per = c_pow3[ll];
+        bool handed = l2 == ll;
+        for (int a = 0; a < t.d && handed; ++a) {
+          int64_t r = (j2[a] - t.leaf_coords[(int64_t)L1 * t.d + a]) % per;
+          if (r < 0) r += per;
+          handed = r <= 1;
+        }
+        if (!handed) {
+          int m = l1 < l2 ? l1 : l2;
+          for (int l = l1; l > m; --l)
+            for (int a = 0; a < t.d; ++a) j1[a] = ((j1[a] + 1) / 3) % (int64_t)c_pow3[l - 1];
+          for (int l = l2; l > m; --l)
+            for (int a = 0; a < t.d; ++a) j2[a] = ((j2[a] + 1) / 3) % (int64_t)c_pow3[l - 1];
+          while (m > 0 && (j1[0] != j2[0] || j1[1] != j2[1] || j1[2] != j2[2])) {
+            for (int a = 0; a < t.d; ++a) {
+              j1[a] = ((j1[a] + 1) / 3) % (int64_t)c_pow3[m - 1];
+              j2[a] = ((j2[a] + 1) / 3) % (int64_t)c_pow3[m - 1];
+            }
+            --m;
+          }
+          lifts = (unsigned)(l1 - m);
+          drops = (unsigned)(l2 - m);
+        }
+      }
+    }
   }
+  add_counts(lifts, drops, tun, counts);
 }
 
 void launch_scatter_by_id(const int32_t *ids, const int32_t *leaf, int64_t n, int32_t *by_id, cudaStream_t s) {
@@ -1260,6 +1357,16 @@ void launch_scatter_by_id(const int32_t *ids, const int32_t *leaf, int64_t n, in
 void launch_lift_drop(const DevTree &t, const int32_t *ids, const int32_t *leaf, const int32_t *old_by_id, int64_t n,
                       unsigned long long *counts, cudaStream_t s) {
   if (n > 0) { COUNT(1); k_lift_drop<<<grid_for(n), kBlock, 0, s>>>(t, ids, leaf, old_by_id, n, counts); }
+}
+
+void launch_lift_drop_pidt(const DevTree &t, const int32_t *pv_level, const int32_t *pv_j, const int32_t *ids,
+                           const int32_t *leaf, const int32_t *key, const int32_t *old_leaf_by_id,
+                           const int32_t *old_key_by_id, int64_t n, unsigned long long *counts, cudaStream_t s) {
+  if (n > 0) {
+    COUNT(1);
+    k_lift_drop_pidt<<<grid_for(n), kBlock, 0, s>>>(t, pv_level, pv_j, ids, leaf, key, old_leaf_by_id, old_key_by_id,
+                                                    n, counts);
+  }
 }
 
 void launch_half_kick(bool split, const void *Ep, int64_t n_total, double c, void *v, cudaStream_t s) {

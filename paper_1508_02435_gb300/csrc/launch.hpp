@@ -190,9 +190,14 @@ void launch_widen(const float *in, int64_t n, double *out, cudaStream_t s);
 void launch_gather_only(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n,
                         const void *Ev, void *Ep, cudaStream_t s);
 void launch_half_kick(bool split, const void *Ep, int64_t n_total, double c, void *v, cudaStream_t s);
-// lift and drop counts (diagnostic, PIT)
+// lift and drop counts (diagnostic): counts[0..2] = lifts, drops, tunnellers
 void launch_scatter_by_id(const int32_t *ids, const int32_t *leaf, int64_t n, int32_t *by_id, cudaStream_t s);
 void launch_lift_drop(const DevTree &t, const int32_t *ids, const int32_t *leaf, const int32_t *old_by_id, int64_t n,
                       unsigned long long *counts, cudaStream_t s);
+// PIDT: pv_level / pv_j are the owner-vertex table (adaptive trees; unused on
+// uniform ones); counts[0..2] = lifts, drops, tunnellers.
+void launch_lift_drop_pidt(const DevTree &t, const int32_t *pv_level, const int32_t *pv_j, const int32_t *ids,
+                           const int32_t *leaf, const int32_t *key, const int32_t *old_leaf_by_id,
+                           const int32_t *old_key_by_id, int64_t n, unsigned long long *counts, cudaStream_t s);
 
 }  // namespace pic

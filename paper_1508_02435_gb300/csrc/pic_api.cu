@@ -72,10 +72,12 @@ struct pic_s {
   std::string last_error;
   long long wait_cycles = 4000000000LL;  // bounded device waits of the brick kernels (pic_set_wait_limit)
 
-  // lift and drop counts of the steps (pic_count_lifts; PIT, tracked ids)
+  // lift and drop counts of the steps (pic_count_lifts; tracked ids)
   bool count_lifts = false;
   int32_t *lift_old = nullptr;             // leaf before the step, by particle id
-  unsigned long long *lift_counts = nullptr;  // [0] lifts, [1] drops
+  int32_t *lift_oldkey = nullptr;          // PIDT: key before the step, by particle id
+  int32_t *lift_pvl = nullptr, *lift_pvj = nullptr;  // PIDT, adaptive: owner-vertex levels and indices
+  unsigned long long *lift_counts = nullptr;  // [0] lifts, [1] drops, [2] tunnellers
   int64_t lift_steps = 0;
   std::vector<DevBuf> diag_bufs;
 
@@ -1039,6 +1041,7 @@ static int lift_before(pic_t h) {
   int rc;
   if ((rc = ensure_leaf(h))) return rc;
   launch_scatter_by_id(h->ids[0], h->leaf[0], h->n, h->lift_old, h->stream);
+  if (h->scheme == PIC_PIDT) launch_scatter_by_id(h->ids[0], h->key[0], h->n, h->lift_oldkey, h->stream);
   CK(cudaGetLastError());
   return PIC_OK;
 }
@@ -1046,7 +1049,11 @@ static int lift_before(pic_t h) {
 static int lift_after(pic_t h) {
   int rc;
   if ((rc = ensure_leaf(h))) return rc;
-  launch_lift_drop(h->dt, h->ids[0], h->leaf[0], h->lift_old, h->n, h->lift_counts, h->stream);
+  if (h->scheme == PIC_PIDT)
+    launch_lift_drop_pidt(h->dt, h->lift_pvl, h->lift_pvj, h->ids[0], h->leaf[0], h->key[0], h->lift_old,
+                          h->lift_oldkey, h->n, h->lift_counts, h->stream);
+  else
+    launch_lift_drop(h->dt, h->ids[0], h->leaf[0], h->lift_old, h->n, h->lift_counts, h->stream);
   CK(cudaGetLastError());
   h->lift_steps++;
   return PIC_OK;
@@ -1079,42 +1086,64 @@ int pic_step_fixed_field(pic_t h, double dt) {
   return PIC_OK;
 }
 
+static void lift_bufs_forget(pic_t h) {
+  h->lift_old = nullptr;
+  h->lift_oldkey = nullptr;
+  h->lift_pvl = nullptr;
+  h->lift_pvj = nullptr;
+  h->lift_counts = nullptr;
+}
+
 int pic_count_lifts(pic_t h, int32_t enable) {
   if (check_handle(h)) return PIC_EINVAL;
   if (!enable) {
     h->count_lifts = false;
     free_bufs(h, h->diag_bufs);
-    h->lift_old = nullptr;
-    h->lift_counts = nullptr;
+    lift_bufs_forget(h);
     return PIC_OK;
   }
-  if (h->scheme != PIC_PIT) return fail(h, PIC_ESTATE, "lift and drop counts are kept for PIT handles only");
   if (!h->cfg.track_ids) return fail(h, PIC_ESTATE, "lift and drop counts need track_ids = 1");
+  if (h->scheme == PIC_PIDT && h->dt.n_inst > 1)
+    return fail(h, PIC_ESTATE, "PIDT lift and drop counts are kept for single-instance handles");
   drop_graphs(h);
-  int rc;
+  int rc = PIC_OK;
   if (!h->count_lifts) {
-    if ((rc = dalloc(h, h->diag_bufs, &h->lift_old, h->n)) ||
-        (rc = dalloc(h, h->diag_bufs, &h->lift_counts, 2))) {
+    rc = dalloc(h, h->diag_bufs, &h->lift_old, h->n);
+    if (!rc) rc = dalloc(h, h->diag_bufs, &h->lift_counts, 3);
+    if (!rc && h->scheme == PIC_PIDT) rc = dalloc(h, h->diag_bufs, &h->lift_oldkey, h->n);
+    if (!rc && h->scheme == PIC_PIDT && !h->dt.uniform) {
+      // owner-vertex table on the device (levels; indices per axis as int32)
+      const auto &t = h->ht;
+      std::vector<int32_t> pvl(t.pv_level.begin(), t.pv_level.end());
+      std::vector<int32_t> pvj(t.pv_j.size());
+      for (size_t i = 0; i < pvj.size(); ++i) pvj[i] = (int32_t)t.pv_j[i];
+      const int32_t *a = nullptr, *b = nullptr;
+      rc = upload(h, h->diag_bufs, &a, pvl);
+      if (!rc) rc = upload(h, h->diag_bufs, &b, pvj);
+      h->lift_pvl = const_cast<int32_t *>(a);
+      h->lift_pvj = const_cast<int32_t *>(b);
+    }
+    if (rc) {
       free_bufs(h, h->diag_bufs);
-      h->lift_old = nullptr;
-      h->lift_counts = nullptr;
+      lift_bufs_forget(h);
       return rc;
     }
   }
-  CK(cudaMemsetAsync(h->lift_counts, 0, 2 * sizeof(unsigned long long), h->stream));
+  CK(cudaMemsetAsync(h->lift_counts, 0, 3 * sizeof(unsigned long long), h->stream));
   h->lift_steps = 0;
   h->count_lifts = true;
   return PIC_OK;
 }
 
-int pic_lift_counts(pic_t h, int64_t *lifts, int64_t *drops, int64_t *steps) {
+int pic_lift_counts(pic_t h, int64_t *lifts, int64_t *drops, int64_t *tunnellers, int64_t *steps) {
   if (check_handle(h)) return PIC_EINVAL;
   if (!h->count_lifts) return fail(h, PIC_ESTATE, "lift counting is off (pic_count_lifts)");
-  unsigned long long c[2] = {0, 0};
+  unsigned long long c[3] = {0, 0, 0};
   CK(cudaMemcpyAsync(c, h->lift_counts, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (lifts) *lifts = (int64_t)c[0];
   if (drops) *drops = (int64_t)c[1];
+  if (tunnellers) *tunnellers = (int64_t)c[2];
   if (steps) *steps = h->lift_steps;
   return PIC_OK;
 }
@@ -1499,7 +1528,14 @@ int pic_stats(pic_t h, pic_stats_t *o) {
   o->max_bucket = sc[2];
   o->total_charge = tot;
   o->residual = std::sqrt(r2);
-  o->error = (err & 1) ? PIC_ERANGE : (err ? PIC_ESTATE : PIC_OK);
+  o->error = (err & 1) ? PIC_ERANGE : (err & 8) ? PIC_ETIMEOUT : (err ? PIC_ESTATE : PIC_OK);
+  o->tunnellers = -1;
+  if (h->count_lifts) {
+    unsigned long long c[3] = {0, 0, 0};
+    CK(cudaMemcpyAsync(c, h->lift_counts, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    o->tunnellers = (int64_t)c[2];
+  }
   return PIC_OK;
 }
 

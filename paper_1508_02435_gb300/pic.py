@@ -55,7 +55,8 @@ class Info(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("movers", C.c_int64), ("max_bucket", C.c_int64),
-                ("total_charge", C.c_double), ("residual", C.c_double), ("error", C.c_int32)]
+                ("total_charge", C.c_double), ("residual", C.c_double), ("error", C.c_int32),
+                ("tunnellers", C.c_int64)]
 
 
 SOLVE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p)
@@ -106,7 +107,7 @@ SIGNATURES = [
     ("pic_tree_flags", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_set_allocator", C.c_int, [ALLOC_FN, FREE_FN, C.c_void_p]),
     ("pic_count_lifts", C.c_int, [C.c_void_p, C.c_int32]),
-    ("pic_lift_counts", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pic_lift_counts", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_save", C.c_int, [C.c_void_p, C.c_char_p]),
     ("pic_load", C.c_int, [C.POINTER(C.c_void_p), C.c_char_p, C.c_void_p]),
     ("pic_set_wait_limit", C.c_int, [C.c_void_p, C.c_int64]),
@@ -422,15 +423,17 @@ class Pic:
         self._check(self.lib.pic_set_wait_limit(self.h, int(cycles)))
 
     def count_lifts(self, enable: bool = True):
-        """Start (from zero) or stop counting the lifts and drops of every
-        step (pic_count_lifts; PIT handles with tracked ids)."""
+        """Start (from zero) or stop counting the lifts, drops and tunnellers
+        of every step (pic_count_lifts; handles with tracked ids)."""
         self._check(self.lib.pic_count_lifts(self.h, 1 if enable else 0))
 
     def lift_counts(self):
-        """(lifts, drops, steps) since counting started (pic_lift_counts)."""
-        lifts, drops, steps = C.c_int64(0), C.c_int64(0), C.c_int64(0)
-        self._check(self.lib.pic_lift_counts(self.h, C.byref(lifts), C.byref(drops), C.byref(steps)))
-        return lifts.value, drops.value, steps.value
+        """(lifts, drops, tunnellers, steps) since counting started
+        (pic_lift_counts)."""
+        lifts, drops, tun, steps = C.c_int64(0), C.c_int64(0), C.c_int64(0), C.c_int64(0)
+        self._check(self.lib.pic_lift_counts(self.h, C.byref(lifts), C.byref(drops), C.byref(tun),
+                                             C.byref(steps)))
+        return lifts.value, drops.value, tun.value, steps.value
 
     def stats(self) -> Stats:
         out = Stats()

@@ -550,3 +550,88 @@ def test_init_leapfrog_cold_langmuir_half_kick(precision):
     rel = np.linalg.norm(vx - expect) / np.linalg.norm(expect)
     assert rel < 0.03, rel
     assert np.max(np.abs(np.asarray(st.v[1], np.float64))) < 0.03 * np.abs(expect).max()
+
+
+# ---------------------------------------------------------------------------
+# lift and drop counts of PIDT, tunnellers
+# ---------------------------------------------------------------------------
+
+def _dual_cell(level, j):
+    """Half-open dual cell of vertex (level, j) on one axis, in units of
+    1 / (2 3^18): [(2j - 1) 3^(18 - l), (2j + 1) 3^(18 - l))."""
+    s = 3 ** (18 - level)
+    return (2 * j - 1) * s, 2 * s
+
+
+def _contains(outer, inner, P):
+    (a, wa), (b, wb) = outer, inner
+    return (b - a) % P + wb <= wa
+
+
+@pytest.mark.parametrize("d,depth,p,seed", [(2, 4, 0.35, 201), (3, 3, 0.3, 202)])
+def test_pidt_lifts_against_dual_cell_geometry(d, depth, p, seed):
+    """PIDT lifts and drops: zero when the new owner is a vertex of the old
+    leaf on its level (hand-over inside the cell), else up to the deepest
+    vertex whose dual cell contains both owners' dual cells (found here by
+    scanning every vertex of every level, exact integer intervals) and down
+    to the new owner."""
+    flags = W.random_tree_flags(d, depth, p, seed, min_depth=1)
+    t = oracle.Tree(d, flags)
+    x, v = W.random_particles(d, 1500, seed, vmax=0.3)
+    x2 = np.mod(x + v * 0.5, 1.0)
+    old_leaf = t.pit_owner(x)
+    k1, k2 = t.keys64(oracle.PIDT, x), t.keys64(oracle.PIDT, x2)
+    lifts, drops = t.pidt_lifts(old_leaf, k1, k2)
+    lev, co = t.leaf_info()
+    pv_lev, pv_j = t.pidt_vertices()
+    nc = 1 << d
+    P = 2 * 3 ** 18
+    expect_l, expect_d = np.zeros(len(k1), np.int64), np.zeros(len(k1), np.int64)
+    for i in range(len(k1)):
+        a, b = int(k1[i]) // nc, int(k2[i]) // nc
+        l1, l2 = int(pv_lev[a]), int(pv_lev[b])
+        j1, j2 = [int(c) for c in pv_j[a]], [int(c) for c in pv_j[b]]
+        L = int(old_leaf[i])
+        ll = int(lev[L])
+        corners = {tuple((int(co[L, ax]) + e[ax]) % 3 ** ll for ax in range(d))
+                   for e in itertools.product((0, 1), repeat=d)}
+        if a == b or (l2 == ll and tuple(j2) in corners):
+            continue
+        m_found = None
+        for m in range(min(l1, l2), -1, -1):
+            ok = True
+            for ax in range(d):
+                c1, c2 = _dual_cell(l1, j1[ax]), _dual_cell(l2, j2[ax])
+                if not any(_contains(_dual_cell(m, J), c1, P) and _contains(_dual_cell(m, J), c2, P)
+                           for J in range(3 ** m)):
+                    ok = False
+                    break
+            if ok:
+                m_found = m
+                break
+        assert m_found is not None
+        expect_l[i], expect_d[i] = l1 - m_found, l2 - m_found
+    assert np.array_equal(lifts, expect_l) and np.array_equal(drops, expect_d)
+    assert lifts.sum() > 0 and (lifts == 0).sum() > 0
+
+
+@pytest.mark.parametrize("d,depth,p,seed", [(2, 4, 0.35, 203), (3, 3, 0.3, 204)])
+def test_tunnellers_exact_geometry(d, depth, p, seed):
+    """A particle tunnels when its new leaf's closed box shares no point with
+    its old leaf's (periodic): checked with exact interval arithmetic over the
+    three periodic images."""
+    flags = W.random_tree_flags(d, depth, p, seed, min_depth=1)
+    t = oracle.Tree(d, flags)
+    x, v = W.random_particles(d, 2000, seed, vmax=0.2)
+    L1, L2 = t.pit_owner(x), t.pit_owner(np.mod(x + v * 0.5, 1.0))
+    tun = t.tunnellers(L1, L2)
+    lev, co = t.leaf_info()
+    for i in range(len(L1)):
+        a, b = int(L1[i]), int(L2[i])
+        touch = True
+        for ax in range(d):
+            lo1, hi1 = Fraction(int(co[a, ax]), 3 ** int(lev[a])), Fraction(int(co[a, ax]) + 1, 3 ** int(lev[a]))
+            lo2, hi2 = Fraction(int(co[b, ax]), 3 ** int(lev[b])), Fraction(int(co[b, ax]) + 1, 3 ** int(lev[b]))
+            touch &= any(lo1 <= hi2 + s and lo2 + s <= hi1 for s in (-1, 0, 1))
+        assert bool(tun[i]) == (not touch), i
+    assert tun.sum() > 0 and (~tun).sum() > 0
