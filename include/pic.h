@@ -349,6 +349,18 @@ PIC_API int pic_pidt_table(pic_t h, int32_t *level, int64_t *j);
  * Synchronous. */
 PIC_API int pic_retree(pic_t h, const pic_tree_desc *tree);
 
+/* The raPIDT tree attribute v_max (Section 5.4, the v_max equation): per node
+ * of the tree, in the level order of its refinement flags, the largest
+ * velocity component magnitude of the particles below it -- on a leaf, of its
+ * own particles (PIT) or of the particles of its 2^d vertices, i.e. of every
+ * dual cell intersecting it (PIDT); on a refined cell, the largest of its
+ * children's values.  node_vmax[n_nodes] (host memory, may be NULL);
+ * *n_closed (may be NULL) = the nodes with v_max dt < 3^-level, from which no
+ * particle can be removed by a lift within a step of dt.  Computed from the
+ * current particles on the device; synchronous; single-instance handles only
+ * (PIC_ESTATE otherwise). */
+PIC_API int pic_vmax(pic_t h, double *node_vmax, double dt, int64_t *n_closed);
+
 /* Level-order refinement flags of the current tree: with flags == NULL only
  * *n_nodes is written; else flags[n_nodes] (host memory). */
 PIC_API int pic_tree_flags(pic_t h, uint8_t *flags, int64_t *n_nodes);

@@ -227,6 +227,50 @@ class Tree:
         touch = (np.mod(lo2 - lo1, P) <= s1) | (np.mod(lo1 - lo2, P) <= s2)
         return ~np.all(touch, axis=1)
 
+    def vmax(self, scheme: int, leaf, key, v) -> np.ndarray:
+        """The raPIDT tree attribute v_max (Section 5.4) per tree node in the
+        level order of the refinement flags: on a leaf the largest velocity
+        component magnitude of its particles (PIT) or of the particles of its
+        2^d vertices, every dual cell intersecting it (PIDT); on a refined
+        cell the largest of its children's values (the v_max equation)."""
+        d = self.d
+        nc, nch = 1 << d, 3 ** d
+        v = np.abs(np.asarray(v, np.float64)).max(axis=0)
+        lev, co = self.leaf_info()
+        leaf_v = np.zeros(self.n_leaves)
+        if scheme == PIT:
+            np.maximum.at(leaf_v, np.asarray(leaf, np.int64), v)
+        else:
+            pv_lev, pv_j = self.pidt_vertices()
+            vert_v = np.zeros(len(pv_lev))
+            np.maximum.at(vert_v, np.asarray(key, np.int64) // nc, v)
+            index = {(int(l), tuple(int(c) for c in j)): i for i, (l, j) in enumerate(zip(pv_lev, pv_j))}
+            for L in range(self.n_leaves):
+                per = 3 ** int(lev[L])
+                for e in range(nc):
+                    j = tuple((int(co[L, a]) + ((e >> a) & 1)) % per for a in range(d))
+                    leaf_v[L] = max(leaf_v[L], vert_v[index[(int(lev[L]), j)]])
+        # level-order nodes: children of the k-th refined node are 1 + nch k ...
+        flags = self.flags
+        n_nodes = len(flags)
+        child0 = np.full(n_nodes, -1, np.int64)
+        refined = np.flatnonzero(flags)
+        child0[refined] = 1 + nch * np.arange(len(refined))
+        # depth-first leaf numbering (children in digit order)
+        leaf_of_node = np.full(n_nodes, -1, np.int64)
+        stack, next_leaf = [0], 0
+        while stack:
+            i = stack.pop()
+            if child0[i] < 0:
+                leaf_of_node[i] = next_leaf
+                next_leaf += 1
+            else:
+                stack.extend(range(child0[i] + nch - 1, child0[i] - 1, -1))
+        out = np.zeros(n_nodes)
+        for i in range(n_nodes - 1, -1, -1):  # children follow their parents in level order
+            out[i] = leaf_v[leaf_of_node[i]] if child0[i] < 0 else out[child0[i]:child0[i] + nch].max()
+        return out
+
     # ---- keys -----------------------------------------------------------
     def pit_owner(self, x: np.ndarray) -> np.ndarray:
         x = _c(x, np.float64)

@@ -491,7 +491,17 @@ __global__ void k_push64(DevTree t, Push64Args a) {
       L2 = I.leaf_off + uniform_leaf_of_cell(t.spread + I.spread_off, I.M, cc, d);
       lev2 = I.depth;
     } else {
-      L2 = descend_q(t.tab, d, Q, &lev2, I.tab_root);
+      // still inside its leaf (the radius of operation of Section 5.3): the
+      // covering leaf is the old one, no descent
+      const uint32_t step = 2u * c_pow3[18 - lev];
+      bool inside = true;
+      for (int ax = 0; ax < d; ++ax) inside &= Q[ax] / step == (uint32_t)c[ax];
+      if (inside) {
+        L2 = L;
+        lev2 = lev;
+      } else {
+        L2 = descend_q(t.tab, d, Q, &lev2, I.tab_root);
+      }
     }
     knew = key_of(t, L2, pidt_corner_q(Q, lev2, d));
     int32_t kold = t.scheme == 0 ? L : a.key[p];
@@ -568,8 +578,16 @@ __global__ void k_push32(DevTree t, Push32Args a) {
     float o2[3] = {0.f, 0.f, 0.f};
     int lev2;
     int32_t L2;
+    bool inside = true;  // target cell == the particle's own leaf cell
+    for (int ax = 0; ax < d; ++ax) inside &= I[ax] == c[ax];
     if (t.uniform) {  // the covering leaf is the target cell itself; o = f
       L2 = Ins.leaf_off + uniform_leaf_of_cell(t.spread + Ins.spread_off, Ins.M, I, d);
+      for (int ax = 0; ax < d; ++ax) o2[ax] = clamp_off(f[ax]);
+    } else if (inside) {
+      // still inside its leaf (the radius of operation of Section 5.3): no
+      // lift, no drop -- the covering leaf is the old one and o = f
+      L2 = L;
+      lev2 = lev;
       for (int ax = 0; ax < d; ++ax) o2[ax] = clamp_off(f[ax]);
     } else {
       L2 = descend_split(t.tab, d, lev, I, f, o2, &lev2, Ins.tab_root);
@@ -1366,6 +1384,72 @@ void launch_lift_drop_pidt(const DevTree &t, const int32_t *pv_level, const int3
     COUNT(1);
     k_lift_drop_pidt<<<grid_for(n), kBlock, 0, s>>>(t, pv_level, pv_j, ids, leaf, key, old_leaf_by_id, old_key_by_id,
                                                     n, counts);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// raPIDT tree attribute v_max (Section 5.4)
+// ---------------------------------------------------------------------------
+
+// Per leaf: the largest velocity component magnitude of its particles -- PIT:
+// the leaf's bucket; PIDT: the buckets of the leaf's 2^d vertices, i.e. every
+// dual cell intersecting the leaf (the paper's definition).
+template <typename T>
+__global__ void k_leaf_vmax(DevTree t, const int32_t *__restrict__ start, const T *__restrict__ v, int64_t n,
+                            double *leaf_vmax) {
+  const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= t.n_leaves) return;
+  double m = 0.0;
+  const int na = t.scheme == 0 ? 1 : t.nc;
+  for (int a = 0; a < na; ++a) {
+    int32_t k0, k1;
+    if (t.scheme == 0) {
+      k0 = (int32_t)L;
+      k1 = k0 + 1;
+    } else {
+      k0 = pidt_vertex(t, (int32_t)L, a) * t.nc;
+      k1 = k0 + t.nc;
+    }
+    for (int32_t p = start[k0]; p < start[k1]; ++p)
+      for (int ax = 0; ax < t.d; ++ax) {
+        const double x = fabs((double)v[ax * n + p]);
+        m = x > m ? x : m;
+      }
+  }
+  leaf_vmax[L] = m;
+}
+
+// Per tree node of one level (level order): a leaf takes its leaf's value,
+// a refined node the largest of its 3^d children's (Eq. v_max).
+__global__ void k_node_vmax(const int32_t *child0, const int32_t *leaf_of_node, int64_t b, int64_t e, int nch,
+                            const double *leaf_vmax, double *node_vmax) {
+  const int64_t i = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= e) return;
+  if (leaf_of_node[i] >= 0) {
+    node_vmax[i] = leaf_vmax[leaf_of_node[i]];
+    return;
+  }
+  double m = 0.0;
+  for (int k = 0; k < nch; ++k) {
+    const double x = node_vmax[child0[i] + k];
+    m = x > m ? x : m;
+  }
+  node_vmax[i] = m;
+}
+
+void launch_vmax(const DevTree &t, bool split, const int32_t *start, const void *v, int64_t n, const int32_t *child0,
+                 const int32_t *leaf_of_node, const int64_t *level_begin, int depth, double *leaf_vmax,
+                 double *node_vmax, cudaStream_t s) {
+  COUNT(1);
+  if (split)
+    k_leaf_vmax<float><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, (const float *)v, n, leaf_vmax);
+  else
+    k_leaf_vmax<double><<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, start, (const double *)v, n, leaf_vmax);
+  for (int l = depth; l >= 0; --l) {
+    const int64_t b = level_begin[l], e = level_begin[l + 1];
+    if (e <= b) continue;
+    COUNT(1);
+    k_node_vmax<<<grid_for(e - b), kBlock, 0, s>>>(child0, leaf_of_node, b, e, t.nch, leaf_vmax, node_vmax);
   }
 }
 

@@ -190,6 +190,12 @@ void launch_widen(const float *in, int64_t n, double *out, cudaStream_t s);
 void launch_gather_only(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n,
                         const void *Ev, void *Ep, cudaStream_t s);
 void launch_half_kick(bool split, const void *Ep, int64_t n_total, double c, void *v, cudaStream_t s);
+// raPIDT v_max: per leaf (largest |velocity component| of its particles, or
+// of its vertices' particles for PIDT), then per node of the level-ordered
+// tree bottom-up (level_begin[l] = first node of level l, depth + 2 entries).
+void launch_vmax(const DevTree &t, bool split, const int32_t *start, const void *v, int64_t n, const int32_t *child0,
+                 const int32_t *leaf_of_node, const int64_t *level_begin, int depth, double *leaf_vmax,
+                 double *node_vmax, cudaStream_t s);
 // lift and drop counts (diagnostic): counts[0..2] = lifts, drops, tunnellers
 void launch_scatter_by_id(const int32_t *ids, const int32_t *leaf, int64_t n, int32_t *by_id, cudaStream_t s);
 void launch_lift_drop(const DevTree &t, const int32_t *ids, const int32_t *leaf, const int32_t *old_by_id, int64_t n,

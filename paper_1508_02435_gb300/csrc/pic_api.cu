@@ -1790,6 +1790,44 @@ int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax) {
   return pic_retree(h, &td);
 }
 
+int pic_vmax(pic_t h, double *node_vmax, double dt, int64_t *n_closed) {
+  if (check_handle(h)) return PIC_EINVAL;
+  if (h->dt.n_inst > 1) return fail(h, PIC_ESTATE, "v_max is kept for single-instance handles");
+  int rc;
+  if ((rc = ensure_leaf(h))) return rc;
+  const auto &t = h->ht;
+  std::vector<int64_t> lb(t.depth + 2, t.n_nodes);
+  for (int64_t i = t.n_nodes - 1; i >= 0; --i) lb[t.level[i]] = i;  // level order: first node of each level
+  for (int l = t.depth; l >= 0; --l) lb[l] = std::min(lb[l], lb[l + 1]);
+  std::vector<DevBuf> tmp;
+  const int32_t *c0 = nullptr, *lon = nullptr;
+  double *leaf_v = nullptr, *node_v = nullptr;
+  if ((rc = upload(h, tmp, &c0, t.child0)) || (rc = upload(h, tmp, &lon, t.leaf_of_node)) ||
+      (rc = dalloc(h, tmp, &leaf_v, std::max<int64_t>(t.n_leaves, 1))) ||
+      (rc = dalloc(h, tmp, &node_v, std::max<int64_t>(t.n_nodes, 1)))) {
+    free_bufs(h, tmp);
+    return rc;
+  }
+  launch_vmax(h->dt, h->split, h->start_cur, h->vel[0], h->n, c0, lon, lb.data(), t.depth, leaf_v, node_v,
+              h->stream);
+  std::vector<double> out(t.n_nodes);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out.data(), node_v, sizeof(double) * t.n_nodes, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  free_bufs(h, tmp);
+  if (e != cudaSuccess) return cuda_fail(h, e, "v_max");
+  if (node_vmax) std::copy(out.begin(), out.end(), node_vmax);
+  if (n_closed) {
+    // cells no particle can leave by a lift within dt: v_max dt < h = 3^-level
+    int64_t c = 0;
+    for (int64_t i = 0; i < t.n_nodes; ++i)
+      if (out[i] * dt < 1.0 / (double)pow3(t.level[i])) ++c;
+    *n_closed = c;
+  }
+  return PIC_OK;
+}
+
 int pic_tree_flags(pic_t h, uint8_t *flags, int64_t *n_nodes) {
   if (check_handle(h)) return PIC_EINVAL;
   int64_t total = 0;

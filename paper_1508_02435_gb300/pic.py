@@ -111,6 +111,7 @@ SIGNATURES = [
     ("pic_save", C.c_int, [C.c_void_p, C.c_char_p]),
     ("pic_load", C.c_int, [C.POINTER(C.c_void_p), C.c_char_p, C.c_void_p]),
     ("pic_set_wait_limit", C.c_int, [C.c_void_p, C.c_int64]),
+    ("pic_vmax", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
     ("pic_wait_selftest", C.c_int, [C.c_int64, C.c_void_p]),
 ]
 
@@ -417,6 +418,16 @@ class Pic:
 
     def sync(self):
         self._check(self.lib.pic_sync(self.h))
+
+    def vmax(self, dt: float = 0.0):
+        """(v_max per tree node in level order, nodes closed for a step of dt)
+        -- the raPIDT tree attribute (pic_vmax)."""
+        nn = C.c_int64(0)
+        self._check(self.lib.pic_tree_flags(self.h, None, C.byref(nn)))
+        out = np.zeros(nn.value)
+        closed = C.c_int64(0)
+        self._check(self.lib.pic_vmax(self.h, _ptr(out)[0], float(dt), C.byref(closed)))
+        return out, closed.value
 
     def set_wait_limit(self, cycles: int):
         """Limit (SM clocks) of the bounded device waits of later steps."""

@@ -635,3 +635,51 @@ def test_tunnellers_exact_geometry(d, depth, p, seed):
             touch &= any(lo1 <= hi2 + s and lo2 + s <= hi1 for s in (-1, 0, 1))
         assert bool(tun[i]) == (not touch), i
     assert tun.sum() > 0 and (~tun).sum() > 0
+
+
+@pytest.mark.parametrize("scheme", [oracle.PIT, oracle.PIDT])
+def test_vmax_is_the_subtree_maximum(scheme):
+    """raPIDT v_max per node equals, by brute force over the subtree's leaf
+    boxes, the largest velocity component of the particles inside it (PIT) or
+    inside any dual cell that meets a leaf below it (PIDT: the dual cell of
+    vertex (l, j) of a leaf on level l, found by scanning the particles'
+    owners)."""
+    d = 2
+    flags = W.random_tree_flags(d, 4, 0.35, 301, min_depth=1)
+    t = oracle.Tree(d, flags)
+    x, v = W.random_particles(d, 3000, 301, vmax=1.0)
+    leaf = t.pit_owner(x)
+    key = t.keys64(oracle.PIDT, x)
+    out = t.vmax(scheme, leaf, key, v)
+    vabs = np.abs(v).max(axis=0)
+    root = LA.parse_tree(d, flags)
+    nodes, queue = [], [root]          # level order
+    while queue:
+        c = queue.pop(0)
+        nodes.append(c)
+        if c.children:
+            queue.extend(c.children)
+    assert len(nodes) == len(out)
+    pv_lev, pv_j = t.pidt_vertices()
+    own_l = pv_lev[key // 4]
+    own_j = pv_j[key // 4]
+    Q = quantise_np(x)
+    for i, c in enumerate(nodes):
+        s = 2 * 3 ** (18 - c.level)
+        if scheme == oracle.PIT:
+            inside = np.all([(Q[a] >= c.coords[a] * s) & (Q[a] < (c.coords[a] + 1) * s) for a in range(d)], axis=0)
+        else:
+            # particles whose owner vertex is a corner of a leaf inside c
+            inside = np.zeros(x.shape[1], bool)
+            stack = [c]
+            while stack:
+                cc = stack.pop()
+                if cc.children:
+                    stack.extend(cc.children)
+                    continue
+                per = 3 ** cc.level
+                for e in itertools.product((0, 1), repeat=d):
+                    j = [(cc.coords[a] + e[a]) % per for a in range(d)]
+                    inside |= (own_l == cc.level) & np.all(own_j == np.array(j)[None, :], axis=1)
+        expect = vabs[inside].max() if inside.any() else 0.0
+        assert out[i] == expect, (i, c.level, c.coords)
