@@ -1,7 +1,8 @@
 """The raPIDT tree attribute v_max (pic_vmax) against the oracle's, after
-steps, on adaptive and uniform trees, PIT and PIDT, FP64 and split: equal
-node by node (a maximum is exact), and the count of closed cells
-(v_max dt < 3^-level) the same."""
+steps, on adaptive and uniform trees, PIT and PIDT, FP64 and split: node by
+node equal (split: the same FP32 velocities, so the same maxima) or within
+1e-12 (FP64 velocities, whose last bits follow the field's summation
+order), and the count of closed cells (v_max dt < 3^-level) the same."""
 from __future__ import annotations
 
 import numpy as np
@@ -44,7 +45,10 @@ def test_vmax_matches_oracle(d, flags_fn, scheme, precision):
     leaf = st.leaf if split else ot.pit_owner(st.x)
     expect = ot.vmax(scheme, leaf, st.key, st.v)
     got, closed = g.vmax(dt=0.05)
-    assert np.array_equal(got, expect)
+    if split:   # the same FP32 velocities: the maxima are the same bits
+        assert np.array_equal(got, expect)
+    else:       # FP64 velocities agree to 1e-12 (the field's summation order differs)
+        assert np.allclose(got, expect, rtol=1e-12, atol=0.0)
     lev = np.zeros(len(expect), np.int64)
     # node levels in level order, from the flags
     nch, cur, i = 3 ** d, [0], 0
