@@ -868,7 +868,7 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
   __shared__ int32_t cur[K::LH];
   __shared__ int32_t wsum[kStThreads / 32];
   __shared__ int32_t s_max, s_ccount[4];
-  __shared__ uint64_t s_bar;
+  __shared__ uint64_t s_bar, s_bar2;  // keys and codes; offsets and velocities
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const BrickStage &st = a.st;
   const int32_t u = blockIdx.x, b = u >> 1;
@@ -882,35 +882,46 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
   if (tid == 0) {
     s_max = 0;
     if (nin > 0) {
+      // keys and codes on one barrier, the state rows on another: the counts,
+      // offsets and per-leaf sorts need only the former, so they start while
+      // the state (24 of the 30 bytes per arrival) is still landing
       mbar_init(&s_bar, 1);
+      mbar_init(&s_bar2, 1);
       const uint32_t rb = (uint32_t)((nin * 4 + 15) & ~15), cb = (uint32_t)((nin * 2 + 15) & ~15);
-      mbar_expect_tx(&s_bar, 2u * D * rb + rb + cb);
-      for (int ax = 0; ax < D; ++ax) {
-        bulk_g2s(so + ax * kStCap, st.o + ax * st.row + at, rb, &s_bar);
-        bulk_g2s(sv + ax * kStCap, st.v + ax * st.row + at, rb, &s_bar);
-      }
+      mbar_expect_tx(&s_bar, rb + cb);
       bulk_g2s(key, st.key + at, rb, &s_bar);
       bulk_g2s(code, st.code + at, cb, &s_bar);
+      mbar_expect_tx(&s_bar2, 2u * D * rb);
+      for (int ax = 0; ax < D; ++ax) {
+        bulk_g2s(so + ax * kStCap, st.o + ax * st.row + at, rb, &s_bar2);
+        bulk_g2s(sv + ax * kStCap, st.v + ax * st.row + at, rb, &s_bar2);
+      }
     }
   }
   for (int i = tid; i <= nlf; i += blockDim.x) cnt[i] = 0;
-  __syncthreads();  // the barrier is initialised and armed before anyone waits on it
+  __syncthreads();  // the barriers are initialised and armed before anyone waits on them
   {
     const bool landed = nin == 0 || mbar_wait(&s_bar, 0, a.wait_cycles);
     if (__syncthreads_or(!landed)) {
-      if (!landed) mbar_wait(&s_bar, 0, kWaitCycles);  // let copies in flight land before leaving
+      if (nin > 0) {  // let copies in flight land before leaving
+        if (!landed) mbar_wait(&s_bar, 0, kWaitCycles);
+        mbar_wait(&s_bar2, 0, kWaitCycles);
+      }
       if (tid == 0) atomicOr(a.err, kErrTimeout);
       return;
     }
   }
-  // leaf counts: four consecutive arrivals per thread, one shared atomic per run
+  // leaf counts: four consecutive arrivals per thread (one 8-byte load of
+  // their codes), one shared atomic per run
   bool badc = false;
   for (int32_t r0 = 4 * tid; r0 < nin; r0 += 4 * kStThreads) {
     int leaf = -1, run = 0;
+    const uint2 c4 = *reinterpret_cast<const uint2 *>(code + r0);
+    const uint32_t cw[2] = {c4.x, c4.y};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (r0 + k >= nin) break;
-      const int lf = (code[r0 + k] & 0x3ff) - lf0;
+      const int lf = (int)((cw[k >> 1] >> (16 * (k & 1))) & 0x3ffu) - lf0;
       if (lf < 0 || lf >= nlf) {
         badc = true;
         continue;
@@ -987,7 +998,14 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
   for (int l = tid; l < nlf; l += blockDim.x) a.new_start[L0 + l] = bstart + cnt[l];
   if (u == 2 * g.n_bricks - 1 && tid == 0) a.new_start[(int64_t)g.n_bricks * K::LB] = bstart + nin;
   if (tid == 0 && s_max > 0) atomicMax(a.max_bucket, s_max);
-  __syncthreads();
+  {
+    const bool landed = nin == 0 || mbar_wait(&s_bar2, 0, a.wait_cycles);
+    if (__syncthreads_or(!landed)) {
+      if (!landed) mbar_wait(&s_bar2, 0, kWaitCycles);  // let copies in flight land before leaving
+      if (tid == 0) atomicOr(a.err, kErrTimeout);
+      return;
+    }
+  }
   // coalesced writes in destination order
   {
     float *gO[D], *gV[D];
