@@ -327,11 +327,11 @@ __device__ __forceinline__ void stage_put(const BrickStage &st, int32_t dest, in
                                           const float *vn, uint16_t code, uint32_t key, int32_t id, bool with_id,
                                           int32_t *err) {
   if (slot < st.cap) {
-    const int64_t at = (int64_t)dest * st.cap + slot;
+    const uint32_t at = (uint32_t)dest * (uint32_t)st.cap + (uint32_t)slot;  // < 2^31 (checked at set-up)
 #pragma unroll
     for (int ax = 0; ax < D; ++ax) {
-      st.o[ax * st.row + at] = on[ax];
-      st.v[ax * st.row + at] = vn[ax];
+      st.orow[ax][at] = on[ax];
+      st.vrow[ax][at] = vn[ax];
     }
     st.code[at] = code;
     st.key[at] = key;

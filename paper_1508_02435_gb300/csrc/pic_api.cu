@@ -523,9 +523,13 @@ int setup_brick(pic_t h) {
   st.row = nu * st.cap + 16;
   // a tree with many more bricks than particles would spend more memory on
   // empty staging areas than on the particles: the generic path serves it
-  if (nu * st.cap > 16 * n + (int64_t(1) << 24)) return PIC_OK;
+  if (nu * st.cap > 16 * n + (int64_t(1) << 24) || st.row >= (int64_t(1) << 31)) return PIC_OK;
   if ((rc = dalloc(h, bb, &st.o, st.row * t.d))) return rc;
   if ((rc = dalloc(h, bb, &st.v, st.row * t.d))) return rc;
+  for (int ax = 0; ax < 3; ++ax) {
+    st.orow[ax] = st.o + (ax < t.d ? ax : 0) * st.row;
+    st.vrow[ax] = st.v + (ax < t.d ? ax : 0) * st.row;
+  }
   if ((rc = dalloc(h, bb, &st.code, st.row))) return rc;
   if ((rc = dalloc(h, bb, &st.key, st.row))) return rc;
   if (h->cfg.track_ids && (rc = dalloc(h, bb, &st.id, st.row))) return rc;
