@@ -78,6 +78,8 @@ def _load():
             "or_efield64": (None, [P, P, P]),
             "or_push64": (None, [P, i64, P, P, P, f64, f64]),
             "or_gather64": (None, [P, i64, P, P, P]),
+            "or_move64": (None, [P, i64, P, P, f64, i32]),
+            "or_move32": (None, [P, i64, P, P, P, f64, i32]),
             "or_split_from64": (None, [P, i64, P, P, P, P, P]),
             "or_split_to64": (None, [P, i64, P, P, P]),
             "or_keys32": (None, [P, i32, i64, P, P, P]),
@@ -431,6 +433,17 @@ class Tree:
         Ev = _c(Ev, np.float32)
         self._lib.or_push32(self._h, len(leaf), _p(leaf), _p(o), _p(v), _p(Ev), qm, dt)
 
+    def move64(self, x, v, dt, reflect):
+        """In place: the particle-handling move of Section 6 (no field),
+        periodic (reflect = 0) or reflecting walls (reflect = 1)."""
+        assert x.dtype == np.float64 and x.flags.c_contiguous and v.flags.c_contiguous
+        self._lib.or_move64(self._h, x.shape[1], _p(x), _p(v), dt, int(reflect))
+
+    def move32(self, leaf, o, v, dt, reflect):
+        """In place: the same move in the split representation."""
+        assert leaf.dtype == np.int32 and o.dtype == np.float32 and v.dtype == np.float32
+        self._lib.or_move32(self._h, len(leaf), _p(leaf), _p(o), _p(v), dt, int(reflect))
+
     def rebin32_into(self, new_tree: "Tree", leaf, o):
         """In place: same split positions, re-located in ``new_tree``."""
         self._lib.or_rebin32(self._h, new_tree._h, len(leaf), _p(leaf), _p(o))
@@ -529,6 +542,11 @@ class State64:
         self.v = self.v - (self.p.qm * (0.5 * dt)) * Ep
         return Q
 
+    def move(self, dt, reflect):
+        """The particle-handling step of Section 6: move (no field) and re-bin."""
+        self.tree.move64(self.x, self.v, dt, reflect)
+        self.rebin()
+
     def step(self, dt):
         """One PIC step: deposit, solve, field, gather + push, re-bin.
         Returns (Q, total charge, residual, vertex field) of x_n."""
@@ -573,6 +591,10 @@ class State32:
         half = np.float32(self.p.qm * (0.5 * dt))
         self.v = (self.v - half * Ep).astype(np.float32)
         return Q
+
+    def move(self, dt, reflect):
+        self.tree.move32(self.leaf, self.o, self.v, dt, reflect)
+        self.rebin()
 
     def step(self, dt):
         Q, tot, res, E = self.field()

@@ -847,6 +847,43 @@ OR_API void or_push64(ortree *t, int64_t n, double *x, double *v, const double *
   }
 }
 
+/* The particle-handling step of the paper's experiments (Section 6): no PDE
+ * and no particle-grid interplay, every particle moves with its own velocity,
+ * x <- x + RN(v dt), and either wraps (periodic, reflect = 0) or is reflected
+ * at the walls of the unit box without any other change of its velocity
+ * (reflect = 1).  Reading of the reflection for any number of wall hits:
+ * y = x + v dt is folded into [0, 2) (y - 2 floor(y / 2), exact), and
+ * y >= 1 becomes 2 - y (exact) with the velocity component negated (an odd
+ * number of reflections); a particle that lands exactly on the far wall
+ * (y == 1) is placed at the largest double below 1. */
+static const double OR_ONE_MINUS64 = 0x1.fffffffffffffp-1;
+
+static double fold64(double y, int *flip) {
+  double m = y - 2.0 * floor(y * 0.5);
+  *flip = 0;
+  if (m >= 1.0) {
+    m = 2.0 - m;
+    *flip = 1;
+    if (m >= 1.0) m = OR_ONE_MINUS64;
+  }
+  return m;
+}
+
+OR_API void or_move64(ortree *t, int64_t n, double *x, double *v, double dt, int reflect) {
+  int d = t->d;
+  for (int64_t p = 0; p < n; ++p)
+    for (int a = 0; a < d; ++a) {
+      double y = x[a * n + p] + v[a * n + p] * dt;
+      if (reflect) {
+        int flip;
+        x[a * n + p] = fold64(y, &flip);
+        if (flip) v[a * n + p] = -v[a * n + p];
+      } else {
+        x[a * n + p] = wrap01(y);
+      }
+    }
+}
+
 /* Only the gather (for tests): E at the particles, [d][n]. */
 OR_API void or_gather64(ortree *t, int64_t n, const double *x, const double *Ev, double *Ep) {
   or_grid_build(t);
@@ -1136,6 +1173,61 @@ OR_API void or_push32(ortree *t, int64_t n, int32_t *leaf, float *o, float *v, c
     for (int a = 0; a < d; ++a) o[a * n + p] = on[a];
   }
   free(Ec);
+}
+
+/* The particle-handling step (or_move64) in the split representation: t =
+ * RN32(o + RN32(v s_l)), n = floor t, f = t - n, target cell I = c + n on the
+ * leaf's level (per = 3^l cells).  Periodic: I mod per.  Reflecting: with
+ * Im = I mod 2 per, Im < per keeps (Im, f); otherwise the point is mirrored,
+ * (2 per - 1 - Im, RN32(1 - f)) for f > 0 and (2 per - Im, 0) for f = 0, and
+ * the velocity component negated; a point on the far wall goes to the last
+ * cell with the largest offset below 1.  Then the integer lift/drop
+ * re-location of or_push32. */
+OR_API void or_move32(ortree *t, int64_t n, int32_t *leaf, float *o, float *v, double dt, int reflect) {
+  int d = t->d;
+  for (int64_t p = 0; p < n; ++p) {
+    int32_t nd = t->leaf_node[leaf[p]];
+    int lev = t->level[nd];
+    int64_t per = p3(lev);
+    float sl = (float)(dt * (double)per);
+    int64_t I[3] = {0, 0, 0};
+    float f[3] = {0.0f, 0.0f, 0.0f};
+    for (int a = 0; a < d; ++a) {
+      float vn = v[a * n + p];
+      float tt = o[a * n + p] + vn * sl;
+      float fl = floorf(tt);
+      float fr = tt - fl;
+      int64_t c = t->coords[nd * 3 + a] + (int64_t)fl;
+      if (!reflect) {
+        c %= per;
+        if (c < 0) c += per;
+      } else {
+        int64_t p2 = 2 * per, im = c % p2;
+        if (im < 0) im += p2;
+        if (im < per) {
+          c = im;
+        } else {
+          v[a * n + p] = -vn;
+          if (fr > 0.0f) {
+            c = p2 - 1 - im;
+            fr = clamp_off(1.0f - fr);
+          } else {
+            c = p2 - im;
+            if (c >= per) {
+              c = per - 1;
+              fr = OR_ONE_MINUS;
+            }
+          }
+        }
+      }
+      I[a] = c;
+      f[a] = fr;
+    }
+    float on[3];
+    int32_t nn = resolve32(t, lev, I, f, on);
+    leaf[p] = t->leaf_id[nn];
+    for (int a = 0; a < d; ++a) o[a * n + p] = on[a];
+  }
 }
 
 OR_API void or_gather32(ortree *t, int64_t n, const int32_t *leaf, const float *o, const float *Ev,

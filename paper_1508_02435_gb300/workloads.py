@@ -33,6 +33,7 @@ __all__ = [
     "batched_langmuir",
     "random_tree_flags",
     "random_particles",
+    "particle_handling",
     "random_field",
 ]
 
@@ -259,6 +260,22 @@ def batched_langmuir(n_inst: int = 256, n_min: int = 1000, n_max: int = 1_000_00
                             q=-1.0 / n, qm=-1.0, ion=1.0, dt=dt, steps=steps, k_mode=k,
                             vth=vth, extra={"depth": depth}))
     return out
+
+
+def particle_handling(d: int, n: int, dam: bool = False, seed: int = 0, base_depth: int = 1) -> Workload:
+    """The particle-handling workload of the paper's experiments (Section 6):
+    no field; positions uniform in the unit box, or in the corner (0, 0.1)^d
+    ("breaking dam", dam=True); velocities of uniformly distributed speed
+    0 <= |v| <= 1 in a uniformly random direction.  The tree returned is the
+    uniform base tree; the ppc criterion refines it."""
+    rng = np.random.default_rng(seed)
+    x = rng.random((d, n)) * (0.1 if dam else 1.0)
+    dirs = rng.standard_normal((d, n))
+    dirs /= np.linalg.norm(dirs, axis=0, keepdims=True)
+    v = dirs * rng.random(n)[None, :]
+    return Workload(name="particle_handling_dam" if dam else "particle_handling", d=d,
+                    flags=uniform_tree_flags(d, base_depth), x=x, v=v, q=0.0, qm=0.0, ion=0.0, dt=1e-3,
+                    steps=10, extra={"dam": dam, "base_depth": base_depth})
 
 
 def random_particles(d: int, n: int, seed: int, vmax: float = 1.0) -> tuple[np.ndarray, np.ndarray]:

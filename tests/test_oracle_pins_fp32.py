@@ -683,3 +683,78 @@ def test_vmax_is_the_subtree_maximum(scheme):
                     inside |= (own_l == cc.level) & np.all(own_j == np.array(j)[None, :], axis=1)
         expect = vabs[inside].max() if inside.any() else 0.0
         assert out[i] == expect, (i, c.level, c.coords)
+
+
+# ---------------------------------------------------------------------------
+# the particle-handling step of Section 6 (no field, reflecting walls)
+# ---------------------------------------------------------------------------
+
+def _triangle(y: Fraction) -> tuple[Fraction, int]:
+    """Exact position after reflections at 0 and 1 of the free motion to y,
+    and the number of wall hits."""
+    k = y // 1                                  # floor
+    r = y - k
+    hits = int(k) if k >= 0 else -int(k)
+    if int(k) % 2 == 0:
+        return r, hits
+    return 1 - r, hits
+
+
+def test_move64_reflection_closed_form():
+    """A free particle between reflecting walls follows the triangle wave of
+    x0 + v t: after every FP64 step the position equals the exact fold of
+    the (rounded) free path to within the roundings of that path, and the
+    velocity's sign is (-1)^(wall hits)."""
+    d = 2
+    t = oracle.Tree(d, W.uniform_tree_flags(d, 2))
+    x0 = np.array([[0.1, 0.95, 0.5, 0.0], [0.3, 0.02, 0.999, 0.7]])
+    v0 = np.array([[0.9, -3.3, 12.25, 0.0], [-0.45, 1.0, 7.0, -2.5]])
+    x, v = x0.copy(), v0.copy()
+    dt = 0.125
+    for step in range(1, 9):
+        t.move64(x, v, dt, 1)
+        for a in range(d):
+            for p in range(x.shape[1]):
+                y = Fraction(float(x0[a, p])) + Fraction(float(v0[a, p])) * step * Fraction(dt)
+                r, hits = _triangle(y)
+                assert abs(float(r) - x[a, p]) <= 1e-14 * step, (a, p, step)
+                assert np.sign(v[a, p]) == np.sign(v0[a, p]) * (-1) ** hits or v0[a, p] == 0.0
+                assert 0.0 <= x[a, p] < 1.0
+    assert np.array_equal(np.abs(v), np.abs(v0))
+
+
+def test_move64_far_wall_tie_and_periodic_mode():
+    d = 2
+    t = oracle.Tree(d, W.uniform_tree_flags(d, 1))
+    x = np.array([[0.5], [0.25]])
+    v = np.array([[0.5], [-0.25]])
+    t.move64(x, v, 1.0, 1)          # 0.5 + 0.5 = 1 exactly: the far wall
+    assert x[0, 0] == np.nextafter(1.0, 0.0) and v[0, 0] == -0.5
+    assert x[1, 0] == 0.0 and v[1, 0] == -0.25   # 0.25 - 0.25 = 0: no reflection
+    x = np.array([[0.75], [0.1]])
+    v = np.array([[0.5], [-0.3]])
+    t.move64(x, v, 1.0, 0)          # periodic: wrap, velocity kept
+    assert x[0, 0] == 0.25 and v[0, 0] == 0.5
+    assert abs(x[1, 0] - 0.8) < 1e-15 and v[1, 0] == -0.3
+
+
+@pytest.mark.parametrize("d,flags_fn", TREES)
+def test_move32_tracks_move64(d, flags_fn):
+    """The split move lands every particle in the leaf that covers the FP64
+    move of the same particle (away from faces by 2^-18 of a cell), at the
+    same position to FP32 rounding of the cell-unit displacement, with the
+    same velocity signs."""
+    flags = flags_fn()
+    t = oracle.Tree(d, flags)
+    w = W.particle_handling(d, 4000, seed=31)
+    leaf, o, vf = t.split_from64(w.x, w.v)
+    x64, v64 = t.split_to64(leaf, o), vf.astype(np.float64)
+    dt = 0.3
+    t.move32(leaf, o, vf, dt, 1)
+    t.move64(x64, v64, dt, 1)
+    xr = t.split_to64(leaf, o)
+    assert np.all((o >= 0) & (o < 1))
+    assert np.max(np.abs(xr - x64)) < 1e-5
+    assert np.array_equal(np.sign(vf), np.sign(v64)) or np.all((np.sign(vf) == np.sign(v64)) | (v64 == 0))
+    near = np.any((o < 2 ** -18) | (o > 1 - 2 ** -18), axis=0)
+    assert np.all((t.pit_owner(x64) == leaf) | near)
