@@ -196,6 +196,22 @@ PIC_API int pic_step(pic_t h, double dt, pic_solve_fn hook, void *user);
  * solve: deposit of the current positions, gather + push + key, re-bin. */
 PIC_API int pic_step_fixed_field(pic_t h, double dt);
 
+/* The particle-handling step of the paper's experiments (Section 6): no
+ * field solve and no particle-grid interplay -- every particle moves by its
+ * own velocity, x <- x + v dt, then is re-binned (PIT / PIDT) like after a
+ * PIC push.  boundary = PIC_PERIODIC wraps the unit box; PIC_REFLECT
+ * reflects at its walls without any other change of the velocity (the
+ * velocity component is negated after an odd number of wall hits; a particle
+ * landing exactly on the far wall is placed just inside it).  flops (0 ..
+ * 65536) artificial floating-point operations are spent per particle move
+ * (the paper's 0-4096 flops per move); they do not change any result.  The
+ * brick path is not used for this step (its kernels gather the field); lift
+ * counting applies.  Invalid boundary, flops or dt: PIC_EINVAL.  Drops
+ * captured graphs.  Asynchronous. */
+#define PIC_PERIODIC 0
+#define PIC_REFLECT 1
+PIC_API int pic_step_particles(pic_t h, double dt, int32_t boundary, int32_t flops);
+
 /* Capture the fixed-field step (deposit when due, gather + push + key,
  * re-bin) as CUDA graphs after one ordinary step; the handle's stream must
  * not be the legacy default stream.  Two graphs are kept because a step

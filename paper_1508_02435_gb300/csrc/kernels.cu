@@ -443,6 +443,30 @@ __device__ __forceinline__ void count_and_ballot(bool act, int32_t knew, bool mo
   }
 }
 
+// Artificial work of the paper's experiments (Section 6): `flops` floating
+// point operations per particle move (fused multiply-adds, two each), on a
+// value the move does not use; the never-taken test keeps them.
+template <typename T>
+__device__ __forceinline__ void artificial_flops(T seed, int32_t flops, int32_t *err) {
+  T acc = seed;
+  for (int32_t i = 0; i < flops; i += 2) acc = fma(acc, (T)0.999, (T)1e-3);
+  if (acc == (T)-12345.0) atomicOr(err, 0);
+}
+
+// Reflection at the walls of the unit box, FP64 (the oracle's reading): the
+// free path y folds into [0, 2); y >= 1 mirrors to 2 - y with the velocity
+// component negated; the far wall itself goes to the largest double below 1.
+__device__ __forceinline__ double fold64(double y, bool *flip) {
+  double m = y - 2.0 * floor(y * 0.5);
+  *flip = false;
+  if (m >= 1.0) {
+    m = 2.0 - m;
+    *flip = true;
+    if (m >= 1.0) m = 0x1.fffffffffffffp-1;
+  }
+  return m;
+}
+
 __global__ void k_push64(DevTree t, Push64Args a) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool act = p < a.n;
@@ -459,7 +483,9 @@ __global__ void k_push64(DevTree t, Push64Args a) {
     local_coords(a.x, n, p, lev, c, d, tl);
     double E[3] = {0.0, 0.0, 0.0};
     const InstInfo &I = inst_of_leaf(t, L);
-    if (t.uniform) {
+    if (!a.E) {
+      // the particle-handling move: no field, no kick
+    } else if (t.uniform) {
       int32_t vid[8];
       corner_vertices(I, c, d, vid);
       for (int e = 0; e < nc; ++e) {
@@ -475,13 +501,22 @@ __global__ void k_push64(DevTree t, Push64Args a) {
     uint32_t Q[3] = {0u, 0u, 0u};
     bool bad = false;
     for (int ax = 0; ax < d; ++ax) {
-      double vn = a.v[ax * n + p] + a.qmdt * E[ax];
-      double xn = wrap01(a.x[ax * n + p] + vn * a.dt);
+      double vn = a.E ? a.v[ax * n + p] + a.qmdt * E[ax] : a.v[ax * n + p];
+      const double y = a.x[ax * n + p] + vn * a.dt;
+      double xn;
+      if (a.reflect) {
+        bool flip;
+        xn = fold64(y, &flip);
+        if (flip) vn = -vn;
+      } else {
+        xn = wrap01(y);
+      }
       if (!isfinite(vn) || !isfinite(xn)) { bad = true; xn = 0.0; }
       a.tv[ax * n + p] = vn;
       a.tx[ax * n + p] = xn;
       Q[ax] = quantise(xn);
     }
+    if (a.flops > 0) artificial_flops<double>(tl[0], a.flops, a.err);
     if (bad) atomicOr(a.err, 1);
     int lev2;
     int32_t L2;
@@ -528,7 +563,9 @@ __global__ void k_push32(DevTree t, Push32Args a) {
     for (int ax = 0; ax < d; ++ax) o[ax] = a.o[ax * n + p];
     float E[3] = {0.f, 0.f, 0.f};
     const InstInfo &Ins = inst_of_leaf(t, L);
-    if (t.uniform) {
+    if (!a.E && !a.Ec) {
+      // the particle-handling move: no field, no kick
+    } else if (t.uniform) {
       int32_t vid[8];
       corner_vertices(Ins, c, d, vid);
       for (int e = 0; e < nc; ++e) {
@@ -554,26 +591,52 @@ __global__ void k_push32(DevTree t, Push32Args a) {
     int32_t I[3] = {0, 0, 0};
     float f[3] = {0.f, 0.f, 0.f};
     bool bad = false;
+    const bool field = a.E || a.Ec;
     for (int ax = 0; ax < d; ++ax) {
-      float vn = a.v[ax * n + p] + a.qmdt * E[ax];
+      float vn = field ? a.v[ax * n + p] + a.qmdt * E[ax] : a.v[ax * n + p];
       float tt = o[ax] + vn * sl;
       if (!isfinite(vn) || !isfinite(tt)) { bad = true; tt = 0.0f; }
       float fl = floorf(tt);
       f[ax] = tt - fl;
       int32_t cc;
-      if (fabsf(fl) < 1.0e9f) {
-        cc = c[ax] + (int32_t)fl;               // periodic wrap, 32-bit
-        if (cc < 0 || cc >= per) {
-          cc %= per;
-          if (cc < 0) cc += per;
+      if (!a.reflect) {
+        if (fabsf(fl) < 1.0e9f) {
+          cc = c[ax] + (int32_t)fl;               // periodic wrap, 32-bit
+          if (cc < 0 || cc >= per) {
+            cc %= per;
+            if (cc < 0) cc += per;
+          }
+        } else {
+          int64_t c64 = ((int64_t)c[ax] + (int64_t)fminf(fmaxf(fl, -1.0e15f), 1.0e15f)) % per;
+          cc = (int32_t)(c64 < 0 ? c64 + per : c64);
         }
       } else {
-        int64_t c64 = ((int64_t)c[ax] + (int64_t)fminf(fmaxf(fl, -1.0e15f), 1.0e15f)) % per;
-        cc = (int32_t)(c64 < 0 ? c64 + per : c64);
+        // reflecting walls (the oracle's reading): cell index folded modulo
+        // 2 per; the mirrored half maps to (2 per - 1 - Im, 1 - f), or to
+        // (2 per - Im, 0) when f = 0, with the velocity component negated
+        const int64_t p2 = 2 * (int64_t)per;
+        int64_t im = ((int64_t)c[ax] + (int64_t)fminf(fmaxf(fl, -1.0e15f), 1.0e15f)) % p2;
+        if (im < 0) im += p2;
+        if (im < per) {
+          cc = (int32_t)im;
+        } else {
+          vn = -vn;
+          if (f[ax] > 0.0f) {
+            cc = (int32_t)(p2 - 1 - im);
+            f[ax] = clamp_off(1.0f - f[ax]);
+          } else {
+            cc = (int32_t)(p2 - im);
+            if (cc >= per) {
+              cc = per - 1;
+              f[ax] = 0x1.fffffep-1f;
+            }
+          }
+        }
       }
       I[ax] = cc;
       a.tv[ax * n + p] = vn;
     }
+    if (a.flops > 0) artificial_flops<float>(o[0], a.flops, a.err);
     if (bad) atomicOr(a.err, 1);
     float o2[3] = {0.f, 0.f, 0.f};
     int lev2;

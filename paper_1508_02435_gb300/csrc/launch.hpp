@@ -15,12 +15,14 @@ struct Push64Args {
   const int32_t *leaf, *key;    // key used by PIDT only
   double *tx, *tv;              // pushed state, same index
   int32_t *tleaf, *keyn;
-  const double *E;              // [d][n_vert]
+  const double *E;              // [d][n_vert]; NULL: no field (the particle-handling move, no kick)
   double qmdt, dt;
   int32_t *count;               // per key, zeroed before the launch
   uint32_t *mover_words;        // one ballot word per warp
   int32_t *block_movers;        // movers per block
   int32_t *err;
+  int32_t reflect;              // 1: reflecting walls of the unit box; 0: periodic
+  int32_t flops;                // artificial floating-point operations per particle move
 };
 
 struct Push32Args {
@@ -29,7 +31,7 @@ struct Push32Args {
   const int32_t *leaf, *key;
   float *to, *tv;
   int32_t *tleaf, *keyn;
-  const float *E;
+  const float *E;               // NULL (and Ec NULL): no field (the particle-handling move, no kick)
   const float4 *Ec;             // field at every leaf corner [leaf][corner] (adaptive trees), or NULL
   float qmdt;
   double dt;
@@ -38,6 +40,8 @@ struct Push32Args {
   uint32_t *mover_words;
   int32_t *block_movers;
   int32_t *err;
+  int32_t reflect;              // 1: reflecting walls of the unit box; 0: periodic
+  int32_t flops;                // artificial floating-point operations per particle move
 };
 
 struct RebinArgs {

@@ -743,8 +743,16 @@ int field(pic_t h, pic_solve_fn hook, void *user) {
   return PIC_OK;
 }
 
-int push_and_rebin(pic_t h, double dt) {
-  if (h->brick) return brick_push_and_rebin(h, dt);
+// What moves the particles: the PIC push (gather + kick + drift, periodic)
+// or the particle-handling move of the paper's experiments (no field,
+// periodic or reflecting walls, artificial flops per move).
+struct MoveKind {
+  bool field = true;
+  int32_t reflect = 0, flops = 0;
+};
+
+int push_and_rebin(pic_t h, double dt, MoveKind mk = MoveKind{}) {
+  if (h->brick && mk.field) return brick_push_and_rebin(h, dt);
   int rc0 = ensure_leaf(h);
   if (rc0) return rc0;
   h->q_valid = false;
@@ -763,14 +771,16 @@ int push_and_rebin(pic_t h, double dt) {
     a.tv = (float *)h->vel[1];
     a.tleaf = h->leaf[1];
     a.keyn = h->key[1];
-    a.E = (const float *)h->E;
-    if (h->ecorner) {
+    a.E = mk.field ? (const float *)h->E : nullptr;
+    if (h->ecorner && mk.field) {
       if (!h->ecorner_valid) {
         launch_corner_field32(h->dt, (const float *)h->E, h->ecorner, s);
         h->ecorner_valid = true;
       }
       a.Ec = h->ecorner;
     }
+    a.reflect = mk.reflect;
+    a.flops = mk.flops;
     a.qmdt = (float)(h->cfg.qm * dt);
     a.dt = dt;
     for (int l = 0; l <= 18; ++l) a.sl[l] = (float)(dt * (double)pow3(l));
@@ -790,7 +800,9 @@ int push_and_rebin(pic_t h, double dt) {
     a.tv = (double *)h->vel[1];
     a.tleaf = h->leaf[1];
     a.keyn = h->key[1];
-    a.E = (const double *)h->E;
+    a.E = mk.field ? (const double *)h->E : nullptr;
+    a.reflect = mk.reflect;
+    a.flops = mk.flops;
     a.qmdt = h->cfg.qm * dt;
     a.dt = dt;
     a.count = h->count;
@@ -1063,10 +1075,10 @@ static int lift_after(pic_t h) {
   return PIC_OK;
 }
 
-static int counted_push_and_rebin(pic_t h, double dt) {
+static int counted_push_and_rebin(pic_t h, double dt, MoveKind mk = MoveKind{}) {
   int rc;
   if (h->count_lifts && (rc = lift_before(h))) return rc;
-  if ((rc = push_and_rebin(h, dt))) return rc;
+  if ((rc = push_and_rebin(h, dt, mk))) return rc;
   if (h->count_lifts && (rc = lift_after(h))) return rc;
   return PIC_OK;
 }
@@ -1096,6 +1108,24 @@ static void lift_bufs_forget(pic_t h) {
   h->lift_pvl = nullptr;
   h->lift_pvj = nullptr;
   h->lift_counts = nullptr;
+}
+
+int pic_step_particles(pic_t h, double dt, int32_t boundary, int32_t flops) {
+  if (check_handle(h)) return PIC_EINVAL;
+  if (boundary != PIC_PERIODIC && boundary != PIC_REFLECT)
+    return fail(h, PIC_EINVAL, "boundary is PIC_PERIODIC or PIC_REFLECT");
+  if (flops < 0 || flops > (1 << 16)) return fail(h, PIC_EINVAL, "flops outside [0, 65536]");
+  if (!std::isfinite(dt)) return fail(h, PIC_EINVAL, "dt is not finite");
+  MoveKind mk;
+  mk.field = false;
+  mk.reflect = boundary == PIC_REFLECT ? 1 : 0;
+  mk.flops = flops;
+  int rc;
+  if ((rc = ensure_leaf(h))) return rc;
+  drop_graphs(h);
+  if ((rc = counted_push_and_rebin(h, dt, mk))) return rc;
+  h->step++;
+  return PIC_OK;
 }
 
 int pic_count_lifts(pic_t h, int32_t enable) {

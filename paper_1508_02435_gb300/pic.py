@@ -14,6 +14,7 @@ import threading
 import numpy as np
 
 PIT, PIDT = 0, 1
+PERIODIC, REFLECT = 0, 1
 PATH_AUTO, PATH_GENERIC = 0, 1
 FP64, FP32_SPLIT = 0, 1
 HOST, DEVICE = 0, 1
@@ -112,6 +113,7 @@ SIGNATURES = [
     ("pic_load", C.c_int, [C.POINTER(C.c_void_p), C.c_char_p, C.c_void_p]),
     ("pic_set_wait_limit", C.c_int, [C.c_void_p, C.c_int64]),
     ("pic_vmax", C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
+    ("pic_step_particles", C.c_int, [C.c_void_p, C.c_double, C.c_int32, C.c_int32]),
     ("pic_wait_selftest", C.c_int, [C.c_int64, C.c_void_p]),
 ]
 
@@ -412,6 +414,12 @@ class Pic:
 
     def step(self, dt: float, hook=None, user=None):
         self._check(self.lib.pic_step(self.h, dt, hook, user))
+
+    def step_particles(self, dt: float, reflect: bool = True, flops: int = 0):
+        """The particle-handling step of the paper's experiments: move by
+        v dt (no field), reflecting or periodic walls, flops per move,
+        re-bin (pic_step_particles)."""
+        self._check(self.lib.pic_step_particles(self.h, dt, 1 if reflect else 0, int(flops)))
 
     def step_fixed_field(self, dt: float):
         self._check(self.lib.pic_step_fixed_field(self.h, dt))

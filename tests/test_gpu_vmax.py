@@ -44,7 +44,7 @@ def test_vmax_matches_oracle(d, flags_fn, scheme, precision):
     g.sync()
     leaf = st.leaf if split else ot.pit_owner(st.x)
     expect = ot.vmax(scheme, leaf, st.key, st.v)
-    got, closed = g.vmax(dt=0.05)
+    got, closed = g.vmax(dt=0.5)   # v_max dt ~ 0.1: open on the finest levels, closed above
     if split:   # the same FP32 velocities: the maxima are the same bits
         assert np.array_equal(got, expect)
     else:       # FP64 velocities agree to 1e-12 (the field's summation order differs)
@@ -58,5 +58,5 @@ def test_vmax_matches_oracle(d, flags_fn, scheme, precision):
         for c in range(1 + nch * k, 1 + nch * (k + 1)):
             level_of[c] = level_of[int(r)] + 1
     lev = np.array([level_of[i] for i in range(len(expect))])
-    assert closed == int(np.sum(expect * 0.05 < 3.0 ** -lev))
+    assert closed == int(np.sum(expect * 0.5 < 3.0 ** -lev))
     assert 0 < closed < len(expect)
