@@ -479,6 +479,87 @@ def run_twostream(args):
     return out
 
 
+def run_particles(args):
+    """The particle-handling benchmark of the paper's experiments (Section 6):
+    no field, velocities of uniform speed 0 <= |v| <= 1 in random directions,
+    reflecting walls, the tree re-refined by the ppc criterion before every
+    step (pic_adapt: refine above ppc, coarsen sibling sets whose union stays
+    within ppc).  2D, 1e7 particles, ppc = 1000, homogeneous and (0, 0.1)^2
+    ("breaking dam") starts, PIT and PIDT, dt in {1e-4, 1e-3, 1e-2}, FP32
+    split.  Throughput = particle updates per second over 50 steps including
+    the re-refinements (set-up excluded); lifts, drops and tunnellers per
+    particle and step from a second, counting run of the first 50 steps; the
+    artificial flops per move (0 ... 4096) on the homogeneous PIT case."""
+    import torch
+    from paper_1508_02435_gb300 import pic
+
+    d, n, ppc, dmin, dmax, steps = 2, 10_000_000, 1000, 1, 8, 50
+    hbm = float(load_peaks()[0]["hbm_gbs"])
+    state_b = 4 + 2 * d * 4          # leaf id + FP32 offsets + FP32 velocities
+    rows = []
+
+    def run(dam, scheme, dt, flops, precision=pic.FP32_SPLIT, count=False):
+        w = W.particle_handling(d, n, dam=dam, seed=7)
+        stream = torch.cuda.Stream()
+        g = pic.Pic(d, w.flags, w.x, w.v, scheme=scheme, precision=precision, q=0.0, qm=0.0, ion=0.0,
+                    sweeps=0, track_ids=count, stream=stream)
+        del w
+        g.adapt(ppc, dmin, dmax)                       # set-up, not timed
+        if count:
+            g.count_lifts(True)
+        else:
+            for _ in range(3):
+                g.adapt(ppc, dmin, dmax)
+                g.step_particles(dt, reflect=True, flops=flops)
+        g.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            g.adapt(ppc, dmin, dmax)
+            g.step_particles(dt, reflect=True, flops=flops)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        info = g.info()
+        if g.stats().error:
+            raise SystemExit("device reported non-finite particle state")
+        res = {"ms_per_step": ms, "value": n / (ms / 1e3), "leaves": int(info.n_leaves),
+               "depth": int(info.depth)}
+        if count:
+            li, dr, tu, st = g.lift_counts()
+            res = {"lifts_per_particle_step": li / (n * st), "drops_per_particle_step": dr / (n * st),
+                   "tunnellers_per_particle_step": tu / (n * st)}
+        g.close()
+        torch.cuda.empty_cache()
+        return res
+
+    for dam in (False, True):
+        for scheme in (pic.PIT, pic.PIDT):
+            for dt in (1e-4, 1e-3, 1e-2):
+                r = run(dam, scheme, dt, 0)
+                r.update(run(dam, scheme, dt, 0, count=True))
+                rows.append({"start": "dam" if dam else "homogeneous",
+                             "scheme": "PIT" if scheme == pic.PIT else "PIDT", "dt": dt, **r})
+    flops_rows = []
+    for fl in (128, 1024, 4096):
+        r = run(False, pic.PIT, 1e-4, fl)
+        flops_rows.append({"flops": fl, **r, "flop_rate_tflops": fl * n / (r["ms_per_step"] / 1e3) / 1e12})
+    fp64 = run(False, pic.PIT, 1e-4, 0, precision=pic.FP64)
+    head = rows[0]
+    return {"metric": "particle-updates/s (particle handling: move + re-bin + re-refinement)",
+            "value": head["value"], "unit": "particle-updates/s", "n_gpus": 1, "steps": steps, "warmup": 3,
+            "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"2D particle handling, {n} particles, ppc {ppc}, depth {dmin}-{dmax}, "
+                                   "reflecting walls, re-refined before every step; headline: homogeneous "
+                                   "start, PIT, dt 1e-4",
+                       "precision": "fp32_split", "d": d, "parallelism": "1 GPU",
+                       "l2": "inputs larger than L2 (state 200 MB per buffer)"},
+            "step_roofline": {"bytes_per_particle": 2 * state_b,
+                              "frac": 2 * state_b * n / (head["ms_per_step"] / 1e3) / 1e9 / hbm},
+            "sweep": rows, "flops": flops_rows, "fp64": fp64}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -734,7 +815,8 @@ def main():
         g.close()
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
-        out["workloads"] = {"twostream3d": run_twostream(args), "batch256": run_batch(args)}
+        out["workloads"] = {"twostream3d": run_twostream(args), "batch256": run_batch(args),
+                            "particle_handling2d": run_particles(args)}
     if world == 1 and not args.no_cpu_baseline:
         rate, info = oracle_rate(d, split, 0, args.oracle_seconds)
         out["cpu_baseline"] = {"value": rate, "unit": "particle-updates/s", **info}
