@@ -350,7 +350,8 @@ PIC_API int pic_phase_times(pic_t h, double *ms, int64_t *kernels);
 
 /* Tables for tests: leaf level[n_leaves] and coords[n_leaves][d]; vertex
  * positions pos[d][n_vertices] in units of 3^-depth; PIDT owner vertices
- * level[n_buckets], j[n_buckets][d] (host memory). */
+ * level[n_buckets], j[n_buckets][d] (host memory; PIDT handles only, else
+ * PIC_ESTATE). */
 PIC_API int pic_leaf_table(pic_t h, int32_t *level, int64_t *coords);
 PIC_API int pic_vertex_table(pic_t h, int64_t *pos);
 PIC_API int pic_pidt_table(pic_t h, int32_t *level, int64_t *j);

@@ -984,6 +984,16 @@ __global__ void k_threshold_bits(const int32_t *count, int64_t ncells, int64_t p
   bits[wd] = b;
 }
 
+// Cell counts of one level from those of the level below: the sum over the
+// 3^d children (child ch of cell c is cell c 3^d + ch).
+__global__ void k_count_parent(const int32_t *fine, int64_t ncoarse, int nch, int32_t *coarse) {
+  int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncoarse) return;
+  int32_t t = 0;
+  for (int ch = 0; ch < nch; ++ch) t += fine[c * nch + ch];
+  coarse[c] = t;
+}
+
 // Split particles of tree `from` re-located in tree `to` (same positions):
 // the resolver of the split push with zero displacement.
 __global__ void k_relocate32(DevTree from, DevTree to, const int32_t *leaf, const float *o, const float *v,
@@ -1091,12 +1101,24 @@ void launch_fine_keys(const DevTree &t, bool split, const void *pos, const int32
     k_fine_key64<<<grid_for(n), kBlock, 0, s>>>(t, (const double *)pos, n, dmax, key);
 }
 
-void launch_level_bits(const uint32_t *key, int64_t n, uint32_t div, int32_t *count, int64_t ncells, int64_t ppc,
-                       uint32_t *bits, cudaStream_t s) {
-  cudaMemsetAsync(count, 0, sizeof(int32_t) * ncells, s);
-  if (n > 0) { COUNT(1); k_level_count<<<grid_for(n), kBlock, 0, s>>>(key, n, div, count); }
-  COUNT(1);
-  k_threshold_bits<<<grid_for((ncells + 31) / 32), kBlock, 0, s>>>(count, ncells, ppc, bits);
+void launch_adapt_bits(const uint32_t *key, int64_t n, int nch, int dmin, int dmax, int64_t ppc, int32_t *count,
+                       const int64_t *cnt_off, uint32_t *bits, const int64_t *bit_off, cudaStream_t s) {
+  if (dmax <= dmin) return;
+  int64_t ncells = 1;
+  for (int m = 0; m < dmax - 1; ++m) ncells *= nch;
+  int32_t *fine = count + cnt_off[dmax - 1];
+  cudaMemsetAsync(fine, 0, sizeof(int32_t) * ncells, s);
+  if (n > 0) { COUNT(1); k_level_count<<<grid_for(n), kBlock, 0, s>>>(key, n, (uint32_t)nch, fine); }
+  for (int m = dmax - 1; m >= dmin; --m) {
+    if (m < dmax - 1) {
+      COUNT(1);
+      k_count_parent<<<grid_for(ncells), kBlock, 0, s>>>(count + cnt_off[m + 1], ncells, nch, count + cnt_off[m]);
+    }
+    COUNT(1);
+    k_threshold_bits<<<grid_for((ncells + 31) / 32), kBlock, 0, s>>>(count + cnt_off[m], ncells, ppc,
+                                                                    bits + bit_off[m]);
+    ncells /= nch;
+  }
 }
 
 void launch_relocate32(const DevTree &from, const DevTree &to, const int32_t *leaf, const float *o, const float *v,

@@ -163,8 +163,11 @@ void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *m
 // level m (index key / div) holding more than ppc particles as a bitmap.
 void launch_fine_keys(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n, int dmax,
                       uint32_t *key, cudaStream_t s);
-void launch_level_bits(const uint32_t *key, int64_t n, uint32_t div, int32_t *count, int64_t ncells, int64_t ppc,
-                       uint32_t *bits, cudaStream_t s);
+// Threshold bits (count > ppc) of every cell on levels dmin .. dmax-1 from
+// the level-dmax cell keys: counts on level dmax-1 summed up child by child;
+// level m's counts at count + cnt_off[m], its bits at bits + bit_off[m].
+void launch_adapt_bits(const uint32_t *key, int64_t n, int nch, int dmin, int dmax, int64_t ppc, int32_t *count,
+                       const int64_t *cnt_off, uint32_t *bits, const int64_t *bit_off, cudaStream_t s);
 void launch_relocate32(const DevTree &from, const DevTree &to, const int32_t *leaf, const float *o, const float *v,
                        int64_t n, int32_t *leaf2, float *o2, float *v2, cudaStream_t s);
 

@@ -41,12 +41,21 @@ struct pic_s {
   void *alloc_user = nullptr;
   int d = 0, scheme = 0, split = 0;
   int64_t n = 0;
-  HostTree ht;                 // instance 0 (the only one unless batched)
   std::vector<HostTree> hts;   // every instance
+  HostTree &ht0() { return hts[0]; }  // instance 0 (the only one unless batched)
   std::vector<InstInfo> inst;
   DevTree dt{};
-  std::vector<DevBuf> tree_bufs, state_bufs;
+  uint64_t tree_gen = 0;  // counts installed trees
+  // state_bufs: sized by the particle count (kept across re-trees);
+  // grid_bufs: sized by the tree (leaves, vertices, keys)
+  std::vector<DevBuf> tree_bufs, state_bufs, grid_bufs;
   int64_t device_bytes = 0;
+  // re-refinement (pic_adapt): cell counts of every decision level and their
+  // threshold bits, kept between calls
+  std::vector<DevBuf> adapt_bufs;
+  int64_t adapt_cells = 0, adapt_words = 0;
+  int32_t *adapt_count = nullptr;
+  uint32_t *adapt_bits = nullptr;
 
   // particle state: [0] current (bucket-sorted), [1] pushed (same index)
   void *pos[2] = {nullptr, nullptr};  // x (double) or o (float), [d][n]
@@ -77,6 +86,8 @@ struct pic_s {
   int32_t *lift_old = nullptr;             // leaf before the step, by particle id
   int32_t *lift_oldkey = nullptr;          // PIDT: key before the step, by particle id
   int32_t *lift_pvl = nullptr, *lift_pvj = nullptr;  // PIDT, adaptive: owner-vertex levels and indices
+  std::vector<DevBuf> lift_tab_bufs;                  // holds lift_pvl / lift_pvj of tree lift_gen
+  uint64_t lift_gen = ~0ull;
   unsigned long long *lift_counts = nullptr;  // [0] lifts, [1] drops, [2] tunnellers
   int64_t lift_steps = 0;
   std::vector<DevBuf> diag_bufs;
@@ -216,7 +227,7 @@ int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const st
     for (int a = 0; a < ht.d; ++a) mv *= ht.M;
     if (mv > INT32_MAX) return fail(h, PIC_EINVAL, "finest level has more than 2^31 grid points");
     ht.build_grid();
-    ht.build_pidt();
+    if (h->scheme == PIC_PIDT) ht.build_pidt();  // PIT handles build it on demand
   }
   const HostTree &h0 = hts[0];
   const int d = h0.d, nc = h0.nc;
@@ -338,8 +349,8 @@ int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const st
   h->d = d;
   h->inst = inst;
   h->hts = std::move(hts);
-  h->ht = h->hts[0];
   h->dt = dt;
+  h->tree_gen++;
   if (old)
     old->swap(prev);
   else
@@ -359,13 +370,28 @@ int set_particle_offsets(pic_t h, const std::vector<int64_t> &poff) {
   return PIC_OK;
 }
 
-// Per-particle and per-grid buffers sized from n and the installed tree.
-int alloc_state(pic_t h) {
+// The solver's warm start, the vertex field and the charge totals start
+// from zero (after a new tree is installed, or an unchanged one confirmed).
+int reset_grid_state(pic_t h) {
+  cudaStream_t s = h->stream;
+  const size_t fs = h->split ? sizeof(float) : sizeof(double);
+  const int64_t nv = h->dt.n_vert;
+  CK(cudaMemsetAsync(h->V, 0, fs * nv, s));
+  CK(cudaMemsetAsync(h->E, 0, fs * nv * h->d, s));
+  CK(cudaMemsetAsync(h->total, 0, sizeof(double) * (2 + h->dt.n_inst), s));
+  CK(cudaMemsetAsync(h->resid2, 0, sizeof(double) * 2, s));
+  h->ecorner_valid = false;
+  h->ebrick_valid = false;
+  h->q_valid = false;
+  return PIC_OK;
+}
+
+// Per-particle buffers, sized from n alone: a re-tree keeps them.
+int alloc_particles(pic_t h) {
   free_bufs(h, h->state_bufs);
   auto &sb = h->state_bufs;
   const int64_t n = h->n, d = h->d;
   const size_t fs = h->split ? sizeof(float) : sizeof(double);
-  const int64_t nk = h->dt.n_keys, nv = h->dt.n_vert, nl = h->dt.n_leaves;
   const int64_t nblk = (n + 127) / 128 + 1;  // blocks of the smallest tuned block size
   int rc;
   for (int s = 0; s < 2; ++s) {
@@ -383,21 +409,37 @@ int alloc_state(pic_t h) {
     }
     if ((rc = dalloc(h, sb, &h->ids[s], n))) return rc;
   }
+  if ((rc = dalloc(h, sb, &h->perm, n))) return rc;
+  if ((rc = dalloc(h, sb, &h->movers, n))) return rc;
+  if ((rc = dalloc(h, sb, &h->block_movers, nblk))) return rc;
+  if ((rc = dalloc(h, sb, &h->block_offsets, nblk + 1))) return rc;
+  if ((rc = dalloc(h, sb, &h->mover_words, (n + 31) / 32 + 64))) return rc;
+  if ((rc = dalloc(h, sb, &h->tile_sums2, scan_tiles_needed(nblk) + 1))) return rc;
+  if ((rc = dalloc(h, sb, &h->scalars, 8))) return rc;
+  if ((rc = dalloc(h, sb, &h->err, 1))) return rc;
+  cudaStream_t s = h->stream;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int32_t), s));
+  CK(cudaMemsetAsync(h->scalars, 0, sizeof(int32_t) * 8, s));
+  return PIC_OK;
+}
+
+// Buffers sized from the installed tree (bucket offsets and counts, leaf
+// partials, vertex fields, the FP64 staging area); the solver's warm start
+// and the field start from zero.
+int alloc_grid(pic_t h) {
+  free_bufs(h, h->grid_bufs);
+  auto &sb = h->grid_bufs;
+  const int64_t n = h->n, d = h->d;
+  const size_t fs = h->split ? sizeof(float) : sizeof(double);
+  const int64_t nk = h->dt.n_keys, nv = h->dt.n_vert, nl = h->dt.n_leaves;
+  int rc;
   // bucket offsets, padded: the brick kernels copy whole 16-byte units of them
   if ((rc = dalloc(h, sb, &h->start_cur, nk + 8))) return rc;
   if ((rc = dalloc(h, sb, &h->start_new, nk + 8))) return rc;
   if ((rc = dalloc(h, sb, &h->count, nk))) return rc;
   if ((rc = dalloc(h, sb, &h->n_stay, nk))) return rc;
   if ((rc = dalloc(h, sb, &h->cursor, nk))) return rc;
-  if ((rc = dalloc(h, sb, &h->perm, n))) return rc;
-  if ((rc = dalloc(h, sb, &h->movers, n))) return rc;
-  if ((rc = dalloc(h, sb, &h->block_movers, nblk))) return rc;
-  if ((rc = dalloc(h, sb, &h->block_offsets, nblk + 1))) return rc;
-  if ((rc = dalloc(h, sb, &h->mover_words, (n + 31) / 32 + 64))) return rc;
   if ((rc = dalloc(h, sb, &h->tile_sums, scan_tiles_needed(nk) + 1))) return rc;
-  if ((rc = dalloc(h, sb, &h->tile_sums2, scan_tiles_needed(nblk) + 1))) return rc;
-  if ((rc = dalloc(h, sb, &h->scalars, 8))) return rc;
-  if ((rc = dalloc(h, sb, &h->err, 1))) return rc;
   char *p;
   if ((rc = dalloc(h, sb, &p, fs * nl * h->dt.nc))) return rc;
   h->part = p;
@@ -419,15 +461,15 @@ int alloc_state(pic_t h) {
   h->Ep = p;
   h->ecorner = nullptr;
   h->ecorner_valid = false;
+  h->ebrick_valid = false;
   if (h->split && !h->dt.uniform && (rc = dalloc(h, sb, &h->ecorner, nl * h->dt.nc))) return rc;
-  cudaStream_t s = h->stream;
-  CK(cudaMemsetAsync(h->V, 0, fs * nv, s));
-  CK(cudaMemsetAsync(h->E, 0, fs * nv * d, s));
-  CK(cudaMemsetAsync(h->err, 0, sizeof(int32_t), s));
-  CK(cudaMemsetAsync(h->scalars, 0, sizeof(int32_t) * 8, s));
-  CK(cudaMemsetAsync(h->total, 0, sizeof(double) * (2 + h->dt.n_inst), s));
-  CK(cudaMemsetAsync(h->resid2, 0, sizeof(double) * 2, s));
-  return PIC_OK;
+  return reset_grid_state(h);
+}
+
+int alloc_state(pic_t h) {
+  int rc;
+  if ((rc = alloc_particles(h))) return rc;
+  return alloc_grid(h);
 }
 
 cudaEvent_t take_event(pic_t h) {
@@ -482,7 +524,7 @@ int setup_brick(pic_t h) {
   free_bufs(h, h->brick_bufs);
   h->brick = false;
   h->brick_ok = false;
-  const auto &t = h->ht;
+  const auto &t = h->ht0();
   if (h->cfg.path != PIC_PATH_AUTO || !t.uniform || h->scheme != PIC_PIT || !h->split || t.depth < 3 ||
       h->dt.n_inst > 1)
     return PIC_OK;
@@ -586,7 +628,7 @@ int brick_push_and_rebin(pic_t h, double dt) {
   }
   pa.Ebrick = h->ebrick;
   pa.qmdt = (float)(h->cfg.qm * dt);
-  pa.sl = (float)(dt * (double)pow3(h->ht.depth));
+  pa.sl = (float)(dt * (double)pow3(h->ht0().depth));
   pa.st = h->stage;
   pa.st.ovf_o = (float *)h->pos[1];  // the current assignment: re-bins elsewhere swap the rows
   pa.st.ovf_v = (float *)h->vel[1];
@@ -928,7 +970,10 @@ void pic_destroy(pic_t h) {
   for (auto e : h->event_pool) cudaEventDestroy(e);
   drop_graphs(h);
   free_bufs(h, h->diag_bufs);
+  free_bufs(h, h->lift_tab_bufs);
+  free_bufs(h, h->adapt_bufs);
   free_bufs(h, h->brick_bufs);
+  free_bufs(h, h->grid_bufs);
   free_bufs(h, h->state_bufs);
   free_bufs(h, h->tree_bufs);
   delete h;
@@ -1026,7 +1071,7 @@ int pic_info(pic_t h, pic_info_t *o) {
   o->d = h->d;
   o->scheme = h->scheme;
   o->precision = h->split ? PIC_FP32_SPLIT : PIC_FP64;
-  o->depth = h->ht.depth;
+  o->depth = h->ht0().depth;
   o->n_particles = h->n;
   o->n_leaves = h->dt.n_leaves;
   o->n_vertices = h->dt.n_vert;
@@ -1051,11 +1096,38 @@ int pic_init_leapfrog(pic_t h, double dt, pic_solve_fn hook, void *user) {
   return PIC_OK;
 }
 
+// PIDT on an adaptive tree: the owner-vertex table (levels; indices per axis
+// as int32) of the installed tree on the device, uploaded again after every
+// re-tree.
+static int lift_tables(pic_t h) {
+  if (h->scheme != PIC_PIDT || h->lift_gen == h->tree_gen) return PIC_OK;
+  free_bufs(h, h->lift_tab_bufs);
+  h->lift_pvl = h->lift_pvj = nullptr;
+  if (!h->dt.uniform) {
+    HostTree &t = h->ht0();
+    t.build_pidt();
+    std::vector<int32_t> pvl(t.pv_level.begin(), t.pv_level.end());
+    std::vector<int32_t> pvj(t.pv_j.size());
+    for (size_t i = 0; i < pvj.size(); ++i) pvj[i] = (int32_t)t.pv_j[i];
+    const int32_t *a = nullptr, *b = nullptr;
+    int rc = upload(h, h->lift_tab_bufs, &a, pvl);
+    if (!rc) rc = upload(h, h->lift_tab_bufs, &b, pvj);
+    if (rc) {
+      free_bufs(h, h->lift_tab_bufs);
+      return rc;
+    }
+    h->lift_pvl = const_cast<int32_t *>(a);
+    h->lift_pvj = const_cast<int32_t *>(b);
+  }
+  h->lift_gen = h->tree_gen;
+  return PIC_OK;
+}
+
 // Lift and drop counting around the push and re-bin of a step: the leaf of
 // every particle by id before, the per-particle counts after.
 static int lift_before(pic_t h) {
   int rc;
-  if ((rc = ensure_leaf(h))) return rc;
+  if ((rc = ensure_leaf(h)) || (rc = lift_tables(h))) return rc;
   launch_scatter_by_id(h->ids[0], h->leaf[0], h->n, h->lift_old, h->stream);
   if (h->scheme == PIC_PIDT) launch_scatter_by_id(h->ids[0], h->key[0], h->n, h->lift_oldkey, h->stream);
   CK(cudaGetLastError());
@@ -1103,6 +1175,8 @@ int pic_step_fixed_field(pic_t h, double dt) {
 }
 
 static void lift_bufs_forget(pic_t h) {
+  free_bufs(h, h->lift_tab_bufs);
+  h->lift_gen = ~0ull;
   h->lift_old = nullptr;
   h->lift_oldkey = nullptr;
   h->lift_pvl = nullptr;
@@ -1145,18 +1219,7 @@ int pic_count_lifts(pic_t h, int32_t enable) {
     rc = dalloc(h, h->diag_bufs, &h->lift_old, h->n);
     if (!rc) rc = dalloc(h, h->diag_bufs, &h->lift_counts, 3);
     if (!rc && h->scheme == PIC_PIDT) rc = dalloc(h, h->diag_bufs, &h->lift_oldkey, h->n);
-    if (!rc && h->scheme == PIC_PIDT && !h->dt.uniform) {
-      // owner-vertex table on the device (levels; indices per axis as int32)
-      const auto &t = h->ht;
-      std::vector<int32_t> pvl(t.pv_level.begin(), t.pv_level.end());
-      std::vector<int32_t> pvj(t.pv_j.size());
-      for (size_t i = 0; i < pvj.size(); ++i) pvj[i] = (int32_t)t.pv_j[i];
-      const int32_t *a = nullptr, *b = nullptr;
-      rc = upload(h, h->diag_bufs, &a, pvl);
-      if (!rc) rc = upload(h, h->diag_bufs, &b, pvj);
-      h->lift_pvl = const_cast<int32_t *>(a);
-      h->lift_pvj = const_cast<int32_t *>(b);
-    }
+    if (!rc) rc = lift_tables(h);
     if (rc) {
       free_bufs(h, h->diag_bufs);
       lift_bufs_forget(h);
@@ -1675,8 +1738,10 @@ int pic_tree_tabulate(int32_t d, const uint8_t *flags, int64_t n_flags, pic_tree
 
 int pic_pidt_table(pic_t h, int32_t *level, int64_t *j) {
   if (check_handle(h)) return PIC_EINVAL;
+  if (h->scheme != PIC_PIDT) return fail(h, PIC_ESTATE, "owner-vertex tables belong to PIDT handles");
   int64_t base = 0;
-  for (const auto &t : h->hts) {
+  for (auto &t : h->hts) {
+    t.build_pidt();
     for (int64_t v = 0; v < t.n_pv; ++v) {
       if (t.uniform) {
         if (level) level[base + v] = t.depth;
@@ -1705,48 +1770,34 @@ int pic_retree(pic_t h, const pic_tree_desc *tree) {
   if ((rc = ensure_leaf(h))) return rc;
   cudaStream_t s = h->stream;
   const int64_t n = h->n;
-  const int d = h->d;
-  const size_t fs = h->split ? sizeof(float) : sizeof(double);
-  // keep the particles (storage order) while the buffers are rebuilt
-  std::vector<DevBuf> keep;
-  char *tpos, *tvel;
-  int32_t *tleaf, *tids;
-  if ((rc = dalloc(h, keep, &tpos, fs * d * n)) || (rc = dalloc(h, keep, &tvel, fs * d * n)) ||
-      (rc = dalloc(h, keep, &tleaf, n)) || (rc = dalloc(h, keep, &tids, n))) {
-    free_bufs(h, keep);
-    return rc;
-  }
-  CK(cudaMemcpyAsync(tpos, h->pos[0], fs * d * n, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(tvel, h->vel[0], fs * d * n, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(tleaf, h->leaf[0], sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(tids, h->ids[0], sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
-  CK(cudaStreamSynchronize(s));
+  // the particles stay in state [0] (storage order) while the tree and the
+  // tree-sized buffers are rebuilt; the particle-sized buffers are kept and
+  // the re-located state lands in [1]
   const DevTree old_dt = h->dt;
   std::vector<DevBuf> old_tree;
-  if ((rc = install_tree(h, tree, &old_tree))) {
-    free_bufs(h, keep);
-    return rc;
-  }
-  if ((rc = alloc_state(h))) {
+  if ((rc = install_tree(h, tree, &old_tree))) return rc;
+  if ((rc = alloc_grid(h))) {
     free_bufs(h, old_tree);
-    free_bufs(h, keep);
     return rc;
   }
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int32_t), s));
+  CK(cudaMemsetAsync(h->scalars, 0, sizeof(int32_t) * 8, s));
   if (h->split) {
-    launch_relocate32(old_dt, h->dt, tleaf, (const float *)tpos, (const float *)tvel, n, h->leaf[1],
-                      (float *)h->pos[1], (float *)h->vel[1], s);
+    launch_relocate32(old_dt, h->dt, h->leaf[0], (const float *)h->pos[0], (const float *)h->vel[0], n,
+                      h->leaf[1], (float *)h->pos[1], (float *)h->vel[1], s);
     launch_rekey32(h->dt, h->leaf[1], (const float *)h->pos[1], n, h->key[1], h->err, s);
   } else {
-    CK(cudaMemcpyAsync(h->pos[1], tpos, fs * d * n, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(h->vel[1], tvel, fs * d * n, cudaMemcpyDeviceToDevice, s));
+    std::swap(h->pos[0], h->pos[1]);  // FP64 positions do not change
+    std::swap(h->vel[0], h->vel[1]);
     launch_init64(h->dt, (double *)h->pos[1], n, h->leaf[1], h->key[1], h->err, s);
   }
-  CK(cudaMemcpyAsync(h->ids[0], tids, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
   CK(cudaGetLastError());
-  if ((rc = bin_fresh(h))) return rc;
-  CK(cudaStreamSynchronize(s));
+  if ((rc = bin_fresh(h))) {
+    free_bufs(h, old_tree);
+    return rc;
+  }
+  CK(cudaStreamSynchronize(s));  // the re-location read the old tables
   free_bufs(h, old_tree);
-  free_bufs(h, keep);
   h->leaf_stale = false;
   h->q_valid = false;
   return setup_brick(h);
@@ -1762,64 +1813,60 @@ int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax) {
   if ((rc = ensure_leaf(h))) return rc;
   cudaStream_t s = h->stream;
   const int64_t n = h->n;
-  uint32_t *key = (uint32_t *)h->perm;  // scratch until the re-bin
-  launch_fine_keys(h->dt, h->split, h->pos[0], h->leaf[0], n, dmax, key, s);
-  // refinement bitmaps of levels dmin .. dmax-1
-  std::vector<std::vector<uint32_t>> bits(dmax + 1);
+  const int nch = (int)pow3(d);
+  // particles per cell on every decision level dmin .. dmax-1: one count on
+  // level dmax-1, summed child by child up to dmin; one bit per cell (count
+  // above ppc), every level's bits in one array read back at once
+  std::vector<int64_t> coff(dmax + 1, 0), boff(dmax + 1, 0);
+  int64_t cells = 0, words = 0;
+  for (int m = dmin; m < dmax; ++m) {
+    coff[m] = cells;
+    boff[m] = words;
+    cells += pow3(d * m);
+    words += (pow3(d * m) + 31) / 32;
+  }
+  std::vector<uint32_t> bits(std::max<int64_t>(words, 1));
   if (dmax > dmin) {
-    const int64_t maxcells = pow3(d * (dmax - 1));
-    std::vector<DevBuf> tmp;
-    int32_t *count;
-    uint32_t *dbits;
-    if ((rc = dalloc(h, tmp, &count, maxcells)) || (rc = dalloc(h, tmp, &dbits, (maxcells + 31) / 32))) {
-      free_bufs(h, tmp);
-      return rc;
+    if (cells > h->adapt_cells || words > h->adapt_words) {
+      free_bufs(h, h->adapt_bufs);
+      h->adapt_cells = h->adapt_words = 0;
+      if ((rc = dalloc(h, h->adapt_bufs, &h->adapt_count, cells)) ||
+          (rc = dalloc(h, h->adapt_bufs, &h->adapt_bits, words)))
+        return rc;
+      h->adapt_cells = cells;
+      h->adapt_words = words;
     }
-    for (int m = dmin; m < dmax; ++m) {
-      const int64_t ncells = pow3(d * m);
-      const uint32_t div = (uint32_t)pow3(d * (dmax - m));
-      launch_level_bits(key, n, div, count, ncells, ppc, dbits, s);
-      bits[m].resize((ncells + 31) / 32);
-      cudaError_t e = cudaMemcpyAsync(bits[m].data(), dbits, sizeof(uint32_t) * bits[m].size(),
-                                      cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) {
-        free_bufs(h, tmp);
-        return cuda_fail(h, e, "adapt counts");
-      }
-    }
-    free_bufs(h, tmp);
+    uint32_t *key = (uint32_t *)h->perm;  // scratch until the next re-bin
+    launch_fine_keys(h->dt, h->split, h->pos[0], h->leaf[0], n, dmax, key, s);
+    launch_adapt_bits(key, n, nch, dmin, dmax, ppc, h->adapt_count, coff.data(), h->adapt_bits, boff.data(), s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(bits.data(), h->adapt_bits, sizeof(uint32_t) * words, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
   }
   // level-order flags: refined iff level < dmin, or level < dmax and the
-  // cell holds more than ppc particles
-  const int nch = (int)pow3(d);
+  // cell holds more than ppc particles.  A cell is named by its index on its
+  // level, base-3^d digits from the root (child ch of cell L: L 3^d + ch).
   std::vector<uint8_t> flags;
-  std::vector<int32_t> cur = {0, 0, 0}, nxt;
+  flags.reserve(h->ht0().n_nodes + 64);
+  std::vector<int64_t> cur(1, 0), nxt;
   for (int m = 0; m <= dmax && !cur.empty(); ++m) {
     nxt.clear();
-    for (size_t i = 0; i < cur.size(); i += 3) {
+    const uint32_t *bm = bits.data() + boff[m];
+    for (int64_t L : cur) {
       bool refine = m < dmin;
-      if (!refine && m < dmax) {
-        int64_t local = 0, mul = 1;
-        int32_t c[3] = {cur[i], cur[i + 1], cur[i + 2]};
-        for (int k = 0; k < m; ++k) {
-          int dg = c[0] % 3 + 3 * (c[1] % 3) + (d == 3 ? 9 * (c[2] % 3) : 0);
-          c[0] /= 3; c[1] /= 3; c[2] /= 3;
-          local += dg * mul;
-          mul *= nch;
-        }
-        refine = (bits[m][local >> 5] >> (local & 31)) & 1u;
-      }
+      if (!refine && m < dmax) refine = (bm[L >> 5] >> (L & 31)) & 1u;
       flags.push_back(refine ? 1 : 0);
       if (refine)
-        for (int ch = 0; ch < nch; ++ch) {
-          nxt.push_back(3 * cur[i] + ch % 3);
-          nxt.push_back(3 * cur[i + 1] + (ch / 3) % 3);
-          nxt.push_back(d == 3 ? 3 * cur[i + 2] + ch / 9 : 0);
-        }
+        for (int ch = 0; ch < nch; ++ch) nxt.push_back(L * nch + ch);
     }
     cur.swap(nxt);
   }
+  // the same tree: every particle keeps its bucket, and its storage order is
+  // already the stable order by key that a re-tree produces
+  const HostTree &t = h->ht0();
+  bool same = (int64_t)flags.size() == t.n_nodes;
+  for (int64_t i = 0; same && i < t.n_nodes; ++i) same = (t.child0[i] >= 0) == (flags[i] != 0);
+  if (same) return reset_grid_state(h);
   pic_tree_desc td{d, (int64_t)flags.size(), flags.data()};
   return pic_retree(h, &td);
 }
@@ -1829,7 +1876,7 @@ int pic_vmax(pic_t h, double *node_vmax, double dt, int64_t *n_closed) {
   if (h->dt.n_inst > 1) return fail(h, PIC_ESTATE, "v_max is kept for single-instance handles");
   int rc;
   if ((rc = ensure_leaf(h))) return rc;
-  const auto &t = h->ht;
+  const auto &t = h->ht0();
   std::vector<int64_t> lb(t.depth + 2, t.n_nodes);
   for (int64_t i = t.n_nodes - 1; i >= 0; --i) lb[t.level[i]] = i;  // level order: first node of each level
   for (int l = t.depth; l >= 0; --l) lb[l] = std::min(lb[l], lb[l + 1]);

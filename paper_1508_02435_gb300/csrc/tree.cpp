@@ -2,8 +2,11 @@
 #include "tree.hpp"
 
 #include <algorithm>
+#include <condition_variable>
 #include <cstdlib>
+#include <functional>
 #include <memory>
+#include <mutex>
 #include <thread>
 
 namespace pic {
@@ -13,6 +16,7 @@ int HostTree::build(int d_, int64_t n_flags, const uint8_t *flags, std::string *
   if (n_flags < 1 || !flags) { *err = "empty tree"; return -1; }
   if (n_flags > INT32_MAX - 64) { *err = "tree too large"; return -1; }
   d = d_;
+  pidt_built = false;
   nch = (int)pow3(d);
   nc = 1 << d;
   n_nodes = n_flags;
@@ -123,17 +127,6 @@ double kref(int d, int e, int f) {
   return k3[diff];
 }
 
-// Runs fn(t, lo, hi) on nt threads over [0, n) split into equal chunks.
-template <typename F>
-void parallel_chunks(int64_t n, unsigned nt, F fn) {
-  std::vector<std::thread> th;
-  for (unsigned t = 0; t < nt; ++t) {
-    const int64_t lo = n * t / nt, hi = n * (t + 1) / nt;
-    th.emplace_back([=, &fn] { fn(t, lo, hi); });
-  }
-  for (auto &x : th) x.join();
-}
-
 // Host threads for the tabulation: PIC_HOST_THREADS if set (1..64), else the
 // hardware concurrency (at most 32).  The tables do not depend on it.
 unsigned host_threads() {
@@ -145,14 +138,82 @@ unsigned host_threads() {
   return std::max(1u, std::min(hw == 0 ? 1u : hw, 32u));
 }
 
-// Stable LSD radix sort of records by the 64-bit value key(rec), 16 bits a
+// Worker threads started once per process; one job at a time (jobs from
+// several handles queue on job_mu_).  The calling thread takes tasks as
+// well, so a job completes with any number of workers, none included.
+class Pool {
+ public:
+  explicit Pool(unsigned workers) {
+    for (unsigned i = 0; i < workers; ++i) std::thread([this] { loop(); }).detach();
+  }
+  void run(unsigned tasks, const std::function<void(unsigned)> &fn) {
+    std::lock_guard<std::mutex> job(job_mu_);
+    std::unique_lock<std::mutex> lk(mu_);
+    fn_ = &fn;
+    tasks_ = tasks;
+    next_ = done_ = 0;
+    ++gen_;
+    cv_.notify_all();
+    work(lk);
+    done_cv_.wait(lk, [&] { return done_ == tasks_; });
+    fn_ = nullptr;
+  }
+
+ private:
+  void work(std::unique_lock<std::mutex> &lk) {
+    while (next_ < tasks_) {
+      const unsigned t = next_++;
+      const std::function<void(unsigned)> *fn = fn_;
+      lk.unlock();
+      (*fn)(t);
+      lk.lock();
+      if (++done_ == tasks_) done_cv_.notify_all();
+    }
+  }
+  void loop() {
+    std::unique_lock<std::mutex> lk(mu_);
+    uint64_t seen = 0;
+    for (;;) {
+      cv_.wait(lk, [&] { return gen_ != seen; });
+      seen = gen_;
+      work(lk);
+    }
+  }
+  std::mutex job_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(unsigned)> *fn_ = nullptr;
+  unsigned tasks_ = 0, next_ = 0, done_ = 0;
+  uint64_t gen_ = 0;
+};
+
+Pool &pool() {
+  static Pool *p = new Pool(host_threads() - 1);  // lives as long as the process
+  return *p;
+}
+
+// Runs fn(t, lo, hi) for t < nt over [0, n) split into nt equal chunks.
+template <typename F>
+void parallel_chunks(int64_t n, unsigned nt, F fn) {
+  if (nt <= 1) {
+    fn(0u, (int64_t)0, n);
+    return;
+  }
+  pool().run(nt, [&](unsigned t) { fn(t, n * t / nt, n * (t + 1) / nt); });
+}
+
+// Chunks for a loop of n items: one per 16 Ki items, at most one per thread.
+unsigned chunks_for(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(host_threads(), n >> 14));
+}
+
+// Stable LSD radix sort of records by the 64-bit value key(rec), 11 bits a
 // pass, passes on host threads over contiguous chunks (counts per chunk, then
 // bucket-major offsets, so equal keys keep their order).
 template <typename Rec, typename Key>
 void radix_sort(std::unique_ptr<Rec[]> &r, int64_t n, uint64_t key_max, Key key) {
-  constexpr int kBits = 16;
+  constexpr int kBits = 11;
   constexpr size_t kBuckets = size_t(1) << kBits;
-  const unsigned nt = host_threads();
+  const unsigned nt = chunks_for(n);
   std::unique_ptr<Rec[]> tmp(new Rec[n > 0 ? n : 1]);
   std::vector<int64_t> cnt((size_t)nt * kBuckets);
   for (int shift = 0; shift < 64 && (shift == 0 || (key_max >> shift) != 0); shift += kBits) {
@@ -195,7 +256,7 @@ void HostTree::build_grid() {
     for (int a = 0; a < d; ++a) { k += p[a] * m; m *= M; }
     return k;
   };
-  const unsigned nt = host_threads();
+  const unsigned nt = chunks_for(n_leaves * nc);
   const int64_t nlc = n_leaves * nc;
   // grid points: the distinct leaf corners, by row-major key on the finest
   // level (sorted keys; a corner's point is its key's rank)
@@ -481,6 +542,8 @@ void HostTree::build_grid() {
 
 
 void HostTree::build_pidt() {
+  if (pidt_built) return;
+  pidt_built = true;
   if (uniform) {
     n_pv = 1;
     for (int a = 0; a < d; ++a) n_pv *= M;
@@ -498,7 +561,7 @@ void HostTree::build_pidt() {
   };
   const int64_t nlc = n_leaves * nc;
   std::unique_ptr<Rec[]> r(new Rec[nlc > 0 ? nlc : 1]);
-  const unsigned nt = host_threads();
+  const unsigned nt = chunks_for(nlc);
   std::vector<uint64_t> rm_max_t(nt, 0);
   parallel_chunks(n_leaves, nt, [&](unsigned t, int64_t lo, int64_t hi) {
     uint64_t mx = 0;

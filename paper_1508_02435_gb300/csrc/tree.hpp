@@ -80,6 +80,7 @@ struct HostTree {
 
   // PIDT owner vertices (adaptive only; uniform trees use the FE vertices)
   int64_t n_pv = 0;
+  bool pidt_built = false;  // build_pidt ran (PIT handles run it on demand)
   table<int32_t> corner_pv, pv_level;
   table<int64_t> pv_j;  // d per vertex
 

@@ -150,3 +150,48 @@ def test_brick_handle_alternates_field_and_particle_steps():
             st.step(0.05)
             g.step(0.05)
         compare(g, st, True)
+
+
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_SPLIT])
+def test_pidt_lift_counts_across_refinements(precision):
+    """PIDT lifts, drops and tunnellers of particle steps with the tree
+    re-refined by ppc before every step: each step counts on the tree it ran
+    on (the owner-vertex tables follow every new tree)."""
+    d, ppc, dmin, dmax = 2, 40, 1, 6
+    w = W.particle_handling(d, 20_000, dam=True, seed=46)
+    split = precision == pic.FP32_SPLIT
+    prm = oracle.Params(scheme=pic.PIDT, q=0.0, qm=0.0, ion=0.0, sweeps=0)
+    st = (oracle.State32 if split else oracle.State64)(oracle.Tree(d, w.flags), w.x, w.v, prm)
+    g = pic.Pic(d, w.flags, w.x, w.v, scheme=pic.PIDT, precision=precision, q=0.0, qm=0.0, ion=0.0, sweeps=0)
+    g.count_lifts(True)
+
+    def by_id(a):
+        out = np.empty(len(a), np.int64)
+        out[st.ids] = a
+        return out
+
+    lifts = drops = tun = 0
+    sizes = set()
+    for _ in range(4):
+        g.adapt(ppc, dmin, dmax)
+        flags = (oracle.retree32(st.tree, st.leaf, st.o, ppc, dmin, dmax) if split
+                 else oracle.retree64(d, st.x, ppc, dmin, dmax))
+        nt = oracle.Tree(d, flags)
+        sizes.add(nt.n_leaves)
+        if split:
+            st.tree.rebin32_into(nt, st.leaf, st.o)
+        st.tree = nt
+        del st.key
+        st.rebin()
+        leaf0 = by_id(st.leaf if split else nt.pit_owner(st.x))
+        key0 = by_id(st.key)
+        st.move(0.08, 1)
+        leaf1 = by_id(st.leaf if split else nt.pit_owner(st.x))
+        li, dr = nt.pidt_lifts(leaf0, key0, by_id(st.key))
+        lifts += int(li.sum())
+        drops += int(dr.sum())
+        tun += int(nt.tunnellers(leaf0, leaf1).sum())
+        g.step_particles(0.08, reflect=True)
+        compare(g, st, split)
+    assert len(sizes) > 1 and lifts > 0
+    assert g.lift_counts() == (lifts, drops, tun, 4)
