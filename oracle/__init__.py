@@ -12,7 +12,8 @@ push, then re-bin every particle into the leaf (PIT, Algorithm 1) or dual cell
 (PIDT, Algorithms 2-3) that covers it.
 
 Parity pins (tests/test_oracle_*.py) check this oracle against brute force,
-literal executions of Algorithms 1-3, closed forms and conservation laws.
+the lift and drop rules applied to a fixed point, closed forms and
+conservation laws.
 """
 from __future__ import annotations
 

@@ -1,5 +1,5 @@
 """Pins of the CPU oracle against things other than itself: brute force,
-literal executions of Algorithms 1-3, closed forms of the d-linear finite
+lifts and drops applied as rewrite rules to a fixed point, closed forms of the d-linear finite
 elements, conservation laws and the Vlasov-Poisson dispersion relation.
 
 No GPU is needed.
@@ -16,7 +16,7 @@ import pytest
 
 import oracle
 from paper_1508_02435_gb300 import workloads as W
-from tests import literal_algorithms as LA
+from tests import lift_drop_rules as LA
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 QS = 2 * 3 ** 18
@@ -105,8 +105,8 @@ def test_pit_uniform_is_textbook_binning():
 
 @pytest.mark.parametrize("d,depth,p,seed,vmax", [(2, 4, 0.4, 11, 0.3), (2, 5, 0.3, 12, 0.05),
                                                  (3, 3, 0.35, 13, 0.4)])
-def test_pit_equals_literal_algorithm1(d, depth, p, seed, vmax):
-    """Lifts and drops of Algorithm 1 on a depth-first traversal end in the
+def test_pit_owner_equals_lift_drop_fixed_point(d, depth, p, seed, vmax):
+    """The PIT lift and drop rules, applied until neither fires, end in the
     oracle's owner (Theorem 1), with particles tunnelling several cells."""
     flags = random_tree(d, depth, p, seed)
     t = oracle.Tree(d, flags)
@@ -114,7 +114,7 @@ def test_pit_equals_literal_algorithm1(d, depth, p, seed, vmax):
     x0, v = W.random_particles(d, 300, seed, vmax=vmax)
     x1 = np.mod(x0 + v, 1.0)
     Q0, Q1 = quantise_np(x0).T.tolist(), quantise_np(x1).T.tolist()
-    lit = LA.pit_literal(d, flags, Q0, Q1)
+    lit = LA.pit_by_rules(d, flags, Q0, Q1)
     leaf = t.pit_owner(x1)
     for pi in range(x1.shape[1]):
         assert lit[pi] == (lev[leaf[pi]], tuple(int(c) for c in co[leaf[pi]]))
@@ -122,17 +122,17 @@ def test_pit_equals_literal_algorithm1(d, depth, p, seed, vmax):
 
 @pytest.mark.parametrize("d,depth,p,seed,vmax", [(2, 4, 0.4, 11, 0.3), (2, 5, 0.3, 12, 0.05),
                                                  (3, 3, 0.35, 13, 0.4), (2, 5, 0.5, 14, 0.8)])
-def test_pit_lift_counts_equal_literal_algorithm1(d, depth, p, seed, vmax):
+def test_pit_lift_counts_equal_rule_firings(d, depth, p, seed, vmax):
     """The oracle's lift and drop counts per particle (old leaf up to the
-    deepest common ancestor, down to the new leaf) equal the lift and drop
-    events of Algorithm 1 executed on a depth-first traversal."""
+    deepest common ancestor, down to the new leaf) equal the number of times
+    the lift and drop rules fire for it."""
     flags = random_tree(d, depth, p, seed)
     t = oracle.Tree(d, flags)
     x0, v = W.random_particles(d, 300, seed, vmax=vmax)
     x1 = np.mod(x0 + v, 1.0)
     Q0, Q1 = quantise_np(x0).T.tolist(), quantise_np(x1).T.tolist()
     counts = {}
-    LA.pit_literal(d, flags, Q0, Q1, counts=counts)
+    LA.pit_by_rules(d, flags, Q0, Q1, counts=counts)
     lifts, drops = t.pit_lifts(t.pit_owner(x0), t.pit_owner(x1))
     assert np.array_equal(lifts, counts["lifts"])
     assert np.array_equal(drops, counts["drops"])
@@ -236,15 +236,16 @@ def test_lifts_of_stayers_movers_and_uniform_trees():
 
 @pytest.mark.parametrize("d,depth,p,seed,vmax", [(2, 4, 0.4, 21, 0.2), (2, 5, 0.3, 22, 0.03),
                                                  (3, 3, 0.35, 23, 0.3)])
-def test_pidt_equals_literal_algorithms2_3(d, depth, p, seed, vmax):
-    """Drops, moves, linked-list hand-overs and lifts of Algorithms 2-3 end in
-    the oracle's owner vertex (Theorem 2)."""
+def test_pidt_owner_equals_lift_drop_fixed_point(d, depth, p, seed, vmax):
+    """The PIDT lift (to the dual parent) and drop (to the child-level vertex)
+    rules, applied until neither fires, end in the oracle's owner vertex
+    (Theorem 2)."""
     flags = random_tree(d, depth, p, seed)
     t = oracle.Tree(d, flags)
     x0, v = W.random_particles(d, 250, seed, vmax=vmax)
     x1 = np.mod(x0 + v, 1.0)
     Q0, Q1 = quantise_np(x0).T.tolist(), quantise_np(x1).T.tolist()
-    lit = LA.pidt_literal(d, flags, Q0, Q1)
+    lit = LA.pidt_by_rules(d, flags, Q0, Q1)
     vl, vj = t.pidt_owner(x1)
     for pi in range(x1.shape[1]):
         assert lit[pi] == (int(vl[pi]), tuple(int(j) for j in vj[:, pi]))

@@ -24,7 +24,7 @@ import pytest
 
 import oracle
 from paper_1508_02435_gb300 import workloads as W
-from tests import literal_algorithms as LA
+from tests import lift_drop_rules as LA
 
 U32 = 2.0 ** -24       # unit roundoff of FP32 (round to nearest)
 QS = 2 * 3 ** 18
