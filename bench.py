@@ -43,16 +43,19 @@ STEP_BYTES = {(3, 1): 70.0, (3, 0): 132.0, (2, 1): 48.5, (2, 0): 89.0}
 # kernel sources at capture time; a row whose digest differs from the current
 # sources is stale and reads as unmeasured.
 TRAFFIC_CSV = os.path.join(ROOT, "profiles", "dram_traffic_langmuir3d_243cubed_8ppc.csv")
-KERNEL_SOURCES = ("paper_1508_02435_gb300/csrc/brick.cu", "paper_1508_02435_gb300/csrc/dev.cuh",
-                  "paper_1508_02435_gb300/csrc/segsort.cuh", "paper_1508_02435_gb300/csrc/kernels.cu",
-                  "paper_1508_02435_gb300/csrc/launch.hpp")
+_BRICK_SOURCES = ("paper_1508_02435_gb300/csrc/brick.cu", "paper_1508_02435_gb300/csrc/dev.cuh",
+                  "paper_1508_02435_gb300/csrc/segsort.cuh", "paper_1508_02435_gb300/csrc/launch.hpp")
+# the sources each measured kernel is compiled from
+KERNEL_SOURCES = {"k_brick_push_st": _BRICK_SOURCES, "k_brick_pull_st": _BRICK_SOURCES,
+                  "k_vertex_charge": ("paper_1508_02435_gb300/csrc/kernels.cu", "paper_1508_02435_gb300/csrc/dev.cuh",
+                                      "paper_1508_02435_gb300/csrc/launch.hpp")}
 PHASE_KERNEL = {"push": "k_brick_push_st", "rebin": "k_brick_pull_st", "deposit": "k_vertex_charge"}
 
 
-def kernel_digest() -> str:
+def kernel_digest(kernel: str) -> str:
     import hashlib
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -68,7 +71,7 @@ def measured_traffic(workload: str, kernel: str):
         return None, None
     for r in rows:
         if r["workload"] == workload and r["kernel"] == kernel:
-            if r["sources_digest"] != kernel_digest():
+            if r["sources_digest"] != kernel_digest(kernel):
                 return None, r
             return (float(r["read_bytes"]) + float(r["write_bytes"])) / float(r["launches"]), r
     return None, None
@@ -103,7 +106,7 @@ def ingest_ncu(path: str, workload: str, particles: int) -> str:
            "workload,kernel,launches,read_bytes,write_bytes,duration_ns,particles,sources_digest"]
     for k, d in acc.items():
         out.append(f"{workload},{k},{len(d['ids'])},{d['read']:.0f},{d['write']:.0f},{d['ns']:.0f},{particles},"
-                   f"{kernel_digest()}")
+                   f"{kernel_digest(k)}")
     return "\n".join(out) + "\n"
 
 

@@ -251,6 +251,46 @@ def test_pidt_owner_equals_lift_drop_fixed_point(d, depth, p, seed, vmax):
         assert lit[pi] == (int(vl[pi]), tuple(int(j) for j in vj[:, pi]))
 
 
+@pytest.mark.parametrize("d,depth,p,seed", [(2, 5, 0.35, 24), (3, 3, 0.35, 25)])
+def test_owners_on_faces_equal_fixed_point(d, depth, p, seed):
+    """Positions exactly on cell faces and on dual-cell faces (the centre
+    planes of the leaves): the half-open rules (a face belongs to the upper
+    cell or dual cell) decide both owners, PIT and PIDT, as the lift and drop
+    rules do."""
+    flags = random_tree(d, depth, p, seed)
+    t = oracle.Tree(d, flags)
+    lev, co = t.leaf_info()
+    rng = np.random.default_rng(seed)
+    n = 400
+    L = rng.integers(0, len(lev), n)
+    s = 3 ** (18 - lev[L].astype(np.int64))
+    kind = rng.integers(0, 3, (d, n))          # 0: lower face, 1: centre plane, 2: inside
+    inside = (rng.random((d, n)) * (2 * s)).astype(np.int64)
+    Q = 2 * co[L].T * s + np.where(kind == 0, 0, np.where(kind == 1, s, inside))
+    x = (Q + 0.5) / QS                         # the middle of the quantum whose Q is on the face
+    assert np.array_equal(quantise_np(x), Q)
+    assert (kind == 1).sum() > n // 3 and (kind == 0).sum() > n // 3
+    Ql = Q.T.tolist()
+    pit = LA.pit_by_rules(d, flags, Ql, Ql)
+    pidt = LA.pidt_by_rules(d, flags, Ql, Ql)
+    leaf = t.pit_owner(x)
+    vl, vj = t.pidt_owner(x)
+    # the PIDT sort key: owner vertex id * 2^d + the quadrant 2^d - 1 - corner,
+    # corner = the owner's place among the covering leaf's corners
+    key = t.keys64(oracle.PIDT, x)
+    pv_lev, pv_j = t.pidt_vertices()
+    nc = 1 << d
+    for pi in range(n):
+        assert pit[pi] == (lev[leaf[pi]], tuple(int(c) for c in co[leaf[pi]]))
+        assert pidt[pi] == (int(vl[pi]), tuple(int(j) for j in vj[:, pi]))
+        lv, j = pidt[pi]
+        vid = key[pi] // nc
+        assert (int(pv_lev[vid]), tuple(int(c) for c in pv_j[vid])) == (lv, j)
+        per = 3 ** lv
+        corner = sum(1 << a for a in range(d) if j[a] != co[leaf[pi], a] % per)
+        assert key[pi] % nc == nc - 1 - corner
+
+
 def test_pidt_owner_brute_force():
     """Owner = vertex on the covering leaf's level whose dual cell contains the
     particle; scan over all leaf corners."""
