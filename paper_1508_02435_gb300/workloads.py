@@ -278,6 +278,21 @@ def particle_handling(d: int, n: int, dam: bool = False, seed: int = 0, base_dep
                     steps=10, extra={"dam": dam, "base_depth": base_depth})
 
 
+def thermal_plasma(d: int = 2, depth: int = 5, ppc: int = 100, dt: float = 0.01, seed: int = 0) -> Workload:
+    """The validation plasma of Appendix A: a uniform grid of 3^depth cells per
+    axis whose cell is one Debye length, ppc particles per cell at uniformly
+    random positions, Maxwellian velocities of thermal speed v_th = lambda_D
+    omega_p per component (one cell width per plasma time), q/m = -1 and a
+    neutralising ion background; omega_p dt = 0.01.  The random start seeds a
+    sea of Langmuir waves at every wave vector."""
+    rng = np.random.default_rng(seed)
+    n = ppc * 3 ** (depth * d)
+    x = rng.random((d, n))
+    v = rng.standard_normal((d, n)) * (1.0 / 3 ** depth)
+    return Workload(name="thermal_plasma", d=d, flags=uniform_tree_flags(d, depth), x=x, v=v, q=-1.0 / n,
+                    qm=-1.0, ion=1.0, dt=dt, steps=0, extra={"vth": 1.0 / 3 ** depth, "ppc": ppc})
+
+
 def random_particles(d: int, n: int, seed: int, vmax: float = 1.0) -> tuple[np.ndarray, np.ndarray]:
     """Uniform positions in [0,1)^d and velocities uniform in [-vmax, vmax]^d."""
     rng = np.random.default_rng(seed)
