@@ -146,7 +146,8 @@ typedef struct {
  * user on that stream at once.  The setting is process-wide and
  * taken by handles created afterwards, which keep it for all their later
  * allocations and frees; both NULL restores cudaMalloc / cudaFree.  Only one
- * of the two NULL: PIC_EINVAL.  Host only; no device call. */
+ * of the two NULL: PIC_EINVAL.  Host only; no device call.  The paper has no
+ * counterpart: a library utility. */
 typedef void *(*pic_alloc_fn)(void *user, size_t bytes, void *stream);
 typedef void (*pic_free_fn)(void *user, void *ptr, size_t bytes, void *stream);
 PIC_API int pic_set_allocator(pic_alloc_fn alloc, pic_free_fn free_fn, void *user);
@@ -168,24 +169,29 @@ PIC_API int pic_create(pic_t *out, const pic_tree_desc *tree, const pic_particle
  * grid and particle containers have no counterpart to release: a library
  * utility. */
 PIC_API void pic_destroy(pic_t h);
+/* Error text of a return code, and the message of the handle's last failure
+ * (NULL handle: of the last failed creation on this thread); sizes and mode
+ * of a handle.  Library utilities without a counterpart in the paper. */
 PIC_API const char *pic_strerror(int code);
 PIC_API const char *pic_last_error(pic_t h);
 PIC_API int pic_info(pic_t h, pic_info_t *out);
 
 /* Batch of n_inst independent plasmas of uneven size with uniform trees of
  * any depth (same d): trees[i], parts[i], charge per particle q[i] (NULL:
- * cfg->q for all).  Leaves, vertices, buckets and particles are concatenated
+ * cfg->q for all).  No counterpart in the paper (each instance is the problem
+ * of pic_create; the batch fills one GPU with many small ones).  Leaves, vertices, buckets and particles are concatenated
  * instance by instance; every phase of a step is one launch over the whole
  * batch.  Particle ids run over the batch in input order. */
 PIC_API int pic_create_batch(pic_t *out, int32_t n_inst, const pic_tree_desc *trees,
                              const pic_particles_desc *parts, const double *q, const pic_config *cfg);
 
-/* Per-instance offsets into the concatenated particle storage, vertex arrays
- * and bucket list; each array has n_instances + 1 entries (host memory, any
+/* Per-instance offsets (no counterpart in the paper) into the concatenated
+ * particle storage, vertex arrays and bucket list; each array has n_instances + 1 entries (host memory, any
  * may be NULL).  Particle ranges are fixed: no particle leaves its instance. */
 PIC_API int pic_instances(pic_t h, int64_t *particle_start, int64_t *vertex_start, int64_t *bucket_start);
 
-/* Leapfrog start: v_{-1/2} = v_0 - (q/m) E(x_0) dt/2 (deposit, solve, gather). */
+/* Leapfrog start: v_{-1/2} = v_0 - (q/m) E(x_0) dt/2 (deposit, solve, gather):
+ * the time integration of Section 3 item 4 read as leapfrog. */
 PIC_API int pic_init_leapfrog(pic_t h, double dt, pic_solve_fn hook, void *user);
 
 /* One PIC step (Section 3 items 1-4) plus the PIT/PIDT re-bin (Section 5),
@@ -193,7 +199,8 @@ PIC_API int pic_init_leapfrog(pic_t h, double dt, pic_solve_fn hook, void *user)
 PIC_API int pic_step(pic_t h, double dt, pic_solve_fn hook, void *user);
 
 /* Only the timed hot path of a step, with the field E held fixed from the last
- * solve: deposit of the current positions, gather + push + key, re-bin. */
+ * solve: deposit of the current positions (Section 3 item 1), gather + push
+ * (items 3-4), key and re-bin (Section 5). */
 PIC_API int pic_step_fixed_field(pic_t h, double dt);
 
 /* The particle-handling step of the paper's experiments (Section 6): no
@@ -212,8 +219,9 @@ PIC_API int pic_step_fixed_field(pic_t h, double dt);
 #define PIC_REFLECT 1
 PIC_API int pic_step_particles(pic_t h, double dt, int32_t boundary, int32_t flops);
 
-/* Capture the fixed-field step (deposit when due, gather + push + key,
- * re-bin) as CUDA graphs after one ordinary step; the handle's stream must
+/* No counterpart in the paper (launch machinery of this library).  Capture
+ * the fixed-field step (deposit when due, gather + push + key, re-bin) as
+ * CUDA graphs after one ordinary step; the handle's stream must
  * not be the legacy default stream.  Two graphs are kept because a step
  * swaps ping-pong buffers.  Any call that rebuilds buffers (re-tree, tuning)
  * drops them. */
@@ -227,7 +235,8 @@ PIC_API int pic_graph_capture_step(pic_t h, double dt);
 /* Replay `steps` captured steps on the handle's stream (asynchronous). */
 PIC_API int pic_graph_launch(pic_t h, int32_t steps);
 
-/* Tuning = {path (1 brick, 0 generic), threads per block of the push, of
+/* Launch tuning (no counterpart in the paper).  Tuning = {path (1 brick, 0
+ * generic), threads per block of the push, of
  * the per-leaf deposit, of the per-vertex kernels}.  pic_autotune times
  * every candidate for `trials` fixed-field steps on the handle's own
  * particles, keeps the fastest and restores the particle state; the chosen
@@ -238,7 +247,8 @@ PIC_API int pic_set_tuning(pic_t h, const int32_t *tuned);
 PIC_API int pic_get_tuning(pic_t h, int32_t *tuned);
 
 /* Wait for the handle's stream; returns the sticky device error if any
- * (PIC_ERANGE, PIC_ETIMEOUT when a bounded device wait gave up). */
+ * (PIC_ERANGE, PIC_ETIMEOUT when a bounded device wait gave up).  A library
+ * utility without a counterpart in the paper. */
 PIC_API int pic_sync(pic_t h);
 
 /* Failure detection of device waits (no counterpart in the paper; a library
@@ -279,8 +289,9 @@ PIC_API int pic_potential(pic_t h, double *V_out, int32_t where);
  * device per `where`. */
 PIC_API int pic_bins(pic_t h, int64_t *bucket_start, int32_t *perm, int32_t where);
 
-/* Sort keys per particle in storage order (leaf id, or owner vertex * 2^d +
- * quadrant for PIDT). */
+/* Sort keys per particle in storage order: the PIT leaf (Section 5.1) or the
+ * PIDT owner vertex (Section 5.2) as leaf id, or owner vertex * 2^d +
+ * quadrant.  Caller-owned, host or device per `where`. */
 PIC_API int pic_keys(pic_t h, int32_t *keys, int32_t where);
 
 /* Particles in storage order: absolute FP64 positions x[d][n] in [0, 1)^d
@@ -290,7 +301,8 @@ PIC_API int pic_keys(pic_t h, int32_t *keys, int32_t where);
  * `where`; either pointer may be NULL. */
 PIC_API int pic_get_particles(pic_t h, double *x, double *v, int32_t where);
 
-/* Native state in storage order, for checkpoints and host round trips.
+/* Native state in storage order (the particle state of Section 3 in the
+ * handle's precision), for checkpoints and host round trips.
  * FP64: x[d][n], v[d][n] (double).  Split: leaf[n] (int32), o[d][n], v[d][n]
  * (float).  Unused pointers may be NULL.  pic_set_state replaces the particles
  * (same n) and re-bins them. */
@@ -338,7 +350,8 @@ PIC_API int pic_lift_counts(pic_t h, int64_t *lifts, int64_t *drops, int64_t *tu
 #define PIC_PHASE_PERMUTE 4  /* permutation of the particle arrays into bucket order */
 #define PIC_NPHASES 5
 
-/* Per-phase device timing with CUDA events recorded on the handle's stream
+/* Diagnostics without a counterpart in the paper.  Per-phase device timing
+ * with CUDA events recorded on the handle's stream
  * around every phase of every later call.  enable = 0 stops recording;
  * enable = 1 (re)starts it from zero. */
 PIC_API int pic_profile(pic_t h, int32_t enable);
@@ -348,7 +361,9 @@ PIC_API int pic_profile(pic_t h, int32_t enable);
  * last pic_profile(h, 1).  Both arrays have PIC_NPHASES entries. */
 PIC_API int pic_phase_times(pic_t h, double *ms, int64_t *kernels);
 
-/* Tables for tests: leaf level[n_leaves] and coords[n_leaves][d]; vertex
+/* Tables of the spacetree (Section 4), its finite-element grid (Section 3)
+ * and dual tree (Section 4.1), for tests: leaf level[n_leaves] and
+ * coords[n_leaves][d]; vertex
  * positions pos[d][n_vertices] in units of 3^-depth; PIDT owner vertices
  * level[n_buckets], j[n_buckets][d] (host memory; PIDT handles only, else
  * PIC_ESTATE). */
@@ -378,8 +393,9 @@ PIC_API int pic_retree(pic_t h, const pic_tree_desc *tree);
  * (PIC_ESTATE otherwise). */
 PIC_API int pic_vmax(pic_t h, double *node_vmax, double dt, int64_t *n_closed);
 
-/* Level-order refinement flags of the current tree: with flags == NULL only
- * *n_nodes is written; else flags[n_nodes] (host memory). */
+/* Level-order refinement flags of the current spacetree (Section 4; the
+ * encoding of pic_tree_desc): with flags == NULL only *n_nodes is written;
+ * else flags[n_nodes] (host memory). */
 PIC_API int pic_tree_flags(pic_t h, uint8_t *flags, int64_t *n_nodes);
 
 /* ---- checkpoint / resume ----------------------------------------------------
@@ -422,7 +438,10 @@ PIC_API int pic_load(pic_t *out, const char *path, void *stream);
  * iff m < dmin, or m < dmax and C holds more than ppc particles (Section 6
  * setup: refine on overrun, coarsen when the union stays within ppc).  Counts
  * per level are taken on the device; dmax <= 6 in 3D, <= 10 in 2D.  Split
- * positions below their leaf are resolved with the drop rule.  Synchronous. */
+ * positions below their leaf are resolved with the drop rule.  A resulting
+ * tree equal to the current one keeps every bucket (only the solver's warm
+ * start and the field are reset, as by pic_retree); any other is installed by
+ * pic_retree.  Synchronous. */
 PIC_API int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax);
 
 /* ---- no-allocation entry point -------------------------------------------
