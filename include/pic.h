@@ -370,6 +370,15 @@ PIC_API int pic_phase_times(pic_t h, double *ms, int64_t *kernels);
 PIC_API int pic_leaf_table(pic_t h, int32_t *level, int64_t *coords);
 PIC_API int pic_vertex_table(pic_t h, int64_t *pos);
 PIC_API int pic_pidt_table(pic_t h, int32_t *level, int64_t *j);
+/* The finite-element tables of a single-instance handle with an adaptive tree
+ * (Section 3 grid on the Section 4 tree; PIC_ESTATE otherwise), as the
+ * kernels read them, for tests: every leaf corner expanded onto vertices,
+ * cexp_ptr[n_leaves 2^d + 1], cexp_vid[*n_entries], cexp_w[*n_entries], and
+ * per vertex ion_load[n_vertices] and diag[n_vertices] (host memory; any
+ * pointer may be NULL; pass NULL arrays first to learn *n_entries).  The
+ * layout is that of pic_tree_tabulate. */
+PIC_API int pic_grid_tables(pic_t h, int64_t *n_entries, int32_t *cexp_ptr, int32_t *cexp_vid, double *cexp_w,
+                            double *ion_load, double *diag);
 
 /* Replace the tree (same d) and re-bin the particles into it: the dynamic
  * adaptivity of Section 5's introduction (the grid changes between steps and

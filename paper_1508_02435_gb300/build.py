@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpic.so")
-SOURCES = ["kernels.cu", "brick.cu", "pic_api.cu", "noalloc.cu", "calibrate.cu", "tree.cpp", "snapshot.cpp"]
+SOURCES = ["kernels.cu", "brick.cu", "pic_api.cu", "noalloc.cu", "calibrate.cu", "tree_dev.cu", "tree.cpp", "snapshot.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,8 +36,10 @@ def _stale() -> bool:
 
 def _compile(src: str, extra: list[str]) -> str:
     out = os.path.join(BUILD, os.path.basename(src) + ".o")
+    # host and device arithmetic both in program order, one rounding per operation
     cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
-           "-Xcompiler", "-fvisibility=hidden", *extra, "-c", os.path.join(CSRC, src), "-o", out]
+           "-Xcompiler", "-fvisibility=hidden", "-Xcompiler", "-ffp-contract=off", *extra, "-c",
+           os.path.join(CSRC, src), "-o", out]
     if src.endswith(".cpp"):
         cmd.insert(1, "-x")
         cmd.insert(2, "cu")

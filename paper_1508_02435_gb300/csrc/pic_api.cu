@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -18,6 +19,7 @@
 #include "launch.hpp"
 #include "snapshot.hpp"
 #include "tree.hpp"
+#include "tree_dev.hpp"
 
 using namespace pic;
 
@@ -53,6 +55,11 @@ struct pic_s {
   // re-refinement (pic_adapt): cell counts of every decision level and their
   // threshold bits, kept between calls
   std::vector<DevBuf> adapt_bufs;
+  // device tabulation of adaptive trees: its tables (when grid_dev) and its
+  // scratch, kept for the next re-tree while it is small
+  DeviceGrid gdev{};
+  bool grid_dev = false;
+  std::vector<DevBuf> tab_scratch;
   int64_t adapt_cells = 0, adapt_words = 0;
   int32_t *adapt_count = nullptr;
   uint32_t *adapt_bits = nullptr;
@@ -209,6 +216,59 @@ int upload(pic_t h, std::vector<DevBuf> &bufs, const T **out, const std::vector<
 // (leaves, vertices and keys concatenated instance by instance).  The previous
 // device buffers are handed back in *old (freed by the caller) so particles
 // can still be re-located from them.
+// Host tabulation instead of the device one (PIC_HOST_TABLES=1), for
+// comparing the two; the tables, and so every result, are the same.
+bool host_tables_forced() {
+  const char *e = std::getenv("PIC_HOST_TABLES");
+  return e && e[0] == '1';
+}
+
+// Device memory of the device tabulation: its tables go to the tree's
+// buffers; its scratch buffers are slots of h->tab_scratch, reused by the
+// next re-tree when large enough (the same sequence of requests).
+struct TabCtx {
+  pic_t h;
+  std::vector<DevBuf> *keep;
+  size_t next;
+};
+
+int tab_alloc(void *c, void **out, size_t bytes, bool keep) {
+  TabCtx *ctx = (TabCtx *)c;
+  pic_t h = ctx->h;
+  char *p = nullptr;
+  if (keep) {
+    if (dalloc(h, *ctx->keep, &p, bytes)) return kTabNoMemory;
+    *out = p;
+    return 0;
+  }
+  auto &sc = h->tab_scratch;
+  const size_t k = ctx->next++;
+  if (k < sc.size() && sc[k].bytes >= bytes) {
+    *out = sc[k].p;
+    return 0;
+  }
+  std::vector<DevBuf> fresh;
+  if (dalloc(h, fresh, &p, bytes + bytes / 4)) return kTabNoMemory;
+  if (k < sc.size()) {
+    std::vector<DevBuf> one(1, sc[k]);
+    free_bufs(h, one);
+    sc[k] = fresh[0];
+  } else {
+    sc.push_back(fresh[0]);
+  }
+  *out = p;
+  return 0;
+}
+
+void tab_release(void *, void *) {}  // slots stay for the next re-tree (trim_tab_scratch)
+
+// Scratch is kept only while it is small (frequent re-trees of small trees).
+void trim_tab_scratch(pic_t h) {
+  int64_t bytes = 0;
+  for (const auto &b : h->tab_scratch) bytes += (int64_t)b.bytes;
+  if (bytes > (int64_t)256 << 20) free_bufs(h, h->tab_scratch);
+}
+
 int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const std::vector<double> &qs,
                    std::vector<DevBuf> *old = nullptr) {
   if (!trees || n_inst < 1) return fail(h, PIC_EINVAL, "tree descriptor is NULL");
@@ -226,9 +286,11 @@ int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const st
     int64_t mv = 1;
     for (int a = 0; a < ht.d; ++a) mv *= ht.M;
     if (mv > INT32_MAX) return fail(h, PIC_EINVAL, "finest level has more than 2^31 grid points");
+    if (n_inst == 1 && grid_on_device_fits(ht) && !host_tables_forced()) continue;  // tabulated on the device below
     ht.build_grid();
     if (h->scheme == PIC_PIDT) ht.build_pidt();  // PIT handles build it on demand
   }
+  const bool on_device = n_inst == 1 && grid_on_device_fits(hts[0]) && !host_tables_forced();
   const HostTree &h0 = hts[0];
   const int d = h0.d, nc = h0.nc;
   int64_t nl = 0, nv = 0, npv = 0, ntab = 0, nspread = 0;
@@ -259,7 +321,7 @@ int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const st
     ntab += (int64_t)ht.tab.size();
     if (ht.uniform) nspread += (int64_t)d * ht.M;
   }
-  const int64_t nkeys = h->scheme == PIC_PIT ? nl : npv * nc;
+  int64_t nkeys = h->scheme == PIC_PIT ? nl : npv * nc;
   if (nl >= INT32_MAX / 8 || nv >= INT32_MAX || nkeys >= INT32_MAX)
     return fail(h, PIC_EINVAL, "more than 2^31 leaves, vertices or sort keys");
   std::vector<TabEntry> tab;
@@ -316,6 +378,58 @@ int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const st
   if ((rc = upload(h, tb, &dt.tab, tab))) return rc;
   if ((rc = upload(h, tb, &dt.leaf_level, leaf_level))) return rc;
   if ((rc = upload(h, tb, &dt.leaf_coords, leaf_coords))) return rc;
+  bool device_tables = false;
+  if (on_device) {
+    // the grid and owner tables of the adaptive tree, built on the GPU
+    HostTree &ht = hts[0];
+    TabCtx ctx{h, &tb, 0};
+    GridAlloc A{&ctx, tab_alloc, tab_release};
+    DeviceGrid G;
+    const int trc = tabulate_on_device(ht, dt.tab, dt.leaf_level, dt.leaf_coords, h->scheme == PIC_PIDT, h->stream,
+                                       A, &G);
+    trim_tab_scratch(h);
+    if (trc == kTabNoMemory) return fail(h, PIC_ENOMEM, "device memory for the tree tables");
+    if (trc == kTabCuda) return cuda_fail(h, cudaGetLastError(), "device tabulation of the tree");
+    if (trc == 0) {
+      device_tables = true;
+      nv = G.n_vert;
+      npv = h->scheme == PIC_PIDT ? G.n_pv : 0;
+      nkeys = h->scheme == PIC_PIT ? nl : npv * nc;
+      if (nv >= INT32_MAX || nkeys >= INT32_MAX) return fail(h, PIC_EINVAL, "more than 2^31 vertices or sort keys");
+      ht.n_vert = nv;
+      ht.n_pv = npv;
+      ht.pidt_built = h->scheme == PIC_PIDT;  // the owner tables live on the device (gdev)
+      inst[0].n_vert = (int32_t)nv;
+      dt.n_vert = nv;
+      dt.n_pv = npv;
+      dt.n_keys = nkeys;
+      dt.cexp_ptr = G.cexp_ptr;
+      dt.cexp_vid = G.cexp_vid;
+      dt.cexp_w64 = G.cexp_w64;
+      dt.cexp_w32 = G.cexp_w32;
+      dt.inc_ptr = G.inc_ptr;
+      dt.inc_lc = G.inc_lc;
+      dt.inc_w64 = G.inc_w64;
+      dt.inc_w32 = G.inc_w32;
+      dt.ion64 = G.ion64;
+      dt.ion32 = G.ion32;
+      dt.diag64 = G.diag64;
+      dt.diag32 = G.diag32;
+      dt.dcnt = G.dcnt;
+      dt.corner_pv = G.corner_pv;
+      h->gdev = G;
+    } else {  // an expansion too long for the device path: the host tables
+      ht.build_grid();
+      if (h->scheme == PIC_PIDT) ht.build_pidt();
+      nv = ht.n_vert;
+      npv = h->scheme == PIC_PIDT ? ht.n_pv : 0;
+      nkeys = h->scheme == PIC_PIT ? nl : npv * nc;
+      inst[0].n_vert = (int32_t)nv;
+      dt.n_vert = nv;
+      dt.n_pv = npv;
+      dt.n_keys = nkeys;
+    }
+  }
   if ((rc = upload(h, tb, &dt.inst, inst))) return rc;
   if (n_inst > 1) {
     if ((rc = upload(h, tb, &dt.inst_of_leaf, iol))) return rc;
@@ -323,7 +437,7 @@ int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const st
   }
   if (h0.uniform) {
     if ((rc = upload(h, tb, &dt.spread, spread))) return rc;
-  } else {
+  } else if (!device_tables) {
     const HostTree &ht = h0;
     std::vector<float> f;
     auto to32 = [&](const table<double> &v) {
@@ -350,6 +464,8 @@ int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const st
   h->inst = inst;
   h->hts = std::move(hts);
   h->dt = dt;
+  h->grid_dev = device_tables;
+  if (!device_tables) h->gdev = DeviceGrid{};
   h->tree_gen++;
   if (old)
     old->swap(prev);
@@ -972,6 +1088,7 @@ void pic_destroy(pic_t h) {
   free_bufs(h, h->diag_bufs);
   free_bufs(h, h->lift_tab_bufs);
   free_bufs(h, h->adapt_bufs);
+  free_bufs(h, h->tab_scratch);
   free_bufs(h, h->brick_bufs);
   free_bufs(h, h->grid_bufs);
   free_bufs(h, h->state_bufs);
@@ -1103,7 +1220,10 @@ static int lift_tables(pic_t h) {
   if (h->scheme != PIC_PIDT || h->lift_gen == h->tree_gen) return PIC_OK;
   free_bufs(h, h->lift_tab_bufs);
   h->lift_pvl = h->lift_pvj = nullptr;
-  if (!h->dt.uniform) {
+  if (!h->dt.uniform && h->grid_dev) {  // tabulated on the device: already int32 device arrays
+    h->lift_pvl = h->gdev.pv_level;
+    h->lift_pvj = h->gdev.pv_j;
+  } else if (!h->dt.uniform) {
     HostTree &t = h->ht0();
     t.build_pidt();
     std::vector<int32_t> pvl(t.pv_level.begin(), t.pv_level.end());
@@ -1676,10 +1796,15 @@ int pic_leaf_table(pic_t h, int32_t *level, int64_t *coords) {
 int pic_vertex_table(pic_t h, int64_t *pos) {
   if (check_handle(h) || !pos) return PIC_EINVAL;
   const int64_t nv = h->dt.n_vert;
+  std::vector<int64_t> dkeys;  // vertex keys of device-tabulated tables
+  if (h->grid_dev) {
+    dkeys.resize(nv);
+    CK(cudaMemcpy(dkeys.data(), h->gdev.vert_key, sizeof(int64_t) * nv, cudaMemcpyDeviceToHost));
+  }
   int64_t base = 0;
   for (const auto &t : h->hts) {
     for (int64_t v = 0; v < t.n_vert; ++v) {
-      int64_t k = t.uniform ? v : t.vert_key[v];
+      int64_t k = t.uniform ? v : (h->grid_dev ? dkeys[v] : t.vert_key[v]);
       for (int a = 0; a < t.d; ++a) {
         pos[a * nv + base + v] = k % t.M;
         k /= t.M;
@@ -1736,9 +1861,38 @@ int pic_tree_tabulate(int32_t d, const uint8_t *flags, int64_t n_flags, pic_tree
   return PIC_OK;
 }
 
+int pic_grid_tables(pic_t h, int64_t *n_entries, int32_t *cexp_ptr, int32_t *cexp_vid, double *cexp_w,
+                    double *ion_load, double *diag) {
+  if (check_handle(h)) return PIC_EINVAL;
+  if (h->dt.n_inst != 1 || h->dt.uniform)
+    return fail(h, PIC_ESTATE, "grid tables belong to single-instance handles with an adaptive tree");
+  const int64_t nlc = h->dt.n_leaves * h->dt.nc, nv = h->dt.n_vert;
+  int32_t nnz = 0;
+  CK(cudaMemcpy(&nnz, h->dt.cexp_ptr + nlc, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (n_entries) *n_entries = nnz;
+  if (cexp_ptr) CK(cudaMemcpy(cexp_ptr, h->dt.cexp_ptr, sizeof(int32_t) * (nlc + 1), cudaMemcpyDeviceToHost));
+  if (cexp_vid) CK(cudaMemcpy(cexp_vid, h->dt.cexp_vid, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+  if (cexp_w) CK(cudaMemcpy(cexp_w, h->dt.cexp_w64, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+  if (ion_load) CK(cudaMemcpy(ion_load, h->dt.ion64, sizeof(double) * nv, cudaMemcpyDeviceToHost));
+  if (diag) CK(cudaMemcpy(diag, h->dt.diag64, sizeof(double) * nv, cudaMemcpyDeviceToHost));
+  return PIC_OK;
+}
+
 int pic_pidt_table(pic_t h, int32_t *level, int64_t *j) {
   if (check_handle(h)) return PIC_EINVAL;
   if (h->scheme != PIC_PIDT) return fail(h, PIC_ESTATE, "owner-vertex tables belong to PIDT handles");
+  if (h->grid_dev) {  // one adaptive instance, tabulated on the device
+    const HostTree &t = h->ht0();
+    std::vector<int32_t> pl(t.n_pv), pj(t.n_pv * t.d);
+    CK(cudaMemcpy(pl.data(), h->gdev.pv_level, sizeof(int32_t) * pl.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(pj.data(), h->gdev.pv_j, sizeof(int32_t) * pj.size(), cudaMemcpyDeviceToHost));
+    for (int64_t v = 0; v < t.n_pv; ++v) {
+      if (level) level[v] = pl[v];
+      if (j)
+        for (int a = 0; a < t.d; ++a) j[v * t.d + a] = pj[v * t.d + a];
+    }
+    return PIC_OK;
+  }
   int64_t base = 0;
   for (auto &t : h->hts) {
     t.build_pidt();

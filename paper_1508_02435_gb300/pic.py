@@ -103,6 +103,7 @@ SIGNATURES = [
     ("pic_leaf_table", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     ("pic_vertex_table", C.c_int, [C.c_void_p, C.c_void_p]),
     ("pic_pidt_table", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("pic_grid_tables", C.c_int, [C.c_void_p, C.c_void_p] + [C.c_void_p] * 5),
     ("pic_retree", C.c_int, [C.c_void_p, C.POINTER(TreeDesc)]),
     ("pic_adapt", C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_int32]),
     ("pic_tree_flags", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -602,6 +603,18 @@ class Pic:
         j = np.zeros((nb, self.d), np.int64)
         self._check(self.lib.pic_pidt_table(self.h, _ptr(lev)[0], _ptr(j)[0]))
         return lev, j
+
+    def grid_tables(self) -> dict:
+        """The finite-element tables the kernels read (adaptive single-instance
+        handles): cexp_ptr, cexp_vid, cexp_w, ion_load, diag (pic_grid_tables)."""
+        nnz = C.c_int64(0)
+        self._check(self.lib.pic_grid_tables(self.h, C.byref(nnz), None, None, None, None, None))
+        nlc = int(self._info.n_leaves) * (1 << self.d)
+        out = {"cexp_ptr": np.zeros(nlc + 1, np.int32), "cexp_vid": np.zeros(nnz.value, np.int32),
+               "cexp_w": np.zeros(nnz.value), "ion_load": np.zeros(self.n_vertices), "diag": np.zeros(self.n_vertices)}
+        self._check(self.lib.pic_grid_tables(self.h, None, *(_ptr(out[k])[0] for k in
+                                                             ("cexp_ptr", "cexp_vid", "cexp_w", "ion_load", "diag"))))
+        return out
 
     def retree(self, flags):
         flags = np.ascontiguousarray(flags, dtype=np.uint8)
