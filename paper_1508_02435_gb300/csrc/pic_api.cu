@@ -60,6 +60,12 @@ struct pic_s {
   DeviceGrid gdev{};
   bool grid_dev = false;
   std::vector<DevBuf> tab_scratch;
+  // buffers of superseded trees and grids, reused by the next re-tree
+  struct Spare {
+    DevBuf b;
+    uint64_t gen;
+  };
+  std::vector<Spare> spare;
   int64_t adapt_cells = 0, adapt_words = 0;
   int32_t *adapt_count = nullptr;
   uint32_t *adapt_bits = nullptr;
@@ -212,6 +218,52 @@ int upload(pic_t h, std::vector<DevBuf> &bufs, const T **out, const std::vector<
   return PIC_OK;
 }
 
+// Tree and grid buffers go through a spare list: a superseded tree's or
+// grid's buffers are kept, and a request takes the smallest spare buffer that
+// holds it (at most twice its size), so re-trees of similar trees need no
+// cudaMalloc / cudaFree.  Spares not taken by the next re-tree are freed.
+template <typename T>
+int galloc(pic_t h, std::vector<DevBuf> &bufs, T **out, size_t count) {
+  const size_t bytes = sizeof(T) * (count ? count : 1);
+  int best = -1;
+  for (size_t i = 0; i < h->spare.size(); ++i) {
+    const size_t b = h->spare[i].b.bytes;
+    if (b >= bytes && b <= 2 * bytes + 65536 && (best < 0 || b < h->spare[best].b.bytes)) best = (int)i;
+  }
+  if (best < 0) return dalloc(h, bufs, out, count);
+  bufs.push_back(h->spare[best].b);
+  *out = (T *)h->spare[best].b.p;
+  h->spare.erase(h->spare.begin() + best);
+  return PIC_OK;
+}
+
+void retire(pic_t h, std::vector<DevBuf> &bufs) {
+  for (auto &b : bufs) h->spare.push_back({b, h->tree_gen});
+  bufs.clear();
+}
+
+// Frees the spares retired before tree generation `gen`.
+void drop_spares(pic_t h, uint64_t gen) {
+  std::vector<DevBuf> old;
+  size_t k = 0;
+  for (auto &sp : h->spare) {
+    if (sp.gen < gen) old.push_back(sp.b);
+    else h->spare[k++] = sp;
+  }
+  h->spare.resize(k);
+  free_bufs(h, old);
+}
+
+template <typename T, typename A>
+int gupload(pic_t h, std::vector<DevBuf> &bufs, const T **out, const std::vector<T, A> &v) {
+  T *p = nullptr;
+  int rc = galloc(h, bufs, &p, v.size());
+  if (rc) return rc;
+  if (!v.empty()) CK(cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  *out = p;
+  return PIC_OK;
+}
+
 // Tabulate the trees of all instances on the host and upload the device view
 // (leaves, vertices and keys concatenated instance by instance).  The previous
 // device buffers are handed back in *old (freed by the caller) so particles
@@ -237,7 +289,7 @@ int tab_alloc(void *c, void **out, size_t bytes, bool keep) {
   pic_t h = ctx->h;
   char *p = nullptr;
   if (keep) {
-    if (dalloc(h, *ctx->keep, &p, bytes)) return kTabNoMemory;
+    if (galloc(h, *ctx->keep, &p, bytes)) return kTabNoMemory;
     *out = p;
     return 0;
   }
@@ -375,9 +427,9 @@ int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const st
   dt.n_tab = (int32_t)tab.size();
   int rc;
   auto &tb = h->tree_bufs;
-  if ((rc = upload(h, tb, &dt.tab, tab))) return rc;
-  if ((rc = upload(h, tb, &dt.leaf_level, leaf_level))) return rc;
-  if ((rc = upload(h, tb, &dt.leaf_coords, leaf_coords))) return rc;
+  if ((rc = gupload(h, tb, &dt.tab, tab))) return rc;
+  if ((rc = gupload(h, tb, &dt.leaf_level, leaf_level))) return rc;
+  if ((rc = gupload(h, tb, &dt.leaf_coords, leaf_coords))) return rc;
   bool device_tables = false;
   if (on_device) {
     // the grid and owner tables of the adaptive tree, built on the GPU
@@ -430,13 +482,13 @@ int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const st
       dt.n_keys = nkeys;
     }
   }
-  if ((rc = upload(h, tb, &dt.inst, inst))) return rc;
+  if ((rc = gupload(h, tb, &dt.inst, inst))) return rc;
   if (n_inst > 1) {
-    if ((rc = upload(h, tb, &dt.inst_of_leaf, iol))) return rc;
-    if ((rc = upload(h, tb, &dt.inst_of_vert, iov))) return rc;
+    if ((rc = gupload(h, tb, &dt.inst_of_leaf, iol))) return rc;
+    if ((rc = gupload(h, tb, &dt.inst_of_vert, iov))) return rc;
   }
   if (h0.uniform) {
-    if ((rc = upload(h, tb, &dt.spread, spread))) return rc;
+    if ((rc = gupload(h, tb, &dt.spread, spread))) return rc;
   } else if (!device_tables) {
     const HostTree &ht = h0;
     std::vector<float> f;
@@ -445,20 +497,20 @@ int install_forest(pic_t h, const pic_tree_desc *trees, int32_t n_inst, const st
       for (size_t i = 0; i < v.size(); ++i) f[i] = (float)v[i];
       return f;
     };
-    if ((rc = upload(h, tb, &dt.cexp_ptr, ht.cexp_ptr))) return rc;
-    if ((rc = upload(h, tb, &dt.cexp_vid, ht.cexp_vid))) return rc;
-    if ((rc = upload(h, tb, &dt.cexp_w64, ht.cexp_w))) return rc;
-    if ((rc = upload(h, tb, &dt.cexp_w32, to32(ht.cexp_w)))) return rc;
-    if ((rc = upload(h, tb, &dt.inc_ptr, ht.inc_ptr))) return rc;
-    if ((rc = upload(h, tb, &dt.inc_lc, ht.inc_lc))) return rc;
-    if ((rc = upload(h, tb, &dt.inc_w64, ht.inc_w))) return rc;
-    if ((rc = upload(h, tb, &dt.inc_w32, to32(ht.inc_w)))) return rc;
-    if ((rc = upload(h, tb, &dt.ion64, ht.ion_load))) return rc;
-    if ((rc = upload(h, tb, &dt.ion32, to32(ht.ion_load)))) return rc;
-    if ((rc = upload(h, tb, &dt.diag64, ht.diag))) return rc;
-    if ((rc = upload(h, tb, &dt.diag32, to32(ht.diag)))) return rc;
-    if ((rc = upload(h, tb, &dt.dcnt, ht.direct_cnt))) return rc;
-    if ((rc = upload(h, tb, &dt.corner_pv, ht.corner_pv))) return rc;
+    if ((rc = gupload(h, tb, &dt.cexp_ptr, ht.cexp_ptr))) return rc;
+    if ((rc = gupload(h, tb, &dt.cexp_vid, ht.cexp_vid))) return rc;
+    if ((rc = gupload(h, tb, &dt.cexp_w64, ht.cexp_w))) return rc;
+    if ((rc = gupload(h, tb, &dt.cexp_w32, to32(ht.cexp_w)))) return rc;
+    if ((rc = gupload(h, tb, &dt.inc_ptr, ht.inc_ptr))) return rc;
+    if ((rc = gupload(h, tb, &dt.inc_lc, ht.inc_lc))) return rc;
+    if ((rc = gupload(h, tb, &dt.inc_w64, ht.inc_w))) return rc;
+    if ((rc = gupload(h, tb, &dt.inc_w32, to32(ht.inc_w)))) return rc;
+    if ((rc = gupload(h, tb, &dt.ion64, ht.ion_load))) return rc;
+    if ((rc = gupload(h, tb, &dt.ion32, to32(ht.ion_load)))) return rc;
+    if ((rc = gupload(h, tb, &dt.diag64, ht.diag))) return rc;
+    if ((rc = gupload(h, tb, &dt.diag32, to32(ht.diag)))) return rc;
+    if ((rc = gupload(h, tb, &dt.dcnt, ht.direct_cnt))) return rc;
+    if ((rc = gupload(h, tb, &dt.corner_pv, ht.corner_pv))) return rc;
   }
   h->d = d;
   h->inst = inst;
@@ -543,42 +595,42 @@ int alloc_particles(pic_t h) {
 // partials, vertex fields, the FP64 staging area); the solver's warm start
 // and the field start from zero.
 int alloc_grid(pic_t h) {
-  free_bufs(h, h->grid_bufs);
+  retire(h, h->grid_bufs);  // stream-ordered reuse: every later use is queued after the old one
   auto &sb = h->grid_bufs;
   const int64_t n = h->n, d = h->d;
   const size_t fs = h->split ? sizeof(float) : sizeof(double);
   const int64_t nk = h->dt.n_keys, nv = h->dt.n_vert, nl = h->dt.n_leaves;
   int rc;
   // bucket offsets, padded: the brick kernels copy whole 16-byte units of them
-  if ((rc = dalloc(h, sb, &h->start_cur, nk + 8))) return rc;
-  if ((rc = dalloc(h, sb, &h->start_new, nk + 8))) return rc;
-  if ((rc = dalloc(h, sb, &h->count, nk))) return rc;
-  if ((rc = dalloc(h, sb, &h->n_stay, nk))) return rc;
-  if ((rc = dalloc(h, sb, &h->cursor, nk))) return rc;
-  if ((rc = dalloc(h, sb, &h->tile_sums, scan_tiles_needed(nk) + 1))) return rc;
+  if ((rc = galloc(h, sb, &h->start_cur, nk + 8))) return rc;
+  if ((rc = galloc(h, sb, &h->start_new, nk + 8))) return rc;
+  if ((rc = galloc(h, sb, &h->count, nk))) return rc;
+  if ((rc = galloc(h, sb, &h->n_stay, nk))) return rc;
+  if ((rc = galloc(h, sb, &h->cursor, nk))) return rc;
+  if ((rc = galloc(h, sb, &h->tile_sums, scan_tiles_needed(nk) + 1))) return rc;
   char *p;
-  if ((rc = dalloc(h, sb, &p, fs * nl * h->dt.nc))) return rc;
+  if ((rc = galloc(h, sb, &p, fs * nl * h->dt.nc))) return rc;
   h->part = p;
-  if ((rc = dalloc(h, sb, &p, fs * nv))) return rc;
+  if ((rc = galloc(h, sb, &p, fs * nv))) return rc;
   h->Q = p;
-  if ((rc = dalloc(h, sb, &p, fs * nv))) return rc;
+  if ((rc = galloc(h, sb, &p, fs * nv))) return rc;
   h->b = p;
-  if ((rc = dalloc(h, sb, &p, fs * nv))) return rc;
+  if ((rc = galloc(h, sb, &p, fs * nv))) return rc;
   h->V = p;
-  if ((rc = dalloc(h, sb, &p, fs * nv))) return rc;
+  if ((rc = galloc(h, sb, &p, fs * nv))) return rc;
   h->Vtmp = p;
-  if ((rc = dalloc(h, sb, &p, fs * nv * d))) return rc;
+  if ((rc = galloc(h, sb, &p, fs * nv * d))) return rc;
   h->E = p;
-  if ((rc = dalloc(h, sb, &h->block_sum, (nv + 127) / 128 + 1))) return rc;
-  if ((rc = dalloc(h, sb, &h->total, 2 + h->dt.n_inst))) return rc;
-  if ((rc = dalloc(h, sb, &h->resid2, 2))) return rc;
+  if ((rc = galloc(h, sb, &h->block_sum, (nv + 127) / 128 + 1))) return rc;
+  if ((rc = galloc(h, sb, &h->total, 2 + h->dt.n_inst))) return rc;
+  if ((rc = galloc(h, sb, &h->resid2, 2))) return rc;
   // FP64 staging: particle arrays (d * n) and widened vertex fields (d * n_vert)
-  if ((rc = dalloc(h, sb, &p, sizeof(double) * d * std::max(n, nv)))) return rc;
+  if ((rc = galloc(h, sb, &p, sizeof(double) * d * std::max(n, nv)))) return rc;
   h->Ep = p;
   h->ecorner = nullptr;
   h->ecorner_valid = false;
   h->ebrick_valid = false;
-  if (h->split && !h->dt.uniform && (rc = dalloc(h, sb, &h->ecorner, nl * h->dt.nc))) return rc;
+  if (h->split && !h->dt.uniform && (rc = galloc(h, sb, &h->ecorner, nl * h->dt.nc))) return rc;
   return reset_grid_state(h);
 }
 
@@ -1089,6 +1141,11 @@ void pic_destroy(pic_t h) {
   free_bufs(h, h->lift_tab_bufs);
   free_bufs(h, h->adapt_bufs);
   free_bufs(h, h->tab_scratch);
+  for (auto &sp : h->spare) {
+    std::vector<DevBuf> one(1, sp.b);
+    free_bufs(h, one);
+  }
+  h->spare.clear();
   free_bufs(h, h->brick_bufs);
   free_bufs(h, h->grid_bufs);
   free_bufs(h, h->state_bufs);
@@ -1951,7 +2008,8 @@ int pic_retree(pic_t h, const pic_tree_desc *tree) {
     return rc;
   }
   CK(cudaStreamSynchronize(s));  // the re-location read the old tables
-  free_bufs(h, old_tree);
+  drop_spares(h, h->tree_gen);    // spares of earlier re-trees that this one did not take
+  retire(h, old_tree);
   h->leaf_stale = false;
   h->q_valid = false;
   return setup_brick(h);

@@ -40,6 +40,11 @@ unsigned grid_of(int64_t n) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
+// Per leaf level l: the corner integral of a unit density, (3^-l)^d / 2^d,
+// and the stiffness scale (1 in 2D, 3^-l in 3D), formed on the host by the
+// same operations as the host tabulation forms them per leaf.
+__constant__ double c_tg_cint[kMaxLevel + 1], c_tg_hs[kMaxLevel + 1];
+
 struct HexEntry {
   int32_t pid;
   int32_t pad;
@@ -383,24 +388,29 @@ __device__ __forceinline__ double kref_dev(int d, int e, int f) {
 
 // Per vertex: ion load, stiffness diagonal and the number of leaf corners that
 // are the vertex itself, summed over the incident corners in leaf-corner
-// order, pairs of corners of one leaf in (e, f) order.
+// order, pairs of corners of one leaf in (e, f) order.  Vertices with up to
+// kSmallSeg incidences take one thread each; longer lists (the masters of
+// many hanging points) are listed for one warp each.
 __global__ void k_tg_vertex_aux(TV v, const int32_t *inc_ptr, const int32_t *inc_lc, const double *inc_w,
                                 const int32_t *cexp_ptr, const int32_t *corner_pt, const uint8_t *hanging,
-                                int64_t nv, double *ion_load, double *diag, int32_t *dcnt) {
+                                int64_t nv, double *ion_load, double *diag, int32_t *dcnt, int32_t *long_list,
+                                int32_t *n_long) {
   const int64_t vx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (vx >= nv) return;
   const int nc = v.nc, d = v.d;
+  const int32_t end = inc_ptr[vx + 1];
+  if (end - inc_ptr[vx] > kSmallSeg) {
+    long_list[atomicAdd(n_long, 1)] = (int32_t)vx;
+    return;
+  }
   double ion = 0.0, dg = 0.0;
   int32_t dc = 0;
-  const int32_t end = inc_ptr[vx + 1];
   for (int32_t j = inc_ptr[vx]; j < end;) {
     const int64_t leaf = inc_lc[j] / nc;
     int32_t k = j;
     while (k < end && inc_lc[k] / nc == leaf) ++k;
-    const double h = 1.0 / (double)p3_64(v.leaf_level[leaf]);
-    double vol = 1.0;
-    for (int a = 0; a < d; ++a) vol *= h;
-    const double cint = vol / (double)nc, hs = d == 2 ? 1.0 : h;
+    const int lev = v.leaf_level[leaf];
+    const double cint = c_tg_cint[lev], hs = c_tg_hs[lev];
     for (int32_t a1 = j; a1 < k; ++a1) {
       const int64_t i = inc_lc[a1];
       ion += inc_w[a1] * cint;
@@ -416,6 +426,66 @@ __global__ void k_tg_vertex_aux(TV v, const int32_t *inc_ptr, const int32_t *inc
   ion_load[vx] = ion;
   diag[vx] = dg;
   dcnt[vx] = dc;
+}
+
+// The same for one long list per warp: 32 incidences at a time, each lane
+// forms the terms of one incidence (its ion term, its direct-corner flag and
+// its pair terms with the corners of the same leaf), then lane 0 adds them
+// in the order of the one-thread loop.
+__global__ void __launch_bounds__(kTB) k_tg_vertex_aux_long(TV v, const int32_t *inc_ptr, const int32_t *inc_lc,
+                                                            const double *inc_w, const int32_t *cexp_ptr,
+                                                            const int32_t *corner_pt, const uint8_t *hanging,
+                                                            const int32_t *long_list, const int32_t *n_long,
+                                                            double *ion_load, double *diag, int32_t *dcnt) {
+  __shared__ double s_ion[kTB], s_pair[kTB * 8];
+  __shared__ uint8_t s_np[kTB], s_dir[kTB];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int32_t warp = (int32_t)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int32_t nw = (int32_t)(((int64_t)gridDim.x * blockDim.x) >> 5);
+  const int nc = v.nc, d = v.d;
+  double *pi = s_ion + wib * 32, *pp = s_pair + wib * 32 * 8;
+  uint8_t *np = s_np + wib * 32, *dir = s_dir + wib * 32;
+  for (int32_t t = warp; t < *n_long; t += nw) {
+    const int32_t vx = long_list[t];
+    const int32_t b = inc_ptr[vx], end = inc_ptr[vx + 1];
+    double ion = 0.0, dg = 0.0;
+    int32_t dc = 0;
+    for (int32_t c0 = b; c0 < end; c0 += 32) {
+      const int32_t a1 = c0 + lane;
+      if (a1 < end) {
+        const int64_t i = inc_lc[a1];
+        const int64_t leaf = i / nc;
+        int32_t j = a1, k = a1 + 1;  // the run of incidences of the same leaf
+        while (j > b && inc_lc[j - 1] / nc == leaf) --j;
+        while (k < end && inc_lc[k] / nc == leaf) ++k;
+        const int lev = v.leaf_level[leaf];
+        const double cint = c_tg_cint[lev], hs = c_tg_hs[lev];
+        pi[lane] = inc_w[a1] * cint;
+        dir[lane] = cexp_ptr[i + 1] - cexp_ptr[i] == 1 && !hanging[corner_pt[i]];
+        const int e = (int)(i % nc);
+        np[lane] = (uint8_t)(k - j);
+        for (int32_t a2 = j; a2 < k; ++a2) {
+          const int f = (int)(inc_lc[a2] % nc);
+          pp[lane * 8 + (a2 - j)] = kref_dev(d, e, f) * hs * inc_w[a1] * inc_w[a2];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        const int m = end - c0 < 32 ? end - c0 : 32;
+        for (int q = 0; q < m; ++q) {
+          ion += pi[q];
+          dc += dir[q];
+          for (int r = 0; r < np[q]; ++r) dg += pp[q * 8 + r];
+        }
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      ion_load[vx] = ion;
+      diag[vx] = dg;
+      dcnt[vx] = dc;
+    }
+  }
 }
 
 __global__ void k_tg_to32(const double *in, int64_t n, float *out) {
@@ -507,6 +577,16 @@ int tabulate_on_device(const HostTree &ht, const TabEntry *tab, const uint8_t *l
     p3[0] = 1;
     for (int i = 1; i < 21; ++i) p3[i] = p3[i - 1] * 3u;
     TG_CK(cudaMemcpyToSymbolAsync(c_pow3, p3, sizeof(p3), 0, cudaMemcpyHostToDevice, s));
+    double cint[kMaxLevel + 1], hs[kMaxLevel + 1];
+    for (int l = 0; l <= kMaxLevel; ++l) {
+      const double h = 1.0 / (double)pow3(l);
+      double vol = 1.0;
+      for (int a = 0; a < ht.d; ++a) vol *= h;
+      cint[l] = vol / (double)ht.nc;
+      hs[l] = ht.d == 2 ? 1.0 : h;
+    }
+    TG_CK(cudaMemcpyToSymbolAsync(c_tg_cint, cint, sizeof(cint), 0, cudaMemcpyHostToDevice, s));
+    TG_CK(cudaMemcpyToSymbolAsync(c_tg_hs, hs, sizeof(hs), 0, cudaMemcpyHostToDevice, s));
   }
   const int d = ht.d, nc = ht.nc;
   const int64_t nl = ht.n_leaves, nlc = nl * nc;
@@ -685,9 +765,13 @@ int tabulate_on_device(const HostTree &ht, const TabEntry *tab, const uint8_t *l
   TG_TAKE(out->ion32, float, nv, true);
   TG_TAKE(out->diag32, float, nv, true);
   TG_TAKE(out->dcnt, int32_t, nv, true);
+  TG_CK(cudaMemsetAsync(scal + 3, 0, sizeof(int32_t), s));
   ++launched;
   k_tg_vertex_aux<<<grid_of(nv), kTB, 0, s>>>(v, out->inc_ptr, out->inc_lc, out->inc_w64, out->cexp_ptr, corner_pt,
-                                              hanging, nv, out->ion64, out->diag64, out->dcnt);
+                                              hanging, nv, out->ion64, out->diag64, out->dcnt, long_list, scal + 3);
+  ++launched;
+  k_tg_vertex_aux_long<<<304, kTB, 0, s>>>(v, out->inc_ptr, out->inc_lc, out->inc_w64, out->cexp_ptr, corner_pt,
+                                           hanging, long_list, scal + 3, out->ion64, out->diag64, out->dcnt);
   ++launched;
   k_tg_to32<<<grid_of(nnz), kTB, 0, s>>>(out->cexp_w64, nnz, out->cexp_w32);
   ++launched;
