@@ -994,6 +994,34 @@ __global__ void k_count_parent(const int32_t *fine, int64_t ncoarse, int nch, in
   coarse[c] = t;
 }
 
+// Whether the particles-per-cell criterion keeps the installed tree: every
+// leaf on level l needs dmin <= l <= dmax and (l == dmax or its count <= ppc),
+// every ancestor on levels dmin .. l-1 a count > ppc.  Any leaf that fails
+// sets *changed.  Counts of level m at count + coff[m].
+struct AdaptCheck {
+  const int32_t *count;
+  int64_t coff[11];
+  int dmin, dmax;
+  int64_t ppc;
+};
+
+__global__ void k_adapt_check(DevTree t, AdaptCheck ac, int32_t *changed) {
+  const int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (L >= t.n_leaves) return;
+  int l;
+  int32_t c[3] = {0, 0, 0};
+  leaf_info(t, (int32_t)L, &l, c);
+  bool bad = l < ac.dmin || l > ac.dmax;
+  for (int m = ac.dmin; !bad && m <= l && m < ac.dmax; ++m) {
+    const uint32_t sh = c_pow3[l - m];
+    const int32_t idx = local_index((uint32_t)c[0] / sh, (uint32_t)c[1] / sh, t.d == 3 ? (uint32_t)c[2] / sh : 0u,
+                                    t.d, m);
+    const int32_t cnt = ac.count[ac.coff[m] + idx];
+    bad = m < l ? cnt <= ac.ppc : cnt > ac.ppc;
+  }
+  if (bad) *changed = 1;
+}
+
 // Split particles of tree `from` re-located in tree `to` (same positions):
 // the resolver of the split push with zero displacement.
 __global__ void k_relocate32(DevTree from, DevTree to, const int32_t *leaf, const float *o, const float *v,
@@ -1119,6 +1147,17 @@ void launch_adapt_bits(const uint32_t *key, int64_t n, int nch, int dmin, int dm
                                                                     bits + bit_off[m]);
     ncells /= nch;
   }
+}
+
+void launch_adapt_check(const DevTree &t, const int32_t *count, const int64_t *coff, int dmin, int dmax, int64_t ppc,
+                        int32_t *changed, cudaStream_t s) {
+  AdaptCheck ac{};
+  ac.count = count;
+  for (int m = 0; m <= dmax && m < 11; ++m) ac.coff[m] = coff[m];
+  ac.dmin = dmin;
+  ac.dmax = dmax;
+  ac.ppc = ppc;
+  if (t.n_leaves > 0) { COUNT(1); k_adapt_check<<<grid_for(t.n_leaves), kBlock, 0, s>>>(t, ac, changed); }
 }
 
 void launch_relocate32(const DevTree &from, const DevTree &to, const int32_t *leaf, const float *o, const float *v,

@@ -163,6 +163,11 @@ void launch_count_all(const int32_t *key, int64_t n, int32_t *count, uint32_t *m
 // level m (index key / div) holding more than ppc particles as a bitmap.
 void launch_fine_keys(const DevTree &t, bool split, const void *pos, const int32_t *leaf, int64_t n, int dmax,
                       uint32_t *key, cudaStream_t s);
+// *changed = 1 unless every leaf of t passes the particles-per-cell criterion
+// on the counts of levels dmin .. dmax-1 (level m at count + coff[m]), i.e.
+// unless the criterion gives back the installed tree.
+void launch_adapt_check(const DevTree &t, const int32_t *count, const int64_t *coff, int dmin, int dmax, int64_t ppc,
+                        int32_t *changed, cudaStream_t s);
 // Threshold bits (count > ppc) of every cell on levels dmin .. dmax-1 from
 // the level-dmax cell keys: counts on level dmax-1 summed up child by child;
 // level m's counts at count + cnt_off[m], its bits at bits + bit_off[m].

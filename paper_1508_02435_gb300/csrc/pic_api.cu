@@ -2051,7 +2051,20 @@ int pic_adapt(pic_t h, int64_t ppc, int32_t dmin, int32_t dmax) {
     uint32_t *key = (uint32_t *)h->perm;  // scratch until the next re-bin
     launch_fine_keys(h->dt, h->split, h->pos[0], h->leaf[0], n, dmax, key, s);
     launch_adapt_bits(key, n, nch, dmin, dmax, ppc, h->adapt_count, coff.data(), h->adapt_bits, boff.data(), s);
+  }
+  // the criterion on the installed tree's leaves first: when it keeps the
+  // tree, no flags are built
+  {
+    int32_t *changed = h->scalars + 7;  // free between re-bins
+    CK(cudaMemsetAsync(changed, 0, sizeof(int32_t), s));
+    launch_adapt_check(h->dt, h->adapt_count, coff.data(), dmin, dmax, ppc, changed, s);
+    int32_t ch = 1;
     CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&ch, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!ch) return reset_grid_state(h);
+  }
+  if (dmax > dmin) {
     CK(cudaMemcpyAsync(bits.data(), h->adapt_bits, sizeof(uint32_t) * words, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
   }
