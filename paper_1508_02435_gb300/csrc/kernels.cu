@@ -747,16 +747,27 @@ __global__ void k_scan_apply(const int32_t *in, int64_t n, const int32_t *tile_o
 }
 
 // Stayers of old bucket k keep their storage order at the head of new bucket k.
+// The largest new bucket goes to *max_bucket with one atomic per block.
 __global__ void k_stayers(const int32_t *old_start, const int32_t *keyn, const int32_t *new_start,
                           int64_t n_keys, int32_t *perm, int32_t *n_stay, int32_t *max_bucket) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n_keys) return;
-  int32_t r = 0, dst = new_start[k];
-  for (int32_t i = old_start[k]; i < old_start[k + 1]; ++i)
-    if (keyn[i] == (int32_t)k) perm[dst + r++] = i;
-  n_stay[k] = r;
-  int32_t sz = new_start[k + 1] - new_start[k];
-  if (sz > 0) atomicMax(max_bucket, sz);
+  __shared__ int32_t wmax[32];
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int32_t sz = 0;
+  if (k < n_keys) {
+    int32_t r = 0, dst = new_start[k];
+    for (int32_t i = old_start[k]; i < old_start[k + 1]; ++i)
+      if (keyn[i] == (int32_t)k) perm[dst + r++] = i;
+    n_stay[k] = r;
+    sz = new_start[k + 1] - new_start[k];
+  }
+  const int32_t m = __reduce_max_sync(0xffffffffu, sz);
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = b > wmax[w] ? b : wmax[w];
+    if (b > 0) atomicMax(max_bucket, b);
+  }
 }
 
 // Ballot words -> mover list in storage order.
@@ -847,6 +858,22 @@ __global__ void __launch_bounds__(kLargeThreads) k_sort_large(const int32_t *new
     block_sort_global<int32_t, int32_t>(perm + b, nullptr, m, sv, nullptr, kLargeSeg);
     __syncthreads();
   }
+}
+
+// The whole particle state into bucket order in one pass: positions and
+// velocities ([d][n]), leaves, and keys and ids where given.
+template <typename T>
+__global__ void k_gather_state(const int32_t *perm, int64_t n, int d, const T *x, T *x2, const T *v, T *v2,
+                               const int32_t *leaf, int32_t *leaf2, const int32_t *key, int32_t *key2,
+                               const int32_t *ids, int32_t *ids2) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int32_t i = perm[p];
+  for (int a = 0; a < d; ++a) x2[a * n + p] = x[a * n + i];
+  for (int a = 0; a < d; ++a) v2[a * n + p] = v[a * n + i];
+  leaf2[p] = leaf[i];
+  if (key) key2[p] = key[i];
+  if (ids) ids2[p] = ids[i];
 }
 
 template <typename T>
@@ -1310,6 +1337,20 @@ void launch_rebin(const RebinArgs &r, cudaStream_t s) {
       r.new_start, r.n_stay, r.movers, r.scalars + 7, r.perm); }
   { COUNT(1); k_sort_large<<<304, kLargeThreads, sizeof(int32_t) * kLargeSeg, s>>>(r.new_start, r.n_stay, r.cursor,
                                                                                   r.scalars + 5, r.perm); }
+}
+
+void launch_gather_state(bool split, const int32_t *perm, int64_t n, int d, const void *x, void *x2, const void *v,
+                         void *v2, const int32_t *leaf, int32_t *leaf2, const int32_t *key, int32_t *key2,
+                         const int32_t *ids, int32_t *ids2, cudaStream_t s) {
+  if (n <= 0) return;
+  COUNT(1);
+  if (split)
+    k_gather_state<float><<<grid_for(n), kBlock, 0, s>>>(perm, n, d, (const float *)x, (float *)x2, (const float *)v,
+                                                          (float *)v2, leaf, leaf2, key, key2, ids, ids2);
+  else
+    k_gather_state<double><<<grid_for(n), kBlock, 0, s>>>(perm, n, d, (const double *)x, (double *)x2,
+                                                           (const double *)v, (double *)v2, leaf, leaf2, key, key2,
+                                                           ids, ids2);
 }
 
 void launch_gather_f64(const int32_t *perm, int64_t n, int d, const double *src, double *dst, cudaStream_t s) {

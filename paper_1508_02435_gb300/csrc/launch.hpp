@@ -194,6 +194,11 @@ void launch_corner_field32(const DevTree &t, const float *E, float4 *Ec, cudaStr
 void launch_exclusive_scan(const int32_t *in, int64_t n, int32_t *out, int32_t *tile_sums, int32_t *total,
                            cudaStream_t s);
 void launch_rebin(const RebinArgs &r, cudaStream_t s);
+// dst[p] = src[perm[p]] for positions, velocities ([d][n]), leaves and,
+// where not NULL, keys and ids, in one kernel (split: float, else double).
+void launch_gather_state(bool split, const int32_t *perm, int64_t n, int d, const void *x, void *x2, const void *v,
+                         void *v2, const int32_t *leaf, int32_t *leaf2, const int32_t *key, int32_t *key2,
+                         const int32_t *ids, int32_t *ids2, cudaStream_t s);
 void launch_gather_f64(const int32_t *perm, int64_t n, int d, const double *src, double *dst, cudaStream_t s);
 void launch_gather_f32(const int32_t *perm, int64_t n, int d, const float *src, float *dst, cudaStream_t s);
 void launch_gather_i32(const int32_t *perm, int64_t n, const int32_t *src, int32_t *dst, cudaStream_t s);

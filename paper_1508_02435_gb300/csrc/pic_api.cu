@@ -877,18 +877,28 @@ int rebin_and_gather(pic_t h, const int32_t *old_start) {
   }
   PhaseScope ps(h, PIC_PHASE_PERMUTE);
   const int d = h->d;
-  if (h->split) {
+  if (h->scheme == PIC_PIT) {
+    // one pass over the permutation (measured faster for PIT; PIDT's extra
+    // key array makes the separate passes faster: 6.1 against 6.7 ms on the
+    // 2e8-particle 3D two-stream step)
+    launch_gather_state(h->split, h->perm, n, d, h->pos[1], h->pos[0], h->vel[1], h->vel[0], h->leaf[1],
+                        h->leaf[0], nullptr, nullptr, h->cfg.track_ids ? h->ids[0] : nullptr,
+                        h->cfg.track_ids ? h->ids[1] : nullptr, s);
+    if (h->cfg.track_ids) std::swap(h->ids[0], h->ids[1]);
+  } else if (h->split) {
     launch_gather_f32(h->perm, n, d, (const float *)h->pos[1], (float *)h->pos[0], s);
     launch_gather_f32(h->perm, n, d, (const float *)h->vel[1], (float *)h->vel[0], s);
   } else {
     launch_gather_f64(h->perm, n, d, (const double *)h->pos[1], (double *)h->pos[0], s);
     launch_gather_f64(h->perm, n, d, (const double *)h->vel[1], (double *)h->vel[0], s);
   }
-  launch_gather_i32(h->perm, n, h->leaf[1], h->leaf[0], s);
-  if (h->scheme != PIC_PIT) launch_gather_i32(h->perm, n, h->key[1], h->key[0], s);
-  if (h->cfg.track_ids) {
-    launch_gather_i32(h->perm, n, h->ids[0], h->ids[1], s);
-    std::swap(h->ids[0], h->ids[1]);
+  if (h->scheme != PIC_PIT) {
+    launch_gather_i32(h->perm, n, h->leaf[1], h->leaf[0], s);
+    launch_gather_i32(h->perm, n, h->key[1], h->key[0], s);
+    if (h->cfg.track_ids) {
+      launch_gather_i32(h->perm, n, h->ids[0], h->ids[1], s);
+      std::swap(h->ids[0], h->ids[1]);
+    }
   }
   std::swap(h->start_cur, h->start_new);
   h->leaf_stale = false;
