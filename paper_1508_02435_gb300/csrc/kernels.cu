@@ -467,13 +467,16 @@ __device__ __forceinline__ double fold64(double y, bool *flip) {
   return m;
 }
 
+// D = t.d as a compile-time constant: the per-axis loops unroll and the
+// per-particle arrays stay in registers.
+template <int D>
 __global__ void k_push64(DevTree t, Push64Args a) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool act = p < a.n;
   int32_t knew = 0;
   bool moved = false;
   if (act) {
-    const int d = t.d, nc = t.nc;
+    constexpr int d = D, nc = 1 << D;
     const int64_t n = a.n, nv = t.n_vert;
     int32_t L = a.leaf[p];
     int lev;
@@ -547,13 +550,14 @@ __global__ void k_push64(DevTree t, Push64Args a) {
   count_and_ballot(act, knew, moved, a.count, a.mover_words, a.block_movers);
 }
 
+template <int D>
 __global__ void k_push32(DevTree t, Push32Args a) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool act = p < a.n;
   int32_t knew = 0;
   bool moved = false;
   if (act) {
-    const int d = t.d, nc = t.nc;
+    constexpr int d = D, nc = 1 << D;
     const int64_t n = a.n, nv = t.n_vert;
     int32_t L = a.leaf[p];
     int lev;
@@ -1275,7 +1279,9 @@ void launch_efield(const DevTree &t, bool split, const void *V, void *E, cudaStr
 }
 
 void launch_push64(const DevTree &t, const Push64Args &a, cudaStream_t s) {
-  { COUNT(1); k_push64<<<grid_for(a.n, bsz(t.block_push)), bsz(t.block_push), 0, s>>>(t, a); }
+  COUNT(1);
+  if (t.d == 3) k_push64<3><<<grid_for(a.n, bsz(t.block_push)), bsz(t.block_push), 0, s>>>(t, a);
+  else k_push64<2><<<grid_for(a.n, bsz(t.block_push)), bsz(t.block_push), 0, s>>>(t, a);
 }
 
 // Field at every leaf corner: the same expansion sums the push would form
@@ -1299,7 +1305,9 @@ void launch_corner_field32(const DevTree &t, const float *E, float4 *Ec, cudaStr
 }
 
 void launch_push32(const DevTree &t, const Push32Args &a, cudaStream_t s) {
-  { COUNT(1); k_push32<<<grid_for(a.n, bsz(t.block_push)), bsz(t.block_push), 0, s>>>(t, a); }
+  COUNT(1);
+  if (t.d == 3) k_push32<3><<<grid_for(a.n, bsz(t.block_push)), bsz(t.block_push), 0, s>>>(t, a);
+  else k_push32<2><<<grid_for(a.n, bsz(t.block_push)), bsz(t.block_push), 0, s>>>(t, a);
 }
 
 int64_t scan_tiles_needed(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
