@@ -184,7 +184,7 @@ __device__ __forceinline__ void local_coords(const double *x, int64_t n, int64_t
 
 // Per leaf: partial sums of the 2^d shape functions over the leaf's particles
 // in bucket order (PIDT: the leaf's 2^d sub-buckets in corner order).
-template <bool kSplit>
+template <bool kSplit, int D>
 __global__ void k_leaf_partials(DevTree t, const int32_t *__restrict__ start, const void *pos, int64_t n,
                                 void *part_out) {
   int64_t L = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -192,16 +192,16 @@ __global__ void k_leaf_partials(DevTree t, const int32_t *__restrict__ start, co
   int lev;
   int32_t c[3] = {0, 0, 0};
   leaf_info(t, (int32_t)L, &lev, c);
-  const int nc = t.nc, d = t.d;
+  constexpr int nc = 1 << D, d = D;
   const int na = t.scheme == 0 ? 1 : nc;
   if (kSplit) {
     const float *o = (const float *)pos;
-    float acc[8];
+    float acc[nc];
     for (int e = 0; e < nc; ++e) acc[e] = 0.0f;
     for (int a = 0; a < na; ++a) {
       int32_t k = key_of(t, (int32_t)L, a);
       for (int32_t p = start[k]; p < start[k + 1]; ++p) {
-        float tl[3];
+        float tl[d];
         for (int b = 0; b < d; ++b) tl[b] = o[b * n + p];
         for (int e = 0; e < nc; ++e) acc[e] = acc[e] + shape<float>(tl, e, d);
       }
@@ -210,12 +210,12 @@ __global__ void k_leaf_partials(DevTree t, const int32_t *__restrict__ start, co
     for (int e = 0; e < nc; ++e) part[L * nc + e] = acc[e];
   } else {
     const double *x = (const double *)pos;
-    double acc[8];
+    double acc[nc];
     for (int e = 0; e < nc; ++e) acc[e] = 0.0;
     for (int a = 0; a < na; ++a) {
       int32_t k = key_of(t, (int32_t)L, a);
       for (int32_t p = start[k]; p < start[k + 1]; ++p) {
-        double tl[3];
+        double tl[d];
         local_coords(x, n, p, lev, c, d, tl);
         for (int e = 0; e < nc; ++e) acc[e] = acc[e] + shape<double>(tl, e, d);
       }
@@ -1239,9 +1239,11 @@ void launch_vertex_charge(const DevTree &t, bool split, const void *part, void *
 void launch_deposit(const DevTree &t, bool split, const int32_t *start, const void *pos, int64_t n, void *part,
                     void *Q, double *block_sum, double *total, cudaStream_t s) {
   if (split) {
-    { COUNT(1); k_leaf_partials<true><<<grid_for(t.n_leaves, bsz(t.block_leaf)), bsz(t.block_leaf), 0, s>>>(t, start, pos, n, part); }
+    { COUNT(1); if (t.d == 3) k_leaf_partials<true, 3><<<grid_for(t.n_leaves, bsz(t.block_leaf)), bsz(t.block_leaf), 0, s>>>(t, start, pos, n, part);
+      else k_leaf_partials<true, 2><<<grid_for(t.n_leaves, bsz(t.block_leaf)), bsz(t.block_leaf), 0, s>>>(t, start, pos, n, part); }
   } else {
-    { COUNT(1); k_leaf_partials<false><<<grid_for(t.n_leaves, bsz(t.block_leaf)), bsz(t.block_leaf), 0, s>>>(t, start, pos, n, part); }
+    { COUNT(1); if (t.d == 3) k_leaf_partials<false, 3><<<grid_for(t.n_leaves, bsz(t.block_leaf)), bsz(t.block_leaf), 0, s>>>(t, start, pos, n, part);
+      else k_leaf_partials<false, 2><<<grid_for(t.n_leaves, bsz(t.block_leaf)), bsz(t.block_leaf), 0, s>>>(t, start, pos, n, part); }
   }
   launch_vertex_charge(t, split, part, Q, block_sum, total, s);
 }
