@@ -56,6 +56,14 @@ __device__ __forceinline__ void leaf_info(const DevTree &t, int32_t L, int *lev,
   for (int a = 0; a < t.d; ++a) c[a] = t.leaf_coords[(int64_t)L * t.d + a];
 }
 
+// The same with the dimension known at compile time (the loop unrolls).
+template <int D>
+__device__ __forceinline__ void leaf_info_d(const DevTree &t, int32_t L, int *lev, int32_t *c) {
+  *lev = t.leaf_level[L];
+#pragma unroll
+  for (int a = 0; a < D; ++a) c[a] = t.leaf_coords[(int64_t)L * D + a];
+}
+
 __device__ __forceinline__ const InstInfo &inst_of_leaf(const DevTree &t, int32_t L) {
   return t.inst[t.n_inst > 1 ? t.inst_of_leaf[L] : 0];
 }
@@ -191,7 +199,7 @@ __global__ void k_leaf_partials(DevTree t, const int32_t *__restrict__ start, co
   if (L >= t.n_leaves) return;
   int lev;
   int32_t c[3] = {0, 0, 0};
-  leaf_info(t, (int32_t)L, &lev, c);
+  leaf_info_d<D>(t, (int32_t)L, &lev, c);
   constexpr int nc = 1 << D, d = D;
   const int na = t.scheme == 0 ? 1 : nc;
   if (kSplit) {
@@ -481,7 +489,7 @@ __global__ void k_push64(DevTree t, Push64Args a) {
     int32_t L = a.leaf[p];
     int lev;
     int32_t c[3] = {0, 0, 0};
-    leaf_info(t, L, &lev, c);
+    leaf_info_d<D>(t, L, &lev, c);
     double tl[3];
     local_coords(a.x, n, p, lev, c, d, tl);
     double E[3] = {0.0, 0.0, 0.0};
@@ -562,7 +570,7 @@ __global__ void k_push32(DevTree t, Push32Args a) {
     int32_t L = a.leaf[p];
     int lev;
     int32_t c[3] = {0, 0, 0};
-    leaf_info(t, L, &lev, c);
+    leaf_info_d<D>(t, L, &lev, c);
     float o[3] = {0.f, 0.f, 0.f};
     for (int ax = 0; ax < d; ++ax) o[ax] = a.o[ax * n + p];
     float E[3] = {0.f, 0.f, 0.f};
