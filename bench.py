@@ -572,6 +572,8 @@ def main():
     ap.add_argument("--workload", default="langmuir3d",
                     choices=["langmuir3d", "langmuir3d-small", "langmuir2d", "batch256", "twostream3d"])
     ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--profile-range", action="store_true",
+                    help="start and stop the CUDA profiler around the timed steps (for ncu --profile-from-start off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run")
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
@@ -657,11 +659,15 @@ def main():
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
+        if args.profile_range:   # the profiler captures exactly the timed steps (ncu --profile-from-start off)
+            torch.cuda.profiler.start()
         ev0.record(stream)
         for _ in range(args.steps):
             g.step_fixed_field(w.dt)
         ev1.record(stream)
         torch.cuda.synchronize()
+        if args.profile_range:
+            torch.cuda.profiler.stop()
         barrier()
     ms = ev0.elapsed_time(ev1)
     phases = g.phase_times()
