@@ -794,22 +794,15 @@ __global__ void k_compact_movers(const uint32_t *mover_words, const int32_t *blo
   if (p < n && ((word >> lane) & 1u)) movers[off + __popc(word & ((1u << lane) - 1u))] = (int32_t)p;
 }
 
-// Movers of a warp with the same key take consecutive slots (in storage
-// order) with one atomic.
 __global__ void k_mover_slots(const int32_t *movers, const int32_t *n_movers, const int32_t *keyn,
                               const int32_t *new_start, const int32_t *n_stay, int32_t *cursor,
                               int32_t *perm) {
-  const int32_t m = blockIdx.x * blockDim.x + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  const bool act = m < *n_movers;
-  const int32_t p = act ? movers[m] : 0;
-  const int32_t k = act ? keyn[p] : -1;
-  const unsigned peers = __match_any_sync(0xffffffffu, k);
-  const int leader = __ffs(peers) - 1;
-  int32_t base = 0;
-  if (act && lane == leader) base = atomicAdd(&cursor[k], __popc(peers));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (act) perm[new_start[k] + n_stay[k] + base + __popc(peers & ((1u << lane) - 1u))] = p;
+  int32_t m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= *n_movers) return;
+  int32_t p = movers[m];
+  int32_t k = keyn[p];
+  int32_t slot = atomicAdd(&cursor[k], 1);
+  perm[new_start[k] + n_stay[k] + slot] = p;
 }
 
 // The movers of every bucket in storage order (undoes the atomic slot order).
