@@ -438,7 +438,7 @@ def run_twostream(args):
     import torch
     from paper_1508_02435_gb300 import pic
 
-    w = W.two_stream()
+    w = W.two_stream(n=getattr(args, "twostream_particles", 200_000_000))
     n = w.n
     stream = torch.cuda.Stream()
     g = pic.Pic(3, w.flags, w.x, w.v, scheme=pic.PIDT, precision=pic.FP32_SPLIT, q=w.q, qm=w.qm, ion=w.ion,
@@ -456,11 +456,15 @@ def run_twostream(args):
     g.sync()
     g.profile(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if getattr(args, "profile_range", False):
+        torch.cuda.profiler.start()
     e0.record(stream)
     for _ in range(args.steps):
         g.step_fixed_field(w.dt)
     e1.record(stream)
     torch.cuda.synchronize()
+    if getattr(args, "profile_range", False):
+        torch.cuda.profiler.stop()
     ms = e0.elapsed_time(e1) / args.steps
     phases = g.phase_times()
     if g.stats().error:
@@ -572,6 +576,8 @@ def main():
     ap.add_argument("--workload", default="langmuir3d",
                     choices=["langmuir3d", "langmuir3d-small", "langmuir2d", "batch256", "twostream3d"])
     ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--twostream-particles", type=int, default=200_000_000,
+                    help="particles of the 3D two-stream configuration (smaller for profiling)")
     ap.add_argument("--profile-range", action="store_true",
                     help="start and stop the CUDA profiler around the timed steps (for ncu --profile-from-start off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
