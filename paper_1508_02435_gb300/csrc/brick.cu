@@ -40,6 +40,7 @@ constexpr int kSelfDir = 13;         // (0, 0, 0)
 constexpr uint16_t kStayBit = 0x8000;
 constexpr uint16_t kMoverCode = 0;   // leaf code flags of an arrival from another leaf
 constexpr int kPushThreads = 512;
+constexpr unsigned kFallbackBlocks = 608;  // blocks of the global-memory fallback kernels (4 per SM)
 constexpr int kPullThreads = 256;
 
 // Compile-time brick shape: B = 9 leaves per axis (two levels).
@@ -703,14 +704,15 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
 // K1 for bricks over 2 kHalfCap particles: the same arithmetic (push_core),
 // particles and field read from global memory, one thread per particle.
 template <int D>
-__global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeom g, BrickPushArgs a) {
+__device__ __forceinline__ void brick_push_fallback(const DevTree &t, const BrickGeom &g, const BrickPushArgs &a,
+                                                    const int32_t b) {
   using K = BK<D>;
   __shared__ int32_t ls[K::LB + 1];
   __shared__ uint32_t dec[K::LB];
   __shared__ float Eb[D * K::NVB];
   __shared__ int32_t s_movers;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int32_t b = blockIdx.x, L0 = b * K::LB;
+  const int32_t L0 = b * K::LB;
   const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nb = pe - ps;
   if (nb <= 2 * kHalfCap) return;  // the shared-memory kernel took this brick
   int32_t origin[3] = {0, 0, 0}, bc[3] = {0, 0, 0};
@@ -758,6 +760,16 @@ __global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeo
   if (lane == 0) atomicAdd(&s_movers, movers);
   __syncthreads();
   if (tid == 0 && s_movers) atomicAdd(a.n_movers, s_movers);
+}
+
+// Bricks too large for the shared-memory kernel, from global memory; the
+// blocks take bricks in turn and pass over the others at once.
+template <int D>
+__global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeom g, BrickPushArgs a) {
+  for (int32_t b = blockIdx.x; b < g.n_bricks; b += gridDim.x) {
+    brick_push_fallback<D>(t, g, a, b);
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1084,7 +1096,8 @@ constexpr int kPullSmallLeaf = 32;  // leaves up to this many arrivals: one thre
 constexpr int kPullChunk = 2048;    // (key, index) pairs of a crowded leaf sorted at once in shared memory
 
 template <int D>
-__global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeom g, BrickPullArgs a) {
+__device__ __forceinline__ void brick_pull_fallback(const DevTree &t, const BrickGeom &g, const BrickPullArgs &a,
+                                                    const int32_t u) {
   using K = BK<D>;
   __shared__ uint32_t sk[kPullChunk];
   __shared__ int32_t sv[kPullChunk];
@@ -1094,7 +1107,7 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
   __shared__ int32_t s_max;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, nw = blockDim.x >> 5;
   const BrickStage &st = a.st;
-  const int32_t u = blockIdx.x, b = u >> 1;
+  const int32_t b = u >> 1;
   const int lf0 = (u & 1) ? K::LH : 0, nlf = (u & 1) ? K::LB - K::LH : K::LH;
   const int32_t L0 = b * K::LB + lf0;
   const int64_t n = a.n;
@@ -1220,6 +1233,16 @@ __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeo
   }
 }
 
+// Destination units whose arrivals overflow their staging area, from global
+// memory; the blocks take units in turn and pass over the others at once.
+template <int D>
+__global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeom g, BrickPullArgs a) {
+  for (int32_t u = blockIdx.x; u < 2 * g.n_bricks; u += gridDim.x) {
+    brick_pull_fallback<D>(t, g, a, u);
+    __syncthreads();
+  }
+}
+
 __global__ void k_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t *leaf) {
   int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= n_leaves) return;
@@ -1242,8 +1265,9 @@ void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs
     if (al) k_brick_push_st<2, true><<<2 * nb, kHThreads, push_st_smem<2>(), s>>>(t, g, pa);
     else k_brick_push_st<2, false><<<2 * nb, kHThreads, push_st_smem<2>(), s>>>(t, g, pa);
   }
-  if (g.d == 3) k_brick_push<3><<<nb, kPushThreads, 0, s>>>(t, g, pa);
-  else k_brick_push<2><<<nb, kPushThreads, 0, s>>>(t, g, pa);
+  const unsigned nf = std::min(nb, kFallbackBlocks);  // the fallback visits every brick with fewer blocks
+  if (g.d == 3) k_brick_push<3><<<nf, kPushThreads, 0, s>>>(t, g, pa);
+  else k_brick_push<2><<<nf, kPushThreads, 0, s>>>(t, g, pa);
   count_launches(2);
 }
 
@@ -1259,10 +1283,10 @@ void launch_brick_pull(const DevTree &t, const BrickGeom &g, const BrickPullArgs
   launch_exclusive_scan(qa.tot_w, nu, qa.bstart_w, tile_sums, scratch_total, s);
   if (g.d == 3) {
     k_brick_pull_st<3><<<(unsigned)nu, kStThreads, pull_st_smem<3>(), s>>>(t, g, qa);
-    k_brick_pull<3><<<(unsigned)nu, kPullThreads, 0, s>>>(t, g, qa);
+    k_brick_pull<3><<<std::min((unsigned)nu, kFallbackBlocks), kPullThreads, 0, s>>>(t, g, qa);
   } else {
     k_brick_pull_st<2><<<(unsigned)nu, kStThreads, pull_st_smem<2>(), s>>>(t, g, qa);
-    k_brick_pull<2><<<(unsigned)nu, kPullThreads, 0, s>>>(t, g, qa);
+    k_brick_pull<2><<<std::min((unsigned)nu, kFallbackBlocks), kPullThreads, 0, s>>>(t, g, qa);
   }
   count_launches(5);  // overflow count, overflow scatter, totals, two pull kernels (the scans count themselves)
 }
