@@ -559,7 +559,7 @@ __global__ void k_push64(DevTree t, Push64Args a) {
 }
 
 template <int D>
-__global__ void k_push32(DevTree t, Push32Args a) {
+__global__ void __launch_bounds__(512, 3) k_push32(DevTree t, Push32Args a) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool act = p < a.n;
   int32_t knew = 0;
