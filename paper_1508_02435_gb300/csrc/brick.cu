@@ -329,10 +329,13 @@ __device__ __forceinline__ void stage_put(const BrickStage &st, int32_t dest, in
                                           int32_t *err) {
   if (slot < st.cap) {
     const uint32_t at = (uint32_t)dest * (uint32_t)st.cap + (uint32_t)slot;  // < 2^31 (checked at set-up)
-#pragma unroll
-    for (int ax = 0; ax < D; ++ax) {
-      st.orow[ax][at] = on[ax];
-      st.vrow[ax][at] = vn[ax];
+    float *r = st.rec + (size_t)at * (2 * D);  // 8-byte aligned (3D) / 16-byte aligned (2D)
+    if constexpr (D == 3) {
+      reinterpret_cast<float2 *>(r)[0] = make_float2(on[0], on[1]);
+      reinterpret_cast<float2 *>(r)[1] = make_float2(on[2], vn[0]);
+      reinterpret_cast<float2 *>(r)[2] = make_float2(vn[1], vn[2]);
+    } else {
+      *reinterpret_cast<float4 *>(r) = make_float4(on[0], on[1], vn[0], vn[1]);
     }
     st.code[at] = code;
     st.key[at] = key;
@@ -871,9 +874,8 @@ template <int D>
 __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, BrickGeom g, BrickPullArgs a) {
   using K = BK<D>;
   extern __shared__ __align__(128) float smf[];
-  float *so = smf;                                   // D rows of kStCap offsets (arrival order)
-  float *sv = so + D * kStCap;                       // D rows of velocities
-  uint32_t *key = (uint32_t *)(sv + D * kStCap);     // canonical keys
+  float *srec = smf;                                 // kStCap records of 2 D floats (arrival order)
+  uint32_t *key = (uint32_t *)(srec + 2 * D * kStCap);  // canonical keys
   uint16_t *code = (uint16_t *)(key + kStCap);       // local leaf | stayer bit; later the final position
   uint16_t *map = code + kStCap;                     // bucket position -> arrival
   __shared__ int32_t cnt[K::LH + 1];
@@ -903,11 +905,9 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
       mbar_expect_tx(&s_bar, rb + cb);
       bulk_g2s(key, st.key + at, rb, &s_bar);
       bulk_g2s(code, st.code + at, cb, &s_bar);
-      mbar_expect_tx(&s_bar2, 2u * D * rb);
-      for (int ax = 0; ax < D; ++ax) {
-        bulk_g2s(so + ax * kStCap, st.o + ax * st.row + at, rb, &s_bar2);
-        bulk_g2s(sv + ax * kStCap, st.v + ax * st.row + at, rb, &s_bar2);
-      }
+      const uint32_t sb = (uint32_t)((nin * 8 * D + 15) & ~15);
+      mbar_expect_tx(&s_bar2, sb);
+      bulk_g2s(srec, st.rec + at * (2 * D), sb, &s_bar2);
     }
   }
   for (int i = tid; i <= nlf; i += blockDim.x) cnt[i] = 0;
@@ -1027,11 +1027,16 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
       gV[ax] = a.v + ax * n + bstart;
     }
     for (int32_t j = tid; j < nin; j += blockDim.x) {
-      const int32_t i = map[j];
-#pragma unroll
-      for (int ax = 0; ax < D; ++ax) {
-        gO[ax][j] = so[ax * kStCap + i];
-        gV[ax][j] = sv[ax * kStCap + i];
+      const float *r = srec + 2 * D * map[j];
+      if constexpr (D == 3) {
+        const float2 r0 = reinterpret_cast<const float2 *>(r)[0], r1 = reinterpret_cast<const float2 *>(r)[1],
+                     r2 = reinterpret_cast<const float2 *>(r)[2];
+        gO[0][j] = r0.x; gO[1][j] = r0.y; gO[2][j] = r1.x;
+        gV[0][j] = r1.y; gV[1][j] = r2.x; gV[2][j] = r2.y;
+      } else {
+        const float4 r0 = *reinterpret_cast<const float4 *>(r);
+        gO[0][j] = r0.x; gO[1][j] = r0.y;
+        gV[0][j] = r0.z; gV[1][j] = r0.w;
       }
     }
     if (a.ids)
@@ -1047,9 +1052,9 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
       const int32_t lo = cnt[l], hi = cnt[l + 1];
       float on[D];
       if (lo < hi) {
-        const int32_t i = map[lo];
+        const float *r = srec + 2 * D * map[lo];
 #pragma unroll
-        for (int ax = 0; ax < D; ++ax) on[ax] = so[ax * kStCap + i];
+        for (int ax = 0; ax < D; ++ax) on[ax] = r[ax];
       }
       for (int32_t j = lo; j < hi; ++j) {
         float o[D], om[D];
@@ -1059,9 +1064,9 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
           om[ax] = 1.0f - o[ax];
         }
         if (j + 1 < hi) {
-          const int32_t i = map[j + 1];
+          const float *r = srec + 2 * D * map[j + 1];
 #pragma unroll
-          for (int ax = 0; ax < D; ++ax) on[ax] = so[ax * kStCap + i];
+          for (int ax = 0; ax < D; ++ax) on[ax] = r[ax];
         }
         // corner weights (f0 * f1) [* f2] as in the push, two corners per
         // paired multiply, then summed per corner in bucket order
@@ -1190,9 +1195,10 @@ __device__ __forceinline__ void brick_pull_fallback(const DevTree &t, const Bric
     const int32_t dst = bstart + j;
     if (r < nf) {
 #pragma unroll
+      const float *rr = st.rec + (at + r) * (2 * D);
       for (int ax = 0; ax < D; ++ax) {
-        a.o[ax * n + dst] = st.o[ax * st.row + at + r];
-        a.v[ax * n + dst] = st.v[ax * st.row + at + r];
+        a.o[ax * n + dst] = rr[ax];
+        a.v[ax * n + dst] = rr[D + ax];
       }
       if (a.ids) a.ids[dst] = st.id[at + r];
     } else {

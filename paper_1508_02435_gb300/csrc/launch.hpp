@@ -79,9 +79,8 @@ struct BrickGeom {
 // overflow list.
 struct BrickStage {
   int32_t cap;                   // slots per destination unit (a multiple of 8)
-  int64_t row;                   // elements per row (2 n_bricks cap, padded)
-  float *o, *v;                  // D rows each
-  float *orow[3], *vrow[3];      // the rows' starts (o + ax row, v + ax row)
+  int64_t row;                   // slots in all (2 n_bricks cap, padded)
+  float *rec;                    // [row][2 D] one record per slot: the D offsets, then the D velocities
   uint16_t *code;                // destination local leaf | stayer bit
   uint32_t *key;                 // moved << 31 | storage index before the step (canonical order)
   int32_t *id;                   // particle ids (tracked ids only)

@@ -724,9 +724,10 @@ int setup_brick(pic_t h) {
   int rc;
   if ((rc = upload(h, bb, &g.decodeL, dec))) return rc;
   const int64_t n = h->n, nu = 2 * g.n_bricks;  // destination units: half bricks
-  // staging rows: cap slots per destination unit (a multiple of 8, so every
-  // unit's area starts on a 16-byte boundary in each row), plus a tail for the
-  // bulk copies of the last unit, which read whole 16-byte units
+  // staging: cap slots per destination unit (a multiple of 8, so every unit's
+  // area starts on a 16-byte boundary in the record array and in the code and
+  // key rows), plus a tail for the bulk copies of the last unit, which read
+  // whole 16-byte units
   BrickStage &st = h->stage;
   st = BrickStage{};
   st.cap = brick_stage_cap(n, nu);
@@ -734,12 +735,7 @@ int setup_brick(pic_t h) {
   // a tree with many more bricks than particles would spend more memory on
   // empty staging areas than on the particles: the generic path serves it
   if (nu * st.cap > 16 * n + (int64_t(1) << 24) || st.row >= (int64_t(1) << 31)) return PIC_OK;
-  if ((rc = dalloc(h, bb, &st.o, st.row * t.d))) return rc;
-  if ((rc = dalloc(h, bb, &st.v, st.row * t.d))) return rc;
-  for (int ax = 0; ax < 3; ++ax) {
-    st.orow[ax] = st.o + (ax < t.d ? ax : 0) * st.row;
-    st.vrow[ax] = st.v + (ax < t.d ? ax : 0) * st.row;
-  }
+  if ((rc = dalloc(h, bb, &st.rec, st.row * 2 * t.d))) return rc;
   if ((rc = dalloc(h, bb, &st.code, st.row))) return rc;
   if ((rc = dalloc(h, bb, &st.key, st.row))) return rc;
   if (h->cfg.track_ids && (rc = dalloc(h, bb, &st.id, st.row))) return rc;
