@@ -535,9 +535,14 @@ __device__ __forceinline__ void push_half_warp(const DevTree &t, const BrickGeom
   }
   // the warp reserves its runs in the destination units' staging areas (one
   // atomic per unit it sends to; the count becomes the run's first slot)
-  for (int us = lane; us < 54; us += 32) {
-    const int32_t c = wc[us];
-    if (c > 0) wc[us] = atomicAdd(&a.st.fill[2 * hv.nbr[us >> 1] + (us & 1)], c);
+  {  // both of a lane's atomics in flight at once
+    const int us1 = lane + 32;
+    const int32_t c0 = wc[lane], c1 = us1 < 54 ? wc[us1] : 0;
+    int32_t r0 = 0, r1 = 0;
+    if (c0 > 0) r0 = atomicAdd(&a.st.fill[2 * hv.nbr[lane >> 1] + (lane & 1)], c0);
+    if (c1 > 0) r1 = atomicAdd(&a.st.fill[2 * hv.nbr[us1 >> 1] + (us1 & 1)], c1);
+    if (c0 > 0) wc[lane] = r0;
+    if (c1 > 0) wc[us1] = r1;
   }
   __syncwarp();
   // pass B, the warp's own chunks: every arrival to its reserved slot

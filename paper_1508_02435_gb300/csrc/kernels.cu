@@ -431,13 +431,32 @@ __global__ void k_rekey32(DevTree t, const int32_t *leaf, const float *o, int64_
 // a3 + a4 + a1/a2 + a5: fused gather, push, re-location, key, moved flag
 // ---------------------------------------------------------------------------
 
-// Warp-aggregated bucket count, mover ballot word and per-block mover count.
+// Adds to count[key] the length of every run of equal keys in adjacent
+// active lanes, one atomic per run (particles in bucket order mostly share
+// their new bucket with their neighbours; equal keys apart count as separate
+// runs).  Active lanes are a prefix of the warp or all of it.
+__device__ __forceinline__ void add_runs(int32_t *count, int32_t key, bool act) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int32_t prev = __shfl_up_sync(full, key, 1);
+  const unsigned acts = __ballot_sync(full, act);
+  const bool head = act && (lane == 0 || prev != key);
+  const unsigned heads = __ballot_sync(full, head);
+  if (head) {
+    const unsigned after = ~((2u << lane) - 1u);  // lanes above this one (none for lane 31)
+    const unsigned stop = (heads | ~acts) & after;
+    const int end = stop ? __ffs(stop) - 1 : 32;
+    atomicAdd(&count[key], end - lane);
+  }
+}
+
+// Bucket counts (per run of equal keys), mover ballot word and per-block
+// mover count.
 __device__ __forceinline__ void count_and_ballot(bool act, int32_t knew, bool moved, int32_t *count,
                                                  uint32_t *mover_words, int32_t *block_movers) {
   const unsigned full = 0xffffffffu;
   int lane = threadIdx.x & 31;
-  unsigned peers = __match_any_sync(full, act ? knew : -1);
-  if (act && lane == __ffs(peers) - 1) atomicAdd(&count[knew], __popc(peers));
+  add_runs(count, knew, act);
   unsigned mv = __ballot_sync(full, act && moved);
   int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (lane == 0) mover_words[gw] = mv;
@@ -1008,8 +1027,7 @@ __global__ void k_level_count(const uint32_t *key, int64_t n, uint32_t div, int3
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = p < n;
   const uint32_t c = act ? key[p] / div : 0xffffffffu;
-  const unsigned peers = __match_any_sync(0xffffffffu, c);
-  if (act && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&count[c], __popc(peers));
+  add_runs(count, (int32_t)c, act);
 }
 
 __global__ void k_threshold_bits(const int32_t *count, int64_t ncells, int64_t ppc, uint32_t *bits) {
