@@ -1199,8 +1199,8 @@ __device__ __forceinline__ void brick_pull_fallback(const DevTree &t, const Bric
     const int32_t r = a.fb_idx[bstart + j];
     const int32_t dst = bstart + j;
     if (r < nf) {
-#pragma unroll
       const float *rr = st.rec + (at + r) * (2 * D);
+#pragma unroll
       for (int ax = 0; ax < D; ++ax) {
         a.o[ax * n + dst] = rr[ax];
         a.v[ax * n + dst] = rr[D + ax];

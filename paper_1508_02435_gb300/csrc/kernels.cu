@@ -529,6 +529,7 @@ __global__ void k_push64(DevTree t, Push64Args a) {
       }
     }
     uint32_t Q[3] = {0u, 0u, 0u};
+    double x0n = 0.0, x1n = 0.0, x2n = 0.0, v0n = 0.0, v1n = 0.0, v2n = 0.0;  // record path
     bool bad = false;
     for (int ax = 0; ax < d; ++ax) {
       double vn = a.E ? a.v[ax * n + p] + a.qmdt * E[ax] : a.v[ax * n + p];
@@ -542,8 +543,14 @@ __global__ void k_push64(DevTree t, Push64Args a) {
         xn = wrap01(y);
       }
       if (!isfinite(vn) || !isfinite(xn)) { bad = true; xn = 0.0; }
-      a.tv[ax * n + p] = vn;
-      a.tx[ax * n + p] = xn;
+      if (a.rec) {
+        if (ax == 0) { x0n = xn; v0n = vn; }
+        if (ax == 1) { x1n = xn; v1n = vn; }
+        if (ax == 2) { x2n = xn; v2n = vn; }
+      } else {
+        a.tv[ax * n + p] = vn;
+        a.tx[ax * n + p] = xn;
+      }
       Q[ax] = quantise(xn);
     }
     if (a.flops > 0) artificial_flops<double>(tl[0], a.flops, a.err);
@@ -571,8 +578,16 @@ __global__ void k_push64(DevTree t, Push64Args a) {
     knew = key_of(t, L2, pidt_corner_q(Q, lev2, d));
     int32_t kold = t.scheme == 0 ? L : a.key[p];
     moved = knew != kold;
-    a.tleaf[p] = L2;
-    if (t.scheme != 0) a.keyn[p] = knew;  // PIT: the key array is the leaf array
+    if (a.rec) {  // one 64-byte record per particle: the re-bin gathers it whole
+      double2 *r = a.rec + 4 * p;
+      r[0] = make_double2(x0n, x1n);
+      r[1] = make_double2(x2n, v0n);
+      r[2] = make_double2(v1n, v2n);
+      r[3] = make_double2(__longlong_as_double((long long)(((uint64_t)(uint32_t)knew << 32) | (uint32_t)L2)), 0.0);
+    } else {
+      a.tleaf[p] = L2;
+    }
+    a.keyn[p] = knew;  // PIT: the leaf (the key array is the leaf array)
   }
   count_and_ballot(act, knew, moved, a.count, a.mover_words, a.block_movers);
 }
@@ -620,7 +635,7 @@ __global__ void __launch_bounds__(512, 3) k_push32(DevTree t, Push32Args a) {
     const int32_t per = (int32_t)c_pow3[lev];
     const float sl = a.sl[lev];
     int32_t I[3] = {0, 0, 0};
-    float f[3] = {0.f, 0.f, 0.f};
+    float f[3] = {0.f, 0.f, 0.f}, vnew[3] = {0.f, 0.f, 0.f};
     bool bad = false;
     const bool field = a.E || a.Ec;
     for (int ax = 0; ax < d; ++ax) {
@@ -665,7 +680,8 @@ __global__ void __launch_bounds__(512, 3) k_push32(DevTree t, Push32Args a) {
         }
       }
       I[ax] = cc;
-      a.tv[ax * n + p] = vn;
+      if (a.rec) vnew[ax] = vn;
+      else a.tv[ax * n + p] = vn;
     }
     if (a.flops > 0) artificial_flops<float>(o[0], a.flops, a.err);
     if (bad) atomicOr(a.err, 1);
@@ -686,12 +702,17 @@ __global__ void __launch_bounds__(512, 3) k_push32(DevTree t, Push32Args a) {
     } else {
       L2 = descend_split(t.tab, d, lev, I, f, o2, &lev2, Ins.tab_root);
     }
-    for (int ax = 0; ax < d; ++ax) a.to[ax * n + p] = o2[ax];
     knew = key_of(t, L2, pidt_corner_o(o2, d));
     int32_t kold = t.scheme == 0 ? L : a.key[p];
     moved = knew != kold;
-    a.tleaf[p] = L2;
-    if (t.scheme != 0) a.keyn[p] = knew;  // PIT: the key array is the leaf array
+    if (a.rec) {  // one 32-byte record per particle: the re-bin gathers it whole
+      a.rec[2 * p] = make_float4(o2[0], o2[1], o2[2], vnew[0]);
+      a.rec[2 * p + 1] = make_float4(vnew[1], vnew[2], __int_as_float(L2), __int_as_float(knew));
+    } else {
+      for (int ax = 0; ax < d; ++ax) a.to[ax * n + p] = o2[ax];
+      a.tleaf[p] = L2;
+    }
+    a.keyn[p] = knew;  // PIT: the leaf (the key array is the leaf array)
   }
   count_and_ballot(act, knew, moved, a.count, a.mover_words, a.block_movers);
 }
@@ -904,6 +925,49 @@ __global__ void k_gather_state(const int32_t *perm, int64_t n, int d, const T *x
   for (int a = 0; a < d; ++a) v2[a * n + p] = v[a * n + i];
   leaf2[p] = leaf[i];
   if (key) key2[p] = key[i];
+  if (ids) ids2[p] = ids[i];
+}
+
+// The pushed-state records in bucket order (two or four 16-byte loads per
+// particle instead of one scattered 4- or 8-byte load per array).
+__global__ void k_gather_rec32(const int32_t *perm, int64_t n, int d, const float4 *rec, float *x2, float *v2,
+                               int32_t *leaf2, int32_t *key2, const int32_t *ids, int32_t *ids2) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int32_t i = perm[p];
+  const float4 r0 = rec[2 * (int64_t)i], r1 = rec[2 * (int64_t)i + 1];
+  x2[p] = r0.x;
+  x2[n + p] = r0.y;
+  if (d == 3) {
+    x2[2 * n + p] = r0.z;
+    v2[p] = r0.w;
+    v2[n + p] = r1.x;
+    v2[2 * n + p] = r1.y;
+  } else {
+    v2[p] = r0.w;
+    v2[n + p] = r1.x;
+  }
+  leaf2[p] = __float_as_int(r1.z);
+  if (key2) key2[p] = __float_as_int(r1.w);
+  if (ids) ids2[p] = ids[i];
+}
+
+__global__ void k_gather_rec64(const int32_t *perm, int64_t n, int d, const double2 *rec, double *x2, double *v2,
+                               int32_t *leaf2, int32_t *key2, const int32_t *ids, int32_t *ids2) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int32_t i = perm[p];
+  const double2 *r = rec + 4 * (int64_t)i;
+  const double2 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3];
+  x2[p] = r0.x;
+  x2[n + p] = r0.y;
+  if (d == 3) x2[2 * n + p] = r1.x;
+  v2[p] = r1.y;
+  v2[n + p] = r2.x;
+  if (d == 3) v2[2 * n + p] = r2.y;
+  const uint64_t lk = (uint64_t)__double_as_longlong(r3.x);
+  leaf2[p] = (int32_t)(uint32_t)lk;
+  if (key2) key2[p] = (int32_t)(uint32_t)(lk >> 32);
   if (ids) ids2[p] = ids[i];
 }
 
@@ -1387,6 +1451,18 @@ void launch_gather_state(bool split, const int32_t *perm, int64_t n, int d, cons
     k_gather_state<double><<<grid_for(n), kBlock, 0, s>>>(perm, n, d, (const double *)x, (double *)x2,
                                                            (const double *)v, (double *)v2, leaf, leaf2, key, key2,
                                                            ids, ids2);
+}
+
+void launch_gather_records(bool split, const int32_t *perm, int64_t n, int d, const void *rec, void *x2, void *v2,
+                           int32_t *leaf2, int32_t *key2, const int32_t *ids, int32_t *ids2, cudaStream_t s) {
+  if (n <= 0) return;
+  COUNT(1);
+  if (split)
+    k_gather_rec32<<<grid_for(n), kBlock, 0, s>>>(perm, n, d, (const float4 *)rec, (float *)x2, (float *)v2, leaf2,
+                                                   key2, ids, ids2);
+  else
+    k_gather_rec64<<<grid_for(n), kBlock, 0, s>>>(perm, n, d, (const double2 *)rec, (double *)x2, (double *)v2,
+                                                   leaf2, key2, ids, ids2);
 }
 
 void launch_gather_f64(const int32_t *perm, int64_t n, int d, const double *src, double *dst, cudaStream_t s) {

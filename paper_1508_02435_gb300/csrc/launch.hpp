@@ -13,8 +13,9 @@ struct Push64Args {
   int64_t n;
   const double *x, *v;          // current state, bucket-sorted
   const int32_t *leaf, *key;    // key used by PIDT only
-  double *tx, *tv;              // pushed state, same index
-  int32_t *tleaf, *keyn;
+  double2 *rec;                 // [n][4] pushed state: x0 x1 | x2 v0 | v1 v2 | (leaf, key as bits), 0, or NULL:
+  double *tx, *tv;              // the pushed state in rows [d][n] and tleaf
+  int32_t *tleaf, *keyn;        // keyn: new key per particle (PIT: the leaf)
   const double *E;              // [d][n_vert]; NULL: no field (the particle-handling move, no kick)
   double qmdt, dt;
   int32_t *count;               // per key, zeroed before the launch
@@ -29,8 +30,9 @@ struct Push32Args {
   int64_t n;
   const float *o, *v;
   const int32_t *leaf, *key;
-  float *to, *tv;
-  int32_t *tleaf, *keyn;
+  float4 *rec;                  // [n][2] pushed state: o0 o1 o2 v0 | v1 v2 leaf key (leaf, key as bits), or NULL:
+  float *to, *tv;               // the pushed state in rows [d][n] and tleaf
+  int32_t *tleaf, *keyn;        // keyn: new key per particle (PIT: the leaf)
   const float *E;               // NULL (and Ec NULL): no field (the particle-handling move, no kick)
   const float4 *Ec;             // field at every leaf corner [leaf][corner] (adaptive trees), or NULL
   float qmdt;
@@ -195,6 +197,10 @@ void launch_exclusive_scan(const int32_t *in, int64_t n, int32_t *out, int32_t *
 void launch_rebin(const RebinArgs &r, cudaStream_t s);
 // dst[p] = src[perm[p]] for positions, velocities ([d][n]), leaves and,
 // where not NULL, keys and ids, in one kernel (split: float, else double).
+// Bucket order from the pushed-state records: x2/v2 [d][n] rows, leaf2, and
+// key2 unless NULL (PIT), ids2 from ids unless NULL.
+void launch_gather_records(bool split, const int32_t *perm, int64_t n, int d, const void *rec, void *x2, void *v2,
+                           int32_t *leaf2, int32_t *key2, const int32_t *ids, int32_t *ids2, cudaStream_t s);
 void launch_gather_state(bool split, const int32_t *perm, int64_t n, int d, const void *x, void *x2, const void *v,
                          void *v2, const int32_t *leaf, int32_t *leaf2, const int32_t *key, int32_t *key2,
                          const int32_t *ids, int32_t *ids2, cudaStream_t s);

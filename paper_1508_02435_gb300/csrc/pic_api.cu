@@ -72,6 +72,7 @@ struct pic_s {
 
   // particle state: [0] current (bucket-sorted), [1] pushed (same index)
   void *pos[2] = {nullptr, nullptr};  // x (double) or o (float), [d][n]
+  void *prec = nullptr;               // 3D: pushed-state records of the generic step, 32 (split) or 64 bytes each
   void *vel[2] = {nullptr, nullptr};
   int32_t *leaf[2] = {nullptr, nullptr};
   int32_t *key[2] = {nullptr, nullptr};  // [1] doubles as the new key
@@ -577,6 +578,12 @@ int alloc_particles(pic_t h) {
     }
     if ((rc = dalloc(h, sb, &h->ids[s], n))) return rc;
   }
+  h->prec = nullptr;
+  if (d == 3) {  // 3D: eight arrays per particle, gathered as one record (2D keeps the rows)
+    char *p;
+    if ((rc = dalloc(h, sb, &p, (h->split ? 32 : 64) * n))) return rc;
+    h->prec = p;
+  }
   if ((rc = dalloc(h, sb, &h->perm, n))) return rc;
   if ((rc = dalloc(h, sb, &h->movers, n))) return rc;
   if ((rc = dalloc(h, sb, &h->block_movers, nblk))) return rc;
@@ -844,9 +851,10 @@ int brick_push_and_rebin(pic_t h, double dt) {
   return PIC_OK;
 }
 
-// Stable re-bin of the pushed state [1] into the current state [0].
+// Stable re-bin of the pushed state into the current state [0]: from the
+// records of the generic push (records) or from the rows [1] (fresh state).
 // old_start == NULL: fresh particles, every one counted as a mover.
-int rebin_and_gather(pic_t h, const int32_t *old_start) {
+int rebin_and_gather(pic_t h, const int32_t *old_start, bool records = false) {
   cudaStream_t s = h->stream;
   const int64_t n = h->n;
   RebinArgs r{};
@@ -873,7 +881,12 @@ int rebin_and_gather(pic_t h, const int32_t *old_start) {
   }
   PhaseScope ps(h, PIC_PHASE_PERMUTE);
   const int d = h->d;
-  if (h->scheme == PIC_PIT) {
+  if (records) {  // the pushed state, one record per particle
+    launch_gather_records(h->split, h->perm, n, d, h->prec, h->pos[0], h->vel[0], h->leaf[0],
+                          h->scheme == PIC_PIT ? nullptr : h->key[0], h->cfg.track_ids ? h->ids[0] : nullptr,
+                          h->cfg.track_ids ? h->ids[1] : nullptr, s);
+    if (h->cfg.track_ids) std::swap(h->ids[0], h->ids[1]);
+  } else if (h->scheme == PIC_PIT) {
     // one pass over the permutation (measured faster for PIT; PIDT's extra
     // key array makes the separate passes faster: 6.1 against 6.7 ms on the
     // 2e8-particle 3D two-stream step)
@@ -888,7 +901,7 @@ int rebin_and_gather(pic_t h, const int32_t *old_start) {
     launch_gather_f64(h->perm, n, d, (const double *)h->pos[1], (double *)h->pos[0], s);
     launch_gather_f64(h->perm, n, d, (const double *)h->vel[1], (double *)h->vel[0], s);
   }
-  if (h->scheme != PIC_PIT) {
+  if (!records && h->scheme != PIC_PIT) {
     launch_gather_i32(h->perm, n, h->leaf[1], h->leaf[0], s);
     launch_gather_i32(h->perm, n, h->key[1], h->key[0], s);
     if (h->cfg.track_ids) {
@@ -983,6 +996,7 @@ int push_and_rebin(pic_t h, double dt, MoveKind mk = MoveKind{}) {
     a.v = (const float *)h->vel[0];
     a.leaf = h->leaf[0];
     a.key = h->key[0];
+    a.rec = (float4 *)h->prec;
     a.to = (float *)h->pos[1];
     a.tv = (float *)h->vel[1];
     a.tleaf = h->leaf[1];
@@ -1012,6 +1026,7 @@ int push_and_rebin(pic_t h, double dt, MoveKind mk = MoveKind{}) {
     a.v = (const double *)h->vel[0];
     a.leaf = h->leaf[0];
     a.key = h->key[0];
+    a.rec = (double2 *)h->prec;
     a.tx = (double *)h->pos[1];
     a.tv = (double *)h->vel[1];
     a.tleaf = h->leaf[1];
@@ -1029,7 +1044,7 @@ int push_and_rebin(pic_t h, double dt, MoveKind mk = MoveKind{}) {
   }
   delete ps;
   CK(cudaGetLastError());
-  return rebin_and_gather(h, h->start_cur);
+  return rebin_and_gather(h, h->start_cur, h->prec != nullptr);
 }
 
 int check_handle(pic_t h) { return h ? PIC_OK : PIC_EINVAL; }
