@@ -41,6 +41,7 @@ constexpr uint16_t kStayBit = 0x8000;
 constexpr uint16_t kMoverCode = 0;   // leaf code flags of an arrival from another leaf
 constexpr int kPushThreads = 512;
 constexpr unsigned kFallbackBlocks = 608;  // blocks of the global-memory fallback kernels (4 per SM)
+constexpr unsigned kPersistBlocks = 304;   // CTAs of K1's shared-memory kernel (2 per SM, each taking half bricks in turn)
 constexpr int kPullThreads = 256;
 
 // Compile-time brick shape: B = 9 leaves per axis (two levels).
@@ -599,8 +600,11 @@ __device__ __forceinline__ int32_t neighbour_brick(const DevTree &t, const Brick
   return (D == 2 && dir_delta(dir, 2) != 0) ? -1 : brick_of_coords<D>(t, sc);
 }
 
-// K1, shared-memory form, one CTA per half brick: its copies land, the leaf
-// map is built, and every warp pushes its share (push_half_warp).
+// K1, shared-memory form: every CTA takes half bricks in turn (a grid of two
+// CTAs per SM); per half brick its copies land, the leaf map is built, and
+// every warp pushes its share (push_half_warp).  The next half brick's leaf
+// offsets are read while the current one is pushed, so its copies go out as
+// soon as the shared memory is free.
 template <int D, bool kAligned>
 __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, BrickGeom g, BrickPushArgs a) {
   using K = BK<D>;
@@ -620,91 +624,119 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
   __shared__ int32_t s_movers;
   __shared__ uint64_t s_bar;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int32_t b = blockIdx.x >> 1, h = blockIdx.x & 1, L0 = b * K::LB;
-  const int32_t ps = a.start[L0], pe = a.start[L0 + K::LB], nbr_n = pe - ps;
-  if (nbr_n > 2 * kHalfCap) return;  // the global-memory kernel takes this brick
-  const int32_t q0 = half_start(nbr_n, h), q1 = h ? nbr_n : half_start(nbr_n, 1), nb = q1 - q0;
-  const int32_t hs = ps + q0;  // storage index of this half's first particle
   const int64_t n = a.n;
-  if (nb == 0) return;  // an empty half: nothing to push
-  HalfView<D> hv;
-  hv.so = so;
-  hv.sv = sv;
-  hv.pos = pos;
-  hv.lslot = lslot;
-  hv.Eb = Eb;
-  hv.dec = dec;
-  hv.rel = rel;
-  hv.nbr = nbr;
-  hv.nb = nb;
-  hv.hs = hs;
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    hv.origin[ax] = ax < D ? t.leaf_coords[(int64_t)L0 * D + ax] : 0;
-    hv.bc[ax] = hv.origin[ax] / K::B;
-  }
+  const int32_t nh = 2 * g.n_bricks;
+  // brick-independent tables, once per CTA
   fill_rel<D>(rel, tid);
-  if (tid >= 128 && tid < 128 + 27) nbr[tid - 128] = neighbour_brick<D>(t, g, hv.bc, tid - 128);
-  // the half's particle rows: one bulk copy per row from the 16-byte boundary
-  // at or below its first particle; row r holds particle q at index off[r] + q
-#pragma unroll
-  for (int r = 0; r < 2 * D; ++r) {
-    const float *src = (r < D ? a.o + r * n : a.v + (r - D) * n) + hs;
-    const int32_t head = (int32_t)(((uintptr_t)src & 15u) >> 2);
-    if (r < D) hv.offO[r] = r * kHS + head;
-    else hv.offV[r - D] = (r - D) * kHS + head;
-  }
-  // the brick's leaf offsets start at the 16-byte boundary at or below L0
-  const int32_t lhead = (int32_t)(((uintptr_t)(a.start + L0) & 15u) >> 2);
-  const int32_t *ls = lsb + lhead;
-  for (int i = tid; i < kW * kUnitSlots; i += blockDim.x) wc[i] = 0;
+  for (int i = tid; i < K::DECW; i += blockDim.x) dec[i] = g.decodeL[i];
+  for (int i = tid; i < kW * kUnitSlots; i += blockDim.x) wc[i] = 0;  // each warp leaves its counts at zero
   if (tid == 0) {
-    // every global -> shared copy is one bulk copy, issued before any is
-    // awaited: the particle rows of the half, the brick's leaf offsets, the
-    // local-leaf decode table and the brick's field (one vector per vertex,
-    // laid out brick by brick when the field was set)
     s_movers = 0;
     mbar_init(&s_bar, 1);
-    uint32_t total = 0, bytes[2 * D];
-    const float *src[2 * D];
-#pragma unroll
-    for (int r = 0; r < 2 * D; ++r) {
-      const float *p = (r < D ? a.o + r * n : a.v + (r - D) * n) + hs;
-      const uintptr_t a0 = (uintptr_t)p & ~(uintptr_t)15;
-      src[r] = (const float *)a0;
-      bytes[r] = (uint32_t)(((uintptr_t)(p + nb) - a0 + 15u) & ~(uintptr_t)15);
-      total += bytes[r];
-    }
-    const int32_t *ls0 = a.start + L0 - lhead;
-    const uint32_t lbytes = (uint32_t)(((lhead + K::LB + 1) * 4 + 15) & ~15);
-    constexpr uint32_t dbytes = K::DECW * 4, ebytes = K::NVB * sizeof(EV);
-    total += lbytes + dbytes + ebytes;
-    mbar_expect_tx(&s_bar, total);
-#pragma unroll
-    for (int r = 0; r < 2 * D; ++r)
-      bulk_g2s(r < D ? so + r * kHS : sv + (r - D) * kHS, src[r], bytes[r], &s_bar);
-    bulk_g2s(lsb, ls0, lbytes, &s_bar);
-    bulk_g2s(dec, g.decodeL, dbytes, &s_bar);
-    bulk_g2s(Eb, (const EV *)a.Ebrick + (int64_t)b * K::NVB, ebytes, &s_bar);
   }
-  __syncthreads();  // the barrier is initialised and armed before anyone waits on it
-  const bool landed = mbar_wait(&s_bar, 0, a.wait_cycles);
-  if (__syncthreads_or(!landed)) {
-    if (!landed) mbar_wait(&s_bar, 0, kWaitCycles);  // let copies in flight land before leaving
-    if (tid == 0) atomicOr(a.err, kErrTimeout);
-    return;
-  }
-  for (int l = tid; l < K::LB; l += blockDim.x) {
-    const int32_t lo = max(ls[l] - hs, 0), hi = min(ls[l + 1] - hs, nb);
-    for (int32_t q = lo; q < hi; ++q) pos[q] = (uint16_t)l;
-  }
-  __syncthreads();
   bool bad = false;
   int movers = 0;
-  push_half_warp<D, kAligned>(t, g, a, hv, w, kW, wc + w * kUnitSlots, bad, movers);
+  unsigned parity = 0;  // phase of s_bar the current half brick's copies complete
+  int32_t hb = blockIdx.x;
+  int32_t ps = 0, pe = 0;
+  if (hb < nh) {
+    ps = a.start[(hb >> 1) * K::LB];
+    pe = a.start[(hb >> 1) * K::LB + K::LB];
+  }
+  __syncthreads();  // tables written, barrier initialised
+  for (; hb < nh; hb += gridDim.x) {
+    const int32_t b = hb >> 1, h = hb & 1, L0 = b * K::LB;
+    const int32_t nbr_n = pe - ps;
+    const int32_t q0 = half_start(nbr_n, h), q1 = h ? nbr_n : half_start(nbr_n, 1), nb = q1 - q0;
+    const int32_t hs = ps + q0;  // storage index of this half's first particle
+    // the next half brick's offsets, read now and used after this one
+    const int32_t hn = hb + (int32_t)gridDim.x;
+    int32_t ps_next = 0, pe_next = 0;
+    if (hn < nh) {
+      ps_next = a.start[(hn >> 1) * K::LB];
+      pe_next = a.start[(hn >> 1) * K::LB + K::LB];
+    }
+    // bricks over 2 kHalfCap particles: the global-memory kernel; empty halves: nothing to push
+    if (nbr_n <= 2 * kHalfCap && nb > 0) {
+      HalfView<D> hv;
+      hv.so = so;
+      hv.sv = sv;
+      hv.pos = pos;
+      hv.lslot = lslot;
+      hv.Eb = Eb;
+      hv.dec = dec;
+      hv.rel = rel;
+      hv.nbr = nbr;
+      hv.nb = nb;
+      hv.hs = hs;
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        hv.origin[ax] = ax < D ? t.leaf_coords[(int64_t)L0 * D + ax] : 0;
+        hv.bc[ax] = hv.origin[ax] / K::B;
+      }
+      if (tid >= 128 && tid < 128 + 27) nbr[tid - 128] = neighbour_brick<D>(t, g, hv.bc, tid - 128);
+      // the half's particle rows: one bulk copy per row from the 16-byte
+      // boundary at or below its first particle; row r holds particle q at
+      // index off[r] + q
+#pragma unroll
+      for (int r = 0; r < 2 * D; ++r) {
+        const float *src = (r < D ? a.o + r * n : a.v + (r - D) * n) + hs;
+        const int32_t head = (int32_t)(((uintptr_t)src & 15u) >> 2);
+        if (r < D) hv.offO[r] = r * kHS + head;
+        else hv.offV[r - D] = (r - D) * kHS + head;
+      }
+      // the brick's leaf offsets start at the 16-byte boundary at or below L0
+      const int32_t lhead = (int32_t)(((uintptr_t)(a.start + L0) & 15u) >> 2);
+      const int32_t *ls = lsb + lhead;
+      if (tid == 0) {
+        // every global -> shared copy of the half brick is one bulk copy,
+        // issued before any is awaited: the particle rows of the half, the
+        // brick's leaf offsets and the brick's field (one vector per vertex,
+        // laid out brick by brick when the field was set).  The shared memory
+        // they overwrite was last read and written by the generic proxy.
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        uint32_t total = 0, bytes[2 * D];
+        const float *src[2 * D];
+#pragma unroll
+        for (int r = 0; r < 2 * D; ++r) {
+          const float *p = (r < D ? a.o + r * n : a.v + (r - D) * n) + hs;
+          const uintptr_t a0 = (uintptr_t)p & ~(uintptr_t)15;
+          src[r] = (const float *)a0;
+          bytes[r] = (uint32_t)(((uintptr_t)(p + nb) - a0 + 15u) & ~(uintptr_t)15);
+          total += bytes[r];
+        }
+        const int32_t *ls0 = a.start + L0 - lhead;
+        const uint32_t lbytes = (uint32_t)(((lhead + K::LB + 1) * 4 + 15) & ~15);
+        constexpr uint32_t ebytes = K::NVB * sizeof(EV);
+        total += lbytes + ebytes;
+        mbar_expect_tx(&s_bar, total);
+#pragma unroll
+        for (int r = 0; r < 2 * D; ++r)
+          bulk_g2s(r < D ? so + r * kHS : sv + (r - D) * kHS, src[r], bytes[r], &s_bar);
+        bulk_g2s(lsb, ls0, lbytes, &s_bar);
+        bulk_g2s(Eb, (const EV *)a.Ebrick + (int64_t)b * K::NVB, ebytes, &s_bar);
+      }
+      const bool landed = mbar_wait(&s_bar, parity, a.wait_cycles);
+      if (__syncthreads_or(!landed)) {
+        if (!landed) mbar_wait(&s_bar, parity, kWaitCycles);  // let copies in flight land before leaving
+        if (tid == 0) atomicOr(a.err, kErrTimeout);
+        return;
+      }
+      parity ^= 1u;
+      for (int l = tid; l < K::LB; l += blockDim.x) {
+        const int32_t lo = max(ls[l] - hs, 0), hi = min(ls[l + 1] - hs, nb);
+        for (int32_t q = lo; q < hi; ++q) pos[q] = (uint16_t)l;
+      }
+      __syncthreads();  // leaf map and neighbour bricks written
+      push_half_warp<D, kAligned>(t, g, a, hv, w, kW, wc + w * kUnitSlots, bad, movers);
+      __syncthreads();  // the shared memory is free for the next half brick's copies
+    }
+    ps = ps_next;
+    pe = pe_next;
+  }
   if (bad) atomicOr(a.err, 1);
   for (int o = 16; o > 0; o >>= 1) movers += __shfl_down_sync(0xffffffffu, movers, o);
-  if (lane == 0) atomicAdd(&s_movers, movers);
+  if (lane == 0 && movers) atomicAdd(&s_movers, movers);
   __syncthreads();
   if (tid == 0 && s_movers) atomicAdd(a.n_movers, s_movers);
 }
@@ -1269,12 +1301,13 @@ void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs
   cudaMemsetAsync(pa.st.ovf_n, 0, sizeof(int32_t), s);
   const unsigned nb = (unsigned)g.n_bricks;
   const bool al = pa.n % 4 == 0;
+  const unsigned np = std::min(2 * nb, kPersistBlocks);
   if (g.d == 3) {
-    if (al) k_brick_push_st<3, true><<<2 * nb, kHThreads, push_st_smem<3>(), s>>>(t, g, pa);
-    else k_brick_push_st<3, false><<<2 * nb, kHThreads, push_st_smem<3>(), s>>>(t, g, pa);
+    if (al) k_brick_push_st<3, true><<<np, kHThreads, push_st_smem<3>(), s>>>(t, g, pa);
+    else k_brick_push_st<3, false><<<np, kHThreads, push_st_smem<3>(), s>>>(t, g, pa);
   } else {
-    if (al) k_brick_push_st<2, true><<<2 * nb, kHThreads, push_st_smem<2>(), s>>>(t, g, pa);
-    else k_brick_push_st<2, false><<<2 * nb, kHThreads, push_st_smem<2>(), s>>>(t, g, pa);
+    if (al) k_brick_push_st<2, true><<<np, kHThreads, push_st_smem<2>(), s>>>(t, g, pa);
+    else k_brick_push_st<2, false><<<np, kHThreads, push_st_smem<2>(), s>>>(t, g, pa);
   }
   const unsigned nf = std::min(nb, kFallbackBlocks);  // the fallback visits every brick with fewer blocks
   if (g.d == 3) k_brick_push<3><<<nf, kPushThreads, 0, s>>>(t, g, pa);
