@@ -986,6 +986,7 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
     if (run) atomicAdd(&cnt[leaf], run);
   }
   if (__syncthreads_or(badc)) {  // a staged code names no leaf of the unit
+    if (nin > 0) mbar_wait(&s_bar2, 0, kWaitCycles);  // let the state copy land before leaving
     if (tid == 0) atomicOr(a.err, kErrCode);
     return;
   }
