@@ -656,7 +656,9 @@ __global__ void __launch_bounds__(kHThreads, 2) k_brick_push_st(DevTree t, Brick
       ps_next = a.start[(hn >> 1) * K::LB];
       pe_next = a.start[(hn >> 1) * K::LB + K::LB];
     }
-    // bricks over 2 kHalfCap particles: the global-memory kernel; empty halves: nothing to push
+    // bricks over 2 kHalfCap particles: listed for the global-memory kernel;
+    // empty halves: nothing to push
+    if (nbr_n > 2 * kHalfCap && h == 0 && tid == 0) a.st.over_bricks[atomicAdd(&a.st.over[0], 1)] = b;
     if (nbr_n <= 2 * kHalfCap && nb > 0) {
       HalfView<D> hv;
       hv.so = so;
@@ -802,12 +804,13 @@ __device__ __forceinline__ void brick_push_fallback(const DevTree &t, const Bric
   if (tid == 0 && s_movers) atomicAdd(a.n_movers, s_movers);
 }
 
-// Bricks too large for the shared-memory kernel, from global memory; the
-// blocks take bricks in turn and pass over the others at once.
+// Bricks too large for the shared-memory kernel (listed by it), from global
+// memory; the blocks take the listed bricks in turn.
 template <int D>
 __global__ void __launch_bounds__(kPushThreads) k_brick_push(DevTree t, BrickGeom g, BrickPushArgs a) {
-  for (int32_t b = blockIdx.x; b < g.n_bricks; b += gridDim.x) {
-    brick_push_fallback<D>(t, g, a, b);
+  const int32_t m = min(*a.st.over, (int32_t)g.n_bricks);
+  for (int32_t i = blockIdx.x; i < m; i += gridDim.x) {
+    brick_push_fallback<D>(t, g, a, a.st.over_bricks[i]);
     __syncthreads();
   }
 }
@@ -927,7 +930,10 @@ __global__ void __launch_bounds__(kStThreads, 2) k_brick_pull_st(DevTree t, Bric
   const int32_t L0 = b * K::LB + lf0;  // first leaf of the unit
   const int64_t n = a.n;
   const int32_t nin = st.fill[u];
-  if (nin > st.cap) return;  // the global-memory kernel takes this unit
+  if (nin > st.cap) {  // listed for the global-memory kernel
+    if (tid == 0) st.over_units[atomicAdd(&st.over[1], 1)] = u;
+    return;
+  }
   const int64_t at = (int64_t)u * st.cap;
   if (tid < 4) s_ccount[tid] = 0;
   if (tid == 0) {
@@ -1277,12 +1283,14 @@ __device__ __forceinline__ void brick_pull_fallback(const DevTree &t, const Bric
   }
 }
 
-// Destination units whose arrivals overflow their staging area, from global
-// memory; the blocks take units in turn and pass over the others at once.
+// Destination units whose arrivals overflow their staging area (listed by
+// the shared-memory kernel), from global memory; the blocks take the listed
+// units in turn.
 template <int D>
 __global__ void __launch_bounds__(kPullThreads) k_brick_pull(DevTree t, BrickGeom g, BrickPullArgs a) {
-  for (int32_t u = blockIdx.x; u < 2 * g.n_bricks; u += gridDim.x) {
-    brick_pull_fallback<D>(t, g, a, u);
+  const int32_t m = min(a.st.over[1], (int32_t)(2 * g.n_bricks));
+  for (int32_t i = blockIdx.x; i < m; i += gridDim.x) {
+    brick_pull_fallback<D>(t, g, a, a.st.over_units[i]);
     __syncthreads();
   }
 }
@@ -1300,6 +1308,7 @@ __global__ void k_expand_leaves(const int32_t *start, int64_t n_leaves, int32_t 
 void launch_brick_push(const DevTree &t, const BrickGeom &g, const BrickPushArgs &pa, cudaStream_t s) {
   cudaMemsetAsync(pa.st.fill, 0, sizeof(int32_t) * 2 * g.n_bricks, s);
   cudaMemsetAsync(pa.st.ovf_n, 0, sizeof(int32_t), s);
+  cudaMemsetAsync(pa.st.over, 0, 2 * sizeof(int32_t), s);
   const unsigned nb = (unsigned)g.n_bricks;
   const bool al = pa.n % 4 == 0;
   const unsigned np = std::min(2 * nb, kPersistBlocks);

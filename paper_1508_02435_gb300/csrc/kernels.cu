@@ -450,13 +450,21 @@ __device__ __forceinline__ void add_runs(int32_t *count, int32_t key, bool act) 
   }
 }
 
-// Bucket counts (per run of equal keys), mover ballot word and per-block
-// mover count.
+// Bucket counts, mover ballot word and per-block mover count.  kRuns: one
+// atomic per run of equal adjacent keys (3D, where most particles of a warp
+// take distinct new keys); else one per distinct key of the warp (2D, where
+// repeats of a key are often apart; measured faster on each).
+template <bool kRuns>
 __device__ __forceinline__ void count_and_ballot(bool act, int32_t knew, bool moved, int32_t *count,
                                                  uint32_t *mover_words, int32_t *block_movers) {
   const unsigned full = 0xffffffffu;
   int lane = threadIdx.x & 31;
-  add_runs(count, knew, act);
+  if (kRuns) {
+    add_runs(count, knew, act);
+  } else {
+    const unsigned peers = __match_any_sync(full, act ? knew : -1);
+    if (act && lane == __ffs(peers) - 1) atomicAdd(&count[knew], __popc(peers));
+  }
   unsigned mv = __ballot_sync(full, act && moved);
   int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (lane == 0) mover_words[gw] = mv;
@@ -587,9 +595,9 @@ __global__ void k_push64(DevTree t, Push64Args a) {
     } else {
       a.tleaf[p] = L2;
     }
-    a.keyn[p] = knew;  // PIT: the leaf (the key array is the leaf array)
+    if (a.rec || t.scheme != 0) a.keyn[p] = knew;  // PIT rows: the key array is the leaf array
   }
-  count_and_ballot(act, knew, moved, a.count, a.mover_words, a.block_movers);
+  count_and_ballot<D == 3>(act, knew, moved, a.count, a.mover_words, a.block_movers);
 }
 
 template <int D>
@@ -712,9 +720,9 @@ __global__ void __launch_bounds__(512, 3) k_push32(DevTree t, Push32Args a) {
       for (int ax = 0; ax < d; ++ax) a.to[ax * n + p] = o2[ax];
       a.tleaf[p] = L2;
     }
-    a.keyn[p] = knew;  // PIT: the leaf (the key array is the leaf array)
+    if (a.rec || t.scheme != 0) a.keyn[p] = knew;  // PIT rows: the key array is the leaf array
   }
-  count_and_ballot(act, knew, moved, a.count, a.mover_words, a.block_movers);
+  count_and_ballot<D == 3>(act, knew, moved, a.count, a.mover_words, a.block_movers);
 }
 
 // Key counts of freshly converted particles (every particle a mover).
@@ -723,7 +731,7 @@ __global__ void k_count_all(const int32_t *key, int64_t n, int32_t *count, uint3
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool act = p < n;
   int32_t k = act ? key[p] : 0;
-  count_and_ballot(act, k, true, count, mover_words, block_movers);
+  count_and_ballot<false>(act, k, true, count, mover_words, block_movers);
 }
 
 // ---------------------------------------------------------------------------

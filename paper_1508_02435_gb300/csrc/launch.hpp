@@ -87,6 +87,9 @@ struct BrickStage {
   uint32_t *key;                 // moved << 31 | storage index before the step (canonical order)
   int32_t *id;                   // particle ids (tracked ids only)
   int32_t *fill;                 // [2 n_bricks] arrivals per destination unit (may exceed cap)
+  int32_t *over;                 // [2] bricks listed for the global-memory K1, units for the global-memory K2
+  int32_t *over_bricks;          // [n_bricks] bricks over the shared-memory K1's capacity (any order)
+  int32_t *over_units;           // [2 n_bricks] units over their staging capacity (any order)
   int32_t *ovf_n;                // overflow count
   int32_t ovf_cap;
   int32_t *ovf_dest;             // [ovf_cap] destination unit

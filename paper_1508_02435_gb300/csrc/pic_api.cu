@@ -747,6 +747,9 @@ int setup_brick(pic_t h) {
   if ((rc = dalloc(h, bb, &st.key, st.row))) return rc;
   if (h->cfg.track_ids && (rc = dalloc(h, bb, &st.id, st.row))) return rc;
   if ((rc = dalloc(h, bb, &st.fill, nu))) return rc;
+  if ((rc = dalloc(h, bb, &st.over, 2))) return rc;
+  if ((rc = dalloc(h, bb, &st.over_bricks, g.n_bricks))) return rc;
+  if ((rc = dalloc(h, bb, &st.over_units, nu))) return rc;
   // the field laid out brick by brick, one vector per vertex of the brick
   // and its upper faces ((9+1)^d vertices), refreshed whenever E changes
   if ((rc = dalloc(h, bb, &h->ebrick, g.n_bricks * (t.d == 3 ? 1000 * 4 : 100 * 2)))) return rc;
