@@ -299,7 +299,7 @@ __device__ __noinline__ SlowOut relocate_slow(const DevTree &t, const BrickGeom 
 // order); bricks with more than 2 kHalfCap particles take k_brick_push.
 constexpr int kHThreads = 512;
 constexpr int kUnitSlots = 56;       // destination units by direction: 27 neighbour bricks x 2 halves (+ pad)
-constexpr int kHalfCap = 3040;       // particles of one half held in shared memory
+constexpr int kHalfCap = 3200;       // particles of one half held in shared memory (two CTAs still fit an SM)
 constexpr int kHS = kHalfCap + 8;    // shared row stride (room for a 16-byte aligned head)
 
 // First storage offset (within the brick) of half h of a brick holding nb particles.

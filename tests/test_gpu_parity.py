@@ -225,8 +225,9 @@ def test_device_inputs_and_determinism():
 @pytest.mark.parametrize("d,depth,n,vmax", [(2, 4, 150_001, 2.0), (3, 3, 120_001, 0.3),
                                             (3, 4, 200_003, 2.0), (2, 3, 11_664, 0.05),
                                             (2, 3, 150_001, 0.3),     # every brick over the on-chip capacity
-                                            (3, 3, 193_536, 0.3),     # bricks on both sides of it
-                                            (3, 3, 164_160, 0.3)])    # half-brick capacity crossed both ways
+                                            (3, 3, 193_536, 0.3),     # every brick over it (27 bricks of 7,168)
+                                            (3, 3, 170_100, 0.3),     # about one brick in ten over it
+                                            (3, 3, 172_800, 0.3)])    # bricks at the capacity (2 x 3,200) on both sides
 def test_brick_path_bit_identical_to_generic(d, depth, n, vmax):
     """Same state, bucket offsets and ids after several steps, with particles
     that stay, move to neighbour bricks and tunnel across several bricks."""
